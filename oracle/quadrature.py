@@ -1,0 +1,55 @@
+"""Quadrature rules on segments, triangles and convex polygons (FP64).
+
+The paper does not fix a quadrature (Sec. 3 only says the forms are integrated
+on polytopal elements).  The rules here: Gauss-Legendre on segments; on a
+triangle the collapsed (Duffy) tensor rule x(s,t) = A + s(B-A) + s t (C-B)
+with Jacobian 2|T| s; on a convex polygon the fan of triangles
+(v0, v_k, v_{k+1}).  With n points per direction a triangle rule integrates
+polynomials of total degree 2n-2 exactly; n = p + 1 makes the mass, stiffness
+and coarse-transfer integrands exact.
+
+Pins (tests/test_oracle_quadrature.py): exact monomial integrals over
+polygons via the divergence theorem, and Gauss-Legendre nodes against the
+closed forms for n = 1..3.
+"""
+import numpy as np
+
+
+def gauss_legendre_01(n: int):
+    """n-point Gauss-Legendre nodes and weights on [0, 1] (library routine)."""
+    t, w = np.polynomial.legendre.leggauss(n)
+    return 0.5 * (t + 1.0), 0.5 * w
+
+
+def segment_rule(a, b, n: int):
+    """Nodes [n, 2] and weights [n] on the segment from a to b (weights sum to |b-a|)."""
+    s, w = gauss_legendre_01(n)
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    pts = a[None, :] + s[:, None] * (b - a)[None, :]
+    return pts, w * np.linalg.norm(b - a)
+
+
+def triangle_rule(A, B, C, n: int):
+    """Collapsed tensor rule with n x n points on triangle ABC (any orientation)."""
+    s, ws = gauss_legendre_01(n)
+    A, B, C = (np.asarray(v, float) for v in (A, B, C))
+    twice_area = abs((B[0] - A[0]) * (C[1] - A[1]) - (B[1] - A[1]) * (C[0] - A[0]))
+    pts, wts = [], []
+    for i in range(n):          # s: from A towards edge BC
+        for j in range(n):      # t: along the edge at parameter s
+            x = A + s[i] * (B - A) + s[i] * s[j] * (C - B)
+            pts.append(x)
+            wts.append(ws[i] * ws[j] * s[i] * twice_area)
+    return np.asarray(pts), np.asarray(wts)
+
+
+def polygon_rule(P, n: int):
+    """Fan rule on the convex polygon with vertices P [m, 2] (triangles v0, v_k, v_{k+1})."""
+    P = np.asarray(P, float)
+    pts, wts = [], []
+    for k in range(1, len(P) - 1):
+        x, w = triangle_rule(P[0], P[k], P[k + 1], n)
+        pts.append(x)
+        wts.append(w)
+    return np.concatenate(pts), np.concatenate(wts)

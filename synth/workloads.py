@@ -1,0 +1,76 @@
+"""Named synthetic workloads: meshes, partitions, coefficients and parameters.
+
+Each workload is plain data.  The two named ones mirror the paper's test
+setting (a 2D unit square with polygonal elements, nested agglomerates as
+subdomains and coarse cells) at the sizes the solver is measured on.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .meshes import (Mesh, cartesian_square, voronoi_square, block_partition,
+                     kmeans_partition, fibre_conductivity, isotropic_conductivity)
+
+
+@dataclass
+class Workload:
+    name: str
+    mesh: Mesh
+    p: int                     # fine polynomial degree
+    q: int                     # coarse polynomial degree
+    sigma: np.ndarray          # [nc, 2, 2] per-cell conductivity
+    subdomain: np.ndarray      # [nc] int32 subdomain id per cell
+    coarse: np.ndarray         # [nc] int32 coarse agglomerate id per cell
+    eta0: float = 10.0
+    dt: float = 0.1
+    chi_cm: float = 1.0
+    rtol: float = 1e-8
+    n_steps: int = 1
+    u_rest: float = -67.0
+    stimulus: dict = field(default_factory=dict)
+
+
+def random_rhs(n: int, seed: int) -> np.ndarray:
+    """Seeded standard-normal vector of length n (float64)."""
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal(n)
+
+
+def stimulus_params(seed: int, amplitude: float = 250.0, width: float = 0.05,
+                    duration: float = 1.0) -> dict:
+    """Gaussian external current I = A exp(-|x-x0|^2 / (2 w^2)) while t < duration."""
+    x0 = 0.25 + 0.5 * np.random.Generator(np.random.PCG64(seed)).random(2)
+    return {"x0": float(x0[0]), "y0": float(x0[1]), "amplitude": amplitude,
+            "width": width, "duration": duration}
+
+
+def square16_p2() -> Workload:
+    """16x16 unit-square Cartesian mesh, P2, sigma = 1, 4x4 subdomains of 4x4 cells,
+    coarse P1 on the subdomains, one step dt = 0.1, eta0 = 10."""
+    mesh = cartesian_square(16)
+    part = block_partition(16, 4)
+    return Workload("square16_p2", mesh, p=2, q=1,
+                    sigma=isotropic_conductivity(mesh.n_cells, 1.0),
+                    subdomain=part, coarse=part.copy(), eta0=10.0, dt=0.1,
+                    rtol=1e-10)
+
+
+def voronoi4096_p3(n_cells: int = 4096, seed: int = 2, n_parts: int = 64,
+                   n_steps: int = 200) -> Workload:
+    """Voronoi mesh of n_cells (5 Lloyd steps), P3, anisotropic fibre conductivity
+    (sigma_l 1.3, sigma_t 0.2), k-means subdomains = coarse cells, dt = 0.05 ms."""
+    mesh = voronoi_square(n_cells, seed, lloyd=5)
+    part = kmeans_partition(mesh, n_parts, seed)
+    return Workload(f"voronoi{n_cells}_p3", mesh, p=3, q=1,
+                    sigma=fibre_conductivity(mesh, 1.3, 0.2, seed),
+                    subdomain=part, coarse=part.copy(), eta0=10.0, dt=0.05,
+                    rtol=1e-8, n_steps=n_steps, stimulus=stimulus_params(seed))
+
+
+def make_workload(name: str, **kw) -> Workload:
+    if name == "square16_p2":
+        return square16_p2()
+    if name.startswith("voronoi"):
+        return voronoi4096_p3(**kw)
+    raise KeyError(name)
