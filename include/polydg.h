@@ -1,0 +1,204 @@
+/*
+ * polydg.h -- C ABI of the GB300 PolyDG monodomain solver library (libpolydg.so).
+ *
+ * The library computes, on one NVIDIA GB300 (sm_103a), the time step of the
+ * PolyDG-discretised monodomain + Barreto-Cressman model of arXiv 2512.19536:
+ *
+ *   polydg_setup     Sec. 3 (Eq. eta, Eq. coer): SIP-DG assembly of M_h, A_h and
+ *                    K_h = chi_m C_m M_h + dt/2 A_h on a polygonal mesh, plus the
+ *                    subdomain partition T_S of Sec. 4.
+ *   asm_setup        Sec. 4: local matrices K_i = R_i K_h R_i^T, the coarse space
+ *                    V_0 = P^q on the agglomerates of T_H with R_0^T the L2
+ *                    projection, K_0 = R_0 K_h R_0^T, and their factorisations.
+ *   asm_apply        Eq. prec: z = B_ad^{-1} r = sum_{i=0}^{N} R_i^T K_i^{-1} R_i r.
+ *   pcg_solve        Sec. 4/5: PCG on K_h x = b with B_ad^{-1}, stopping when
+ *                    |r|_2 <= rtol |b|_2 (Euclidean norm of the relative residual).
+ *   monodomain_step  Eq. fully-discrete-1: explicit ionic update at the element
+ *                    quadrature nodes, right-hand side, PCG solve, per time step.
+ *
+ * Conventions shared by every call:
+ *   - All integer arguments and host arrays are read during the call only; the
+ *     library copies what it keeps.  Contexts are owned by the library and are
+ *     released only by the matching *_destroy call.
+ *   - Vectors passed as `*_dev` are caller-owned DEVICE pointers (e.g. from
+ *     torch.Tensor.data_ptr()) to contiguous float64 arrays of n_dofs entries,
+ *     laid out element-major in the CALLER's cell order: entry c * n_p + j is
+ *     the coefficient of basis function j on cell c.  They must not alias
+ *     each other unless stated.
+ *   - Basis (the paper fixes none): on cell c with axis-aligned bounding box
+ *     [x0,x1]x[y0,y1], phi_(a,b) = L_a(xi) L_b(eta), a + b <= p, L_n the Legendre
+ *     polynomials, xi = (2x-x0-x1)/(x1-x0), eta likewise; ordered by total
+ *     degree, then by increasing b.  n_p = (p+1)(p+2)/2.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; calls that return statistics synchronise it.
+ *   - Every function returns POLYDG_OK (0) or a negative status; the text of
+ *     the last error of the calling thread is available from polydg_last_error.
+ *   - A context is not thread-safe: do not call into one context concurrently.
+ */
+#ifndef POLYDG_H
+#define POLYDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define POLYDG_OK           0
+#define POLYDG_EINVAL      -1   /* bad argument (null pointer, size, degree, mesh) */
+#define POLYDG_ENOMEM      -2   /* device or host allocation failed */
+#define POLYDG_ECUDA       -3   /* a CUDA runtime call failed */
+#define POLYDG_ENOTSPD     -4   /* non-positive pivot in a Cholesky factorisation */
+#define POLYDG_ENOTCONV    -5   /* maxit reached; outputs hold the last iterate */
+#define POLYDG_EBREAKDOWN  -6   /* p^T K p <= 0 or a non-finite PCG coefficient */
+#define POLYDG_ENONFINITE  -7   /* NaN/Inf in an input vector or the residual */
+
+/* ---- storage precision of the local subdomain inverses (asm_setup) --------- */
+#define POLYDG_FP64  0          /* float64 store, float64 arithmetic            */
+#define POLYDG_FP32  1          /* float32 store, float32 arithmetic            */
+#define POLYDG_BF16  2          /* bfloat16 store, float32 accumulation         */
+
+typedef struct polydg_ctx polydg_ctx;
+typedef struct asm_ctx asm_ctx;
+typedef struct sim_ctx sim_ctx;
+
+/* A 2D polygonal mesh (Sec. 3: T_h, disjoint polygons).  Cells are convex
+ * polygons given as counter-clockwise vertex loops in CSR form; two cells
+ * share an interior face exactly when an edge's two vertex ids appear in both
+ * loops.  Edges used by one cell only are boundary faces (homogeneous Neumann,
+ * Eq. monodomain).  sigma holds the piecewise-constant conductivity tensor
+ * Sigma_K (Sec. 2) of each cell, row-major 2x2, symmetric positive definite. */
+typedef struct {
+    int64_t        n_vertices;
+    const double  *vertices;   /* [n_vertices * 2] host, (x, y) pairs        */
+    int64_t        n_cells;
+    const int64_t *cell_ptr;   /* [n_cells + 1] host, cell_ptr[0] = 0        */
+    const int32_t *cell_vtx;   /* [cell_ptr[n_cells]] host, CCW vertex loops */
+    const double  *sigma;      /* [n_cells * 4] host                         */
+} polydg_mesh;
+
+typedef struct {
+    int64_t n_cells;
+    int64_t n_dofs;            /* n_cells * n_p                              */
+    int64_t n_faces;           /* interior faces                             */
+    int64_t n_blocks;          /* n_p x n_p blocks of K_h (n_cells + 2 n_faces) */
+    int64_t n_nodes;           /* element quadrature nodes (ionic state)     */
+    int32_t p;
+    int32_t n_p;
+    int32_t n_subdomains;
+    int32_t max_subdomain_dofs;
+} polydg_info;
+
+typedef struct {
+    int32_t iterations;        /* PCG iterations taken                       */
+    int32_t status;            /* POLYDG_OK, ENOTCONV, EBREAKDOWN, ENONFINITE */
+    double  relres;            /* |r_k|_2 / |b|_2 at exit (recurrence residual) */
+    double  bnorm;             /* |b|_2                                      */
+} pcg_stats;
+
+/* Parameters of a coupled simulation (Eq. monodomain, Eq. fully-discrete-1).
+ * Initial potential u^0 = u0 (constant), ionic state y^0 = the model's rest
+ * state at u0.  External current I_ext(x, t) = stim_amplitude *
+ * exp(-|x - (stim_x0, stim_y0)|^2 / (2 stim_width^2)) while t < stim_duration,
+ * evaluated at the Crank-Nicolson midpoint t^{k+1/2}.  Each step's PCG starts
+ * from U^k and stops at |r|_2 <= rtol |b|_2. */
+typedef struct {
+    double  u0;
+    double  stim_x0, stim_y0, stim_amplitude, stim_width, stim_duration;
+    double  rtol;
+    int32_t maxit;
+    int32_t flexible;          /* 1: flexible PCG (required with FP32/BF16 local inverses) */
+} sim_params;
+
+typedef struct {
+    int64_t steps_done;        /* steps completed by this call               */
+    int64_t total_iterations;  /* PCG iterations summed over those steps     */
+    int32_t max_iterations;    /* largest per-step PCG iteration count       */
+    int32_t status;            /* first non-OK PCG status, else POLYDG_OK    */
+    double  last_relres;       /* relative residual of the last step's solve */
+} step_stats;
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char *polydg_last_error(void);
+
+/* Assemble K_h (Sec. 3, Eq. eta with Sigma_K read as lambda_max(Sigma_K), Eq. coer)
+ * for degree p (1..6) on `mesh`, with interior-penalty constant eta0 > 0,
+ * chi_cm = chi_m C_m > 0 and time step dt > 0, and record the subdomain
+ * partition T_S (Sec. 4): subdomain_of_cell[c] in [0, n_subdomains), every id
+ * used.  Cells are renumbered internally so each subdomain is contiguous; the
+ * caller never sees that order.  Uploads K_h (block-sparse, float64) and the
+ * quadrature-node tables to the current CUDA device.  Errors: EINVAL for an
+ * invalid mesh (non-matching edges, non-convex or clockwise cell, bad sigma),
+ * ENOMEM, ECUDA. */
+int polydg_setup(const polydg_mesh *mesh, int p, const int32_t *subdomain_of_cell,
+                 double chi_cm, double dt, double eta0, polydg_ctx **out);
+
+int polydg_get_info(const polydg_ctx *ctx, polydg_info *out);
+
+/* Interior faces as (K+, K-) caller cell ids with K+ < K-, sorted
+ * lexicographically; plus/minus are host arrays of n_faces entries. */
+int polydg_get_faces(const polydg_ctx *ctx, int64_t *plus, int64_t *minus);
+
+/* y = K_h x (float64, caller order).  x_dev and y_dev must not alias. */
+int polydg_matvec(polydg_ctx *ctx, const double *x_dev, double *y_dev, void *stream);
+
+/* Build the two-level additive Schwarz preconditioner of Eq. prec on the
+ * subdomains given to polydg_setup.  coarse_of_cell (host, [n_cells]) assigns
+ * every cell to an agglomerate of T_H (ids 0..N_0-1, all used); NULL builds
+ * the one-level operator (no coarse space).  q (1 <= q <= p) is the coarse
+ * degree.  The local inverses K_i^{-1} are formed in float64 on the device by
+ * Cholesky factorisation and stored in `precision` (POLYDG_FP64/FP32/BF16);
+ * the coarse inverse K_0^{-1} is always float64.  R_0 is the Euclidean
+ * transpose of R_0^T, so B_ad is symmetric.  Errors: EINVAL, ENOTSPD, ENOMEM,
+ * ECUDA. */
+int asm_setup(polydg_ctx *ctx, const int32_t *coarse_of_cell, int q, int precision,
+              asm_ctx **out);
+
+/* z = B_ad^{-1} r (Eq. prec).  r_dev and z_dev are caller-order device vectors
+ * and must not alias. */
+int asm_apply(asm_ctx *pc, const double *r_dev, double *z_dev, void *stream);
+
+/* Solve K_h x = b by PCG (Saad Alg. 9.1) with B_ad^{-1} (pc != NULL) or without
+ * preconditioner (pc == NULL: plain CG).  x_dev holds x0 on entry and the
+ * solution on exit.  flexible = 1 takes beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k).
+ * The iteration runs on the device (captured CUDA graph with a device-side
+ * loop); the call synchronises `stream` and fills *stats (may be NULL).
+ * Returns POLYDG_OK, ENOTCONV (x holds the last iterate), EBREAKDOWN,
+ * ENONFINITE, EINVAL (rtol <= 0, maxit < 1), ECUDA.  b = 0 gives x = 0. */
+int pcg_solve(polydg_ctx *ctx, asm_ctx *pc, const double *b_dev, double *x_dev,
+              double rtol, int maxit, int flexible, void *stream, pcg_stats *stats);
+
+/* Create a coupled simulation on ctx/pc (pc may be NULL for plain CG). */
+int sim_create(polydg_ctx *ctx, asm_ctx *pc, const sim_params *params, sim_ctx **out);
+
+/* Advance nsteps Crank-Nicolson steps (Eq. fully-discrete-1).  Per step:
+ * y^{k+1} = y^k - dt m(u^k, y^k) at every quadrature node; I^{k+1} from
+ * u~ = 3/2 U^k - 1/2 U^{k-1} (U^0 on the first step) and y^{k+1}; b =
+ * (chi_cm M - dt/2 A) U^k - chi_cm dt I^{k+1} + dt F^{k+1/2}; PCG from U^k.
+ * Synchronises `stream`; *stats may be NULL.  Stops at the first step whose
+ * solve fails and returns that status. */
+int monodomain_step(sim_ctx *sim, int nsteps, void *stream, step_stats *stats);
+
+/* Copy the current potential U^k (caller order, [n_dofs]) to u_dev and, if
+ * y_dev != NULL, the ionic state ([5][n_nodes], nodes grouped by caller cell
+ * in increasing cell id, each cell's nodes in quadrature order) to y_dev. */
+int sim_get_state(sim_ctx *sim, double *u_dev, double *y_dev, void *stream);
+
+/* Overwrite U^k and U^{k-1} (caller order device vectors; uprev_dev may be
+ * NULL to use u_dev for both). */
+int sim_set_potential(sim_ctx *sim, const double *u_dev, const double *uprev_dev,
+                      void *stream);
+
+/* Current step index k. */
+int64_t sim_step_index(const sim_ctx *sim);
+
+void sim_destroy(sim_ctx *sim);
+void asm_destroy(asm_ctx *pc);
+void polydg_destroy(polydg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLYDG_H */

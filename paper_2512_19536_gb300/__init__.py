@@ -1,0 +1,16 @@
+"""GB300-native PolyDG monodomain solver: two-level additive Schwarz PCG (arXiv 2512.19536).
+
+The compute lives in ``libpolydg.so`` (hand-written sm_103a CUDA behind the C
+ABI of ``include/polydg.h``); this package is its ctypes binding.  Importing
+the package does not load the library; the first call does, and fails loudly
+if it has not been built.
+"""
+from ._native import (PolyDG, ASM, Simulation, PolyDGError, load, polydg_setup, asm_setup,
+                      asm_apply, pcg_solve, sim_create, monodomain_step, sim_get_state,
+                      sim_set_potential, EXPORTS, LIB_PATH, POLYDG_OK, POLYDG_EINVAL,
+                      POLYDG_ENOMEM, POLYDG_ECUDA, POLYDG_ENOTSPD, POLYDG_ENOTCONV,
+                      POLYDG_EBREAKDOWN, POLYDG_ENONFINITE)
+
+__all__ = ["PolyDG", "ASM", "Simulation", "PolyDGError", "load", "polydg_setup", "asm_setup",
+           "asm_apply", "pcg_solve", "sim_create", "monodomain_step", "sim_get_state",
+           "sim_set_potential", "EXPORTS", "LIB_PATH"]

@@ -1,0 +1,270 @@
+"""ctypes binding of libpolydg.so (include/polydg.h): argument marshalling only.
+
+Every computation happens in the library's CUDA kernels.  Device vectors are
+torch CUDA tensors (float64, contiguous, caller cell order); host arrays are
+numpy.  There is no fallback: if the shared library is missing, loading fails
+with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpolydg.so")
+
+POLYDG_OK, POLYDG_EINVAL, POLYDG_ENOMEM, POLYDG_ECUDA = 0, -1, -2, -3
+POLYDG_ENOTSPD, POLYDG_ENOTCONV, POLYDG_EBREAKDOWN, POLYDG_ENONFINITE = -4, -5, -6, -7
+POLYDG_FP64, POLYDG_FP32, POLYDG_BF16 = 0, 1, 2
+PRECISION = {"fp64": POLYDG_FP64, "fp32": POLYDG_FP32, "bf16": POLYDG_BF16}
+
+EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_get_info", "polydg_get_faces",
+           "polydg_matvec", "asm_setup", "asm_apply", "pcg_solve", "sim_create",
+           "monodomain_step", "sim_get_state", "sim_set_potential", "sim_step_index",
+           "sim_destroy", "asm_destroy", "polydg_destroy"]
+
+
+class polydg_mesh(C.Structure):
+    _fields_ = [("n_vertices", C.c_int64), ("vertices", C.POINTER(C.c_double)),
+                ("n_cells", C.c_int64), ("cell_ptr", C.POINTER(C.c_int64)),
+                ("cell_vtx", C.POINTER(C.c_int32)), ("sigma", C.POINTER(C.c_double))]
+
+
+class polydg_info(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("n_dofs", C.c_int64), ("n_faces", C.c_int64),
+                ("n_blocks", C.c_int64), ("n_nodes", C.c_int64), ("p", C.c_int32),
+                ("n_p", C.c_int32), ("n_subdomains", C.c_int32),
+                ("max_subdomain_dofs", C.c_int32)]
+
+
+class pcg_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("relres", C.c_double),
+                ("bnorm", C.c_double)]
+
+
+class sim_params(C.Structure):
+    _fields_ = [("u0", C.c_double), ("stim_x0", C.c_double), ("stim_y0", C.c_double),
+                ("stim_amplitude", C.c_double), ("stim_width", C.c_double),
+                ("stim_duration", C.c_double), ("rtol", C.c_double), ("maxit", C.c_int32),
+                ("flexible", C.c_int32)]
+
+
+class step_stats(C.Structure):
+    _fields_ = [("steps_done", C.c_int64), ("total_iterations", C.c_int64),
+                ("max_iterations", C.c_int32), ("status", C.c_int32),
+                ("last_relres", C.c_double)]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libpolydg.so and declare its signatures (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    L.polydg_last_error.restype = C.c_char_p
+    L.polydg_setup.argtypes = [C.POINTER(polydg_mesh), i32, C.POINTER(C.c_int32), dbl, dbl, dbl,
+                               C.POINTER(vp)]
+    L.polydg_get_info.argtypes = [vp, C.POINTER(polydg_info)]
+    L.polydg_get_faces.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.polydg_matvec.argtypes = [vp, vp, vp, vp]
+    L.asm_setup.argtypes = [vp, C.POINTER(C.c_int32), i32, i32, C.POINTER(vp)]
+    L.asm_apply.argtypes = [vp, vp, vp, vp]
+    L.pcg_solve.argtypes = [vp, vp, vp, vp, dbl, i32, i32, vp, C.POINTER(pcg_stats)]
+    L.sim_create.argtypes = [vp, vp, C.POINTER(sim_params), C.POINTER(vp)]
+    L.monodomain_step.argtypes = [vp, i32, vp, C.POINTER(step_stats)]
+    L.sim_get_state.argtypes = [vp, vp, vp, vp]
+    L.sim_set_potential.argtypes = [vp, vp, vp, vp]
+    L.sim_step_index.argtypes = [vp]
+    L.sim_step_index.restype = i64
+    for name in ("sim_destroy", "asm_destroy", "polydg_destroy"):
+        getattr(L, name).argtypes = [vp]
+        getattr(L, name).restype = None
+    for name in ("polydg_setup", "polydg_get_info", "polydg_get_faces", "polydg_matvec",
+                 "asm_setup", "asm_apply", "pcg_solve", "sim_create", "monodomain_step",
+                 "sim_get_state", "sim_set_potential"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+class PolyDGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def _check(status, allow=()):
+    if status != POLYDG_OK and status not in allow:
+        raise PolyDGError(status, load().polydg_last_error().decode())
+    return status
+
+
+def _ptr(a, dtype):
+    return a.ctypes.data_as(C.POINTER(dtype))
+
+
+def _dev(t):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class PolyDG:
+    """Handle of a polydg_ctx (assembled K_h on the device)."""
+
+    def __init__(self, handle):
+        self.h = handle
+        info = polydg_info()
+        _check(load().polydg_get_info(self.h, C.byref(info)))
+        self.info = info
+
+    @property
+    def n_dofs(self):
+        return self.info.n_dofs
+
+    def faces(self):
+        n = self.info.n_faces
+        plus = np.empty(n, np.int64)
+        minus = np.empty(n, np.int64)
+        _check(load().polydg_get_faces(self.h, _ptr(plus, C.c_int64), _ptr(minus, C.c_int64)))
+        return plus, minus
+
+    def matvec(self, x, y, stream=None):
+        _check(load().polydg_matvec(self.h, _dev(x), _dev(y), _stream(stream)))
+
+    def close(self):
+        if self.h:
+            load().polydg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def polydg_setup(vertices, cell_ptr, cell_vtx, sigma, p, subdomain_of_cell, chi_cm=1.0,
+                 dt=0.1, eta0=10.0) -> PolyDG:
+    v = np.ascontiguousarray(vertices, np.float64)
+    cp = np.ascontiguousarray(cell_ptr, np.int64)
+    cv = np.ascontiguousarray(cell_vtx, np.int32)
+    sg = np.ascontiguousarray(sigma, np.float64).reshape(-1)
+    sub = np.ascontiguousarray(subdomain_of_cell, np.int32)
+    m = polydg_mesh(len(v), _ptr(v, C.c_double), len(cp) - 1, _ptr(cp, C.c_int64),
+                    _ptr(cv, C.c_int32), _ptr(sg, C.c_double))
+    h = C.c_void_p()
+    _check(load().polydg_setup(C.byref(m), int(p), _ptr(sub, C.c_int32), float(chi_cm),
+                               float(dt), float(eta0), C.byref(h)))
+    return PolyDG(h)
+
+
+class ASM:
+    """Handle of an asm_ctx (two-level additive Schwarz preconditioner)."""
+
+    def __init__(self, ctx, handle, precision):
+        self.ctx, self.h, self.precision = ctx, handle, precision
+
+    def close(self):
+        if self.h:
+            load().asm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def asm_setup(ctx: PolyDG, coarse_of_cell=None, q=1, precision="fp64") -> ASM:
+    h = C.c_void_p()
+    if coarse_of_cell is None:
+        cptr = None
+    else:
+        coarse = np.ascontiguousarray(coarse_of_cell, np.int32)
+        cptr = _ptr(coarse, C.c_int32)
+    _check(load().asm_setup(ctx.h, cptr, int(q), PRECISION[precision], C.byref(h)))
+    return ASM(ctx, h, precision)
+
+
+def asm_apply(pc: ASM, r, z, stream=None):
+    _check(load().asm_apply(pc.h, _dev(r), _dev(z), _stream(stream)))
+
+
+def pcg_solve(ctx: PolyDG, pc, b, x, rtol=1e-8, maxit=10000, flexible=False, stream=None,
+              allow=(POLYDG_ENOTCONV,)):
+    st = pcg_stats()
+    status = load().pcg_solve(ctx.h, pc.h if pc is not None else None, _dev(b), _dev(x),
+                              float(rtol), int(maxit), int(bool(flexible)), _stream(stream),
+                              C.byref(st))
+    _check(status, allow)
+    return {"iterations": st.iterations, "status": st.status, "relres": st.relres,
+            "bnorm": st.bnorm}
+
+
+class Simulation:
+    """Handle of a sim_ctx (coupled monodomain + ionic state on the device)."""
+
+    def __init__(self, ctx, pc, handle):
+        self.ctx, self.pc, self.h = ctx, pc, handle
+
+    def close(self):
+        if self.h:
+            load().sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def step_index(self):
+        return load().sim_step_index(self.h)
+
+
+def sim_create(ctx: PolyDG, pc, u0=-67.0, stimulus=None, rtol=1e-8, maxit=10000,
+               flexible=False) -> Simulation:
+    s = stimulus or {"x0": 0.5, "y0": 0.5, "amplitude": 0.0, "width": 1.0, "duration": 0.0}
+    prm = sim_params(float(u0), s["x0"], s["y0"], s["amplitude"], s["width"], s["duration"],
+                     float(rtol), int(maxit), int(bool(flexible)))
+    h = C.c_void_p()
+    _check(load().sim_create(ctx.h, pc.h if pc is not None else None, C.byref(prm), C.byref(h)))
+    return Simulation(ctx, pc, h)
+
+
+def monodomain_step(sim: Simulation, nsteps=1, stream=None):
+    st = step_stats()
+    _check(load().monodomain_step(sim.h, int(nsteps), _stream(stream), C.byref(st)))
+    return {"steps_done": st.steps_done, "total_iterations": st.total_iterations,
+            "max_iterations": st.max_iterations, "status": st.status,
+            "last_relres": st.last_relres}
+
+
+def sim_get_state(sim: Simulation, u, y=None, stream=None):
+    _check(load().sim_get_state(sim.h, _dev(u), _dev(y) if y is not None else None,
+                                _stream(stream)))
+
+
+def sim_set_potential(sim: Simulation, u, uprev=None, stream=None):
+    _check(load().sim_set_potential(sim.h, _dev(u), _dev(uprev) if uprev is not None else None,
+                                    _stream(stream)))

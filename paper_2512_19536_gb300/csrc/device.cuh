@@ -1,0 +1,104 @@
+// Device-side data structures and helpers of libpolydg (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace polydg {
+
+constexpr int kBlock = 256;            // threads per CTA of the streaming kernels
+constexpr int kMaxPartials = 1 << 15;  // partial sums per reduction (>= max grid)
+
+// Scalars of one PCG solve, resident in device memory.  Reductions write
+// per-CTA partials; the last CTA of a launch (ticket counter) sums them in
+// CTA order, so every result is deterministic.
+struct PcgScalars {
+    double bb;        // |b|^2
+    double rr;        // |r_k|^2
+    double rz;        // r_k . z_k
+    double rz_old;
+    double zq;        // z_{k+1} . q_k (flexible beta)
+    double pq;        // p_k . K p_k
+    double alpha, beta;
+    double rtol2;     // rtol^2
+    double relres;
+    int32_t it, maxit, status, done, flexible, pad;
+    uint32_t ticket[8];
+};
+
+enum Ticket { T_MATVEC = 0, T_UPDATE = 1, T_PROLONG = 2, T_INIT = 3, T_IDENT = 4 };
+
+// status values mirrored from polydg.h
+constexpr int kOK = 0, kENOTSPD = -4, kENOTCONV = -5, kEBREAKDOWN = -6, kENONFINITE = -7;
+
+// One dense block of the ragged local/coarse solve (Eq. prec): out[out_off + i] =
+// sum_j A[i][j] in[in_off + j], A row-major with leading dimension ld (padded
+// with zeros to a multiple of 8 columns).  sel = 0: r/z vectors, 1: coarse r0/y0.
+struct GemvBlock {
+    int64_t mat_off;   // element offset into the store of this block's dtype
+    int64_t in_off, out_off;
+    int32_t n, ld;
+    int32_t sel;       // 0 local, 1 coarse
+    int32_t dtype;     // 0 fp64, 1 fp32, 2 bf16
+};
+
+struct GemvTile {
+    int32_t block;
+    int32_t row0;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the CTA; result valid in every thread.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Publish this CTA's partial(s) and return true in the last CTA to arrive.
+// In the last CTA, partials of all CTAs are visible after the call.
+__device__ __forceinline__ bool publish_partials(double* partials, const double* mine, int k,
+                                                 uint32_t* ticket, bool* sh_last) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < k; ++i) partials[i * kMaxPartials + blockIdx.x] = mine[i];
+        __threadfence();
+        const uint32_t t = atomicAdd(ticket, 1u);
+        *sh_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    const bool last = *sh_last;
+    if (last) __threadfence();
+    return last;
+}
+
+// Deterministic sum of partials[0..n) by one CTA (fixed order).
+__device__ __forceinline__ double sum_partials(const double* partials, int n, double* sh) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(partials + i);
+    return block_sum(v, sh);
+}
+
+__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+}  // namespace polydg

@@ -1,0 +1,146 @@
+// Per-quadrature-node ionic update and ion-current load of one Crank-Nicolson
+// step (Eq. fully-discrete-1), plus the per-step bookkeeping kernels.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "ionic_model.cuh"
+#include "kernels.h"
+
+namespace polydg {
+
+// Warp per cell: nodes of cell e are node_ptr[e]..node_ptr[e+1]-1.  Per node:
+//   u^k(x_q), y^{k+1} = y^k + dt y'(u^k, y^k),  u~ = 3/2 U^k - 1/2 U^{k-1} (U^0 at k = 0),
+//   I_e[i] = sum_q w_q f(u~(x_q), y^{k+1}_q) phi_i(x_q).
+template <int NP>
+__global__ void __launch_bounds__(256)
+ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
+             const int64_t* __restrict__ node_ptr, const double* __restrict__ node_w,
+             const double* __restrict__ node_phi, double* __restrict__ y, int64_t nn, int64_t nc,
+             double dt, double* __restrict__ I, const SimScalars* ss) {
+    if (ss->failed) return;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= nc) return;
+    const bool first = (ss->k == 0);
+    double Ue[NP], Ux[NP], acc[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        Ue[j] = U[e * NP + j];
+        Ux[j] = first ? Ue[j] : 1.5 * Ue[j] - 0.5 * Uprev[e * NP + j];
+        acc[j] = 0.0;
+    }
+    const int64_t q1 = node_ptr[e + 1];
+    for (int64_t q = node_ptr[e] + lane; q < q1; q += 32) {
+        const double* ph = node_phi + q * NP;
+        double phv[NP];
+        double uk = 0.0, ux = 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            phv[j] = ph[j];
+            uk = fma(phv[j], Ue[j], uk);
+            ux = fma(phv[j], Ux[j], ux);
+        }
+        double n = y[q], h = y[nn + q], Ko = y[2 * nn + q], Nai = y[3 * nn + q], Cai = y[4 * nn + q];
+        bc::euler(uk, dt, n, h, Ko, Nai, Cai);    // explicit Euler with u^k
+        y[q] = n; y[nn + q] = h; y[2 * nn + q] = Ko; y[3 * nn + q] = Nai; y[4 * nn + q] = Cai;
+        const bc::Currents c = bc::currents(ux, n, h, Ko, Nai, Cai);
+        const double wf = node_w[q] * (c.INa + c.IK + c.ICl);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[j] = fma(wf, phv[j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const double s = warp_sum(acc[j]);
+        if (lane == 0) I[e * NP + j] = s;
+    }
+}
+
+cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int64_t* node_ptr,
+                         const double* node_w, const double* node_phi, double* y, int64_t nn,
+                         int64_t nc, double dt, double* I, const SimScalars* ss, cudaStream_t s) {
+    const unsigned g = (unsigned)((nc * 32 + 255) / 256);
+    switch (np) {
+        case 3: ionic_kernel<3><<<g, 256, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss); break;
+        case 6: ionic_kernel<6><<<g, 256, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss); break;
+        case 10: ionic_kernel<10><<<g, 256, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss); break;
+        case 15: ionic_kernel<15><<<g, 256, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// y_caller[pos[q]][s] = y_int[q][s] for the 5 state rows.
+__global__ void node_gather_kernel(const double* __restrict__ yi, double* __restrict__ yc,
+                                   const int64_t* __restrict__ pos, int64_t nn) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nn) return;
+    const int64_t d = pos[q];
+#pragma unroll
+    for (int s = 0; s < 5; ++s) yc[s * nn + d] = yi[s * nn + q];
+}
+
+cudaError_t launch_node_gather(const double* y_int, double* y_caller,
+                               const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s) {
+    node_gather_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(y_int, y_caller,
+                                                                   node_to_caller_pos, nn);
+    return cudaGetLastError();
+}
+
+__global__ void init_y_kernel(double* y, int64_t nn, const double* y0) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nn) return;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) y[s * nn + q] = y0[s];
+}
+
+cudaError_t launch_init_y(double* y, int64_t nn, const double* y0, cudaStream_t s) {
+    init_y_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(y, nn, y0);
+    return cudaGetLastError();
+}
+
+// Reset the PCG scalars at the start of a step (no-op after a failed step).
+__global__ void step_begin_kernel(PcgScalars* sc, const SimScalars* ss) {
+    if (threadIdx.x != 0) return;
+    sc->done = ss->failed ? 1 : 0;
+    sc->it = 0;
+    sc->status = 0;
+}
+
+cudaError_t launch_step_begin(PcgScalars* sc, const SimScalars* ss, cudaStream_t s) {
+    step_begin_kernel<<<1, 32, 0, s>>>(sc, ss);
+    return cudaGetLastError();
+}
+
+// U^{k-1} <- U^k, U^k <- x, k <- k + 1 and the step statistics.
+__global__ void step_finish_kernel(double* __restrict__ U, double* __restrict__ Uprev,
+                                   const double* __restrict__ x, int64_t n,
+                                   const PcgScalars* sc, SimScalars* ss) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = !ss->failed;
+    if (ok && t < n) {
+        Uprev[t] = U[t];
+        U[t] = x[t];
+    }
+}
+
+__global__ void step_stats_kernel(const PcgScalars* sc, SimScalars* ss) {
+    if (threadIdx.x != 0 || ss->failed) return;
+    ss->k += 1;
+    ss->steps_done += 1;
+    ss->total_its += sc->it;
+    if (sc->it > ss->max_its) ss->max_its = sc->it;
+    ss->last_relres = sc->relres;
+    if (sc->status != 0) {
+        ss->status = sc->status;
+        ss->failed = 1;
+    }
+}
+
+cudaError_t launch_step_finish(double* U, double* Uprev, const double* x, int64_t n,
+                               const PcgScalars* sc, SimScalars* ss, cudaStream_t s) {
+    step_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, Uprev, x, n, sc, ss);
+    step_stats_kernel<<<1, 32, 0, s>>>(sc, ss);
+    return cudaGetLastError();
+}
+
+}  // namespace polydg
