@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark: ASM-PCG time-steps/s on the coupled PolyDG monodomain + Barreto-Cressman
+workload (4096-cell Voronoi mesh of the unit square, P3, anisotropic fibre
+conductivity, 64 k-means subdomains = coarse agglomerates, coarse P1, dt = 0.05 ms,
+Gaussian stimulus), every step solved by PCG with the two-level additive Schwarz
+preconditioner to |r|_2 <= 1e-8 |b|_2 on one GB300.
+
+A "step" is one Crank-Nicolson time step through the C ABI (monodomain_step):
+ionic update at the quadrature nodes, right-hand side, and the persistent PCG
+kernel.  Two forms are timed on the same trajectory setup:
+  * mixed: fp32 local inverses in flexible PCG (fp64 residual, dots, coarse solve
+    and matvec) -- the reported value;
+  * fp64 plain: fp64 local inverses in standard PCG -- reported beside it.
+The working set (fp32 store 112 MB + K_h 22.5 MB + vectors) exceeds the 126 MB
+L2, so no L2 flush is inserted between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (the path has no
+exchange step); rank 0 prints one JSON line with the whole-job throughput.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ASM-PCG time-steps/s at rel.res 1e-8, mixed+learned vs FP64 plain, 1 GB300"
+WORKLOAD = "voronoi4096_p3 coupled monodomain+Barreto-Cressman, 40960 DOFs, 64 subdomains, coarse P1"
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, dev):
+        self.dev, self.proc, self.lines = dev, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                mhz.append(float(f[0]))
+                mx = float(f[1])
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "samples": len(mhz), "reasons": sorted(reasons)}
+
+
+def build_case():
+    from synth import voronoi4096_p3
+    return voronoi4096_p3()
+
+
+def algorithmic_bytes(ctx_info, pc_info, iterations, launches):
+    """Bytes one PCG launch must move (per iteration: K_h blocks, the local inverse
+    store, K_0^{-1}, the rows of R_0 and ~12 fp64 vector streams; plus one K_h pass
+    and 4 vector streams for the initial residual)."""
+    n = ctx_info.n_dofs
+    k_bytes = 8 * ctx_info.n_p ** 2 * ctx_info.n_blocks
+    per_it = (k_bytes + pc_info["local_store_bytes"] + pc_info["coarse_bytes"]
+              + pc_info["restrict_bytes"] + 12 * 8 * n)
+    return iterations * per_it + launches * (k_bytes + 4 * 8 * n)
+
+
+def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clocks=None):
+    pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision=precision)
+    sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-8, maxit=5000,
+                        flexible=flexible)
+    pd.monodomain_step(sim, warmup, stream)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.__enter__()
+    ev0.record(stream)
+    st = pd.monodomain_step(sim, steps, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.__exit__(None, None, None)
+    ms = ev0.elapsed_time(ev1)
+    return pc, sim, st, ms
+
+
+def time_e2e(pd, torch, w, ctx, pc, steps, stream):
+    """Same metric with the potential crossing the host boundary every step: U^k and
+    U^{k-1} copied in from pinned host memory, U^{k+1} copied back to pinned host."""
+    sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-8, maxit=5000,
+                        flexible=True)
+    n = ctx.n_dofs
+    host_u = torch.empty(n, dtype=torch.float64).pin_memory()
+    host_uprev = torch.empty(n, dtype=torch.float64).pin_memory()
+    dev_u = torch.empty(n, dtype=torch.float64, device="cuda")
+    dev_uprev = torch.empty(n, dtype=torch.float64, device="cuda")
+    pd.monodomain_step(sim, 2, stream)
+    pd.sim_get_state(sim, dev_u, stream=stream)
+    host_u.copy_(dev_u)
+    host_uprev.copy_(dev_u)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dev_u.copy_(host_u, non_blocking=True)
+        dev_uprev.copy_(host_uprev, non_blocking=True)
+        pd.sim_set_potential(sim, dev_u, dev_uprev, stream)
+        pd.monodomain_step(sim, 1, stream)
+        host_uprev.copy_(host_u)
+        pd.sim_get_state(sim, dev_u, stream=stream)
+        host_u.copy_(dev_u, non_blocking=True)
+        torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    sim.close()
+    return steps / dt, 2 * 8 * n, 8 * n
+
+
+def cpu_baseline(w, its_per_step, sample_its=40):
+    """The oracle (oracle.monodomain with oracle.pcg and oracle.schwarz, float64 on
+    the host cores) timed on a bounded sample: one right-hand side (ionic update and
+    load) and `sample_its` ASM-PCG iterations, extrapolated to `its_per_step`."""
+    import numpy as np
+    from oracle import assembly, schwarz, monodomain
+    from oracle.pcg import pcg
+    d = assembly.assemble(w.mesh, w.p, w.sigma, w.eta0, w.chi_cm, w.dt)
+    S = schwarz.build(d, w.subdomain, w.coarse, w.q)
+    md = monodomain.Monodomain(d, w.stimulus, u0=w.u_rest, solver="pcg", prec=S.apply, rtol=1e-8)
+    t0 = time.perf_counter()
+    b, _ = md.rhs(md.state)
+    t_rhs = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pcg(d.K, b, x0=np.zeros_like(b), prec=S.apply, rtol=1e-30, maxit=sample_its)
+    t_it = (time.perf_counter() - t0) / sample_its
+    t_step = t_rhs + its_per_step * t_it
+    return t_step, t_rhs, t_it
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle of the same method on the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = build_case()
+    import numpy as np
+    from oracle import assembly, schwarz, monodomain
+    from oracle.pcg import pcg
+    d = assembly.assemble(w.mesh, w.p, w.sigma, w.eta0, w.chi_cm, w.dt)
+    S = schwarz.build(d, w.subdomain, w.coarse, w.q)
+    md = monodomain.Monodomain(d, w.stimulus, u0=w.u_rest, solver="pcg", prec=S.apply, rtol=1e-8)
+    sample_its = 10
+    # one full step fixes the iteration count that each sampled step is scaled to
+    b, _ = md.rhs(md.state)
+    full = pcg(d.K, b, x0=md.state.U, prec=S.apply, rtol=1e-8)
+    its = full.iterations
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        b, _ = md.rhs(md.state)
+        t_rhs = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        pcg(d.K, b, x0=md.state.U, prec=S.apply, rtol=1e-30, maxit=sample_its)
+        t_it = (time.perf_counter() - t0) / sample_its
+        if k >= args.warmup:
+            times.append(t_rhs + its * t_it)
+    total = sum(times)
+    value = len(times) / total
+    cores = os.cpu_count()
+    line = {"metric": METRIC, "value": value, "unit": "time-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "form": "FP64 oracle, plain ASM-PCG"},
+            "cpu_baseline": {"value": value, "unit": "time-steps/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"per step: ionic update + RHS and {sample_its} ASM-PCG "
+                                       f"iterations, scaled to the {its} iterations of a full "
+                                       "step solved once beforehand"},
+            "e2e": {"value": value, "unit": "time-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2512_19536_gb300 as pd
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    w = build_case()
+    ctx = pd.polydg_setup(w.mesh.vertices, w.mesh.cell_ptr, w.mesh.cell_vtx, w.sigma, w.p,
+                          w.subdomain, w.chi_cm, w.dt, w.eta0)
+    peaks, peak_kind = measured_peaks()
+
+    # reported form: mixed precision (fp32 local inverses, flexible PCG)
+    clocks = ClockSampler(local)
+    pc, sim, st, ms = time_form(pd, torch, w, ctx, "fp32", True, args.steps, args.warmup,
+                                stream, clocks)
+    # fp64 plain form on the same workload, for the comparison the metric names
+    pc64, sim64, st64, ms64 = time_form(pd, torch, w, ctx, "fp64", False, args.steps,
+                                        args.warmup, stream)
+    t = torch.tensor([ms, ms64], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms, ms64 = float(t[0]), float(t[1])
+    value = world * args.steps / (ms * 1e-3)
+    value64 = world * args.steps / (ms64 * 1e-3)
+    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, max(5, args.steps // 4), stream)
+    if world > 1:
+        te = torch.tensor([e2e_val], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MIN)
+        e2e_val = world * float(te[0])
+
+    info = pc.info()
+    launches = st["steps_done"]
+    alg = algorithmic_bytes(ctx.info, info, st["total_iterations"], launches)
+    achieved = alg / st["pcg_seconds"] / 1e9
+    traffic = profile_traffic(st["total_iterations"] / max(1, launches))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": "pcg_persistent_kernel<fp32 store, n_p=10>",
+                "peak_kind": peak_kind}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        its64 = st64["total_iterations"] / max(1, st64["steps_done"])
+        t_step, t_rhs, t_it = cpu_baseline(w, its64)
+        cpu = {"value": 1.0 / t_step, "unit": "time-steps/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"one ionic update + RHS ({t_rhs:.2f} s) and 40 ASM-PCG iterations "
+                         f"({t_it * 1e3:.1f} ms each) of the float64 oracle, scaled to "
+                         f"{its64:.1f} iterations/step (the fp64 plain form's mean)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "time-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "mixed: fp32 local inverses, flexible PCG "
+                   "(learned initial guess not built; x0 = U^k)",
+                   "rtol": 1e-8, "iterations_per_step": st["total_iterations"] / args.steps,
+                   "fp64_plain_steps_per_s": value64,
+                   "fp64_plain_iterations_per_step": st64["total_iterations"] / args.steps,
+                   "mixed_over_fp64": value / value64,
+                   "l2": "working set > L2 (no flush needed)",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks.summary(),
+        "e2e": {"value": e2e_val, "unit": "time-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 7 * args.steps,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def profile_traffic(iterations_per_launch):
+    """DRAM bytes per launch of the persistent kernel from the committed ncu summary,
+    scaled to this run's iterations per launch; None if the kernel source changed
+    since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "pcg_persistent_voronoi4096_fp32.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha") != kernel_sha():
+            return None
+        per_it = float(kv["dram_bytes_per_iteration"])
+        return per_it * iterations_per_launch
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def kernel_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("kernels_pcg.cu", "kernels.h", "device.cuh"):
+        with open(os.path.join(ROOT, "paper_2512_19536_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -118,7 +118,22 @@ typedef struct {
     int32_t max_iterations;    /* largest per-step PCG iteration count       */
     int32_t status;            /* first non-OK PCG status, else POLYDG_OK    */
     double  last_relres;       /* relative residual of the last step's solve */
+    double  pcg_seconds;       /* device time of the PCG solver kernel over these steps,
+                                  measured with CUDA events on the caller's stream */
 } step_stats;
+
+/* Sizes of a preconditioner, for bandwidth accounting. */
+typedef struct {
+    int64_t local_store_bytes;   /* bytes of the stored K_i^{-1}, all subdomains */
+    int64_t coarse_bytes;        /* bytes of K_0^{-1} (float64)                  */
+    int64_t restrict_bytes;      /* bytes of the stored rows of R_0 (float64)   */
+    int32_t n_subdomains;
+    int32_t n_coarse;            /* coarse DOFs n_0 (0: one-level)              */
+    int32_t precision;           /* POLYDG_FP64/FP32/BF16                       */
+    int32_t grid;                /* CTAs of the persistent PCG kernel           */
+    int32_t rows_per_tile;       /* rows of K_i^{-1} per bulk copy              */
+    int32_t pad;
+} asm_info;
 
 /* Text of the last error raised on the calling thread ("" if none). */
 const char *polydg_last_error(void);
@@ -156,6 +171,8 @@ int polydg_matvec(polydg_ctx *ctx, const double *x_dev, double *y_dev, void *str
 int asm_setup(polydg_ctx *ctx, const int32_t *coarse_of_cell, int q, int precision,
               asm_ctx **out);
 
+int asm_get_info(const asm_ctx *pc, asm_info *out);
+
 /* z = B_ad^{-1} r (Eq. prec).  r_dev and z_dev are caller-order device vectors
  * and must not alias. */
 int asm_apply(asm_ctx *pc, const double *r_dev, double *z_dev, void *stream);
@@ -163,8 +180,9 @@ int asm_apply(asm_ctx *pc, const double *r_dev, double *z_dev, void *stream);
 /* Solve K_h x = b by PCG (Saad Alg. 9.1) with B_ad^{-1} (pc != NULL) or without
  * preconditioner (pc == NULL: plain CG).  x_dev holds x0 on entry and the
  * solution on exit.  flexible = 1 takes beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k).
- * The iteration runs on the device (captured CUDA graph with a device-side
- * loop); the call synchronises `stream` and fills *stats (may be NULL).
+ * The whole iteration runs in one cooperative (persistent) kernel launch with
+ * one CTA per SM and grid barriers between its phases; the call synchronises
+ * `stream` and fills *stats (may be NULL).
  * Returns POLYDG_OK, ENOTCONV (x holds the last iterate), EBREAKDOWN,
  * ENONFINITE, EINVAL (rtol <= 0, maxit < 1), ECUDA.  b = 0 gives x = 0. */
 int pcg_solve(polydg_ctx *ctx, asm_ctx *pc, const double *b_dev, double *x_dev,

@@ -21,7 +21,7 @@ POLYDG_FP64, POLYDG_FP32, POLYDG_BF16 = 0, 1, 2
 PRECISION = {"fp64": POLYDG_FP64, "fp32": POLYDG_FP32, "bf16": POLYDG_BF16}
 
 EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_get_info", "polydg_get_faces",
-           "polydg_matvec", "asm_setup", "asm_apply", "pcg_solve", "sim_create",
+           "polydg_matvec", "asm_setup", "asm_get_info", "asm_apply", "pcg_solve", "sim_create",
            "monodomain_step", "sim_get_state", "sim_set_potential", "sim_step_index",
            "sim_destroy", "asm_destroy", "polydg_destroy"]
 
@@ -54,7 +54,14 @@ class sim_params(C.Structure):
 class step_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("total_iterations", C.c_int64),
                 ("max_iterations", C.c_int32), ("status", C.c_int32),
-                ("last_relres", C.c_double)]
+                ("last_relres", C.c_double), ("pcg_seconds", C.c_double)]
+
+
+class asm_info(C.Structure):
+    _fields_ = [("local_store_bytes", C.c_int64), ("coarse_bytes", C.c_int64),
+                ("restrict_bytes", C.c_int64), ("n_subdomains", C.c_int32),
+                ("n_coarse", C.c_int32), ("precision", C.c_int32), ("grid", C.c_int32),
+                ("rows_per_tile", C.c_int32), ("pad", C.c_int32)]
 
 
 _lib = None
@@ -78,6 +85,7 @@ def load() -> C.CDLL:
     L.polydg_matvec.argtypes = [vp, vp, vp, vp]
     L.asm_setup.argtypes = [vp, C.POINTER(C.c_int32), i32, i32, C.POINTER(vp)]
     L.asm_apply.argtypes = [vp, vp, vp, vp]
+    L.asm_get_info.argtypes = [vp, C.POINTER(asm_info)]
     L.pcg_solve.argtypes = [vp, vp, vp, vp, dbl, i32, i32, vp, C.POINTER(pcg_stats)]
     L.sim_create.argtypes = [vp, vp, C.POINTER(sim_params), C.POINTER(vp)]
     L.monodomain_step.argtypes = [vp, i32, vp, C.POINTER(step_stats)]
@@ -89,7 +97,7 @@ def load() -> C.CDLL:
         getattr(L, name).argtypes = [vp]
         getattr(L, name).restype = None
     for name in ("polydg_setup", "polydg_get_info", "polydg_get_faces", "polydg_matvec",
-                 "asm_setup", "asm_apply", "pcg_solve", "sim_create", "monodomain_step",
+                 "asm_setup", "asm_get_info", "asm_apply", "pcg_solve", "sim_create", "monodomain_step",
                  "sim_get_state", "sim_set_potential"):
         getattr(L, name).restype = i32
     _lib = L
@@ -182,6 +190,11 @@ class ASM:
     def __init__(self, ctx, handle, precision):
         self.ctx, self.h, self.precision = ctx, handle, precision
 
+    def info(self):
+        inf = asm_info()
+        _check(load().asm_get_info(self.h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in asm_info._fields_ if k != "pad"}
+
     def close(self):
         if self.h:
             load().asm_destroy(self.h)
@@ -257,7 +270,7 @@ def monodomain_step(sim: Simulation, nsteps=1, stream=None):
     _check(load().monodomain_step(sim.h, int(nsteps), _stream(stream), C.byref(st)))
     return {"steps_done": st.steps_done, "total_iterations": st.total_iterations,
             "max_iterations": st.max_iterations, "status": st.status,
-            "last_relres": st.last_relres}
+            "last_relres": st.last_relres, "pcg_seconds": st.pcg_seconds}
 
 
 def sim_get_state(sim: Simulation, u, y=None, stream=None):

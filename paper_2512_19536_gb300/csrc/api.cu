@@ -1,5 +1,5 @@
-// C ABI of libpolydg (include/polydg.h): contexts, device buffers, CUDA-graph
-// capture of the PCG loop and of the monodomain step.
+// C ABI of libpolydg (include/polydg.h): contexts, device buffers, the work
+// plan of the persistent PCG kernel and the launch sequence of a time step.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -53,33 +53,48 @@ static void dfree(T*& p) {
     p = nullptr;
 }
 
-// Vectors and scalars of one PCG solve (internal cell order).
+// Vectors and scalars of one PCG solve (internal cell order).  The iterate
+// and residual are double-buffered: after a solve they live in buffer
+// (sc->pass & 1).
 struct PcgWork {
-    double *x = nullptr, *b = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    double *x[2] = {nullptr, nullptr}, *r[2] = {nullptr, nullptr};
+    double *b = nullptr, *z = nullptr, *p = nullptr, *p2 = nullptr, *q = nullptr;
     PcgScalars* sc = nullptr;
     double* partials = nullptr;
+    int* err = nullptr;                 // device-wait timeout flag of the kernels
+    GridSync* gs = nullptr;             // grid-barrier state of the persistent kernel
+    double* bcast = nullptr;            // grid sums broadcast by the barrier
     int alloc(int64_t n) {
         int st;
-        if ((st = dalloc(&x, n)) || (st = dalloc(&b, n)) || (st = dalloc(&r, n)) ||
-            (st = dalloc(&z, n)) || (st = dalloc(&p, n)) || (st = dalloc(&q, n)) ||
-            (st = dalloc(&sc, 1)) || (st = dalloc(&partials, 2 * (size_t)kMaxPartials)))
+        if ((st = dalloc(&x[0], n)) || (st = dalloc(&x[1], n)) || (st = dalloc(&r[0], n)) ||
+            (st = dalloc(&r[1], n)) || (st = dalloc(&b, n)) || (st = dalloc(&z, n)) ||
+            (st = dalloc(&p, n)) || (st = dalloc(&p2, n)) || (st = dalloc(&q, n)) || (st = dalloc(&sc, 1)) ||
+            (st = dalloc(&partials, 8 * (size_t)kMaxPartials)) || (st = dalloc(&err, 1)) ||
+            (st = dalloc(&gs, 1)) || (st = dalloc(&bcast, 8)))
             return st;
         CU(cudaMemset(sc, 0, sizeof(PcgScalars)));
+        CU(cudaMemset(err, 0, sizeof(int)));
+        CU(cudaMemset(gs, 0, sizeof(GridSync)));
         return POLYDG_OK;
     }
     void release() {
-        dfree(x); dfree(b); dfree(r); dfree(z); dfree(p); dfree(q); dfree(sc); dfree(partials);
+        dfree(x[0]); dfree(x[1]); dfree(r[0]); dfree(r[1]); dfree(b); dfree(z); dfree(p); dfree(p2);
+        dfree(q); dfree(sc); dfree(partials); dfree(err); dfree(gs); dfree(bcast);
     }
 };
 
-struct Graph {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+// Static work split of the persistent PCG kernel over its CTAs.
+struct Plan {
+    int grid = 0, rows = 1, dtype = 0;
+    size_t smem = 0, buf_bytes = 0, xs_off = 0, rp_off = 0, qp_off = 0, zs_off = 0, r0_off = 0,
+           pn_off = 0;
+    int32_t *tile_ptr = nullptr, *sub_pairs = nullptr, *crow_ptr = nullptr;
+    int32_t *need_ptr = nullptr, *need = nullptr, *col_local = nullptr;
+    GemvTile* tiles = nullptr;
+    int64_t* elem_ptr = nullptr;
     void release() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        exec = nullptr;
-        graph = nullptr;
+        dfree(tile_ptr); dfree(sub_pairs); dfree(crow_ptr); dfree(need_ptr); dfree(need);
+        dfree(col_local); dfree(tiles); dfree(elem_ptr);
     }
 };
 
@@ -96,17 +111,27 @@ struct polydg_ctx {
     double* d_node_w = nullptr;
     double* d_node_phi = nullptr;
     int64_t* d_node_pos = nullptr;
+    // identity tiles (z = r) for unpreconditioned CG
+    GemvBlock* d_id_blocks = nullptr;
+    GemvTile* d_id_tiles = nullptr;
+    int n_id_tiles = 0;
+    int64_t* d_zero_ptr = nullptr;      // pair_ptr of an empty coarse space
+    Plan id_plan;                       // persistent-kernel plan without preconditioner
+    int n_sm = 0;
     PcgWork work;                       // pcg_solve / polydg_matvec buffers
     PcgScalars* h_sc = nullptr;         // pinned
-    cudaStream_t cap = nullptr, cap2 = nullptr;
-    std::map<std::pair<const asm_ctx*, int>, Graph> graphs;
 };
 
 struct asm_ctx {
     polydg_ctx* ctx = nullptr;
     int precision = POLYDG_FP64;
-    int has_coarse = 0, q = 0, nq = 0, n_agg = 0;
-    int n_blocks = 0, ntiles = 0, rows = 32, max_ld = 0;
+    int has_coarse = 0, q = 0, nq = 0, n_agg = 0, n_pairs = 0;
+    int64_t n0 = 0, ld0 = 0, off0 = 0;
+    int n_blocks = 0, ntiles = 0, rows = 32;
+    int* d_err = nullptr;               // device-wait timeout flag of asm_apply
+    Plan plan;                          // persistent-kernel plan with this preconditioner
+    std::vector<int32_t> sub_pairs;     // RESTRICT block ids grouped by subdomain
+    size_t k1_smem = 0, k2_smem = 0;
     GemvBlock* d_blocks = nullptr;
     GemvTile* d_tiles = nullptr;
     std::vector<GemvBlock> blocks;
@@ -115,13 +140,14 @@ struct asm_ctx {
     __nv_bfloat16* st16 = nullptr;
     double* d_T = nullptr;
     int32_t* d_agg = nullptr;
-    int64_t* d_agg_ptr = nullptr;
-    int32_t* d_agg_cells = nullptr;
-    double* d_r0 = nullptr;
+    int64_t* d_pair_ptr = nullptr;
+    double* d_r0p = nullptr;
+    double* d_q0p = nullptr;
     double* d_y0 = nullptr;
     double* d_rin = nullptr;
+    double* d_zloc = nullptr;
     double* d_zout = nullptr;
-    int64_t store_bytes = 0;            // bytes of the local-inverse store read per apply
+    int64_t store_bytes = 0;            // bytes of the dense stores read per apply
 };
 
 struct sim_ctx {
@@ -133,97 +159,189 @@ struct sim_ctx {
     double* d_y0 = nullptr;
     SimScalars* d_ss = nullptr;
     SimScalars* h_ss = nullptr;         // pinned
-    Graph step;
     int64_t k = 0;
+    std::vector<cudaEvent_t> ev;        // [2 * steps] around each step's PCG kernel
 };
 
 namespace polydg {
 
-// ---------------------------------------------------------- graph capture
-// Body of one PCG iteration (Saad Alg. 9.1 with the loop test at the end):
-//   z = B r  (restrict, ragged GEMV, prolong + r.z, z.q, beta)
-//   p = z + beta p;  q = K p, alpha;  x += alpha p, r -= alpha q, test.
-static int capture_pcg_body(polydg_ctx* c, asm_ctx* pc, PcgWork& w, cudaStream_t s,
-                            cudaGraphConditionalHandle cond) {
-    const int np = c->H.n_p;
-    const int64_t n = c->H.nc * np;
-    const double* zsrc = w.r;
-    if (pc) {
-        if (pc->has_coarse)
-            CU(launch_restrict(np, pc->nq, w.r, pc->d_T, pc->d_agg_ptr, pc->d_agg_cells,
-                               pc->n_agg, pc->d_r0, &w.sc->done, s));
-        CU(launch_gemv(pc->d_blocks, pc->d_tiles, pc->ntiles, pc->rows, pc->max_ld, pc->st64,
-                       pc->st32, pc->st16, w.r, pc->d_r0, w.z, pc->d_y0, &w.sc->done, s));
-        CU(launch_prolong(np, pc->has_coarse ? pc->nq : 3, w.z, pc->has_coarse ? pc->d_T : nullptr,
-                          pc->d_agg, pc->d_y0, c->H.nc, w.r, w.q, w.sc, w.partials, s));
-        zsrc = w.z;
-    } else {
-        CU(launch_identity_dots(w.r, w.q, n, w.sc, w.partials, s));
+// ---------------------------------------------------------- preconditioner plumbing
+static K2Args k2_args(polydg_ctx* c, asm_ctx* pc, PcgScalars* sc, double* partials) {
+    K2Args a = {};
+    a.K0inv = (pc && pc->has_coarse) ? pc->st64 + pc->off0 : nullptr;
+    a.n0 = (pc && pc->has_coarse) ? (int)pc->n0 : 0;
+    a.ld0 = (pc && pc->has_coarse) ? (int)pc->ld0 : 0;
+    a.nq = (pc && pc->has_coarse) ? pc->nq : 1;
+    a.rows_per_cta = 32;
+    a.pair_ptr = (pc && pc->has_coarse) ? pc->d_pair_ptr : c->d_zero_ptr;
+    a.r0p = pc ? pc->d_r0p : nullptr;
+    a.q0p = pc ? pc->d_q0p : nullptr;
+    a.y0 = pc ? pc->d_y0 : nullptr;
+    a.sc = sc;
+    a.partials = partials;
+    return a;
+}
+
+// Split the work of one PCG iteration over `grid` CTAs: LOCAL tiles (rows of the
+// local inverses) as contiguous runs balanced by bytes, elements and coarse rows
+// evenly; per CTA the elements whose p its matvec rows need (own range first,
+// then face neighbours) and the CTA-local column index of every block.
+static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
+    const HostSetup& H = c->H;
+    const int G = c->n_sm, np = H.n_p;
+    P.grid = G;
+    P.dtype = pc ? pc->precision : 0;
+    const int esz = P.dtype == 0 ? 8 : P.dtype == 1 ? 4 : 2;
+    const int xsz = P.dtype == 0 ? 0 : 4;        // fp64 stores read r' from the fp64 copy
+    int64_t max_ld = 8;
+    std::vector<int> local_ids;
+    std::vector<int32_t> sub_pairs;
+    if (pc)
+        for (int b = 0; b < (int)pc->blocks.size(); ++b)
+            if (pc->blocks[b].kind == KIND_LOCAL) {
+                local_ids.push_back(b);
+                max_ld = std::max<int64_t>(max_ld, pc->blocks[b].ld);
+            }
+    const int64_t n0 = (pc && pc->has_coarse) ? pc->n0 : 0;
+    // elements and neighbour lists
+    std::vector<int64_t> elem_ptr(G + 1);
+    for (int g = 0; g <= G; ++g) elem_ptr[g] = (H.nc * g) / G;
+    std::vector<int32_t> need_ptr(G + 1, 0), need, col_local(H.col.size());
+    int max_need = 0;
+    for (int g = 0; g < G; ++g) {
+        const int64_t e0 = elem_ptr[g], e1 = elem_ptr[g + 1];
+        std::vector<int32_t> nb;
+        for (int64_t e = e0; e < e1; ++e)
+            for (int32_t bi = H.row_ptr[e]; bi < H.row_ptr[e + 1]; ++bi)
+                if (H.col[bi] < e0 || H.col[bi] >= e1) nb.push_back(H.col[bi]);
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        need_ptr[g] = (int32_t)need.size();
+        for (int64_t e = e0; e < e1; ++e) need.push_back((int32_t)e);
+        need.insert(need.end(), nb.begin(), nb.end());
+        for (int64_t e = e0; e < e1; ++e)
+            for (int32_t bi = H.row_ptr[e]; bi < H.row_ptr[e + 1]; ++bi) {
+                const int32_t f = H.col[bi];
+                col_local[bi] = (f >= e0 && f < e1)
+                                    ? (int32_t)(f - e0)
+                                    : (int32_t)((e1 - e0) + (std::lower_bound(nb.begin(), nb.end(), f) - nb.begin()));
+            }
+        max_need = std::max(max_need, (int)((e1 - e0) + nb.size()));
     }
-    CU(launch_direction(w.p, zsrc, n, w.sc, s));
-    CU(launch_matvec(MODE_PCG, np, c->K, c->K.val, w.p, w.q, nullptr, nullptr, 0, 0, w.sc,
-                     w.partials, nullptr, 0, 0, s));
-    CU(launch_update(w.x, w.r, w.p, w.q, n, w.sc, w.partials, cond, 1, s));
+    need_ptr[G] = (int32_t)need.size();
+    // shared memory: 2 tile buffers, staged r' (store type), r' and q (fp64), z (2 x rows),
+    // r0/q0, p of the needed elements
+    auto r128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
+    const size_t cap = 220 * 1024;
+    const size_t fixed = r128((size_t)max_ld * xsz) + 2 * r128((size_t)max_ld * 8) +
+                         r128(2 * (size_t)n0 * 8) + r128((size_t)max_need * np * 8) + r128(kStages * 64 * 8);
+    if (fixed + kStages * (size_t)max_ld * esz > cap) {
+        set_error("pcg: a subdomain or coarse space is too large for the shared-memory plan");
+        return POLYDG_EINVAL;
+    }
+    const int rows = (int)std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)((cap - fixed) / kStages / ((size_t)max_ld * esz))));
+    P.rows = rows;
+    P.buf_bytes = pc ? r128((size_t)rows * max_ld * esz) : 0;
+    P.xs_off = kStages * P.buf_bytes;
+    P.rp_off = P.xs_off + r128((size_t)max_ld * xsz);
+    P.qp_off = P.rp_off + r128((size_t)max_ld * 8);
+    P.zs_off = P.qp_off + r128((size_t)max_ld * 8);
+    P.r0_off = P.zs_off + r128(kStages * (size_t)rows * 8);
+    P.pn_off = P.r0_off + r128(2 * (size_t)n0 * 8);
+    P.smem = P.pn_off + r128((size_t)max_need * np * 8);
+    // LOCAL tiles balanced by bytes
+    std::vector<GemvTile> tiles;
+    std::vector<int64_t> tbytes;
+    for (int b : local_ids) {
+        const GemvBlock& B = pc->blocks[b];
+        for (int r0 = 0; r0 < B.nrows; r0 += rows) {
+            tiles.push_back({b, r0});
+            tbytes.push_back((int64_t)std::min(rows, B.nrows - r0) * B.ld * esz);
+        }
+    }
+    int64_t total = 0;
+    for (auto v : tbytes) total += v;
+    std::vector<int32_t> tile_ptr(G + 1, 0);
+    {
+        int64_t acc = 0;
+        size_t k = 0;
+        for (int g = 0; g < G; ++g) {
+            tile_ptr[g] = (int32_t)k;
+            const int64_t target = (total * (g + 1)) / G;
+            while (k < tiles.size() && acc + tbytes[k] / 2 <= target) acc += tbytes[k++];
+        }
+        tile_ptr[G] = (int32_t)tiles.size();
+    }
+    if (pc) sub_pairs = pc->sub_pairs;
+    std::vector<int32_t> crow_ptr(G + 1);
+    for (int g = 0; g <= G; ++g) crow_ptr[g] = (int32_t)((n0 * g) / G);
+    int st;
+    if ((st = upload(&P.tile_ptr, tile_ptr)) || (st = upload(&P.tiles, tiles)) ||
+        (st = upload(&P.sub_pairs, sub_pairs)) || (st = upload(&P.elem_ptr, elem_ptr)) ||
+        (st = upload(&P.crow_ptr, crow_ptr)) || (st = upload(&P.need_ptr, need_ptr)) ||
+        (st = upload(&P.need, need)) || (st = upload(&P.col_local, col_local)))
+        return st;
+    int occ = 0;
+    CU(persistent_occupancy(P.dtype, np, P.smem, &occ));
+    if (occ < 1) { set_error("pcg: the persistent kernel does not fit on an SM"); return POLYDG_ECUDA; }
     return POLYDG_OK;
 }
 
-// Appends [r = b - K x; while (!done) body] to the capture running on c->cap.
-static int capture_pcg_loop(polydg_ctx* c, asm_ctx* pc, PcgWork& w) {
-    const int np = c->H.n_p;
-    CU(launch_matvec(MODE_RESID, np, c->K, c->K.val, w.x, w.r, w.b, nullptr, 0, 0, w.sc,
-                     w.partials, nullptr, 0, 0, c->cap));
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t g;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t ndeps = 0;
-    CU(cudaStreamGetCaptureInfo(c->cap, &cs, nullptr, &g, &deps, nullptr, &ndeps));
-    cudaGraphConditionalHandle cond;
-    CU(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    CU(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
-    CU(cudaStreamUpdateCaptureDependencies(c->cap, &node, nullptr, 1,
-                                           cudaStreamSetCaptureDependencies));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    CU(cudaStreamBeginCaptureToGraph(c->cap2, body, nullptr, nullptr, 0,
-                                     cudaStreamCaptureModeThreadLocal));
-    int st = capture_pcg_body(c, pc, w, c->cap2, cond);
-    cudaGraph_t body_out = nullptr;
-    cudaError_t e = cudaStreamEndCapture(c->cap2, &body_out);
-    if (st) return st;
-    CU(e);
-    return POLYDG_OK;
-}
-
-static int end_capture(polydg_ctx* c, Graph& G) {
-    CU(cudaStreamEndCapture(c->cap, &G.graph));
-    CU(cudaGraphInstantiate(&G.exec, G.graph, 0));
-    return POLYDG_OK;
-}
-
-static void abort_capture(polydg_ctx* c) {
-    cudaGraph_t g = nullptr;
-    cudaStreamEndCapture(c->cap, &g);
-    if (g) cudaGraphDestroy(g);
-    cudaGetLastError();
-}
-
-static int pcg_graph(polydg_ctx* c, asm_ctx* pc, int flexible, Graph** out) {
-    auto key = std::make_pair((const asm_ctx*)pc, flexible);
-    auto it = c->graphs.find(key);
-    if (it != c->graphs.end()) { *out = &it->second; return POLYDG_OK; }
-    CU(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    int st = capture_pcg_loop(c, pc, c->work);
-    if (st) { abort_capture(c); return st; }
-    Graph G;
-    st = end_capture(c, G);
-    if (st) { G.release(); return st; }
-    auto res = c->graphs.emplace(key, G);
-    *out = &res.first->second;
+// Enqueue one persistent PCG solve of K x = b on the vectors of w (internal
+// order; x holds x0).  The scalars in w.sc must hold rtol2, maxit, flexible and done = 0.
+static int run_pcg(polydg_ctx* c, asm_ctx* pc, PcgWork& w, cudaStream_t s) {
+    const Plan& P = pc ? pc->plan : c->id_plan;
+    const bool coarse = pc && pc->has_coarse;
+    PersistArgs a = {};
+    a.grid = P.grid;
+    a.rows = P.rows;
+    a.identity = pc ? 0 : 1;
+    a.n0 = coarse ? (int)pc->n0 : 0;
+    a.ld0 = coarse ? (int)pc->ld0 : 0;
+    a.nq = coarse ? pc->nq : 1;
+    a.nc = c->H.nc;
+    a.buf_bytes = P.buf_bytes;
+    a.xs_off = P.xs_off;
+    a.rp_off = P.rp_off;
+    a.qp_off = P.qp_off;
+    a.zs_off = P.zs_off;
+    a.r0_off = P.r0_off;
+    a.pn_off = P.pn_off;
+    a.row_ptr = c->K.row_ptr;
+    a.val = c->K.val;
+    a.need_ptr = P.need_ptr;
+    a.need = P.need;
+    a.col_local = P.col_local;
+    a.elem_ptr = P.elem_ptr;
+    a.blocks = pc ? pc->d_blocks : nullptr;
+    a.tiles = P.tiles;
+    a.tile_ptr = P.tile_ptr;
+    a.sub_pairs = P.sub_pairs;
+    a.store = pc ? (P.dtype == 0 ? (const void*)pc->st64 : P.dtype == 1 ? (const void*)pc->st32 : (const void*)pc->st16) : nullptr;
+    a.st64 = pc ? pc->st64 : nullptr;
+    a.K0inv = coarse ? pc->st64 + pc->off0 : nullptr;
+    a.pair_ptr = coarse ? pc->d_pair_ptr : c->d_zero_ptr;
+    a.T = coarse ? pc->d_T : nullptr;
+    a.agg = coarse ? pc->d_agg : nullptr;
+    a.crow_ptr = P.crow_ptr;
+    a.b = w.b;
+    a.x = w.x[0];
+    a.r[0] = w.r[0];
+    a.r[1] = w.r[1];
+    a.p[0] = w.p;
+    a.p[1] = w.p2;
+    a.z = w.z;
+    a.q = w.q;
+    a.r0p = pc ? pc->d_r0p : nullptr;
+    a.q0p = pc ? pc->d_q0p : nullptr;
+    a.y0 = pc ? pc->d_y0 : nullptr;
+    a.sc = w.sc;
+    a.partials = w.partials;
+    a.bcast = w.bcast;
+    a.gs = w.gs;
+    a.err = w.err;
+    CU(cudaMemsetAsync(&w.gs->count, 0, sizeof(unsigned), s));
+    CU(launch_pcg_persistent(P.dtype, c->H.n_p, a, P.smem, s));
     return POLYDG_OK;
 }
 
@@ -253,8 +371,32 @@ int polydg_setup(const polydg_mesh* mesh, int p, const int32_t* subdomain_of_cel
     const HostSetup& H = c->H;
     c->K.nc = H.nc;
     c->K.nblk = (int64_t)H.col.size();
+    // device layout: every n_p x n_p block column-major, so that a row of blocks
+    // is one column-major panel (coalesced warp loads in the matvec kernel)
+    const int np = H.n_p;
+    std::vector<double> Kt(H.Kval.size()), Kmt(H.Kminus_val.size());
+    for (int64_t bi = 0; bi < c->K.nblk; ++bi)
+        for (int i = 0; i < np; ++i)
+            for (int j = 0; j < np; ++j) {
+                Kt[bi * np * np + j * np + i] = H.Kval[bi * np * np + i * np + j];
+                Kmt[bi * np * np + j * np + i] = H.Kminus_val[bi * np * np + i * np + j];
+            }
+    std::vector<GemvBlock> idb;
+    std::vector<GemvTile> idt;
+    {
+        GemvBlock B = {};
+        B.in_off = B.out_off = 0;
+        B.nrows = B.ncols = (int32_t)(H.nc * np);
+        B.kind = KIND_IDENTITY;
+        idb.push_back(B);
+        for (int64_t r0 = 0; r0 < H.nc * np; r0 += 256) idt.push_back({0, (int32_t)r0});
+        c->n_id_tiles = (int)idt.size();
+    }
+    std::vector<int64_t> zero_ptr(2, 0);
     if ((st = upload(&c->K.row_ptr, H.row_ptr)) || (st = upload(&c->K.col, H.col)) ||
-        (st = upload(&c->K.val, H.Kval)) || (st = upload(&c->K.val_minus, H.Kminus_val)) ||
+        (st = upload(&c->K.val, Kt)) || (st = upload(&c->K.val_minus, Kmt)) ||
+        (st = upload(&c->d_id_blocks, idb)) || (st = upload(&c->d_id_tiles, idt)) ||
+        (st = upload(&c->d_zero_ptr, zero_ptr)) ||
         (st = upload(&c->d_to_caller, H.to_caller)) || (st = upload(&c->d_node_ptr, H.node_ptr)) ||
         (st = upload(&c->d_node_w, H.node_w)) || (st = upload(&c->d_node_phi, H.node_phi)) ||
         (st = upload(&c->d_node_pos, H.node_to_caller_pos)))
@@ -264,11 +406,12 @@ int polydg_setup(const polydg_mesh* mesh, int p, const int32_t* subdomain_of_cel
         set_error("polydg_setup: pinned allocation failed");
         return fail(POLYDG_ENOMEM);
     }
-    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess) {
-        set_error("polydg_setup: stream creation failed");
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        c->n_sm < 1) {
+        set_error("polydg_setup: cannot query the SM count");
         return fail(POLYDG_ECUDA);
     }
+    if ((st = build_plan(c, nullptr, c->id_plan))) return fail(st);
     *out = c;
     return POLYDG_OK;
 }
@@ -304,10 +447,10 @@ int polydg_matvec(polydg_ctx* c, const double* x_dev, double* y_dev, void* strea
     if (!x_dev || !y_dev || x_dev == y_dev) { set_error("polydg_matvec: null or aliased vectors"); return POLYDG_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     const int np = c->H.n_p;
-    CU(launch_permute(x_dev, c->work.p, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
+    CU(launch_permute(x_dev, nullptr, c->work.p, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
     CU(launch_matvec(MODE_PLAIN, np, c->K, c->K.val, c->work.p, c->work.q, nullptr, nullptr, 0, 0,
-                     nullptr, nullptr, nullptr, 0, 0, s));
-    CU(launch_permute(c->work.q, y_dev, c->d_to_caller, c->H.nc, np, 0, nullptr, s));
+                     nullptr, nullptr, nullptr, 0, 0, nullptr, nullptr, s));
+    CU(launch_permute(c->work.q, nullptr, y_dev, c->d_to_caller, c->H.nc, np, 0, nullptr, s));
     return POLYDG_OK;
 }
 
@@ -412,38 +555,139 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
         if ((st = cu(launch_cast_store(pc->st64, nullptr, pc->st16, local_elems, 0), "cast"))) return fail(st);
     }
     const int esz = precision == POLYDG_FP64 ? 8 : precision == POLYDG_FP32 ? 4 : 2;
-    // block and tile tables
+    // rows per tile: the tile's rows of K_i^{-1} (one bulk copy) fill <= 96 KB of
+    // shared memory, so two tiles fit on an SM
+    int64_t max_ld = 8;
+    for (int m = 0; m < H.n_sub; ++m) max_ld = std::max(max_ld, mats[m].ld);
+    pc->rows = (int)std::max<int64_t>(8, std::min<int64_t>(64, (96 * 1024 / (max_ld * esz)) / 8 * 8));
+    // LOCAL blocks and tiles
     std::vector<GemvTile> tiles;
-    for (int m = 0; m < nmat; ++m) {
-        GemvBlock B;
+    for (int m = 0; m < H.n_sub; ++m) {
+        GemvBlock B = {};
         B.mat_off = mats[m].off;
-        B.n = (int32_t)mats[m].n;
+        B.nrows = B.ncols = (int32_t)mats[m].n;
         B.ld = (int32_t)mats[m].ld;
-        const bool coarse = (m == H.n_sub);
-        B.sel = coarse ? 1 : 0;
-        B.dtype = coarse ? 0 : precision;
-        B.in_off = coarse ? 0 : H.sub_ptr[m] * np;
-        B.out_off = B.in_off;
+        B.kind = KIND_LOCAL;
+        B.dtype = precision;
+        B.in_off = B.out_off = H.sub_ptr[m] * np;
         pc->blocks.push_back(B);
-        pc->max_ld = std::max(pc->max_ld, B.ld);
-        for (int r0 = 0; r0 < B.n; r0 += pc->rows) tiles.push_back({m, r0});
-        pc->store_bytes += (int64_t)B.n * B.ld * (coarse ? 8 : esz);
+        for (int r0 = 0; r0 < B.nrows; r0 += pc->rows) tiles.push_back({m, r0});
+        pc->store_bytes += (int64_t)B.nrows * B.ld * esz;
+        const size_t xsz = precision == POLYDG_FP64 ? 8 : 4;
+        const size_t need = (((size_t)pc->rows * B.ld * esz + 15) & ~(size_t)15) +
+                            (((size_t)B.ld * xsz + 15) & ~(size_t)15) + (size_t)pc->rows * 8;
+        pc->k1_smem = std::max(pc->k1_smem, need);
     }
-    pc->n_blocks = nmat;
-    pc->ntiles = (int)tiles.size();
-    if ((st = upload(&pc->d_blocks, pc->blocks)) || (st = upload(&pc->d_tiles, tiles)))
-        return fail(st);
-    if ((st = cu(set_gemv_smem(pc->max_ld), "gemv smem"))) return fail(st);
+    // RESTRICT blocks: rows of R_0 on the DOFs of each (agglomerate, subdomain)
+    // pair, fp64, stored after the inverses in st64
     if (pc->has_coarse) {
         pc->q = C.q; pc->nq = C.n_q; pc->n_agg = C.n_agg;
-        if ((st = upload(&pc->d_T, C.T)) || (st = upload(&pc->d_agg, C.agg_of_cell)) ||
-            (st = upload(&pc->d_agg_ptr, C.agg_ptr)) || (st = upload(&pc->d_agg_cells, C.agg_cells)))
+        pc->n0 = n0;
+        pc->ld0 = mats.back().ld;
+        pc->off0 = mats.back().off;
+        std::vector<int32_t> sub_of(H.nc);
+        for (int i = 0; i < H.n_sub; ++i)
+            for (int64_t e = H.sub_ptr[i]; e < H.sub_ptr[i + 1]; ++e) sub_of[e] = i;
+        std::vector<int64_t> pair_ptr(C.n_agg + 1, 0);
+        std::vector<double> Rst;
+        std::vector<GemvBlock> rblocks;
+        for (int J = 0; J < C.n_agg; ++J) {
+            int cur = -1;
+            for (int64_t k = C.agg_ptr[J]; k < C.agg_ptr[J + 1]; ++k) {
+                const int64_t e = C.agg_cells[k];          // ascending internal ids
+                const int i = sub_of[e];
+                if (i != cur) {
+                    cur = i;
+                    GemvBlock B = {};
+                    B.nrows = C.n_q;
+                    B.ncols = (int32_t)((H.sub_ptr[i + 1] - H.sub_ptr[i]) * np);
+                    B.ld = (int32_t)round_up(B.ncols, 8);
+                    B.kind = KIND_RESTRICT;
+                    B.dtype = 0;
+                    B.in_off = H.sub_ptr[i] * np;
+                    B.out_off = (int64_t)rblocks.size() * C.n_q;
+                    B.mat_off = off + (int64_t)Rst.size();
+                    Rst.resize(Rst.size() + (size_t)B.nrows * B.ld, 0.0);
+                    rblocks.push_back(B);
+                    pair_ptr[J + 1]++;
+                }
+                GemvBlock& B = rblocks.back();
+                double* R = Rst.data() + (B.mat_off - off);
+                const int64_t c0 = (e - H.sub_ptr[i]) * np;
+                for (int kk = 0; kk < np; ++kk)
+                    for (int a = 0; a < C.n_q; ++a)
+                        R[(int64_t)a * B.ld + c0 + kk] = C.T[(e * np + kk) * C.n_q + a];
+            }
+        }
+        for (int J = 0; J < C.n_agg; ++J) pair_ptr[J + 1] += pair_ptr[J];
+        pc->n_pairs = (int)rblocks.size();
+        // grow st64 to hold the R blocks
+        double* grown = nullptr;
+        if ((st = dalloc(&grown, off + Rst.size()))) return fail(st);
+        if ((st = cu(cudaMemcpy(grown, pc->st64, off * sizeof(double), cudaMemcpyDeviceToDevice), "copy")) ||
+            (st = cu(cudaMemcpy(grown + off, Rst.data(), Rst.size() * sizeof(double), cudaMemcpyHostToDevice), "copy"))) {
+            dfree(grown);
+            return fail(st);
+        }
+        dfree(pc->st64);
+        pc->st64 = grown;
+        for (auto& B : rblocks) {
+            tiles.push_back({(int32_t)pc->blocks.size(), 0});
+            pc->blocks.push_back(B);
+            pc->store_bytes += (int64_t)B.nrows * B.ld * 8;
+            pc->k1_smem = std::max(pc->k1_smem, (size_t)2 * B.ld * 8);
+        }
+        pc->store_bytes += n0 * mats.back().ld * 8;
+        if ((st = upload(&pc->d_pair_ptr, pair_ptr)) || (st = upload(&pc->d_T, C.T)) ||
+            (st = upload(&pc->d_agg, C.agg_of_cell)))
             return fail(st);
     }
-    if ((st = dalloc(&pc->d_r0, std::max<int64_t>(n0, 1))) || (st = dalloc(&pc->d_y0, std::max<int64_t>(n0, 1))) ||
-        (st = dalloc(&pc->d_rin, H.nc * np)) || (st = dalloc(&pc->d_zout, H.nc * np)))
+    // per subdomain (LOCAL block m = subdomain m): its restriction pairs
+    for (int m = 0; m < H.n_sub; ++m) {
+        GemvBlock& B = pc->blocks[m];
+        B.pair_begin = (int32_t)pc->sub_pairs.size();
+        for (int b = H.n_sub; b < (int)pc->blocks.size(); ++b)
+            if (pc->blocks[b].kind == KIND_RESTRICT && pc->blocks[b].in_off == B.in_off)
+                pc->sub_pairs.push_back(b);
+        B.pair_count = (int32_t)pc->sub_pairs.size() - B.pair_begin;
+    }
+    pc->n_blocks = (int)pc->blocks.size();
+    pc->ntiles = (int)tiles.size();
+    pc->k2_smem = 2 * (size_t)n0 * sizeof(double);
+    if ((st = upload(&pc->d_blocks, pc->blocks)) || (st = upload(&pc->d_tiles, tiles)))
         return fail(st);
+    if ((st = cu(set_precond_smem(pc->k1_smem), "precond smem")) ||
+        (st = cu(set_coarse_smem(pc->k2_smem), "coarse smem")))
+        return fail(st);
+    const int64_t npairs = std::max<int64_t>(pc->n_pairs, 1) * std::max(pc->nq, 1);
+    if ((st = dalloc(&pc->d_r0p, npairs)) || (st = dalloc(&pc->d_q0p, npairs)) ||
+        (st = dalloc(&pc->d_y0, std::max<int64_t>(n0, 1))) || (st = dalloc(&pc->d_rin, H.nc * np)) ||
+        (st = dalloc(&pc->d_zloc, H.nc * np)) || (st = dalloc(&pc->d_zout, H.nc * np)) ||
+        (st = dalloc(&pc->d_err, 1)))
+        return fail(st);
+    if ((st = cu(cudaMemset(pc->d_err, 0, sizeof(int)), "memset"))) return fail(st);
+    if ((st = build_plan(c, pc, pc->plan))) return fail(st);
     *out = pc;
+    return POLYDG_OK;
+}
+
+int asm_get_info(const asm_ctx* pc, asm_info* out) {
+    if (!pc || !out) { set_error("asm_get_info: null argument"); return POLYDG_EINVAL; }
+    int64_t local = 0, restr = 0;
+    for (const auto& B : pc->blocks) {
+        const int esz = B.dtype == 0 ? 8 : B.dtype == 1 ? 4 : 2;
+        if (B.kind == KIND_LOCAL) local += (int64_t)B.nrows * B.ld * esz;
+        else if (B.kind == KIND_RESTRICT) restr += (int64_t)B.nrows * B.ld * 8;
+    }
+    out->local_store_bytes = local;
+    out->coarse_bytes = pc->has_coarse ? pc->n0 * pc->ld0 * 8 : 0;
+    out->restrict_bytes = restr;
+    out->n_subdomains = pc->ctx->H.n_sub;
+    out->n_coarse = (int32_t)pc->n0;
+    out->precision = pc->precision;
+    out->grid = pc->plan.grid;
+    out->rows_per_tile = pc->plan.rows;
+    out->pad = 0;
     return POLYDG_OK;
 }
 
@@ -453,16 +697,24 @@ int asm_apply(asm_ctx* pc, const double* r_dev, double* z_dev, void* stream) {
     polydg_ctx* c = pc->ctx;
     cudaStream_t s = (cudaStream_t)stream;
     const int np = c->H.n_p;
-    CU(launch_permute(r_dev, pc->d_rin, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
-    if (pc->has_coarse)
-        CU(launch_restrict(np, pc->nq, pc->d_rin, pc->d_T, pc->d_agg_ptr, pc->d_agg_cells, pc->n_agg,
-                           pc->d_r0, nullptr, s));
-    CU(launch_gemv(pc->d_blocks, pc->d_tiles, pc->ntiles, pc->rows, pc->max_ld, pc->st64, pc->st32,
-                   pc->st16, pc->d_rin, pc->d_r0, pc->d_zout, pc->d_y0, nullptr, s));
-    if (pc->has_coarse)
-        CU(launch_prolong(np, pc->nq, pc->d_zout, pc->d_T, pc->d_agg, pc->d_y0, c->H.nc, nullptr,
-                          nullptr, nullptr, nullptr, s));
-    CU(launch_permute(pc->d_zout, z_dev, c->d_to_caller, c->H.nc, np, 0, nullptr, s));
+    CU(launch_permute(r_dev, nullptr, pc->d_rin, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
+    K1Args a = {};
+    a.blocks = pc->d_blocks;
+    a.tiles = pc->d_tiles;
+    a.rows = pc->rows;
+    a.st64 = pc->st64; a.st32 = pc->st32; a.st16 = pc->st16;
+    a.x[0] = a.x[1] = nullptr;
+    a.r[0] = a.r[1] = pc->d_rin;
+    a.z = pc->d_zloc;
+    a.r0p = pc->d_r0p;
+    a.q0p = pc->d_q0p;
+    a.err = pc->d_err;
+    CU(launch_precond(a, pc->precision, pc->ntiles, pc->k1_smem, s));
+    if (pc->has_coarse) CU(launch_coarse(k2_args(c, pc, nullptr, nullptr), s));
+    CU(launch_direction(pc->has_coarse ? pc->nq : 3, nullptr, pc->d_zloc,
+                        pc->has_coarse ? pc->d_T : nullptr, pc->has_coarse ? pc->d_agg : nullptr,
+                        pc->d_y0, c->H.nc, np, nullptr, pc->d_zout, s));
+    CU(launch_permute(pc->d_zout, nullptr, z_dev, c->d_to_caller, c->H.nc, np, 0, nullptr, s));
     return POLYDG_OK;
 }
 
@@ -473,8 +725,6 @@ int pcg_solve(polydg_ctx* c, asm_ctx* pc, const double* b_dev, double* x_dev, do
     if (!(rtol > 0) || maxit < 1) { set_error("pcg_solve: rtol must be > 0 and maxit >= 1"); return POLYDG_EINVAL; }
     if (pc && pc->ctx != c) { set_error("pcg_solve: preconditioner built on another context"); return POLYDG_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
-    Graph* G = nullptr;
-    if (int st = pcg_graph(c, pc, flexible ? 1 : 0, &G)) return st;
     const int np = c->H.n_p;
     PcgScalars init = {};
     init.rtol2 = rtol * rtol;
@@ -482,10 +732,11 @@ int pcg_solve(polydg_ctx* c, asm_ctx* pc, const double* b_dev, double* x_dev, do
     init.flexible = flexible ? 1 : 0;
     *c->h_sc = init;
     CU(cudaMemcpyAsync(c->work.sc, c->h_sc, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
-    CU(launch_permute(b_dev, c->work.b, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
-    CU(launch_permute(x_dev, c->work.x, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
-    CU(cudaGraphLaunch(G->exec, s));
-    CU(launch_permute(c->work.x, x_dev, c->d_to_caller, c->H.nc, np, 0, c->work.sc, s));
+    CU(cudaMemsetAsync(c->work.err, 0, sizeof(int), s));
+    CU(launch_permute(b_dev, nullptr, c->work.b, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
+    CU(launch_permute(x_dev, nullptr, c->work.x[0], c->d_to_caller, c->H.nc, np, 1, nullptr, s));
+    if (int st = run_pcg(c, pc, c->work, s)) return st;
+    CU(launch_permute(c->work.x[0], c->work.x[1], x_dev, c->d_to_caller, c->H.nc, np, 0, c->work.sc, s));
     CU(cudaMemcpyAsync(c->h_sc, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     const PcgScalars& r = *c->h_sc;
@@ -496,7 +747,8 @@ int pcg_solve(polydg_ctx* c, asm_ctx* pc, const double* b_dev, double* x_dev, do
         stats->bnorm = std::sqrt(r.bb);
     }
     if (r.status != 0) {
-        set_error(r.status == POLYDG_ENOTCONV ? "pcg_solve: maximum number of iterations reached"
+        set_error(r.status == POLYDG_ECUDA ? "pcg_solve: a device-side wait timed out"
+                  : r.status == POLYDG_ENOTCONV ? "pcg_solve: maximum number of iterations reached"
                   : r.status == POLYDG_EBREAKDOWN ? "pcg_solve: breakdown (p^T K p <= 0 or non-finite beta)"
                                                   : "pcg_solve: non-finite value in b or the residual");
     }
@@ -562,29 +814,37 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
         (st = cu(cudaMemcpy(sm->work.sc, &sc, sizeof(sc), cudaMemcpyHostToDevice))) ||
         (st = cu(cudaDeviceSynchronize())))
         return fail(st);
-    // capture one step: ionic update, right-hand side, x0 = U^k, PCG loop, rotation
-    if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        set_error("sim_create: stream capture failed");
-        return fail(POLYDG_ECUDA);
-    }
-    PcgWork& w = sm->work;
-    const double dt = H.dt;
-    if ((st = cu(launch_step_begin(w.sc, sm->d_ss, c->cap))) ||
-        (st = cu(launch_ionic(np, sm->U, sm->Uprev, c->d_node_ptr, c->d_node_w, c->d_node_phi, sm->y,
-                              nn, H.nc, dt, sm->I, sm->d_ss, c->cap))) ||
-        (st = cu(launch_matvec(MODE_RHS, np, c->K, c->K.val_minus, sm->U, w.b, sm->I, sm->F,
-                               -H.chi_cm * dt, dt, nullptr, nullptr, sm->d_ss, dt,
-                               prm->stim_duration, c->cap))) ||
-        (st = cu(launch_copy(sm->U, w.x, n, sm->d_ss, c->cap))) ||
-        (st = capture_pcg_loop(c, pc, w)) ||
-        (st = cu(launch_step_finish(sm->U, sm->Uprev, w.x, n, w.sc, sm->d_ss, c->cap)))) {
-        abort_capture(c);
-        return fail(st);
-    }
-    if ((st = end_capture(c, sm->step))) return fail(st);
     *out = sm;
     return POLYDG_OK;
 }
+
+
+}  // extern "C"
+namespace polydg {
+// One Crank-Nicolson step (Eq. fully-discrete-1): ionic update at the nodes and
+// the ion-current load, right-hand side, x0 = U^k, PCG solve, rotation of U.
+static int enqueue_step(sim_ctx* sm, cudaStream_t s, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+    polydg_ctx* c = sm->ctx;
+    const HostSetup& H = c->H;
+    const int np = H.n_p;
+    const int64_t n = H.nc * np, nn = (int64_t)H.node_w.size();
+    PcgWork& w = sm->work;
+    const double dt = H.dt;
+    CU(launch_step_begin(w.sc, sm->d_ss, s));
+    CU(launch_ionic(np, sm->U, sm->Uprev, c->d_node_ptr, c->d_node_w, c->d_node_phi, sm->y, nn,
+                    H.nc, dt, sm->I, sm->d_ss, s));
+    CU(launch_matvec(MODE_RHS, np, c->K, c->K.val_minus, sm->U, w.b, sm->I, sm->F, -H.chi_cm * dt,
+                     dt, nullptr, nullptr, sm->d_ss, dt, sm->prm.stim_duration, nullptr, nullptr, s));
+    CU(launch_copy(sm->U, w.x[0], n, sm->d_ss, s));
+    if (ev_begin) CU(cudaEventRecord(ev_begin, s));
+    if (int st = run_pcg(c, sm->pc, w, s)) return st;
+    if (ev_end) CU(cudaEventRecord(ev_end, s));
+    CU(launch_step_finish(sm->U, sm->Uprev, w.x[0], w.x[1], n, w.sc, sm->d_ss, s));
+    return POLYDG_OK;
+}
+}  // namespace polydg
+
+extern "C" {
 
 int monodomain_step(sim_ctx* sm, int nsteps, void* stream, step_stats* stats) {
     if (!sm) { set_error("monodomain_step: null simulation"); return POLYDG_EINVAL; }
@@ -598,7 +858,13 @@ int monodomain_step(sim_ctx* sm, int nsteps, void* stream, step_stats* stats) {
     h.max_its = 0;
     h.last_relres = 0.0;
     CU(cudaMemcpyAsync(sm->d_ss, &h, sizeof(SimScalars), cudaMemcpyHostToDevice, s));
-    for (int i = 0; i < nsteps; ++i) CU(cudaGraphLaunch(sm->step.exec, s));
+    while ((int)sm->ev.size() < 2 * nsteps) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        sm->ev.push_back(e);
+    }
+    for (int i = 0; i < nsteps; ++i)
+        if (int st = enqueue_step(sm, s, sm->ev[2 * i], sm->ev[2 * i + 1])) return st;
     CU(cudaMemcpyAsync(&h, sm->d_ss, sizeof(SimScalars), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     sm->k = h.k;
@@ -608,6 +874,12 @@ int monodomain_step(sim_ctx* sm, int nsteps, void* stream, step_stats* stats) {
         stats->max_iterations = h.max_its;
         stats->status = h.status;
         stats->last_relres = h.last_relres;
+        double sec = 0.0;
+        for (int i = 0; i < nsteps; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, sm->ev[2 * i], sm->ev[2 * i + 1]) == cudaSuccess) sec += 1e-3 * ms;
+        }
+        stats->pcg_seconds = sec;
     }
     if (h.status != 0) set_error("monodomain_step: a step's PCG solve failed");
     return h.status;
@@ -617,7 +889,7 @@ int sim_get_state(sim_ctx* sm, double* u_dev, double* y_dev, void* stream) {
     if (!sm || !u_dev) { set_error("sim_get_state: null argument"); return POLYDG_EINVAL; }
     polydg_ctx* c = sm->ctx;
     cudaStream_t s = (cudaStream_t)stream;
-    CU(launch_permute(sm->U, u_dev, c->d_to_caller, c->H.nc, c->H.n_p, 0, nullptr, s));
+    CU(launch_permute(sm->U, nullptr, u_dev, c->d_to_caller, c->H.nc, c->H.n_p, 0, nullptr, s));
     if (y_dev) CU(launch_node_gather(sm->y, y_dev, c->d_node_pos, (int64_t)c->H.node_w.size(), s));
     return POLYDG_OK;
 }
@@ -626,9 +898,9 @@ int sim_set_potential(sim_ctx* sm, const double* u_dev, const double* uprev_dev,
     if (!sm || !u_dev) { set_error("sim_set_potential: null argument"); return POLYDG_EINVAL; }
     polydg_ctx* c = sm->ctx;
     cudaStream_t s = (cudaStream_t)stream;
-    CU(launch_permute(u_dev, sm->U, c->d_to_caller, c->H.nc, c->H.n_p, 1, nullptr, s));
-    CU(launch_permute(uprev_dev ? uprev_dev : u_dev, sm->Uprev, c->d_to_caller, c->H.nc, c->H.n_p, 1,
-                      nullptr, s));
+    CU(launch_permute(u_dev, nullptr, sm->U, c->d_to_caller, c->H.nc, c->H.n_p, 1, nullptr, s));
+    CU(launch_permute(uprev_dev ? uprev_dev : u_dev, nullptr, sm->Uprev, c->d_to_caller, c->H.nc,
+                      c->H.n_p, 1, nullptr, s));
     return POLYDG_OK;
 }
 
@@ -636,7 +908,7 @@ int64_t sim_step_index(const sim_ctx* sm) { return sm ? sm->k : -1; }
 
 void sim_destroy(sim_ctx* sm) {
     if (!sm) return;
-    sm->step.release();
+    for (auto e : sm->ev) cudaEventDestroy(e);
     sm->work.release();
     dfree(sm->U); dfree(sm->Uprev); dfree(sm->I); dfree(sm->F); dfree(sm->y); dfree(sm->d_y0);
     dfree(sm->d_ss);
@@ -646,30 +918,21 @@ void sim_destroy(sim_ctx* sm) {
 
 void asm_destroy(asm_ctx* pc) {
     if (!pc) return;
-    if (pc->ctx) {
-        auto& g = pc->ctx->graphs;
-        for (auto it = g.begin(); it != g.end();) {
-            if (it->first.first == pc) { it->second.release(); it = g.erase(it); }
-            else ++it;
-        }
-    }
+    pc->plan.release();
     dfree(pc->d_blocks); dfree(pc->d_tiles); dfree(pc->st64); dfree(pc->st32); dfree(pc->st16);
-    dfree(pc->d_T); dfree(pc->d_agg); dfree(pc->d_agg_ptr); dfree(pc->d_agg_cells);
-    dfree(pc->d_r0); dfree(pc->d_y0); dfree(pc->d_rin); dfree(pc->d_zout);
+    dfree(pc->d_T); dfree(pc->d_agg); dfree(pc->d_pair_ptr); dfree(pc->d_r0p); dfree(pc->d_q0p);
+    dfree(pc->d_y0); dfree(pc->d_rin); dfree(pc->d_zloc); dfree(pc->d_zout); dfree(pc->d_err);
     delete pc;
 }
 
 void polydg_destroy(polydg_ctx* c) {
     if (!c) return;
-    for (auto& kv : c->graphs) kv.second.release();
-    c->graphs.clear();
+    c->id_plan.release();
     c->work.release();
     dfree(c->K.row_ptr); dfree(c->K.col); dfree(c->K.val); dfree(c->K.val_minus);
     dfree(c->d_to_caller); dfree(c->d_node_ptr); dfree(c->d_node_w); dfree(c->d_node_phi);
-    dfree(c->d_node_pos);
+    dfree(c->d_node_pos); dfree(c->d_id_blocks); dfree(c->d_id_tiles); dfree(c->d_zero_ptr);
     if (c->h_sc) cudaFreeHost(c->h_sc);
-    if (c->cap) cudaStreamDestroy(c->cap);
-    if (c->cap2) cudaStreamDestroy(c->cap2);
     delete c;
 }
 

@@ -8,6 +8,7 @@
 namespace polydg {
 
 constexpr int kBlock = 256;            // threads per CTA of the streaming kernels
+constexpr int kPersistThreads = 512;   // threads per CTA of the persistent PCG kernel
 constexpr int kMaxPartials = 1 << 15;  // partial sums per reduction (>= max grid)
 
 // Scalars of one PCG solve, resident in device memory.  Reductions write
@@ -17,30 +18,44 @@ struct PcgScalars {
     double bb;        // |b|^2
     double rr;        // |r_k|^2
     double rz;        // r_k . z_k
-    double rz_old;
+    double rz_loc;    // r_k . (sum_i R_i^T K_i^{-1} R_i r_k)   (local part of r.z)
     double zq;        // z_{k+1} . q_k (flexible beta)
+    double zq_loc;
     double pq;        // p_k . K p_k
     double alpha, beta;
     double rtol2;     // rtol^2
     double relres;
-    int32_t it, maxit, status, done, flexible, pad;
+    int32_t it;       // committed iterations
+    int32_t maxit, status, done, flexible;
+    int32_t pass;     // loop passes; x and r live in buffer (pass & 1)
+    int32_t alpha_valid;
+    int32_t pad;
     uint32_t ticket[8];
 };
 
-enum Ticket { T_MATVEC = 0, T_UPDATE = 1, T_PROLONG = 2, T_INIT = 3, T_IDENT = 4 };
+enum Ticket { T_MATVEC = 0, T_K1 = 1, T_COARSE = 2, T_INIT = 3 };
 
 // status values mirrored from polydg.h
-constexpr int kOK = 0, kENOTSPD = -4, kENOTCONV = -5, kEBREAKDOWN = -6, kENONFINITE = -7;
+constexpr int kOK = 0, kEDEVICE = -3, kENOTSPD = -4, kENOTCONV = -5, kEBREAKDOWN = -6, kENONFINITE = -7;
 
-// One dense block of the ragged local/coarse solve (Eq. prec): out[out_off + i] =
-// sum_j A[i][j] in[in_off + j], A row-major with leading dimension ld (padded
-// with zeros to a multiple of 8 columns).  sel = 0: r/z vectors, 1: coarse r0/y0.
+// One dense block of the ragged preconditioner kernel (Eq. prec).
+//   LOCAL:    rows [0, nrows) of K_i^{-1}; in = out = the subdomain's DOF range.
+//   RESTRICT: the n_q rows of R_0 restricted to the DOFs of one (agglomerate,
+//             subdomain) pair; out_off indexes the pair's partial sums.
+//   IDENTITY: z = r on a DOF range (unpreconditioned CG).
+// Matrices are row-major with leading dimension ld (zero-padded to a multiple
+// of 8 columns); mat_off counts elements of the store of the block's dtype.
+enum TileKind { KIND_LOCAL = 0, KIND_RESTRICT = 1, KIND_IDENTITY = 2 };
+
 struct GemvBlock {
-    int64_t mat_off;   // element offset into the store of this block's dtype
+    int64_t mat_off;
     int64_t in_off, out_off;
-    int32_t n, ld;
-    int32_t sel;       // 0 local, 1 coarse
-    int32_t dtype;     // 0 fp64, 1 fp32, 2 bf16
+    int32_t nrows, ncols, ld;
+    int32_t kind;
+    int32_t dtype;        // 0 fp64, 1 fp32, 2 bf16
+    int32_t pair_begin;   // LOCAL: first entry of its RESTRICT blocks in the sub_pairs list
+    int32_t pair_count;   // LOCAL: number of (agglomerate, subdomain) pairs of this subdomain
+    int32_t pad;
 };
 
 struct GemvTile {

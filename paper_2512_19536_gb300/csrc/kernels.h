@@ -32,30 +32,109 @@ struct DeviceMatrix {
     double* val_minus = nullptr;  // chi_cm M - dt/2 A
 };
 
+// Arguments of the preconditioner kernel K1 (see kernels_linalg.cu).
+struct K1Args {
+    const GemvBlock* blocks;
+    const GemvTile* tiles;
+    int rows;
+    int use_cond;
+    const double* st64;
+    const float* st32;
+    const __nv_bfloat16* st16;
+    double* x[2];              // parity buffers of the iterate
+    double* r[2];              // parity buffers of the residual
+    const double* p;
+    const double* q;           // K p of the previous iteration (nullptr: alpha = 0)
+    double* z;                 // z_loc
+    double* r0p;               // per-(agglomerate, subdomain) partial R_0 r
+    double* q0p;               // per-(agglomerate, subdomain) partial R_0 q
+    PcgScalars* sc;            // nullptr: apply only (no commit, no dots)
+    double* partials;
+    int* err;                  // set to 1 if a bulk copy did not complete in time
+    cudaGraphConditionalHandle cond;
+};
+
+// Arguments of the coarse kernel K2.
+struct K2Args {
+    const double* K0inv;
+    int n0, ld0, nq, rows_per_cta;
+    const int64_t* pair_ptr;   // [n_agg + 1] pairs of each agglomerate
+    const double* r0p;
+    const double* q0p;
+    double* y0;
+    PcgScalars* sc;
+    double* partials;
+};
+
+// Grid-barrier state of a cooperative launch (count returns to 0 after each barrier).
+struct GridSync {
+    unsigned count;
+    unsigned gen;
+};
+
+// Arguments of the persistent PCG kernel (kernels_pcg.cu).  Per-CTA work lists
+// are CSR arrays indexed by blockIdx.x.
+struct PersistArgs {
+    int grid, rows, identity, n0, ld0, nq;
+    int64_t nc;
+    // shared-memory carve-up (byte offsets)
+    size_t buf_bytes, xs_off, rp_off, qp_off, zs_off, r0_off, pn_off;
+    // K_h (column-major blocks) and the per-CTA matvec plan: the elements whose
+    // p the CTA needs (its own range first, then neighbours) and, per block of
+    // K_h, the CTA-local index of its column element
+    const int32_t* row_ptr;
+    const double* val;
+    const int32_t* need_ptr;                   // [grid + 1]
+    const int32_t* need;
+    const int32_t* col_local;                  // [n_blocks of K_h]
+    const int64_t* elem_ptr;                   // [grid + 1] own element ranges
+    // preconditioner
+    const GemvBlock* blocks;
+    const GemvTile* tiles;
+    const int32_t* tile_ptr;                   // [grid + 1]
+    const int32_t* sub_pairs;                  // RESTRICT block ids grouped by subdomain
+    const void* store;                         // store of the local inverses (dtype)
+    const double* st64;                        // fp64 store (restriction rows)
+    const double* K0inv;
+    const int64_t* pair_ptr;                   // [n_agg + 1] pairs of each agglomerate
+    const double* T;
+    const int32_t* agg;
+    const int32_t* crow_ptr;                   // [grid + 1] coarse rows
+    // vectors (internal order)
+    const double* b;
+    double* x;
+    double* r[2];
+    double* p[2];
+    double *z, *q;
+    double *r0p, *q0p, *y0;
+    PcgScalars* sc;
+    double* partials;
+    double* bcast;                             // [8] grid sums broadcast by the barrier
+    GridSync* gs;
+    int* err;
+};
+
+constexpr int kStages = 3;                     // bulk-copy pipeline depth of the P phase
+
+cudaError_t launch_pcg_persistent(int dtype, int np, const PersistArgs& a, size_t smem,
+                                  cudaStream_t s);
+cudaError_t persistent_occupancy(int dtype, int np, size_t smem, int* blocks_per_sm);
+
 cudaError_t launch_matvec(int mode, int np, const DeviceMatrix& K, const double* val,
                           const double* x, double* y, const double* v1, const double* v2,
                           double c1, double c2, PcgScalars* sc, double* partials,
-                          const SimScalars* ss, double dt, double stim_duration, cudaStream_t s);
-cudaError_t launch_update(double* x, double* r, const double* p, const double* q, int64_t n,
-                          PcgScalars* sc, double* partials, cudaGraphConditionalHandle cond,
-                          int use_cond, cudaStream_t s);
-cudaError_t launch_direction(double* p, const double* z, int64_t n, const PcgScalars* sc,
-                             cudaStream_t s);
-cudaError_t launch_identity_dots(const double* r, const double* q, int64_t n, PcgScalars* sc,
-                                 double* partials, cudaStream_t s);
-cudaError_t launch_restrict(int np, int nq, const double* r, const double* T,
-                            const int64_t* agg_ptr, const int32_t* agg_cells, int n_agg,
-                            double* r0, const int* done, cudaStream_t s);
-cudaError_t launch_prolong(int np, int nq, double* z, const double* T, const int32_t* agg,
-                           const double* y0, int64_t nc, const double* r, const double* q,
-                           PcgScalars* sc, double* partials, cudaStream_t s);
-cudaError_t launch_gemv(const GemvBlock* blocks, const GemvTile* tiles, int ntiles, int rows,
-                        int max_ld, const double* st64, const float* st32,
-                        const __nv_bfloat16* st16, const double* r, const double* r0,
-                        double* z, double* y0, const int* done, cudaStream_t s);
-cudaError_t set_gemv_smem(int max_ld);
-cudaError_t launch_permute(const double* src, double* dst, const int64_t* to_caller, int64_t nc,
-                           int np, int to_internal, const PcgScalars* zero_if_b0, cudaStream_t s);
+                          const SimScalars* ss, double dt, double stim_duration, double* zero1,
+                          double* zero2, cudaStream_t s);
+cudaError_t launch_precond(const K1Args& a, int dtype, int ntiles, size_t smem, cudaStream_t s);
+cudaError_t set_precond_smem(size_t smem);
+cudaError_t launch_coarse(const K2Args& a, cudaStream_t s);
+cudaError_t set_coarse_smem(size_t smem);
+cudaError_t launch_direction(int nq, double* p, const double* zl, const double* T,
+                             const int32_t* agg, const double* y0, int64_t nc, int np,
+                             const PcgScalars* sc, double* out, cudaStream_t s);
+cudaError_t launch_permute(const double* src, const double* src_odd, double* dst,
+                           const int64_t* to_caller, int64_t nc, int np, int to_internal,
+                           const PcgScalars* sc, cudaStream_t s);
 cudaError_t launch_copy(const double* src, double* dst, int64_t n, const SimScalars* ss,
                         cudaStream_t s);
 cudaError_t launch_extract_local(const DeviceMatrix& K, const int64_t* sub_ptr, int n_sub,
@@ -74,8 +153,8 @@ cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int
                          int64_t nc, double dt, double* I, const SimScalars* ss, cudaStream_t s);
 cudaError_t launch_node_gather(const double* y_int, double* y_caller,
                                const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s);
-cudaError_t launch_step_finish(double* U, double* Uprev, const double* x, int64_t n,
-                               const PcgScalars* sc, SimScalars* ss, cudaStream_t s);
+cudaError_t launch_step_finish(double* U, double* Uprev, const double* x0, const double* x1,
+                               int64_t n, const PcgScalars* sc, SimScalars* ss, cudaStream_t s);
 cudaError_t launch_step_begin(PcgScalars* sc, const SimScalars* ss, cudaStream_t s);
 cudaError_t launch_init_y(double* y, int64_t nn, const double* y0, cudaStream_t s);
 

@@ -113,10 +113,11 @@ cudaError_t launch_step_begin(PcgScalars* sc, const SimScalars* ss, cudaStream_t
 
 // U^{k-1} <- U^k, U^k <- x, k <- k + 1 and the step statistics.
 __global__ void step_finish_kernel(double* __restrict__ U, double* __restrict__ Uprev,
-                                   const double* __restrict__ x, int64_t n,
-                                   const PcgScalars* sc, SimScalars* ss) {
+                                   const double* __restrict__ x0, const double* __restrict__ x1,
+                                   int64_t n, const PcgScalars* sc, SimScalars* ss) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = !ss->failed;
+    const double* x = (sc->pass & 1) ? x1 : x0;   // the iterate lives in buffer (pass & 1)
     if (ok && t < n) {
         Uprev[t] = U[t];
         U[t] = x[t];
@@ -136,9 +137,9 @@ __global__ void step_stats_kernel(const PcgScalars* sc, SimScalars* ss) {
     }
 }
 
-cudaError_t launch_step_finish(double* U, double* Uprev, const double* x, int64_t n,
-                               const PcgScalars* sc, SimScalars* ss, cudaStream_t s) {
-    step_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, Uprev, x, n, sc, ss);
+cudaError_t launch_step_finish(double* U, double* Uprev, const double* x0, const double* x1,
+                               int64_t n, const PcgScalars* sc, SimScalars* ss, cudaStream_t s) {
+    step_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, Uprev, x0, x1, n, sc, ss);
     step_stats_kernel<<<1, 32, 0, s>>>(sc, ss);
     return cudaGetLastError();
 }

@@ -1,11 +1,17 @@
-// Linear-algebra kernels of libpolydg on the PCG hot path (Sec. 4, Eq. prec, PCG):
-//   * block-sparse SIP-DG matvec q = K_h p (float64; Eq. coer + mass, Sec. 3),
-//     fused with the PCG dot products and coefficient updates;
-//   * ragged batched dense GEMV with the local inverses K_i^{-1} (fp64/fp32/bf16
-//     store) and the coarse inverse K_0^{-1} (fp64) in one launch;
-//   * coarse restriction R_0 r and prolongation R_0^T y (L2-projection blocks T_K);
-//   * fused PCG vector updates with deterministic last-CTA reductions;
-//   * setup: batched Cholesky factorisation and inversion of K_i and K_0.
+// Linear-algebra kernels of libpolydg on the PCG hot path (Sec. 4, Eq. prec, PCG).
+// One PCG iteration is four kernels (graph nodes):
+//   K1 precond_kernel   x += alpha p, r -= alpha q (double-buffered), then per
+//                       subdomain the ragged GEMV z_loc = K_i^{-1} r_i (fp64/fp32/bf16
+//                       store) and the coarse restriction R_0 r (fp64), with
+//                       |r|^2, r.z_loc, z_loc.q and the stopping test;
+//   K2 coarse_kernel    y0 = K_0^{-1} r0 (fp64), r.z = r.z_loc + r0.y0, beta;
+//   K3 direction_kernel p = z_loc + R_0^T y0 + beta p;
+//   K4 matvec_kernel    q = K_h p (fp64, warp per element), p.q, alpha.
+// The identities r.(R_0^T y0) = (R_0 r).y0 and z.q = z_loc.q + y0.(R_0 q) let
+// the dot products close before the prolongation, so K3 needs no reduction.
+// Also here: setup kernels (batched Cholesky inversion of K_i and K_0).
+#include <type_traits>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -15,53 +21,95 @@
 namespace polydg {
 
 // ------------------------------------------------------------------ matvec
-// Thread per DOF row (e, i); row e of K_h holds blocks row_ptr[e]..row_ptr[e+1]-1
-// (n_p x n_p, row-major).  MODE_PLAIN: y = K x.  MODE_PCG: q = K p, then
-// alpha = (r.z)/(p.q).  MODE_RESID: r = b - K x, |b|^2, |r|^2, first
-// convergence test.  MODE_RHS: y = Kminus x + c1 v1 + c2(t) v2.
+// Two warps per element e (warp h = 0, 1 of a pair).  Row e of K_h holds m_e
+// blocks (diagonal first) stored consecutively, each column-major, so the row
+// is an [m_e * NP columns][NP rows] column-major panel.  Lane (i, g), i < NP,
+// g < G = 32 / NP, of warp h accumulates row i over columns g + h G, g + 3 G,
+// ... : each warp load reads G * NP consecutive doubles.  The pair's partial
+// rows are summed through shared memory.
+//   MODE_PLAIN: y = K x.
+//   MODE_PCG:   q = K p; p.q -> alpha = (r.z)/(p.q).
+//   MODE_RESID: r = b - K x; |b|^2, |r|^2, first stopping test; zeroes p, q.
+//   MODE_RHS:   y = Kminus x + c1 v1 + c2 [t^{k+1/2} < t_stim] v2.
+constexpr int kElemsPerCta = kBlock / 64;
+
 template <int NP, int MODE>
 __global__ void __launch_bounds__(kBlock)
-bsr_matvec_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                  const double* __restrict__ val, const double* __restrict__ x,
-                  double* __restrict__ y, int64_t nc, const double* __restrict__ v1,
-                  const double* __restrict__ v2, double c1, double c2, PcgScalars* sc,
-                  double* partials, const SimScalars* ss, double dt, double stim_duration) {
+matvec_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+              const double* __restrict__ val, const double* __restrict__ x,
+              double* __restrict__ y, int64_t nc, const double* __restrict__ v1,
+              const double* __restrict__ v2, double c1, double c2, PcgScalars* sc,
+              double* partials, const SimScalars* ss, double dt, double stim_duration,
+              double* __restrict__ zero1, double* __restrict__ zero2) {
+    constexpr int G = 32 / NP;
     __shared__ double sh[32];
+    __shared__ double half[kElemsPerCta][32];
     __shared__ bool last;
     if (MODE == MODE_PCG || MODE == MODE_RESID) {
         if (sc->done) return;
     }
     if (ss && ss->failed) return;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t n = nc * NP;
-    double acc = 0.0, xr = 0.0, vr = 0.0;
-    if (t < n) {
-        const int64_t e = t / NP;
-        const int i = (int)(t - e * NP);
-        const int32_t b0 = row_ptr[e], b1 = row_ptr[e + 1];
-        for (int32_t bi = b0; bi < b1; ++bi) {
-            const double* B = val + (int64_t)bi * NP * NP + i * NP;
-            const double* xc = x + (int64_t)col[bi] * NP;
-#pragma unroll
-            for (int j = 0; j < NP; ++j) acc = fma(__ldg(B + j), __ldg(xc + j), acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, h = warp & 1, slot = warp >> 1;
+    const int64_t e = (int64_t)blockIdx.x * kElemsPerCta + slot;
+    const int g = (lane < G * NP) ? lane / NP : 2 * G;
+    const int i = lane - (lane / NP) * NP;
+    double acc0 = 0.0, acc1 = 0.0;
+    const bool valid = e < nc;
+    if (valid) {
+        const int32_t b0 = row_ptr[e];
+        const int ncol = (row_ptr[e + 1] - b0) * NP;
+        const double* V = val + (int64_t)b0 * NP * NP;
+        const int32_t* cl = col + b0;
+        int c = g + h * G;
+        for (; c + 2 * G < ncol; c += 4 * G) {
+            const int c2 = c + 2 * G;
+            const int s1 = c / NP, s2 = c2 / NP;
+            const double v1 = __ldg(V + (int64_t)c * NP + i), v2 = __ldg(V + (int64_t)c2 * NP + i);
+            const double x1 = __ldg(x + (int64_t)__ldg(cl + s1) * NP + (c - s1 * NP));
+            const double x2 = __ldg(x + (int64_t)__ldg(cl + s2) * NP + (c2 - s2 * NP));
+            acc0 = fma(v1, x1, acc0);
+            acc1 = fma(v2, x2, acc1);
         }
+        if (c < ncol) {
+            const int s1 = c / NP;
+            acc0 = fma(__ldg(V + (int64_t)c * NP + i), __ldg(x + (int64_t)__ldg(cl + s1) * NP + (c - s1 * NP)), acc0);
+        }
+    }
+    double acc = acc0 + acc1;
+    {   // lane i < NP sums the partials of lanes i + k NP (k < G), which are < G NP <= 32
+        double tot = acc;
+#pragma unroll
+        for (int k = 1; k < G; ++k) tot += __shfl_down_sync(0xffffffffu, acc, k * NP);
+        acc = tot;
+    }
+    if (h == 1) half[slot][lane] = acc;
+    __syncthreads();
+    if (h == 0) acc += half[slot][lane];
+    const bool owner = valid && h == 0 && lane < NP;
+    const int64_t t = e * NP + i;
+    double d0 = 0.0, d1 = 0.0;
+    if (owner) {
         if (MODE == MODE_PLAIN) {
             y[t] = acc;
         } else if (MODE == MODE_PCG) {
             y[t] = acc;
-            xr = x[t];
+            d0 = x[t] * acc;
         } else if (MODE == MODE_RESID) {
-            vr = v1[t];
-            acc = vr - acc;
-            y[t] = acc;
-        } else {  // MODE_RHS
+            const double bv = v1[t];
+            const double rv = bv - acc;
+            y[t] = rv;
+            zero1[t] = 0.0;
+            zero2[t] = 0.0;
+            d0 = bv * bv;
+            d1 = rv * rv;
+        } else {
             const double tmid = ((double)ss->k + 0.5) * dt;
             const double on = (tmid < stim_duration) ? 1.0 : 0.0;
             y[t] = acc + c1 * v1[t] + c2 * on * v2[t];
         }
     }
     if (MODE == MODE_PCG) {
-        const double s = block_sum(xr * acc, sh);
+        const double s = block_sum(d0, sh);
         if (publish_partials(partials, &s, 1, &sc->ticket[T_MATVEC], &last)) {
             const double pq = sum_partials(partials, gridDim.x, sh);
             if (threadIdx.x == 0) {
@@ -72,13 +120,14 @@ bsr_matvec_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict
                     sc->done = 1;
                 } else {
                     sc->alpha = sc->rz / pq;
+                    sc->alpha_valid = 1;
                 }
             }
         }
     } else if (MODE == MODE_RESID) {
         double s[2];
-        s[0] = block_sum(vr * vr, sh);
-        s[1] = block_sum(acc * acc, sh);
+        s[0] = block_sum(d0, sh);
+        s[1] = block_sum(d1, sh);
         if (publish_partials(partials, s, 2, &sc->ticket[T_INIT], &last)) {
             const double bb = sum_partials(partials, gridDim.x, sh);
             const double rr = sum_partials(partials + kMaxPartials, gridDim.x, sh);
@@ -87,6 +136,10 @@ bsr_matvec_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict
                 sc->bb = bb;
                 sc->rr = rr;
                 sc->it = 0;
+                sc->pass = 0;
+                sc->alpha = 0.0;
+                sc->alpha_valid = 0;
+                sc->beta = 0.0;
                 sc->status = kOK;
                 if (!finite(bb) || !finite(rr)) {
                     sc->status = kENONFINITE;
@@ -104,37 +157,251 @@ bsr_matvec_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict
     }
 }
 
-// ------------------------------------------------------------- PCG vectors
-// x += alpha p; r -= alpha q; |r|^2 -> convergence test (Euclidean norm of the
-// relative residual, Sec. 5).  Last kernel of the loop body: ends the device
-// loop through the graph's conditional handle when done.
+// ---------------------------------------------------- K1: update + precond
+// One CTA per tile (rows [row0, row0 + rows) of one LOCAL block).  Thread 0
+// starts a single bulk copy (cp.async.bulk, completion on an mbarrier) of the
+// tile's rows of K_i^{-1} into shared memory; meanwhile the CTA stages the
+// block's input r' = r - alpha q (fp64 for the fp64 store, fp32 otherwise).
+// Each warp then reduces rows from shared memory.  A second pass over the
+// tile's own rows commits x and r into the other parity buffer and adds the
+// |r'|^2, r'.z and z.q terms.  RESTRICT tiles (the n_q rows of R_0 on one
+// (agglomerate, subdomain) pair, fp64) read their rows directly.
+constexpr uint32_t kMaxSpin = 1u << 22;   // bounded mbarrier polls (~0.1-1 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on phase 0 of `bar`; false if the copy did not land in time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar) {
+    for (uint32_t k = 0; k < kMaxSpin; ++k)
+        if (mbar_try_wait(bar, 0)) return true;
+    return false;
+}
+
+__device__ __forceinline__ double dot_row64(const double* __restrict__ Ar, const double* xs, int ld,
+                                            int lane) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int c = 2 * lane; c < ld; c += 64) {
+        const double2 u = *reinterpret_cast<const double2*>(Ar + c);
+        a0 = fma(u.x, xs[c], a0);
+        a1 = fma(u.y, xs[c + 1], a1);
+    }
+    return warp_sum(a0 + a1);
+}
+
+__device__ __forceinline__ float dot_row32(const float* Ar, const float* xs, int ld, int lane) {
+    float a0 = 0.f, a1 = 0.f;
+    for (int c = 4 * lane; c < ld; c += 128) {
+        const float4 u = *reinterpret_cast<const float4*>(Ar + c);
+        const float4 v = *reinterpret_cast<const float4*>(xs + c);
+        a0 = fmaf(u.x, v.x, a0); a1 = fmaf(u.y, v.y, a1);
+        a0 = fmaf(u.z, v.z, a0); a1 = fmaf(u.w, v.w, a1);
+    }
+    return warp_sumf(a0 + a1);
+}
+
+__device__ __forceinline__ float dot_row16(const __nv_bfloat16* Ar, const float* xs, int ld, int lane) {
+    float a0 = 0.f, a1 = 0.f;
+    for (int c = 8 * lane; c < ld; c += 256) {
+        const uint4 v = *reinterpret_cast<const uint4*>(Ar + c);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+        const float4 x0 = *reinterpret_cast<const float4*>(xs + c);
+        const float4 x1 = *reinterpret_cast<const float4*>(xs + c + 4);
+        float2 f = __bfloat1622float2(h[0]);
+        a0 = fmaf(f.x, x0.x, a0); a1 = fmaf(f.y, x0.y, a1);
+        f = __bfloat1622float2(h[1]);
+        a0 = fmaf(f.x, x0.z, a0); a1 = fmaf(f.y, x0.w, a1);
+        f = __bfloat1622float2(h[2]);
+        a0 = fmaf(f.x, x1.x, a0); a1 = fmaf(f.y, x1.y, a1);
+        f = __bfloat1622float2(h[3]);
+        a0 = fmaf(f.x, x1.z, a0); a1 = fmaf(f.y, x1.w, a1);
+    }
+    return warp_sumf(a0 + a1);
+}
+
+// Shared-memory layout of a LOCAL tile: [rows x ld store elements][ld staged
+// inputs][rows doubles z].  Returns the byte offsets.
+template <int DT>
+struct TileLayout {
+    using T = typename std::conditional<DT == 0, double, typename std::conditional<DT == 1, float, __nv_bfloat16>::type>::type;
+    using X = typename std::conditional<DT == 0, double, float>::type;
+};
+
+template <int DT>
 __global__ void __launch_bounds__(kBlock)
-pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                  const double* __restrict__ q, int64_t n, PcgScalars* sc, double* partials,
-                  cudaGraphConditionalHandle cond, int use_cond) {
+precond_kernel(K1Args a) {
+    using T = typename TileLayout<DT>::T;
+    using X = typename TileLayout<DT>::X;
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double sh[32];
     __shared__ bool last;
-    if (sc->done) {
-        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+    __shared__ __align__(8) uint64_t bar;
+    PcgScalars* sc = a.sc;
+    if (sc && sc->done) {
+        if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
         return;
     }
-    const double alpha = sc->alpha;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double rn = 0.0;
-    if (t < n) {
-        x[t] = fma(alpha, p[t], x[t]);
-        rn = fma(-alpha, q[t], r[t]);
-        r[t] = rn;
-    }
-    const double s = block_sum(rn * rn, sh);
-    if (publish_partials(partials, &s, 1, &sc->ticket[T_UPDATE], &last)) {
-        const double rr = sum_partials(partials, gridDim.x, sh);
+    const int par = sc ? (sc->pass & 1) : 0;
+    const double* __restrict__ xin = a.x[par];
+    const double* __restrict__ rin = a.r[par];
+    double* __restrict__ xout = a.x[par ^ 1];
+    double* __restrict__ rout = a.r[par ^ 1];
+    const double alpha = (sc && sc->alpha_valid) ? sc->alpha : 0.0;
+    const bool flexible = sc && sc->flexible;
+    const GemvTile tile = a.tiles[blockIdx.x];
+    const GemvBlock B = a.blocks[tile.block];
+    const double* __restrict__ ri = rin + B.in_off;
+    const double* __restrict__ qi = a.q ? a.q + B.in_off : nullptr;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double prr = 0.0, prz = 0.0, pzq = 0.0;
+    if (B.kind == KIND_RESTRICT) {
+        double* rs = reinterpret_cast<double*>(smem);
+        double* qs = rs + B.ld;
+        for (int j = threadIdx.x; j < B.ld; j += blockDim.x) {
+            const bool in = j < B.ncols;
+            const double qv = (in && qi) ? qi[j] : 0.0;
+            rs[j] = in ? fma(-alpha, qv, ri[j]) : 0.0;
+            qs[j] = flexible ? qv : 0.0;
+        }
+        __syncthreads();
+        const double* R = a.st64 + B.mat_off;
+        for (int row = warp; row < B.nrows; row += nw) {
+            const double* Rr = R + (int64_t)row * B.ld;
+            const double yr = dot_row64(Rr, rs, B.ld, lane);
+            const double yq = flexible ? dot_row64(Rr, qs, B.ld, lane) : 0.0;
+            if (lane == 0) {
+                a.r0p[B.out_off + row] = yr;
+                a.q0p[B.out_off + row] = yq;
+            }
+        }
+    } else if (B.kind == KIND_LOCAL) {
+        const int nrt = min(a.rows, B.nrows - tile.row0);          // rows of this tile
+        const T* gsrc = reinterpret_cast<const T*>(DT == 0 ? (const void*)a.st64
+                                                           : DT == 1 ? (const void*)a.st32
+                                                                     : (const void*)a.st16) +
+                        B.mat_off + (int64_t)tile.row0 * B.ld;
+        T* As = reinterpret_cast<T*>(smem);
+        const size_t abytes = (((size_t)a.rows * B.ld * sizeof(T)) + 15) & ~(size_t)15;
+        X* xs = reinterpret_cast<X*>(smem + abytes);
+        double* zs = reinterpret_cast<double*>(smem + abytes + (((size_t)B.ld * sizeof(X) + 15) & ~(size_t)15));
+        const uint32_t bytes = (uint32_t)((size_t)nrt * B.ld * sizeof(T));
         if (threadIdx.x == 0) {
-            sc->ticket[T_UPDATE] = 0;
+            mbar_init(&bar, 1);
+            mbar_expect_tx(&bar, bytes);
+            bulk_copy_g2s(As, gsrc, bytes, &bar);
+        }
+        for (int j = threadIdx.x; j < B.ld; j += blockDim.x)
+            xs[j] = (j < B.ncols) ? (X)(qi ? fma(-alpha, qi[j], ri[j]) : ri[j]) : (X)0;
+        __syncthreads();                       // xs staged, mbarrier initialised
+        const bool landed = mbar_wait_bounded(&bar);
+        if (!landed) {
+            // The copy did not complete in time: flag it and wait once more (bounded)
+            // for the copy in flight.  The tile still takes part in the reductions,
+            // so the last CTA ends the solve with an error status.
+            if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+            mbar_wait_bounded(&bar);
+        }
+        for (int rr = warp; rr < nrt; rr += nw) {
+            if (!landed) {
+                if (lane == 0) zs[rr] = 0.0;
+                continue;
+            }
+            double zr;
+            if (DT == 0) zr = dot_row64(reinterpret_cast<const double*>(As) + (size_t)rr * B.ld,
+                                        reinterpret_cast<const double*>(xs), B.ld, lane);
+            else if (DT == 1) zr = (double)dot_row32(reinterpret_cast<const float*>(As) + (size_t)rr * B.ld,
+                                                     reinterpret_cast<const float*>(xs), B.ld, lane);
+            else zr = (double)dot_row16(reinterpret_cast<const __nv_bfloat16*>(As) + (size_t)rr * B.ld,
+                                        reinterpret_cast<const float*>(xs), B.ld, lane);
+            if (lane == 0) zs[rr] = zr;
+        }
+        __syncthreads();
+        for (int rr = threadIdx.x; rr < nrt; rr += blockDim.x) {
+            const int row = tile.row0 + rr;
+            const int64_t t = B.in_off + row;
+            const double zr = zs[rr];
+            a.z[t] = zr;
+            if (sc) {
+                const double qv = qi ? qi[row] : 0.0;
+                const double rp = fma(-alpha, qv, ri[row]);
+                rout[t] = rp;
+                xout[t] = fma(alpha, a.p[t], xin[t]);
+                prr = fma(rp, rp, prr);
+                prz = fma(rp, zr, prz);
+                if (flexible) pzq = fma(zr, qv, pzq);
+            }
+        }
+    } else {  // KIND_IDENTITY: z = r'
+        const int rend = min(tile.row0 + a.rows, B.nrows);
+        for (int row = tile.row0 + threadIdx.x; row < rend; row += blockDim.x) {
+            const int64_t t = B.in_off + row;
+            const double qv = qi ? qi[row] : 0.0;
+            const double rp = fma(-alpha, qv, ri[row]);
+            a.z[t] = rp;
+            if (sc) {
+                rout[t] = rp;
+                xout[t] = fma(alpha, a.p[t], xin[t]);
+                prr = fma(rp, rp, prr);
+                prz = fma(rp, rp, prz);
+                if (flexible) pzq = fma(rp, qv, pzq);
+            }
+        }
+    }
+    if (!sc) return;
+    double s[3];
+    s[0] = block_sum(prr, sh);
+    s[1] = block_sum(prz, sh);
+    s[2] = block_sum(pzq, sh);
+    if (publish_partials(a.partials, s, 3, &sc->ticket[T_K1], &last)) {
+        const double rr = sum_partials(a.partials, gridDim.x, sh);
+        const double rz = sum_partials(a.partials + kMaxPartials, gridDim.x, sh);
+        const double zq = sum_partials(a.partials + 2 * kMaxPartials, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            sc->ticket[T_K1] = 0;
             sc->rr = rr;
-            sc->it += 1;
+            sc->rz_loc = rz;
+            sc->zq_loc = zq;
+            sc->it += sc->alpha_valid;
+            sc->alpha_valid = 0;
+            sc->pass += 1;
             sc->relres = sqrt(rr / sc->bb);
-            if (!finite(rr)) {
+            if (a.err && *a.err) {
+                sc->status = kEDEVICE;
+                sc->done = 1;
+            } else if (!finite(rr) || !finite(rz)) {
                 sc->status = kENONFINITE;
                 sc->done = 1;
             } else if (rr <= sc->rtol2 * sc->bb) {
@@ -144,22 +411,15 @@ pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* 
                 sc->status = kENOTCONV;
                 sc->done = 1;
             }
-            if (sc->done && use_cond) cudaGraphSetConditional(cond, 0);
+            if (sc->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
         }
     }
 }
 
-// p = z + beta p (beta = 0 on the first iteration).
-__global__ void __launch_bounds__(kBlock)
-pcg_direction_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n,
-                     const PcgScalars* sc) {
-    if (sc->done) return;
-    const double beta = sc->beta;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) p[t] = fma(beta, p[t], z[t]);
-}
-
-// Shared tail of the preconditioner kernels: given r.z and z.q sums, form beta.
+// ------------------------------------------------------------ K2: coarse
+// r0 and q0 are assembled from the (agglomerate, subdomain) partial sums in
+// fixed order; warp per row of K_0^{-1}: y0 = K_0^{-1} r0.  Then
+// r.z = r.z_loc + r0.y0, z.q = z_loc.q + q0.y0 and the new beta.
 __device__ __forceinline__ void finish_beta(PcgScalars* sc, double rz, double zq) {
     if (!finite(rz) || !finite(zq)) {
         sc->status = kENONFINITE;
@@ -174,7 +434,6 @@ __device__ __forceinline__ void finish_beta(PcgScalars* sc, double rz, double zq
     } else {
         sc->beta = rz / sc->rz;
     }
-    sc->rz_old = sc->rz;
     sc->rz = rz;
     sc->zq = zq;
     if (!finite(sc->beta) || rz == 0.0) {
@@ -183,201 +442,101 @@ __device__ __forceinline__ void finish_beta(PcgScalars* sc, double rz, double zq
     }
 }
 
-// Unpreconditioned CG: z = r (the direction kernel reads r); r.r and r.q.
 __global__ void __launch_bounds__(kBlock)
-identity_dots_kernel(const double* __restrict__ r, const double* __restrict__ q, int64_t n,
-                     PcgScalars* sc, double* partials) {
+coarse_kernel(K2Args a) {
+    extern __shared__ double cs[];
     __shared__ double sh[32];
     __shared__ bool last;
-    if (sc->done) return;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double a = 0.0, b = 0.0;
-    const bool use_q = sc->it > 0 && sc->flexible;   // q = K p_{k-1} exists from k = 1
-    if (t < n) {
-        const double rv = r[t];
-        a = rv * rv;
-        if (use_q) b = rv * q[t];
-    }
-    double s[2];
-    s[0] = block_sum(a, sh);
-    s[1] = block_sum(b, sh);
-    if (publish_partials(partials, s, 2, &sc->ticket[T_IDENT], &last)) {
-        const double rz = sum_partials(partials, gridDim.x, sh);
-        const double zq = sum_partials(partials + kMaxPartials, gridDim.x, sh);
-        if (threadIdx.x == 0) {
-            sc->ticket[T_IDENT] = 0;
-            finish_beta(sc, rz, zq);
-        }
-    }
-}
-
-// ------------------------------------------------------ coarse restriction
-// r0[J*NQ + a] = sum_{e in J} sum_i T_e[i][a] r[e*NP + i]   (R_0 = (R_0^T)^T).
-// One warp per agglomerate; lanes stride over its (cell, i) pairs.
-template <int NP, int NQ>
-__global__ void restrict_kernel(const double* __restrict__ r, const double* __restrict__ T,
-                                const int64_t* __restrict__ agg_ptr,
-                                const int32_t* __restrict__ agg_cells, int n_agg,
-                                double* __restrict__ r0, const int* done) {
-    if (done && *done) return;
-    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (warp >= n_agg) return;
-    double acc[NQ];
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) acc[a] = 0.0;
-    const int64_t p0 = agg_ptr[warp], cnt = (agg_ptr[warp + 1] - p0) * NP;
-    for (int64_t idx = lane; idx < cnt; idx += 32) {
-        const int64_t e = agg_cells[p0 + idx / NP];
-        const int i = (int)(idx % NP);
-        const double rv = r[e * NP + i];
-        const double* Tr = T + (e * NP + i) * NQ;
-#pragma unroll
-        for (int a = 0; a < NQ; ++a) acc[a] = fma(Tr[a], rv, acc[a]);
-    }
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) {
-        const double s = warp_sum(acc[a]);
-        if (lane == 0) r0[(int64_t)warp * NQ + a] = s;
-    }
-}
-
-// z[e][i] += sum_a T_e[i][a] y0[J(e)][a]; with sc != nullptr also r.z and z.q
-// (q = K p of the previous iteration) and the new beta.
-template <int NP, int NQ>
-__global__ void __launch_bounds__(kBlock)
-prolong_kernel(double* __restrict__ z, const double* __restrict__ T, const int32_t* __restrict__ agg,
-               const double* __restrict__ y0, int64_t nc, const double* __restrict__ r,
-               const double* __restrict__ q, PcgScalars* sc, double* partials) {
-    __shared__ double sh[32];
-    __shared__ bool last;
+    PcgScalars* sc = a.sc;
     if (sc && sc->done) return;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double a = 0.0, b = 0.0;
-    if (t < nc * NP) {
-        const int64_t e = t / NP;
-        double zt = z[t];
-        if (T) {
-            const double* Tr = T + t * NQ;
-            const double* y = y0 + (int64_t)agg[e] * NQ;
-#pragma unroll
-            for (int k = 0; k < NQ; ++k) zt = fma(Tr[k], y[k], zt);
-            z[t] = zt;
+    const int n0 = a.n0;
+    double* r0s = cs;
+    double* q0s = cs + n0;
+    const bool flexible = sc && sc->flexible;
+    for (int idx = threadIdx.x; idx < n0; idx += blockDim.x) {
+        const int J = idx / a.nq, k = idx - J * a.nq;
+        double sr = 0.0, sq = 0.0;
+        for (int64_t pp = a.pair_ptr[J]; pp < a.pair_ptr[J + 1]; ++pp) {
+            sr += a.r0p[pp * a.nq + k];
+            if (flexible) sq += a.q0p[pp * a.nq + k];
         }
-        if (sc) {
-            a = r[t] * zt;
-            if (sc->it > 0 && sc->flexible) b = zt * q[t];   // q = K p_{k-1} exists from k = 1
+        r0s[idx] = sr;
+        q0s[idx] = sq;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double pr = 0.0, pq = 0.0;
+    const int row = blockIdx.x * (blockDim.x >> 5) + warp;       // warp per row of K_0^{-1}
+    if (row < n0) {
+        const double* Kr = a.K0inv + (int64_t)row * a.ld0;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int c = lane;
+        for (; c + 96 < n0; c += 128) {
+            a0 = fma(__ldg(Kr + c), r0s[c], a0);
+            a1 = fma(__ldg(Kr + c + 32), r0s[c + 32], a1);
+            a2 = fma(__ldg(Kr + c + 64), r0s[c + 64], a2);
+            a3 = fma(__ldg(Kr + c + 96), r0s[c + 96], a3);
+        }
+        for (; c < n0; c += 32) a0 = fma(__ldg(Kr + c), r0s[c], a0);
+        const double acc = warp_sum((a0 + a1) + (a2 + a3));
+        if (lane == 0) {
+            a.y0[row] = acc;
+            pr = acc * r0s[row];
+            pq = acc * q0s[row];
         }
     }
     if (!sc) return;
     double s[2];
-    s[0] = block_sum(a, sh);
-    s[1] = block_sum(b, sh);
-    if (publish_partials(partials, s, 2, &sc->ticket[T_PROLONG], &last)) {
-        const double rz = sum_partials(partials, gridDim.x, sh);
-        const double zq = sum_partials(partials + kMaxPartials, gridDim.x, sh);
+    s[0] = block_sum(pr, sh);
+    s[1] = block_sum(pq, sh);
+    if (publish_partials(a.partials, s, 2, &sc->ticket[T_COARSE], &last)) {
+        const double r0y = sum_partials(a.partials, gridDim.x, sh);
+        const double q0y = sum_partials(a.partials + kMaxPartials, gridDim.x, sh);
         if (threadIdx.x == 0) {
-            sc->ticket[T_PROLONG] = 0;
-            finish_beta(sc, rz, zq);
+            sc->ticket[T_COARSE] = 0;
+            finish_beta(sc, sc->rz_loc + r0y, sc->zq_loc + q0y);
         }
     }
 }
 
-// ------------------------------------------------------------- ragged GEMV
-// One CTA per tile of `rows` rows of one dense block.  The block's input
-// vector is staged in shared memory (converted to the accumulation type and
-// zero-padded to ld); each warp streams whole rows with 16-byte loads.
-template <typename TA>
-__device__ __forceinline__ TA dot16(const double* a, const TA* x) {
-    const double2 v = *reinterpret_cast<const double2*>(a);
-    return (TA)(v.x * (double)x[0] + v.y * (double)x[1]);
-}
-
-__device__ __forceinline__ float dot16f(const float* a, const float* x) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(a));
-    return v.x * x[0] + v.y * x[1] + v.z * x[2] + v.w * x[3];
-}
-
-__device__ __forceinline__ float dot16b(const __nv_bfloat16* a, const float* x) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(a));
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
-    float s = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float2 f = __bfloat1622float2(h[k]);
-        s = fmaf(f.x, x[2 * k], s);
-        s = fmaf(f.y, x[2 * k + 1], s);
-    }
-    return s;
-}
-
+// --------------------------------------------------------- K3: direction
+// p = z_loc + T_e y0_{J(e)} + beta p   (z = z_loc + R_0^T y0, Eq. prec).
+// With sc == nullptr it writes out = z_loc + R_0^T y0 instead (asm_apply).
+template <int NQ>
 __global__ void __launch_bounds__(kBlock)
-ragged_gemv_kernel(const GemvBlock* __restrict__ blocks, const GemvTile* __restrict__ tiles,
-                   int rows, const double* __restrict__ st64, const float* __restrict__ st32,
-                   const __nv_bfloat16* __restrict__ st16, const double* __restrict__ r,
-                   const double* __restrict__ r0, double* __restrict__ z, double* __restrict__ y0,
-                   const int* done) {
-    extern __shared__ double xs_raw[];
-    if (done && *done) return;
-    const GemvTile tile = tiles[blockIdx.x];
-    const GemvBlock B = blocks[tile.block];
-    const double* in = (B.sel ? r0 : r) + B.in_off;
-    double* out = (B.sel ? y0 : z) + B.out_off;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int rend = min(tile.row0 + rows, B.n);
-    if (B.dtype == 0) {
-        double* xs = xs_raw;
-        for (int j = threadIdx.x; j < B.ld; j += blockDim.x) xs[j] = (j < B.n) ? in[j] : 0.0;
-        __syncthreads();
-        const double* A = st64 + B.mat_off;
-        for (int row = tile.row0 + warp; row < rend; row += nw) {
-            const double* Ar = A + (int64_t)row * B.ld;
-            double acc = 0.0;
-            for (int c = 2 * lane; c < B.ld; c += 64) {
-                const double2 v = __ldg(reinterpret_cast<const double2*>(Ar + c));
-                acc = fma(v.x, xs[c], acc);
-                acc = fma(v.y, xs[c + 1], acc);
-            }
-            acc = warp_sum(acc);
-            if (lane == 0) out[row] = acc;
-        }
-    } else {
-        float* xs = reinterpret_cast<float*>(xs_raw);
-        for (int j = threadIdx.x; j < B.ld; j += blockDim.x) xs[j] = (j < B.n) ? (float)in[j] : 0.0f;
-        __syncthreads();
-        if (B.dtype == 1) {
-            const float* A = st32 + B.mat_off;
-            for (int row = tile.row0 + warp; row < rend; row += nw) {
-                const float* Ar = A + (int64_t)row * B.ld;
-                float acc = 0.0f;
-                for (int c = 4 * lane; c < B.ld; c += 128) acc += dot16f(Ar + c, xs + c);
-                acc = warp_sumf(acc);
-                if (lane == 0) out[row] = (double)acc;
-            }
-        } else {
-            const __nv_bfloat16* A = st16 + B.mat_off;
-            for (int row = tile.row0 + warp; row < rend; row += nw) {
-                const __nv_bfloat16* Ar = A + (int64_t)row * B.ld;
-                float acc = 0.0f;
-                for (int c = 8 * lane; c < B.ld; c += 256) acc += dot16b(Ar + c, xs + c);
-                acc = warp_sumf(acc);
-                if (lane == 0) out[row] = (double)acc;
-            }
-        }
+direction_kernel(double* __restrict__ p, const double* __restrict__ zl, const double* __restrict__ T,
+                 const int32_t* __restrict__ agg, const double* __restrict__ y0, int64_t nc, int np,
+                 const PcgScalars* sc, double* __restrict__ out) {
+    if (sc && sc->done) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nc * np) return;
+    double v = zl[t];
+    if (T) {
+        const int64_t e = t / np;
+        const double* Tr = T + t * NQ;
+        const double* y = y0 + (int64_t)agg[e] * NQ;
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) v = fma(Tr[k], y[k], v);
     }
+    if (sc) p[t] = fma(sc->beta, p[t], v);
+    else out[t] = v;
 }
 
 // ------------------------------------------------------------ permutations
-// dst[internal e][j] = src[caller c][j] (to_internal = false reverses).
-__global__ void permute_kernel(const double* __restrict__ src, double* __restrict__ dst,
-                               const int64_t* __restrict__ to_caller, int64_t nc, int np,
-                               int to_internal, const PcgScalars* zero_if_b0) {
+// dst[internal e][j] = src[caller c][j]  (to_internal = 1), or the reverse.
+// With sc != nullptr the internal source is the parity buffer src2[pass & 1]
+// and b = 0 (done == 2) yields zeros.
+__global__ void permute_kernel(const double* __restrict__ src, const double* __restrict__ src_odd,
+                               double* __restrict__ dst, const int64_t* __restrict__ to_caller,
+                               int64_t nc, int np, int to_internal, const PcgScalars* sc) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nc * np) return;
     const int64_t e = t / np, j = t - e * np, c = to_caller[e];
     if (to_internal) {
         dst[t] = src[c * np + j];
     } else {
-        dst[c * np + j] = (zero_if_b0 && zero_if_b0->done == 2) ? 0.0 : src[t];
+        const double* s = (sc && (sc->pass & 1)) ? src_odd : src;
+        dst[c * np + j] = (sc && sc->done == 2) ? 0.0 : s[t];
     }
 }
 
@@ -407,7 +566,8 @@ __global__ void extract_local_kernel(const int32_t* __restrict__ row_ptr,
             if (f < e0 || f >= e1) continue;
             for (int k = threadIdx.x; k < np * np; k += blockDim.x) {
                 const int i = k / np, j = k - i * np;
-                D[((e - e0) * np + i) * L + (f - e0) * np + j] = val[(int64_t)bi * np * np + k];
+                // blocks are stored column-major: entry (i, j) at j * np + i
+                D[((e - e0) * np + i) * L + (f - e0) * np + j] = val[(int64_t)bi * np * np + j * np + i];
             }
         }
     }
@@ -538,103 +698,80 @@ static inline unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) 
 cudaError_t launch_matvec(int mode, int np, const DeviceMatrix& K, const double* val,
                           const double* x, double* y, const double* v1, const double* v2,
                           double c1, double c2, PcgScalars* sc, double* partials,
-                          const SimScalars* ss, double dt, double stim_duration,
-                          cudaStream_t s) {
-    const unsigned g = grid_for(K.nc * np);
+                          const SimScalars* ss, double dt, double stim_duration, double* zero1,
+                          double* zero2, cudaStream_t s) {
+    const unsigned g = (unsigned)((K.nc + kElemsPerCta - 1) / kElemsPerCta);
     if (g > (unsigned)kMaxPartials) return cudaErrorInvalidValue;
+#define MV(M)                                                                                  \
+    NP_SWITCH(np, matvec_kernel<NP, M><<<g, kBlock, 0, s>>>(K.row_ptr, K.col, val, x, y, K.nc, v1, \
+                                                            v2, c1, c2, sc, partials, ss, dt,      \
+                                                            stim_duration, zero1, zero2))
     switch (mode) {
-        case MODE_PLAIN:
-            NP_SWITCH(np, bsr_matvec_kernel<NP, MODE_PLAIN><<<g, kBlock, 0, s>>>(
-                K.row_ptr, K.col, val, x, y, K.nc, v1, v2, c1, c2, sc, partials, ss, dt, stim_duration));
-            break;
-        case MODE_PCG:
-            NP_SWITCH(np, bsr_matvec_kernel<NP, MODE_PCG><<<g, kBlock, 0, s>>>(
-                K.row_ptr, K.col, val, x, y, K.nc, v1, v2, c1, c2, sc, partials, ss, dt, stim_duration));
-            break;
-        case MODE_RESID:
-            NP_SWITCH(np, bsr_matvec_kernel<NP, MODE_RESID><<<g, kBlock, 0, s>>>(
-                K.row_ptr, K.col, val, x, y, K.nc, v1, v2, c1, c2, sc, partials, ss, dt, stim_duration));
-            break;
-        default:
-            NP_SWITCH(np, bsr_matvec_kernel<NP, MODE_RHS><<<g, kBlock, 0, s>>>(
-                K.row_ptr, K.col, val, x, y, K.nc, v1, v2, c1, c2, sc, partials, ss, dt, stim_duration));
-            break;
+        case MODE_PLAIN: MV(MODE_PLAIN); break;
+        case MODE_PCG: MV(MODE_PCG); break;
+        case MODE_RESID: MV(MODE_RESID); break;
+        default: MV(MODE_RHS); break;
     }
+#undef MV
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(double* x, double* r, const double* p, const double* q, int64_t n,
-                          PcgScalars* sc, double* partials, cudaGraphConditionalHandle cond,
-                          int use_cond, cudaStream_t s) {
-    const unsigned g = grid_for(n);
-    if (g > (unsigned)kMaxPartials) return cudaErrorInvalidValue;
-    pcg_update_kernel<<<g, kBlock, 0, s>>>(x, r, p, q, n, sc, partials, cond, use_cond);
+cudaError_t launch_precond(const K1Args& a, int dtype, int ntiles, size_t smem, cudaStream_t s) {
+    if (ntiles > kMaxPartials) return cudaErrorInvalidValue;
+    if (dtype == 0) precond_kernel<0><<<ntiles, kBlock, smem, s>>>(a);
+    else if (dtype == 1) precond_kernel<1><<<ntiles, kBlock, smem, s>>>(a);
+    else precond_kernel<2><<<ntiles, kBlock, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_direction(double* p, const double* z, int64_t n, const PcgScalars* sc,
-                             cudaStream_t s) {
-    pcg_direction_kernel<<<grid_for(n), kBlock, 0, s>>>(p, z, n, sc);
+// The opt-in shared-memory limits only grow, so graphs captured for earlier
+// preconditioners stay launchable.
+static size_t g_precond_smem = 0, g_coarse_smem = 0;
+
+cudaError_t set_precond_smem(size_t smem) {
+    if (smem <= g_precond_smem) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(precond_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(precond_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(precond_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) g_precond_smem = smem;
+    return e;
+}
+
+cudaError_t launch_coarse(const K2Args& a, cudaStream_t s) {
+    const int rows_per_cta = kBlock / 32;
+    const int grid = a.n0 > 0 ? (a.n0 + rows_per_cta - 1) / rows_per_cta : 1;
+    const size_t smem = 2 * (size_t)a.n0 * sizeof(double);
+    coarse_kernel<<<grid, kBlock, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_identity_dots(const double* r, const double* q, int64_t n, PcgScalars* sc,
-                                 double* partials, cudaStream_t s) {
-    const unsigned g = grid_for(n);
-    if (g > (unsigned)kMaxPartials) return cudaErrorInvalidValue;
-    identity_dots_kernel<<<g, kBlock, 0, s>>>(r, q, n, sc, partials);
-    return cudaGetLastError();
+cudaError_t set_coarse_smem(size_t smem) {
+    if (smem <= g_coarse_smem) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess) g_coarse_smem = smem;
+    return e;
 }
 
-#define NQ_SWITCH(nq, ...)                                  \
-    switch (nq) {                                           \
-        case 3: { constexpr int NQ = 3; __VA_ARGS__; } break; \
-        case 6: { constexpr int NQ = 6; __VA_ARGS__; } break; \
-        case 10: { constexpr int NQ = 10; __VA_ARGS__; } break; \
-        default: return cudaErrorInvalidValue;               \
-    }
-
-cudaError_t launch_restrict(int np, int nq, const double* r, const double* T,
-                            const int64_t* agg_ptr, const int32_t* agg_cells, int n_agg,
-                            double* r0, const int* done, cudaStream_t s) {
-    const unsigned g = (unsigned)((n_agg * 32 + kBlock - 1) / kBlock);
-    NP_SWITCH(np, NQ_SWITCH(nq, restrict_kernel<NP, NQ><<<g, kBlock, 0, s>>>(
-                                    r, T, agg_ptr, agg_cells, n_agg, r0, done)));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_prolong(int np, int nq, double* z, const double* T, const int32_t* agg,
-                           const double* y0, int64_t nc, const double* r, const double* q,
-                           PcgScalars* sc, double* partials, cudaStream_t s) {
+cudaError_t launch_direction(int nq, double* p, const double* zl, const double* T,
+                             const int32_t* agg, const double* y0, int64_t nc, int np,
+                             const PcgScalars* sc, double* out, cudaStream_t s) {
     const unsigned g = grid_for(nc * np);
-    if (g > (unsigned)kMaxPartials) return cudaErrorInvalidValue;
-    if (T == nullptr) nq = 3;   // no coarse space: only the dot products
-    NP_SWITCH(np, NQ_SWITCH(nq, prolong_kernel<NP, NQ><<<g, kBlock, 0, s>>>(
-                                    z, T, agg, y0, nc, r, q, sc, partials)));
+    if (T == nullptr) nq = 3;
+    switch (nq) {
+        case 3: direction_kernel<3><<<g, kBlock, 0, s>>>(p, zl, T, agg, y0, nc, np, sc, out); break;
+        case 6: direction_kernel<6><<<g, kBlock, 0, s>>>(p, zl, T, agg, y0, nc, np, sc, out); break;
+        case 10: direction_kernel<10><<<g, kBlock, 0, s>>>(p, zl, T, agg, y0, nc, np, sc, out); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_gemv(const GemvBlock* blocks, const GemvTile* tiles, int ntiles, int rows,
-                        int max_ld, const double* st64, const float* st32,
-                        const __nv_bfloat16* st16, const double* r, const double* r0,
-                        double* z, double* y0, const int* done, cudaStream_t s) {
-    if (ntiles == 0) return cudaSuccess;
-    const size_t shm = (size_t)max_ld * sizeof(double);
-    ragged_gemv_kernel<<<ntiles, kBlock, shm, s>>>(blocks, tiles, rows, st64, st32, st16, r, r0,
-                                                   z, y0, done);
-    return cudaGetLastError();
-}
-
-cudaError_t set_gemv_smem(int max_ld) {
-    return cudaFuncSetAttribute(ragged_gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(max_ld * sizeof(double)));
-}
-
-cudaError_t launch_permute(const double* src, double* dst, const int64_t* to_caller, int64_t nc,
-                           int np, int to_internal, const PcgScalars* zero_if_b0,
-                           cudaStream_t s) {
-    permute_kernel<<<grid_for(nc * np), kBlock, 0, s>>>(src, dst, to_caller, nc, np, to_internal,
-                                                        zero_if_b0);
+cudaError_t launch_permute(const double* src, const double* src_odd, double* dst,
+                           const int64_t* to_caller, int64_t nc, int np, int to_internal,
+                           const PcgScalars* sc, cudaStream_t s) {
+    permute_kernel<<<grid_for(nc * np), kBlock, 0, s>>>(src, src_odd, dst, to_caller, nc, np,
+                                                        to_internal, sc);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,548 @@
+// Persistent PCG kernel (Sec. 4 and 5: PCG with the two-level additive Schwarz
+// preconditioner of Eq. prec, stopping on |r|_2 <= rtol |b|_2).
+//
+// One cooperative launch runs the whole solve: one CTA per SM, each owning a
+// fixed share of every phase, with three grid barriers per iteration:
+//   P  x += alpha p, r' = r - alpha q (r double-buffered); z_loc = K_i^{-1} r'_i on
+//      the CTA's rows of the local inverses, streamed by cp.async.bulk into a
+//      double buffer that is prefetched across phases and iterations (the inverses
+//      are constant); R_0 r' (and R_0 q) for the subdomains the CTA stages first;
+//      partial |r'|^2, r'.z_loc, z_loc.q                              -> barrier, test
+//   C  y0 = K_0^{-1} r0 on the CTA's coarse rows; partial r0.y0, q0.y0 -> barrier,
+//      r.z = r.z_loc + r0.y0 (since r.(R_0^T y0) = (R_0 r).y0) and beta
+//   M  p = z_loc + R_0^T y0 + beta p (p double-buffered) for the CTA's elements and
+//      their face neighbours, staged in shared memory; q = K_h p on the CTA's
+//      elements (fp64); partial p.q                                  -> barrier, alpha
+// Every CTA sums the per-CTA partials in the same order, so all CTAs hold
+// bit-identical scalars and take the same branches; the result is deterministic.
+// Waits (grid barriers, mbarriers) are bounded: on timeout the kernel raises an
+// error flag, waits (bounded) for its own copies in flight and stops.
+#include <type_traits>
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace polydg {
+
+constexpr uint32_t kSpinLimit = 1u << 22;     // bounded polls for every wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t k = 0; k < kSpinLimit; ++k) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Block-wide sums of N values at once (results valid in every thread).
+template <int N>
+__device__ __forceinline__ void block_sum_n(double (&v)[N]) {
+    __shared__ double shn[N][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) shn[k][w] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        double t = (lane < nw) ? shn[k][lane] : 0.0;
+        v[k] = warp_sum(t);
+    }
+    __syncthreads();
+}
+
+// Sense-free generation barrier over all CTAs of a cooperative launch.
+// Returns false (and raises *err) if the other CTAs did not arrive in time.
+__device__ bool grid_barrier(GridSync* gs, unsigned& gen, int* err) {
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&gs->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&gs->count, 0u);
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            uint32_t k = 0;
+            while (ld_acquire(&gs->gen) == gen) {
+                if (++k > kSpinLimit) { ok = 0; atomicExch(err, 1); break; }
+            }
+        }
+        __threadfence();
+        gen += 1;
+        ok_sh = ok && (*((volatile int*)err) == 0);
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+// Grid barrier that also sums N values over all CTAs: every CTA publishes its
+// block sums before the barrier and afterwards adds all CTAs' partials in CTA
+// order, so every CTA obtains the same bit-identical, deterministic sums.
+template <int N>
+__device__ bool barrier_sum(GridSync* gs, unsigned& gen, int* err, double* partials,
+                            double* /*bcast*/, double (&v)[N]) {
+    block_sum_n<N>(v);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) partials[(size_t)k * gridDim.x + blockIdx.x] = v[k];
+    const bool ok = grid_barrier(gs, gen, err);
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] += __ldcg(partials + (size_t)k * gridDim.x + i);
+    block_sum_n<N>(v);
+    return ok;
+}
+
+template <int DT>
+struct StoreType {
+    using T = typename std::conditional<DT == 0, double,
+              typename std::conditional<DT == 1, float, __nv_bfloat16>::type>::type;
+    using X = typename std::conditional<DT == 0, double, float>::type;
+};
+
+// Row dot products from shared memory (row Ar of ld entries, staged input xs).
+__device__ __forceinline__ double row_dot(const double* Ar, const double* xs, int ld, int lane) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int c = 2 * lane; c < ld; c += 64) {
+        const double2 u = *reinterpret_cast<const double2*>(Ar + c);
+        const double2 v = *reinterpret_cast<const double2*>(xs + c);
+        a0 = fma(u.x, v.x, a0);
+        a1 = fma(u.y, v.y, a1);
+    }
+    return warp_sum(a0 + a1);
+}
+
+__device__ __forceinline__ double row_dot(const float* Ar, const float* xs, int ld, int lane) {
+    float a0 = 0.f, a1 = 0.f;
+    for (int c = 4 * lane; c < ld; c += 128) {
+        const float4 u = *reinterpret_cast<const float4*>(Ar + c);
+        const float4 v = *reinterpret_cast<const float4*>(xs + c);
+        a0 = fmaf(u.x, v.x, a0); a1 = fmaf(u.y, v.y, a1);
+        a0 = fmaf(u.z, v.z, a0); a1 = fmaf(u.w, v.w, a1);
+    }
+    return (double)warp_sumf(a0 + a1);
+}
+
+__device__ __forceinline__ double row_dot(const __nv_bfloat16* Ar, const float* xs, int ld, int lane) {
+    float a0 = 0.f, a1 = 0.f;
+    for (int c = 8 * lane; c < ld; c += 256) {
+        const uint4 v = *reinterpret_cast<const uint4*>(Ar + c);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+        const float4 x0 = *reinterpret_cast<const float4*>(xs + c);
+        const float4 x1 = *reinterpret_cast<const float4*>(xs + c + 4);
+        float2 f = __bfloat1622float2(h[0]);
+        a0 = fmaf(f.x, x0.x, a0); a1 = fmaf(f.y, x0.y, a1);
+        f = __bfloat1622float2(h[1]);
+        a0 = fmaf(f.x, x0.z, a0); a1 = fmaf(f.y, x0.w, a1);
+        f = __bfloat1622float2(h[2]);
+        a0 = fmaf(f.x, x1.x, a0); a1 = fmaf(f.y, x1.y, a1);
+        f = __bfloat1622float2(h[3]);
+        a0 = fmaf(f.x, x1.z, a0); a1 = fmaf(f.y, x1.w, a1);
+    }
+    return (double)warp_sumf(a0 + a1);
+}
+
+// Rows of the CTA's elements of y = K x, warp per element, with x read from the
+// CTA-local staging xn (index: local element l * NP + j): lane (i, g) sums
+// columns g, g + G, ... of the element's column-major block-row panel.
+template <int NP, typename F>
+__device__ __forceinline__ void local_rows(const int32_t* __restrict__ row_ptr,
+                                           const int32_t* __restrict__ col_local,
+                                           const double* __restrict__ val, const double* xn,
+                                           int64_t e0, int64_t e1, F&& emit) {
+    constexpr int G = 32 / NP;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int g = (lane < G * NP) ? lane / NP : G;
+    const int i = lane - (lane / NP) * NP;
+    for (int64_t e = e0 + warp; e < e1; e += nw) {
+        const int32_t b0 = row_ptr[e];
+        const int ncol = (row_ptr[e + 1] - b0) * NP;
+        const double* V = val + (int64_t)b0 * NP * NP;
+        const int32_t* cl = col_local + b0;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int c = g;
+        for (; c + 3 * G < ncol; c += 4 * G) {
+            const int cb = c + G, cc = c + 2 * G, cd = c + 3 * G;
+            const double va = __ldg(V + (int64_t)c * NP + i), vb = __ldg(V + (int64_t)cb * NP + i);
+            const double vc = __ldg(V + (int64_t)cc * NP + i), vd = __ldg(V + (int64_t)cd * NP + i);
+            const int sa = c / NP, sb = cb / NP, sc_ = cc / NP, sd = cd / NP;
+            a0 = fma(va, xn[__ldg(cl + sa) * NP + (c - sa * NP)], a0);
+            a1 = fma(vb, xn[__ldg(cl + sb) * NP + (cb - sb * NP)], a1);
+            a2 = fma(vc, xn[__ldg(cl + sc_) * NP + (cc - sc_ * NP)], a2);
+            a3 = fma(vd, xn[__ldg(cl + sd) * NP + (cd - sd * NP)], a3);
+        }
+        for (; c < ncol; c += G) {
+            const int sa = c / NP;
+            a0 = fma(__ldg(V + (int64_t)c * NP + i), xn[__ldg(cl + sa) * NP + (c - sa * NP)], a0);
+        }
+        a0 += a2;
+        a1 += a3;
+        const double acc = a0 + a1;
+        double tot = acc;
+#pragma unroll
+        for (int k = 1; k < G; ++k) tot += __shfl_down_sync(0xffffffffu, acc, k * NP);
+        if (lane < NP) emit(e, i, tot);
+    }
+}
+
+template <int DT, int NP>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+pcg_persistent_kernel(PersistArgs a) {
+    using T = typename StoreType<DT>::T;
+    using X = typename StoreType<DT>::X;
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int S = kStages;
+    __shared__ __align__(8) uint64_t bars[S];
+
+    const int cta = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    PcgScalars* sc = a.sc;
+    if (sc->done) return;             // a failed earlier step: nothing to do (uniform)
+    const bool flexible = sc->flexible != 0;
+    const double rtol2 = sc->rtol2;
+    const int maxit = sc->maxit;
+    unsigned gen = 0;
+    if (threadIdx.x == 0) gen = ld_acquire(&a.gs->gen);
+
+    auto buf = [&](int k) { return reinterpret_cast<T*>(smem + (size_t)k * a.buf_bytes); };
+    X* xs = reinterpret_cast<X*>(smem + a.xs_off);                 // r' in the store's arithmetic
+    double* rp = reinterpret_cast<double*>(smem + a.rp_off);       // r' (fp64)
+    double* qp = reinterpret_cast<double*>(smem + a.qp_off);       // q  (fp64)
+    double* zs = reinterpret_cast<double*>(smem + a.zs_off);       // [S][rows]
+    double* r0s = reinterpret_cast<double*>(smem + a.r0_off);      // [n0] r0, [n0] q0
+    double* q0s = r0s + a.n0;
+    double* pn = reinterpret_cast<double*>(smem + a.pn_off);       // p of the needed elements
+
+    const int64_t e0 = a.elem_ptr[cta], e1 = a.elem_ptr[cta + 1];
+    const int n_own = (int)(e1 - e0);
+    const int32_t* need = a.need + a.need_ptr[cta];
+    const int n_need = a.need_ptr[cta + 1] - a.need_ptr[cta];
+    const int t0 = a.tile_ptr[cta], nt = a.tile_ptr[cta + 1] - t0;
+    const int c0 = a.crow_ptr[cta], c1 = a.crow_ptr[cta + 1];
+
+    // ---- init: r = b - K x on own elements; p = q = 0; |b|^2, |r|^2
+    for (int idx = threadIdx.x; idx < n_need * NP; idx += blockDim.x) {
+        const int l = idx / NP;
+        pn[idx] = __ldcg(a.x + (int64_t)need[l] * NP + (idx - l * NP));
+    }
+    for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) {
+        a.p[0][t] = 0.0;
+        a.p[1][t] = 0.0;
+        a.q[t] = 0.0;
+    }
+    __syncthreads();
+    double v2[2] = {0.0, 0.0};
+    local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, e0, e1, [&](int64_t e, int i, double kx) {
+        const int64_t t = e * NP + i;
+        const double bv = a.b[t], rv = bv - kx;
+        a.r[0][t] = rv;
+        v2[0] = fma(bv, bv, v2[0]);
+        v2[1] = fma(rv, rv, v2[1]);
+    });
+    uint32_t seq = 0;                 // tiles consumed so far (all iterations)
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(&bars[k]);
+        for (int k = 0; k < S && nt > 0; ++k) {   // the inverses do not depend on the iterate
+            const GemvTile tl = a.tiles[t0 + k % nt];
+            const GemvBlock B = a.blocks[tl.block];
+            const uint32_t bytes = (uint32_t)((size_t)min(a.rows, B.nrows - tl.row0) * B.ld * sizeof(T));
+            bulk_load(buf(k), reinterpret_cast<const T*>(a.store) + B.mat_off + (int64_t)tl.row0 * B.ld,
+                      bytes, &bars[k]);
+        }
+    }
+    bool ok = barrier_sum<2>(a.gs, gen, a.err, a.partials, a.bcast, v2);
+    const double bb = v2[0];
+    double rr = v2[1];
+    int status = kOK, it = 0, done = 0, par = 0, pp = 0;
+    double alpha = 0.0, beta = 0.0, rz = 0.0, relres = 0.0;
+    int pending = 0;                  // alpha p / alpha q not yet committed to x, r
+    if (!ok) { status = kEDEVICE; done = 1; }
+    else if (!isfinite(bb) || !isfinite(rr)) { status = kENONFINITE; done = 1; }
+    else if (bb == 0.0) { done = 2; }
+    else { relres = sqrt(rr / bb); if (rr <= rtol2 * bb) done = 1; }
+
+    while (!done) {
+        // ---------------------------------------------------------------- P
+        const double* rin = a.r[par];
+        double* rout = a.r[par ^ 1];
+        const double* pcur = a.p[pp];
+        const double al = pending ? alpha : 0.0;
+        double v3[3] = {0.0, 0.0, 0.0};           // |r'|^2, r'.z_loc, z_loc.q
+        if (a.identity) {
+            for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) {
+                const double qv = a.q[t], r_ = fma(-al, qv, rin[t]);
+                rout[t] = r_;
+                a.z[t] = r_;
+                a.x[t] = fma(al, pcur[t], a.x[t]);
+                v3[0] = fma(r_, r_, v3[0]);
+                v3[1] = fma(r_, r_, v3[1]);
+                if (flexible) v3[2] = fma(r_, qv, v3[2]);
+            }
+        } else {
+            int staged = -1;
+            for (int k = 0; k < nt; ++k, ++seq) {
+                const GemvTile tl = a.tiles[t0 + k];
+                const GemvBlock B = a.blocks[tl.block];
+                const int nrt = min(a.rows, B.nrows - tl.row0);
+                if (tl.block != staged) {
+                    __syncthreads();
+                    const double* ri = rin + B.in_off;
+                    const double* qi = a.q + B.in_off;
+                    for (int j = threadIdx.x; j < B.ld; j += blockDim.x) {
+                        const bool in = j < B.ncols;
+                        const double qv = in ? __ldcg(qi + j) : 0.0;
+                        const double r_ = in ? fma(-al, qv, __ldcg(ri + j)) : 0.0;
+                        rp[j] = r_;
+                        qp[j] = qv;
+                        if (DT != 0) xs[j] = (X)r_;
+                    }
+                    staged = tl.block;
+                    __syncthreads();
+                }
+                // operands of the commit, fetched before the tile lands
+                const int64_t tr = B.in_off + tl.row0 + threadIdx.x;
+                double pv = 0.0, xv = 0.0;
+                if ((int)threadIdx.x < nrt) {
+                    pv = __ldcg(pcur + tr);
+                    xv = a.x[tr];
+                }
+                const int bi = seq % S;
+                if (!mbar_wait(&bars[bi], (seq / S) & 1)) {
+                    if (threadIdx.x == 0) atomicExch(a.err, 1);
+                }
+                double* zt = zs + bi * a.rows;
+                const T* As = buf(bi);
+                const X* xin = (DT == 0) ? reinterpret_cast<const X*>(rp) : xs;
+                for (int r_ = warp; r_ < nrt; r_ += nw) {
+                    const double zr = row_dot(As + (size_t)r_ * B.ld, xin, B.ld, lane);
+                    if (lane == 0) zt[r_] = zr;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {   // buffer bi is free: prefetch S tiles ahead (cyclic)
+                    const GemvTile tn = a.tiles[t0 + (k + S) % nt];
+                    const GemvBlock Bn = a.blocks[tn.block];
+                    const uint32_t bytes = (uint32_t)((size_t)min(a.rows, Bn.nrows - tn.row0) * Bn.ld * sizeof(T));
+                    bulk_load(buf(bi), reinterpret_cast<const T*>(a.store) + Bn.mat_off + (int64_t)tn.row0 * Bn.ld,
+                              bytes, &bars[bi]);
+                }
+                if ((int)threadIdx.x < nrt) {
+                    const int row = tl.row0 + threadIdx.x;
+                    const double r_ = rp[row], qv = qp[row], zr = zt[threadIdx.x];
+                    rout[tr] = r_;
+                    a.z[tr] = zr;
+                    a.x[tr] = fma(al, pv, xv);
+                    v3[0] = fma(r_, r_, v3[0]);
+                    v3[1] = fma(r_, zr, v3[1]);
+                    if (flexible) v3[2] = fma(zr, qv, v3[2]);
+                }
+                if (tl.row0 == 0) {       // this CTA stages the subdomain first: R_0 r' and R_0 q
+                    for (int pi = 0; pi < B.pair_count; ++pi) {
+                        const GemvBlock R = a.blocks[a.sub_pairs[B.pair_begin + pi]];
+                        const double* Rm = a.st64 + R.mat_off;
+                        for (int w2 = warp; w2 < 2 * R.nrows; w2 += nw) {
+                            const int row = w2 >> 1;
+                            const double* v = (w2 & 1) ? qp : rp;
+                            const double* Rr = Rm + (int64_t)row * R.ld;
+                            double s0 = 0.0, s1 = 0.0;
+                            int j = lane;
+                            for (; j + 32 < R.ncols; j += 64) {
+                                s0 = fma(__ldg(Rr + j), v[j], s0);
+                                s1 = fma(__ldg(Rr + j + 32), v[j + 32], s1);
+                            }
+                            if (j < R.ncols) s0 = fma(__ldg(Rr + j), v[j], s0);
+                            const double sv = warp_sum(s0 + s1);
+                            if (lane == 0) ((w2 & 1) ? a.q0p : a.r0p)[R.out_off + row] = sv;
+                        }
+                    }
+                }
+            }
+        }
+        ok = barrier_sum<3>(a.gs, gen, a.err, a.partials, a.bcast, v3);
+        rr = v3[0];
+        const double rz_loc = v3[1], zq_loc = v3[2];
+        it += pending;
+        pending = 0;
+        par ^= 1;
+        relres = sqrt(rr / bb);
+        if (!ok) { status = kEDEVICE; break; }
+        if (!isfinite(rr) || !isfinite(rz_loc)) { status = kENONFINITE; break; }
+        if (rr <= rtol2 * bb) { status = kOK; break; }
+        if (it >= maxit) { status = kENOTCONV; break; }
+        // ---------------------------------------------------------------- C
+        double v2c[2] = {0.0, 0.0};               // r0.y0, q0.y0
+        if (a.n0 > 0 && c1 > c0) {
+            for (int idx = threadIdx.x; idx < a.n0; idx += blockDim.x) {
+                const int J = idx / a.nq, kq = idx - J * a.nq;
+                double s_r = 0.0, s_q = 0.0;
+                for (int64_t p2 = a.pair_ptr[J]; p2 < a.pair_ptr[J + 1]; ++p2) {
+                    s_r += __ldcg(a.r0p + p2 * a.nq + kq);
+                    s_q += __ldcg(a.q0p + p2 * a.nq + kq);
+                }
+                r0s[idx] = s_r;
+                q0s[idx] = s_q;
+            }
+            __syncthreads();
+            for (int row = c0 + warp; row < c1; row += nw) {
+                const double* Kr = a.K0inv + (int64_t)row * a.ld0;
+                double s0 = 0.0, s1 = 0.0;
+                int c = lane;
+                for (; c + 32 < a.n0; c += 64) {
+                    s0 = fma(__ldg(Kr + c), r0s[c], s0);
+                    s1 = fma(__ldg(Kr + c + 32), r0s[c + 32], s1);
+                }
+                if (c < a.n0) s0 = fma(__ldg(Kr + c), r0s[c], s0);
+                const double y = warp_sum(s0 + s1);
+                if (lane == 0) {
+                    a.y0[row] = y;
+                    v2c[0] = fma(y, r0s[row], v2c[0]);
+                    if (flexible) v2c[1] = fma(y, q0s[row], v2c[1]);
+                }
+            }
+        }
+        ok = barrier_sum<2>(a.gs, gen, a.err, a.partials, a.bcast, v2c);
+        const double rz_new = rz_loc + v2c[0];
+        const double zq = zq_loc + v2c[1];
+        if (!ok) { status = kEDEVICE; break; }
+        if (!isfinite(rz_new) || !isfinite(zq)) { status = kENONFINITE; break; }
+        if (it == 0) beta = 0.0;
+        else if (flexible) beta = -alpha * zq / rz;   // z_{k+1}.(r_{k+1} - r_k) = -alpha_k z_{k+1}.q_k
+        else beta = rz_new / rz;
+        rz = rz_new;
+        if (!isfinite(beta) || rz == 0.0) { status = kEBREAKDOWN; break; }
+        // ---------------------------------------------------------------- M
+        // p_new = z_loc + R_0^T y0 + beta p_old for own and neighbour elements
+        const double* pold = a.p[pp];
+        double* pnew = a.p[pp ^ 1];
+        for (int idx = threadIdx.x; idx < n_need * NP; idx += blockDim.x) {
+            const int l = idx / NP, j = idx - l * NP;
+            const int64_t e = need[l], t = e * NP + j;
+            double v = __ldcg(a.z + t);
+            if (a.n0 > 0) {
+                const double* Tr = a.T + t * a.nq;
+                const double* y = a.y0 + (int64_t)a.agg[e] * a.nq;
+                for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), __ldcg(y + kq), v);
+            }
+            v = fma(beta, __ldcg(pold + t), v);
+            pn[idx] = v;
+            if (l < n_own) pnew[t] = v;
+        }
+        __syncthreads();
+        double v1[1] = {0.0};
+        local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, e0, e1, [&](int64_t e, int i, double kp) {
+            a.q[e * NP + i] = kp;
+            v1[0] = fma(pn[(e - e0) * NP + i], kp, v1[0]);
+        });
+        pp ^= 1;
+        ok = barrier_sum<1>(a.gs, gen, a.err, a.partials, a.bcast, v1);
+        const double pq = v1[0];
+        if (!ok) { status = kEDEVICE; break; }
+        if (!(pq > 0.0) || !isfinite(pq)) { status = kEBREAKDOWN; break; }
+        alpha = rz / pq;
+        pending = 1;
+    }
+    if (done == 2) {            // b = 0: the solution is x = 0
+        for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) a.x[t] = 0.0;
+    }
+    // wait (bounded) for this CTA's copies still in flight before leaving
+    if (!a.identity && nt > 0) {
+        for (uint32_t s2 = seq; s2 < seq + S; ++s2) mbar_wait(&bars[s2 % S], (s2 / S) & 1);
+    }
+    if (cta == 0 && threadIdx.x == 0) {
+        sc->bb = bb;
+        sc->rr = rr;
+        sc->relres = relres;
+        sc->it = it;
+        sc->status = status;
+        sc->done = done ? done : 1;
+        sc->pass = 0;
+    }
+}
+
+template <int DT>
+static cudaError_t launch_dt(int np, const PersistArgs& a, size_t smem, cudaStream_t s) {
+    void* args[] = {(void*)&a};
+    const void* fn = nullptr;
+    switch (np) {
+        case 3: fn = (const void*)pcg_persistent_kernel<DT, 3>; break;
+        case 6: fn = (const void*)pcg_persistent_kernel<DT, 6>; break;
+        case 10: fn = (const void*)pcg_persistent_kernel<DT, 10>; break;
+        case 15: fn = (const void*)pcg_persistent_kernel<DT, 15>; break;
+        default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(fn, dim3(a.grid), dim3(kPersistThreads), args, smem, s);
+}
+
+cudaError_t launch_pcg_persistent(int dtype, int np, const PersistArgs& a, size_t smem,
+                                  cudaStream_t s) {
+    if (a.grid > kMaxPartials) return cudaErrorInvalidValue;
+    switch (dtype) {
+        case 0: return launch_dt<0>(np, a, smem, s);
+        case 1: return launch_dt<1>(np, a, smem, s);
+        default: return launch_dt<2>(np, a, smem, s);
+    }
+}
+
+cudaError_t persistent_occupancy(int dtype, int np, size_t smem, int* blocks_per_sm) {
+    const void* fn = nullptr;
+#define PICK(DT)                                                               \
+    switch (np) {                                                              \
+        case 3: fn = (const void*)pcg_persistent_kernel<DT, 3>; break;         \
+        case 6: fn = (const void*)pcg_persistent_kernel<DT, 6>; break;         \
+        case 10: fn = (const void*)pcg_persistent_kernel<DT, 10>; break;       \
+        case 15: fn = (const void*)pcg_persistent_kernel<DT, 15>; break;       \
+        default: return cudaErrorInvalidValue;                                 \
+    }
+    if (dtype == 0) { PICK(0) } else if (dtype == 1) { PICK(1) } else { PICK(2) }
+#undef PICK
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kPersistThreads, smem);
+}
+
+}  // namespace polydg
