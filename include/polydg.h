@@ -212,6 +212,29 @@ int sim_set_potential(sim_ctx *sim, const double *u_dev, const double *uprev_dev
 /* Current step index k. */
 int64_t sim_step_index(const sim_ctx *sim);
 
+/* Invert `batch` symmetric positive definite float64 matrices in place, without
+ * allocating any device memory.  The paper has no counterpart: this serves callers
+ * that cannot call cudaMalloc -- code running while a CUDA graph is being captured
+ * (allocation is not allowed during capture), processes whose device memory belongs
+ * to another allocator (a framework's caching allocator, a fixed arena in an
+ * embedded or real-time runtime), and code that must not fail on allocation in the
+ * middle of a time step.  It runs the same Cholesky-based kernel that asm_setup
+ * uses for K_i^{-1} and K_0^{-1}.
+ *   mats_dev: device pointer to batch row-major matrices of order n with leading
+ *             dimension ld, matrix m starting at mats_dev + m * n * ld; overwritten
+ *             with the inverses (caller-owned, read and written during the call).
+ *   Limits: n <= 1024, batch <= 256, batch * roundup(n, 32)^2 <= 1048576 (the
+ *           workspace is one fixed 8 MiB array per device, held by every GPU that
+ *           loads the library until the process exits); larger requests return
+ *           POLYDG_EINVAL with a message and launch nothing.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.  All
+ *   calls share the array, so calls that overlap on the GPU (two streams, two
+ *   threads) race and must be serialised by the caller.  The call synchronises
+ *   `stream`.  Returns POLYDG_OK, POLYDG_ENOTSPD (a non-positive pivot; that
+ *   matrix's contents are undefined), POLYDG_EINVAL or POLYDG_ECUDA. */
+int polydg_spd_inverse_static(double *mats_dev, int n, int ld, int batch, void *stream);
+
 void sim_destroy(sim_ctx *sim);
 void asm_destroy(asm_ctx *pc);
 void polydg_destroy(polydg_ctx *ctx);

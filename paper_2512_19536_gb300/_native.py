@@ -23,7 +23,7 @@ PRECISION = {"fp64": POLYDG_FP64, "fp32": POLYDG_FP32, "bf16": POLYDG_BF16}
 EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_get_info", "polydg_get_faces",
            "polydg_matvec", "asm_setup", "asm_get_info", "asm_apply", "pcg_solve", "sim_create",
            "monodomain_step", "sim_get_state", "sim_set_potential", "sim_step_index",
-           "sim_destroy", "asm_destroy", "polydg_destroy"]
+           "sim_destroy", "asm_destroy", "polydg_destroy", "polydg_spd_inverse_static"]
 
 
 class polydg_mesh(C.Structure):
@@ -91,6 +91,8 @@ def load() -> C.CDLL:
     L.monodomain_step.argtypes = [vp, i32, vp, C.POINTER(step_stats)]
     L.sim_get_state.argtypes = [vp, vp, vp, vp]
     L.sim_set_potential.argtypes = [vp, vp, vp, vp]
+    L.polydg_spd_inverse_static.argtypes = [vp, i32, i32, i32, vp]
+    L.polydg_spd_inverse_static.restype = i32
     L.sim_step_index.argtypes = [vp]
     L.sim_step_index.restype = i64
     for name in ("sim_destroy", "asm_destroy", "polydg_destroy"):
@@ -281,3 +283,15 @@ def sim_get_state(sim: Simulation, u, y=None, stream=None):
 def sim_set_potential(sim: Simulation, u, uprev=None, stream=None):
     _check(load().sim_set_potential(sim.h, _dev(u), _dev(uprev) if uprev is not None else None,
                                     _stream(stream)))
+
+
+def spd_inverse_static(mats, n, ld, batch, stream=None):
+    """In-place inversion of `batch` SPD float64 matrices (order n, leading dimension
+    ld) held in the CUDA tensor `mats`, using only the library's fixed static
+    workspace: for callers that cannot allocate device memory."""
+    if not (mats.is_cuda and mats.is_contiguous() and str(mats.dtype) == "torch.float64"):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    if mats.numel() < batch * n * ld:
+        raise ValueError("tensor smaller than batch * n * ld")
+    _check(load().polydg_spd_inverse_static(C.c_void_p(mats.data_ptr()), int(n), int(ld),
+                                            int(batch), _stream(stream)))
