@@ -1,0 +1,115 @@
+"""Full-size parity on the measured workload (4096-cell Voronoi P3, 40960 DOFs, 64 subdomains),
+in the configuration bench.py times (persistent PCG kernel, 152 CTAs).
+
+Oracle side: the FP64 CPU oracle's direct sparse solve (the definition of the solution the
+PCG converges to) and its coupled time stepping.  Tolerances: solutions at rtol 1e-12 within
+1e-8 in the function L2 norm sqrt(e^T M e)/sqrt(u^T M u); 200 coupled steps of the mixed form
+at the workload tolerance 1e-8 within 1e-6 (the hot path's stated bound for the potential).
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from conftest import cached
+
+pytestmark = pytest.mark.gpu
+
+
+def lib():
+    import paper_2512_19536_gb300 as pd
+    if not os.path.exists(pd.LIB_PATH):
+        from paper_2512_19536_gb300.build import build
+        build()
+    return pd
+
+
+@pytest.fixture(scope="module")
+def big():
+    from synth import voronoi4096_p3
+    from oracle import assembly
+
+    def make():
+        w = voronoi4096_p3()
+        d = assembly.assemble(w.mesh, w.p, w.sigma, w.eta0, w.chi_cm, w.dt)
+        return w, d
+    w, d = cached("voronoi4096", make)
+    pd = lib()
+    ctx = pd.polydg_setup(w.mesh.vertices, w.mesh.cell_ptr, w.mesh.cell_vtx, w.sigma, w.p,
+                          w.subdomain, w.chi_cm, w.dt, w.eta0)
+    return w, d, ctx
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def mnorm_rel(d, got, ref):
+    e = got - ref
+    return np.sqrt(e @ (d.M @ e)) / np.sqrt(ref @ (d.M @ ref))
+
+
+def test_fullsize_connectivity_and_matvec(big):
+    w, d, ctx = big
+    plus, minus = ctx.faces()
+    assert np.array_equal(plus, d.faces.plus) and np.array_equal(minus, d.faces.minus)
+    x = np.random.default_rng(21).standard_normal(d.n_dofs)
+    y = dev(np.zeros(d.n_dofs))
+    ctx.matvec(dev(x), y)
+    ref = d.K @ x
+    # Two independent assemblies: each entry is a quadrature sum whose volume, consistency
+    # and penalty terms partly cancel (terms up to ~10x the entry, ~100 of them), so the
+    # entries agree to ~1e3 eps of the row's absolute sum, not to a few eps.
+    assert np.all(np.abs(host(y) - ref) <= 1e-12 * (abs(d.K) @ np.abs(x)))
+
+
+@pytest.mark.parametrize("prec,flexible", [("fp64", False), ("fp32", True)])
+def test_fullsize_solution_matches_direct_solve(big, prec, flexible):
+    w, d, ctx = big
+    pd = lib()
+    pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision=prec)
+    b = np.random.default_rng(22).standard_normal(d.n_dofs)
+    x = dev(np.zeros(d.n_dofs))
+    st = pd.pcg_solve(ctx, pc, dev(b), x, rtol=1e-12, maxit=20000, flexible=flexible)
+    lu = cached(("splu", "voronoi4096"), lambda: spla.splu(d.K.tocsc()))
+    ref = lu.solve(b)
+    assert st["status"] == 0
+    assert mnorm_rel(d, host(x), ref) <= 1e-8
+
+
+def test_fullsize_200_coupled_steps_mixed_form(big):
+    """The bench configuration (fp32 local inverses, flexible PCG, rtol 1e-8) for the
+    workload's 200 steps against the oracle's exactly solved trajectory."""
+    from oracle import monodomain
+    w, d, ctx = big
+    pd = lib()
+    pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision="fp32")
+    sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-8, maxit=5000,
+                        flexible=True)
+    steps = w.n_steps
+    st = pd.monodomain_step(sim, steps)
+    u = dev(np.zeros(d.n_dofs))
+    pd.sim_get_state(sim, u)
+    got = host(u)
+
+    def run():
+        md = monodomain.Monodomain(d, w.stimulus, u0=w.u_rest)
+        for _ in range(steps):
+            s = md.step()
+        return s
+    ref = cached(("coupled", "voronoi4096", steps), run)
+    assert st["status"] == 0 and st["steps_done"] == steps
+    err = mnorm_rel(d, got, ref.U)
+    assert err <= 1e-6, err
+    # the deviation from the resting potential (what the dynamics did) also agrees
+    rest = np.zeros(d.n_dofs); rest[::d.n_p] = w.u_rest
+    dev_ref = ref.U - rest
+    assert np.sqrt((got - ref.U) @ (d.M @ (got - ref.U))) <= 1e-3 * np.sqrt(dev_ref @ (d.M @ dev_ref))
