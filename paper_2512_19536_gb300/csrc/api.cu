@@ -58,7 +58,8 @@ static void dfree(T*& p) {
 // (sc->pass & 1).
 struct PcgWork {
     double *x[2] = {nullptr, nullptr}, *r[2] = {nullptr, nullptr};
-    double *b = nullptr, *z = nullptr, *p = nullptr, *p2 = nullptr, *q = nullptr;
+    double *b = nullptr, *z = nullptr, *p = nullptr, *p2 = nullptr, *q = nullptr, *q2 = nullptr;
+    double *zl = nullptr, *w = nullptr;
     PcgScalars* sc = nullptr;
     double* partials = nullptr;
     int* err = nullptr;                 // device-wait timeout flag of the kernels
@@ -68,7 +69,8 @@ struct PcgWork {
         int st;
         if ((st = dalloc(&x[0], n)) || (st = dalloc(&x[1], n)) || (st = dalloc(&r[0], n)) ||
             (st = dalloc(&r[1], n)) || (st = dalloc(&b, n)) || (st = dalloc(&z, n)) ||
-            (st = dalloc(&p, n)) || (st = dalloc(&p2, n)) || (st = dalloc(&q, n)) || (st = dalloc(&sc, 1)) ||
+            (st = dalloc(&p, n)) || (st = dalloc(&p2, n)) || (st = dalloc(&q, n)) || (st = dalloc(&q2, n)) ||
+            (st = dalloc(&zl, n)) || (st = dalloc(&w, n)) || (st = dalloc(&sc, 1)) ||
             (st = dalloc(&partials, 8 * (size_t)kMaxPartials)) || (st = dalloc(&err, 1)) ||
             (st = dalloc(&gs, 1)) || (st = dalloc(&bcast, 8)))
             return st;
@@ -78,7 +80,7 @@ struct PcgWork {
         return POLYDG_OK;
     }
     void release() {
-        dfree(x[0]); dfree(x[1]); dfree(r[0]); dfree(r[1]); dfree(b); dfree(z); dfree(p); dfree(p2);
+        dfree(x[0]); dfree(x[1]); dfree(r[0]); dfree(r[1]); dfree(b); dfree(z); dfree(p); dfree(p2); dfree(q2); dfree(zl); dfree(w);
         dfree(q); dfree(sc); dfree(partials); dfree(err); dfree(gs); dfree(bcast);
     }
 };
@@ -86,14 +88,17 @@ struct PcgWork {
 // Static work split of the persistent PCG kernel over its CTAs.
 struct Plan {
     int grid = 0, rows = 1, dtype = 0;
-    size_t smem = 0, buf_bytes = 0, xs_off = 0, rp_off = 0, qp_off = 0, zs_off = 0, r0_off = 0,
+    int redundant = 1;
+    size_t smem = 0, buf_bytes = 0, xs_off = 0, rp_off = 0, zs_off = 0, r0_off = 0, y0_off = 0,
            pn_off = 0;
     int32_t *tile_ptr = nullptr, *sub_pairs = nullptr, *crow_ptr = nullptr;
     int32_t *need_ptr = nullptr, *need = nullptr, *col_local = nullptr;
+    int32_t *need_aggl = nullptr, *need_agg_ptr = nullptr, *need_agg = nullptr;
     GemvTile* tiles = nullptr;
     int64_t* elem_ptr = nullptr;
     void release() {
         dfree(tile_ptr); dfree(sub_pairs); dfree(crow_ptr); dfree(need_ptr); dfree(need);
+        dfree(need_aggl); dfree(need_agg_ptr); dfree(need_agg);
         dfree(col_local); dfree(tiles); dfree(elem_ptr);
     }
 };
@@ -229,12 +234,38 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
         max_need = std::max(max_need, (int)((e1 - e0) + nb.size()));
     }
     need_ptr[G] = (int32_t)need.size();
+    // agglomerates touched by each CTA's needed elements (coarse rows it solves redundantly)
+    const int nq = (pc && pc->has_coarse) ? pc->nq : 1;
+    std::vector<int32_t> agg_internal(H.nc, 0);
+    if (pc && pc->has_coarse) {
+        std::vector<int32_t> tmp(H.nc);
+        cudaMemcpy(tmp.data(), pc->d_agg, H.nc * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        agg_internal = tmp;
+    }
+    std::vector<int32_t> need_aggl(need.size(), 0), need_agg_ptr(G + 1, 0), need_agg;
+    int max_aggs = 0;
+    for (int g = 0; g < G; ++g) {
+        std::vector<int32_t> js;
+        for (int32_t k = need_ptr[g]; k < need_ptr[g + 1]; ++k) js.push_back(agg_internal[need[k]]);
+        std::sort(js.begin(), js.end());
+        js.erase(std::unique(js.begin(), js.end()), js.end());
+        need_agg_ptr[g] = (int32_t)need_agg.size();
+        for (int32_t k = need_ptr[g]; k < need_ptr[g + 1]; ++k)
+            need_aggl[k] = (int32_t)(std::lower_bound(js.begin(), js.end(), agg_internal[need[k]]) - js.begin());
+        need_agg.insert(need_agg.end(), js.begin(), js.end());
+        max_aggs = std::max(max_aggs, (int)js.size());
+    }
+    need_agg_ptr[G] = (int32_t)need_agg.size();
+    // coarse rows solved redundantly per CTA while that costs little (<= 8k fp64 FMA per CTA);
+    // otherwise distributed over the CTAs with one more grid barrier per iteration
+    P.redundant = ((int64_t)max_aggs * nq * n0 <= 8192) ? 1 : 0;
     // shared memory: 2 tile buffers, staged r' (store type), r' and q (fp64), z (2 x rows),
     // r0/q0, p of the needed elements
     auto r128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
     const size_t cap = 220 * 1024;
-    const size_t fixed = r128((size_t)max_ld * xsz) + 2 * r128((size_t)max_ld * 8) +
-                         r128(2 * (size_t)n0 * 8) + r128((size_t)max_need * np * 8) + r128(kStages * 64 * 8);
+    const size_t fixed = r128((size_t)max_ld * xsz) + r128((size_t)max_ld * 8) + r128((size_t)n0 * 8) +
+                         r128((size_t)max_aggs * nq * 8) + r128((size_t)max_need * np * 8) +
+                         r128(kStages * 64 * 8);
     if (fixed + kStages * (size_t)max_ld * esz > cap) {
         set_error("pcg: a subdomain or coarse space is too large for the shared-memory plan");
         return POLYDG_EINVAL;
@@ -244,10 +275,10 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
     P.buf_bytes = pc ? r128((size_t)rows * max_ld * esz) : 0;
     P.xs_off = kStages * P.buf_bytes;
     P.rp_off = P.xs_off + r128((size_t)max_ld * xsz);
-    P.qp_off = P.rp_off + r128((size_t)max_ld * 8);
-    P.zs_off = P.qp_off + r128((size_t)max_ld * 8);
+    P.zs_off = P.rp_off + r128((size_t)max_ld * 8);
     P.r0_off = P.zs_off + r128(kStages * (size_t)rows * 8);
-    P.pn_off = P.r0_off + r128(2 * (size_t)n0 * 8);
+    P.y0_off = P.r0_off + r128((size_t)n0 * 8);
+    P.pn_off = P.y0_off + r128((size_t)max_aggs * nq * 8);
     P.smem = P.pn_off + r128((size_t)max_need * np * 8);
     // LOCAL tiles balanced by bytes
     std::vector<GemvTile> tiles;
@@ -279,7 +310,9 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
     if ((st = upload(&P.tile_ptr, tile_ptr)) || (st = upload(&P.tiles, tiles)) ||
         (st = upload(&P.sub_pairs, sub_pairs)) || (st = upload(&P.elem_ptr, elem_ptr)) ||
         (st = upload(&P.crow_ptr, crow_ptr)) || (st = upload(&P.need_ptr, need_ptr)) ||
-        (st = upload(&P.need, need)) || (st = upload(&P.col_local, col_local)))
+        (st = upload(&P.need, need)) || (st = upload(&P.col_local, col_local)) ||
+        (st = upload(&P.need_aggl, need_aggl)) || (st = upload(&P.need_agg_ptr, need_agg_ptr)) ||
+        (st = upload(&P.need_agg, need_agg)))
         return st;
     int occ = 0;
     CU(persistent_occupancy(P.dtype, np, P.smem, &occ));
@@ -301,16 +334,20 @@ static int run_pcg(polydg_ctx* c, asm_ctx* pc, PcgWork& w, cudaStream_t s) {
     a.nq = coarse ? pc->nq : 1;
     a.nc = c->H.nc;
     a.buf_bytes = P.buf_bytes;
+    a.redundant = P.redundant;
     a.xs_off = P.xs_off;
     a.rp_off = P.rp_off;
-    a.qp_off = P.qp_off;
     a.zs_off = P.zs_off;
     a.r0_off = P.r0_off;
+    a.y0_off = P.y0_off;
     a.pn_off = P.pn_off;
     a.row_ptr = c->K.row_ptr;
     a.val = c->K.val;
     a.need_ptr = P.need_ptr;
     a.need = P.need;
+    a.need_aggl = P.need_aggl;
+    a.need_agg_ptr = P.need_agg_ptr;
+    a.need_agg = P.need_agg;
     a.col_local = P.col_local;
     a.elem_ptr = P.elem_ptr;
     a.blocks = pc ? pc->d_blocks : nullptr;
@@ -330,10 +367,12 @@ static int run_pcg(polydg_ctx* c, asm_ctx* pc, PcgWork& w, cudaStream_t s) {
     a.r[1] = w.r[1];
     a.p[0] = w.p;
     a.p[1] = w.p2;
+    a.q[0] = w.q;
+    a.q[1] = w.q2;
     a.z = w.z;
-    a.q = w.q;
+    a.zl = w.zl;
+    a.w = w.w;
     a.r0p = pc ? pc->d_r0p : nullptr;
-    a.q0p = pc ? pc->d_q0p : nullptr;
     a.y0 = pc ? pc->d_y0 : nullptr;
     a.sc = w.sc;
     a.partials = w.partials;

@@ -75,17 +75,20 @@ struct GridSync {
 // Arguments of the persistent PCG kernel (kernels_pcg.cu).  Per-CTA work lists
 // are CSR arrays indexed by blockIdx.x.
 struct PersistArgs {
-    int grid, rows, identity, n0, ld0, nq;
+    int grid, rows, identity, n0, ld0, nq, redundant;
     int64_t nc;
     // shared-memory carve-up (byte offsets)
-    size_t buf_bytes, xs_off, rp_off, qp_off, zs_off, r0_off, pn_off;
+    size_t buf_bytes, xs_off, rp_off, zs_off, r0_off, y0_off, pn_off;
     // K_h (column-major blocks) and the per-CTA matvec plan: the elements whose
-    // p the CTA needs (its own range first, then neighbours) and, per block of
-    // K_h, the CTA-local index of its column element
+    // z the CTA needs (its own range first, then face neighbours), their
+    // agglomerates, and per block of K_h the CTA-local index of its column element
     const int32_t* row_ptr;
     const double* val;
     const int32_t* need_ptr;                   // [grid + 1]
     const int32_t* need;
+    const int32_t* need_aggl;                  // per needed element: index into need_agg
+    const int32_t* need_agg_ptr;               // [grid + 1]
+    const int32_t* need_agg;                   // agglomerates of the needed elements
     const int32_t* col_local;                  // [n_blocks of K_h]
     const int64_t* elem_ptr;                   // [grid + 1] own element ranges
     // preconditioner
@@ -99,17 +102,18 @@ struct PersistArgs {
     const int64_t* pair_ptr;                   // [n_agg + 1] pairs of each agglomerate
     const double* T;
     const int32_t* agg;
-    const int32_t* crow_ptr;                   // [grid + 1] coarse rows
+    const int32_t* crow_ptr;                   // [grid + 1] coarse rows (distributed mode)
     // vectors (internal order)
     const double* b;
     double* x;
     double* r[2];
     double* p[2];
-    double *z, *q;
-    double *r0p, *q0p, *y0;
+    double* q[2];
+    double *z, *zl, *w;
+    double *r0p, *y0;
     PcgScalars* sc;
     double* partials;
-    double* bcast;                             // [8] grid sums broadcast by the barrier
+    double* bcast;
     GridSync* gs;
     int* err;
 };

@@ -2,17 +2,20 @@
 // preconditioner of Eq. prec, stopping on |r|_2 <= rtol |b|_2).
 //
 // One cooperative launch runs the whole solve: one CTA per SM, each owning a
-// fixed share of every phase, with three grid barriers per iteration:
-//   P  x += alpha p, r' = r - alpha q (r double-buffered); z_loc = K_i^{-1} r'_i on
-//      the CTA's rows of the local inverses, streamed by cp.async.bulk into a
-//      double buffer that is prefetched across phases and iterations (the inverses
-//      are constant); R_0 r' (and R_0 q) for the subdomains the CTA stages first;
-//      partial |r'|^2, r'.z_loc, z_loc.q                              -> barrier, test
-//   C  y0 = K_0^{-1} r0 on the CTA's coarse rows; partial r0.y0, q0.y0 -> barrier,
-//      r.z = r.z_loc + r0.y0 (since r.(R_0^T y0) = (R_0 r).y0) and beta
-//   M  p = z_loc + R_0^T y0 + beta p (p double-buffered) for the CTA's elements and
-//      their face neighbours, staged in shared memory; q = K_h p on the CTA's
-//      elements (fp64); partial p.q                                  -> barrier, alpha
+// fixed share of every phase.  With w = K z and the recurrences
+//     p_k = z_k + beta p_{k-1},   q_k = w_k + beta q_{k-1}  (= K p_k),
+//     p_{k+1}.q_{k+1} = z.w + 2 beta z.q_k + beta^2 p_k.q_k    (K symmetric),
+// the matvec no longer waits for beta, and one iteration is two phases:
+//   P   p_k, q_k, x += alpha p_k, r' = r - alpha q_k (r, p, q double-buffered);
+//       z_loc = K_i^{-1} r'_i on the CTA's rows of the local inverses, streamed by
+//       cp.async.bulk into a shared-memory ring prefetched across phases and
+//       iterations (the inverses are constant); R_0 r' for the subdomains the
+//       CTA stages first; partial |r'|^2                     -> barrier, test
+//   CM  y0 = K_0^{-1} R_0 r' for the agglomerates the CTA's elements touch
+//       (redundantly per CTA; a distributed coarse phase with one more barrier
+//       when the coarse space is large), z = z_loc + R_0^T y0 for its elements
+//       and their face neighbours in shared memory, w = K z on its elements
+//       (fp64); partial r'.z, z.q_k, z.w                      -> barrier, beta, alpha
 // Every CTA sums the per-CTA partials in the same order, so all CTAs hold
 // bit-identical scalars and take the same branches; the result is deterministic.
 // Waits (grid barriers, mbarriers) are bounded: on timeout the kernel raises an
@@ -44,16 +47,30 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// L2 policy for data streamed once per iteration: evict first, so the streamed
+// local inverses do not push K_h, the vectors and the coarse data out of L2.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    const uint64_t pol = evict_first_policy();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                  "r"(bytes)
                  : "memory");
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
         : "memory");
+}
+
+// Bulk prefetch of [src, src + bytes) into L2 (bytes a multiple of 16, src 16-byte aligned).
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
@@ -251,28 +268,30 @@ pcg_persistent_kernel(PersistArgs a) {
     auto buf = [&](int k) { return reinterpret_cast<T*>(smem + (size_t)k * a.buf_bytes); };
     X* xs = reinterpret_cast<X*>(smem + a.xs_off);                 // r' in the store's arithmetic
     double* rp = reinterpret_cast<double*>(smem + a.rp_off);       // r' (fp64)
-    double* qp = reinterpret_cast<double*>(smem + a.qp_off);       // q  (fp64)
     double* zs = reinterpret_cast<double*>(smem + a.zs_off);       // [S][rows]
-    double* r0s = reinterpret_cast<double*>(smem + a.r0_off);      // [n0] r0, [n0] q0
-    double* q0s = r0s + a.n0;
-    double* pn = reinterpret_cast<double*>(smem + a.pn_off);       // p of the needed elements
+    double* r0s = reinterpret_cast<double*>(smem + a.r0_off);      // [n0]
+    double* y0l = reinterpret_cast<double*>(smem + a.y0_off);      // y0 of the CTA's agglomerates
+    double* pn = reinterpret_cast<double*>(smem + a.pn_off);       // x or z of the needed elements
 
     const int64_t e0 = a.elem_ptr[cta], e1 = a.elem_ptr[cta + 1];
     const int n_own = (int)(e1 - e0);
     const int32_t* need = a.need + a.need_ptr[cta];
+    const int32_t* needj = a.need_aggl + a.need_ptr[cta];
     const int n_need = a.need_ptr[cta + 1] - a.need_ptr[cta];
+    const int32_t* aggs = a.need_agg + a.need_agg_ptr[cta];
+    const int n_aggs = a.need_agg_ptr[cta + 1] - a.need_agg_ptr[cta];
     const int t0 = a.tile_ptr[cta], nt = a.tile_ptr[cta + 1] - t0;
     const int c0 = a.crow_ptr[cta], c1 = a.crow_ptr[cta + 1];
+    const bool coarse = a.n0 > 0;
 
-    // ---- init: r = b - K x on own elements; p = q = 0; |b|^2, |r|^2
+    // ---- init: r = b - K x on own elements; p, q, z, w = 0; |b|^2, |r|^2
     for (int idx = threadIdx.x; idx < n_need * NP; idx += blockDim.x) {
         const int l = idx / NP;
         pn[idx] = __ldcg(a.x + (int64_t)need[l] * NP + (idx - l * NP));
     }
     for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) {
-        a.p[0][t] = 0.0;
-        a.p[1][t] = 0.0;
-        a.q[t] = 0.0;
+        a.p[0][t] = 0.0; a.p[1][t] = 0.0; a.q[0][t] = 0.0; a.q[1][t] = 0.0;
+        a.z[t] = 0.0; a.w[t] = 0.0;
     }
     __syncthreads();
     double v2[2] = {0.0, 0.0};
@@ -298,8 +317,8 @@ pcg_persistent_kernel(PersistArgs a) {
     const double bb = v2[0];
     double rr = v2[1];
     int status = kOK, it = 0, done = 0, par = 0, pp = 0;
-    double alpha = 0.0, beta = 0.0, rz = 0.0, relres = 0.0;
-    int pending = 0;                  // alpha p / alpha q not yet committed to x, r
+    double alpha = 0.0, beta = 0.0, rz = 0.0, pq = 0.0, relres = 0.0;
+    int pending = 0;                  // alpha p_k / alpha q_k not yet committed to x, r
     if (!ok) { status = kEDEVICE; done = 1; }
     else if (!isfinite(bb) || !isfinite(rr)) { status = kENONFINITE; done = 1; }
     else if (bb == 0.0) { done = 2; }
@@ -309,18 +328,22 @@ pcg_persistent_kernel(PersistArgs a) {
         // ---------------------------------------------------------------- P
         const double* rin = a.r[par];
         double* rout = a.r[par ^ 1];
-        const double* pcur = a.p[pp];
-        const double al = pending ? alpha : 0.0;
-        double v3[3] = {0.0, 0.0, 0.0};           // |r'|^2, r'.z_loc, z_loc.q
+        const double* pold = a.p[pp];
+        const double* qold = a.q[pp];
+        double* pnew = a.p[pp ^ 1];
+        double* qnew = a.q[pp ^ 1];
+        const double al = pending ? alpha : 0.0, be = beta;
+        double v1[1] = {0.0};                     // |r'|^2
         if (a.identity) {
             for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) {
-                const double qv = a.q[t], r_ = fma(-al, qv, rin[t]);
+                const double pk = fma(be, pold[t], a.z[t]), qk = fma(be, qold[t], a.w[t]);
+                pnew[t] = pk;
+                qnew[t] = qk;
+                a.x[t] = fma(al, pk, a.x[t]);
+                const double r_ = fma(-al, qk, rin[t]);
                 rout[t] = r_;
-                a.z[t] = r_;
-                a.x[t] = fma(al, pcur[t], a.x[t]);
-                v3[0] = fma(r_, r_, v3[0]);
-                v3[1] = fma(r_, r_, v3[1]);
-                if (flexible) v3[2] = fma(r_, qv, v3[2]);
+                a.zl[t] = r_;
+                v1[0] = fma(r_, r_, v1[0]);
             }
         } else {
             int staged = -1;
@@ -330,14 +353,14 @@ pcg_persistent_kernel(PersistArgs a) {
                 const int nrt = min(a.rows, B.nrows - tl.row0);
                 if (tl.block != staged) {
                     __syncthreads();
-                    const double* ri = rin + B.in_off;
-                    const double* qi = a.q + B.in_off;
                     for (int j = threadIdx.x; j < B.ld; j += blockDim.x) {
-                        const bool in = j < B.ncols;
-                        const double qv = in ? __ldcg(qi + j) : 0.0;
-                        const double r_ = in ? fma(-al, qv, __ldcg(ri + j)) : 0.0;
+                        double r_ = 0.0;
+                        if (j < B.ncols) {
+                            const int64_t t = B.in_off + j;
+                            const double qk = fma(be, __ldcg(qold + t), __ldcg(a.w + t));
+                            r_ = fma(-al, qk, __ldcg(rin + t));
+                        }
                         rp[j] = r_;
-                        qp[j] = qv;
                         if (DT != 0) xs[j] = (X)r_;
                     }
                     staged = tl.block;
@@ -345,9 +368,10 @@ pcg_persistent_kernel(PersistArgs a) {
                 }
                 // operands of the commit, fetched before the tile lands
                 const int64_t tr = B.in_off + tl.row0 + threadIdx.x;
-                double pv = 0.0, xv = 0.0;
+                double zv = 0.0, wv = 0.0, pv = 0.0, qv = 0.0, xv = 0.0;
                 if ((int)threadIdx.x < nrt) {
-                    pv = __ldcg(pcur + tr);
+                    zv = __ldcg(a.z + tr); wv = __ldcg(a.w + tr);
+                    pv = __ldcg(pold + tr); qv = __ldcg(qold + tr);
                     xv = a.x[tr];
                 }
                 const int bi = seq % S;
@@ -370,63 +394,67 @@ pcg_persistent_kernel(PersistArgs a) {
                               bytes, &bars[bi]);
                 }
                 if ((int)threadIdx.x < nrt) {
-                    const int row = tl.row0 + threadIdx.x;
-                    const double r_ = rp[row], qv = qp[row], zr = zt[threadIdx.x];
+                    const double pk = fma(be, pv, zv), qk = fma(be, qv, wv);
+                    const double r_ = rp[tl.row0 + threadIdx.x];
+                    pnew[tr] = pk;
+                    qnew[tr] = qk;
+                    a.x[tr] = fma(al, pk, xv);
                     rout[tr] = r_;
-                    a.z[tr] = zr;
-                    a.x[tr] = fma(al, pv, xv);
-                    v3[0] = fma(r_, r_, v3[0]);
-                    v3[1] = fma(r_, zr, v3[1]);
-                    if (flexible) v3[2] = fma(zr, qv, v3[2]);
+                    a.zl[tr] = zt[threadIdx.x];
+                    v1[0] = fma(r_, r_, v1[0]);
                 }
-                if (tl.row0 == 0) {       // this CTA stages the subdomain first: R_0 r' and R_0 q
+                if (tl.row0 == 0 && coarse) {   // this CTA stages the subdomain first: R_0 r'
                     for (int pi = 0; pi < B.pair_count; ++pi) {
                         const GemvBlock R = a.blocks[a.sub_pairs[B.pair_begin + pi]];
                         const double* Rm = a.st64 + R.mat_off;
-                        for (int w2 = warp; w2 < 2 * R.nrows; w2 += nw) {
-                            const int row = w2 >> 1;
-                            const double* v = (w2 & 1) ? qp : rp;
+                        for (int row = warp; row < R.nrows; row += nw) {
                             const double* Rr = Rm + (int64_t)row * R.ld;
                             double s0 = 0.0, s1 = 0.0;
                             int j = lane;
                             for (; j + 32 < R.ncols; j += 64) {
-                                s0 = fma(__ldg(Rr + j), v[j], s0);
-                                s1 = fma(__ldg(Rr + j + 32), v[j + 32], s1);
+                                s0 = fma(__ldg(Rr + j), rp[j], s0);
+                                s1 = fma(__ldg(Rr + j + 32), rp[j + 32], s1);
                             }
-                            if (j < R.ncols) s0 = fma(__ldg(Rr + j), v[j], s0);
+                            if (j < R.ncols) s0 = fma(__ldg(Rr + j), rp[j], s0);
                             const double sv = warp_sum(s0 + s1);
-                            if (lane == 0) ((w2 & 1) ? a.q0p : a.r0p)[R.out_off + row] = sv;
+                            if (lane == 0) a.r0p[R.out_off + row] = sv;
                         }
                     }
                 }
             }
         }
-        ok = barrier_sum<3>(a.gs, gen, a.err, a.partials, a.bcast, v3);
-        rr = v3[0];
-        const double rz_loc = v3[1], zq_loc = v3[2];
+        if (threadIdx.x == 0 && n_own > 0) {     // K_h rows of the CM phase into L2
+            const char* lo = reinterpret_cast<const char*>(a.val + (int64_t)a.row_ptr[e0] * NP * NP);
+            const char* hi = reinterpret_cast<const char*>(a.val + (int64_t)a.row_ptr[e1] * NP * NP);
+            for (const char* c = lo; c < hi; c += 65536)
+                prefetch_l2(c, (uint32_t)min((int64_t)65536, (int64_t)(hi - c)));
+        }
+        ok = barrier_sum<1>(a.gs, gen, a.err, a.partials, a.bcast, v1);
+        rr = v1[0];
         it += pending;
         pending = 0;
         par ^= 1;
+        pp ^= 1;
         relres = sqrt(rr / bb);
         if (!ok) { status = kEDEVICE; break; }
-        if (!isfinite(rr) || !isfinite(rz_loc)) { status = kENONFINITE; break; }
+        if (!isfinite(rr)) { status = kENONFINITE; break; }
         if (rr <= rtol2 * bb) { status = kOK; break; }
         if (it >= maxit) { status = kENOTCONV; break; }
-        // ---------------------------------------------------------------- C
-        double v2c[2] = {0.0, 0.0};               // r0.y0, q0.y0
-        if (a.n0 > 0 && c1 > c0) {
-            for (int idx = threadIdx.x; idx < a.n0; idx += blockDim.x) {
-                const int J = idx / a.nq, kq = idx - J * a.nq;
-                double s_r = 0.0, s_q = 0.0;
-                for (int64_t p2 = a.pair_ptr[J]; p2 < a.pair_ptr[J + 1]; ++p2) {
-                    s_r += __ldcg(a.r0p + p2 * a.nq + kq);
-                    s_q += __ldcg(a.q0p + p2 * a.nq + kq);
+        const double* rk = a.r[par];              // r_{k+1}
+        const double* qk = a.q[pp];               // q_k
+        // ---------------------------------------------------------------- coarse
+        if (coarse) {
+            if (a.redundant || c1 > c0) {
+                for (int idx = threadIdx.x; idx < a.n0; idx += blockDim.x) {
+                    const int J = idx / a.nq, kq = idx - J * a.nq;
+                    double s_r = 0.0;
+                    for (int64_t p2 = a.pair_ptr[J]; p2 < a.pair_ptr[J + 1]; ++p2)
+                        s_r += __ldcg(a.r0p + p2 * a.nq + kq);
+                    r0s[idx] = s_r;
                 }
-                r0s[idx] = s_r;
-                q0s[idx] = s_q;
+                __syncthreads();
             }
-            __syncthreads();
-            for (int row = c0 + warp; row < c1; row += nw) {
+            auto coarse_row = [&](int row) {
                 const double* Kr = a.K0inv + (int64_t)row * a.ld0;
                 double s0 = 0.0, s1 = 0.0;
                 int c = lane;
@@ -435,52 +463,67 @@ pcg_persistent_kernel(PersistArgs a) {
                     s1 = fma(__ldg(Kr + c + 32), r0s[c + 32], s1);
                 }
                 if (c < a.n0) s0 = fma(__ldg(Kr + c), r0s[c], s0);
-                const double y = warp_sum(s0 + s1);
-                if (lane == 0) {
-                    a.y0[row] = y;
-                    v2c[0] = fma(y, r0s[row], v2c[0]);
-                    if (flexible) v2c[1] = fma(y, q0s[row], v2c[1]);
+                return warp_sum(s0 + s1);
+            };
+            if (a.redundant) {                    // y0 of this CTA's agglomerates only
+                for (int w2 = warp; w2 < n_aggs * a.nq; w2 += nw) {
+                    const int jl = w2 / a.nq, kq = w2 - jl * a.nq;
+                    const double y = coarse_row(aggs[jl] * a.nq + kq);
+                    if (lane == 0) y0l[w2] = y;
                 }
+            } else {                              // distributed coarse rows, then a barrier
+                for (int row = c0 + warp; row < c1; row += nw) {
+                    const double y = coarse_row(row);
+                    if (lane == 0) a.y0[row] = y;
+                }
+                ok = grid_barrier(a.gs, gen, a.err);
+                if (!ok) { status = kEDEVICE; break; }
             }
+            __syncthreads();
         }
-        ok = barrier_sum<2>(a.gs, gen, a.err, a.partials, a.bcast, v2c);
-        const double rz_new = rz_loc + v2c[0];
-        const double zq = zq_loc + v2c[1];
-        if (!ok) { status = kEDEVICE; break; }
-        if (!isfinite(rz_new) || !isfinite(zq)) { status = kENONFINITE; break; }
-        if (it == 0) beta = 0.0;
-        else if (flexible) beta = -alpha * zq / rz;   // z_{k+1}.(r_{k+1} - r_k) = -alpha_k z_{k+1}.q_k
-        else beta = rz_new / rz;
-        rz = rz_new;
-        if (!isfinite(beta) || rz == 0.0) { status = kEBREAKDOWN; break; }
-        // ---------------------------------------------------------------- M
-        // p_new = z_loc + R_0^T y0 + beta p_old for own and neighbour elements
-        const double* pold = a.p[pp];
-        double* pnew = a.p[pp ^ 1];
+        // ---------------------------------------------------------------- CM
+        // z = z_loc + R_0^T y0 for own and neighbour elements; w = K z on own elements
         for (int idx = threadIdx.x; idx < n_need * NP; idx += blockDim.x) {
             const int l = idx / NP, j = idx - l * NP;
             const int64_t e = need[l], t = e * NP + j;
-            double v = __ldcg(a.z + t);
-            if (a.n0 > 0) {
+            double v = __ldcg(a.zl + t);
+            if (coarse) {
                 const double* Tr = a.T + t * a.nq;
-                const double* y = a.y0 + (int64_t)a.agg[e] * a.nq;
-                for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), __ldcg(y + kq), v);
+                if (a.redundant) {
+                    const double* y = y0l + needj[l] * a.nq;
+                    for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), y[kq], v);
+                } else {
+                    const double* y = a.y0 + (int64_t)a.agg[e] * a.nq;
+                    for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), __ldcg(y + kq), v);
+                }
             }
-            v = fma(beta, __ldcg(pold + t), v);
             pn[idx] = v;
-            if (l < n_own) pnew[t] = v;
+            if (l < n_own) a.z[t] = v;
         }
         __syncthreads();
-        double v1[1] = {0.0};
-        local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, e0, e1, [&](int64_t e, int i, double kp) {
-            a.q[e * NP + i] = kp;
-            v1[0] = fma(pn[(e - e0) * NP + i], kp, v1[0]);
+        double v3[3] = {0.0, 0.0, 0.0};           // r.z, z.q_k, z.w
+        local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, e0, e1, [&](int64_t e, int i, double kz) {
+            const int64_t t = e * NP + i;
+            const double zv = pn[(e - e0) * NP + i];
+            a.w[t] = kz;
+            v3[0] = fma(__ldcg(rk + t), zv, v3[0]);
+            v3[1] = fma(zv, __ldcg(qk + t), v3[1]);
+            v3[2] = fma(zv, kz, v3[2]);
         });
-        pp ^= 1;
-        ok = barrier_sum<1>(a.gs, gen, a.err, a.partials, a.bcast, v1);
-        const double pq = v1[0];
+        ok = barrier_sum<3>(a.gs, gen, a.err, a.partials, a.bcast, v3);
         if (!ok) { status = kEDEVICE; break; }
-        if (!(pq > 0.0) || !isfinite(pq)) { status = kEBREAKDOWN; break; }
+        const double rz_new = v3[0], zq = v3[1], zw = v3[2];
+        if (!isfinite(rz_new) || !isfinite(zq) || !isfinite(zw)) { status = kENONFINITE; break; }
+        double bnew;
+        if (it == 0) bnew = 0.0;
+        else if (flexible) bnew = -alpha * zq / rz;   // z_{k+1}.(r_{k+1} - r_k) = -alpha_k z_{k+1}.q_k
+        else bnew = rz_new / rz;
+        if (!isfinite(bnew) || rz_new == 0.0) { status = kEBREAKDOWN; break; }
+        const double pq_new = zw + 2.0 * bnew * zq + bnew * bnew * pq;
+        if (!(pq_new > 0.0) || !isfinite(pq_new)) { status = kEBREAKDOWN; break; }
+        beta = bnew;
+        rz = rz_new;
+        pq = pq_new;
         alpha = rz / pq;
         pending = 1;
     }
