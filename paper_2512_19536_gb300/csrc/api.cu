@@ -90,7 +90,7 @@ struct Plan {
     int grid = 0, rows = 1, dtype = 0;
     int redundant = 1;
     size_t smem = 0, buf_bytes = 0, xs_off = 0, rp_off = 0, zs_off = 0, r0_off = 0, y0_off = 0,
-           pn_off = 0;
+           pn_off = 0, td_off = 0;
     int32_t *tile_ptr = nullptr, *sub_pairs = nullptr, *crow_ptr = nullptr;
     int32_t *need_ptr = nullptr, *need = nullptr, *col_local = nullptr;
     int32_t *need_aggl = nullptr, *need_agg_ptr = nullptr, *need_agg = nullptr;
@@ -270,7 +270,13 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
         set_error("pcg: a subdomain or coarse space is too large for the shared-memory plan");
         return POLYDG_EINVAL;
     }
-    const int rows = (int)std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)((cap - fixed) / kStages / ((size_t)max_ld * esz))));
+    // tile rows: a multiple of the 16 warps, or a power of two that divides them (a row
+    // is then split over 16/rows warps); at most what kStages buffers leave room for
+    const size_t td_reserve = r128(64 * 64);   // descriptors of up to 64 tiles per CTA
+    const int64_t rmax = std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)((cap - fixed - td_reserve) / kStages / ((size_t)max_ld * esz))));
+    int rows = 1;
+    if (rmax >= 16) rows = (int)(rmax / 16 * 16);
+    else while (rows * 2 <= rmax) rows *= 2;
     P.rows = rows;
     P.buf_bytes = pc ? r128((size_t)rows * max_ld * esz) : 0;
     P.xs_off = kStages * P.buf_bytes;
@@ -279,7 +285,8 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
     P.r0_off = P.zs_off + r128(kStages * (size_t)rows * 8);
     P.y0_off = P.r0_off + r128((size_t)n0 * 8);
     P.pn_off = P.y0_off + r128((size_t)max_aggs * nq * 8);
-    P.smem = P.pn_off + r128((size_t)max_need * np * 8);
+    P.td_off = P.pn_off + r128((size_t)max_need * np * 8);
+    P.smem = P.td_off + td_reserve;
     // LOCAL tiles balanced by bytes
     std::vector<GemvTile> tiles;
     std::vector<int64_t> tbytes;
@@ -303,6 +310,11 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
         }
         tile_ptr[G] = (int32_t)tiles.size();
     }
+    for (int g = 0; g < G; ++g)
+        if (tile_ptr[g + 1] - tile_ptr[g] > 64) {
+            set_error("pcg: more than 64 tiles per CTA; subdomains too large for this plan");
+            return POLYDG_EINVAL;
+        }
     if (pc) sub_pairs = pc->sub_pairs;
     std::vector<int32_t> crow_ptr(G + 1);
     for (int g = 0; g <= G; ++g) crow_ptr[g] = (int32_t)((n0 * g) / G);
@@ -341,6 +353,7 @@ static int run_pcg(polydg_ctx* c, asm_ctx* pc, PcgWork& w, cudaStream_t s) {
     a.r0_off = P.r0_off;
     a.y0_off = P.y0_off;
     a.pn_off = P.pn_off;
+    a.td_off = P.td_off;
     a.row_ptr = c->K.row_ptr;
     a.val = c->K.val;
     a.need_ptr = P.need_ptr;

@@ -78,7 +78,7 @@ struct PersistArgs {
     int grid, rows, identity, n0, ld0, nq, redundant;
     int64_t nc;
     // shared-memory carve-up (byte offsets)
-    size_t buf_bytes, xs_off, rp_off, zs_off, r0_off, y0_off, pn_off;
+    size_t buf_bytes, xs_off, rp_off, zs_off, r0_off, y0_off, pn_off, td_off;
     // K_h (column-major blocks) and the per-CTA matvec plan: the elements whose
     // z the CTA needs (its own range first, then face neighbours), their
     // agglomerates, and per block of K_h the CTA-local index of its column element

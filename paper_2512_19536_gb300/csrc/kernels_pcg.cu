@@ -107,27 +107,24 @@ __device__ __forceinline__ void block_sum_n(double (&v)[N]) {
     __syncthreads();
 }
 
-// Sense-free generation barrier over all CTAs of a cooperative launch.
+// Grid barrier over all CTAs of a cooperative launch.  gs->count starts at 0 for
+// the launch and only grows: barrier number k completes when it reaches
+// (k + 1) * gridDim.x, so no CTA has to reset or flip anything.  The arrive is a
+// fire-and-forget release reduction after a fence that publishes the CTA's
+// writes; waiters poll with acquire loads.  `target` lives in thread 0.
 // Returns false (and raises *err) if the other CTAs did not arrive in time.
-__device__ bool grid_barrier(GridSync* gs, unsigned& gen, int* err) {
+__device__ bool grid_barrier(GridSync* gs, unsigned& target, int* err) {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
+        target += gridDim.x;
         __threadfence();
-        const unsigned arrived = atomicAdd(&gs->count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&gs->count, 0u);
-            __threadfence();
-            atomicAdd(&gs->gen, 1u);
-        } else {
-            uint32_t k = 0;
-            while (ld_acquire(&gs->gen) == gen) {
-                if (++k > kSpinLimit) { ok = 0; atomicExch(err, 1); break; }
-            }
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gs->count) : "memory");
+        uint32_t k = 0;
+        while ((int)(ld_acquire(&gs->count) - target) < 0) {
+            if (++k > kSpinLimit) { ok = 0; atomicExch(err, 1); break; }
         }
-        __threadfence();
-        gen += 1;
         ok_sh = ok && (*((volatile int*)err) == 0);
     }
     __syncthreads();
@@ -161,10 +158,12 @@ struct StoreType {
     using X = typename std::conditional<DT == 0, double, float>::type;
 };
 
-// Row dot products from shared memory (row Ar of ld entries, staged input xs).
-__device__ __forceinline__ double row_dot(const double* Ar, const double* xs, int ld, int lane) {
+// Row dot products from shared memory (row Ar of ld entries, staged input xs),
+// over the column chunks part, part + parts, ... of 32 lanes x vector width.
+__device__ __forceinline__ double row_dot(const double* Ar, const double* xs, int ld, int lane,
+                                          int part, int parts) {
     double a0 = 0.0, a1 = 0.0;
-    for (int c = 2 * lane; c < ld; c += 64) {
+    for (int c = 2 * (lane + 32 * part); c < ld; c += 64 * parts) {
         const double2 u = *reinterpret_cast<const double2*>(Ar + c);
         const double2 v = *reinterpret_cast<const double2*>(xs + c);
         a0 = fma(u.x, v.x, a0);
@@ -173,9 +172,10 @@ __device__ __forceinline__ double row_dot(const double* Ar, const double* xs, in
     return warp_sum(a0 + a1);
 }
 
-__device__ __forceinline__ double row_dot(const float* Ar, const float* xs, int ld, int lane) {
+__device__ __forceinline__ double row_dot(const float* Ar, const float* xs, int ld, int lane,
+                                          int part, int parts) {
     float a0 = 0.f, a1 = 0.f;
-    for (int c = 4 * lane; c < ld; c += 128) {
+    for (int c = 4 * (lane + 32 * part); c < ld; c += 128 * parts) {
         const float4 u = *reinterpret_cast<const float4*>(Ar + c);
         const float4 v = *reinterpret_cast<const float4*>(xs + c);
         a0 = fmaf(u.x, v.x, a0); a1 = fmaf(u.y, v.y, a1);
@@ -184,9 +184,10 @@ __device__ __forceinline__ double row_dot(const float* Ar, const float* xs, int 
     return (double)warp_sumf(a0 + a1);
 }
 
-__device__ __forceinline__ double row_dot(const __nv_bfloat16* Ar, const float* xs, int ld, int lane) {
+__device__ __forceinline__ double row_dot(const __nv_bfloat16* Ar, const float* xs, int ld, int lane,
+                                          int part, int parts) {
     float a0 = 0.f, a1 = 0.f;
-    for (int c = 8 * lane; c < ld; c += 256) {
+    for (int c = 8 * (lane + 32 * part); c < ld; c += 256 * parts) {
         const uint4 v = *reinterpret_cast<const uint4*>(Ar + c);
         const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
         const float4 x0 = *reinterpret_cast<const float4*>(xs + c);
@@ -202,6 +203,14 @@ __device__ __forceinline__ double row_dot(const __nv_bfloat16* Ar, const float* 
     }
     return (double)warp_sumf(a0 + a1);
 }
+
+// What the P phase needs of one tile, staged in shared memory at kernel start.
+struct TileDesc {
+    int64_t src_off;      // element offset of the tile's first row in the store
+    int64_t in_off;       // first DOF of the tile's subdomain
+    int32_t row0, nrt, ld, ncols, block, pair_begin, pair_count;
+    uint32_t bytes;       // bulk-copy size
+};
 
 // Rows of the CTA's elements of y = K x, warp per element, with x read from the
 // CTA-local staging xn (index: local element l * NP + j): lane (i, g) sums
@@ -220,24 +229,27 @@ __device__ __forceinline__ void local_rows(const int32_t* __restrict__ row_ptr,
         const int ncol = (row_ptr[e + 1] - b0) * NP;
         const double* V = val + (int64_t)b0 * NP * NP;
         const int32_t* cl = col_local + b0;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        double acc8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc8[u] = 0.0;
         int c = g;
-        for (; c + 3 * G < ncol; c += 4 * G) {
-            const int cb = c + G, cc = c + 2 * G, cd = c + 3 * G;
-            const double va = __ldg(V + (int64_t)c * NP + i), vb = __ldg(V + (int64_t)cb * NP + i);
-            const double vc = __ldg(V + (int64_t)cc * NP + i), vd = __ldg(V + (int64_t)cd * NP + i);
-            const int sa = c / NP, sb = cb / NP, sc_ = cc / NP, sd = cd / NP;
-            a0 = fma(va, xn[__ldg(cl + sa) * NP + (c - sa * NP)], a0);
-            a1 = fma(vb, xn[__ldg(cl + sb) * NP + (cb - sb * NP)], a1);
-            a2 = fma(vc, xn[__ldg(cl + sc_) * NP + (cc - sc_ * NP)], a2);
-            a3 = fma(vd, xn[__ldg(cl + sd) * NP + (cd - sd * NP)], a3);
+        for (; c + 7 * G < ncol; c += 8 * G) {
+            double vv[8], xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int cu = c + u * G, su = cu / NP;
+                vv[u] = __ldg(V + (int64_t)cu * NP + i);
+                xv[u] = xn[__ldg(cl + su) * NP + (cu - su * NP)];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc8[u] = fma(vv[u], xv[u], acc8[u]);
         }
         for (; c < ncol; c += G) {
             const int sa = c / NP;
-            a0 = fma(__ldg(V + (int64_t)c * NP + i), xn[__ldg(cl + sa) * NP + (c - sa * NP)], a0);
+            acc8[0] = fma(__ldg(V + (int64_t)c * NP + i), xn[__ldg(cl + sa) * NP + (c - sa * NP)], acc8[0]);
         }
-        a0 += a2;
-        a1 += a3;
+        const double a0 = (acc8[0] + acc8[4]) + (acc8[2] + acc8[6]);
+        const double a1 = (acc8[1] + acc8[5]) + (acc8[3] + acc8[7]);
         const double acc = a0 + a1;
         double tot = acc;
 #pragma unroll
@@ -262,8 +274,7 @@ pcg_persistent_kernel(PersistArgs a) {
     const bool flexible = sc->flexible != 0;
     const double rtol2 = sc->rtol2;
     const int maxit = sc->maxit;
-    unsigned gen = 0;
-    if (threadIdx.x == 0) gen = ld_acquire(&a.gs->gen);
+    unsigned gen = 0;                 // barrier target of thread 0 (gs->count is 0 at launch)
 
     auto buf = [&](int k) { return reinterpret_cast<T*>(smem + (size_t)k * a.buf_bytes); };
     X* xs = reinterpret_cast<X*>(smem + a.xs_off);                 // r' in the store's arithmetic
@@ -272,6 +283,8 @@ pcg_persistent_kernel(PersistArgs a) {
     double* r0s = reinterpret_cast<double*>(smem + a.r0_off);      // [n0]
     double* y0l = reinterpret_cast<double*>(smem + a.y0_off);      // y0 of the CTA's agglomerates
     double* pn = reinterpret_cast<double*>(smem + a.pn_off);       // x or z of the needed elements
+    TileDesc* td = reinterpret_cast<TileDesc*>(smem + a.td_off);   // this CTA's tiles
+    __shared__ double zpart[kPersistThreads / 32];                 // split-row partial dots
 
     const int64_t e0 = a.elem_ptr[cta], e1 = a.elem_ptr[cta + 1];
     const int n_own = (int)(e1 - e0);
@@ -303,14 +316,28 @@ pcg_persistent_kernel(PersistArgs a) {
         v2[1] = fma(rv, rv, v2[1]);
     });
     uint32_t seq = 0;                 // tiles consumed so far (all iterations)
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+        const GemvTile tl = a.tiles[t0 + k];
+        const GemvBlock B = a.blocks[tl.block];
+        TileDesc d;
+        d.src_off = B.mat_off + (int64_t)tl.row0 * B.ld;
+        d.in_off = B.in_off;
+        d.row0 = tl.row0;
+        d.nrt = min(a.rows, B.nrows - tl.row0);
+        d.ld = B.ld;
+        d.ncols = B.ncols;
+        d.block = tl.block;
+        d.pair_begin = B.pair_begin;
+        d.pair_count = B.pair_count;
+        d.bytes = (uint32_t)((size_t)d.nrt * B.ld * sizeof(T));
+        td[k] = d;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[k]);
         for (int k = 0; k < S && nt > 0; ++k) {   // the inverses do not depend on the iterate
-            const GemvTile tl = a.tiles[t0 + k % nt];
-            const GemvBlock B = a.blocks[tl.block];
-            const uint32_t bytes = (uint32_t)((size_t)min(a.rows, B.nrows - tl.row0) * B.ld * sizeof(T));
-            bulk_load(buf(k), reinterpret_cast<const T*>(a.store) + B.mat_off + (int64_t)tl.row0 * B.ld,
-                      bytes, &bars[k]);
+            const TileDesc& d = td[k % nt];
+            bulk_load(buf(k), reinterpret_cast<const T*>(a.store) + d.src_off, d.bytes, &bars[k]);
         }
     }
     bool ok = barrier_sum<2>(a.gs, gen, a.err, a.partials, a.bcast, v2);
@@ -347,16 +374,16 @@ pcg_persistent_kernel(PersistArgs a) {
             }
         } else {
             int staged = -1;
+            const int parts = (a.rows < nw && nw % a.rows == 0) ? nw / a.rows : 1;
             for (int k = 0; k < nt; ++k, ++seq) {
-                const GemvTile tl = a.tiles[t0 + k];
-                const GemvBlock B = a.blocks[tl.block];
-                const int nrt = min(a.rows, B.nrows - tl.row0);
+                const TileDesc& tl = td[k];
+                const int nrt = tl.nrt;
                 if (tl.block != staged) {
                     __syncthreads();
-                    for (int j = threadIdx.x; j < B.ld; j += blockDim.x) {
+                    for (int j = threadIdx.x; j < tl.ld; j += blockDim.x) {
                         double r_ = 0.0;
-                        if (j < B.ncols) {
-                            const int64_t t = B.in_off + j;
+                        if (j < tl.ncols) {
+                            const int64_t t = tl.in_off + j;
                             const double qk = fma(be, __ldcg(qold + t), __ldcg(a.w + t));
                             r_ = fma(-al, qk, __ldcg(rin + t));
                         }
@@ -367,7 +394,7 @@ pcg_persistent_kernel(PersistArgs a) {
                     __syncthreads();
                 }
                 // operands of the commit, fetched before the tile lands
-                const int64_t tr = B.in_off + tl.row0 + threadIdx.x;
+                const int64_t tr = tl.in_off + tl.row0 + threadIdx.x;
                 double zv = 0.0, wv = 0.0, pv = 0.0, qv = 0.0, xv = 0.0;
                 if ((int)threadIdx.x < nrt) {
                     zv = __ldcg(a.z + tr); wv = __ldcg(a.w + tr);
@@ -381,17 +408,27 @@ pcg_persistent_kernel(PersistArgs a) {
                 double* zt = zs + bi * a.rows;
                 const T* As = buf(bi);
                 const X* xin = (DT == 0) ? reinterpret_cast<const X*>(rp) : xs;
-                for (int r_ = warp; r_ < nrt; r_ += nw) {
-                    const double zr = row_dot(As + (size_t)r_ * B.ld, xin, B.ld, lane);
-                    if (lane == 0) zt[r_] = zr;
+                if (parts == 1) {
+                    for (int r_ = warp; r_ < nrt; r_ += nw) {
+                        const double zr = row_dot(As + (size_t)r_ * tl.ld, xin, tl.ld, lane, 0, 1);
+                        if (lane == 0) zt[r_] = zr;
+                    }
+                    __syncthreads();
+                } else {                  // rows < warps: each row split over `parts` warps
+                    const int r_ = warp % a.rows, part = warp / a.rows;
+                    const double zr = (r_ < nrt) ? row_dot(As + (size_t)r_ * tl.ld, xin, tl.ld, lane, part, parts) : 0.0;
+                    if (lane == 0) zpart[warp] = zr;
+                    __syncthreads();
+                    if ((int)threadIdx.x < nrt) {
+                        double sum = 0.0;
+                        for (int pt = 0; pt < parts; ++pt) sum += zpart[pt * a.rows + threadIdx.x];
+                        zt[threadIdx.x] = sum;
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
                 if (threadIdx.x == 0) {   // buffer bi is free: prefetch S tiles ahead (cyclic)
-                    const GemvTile tn = a.tiles[t0 + (k + S) % nt];
-                    const GemvBlock Bn = a.blocks[tn.block];
-                    const uint32_t bytes = (uint32_t)((size_t)min(a.rows, Bn.nrows - tn.row0) * Bn.ld * sizeof(T));
-                    bulk_load(buf(bi), reinterpret_cast<const T*>(a.store) + Bn.mat_off + (int64_t)tn.row0 * Bn.ld,
-                              bytes, &bars[bi]);
+                    const TileDesc& tn = td[(k + S) % nt];
+                    bulk_load(buf(bi), reinterpret_cast<const T*>(a.store) + tn.src_off, tn.bytes, &bars[bi]);
                 }
                 if ((int)threadIdx.x < nrt) {
                     const double pk = fma(be, pv, zv), qk = fma(be, qv, wv);
@@ -404,8 +441,8 @@ pcg_persistent_kernel(PersistArgs a) {
                     v1[0] = fma(r_, r_, v1[0]);
                 }
                 if (tl.row0 == 0 && coarse) {   // this CTA stages the subdomain first: R_0 r'
-                    for (int pi = 0; pi < B.pair_count; ++pi) {
-                        const GemvBlock R = a.blocks[a.sub_pairs[B.pair_begin + pi]];
+                    for (int pi = 0; pi < tl.pair_count; ++pi) {
+                        const GemvBlock R = a.blocks[a.sub_pairs[tl.pair_begin + pi]];
                         const double* Rm = a.st64 + R.mat_off;
                         for (int row = warp; row < R.nrows; row += nw) {
                             const double* Rr = Rm + (int64_t)row * R.ld;
