@@ -297,19 +297,47 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
             tbytes.push_back((int64_t)std::min(rows, B.nrows - r0) * B.ld * esz);
         }
     }
-    int64_t total = 0;
-    for (auto v : tbytes) total += v;
-    std::vector<int32_t> tile_ptr(G + 1, 0);
-    {
-        int64_t acc = 0;
-        size_t k = 0;
-        for (int g = 0; g < G; ++g) {
-            tile_ptr[g] = (int32_t)k;
-            const int64_t target = (total * (g + 1)) / G;
-            while (k < tiles.size() && acc + tbytes[k] / 2 <= target) acc += tbytes[k++];
-        }
-        tile_ptr[G] = (int32_t)tiles.size();
+    // Split the tile sequence into G contiguous runs of about equal estimated time:
+    // the tile's bytes at the per-SM share of HBM bandwidth, a fixed per-tile cost,
+    // a re-stage of r' whenever a run enters a new subdomain, and the restriction
+    // rows for the run that holds a subdomain's first tile.
+    const double bw_sm = 6.0e12 / G;                     // bytes/s per SM (about HBM / SMs)
+    const double c_tile = 0.6e-6, c_stage = 1.5e-6, c_pair = 2.0e-6;
+    std::vector<double> tcost(tiles.size()), tstage(tiles.size());
+    for (size_t k = 0; k < tiles.size(); ++k) {
+        const GemvBlock& B = pc->blocks[tiles[k].block];
+        tcost[k] = tbytes[k] / bw_sm + c_tile + (tiles[k].row0 == 0 ? c_pair * B.pair_count : 0.0);
+        tstage[k] = c_stage;
     }
+    // greedy packing under a per-CTA budget; the smallest budget that fits in G runs
+    // (bisection) gives the partition with the smallest maximum estimated time
+    auto pack = [&](double budget, std::vector<int32_t>* ptr) {
+        int runs = 0;
+        size_t k = 0;
+        while (k < tiles.size()) {
+            if (ptr) (*ptr)[runs] = (int32_t)k;
+            ++runs;
+            double acc = 0.0;
+            const size_t first = k;
+            while (k < tiles.size()) {
+                const bool stage = (k == first) || tiles[k].block != tiles[k - 1].block;
+                const double c = tcost[k] + (stage ? tstage[k] : 0.0);
+                if (k > first && acc + c > budget) break;
+                acc += c;
+                ++k;
+            }
+        }
+        return runs;
+    };
+    double lo = 0.0, hi = 0.0;
+    for (size_t k = 0; k < tiles.size(); ++k) hi += tcost[k] + tstage[k];
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (pack(mid, nullptr) <= G) hi = mid; else lo = mid;
+    }
+    std::vector<int32_t> tile_ptr(G + 1, (int32_t)tiles.size());
+    const int runs = tiles.empty() ? 0 : pack(hi, &tile_ptr);
+    for (int g = runs; g <= G; ++g) tile_ptr[g] = (int32_t)tiles.size();
     for (int g = 0; g < G; ++g)
         if (tile_ptr[g + 1] - tile_ptr[g] > 64) {
             set_error("pcg: more than 64 tiles per CTA; subdomains too large for this plan");
