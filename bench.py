@@ -15,8 +15,15 @@ The working set (fp32 store 112 MB + K_h 22.5 MB + vectors) exceeds the 126 MB
 L2, so no L2 flush is inserted between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload voronoi4096|batch32]
 Under torchrun (N > 1) every rank runs an independent replica (the path has no
 exchange step); rank 0 prints one JSON line with the whole-job throughput.
+
+--workload batch32 times the batched form instead: 32 independent simulations on 8
+Voronoi meshes of 1024-16384 cells (log-uniform), 4 per mesh with scalar
+conductivities U[0.5, 2] and random stimulus sites, all solves of a step in one
+batched persistent launch (mixed precision), against the same simulations stepped one
+after another in fp64 plain form; the unit is simulation-steps/s.
 """
 import argparse
 import json
@@ -31,6 +38,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "ASM-PCG time-steps/s at rel.res 1e-8, mixed+learned vs FP64 plain, 1 GB300"
+BATCH_WORKLOAD = ("batch32: 32 coupled simulations, 8 Voronoi meshes 1024-16384 cells "
+                  "(log-uniform, seed 4) x 4 conductivities/stimuli, P3, ~64 cells/subdomain")
 WORKLOAD = "voronoi4096_p3 coupled monodomain+Barreto-Cressman, 40960 DOFs, 64 subdomains, coarse P1"
 
 
@@ -229,6 +238,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["voronoi4096", "batch32"], default="voronoi4096")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -244,6 +254,8 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl")
     stream = torch.cuda.current_stream()
+    if args.workload == "batch32":
+        return bench_batch(args, pd, torch, stream, rank, world, local)
     w = build_case()
     ctx = pd.polydg_setup(w.mesh.vertices, w.mesh.cell_ptr, w.mesh.cell_vtx, w.sigma, w.p,
                           w.subdomain, w.chi_cm, w.dt, w.eta0)
@@ -306,6 +318,129 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 7 * args.steps,
         "roofline": roofline,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def bench_batch(args, pd, torch, stream, rank, world, local):
+    """Batched form: simulation-steps/s of 32 simulations of uneven sizes."""
+    import numpy as np
+    from synth import voronoi_batch
+    ws = voronoi_batch()
+    peaks, peak_kind = measured_peaks()
+
+    def make(prec, flex):
+        out = []
+        for w in ws:
+            ctx = pd.polydg_setup(w.mesh.vertices, w.mesh.cell_ptr, w.mesh.cell_vtx, w.sigma,
+                                  w.p, w.subdomain, w.chi_cm, w.dt, w.eta0)
+            pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision=prec)
+            out.append((ctx, pc, pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus,
+                                               rtol=1e-8, maxit=5000, flexible=flex)))
+        return out
+
+    S = len(ws)
+    trip = make("fp32", True)
+    sims = [x[2] for x in trip]
+    bt = pd.batch_create(sims)
+    pd.batch_step(bt, args.warmup, stream)
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.__enter__()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st, sec = pd.batch_step(bt, args.steps, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks.__exit__(None, None, None)
+    ms = ev0.elapsed_time(ev1)
+    # algorithmic bytes of all solves over the device time of the whole batched steps
+    alg = 0.0
+    for (ctx, pc, _), s_ in zip(trip, st):
+        alg += algorithmic_bytes(ctx.info, pc.info(), s_["total_iterations"], s_["steps_done"])
+    achieved = alg / (sec * 1e9)
+    # e2e: every simulation's potential through pinned host memory each step
+    n_all = sum(ctx.n_dofs for ctx, _, _ in trip)
+    hu = [torch.empty(ctx.n_dofs, dtype=torch.float64).pin_memory() for ctx, _, _ in trip]
+    du = [torch.empty(ctx.n_dofs, dtype=torch.float64, device="cuda") for ctx, _, _ in trip]
+    for s_, d_, h_ in zip(sims, du, hu):
+        pd.sim_get_state(s_, d_, stream=stream)
+        h_.copy_(d_)
+    torch.cuda.synchronize()
+    e_steps = max(2, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        for s_, d_, h_ in zip(sims, du, hu):
+            d_.copy_(h_, non_blocking=True)
+            pd.sim_set_potential(s_, d_, None, stream)
+        pd.batch_step(bt, 1, stream)
+        for s_, d_, h_ in zip(sims, du, hu):
+            pd.sim_get_state(s_, d_, stream=stream)
+            h_.copy_(d_, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_val = world * S * e_steps / (time.perf_counter() - t0)
+    its = [s_["total_iterations"] / args.steps for s_ in st]
+    groups = bt.groups().tolist()
+    bt.close()
+    del trip, sims
+    torch.cuda.empty_cache()
+    # baseline: the same simulations in fp64 plain form, one simulation after another
+    trip64 = make("fp64", False)
+    for _, _, s_ in trip64:
+        pd.monodomain_step(s_, args.warmup, stream)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    its64 = []
+    for _, _, s_ in trip64:
+        its64.append(pd.monodomain_step(s_, args.steps, stream)["total_iterations"] / args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms, ms64], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms, ms64 = float(t[0]), float(t[1])
+    value = world * S * args.steps / (ms * 1e-3)
+    value64 = world * S * args.steps / (ms64 * 1e-3)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # oracle on the smallest mesh's first simulation, scaled by DOFs to all 32
+        k = int(np.argmin([w.mesh.n_cells for w in ws]))
+        t_step, t_rhs, t_it = cpu_baseline(ws[k], its64[k], sample_its=10)
+        scale = n_all / (ws[k].mesh.n_cells * 10)
+        cpu = {"value": 1.0 / (t_step * scale) * S, "unit": "simulation-steps/s",
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one step of the {ws[k].mesh.n_cells}-cell simulation (ionic update + "
+                         f"RHS and 10 ASM-PCG iterations of the float64 oracle, scaled to "
+                         f"{its64[k]:.0f} iterations), scaled by DOFs to all 32 simulations"}
+    line = {
+        "metric": METRIC + " (batched form)", "value": value, "unit": "simulation-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "form": "batched: one persistent launch per step "
+                   "for all 32 solves (fp32 local inverses, flexible PCG), captured step graph",
+                   "cells": [w.mesh.n_cells for w in ws[::4]], "dofs": n_all,
+                   "ctas_per_sim": groups, "iterations_per_step": its,
+                   "fp64_plain_per_sim_launches_sim_steps_per_s": value64,
+                   "fp64_plain_iterations_per_step": its64,
+                   "batched_over_fp64_plain": value / value64,
+                   "l2": "working set > L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+        "clocks": clocks.summary(),
+        "e2e": {"value": e2e_val, "unit": "simulation-steps/s",
+                "h2d_bytes_per_step": 8 * n_all, "d2h_bytes_per_step": 8 * n_all},
+        "gpu_launches": (6 * S + 1) * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "pcg_batched_kernel<fp32 store, n_p=10> (whole step time)",
+                     "peak_kind": peak_kind},
         "cpu_baseline": cpu,
     }
     if rank == 0:

@@ -63,6 +63,8 @@ extern "C" {
 typedef struct polydg_ctx polydg_ctx;
 typedef struct asm_ctx asm_ctx;
 typedef struct sim_ctx sim_ctx;
+typedef struct batch_ctx batch_ctx;
+typedef struct guess_model guess_model;
 
 /* A 2D polygonal mesh (Sec. 3: T_h, disjoint polygons).  Cells are convex
  * polygons given as counter-clockwise vertex loops in CSR form; two cells
@@ -120,6 +122,7 @@ typedef struct {
     double  last_relres;       /* relative residual of the last step's solve */
     double  pcg_seconds;       /* device time of the PCG solver kernel over these steps,
                                   measured with CUDA events on the caller's stream */
+    int64_t guesses_taken;     /* steps whose PCG started from the learned guess */
 } step_stats;
 
 /* Sizes of a preconditioner, for bandwidth accounting. */
@@ -131,7 +134,7 @@ typedef struct {
     int32_t n_coarse;            /* coarse DOFs n_0 (0: one-level)              */
     int32_t precision;           /* POLYDG_FP64/FP32/BF16                       */
     int32_t grid;                /* CTAs of the persistent PCG kernel           */
-    int32_t rows_per_tile;       /* rows of K_i^{-1} per bulk copy              */
+    int32_t rows_per_tile;       /* rows of K_i^{-1} per bulk copy (1)          */
     int32_t pad;
 } asm_info;
 
@@ -211,6 +214,89 @@ int sim_set_potential(sim_ctx *sim, const double *u_dev, const double *uprev_dev
 
 /* Current step index k. */
 int64_t sim_step_index(const sim_ctx *sim);
+
+/* Group n independent simulations (different meshes, conductivities and stimuli;
+ * each with its own preconditioner, all with the same degree and local precision,
+ * on one device) so that batch_step advances all of them in one cooperative
+ * kernel launch per step for all their PCG solves.  Simulation i gets its own
+ * group of CTAs (at least one; 1 <= n <= number of SMs), sized so that the bytes
+ * each CTA streams per iteration are as even as possible; within the launch every
+ * group runs its own PCG (own scalars, barrier and stopping test), so simulations
+ * that converge in fewer iterations stop early without affecting the others.
+ * The batch refers to the simulations' own buffers (nothing is copied): the sims
+ * must outlive the batch, and sim_get_state / sim_set_potential / monodomain_step
+ * still work on them between batch_step calls.  Errors: EINVAL (duplicate sim or
+ * shared preconditioner, mixed degree/precision/device, n too large, a subdomain
+ * plan that does not fit), ENOMEM, ECUDA. */
+int batch_create(sim_ctx *const *sims, int n, batch_ctx **out);
+
+/* CTAs of the batched launch given to each simulation (host array [n]). */
+int batch_get_groups(const batch_ctx *batch, int32_t *ctas_of_sim);
+
+/* Advance every simulation of the batch nsteps Crank-Nicolson steps (the step of
+ * monodomain_step).  The first call records one step -- the per-simulation ionic,
+ * right-hand-side and bookkeeping kernels around one batched PCG launch -- into a
+ * CUDA graph on an internal stream; each step is then one launch of that graph on
+ * `stream`.  Synchronises `stream`.  per_sim (host array [n], may be NULL) gets each
+ * simulation's statistics, with pcg_seconds = device time of the whole batched steps
+ * (CUDA events around each graph launch); *seconds (may be NULL) gets the same time.
+ * A simulation whose solve fails stops stepping (the others continue); the first
+ * failing status is returned. */
+int batch_step(batch_ctx *batch, int nsteps, void *stream, step_stats *per_sim, double *seconds);
+
+void batch_destroy(batch_ctx *batch);
+
+/* ---- Learned initial guess.  The paper starts each step's PCG from U^k (Sec. 5);
+ * this optional network proposes x0 = U^k + s_d o per element instead, o being the
+ * output of a two-hidden-layer ReLU network (width 128) applied to features of the
+ * element and its face neighbours from the last three solutions:
+ *   own a = (U^k_e - u_rest e_0)/s_u, d1 = (U^k_e - U^{k-1}_e)/s_d, d2 = (U^{k-1}_e - U^{k-2}_e)/s_d
+ *   (e_0 = the constant mode), then the elementwise mean and the elementwise max of
+ *   [a, d1, d2] over the face neighbours, then h_e/h_ref, dt/dt_ref, (neighbours)/10:
+ *   9 n_p + 3 inputs.  Parameters, flat: W1 [128][9 n_p + 3] row-major, b1 [128],
+ *   W2 [128][128], b2 [128], W3 [n_p][128], b3 [n_p]; scales = {u_rest, s_u, s_d,
+ *   h_ref, dt_ref}.  Inference uses fp16 weights with fp32 activations; training keeps
+ *   fp32 weights and Adam state (beta1 0.9, beta2 0.999, eps 1e-8). */
+
+/* Number of parameters for n_p coefficients per element (or POLYDG_EINVAL).  The
+ * learned guess supports n_p = 3, 6, 10 (p = 1, 2, 3 in 2D). */
+int guess_n_params(int n_p);
+
+/* Create a model on the current device from host parameters [guess_n_params(n_p)]
+ * (copied; rounded to float32) and scales [5] (NULL: -67, 50, 1, 1, 0.05). */
+int guess_create(int n_p, const double *params, const double *scales, guess_model **out);
+
+/* Copy the float32 parameters and Adam moments (each may be NULL) to host arrays of
+ * guess_n_params(n_p) doubles, and the number of Adam steps taken to *adam_t. */
+int guess_get_params(const guess_model *model, double *params, double *adam_m, double *adam_v,
+                     int64_t *adam_t);
+
+int guess_set_scales(guess_model *model, const double *scales);
+
+/* x = U^k + s_d o for caller-order device vectors uk, uk1, uk2 (U^k, U^{k-1}, U^{k-2})
+ * on the mesh of ctx (no safeguard: the raw proposal). */
+int guess_propose(guess_model *model, polydg_ctx *ctx, const double *uk, const double *uk1,
+                  const double *uk2, double *x_dev, void *stream);
+
+/* One Adam step on the mean squared error of o against (U^{k+1}_e - U^k_e)/s_d over
+ * n_samples samples.  traj_dev: device array [n_states][n_dofs] of caller-order
+ * solutions of one run on ctx's mesh; samples: host array [n_samples][2] of (state k,
+ * caller cell id) with 2 <= k <= n_states - 2.  *loss (may be NULL) gets the minibatch
+ * loss before the update.  Synchronises `stream`.  Gradients are summed in a fixed
+ * order, so a step is deterministic. */
+int guess_train_step(guess_model *model, polydg_ctx *ctx, const double *traj_dev, int64_t n_states,
+                     const int64_t *samples, int64_t n_samples, double lr, double *loss,
+                     void *stream);
+
+/* Use `model` (NULL: none) for the initial guess of the simulation's later steps: from
+ * k = 2 on, each step computes the proposal x0 and starts PCG from it --
+ *   policy 0: only if |b - K x0|_2 < |b - K U^k|_2 (else from U^k);
+ *   policy 1: always.
+ * The FP64 stopping test decides convergence either way, so only iteration counts
+ * change.  The model must outlive its use; it may be shared by several simulations. */
+int sim_set_guess(sim_ctx *sim, guess_model *model, int policy);
+
+void guess_destroy(guess_model *model);
 
 /* Invert `batch` symmetric positive definite float64 matrices in place, without
  * allocating any device memory.  The paper has no counterpart: this serves callers

@@ -23,7 +23,10 @@ PRECISION = {"fp64": POLYDG_FP64, "fp32": POLYDG_FP32, "bf16": POLYDG_BF16}
 EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_get_info", "polydg_get_faces",
            "polydg_matvec", "asm_setup", "asm_get_info", "asm_apply", "pcg_solve", "sim_create",
            "monodomain_step", "sim_get_state", "sim_set_potential", "sim_step_index",
-           "sim_destroy", "asm_destroy", "polydg_destroy", "polydg_spd_inverse_static"]
+           "sim_destroy", "asm_destroy", "polydg_destroy", "polydg_spd_inverse_static",
+           "batch_create", "batch_get_groups", "batch_step", "batch_destroy", "guess_n_params",
+           "guess_create", "guess_get_params", "guess_set_scales", "guess_propose",
+           "guess_train_step", "sim_set_guess", "guess_destroy"]
 
 
 class polydg_mesh(C.Structure):
@@ -54,7 +57,8 @@ class sim_params(C.Structure):
 class step_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("total_iterations", C.c_int64),
                 ("max_iterations", C.c_int32), ("status", C.c_int32),
-                ("last_relres", C.c_double), ("pcg_seconds", C.c_double)]
+                ("last_relres", C.c_double), ("pcg_seconds", C.c_double),
+                ("guesses_taken", C.c_int64)]
 
 
 class asm_info(C.Structure):
@@ -95,7 +99,23 @@ def load() -> C.CDLL:
     L.polydg_spd_inverse_static.restype = i32
     L.sim_step_index.argtypes = [vp]
     L.sim_step_index.restype = i64
-    for name in ("sim_destroy", "asm_destroy", "polydg_destroy"):
+    L.batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp)]
+    L.batch_get_groups.argtypes = [vp, C.POINTER(C.c_int32)]
+    L.batch_step.argtypes = [vp, i32, vp, C.POINTER(step_stats), C.POINTER(dbl)]
+    for name in ("batch_create", "batch_get_groups", "batch_step"):
+        getattr(L, name).restype = i32
+    pd_ = C.POINTER(C.c_double)
+    L.guess_n_params.argtypes = [i32]
+    L.guess_create.argtypes = [i32, pd_, pd_, C.POINTER(vp)]
+    L.guess_get_params.argtypes = [vp, pd_, pd_, pd_, C.POINTER(C.c_int64)]
+    L.guess_set_scales.argtypes = [vp, pd_]
+    L.guess_propose.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.guess_train_step.argtypes = [vp, vp, vp, i64, C.POINTER(C.c_int64), i64, dbl, pd_, vp]
+    L.sim_set_guess.argtypes = [vp, vp, i32]
+    for name in ("guess_n_params", "guess_create", "guess_get_params", "guess_set_scales",
+                 "guess_propose", "guess_train_step", "sim_set_guess"):
+        getattr(L, name).restype = i32
+    for name in ("sim_destroy", "asm_destroy", "polydg_destroy", "batch_destroy", "guess_destroy"):
         getattr(L, name).argtypes = [vp]
         getattr(L, name).restype = None
     for name in ("polydg_setup", "polydg_get_info", "polydg_get_faces", "polydg_matvec",
@@ -267,12 +287,57 @@ def sim_create(ctx: PolyDG, pc, u0=-67.0, stimulus=None, rtol=1e-8, maxit=10000,
     return Simulation(ctx, pc, h)
 
 
+def _stats(st):
+    return {"steps_done": st.steps_done, "total_iterations": st.total_iterations,
+            "max_iterations": st.max_iterations, "status": st.status,
+            "last_relres": st.last_relres, "pcg_seconds": st.pcg_seconds,
+            "guesses_taken": st.guesses_taken}
+
+
 def monodomain_step(sim: Simulation, nsteps=1, stream=None):
     st = step_stats()
     _check(load().monodomain_step(sim.h, int(nsteps), _stream(stream), C.byref(st)))
-    return {"steps_done": st.steps_done, "total_iterations": st.total_iterations,
-            "max_iterations": st.max_iterations, "status": st.status,
-            "last_relres": st.last_relres, "pcg_seconds": st.pcg_seconds}
+    return _stats(st)
+
+
+class Batch:
+    """Handle of a batch_ctx: simulations advanced together, one batched PCG launch
+    per step.  Keeps the Simulation objects alive while the batch exists."""
+
+    def __init__(self, sims, handle):
+        self.sims, self.h = list(sims), handle
+
+    def groups(self):
+        g = np.zeros(len(self.sims), np.int32)
+        _check(load().batch_get_groups(self.h, _ptr(g, C.c_int32)))
+        return g
+
+    def close(self):
+        if self.h:
+            load().batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_create(sims) -> Batch:
+    arr = (C.c_void_p * len(sims))(*[s.h for s in sims])
+    h = C.c_void_p()
+    _check(load().batch_create(arr, len(sims), C.byref(h)))
+    return Batch(sims, h)
+
+
+def batch_step(batch: Batch, nsteps=1, stream=None, allow=()):
+    """Advance every simulation nsteps steps; returns (per-simulation statistics,
+    device seconds of the batched steps).  Statuses in `allow` do not raise."""
+    st = (step_stats * len(batch.sims))()
+    sec = C.c_double()
+    _check(load().batch_step(batch.h, int(nsteps), _stream(stream), st, C.byref(sec)), allow)
+    return [_stats(x) for x in st], sec.value
 
 
 def sim_get_state(sim: Simulation, u, y=None, stream=None):
@@ -295,3 +360,79 @@ def spd_inverse_static(mats, n, ld, batch, stream=None):
         raise ValueError("tensor smaller than batch * n * ld")
     _check(load().polydg_spd_inverse_static(C.c_void_p(mats.data_ptr()), int(n), int(ld),
                                             int(batch), _stream(stream)))
+
+
+class GuessModel:
+    """Handle of a guess_model (learned PCG initial guess, include/polydg.h)."""
+
+    def __init__(self, n_p, handle):
+        self.n_p, self.h = n_p, handle
+
+    def params(self):
+        """(parameters, Adam m, Adam v, Adam steps) as float64 numpy arrays."""
+        n = guess_n_params(self.n_p)
+        p, m, v = np.empty(n), np.empty(n), np.empty(n)
+        t = C.c_int64()
+        _check(load().guess_get_params(self.h, _ptr(p, C.c_double), _ptr(m, C.c_double),
+                                       _ptr(v, C.c_double), C.byref(t)))
+        return p, m, v, t.value
+
+    def set_scales(self, scales):
+        sc = np.ascontiguousarray(scales, np.float64)
+        _check(load().guess_set_scales(self.h, _ptr(sc, C.c_double)))
+
+    def close(self):
+        if self.h:
+            load().guess_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def guess_n_params(n_p):
+    return _check_count(load().guess_n_params(int(n_p)))
+
+
+def _check_count(v):
+    if v < 0:
+        raise PolyDGError(v, load().polydg_last_error().decode())
+    return v
+
+
+def guess_create(n_p, params, scales=None) -> GuessModel:
+    p = np.ascontiguousarray(params, np.float64)
+    if p.size != guess_n_params(n_p):
+        raise ValueError("wrong number of parameters")
+    sc = None if scales is None else np.ascontiguousarray(scales, np.float64)
+    h = C.c_void_p()
+    _check(load().guess_create(int(n_p), _ptr(p, C.c_double),
+                               None if sc is None else _ptr(sc, C.c_double), C.byref(h)))
+    g = GuessModel(n_p, h)
+    g._keep = (p, sc)
+    return g
+
+
+def guess_propose(model: GuessModel, ctx: PolyDG, uk, uk1, uk2, x, stream=None):
+    _check(load().guess_propose(model.h, ctx.h, _dev(uk), _dev(uk1), _dev(uk2), _dev(x),
+                                _stream(stream)))
+
+
+def guess_train_step(model: GuessModel, ctx: PolyDG, traj, samples, lr, stream=None):
+    """One Adam step; traj is a [n_states, n_dofs] float64 CUDA tensor (caller order),
+    samples an [n, 2] int64 array of (state k, caller cell id).  Returns the loss."""
+    smp = np.ascontiguousarray(samples, np.int64)
+    loss = C.c_double()
+    _check(load().guess_train_step(model.h, ctx.h, _dev(traj), int(traj.shape[0]),
+                                   _ptr(smp, C.c_int64), int(smp.shape[0]), float(lr),
+                                   C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def sim_set_guess(sim: Simulation, model, policy=0):
+    """policy 0: start from the proposal only if its residual is smaller; 1: always."""
+    _check(load().sim_set_guess(sim.h, model.h if model is not None else None, int(policy)))
+    sim.guess = model

@@ -89,17 +89,21 @@ struct PcgWork {
 struct Plan {
     int grid = 0, rows = 1, dtype = 0;
     int redundant = 1;
-    size_t smem = 0, buf_bytes = 0, xs_off = 0, rp_off = 0, zs_off = 0, r0_off = 0, y0_off = 0,
+    int wstages = 1;
+    size_t smem = 0, slot_bytes = 0, xs_off = 0, rp_off = 0, r0_off = 0, y0_off = 0,
            pn_off = 0, td_off = 0;
-    int32_t *tile_ptr = nullptr, *sub_pairs = nullptr, *crow_ptr = nullptr;
+    int32_t *run_ptr = nullptr, *sub_pairs = nullptr, *crow_ptr = nullptr, *cta_chunk = nullptr;
+    int64_t* chunk_elem = nullptr;
     int32_t *need_ptr = nullptr, *need = nullptr, *col_local = nullptr;
     int32_t *need_aggl = nullptr, *need_agg_ptr = nullptr, *need_agg = nullptr;
-    GemvTile* tiles = nullptr;
+    GemvRun* runs = nullptr;
     int64_t* elem_ptr = nullptr;
+    double est_seconds = 0.0;           // cost model: slowest CTA's P phase per iteration
     void release() {
-        dfree(tile_ptr); dfree(sub_pairs); dfree(crow_ptr); dfree(need_ptr); dfree(need);
+        dfree(run_ptr); dfree(sub_pairs); dfree(crow_ptr); dfree(need_ptr); dfree(need);
+        dfree(cta_chunk); dfree(chunk_elem);
         dfree(need_aggl); dfree(need_agg_ptr); dfree(need_agg);
-        dfree(col_local); dfree(tiles); dfree(elem_ptr);
+        dfree(col_local); dfree(runs); dfree(elem_ptr);
     }
 };
 
@@ -116,6 +120,8 @@ struct polydg_ctx {
     double* d_node_w = nullptr;
     double* d_node_phi = nullptr;
     int64_t* d_node_pos = nullptr;
+    int64_t* d_to_internal = nullptr;   // caller -> internal cell id
+    double* d_diam = nullptr;           // cell diameters, internal order
     // identity tiles (z = r) for unpreconditioned CG
     GemvBlock* d_id_blocks = nullptr;
     GemvTile* d_id_tiles = nullptr;
@@ -155,17 +161,53 @@ struct asm_ctx {
     int64_t store_bytes = 0;            // bytes of the dense stores read per apply
 };
 
+// Learned initial-guess network (fp32 master weights and Adam state, fp16 copy for
+// inference) and its training buffers.
+struct guess_model {
+    int np = 0, P = 0, device = 0;
+    double scales[5] = {-67.0, 50.0, 1.0, 1.0, 0.05};   // u_rest, s_u, s_d, h_ref, dt_ref
+    float *w32 = nullptr, *m = nullptr, *v = nullptr, *part = nullptr;
+    __half* w16 = nullptr;
+    double *lpart = nullptr, *loss = nullptr;
+    int64_t* samples = nullptr;
+    int64_t sample_cap = 0;
+    int grid_max = 0;
+    int64_t t = 0;                      // Adam steps taken
+};
+
 struct sim_ctx {
     polydg_ctx* ctx = nullptr;
     asm_ctx* pc = nullptr;
     sim_params prm{};
     PcgWork work;
+    guess_model* guess = nullptr;       // learned initial guess (nullptr: x0 = U^k)
+    int guess_policy = 0;               // 0: keep the smaller residual, 1: always the proposal
+    int64_t version = 0;                // bumped when the step's kernel sequence changes
+    double *Uprev2 = nullptr, *xg = nullptr;
     double *U = nullptr, *Uprev = nullptr, *I = nullptr, *F = nullptr, *y = nullptr;
     double* d_y0 = nullptr;
     SimScalars* d_ss = nullptr;
     SimScalars* h_ss = nullptr;         // pinned
     int64_t k = 0;
     std::vector<cudaEvent_t> ev;        // [2 * steps] around each step's PCG kernel
+};
+
+// Independent simulations advanced together: one cooperative launch per step in
+// which simulation i owns CTAs [cta_begin[i], cta_begin[i] + group[i]).
+struct batch_ctx {
+    std::vector<sim_ctx*> sims;
+    std::vector<Plan> plans;            // per simulation, for its CTA group
+    std::vector<int> group;             // CTAs per simulation
+    PersistArgs* d_args = nullptr;      // [n]
+    int2* d_map = nullptr;              // [n_cta] (simulation, CTA within its group)
+    int n_cta = 0, dtype = 0, np = 0, device = 0;
+    size_t smem = 0;
+    cudaStream_t cap = nullptr;         // stream the step is captured on
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> versions;      // the simulations' versions when the step was captured
+    std::vector<cudaEvent_t> ev;        // [2 * steps] around each step's graph launch
+    SimScalars* h_ss = nullptr;         // pinned [n]
 };
 
 namespace polydg {
@@ -191,9 +233,9 @@ static K2Args k2_args(polydg_ctx* c, asm_ctx* pc, PcgScalars* sc, double* partia
 // local inverses) as contiguous runs balanced by bytes, elements and coarse rows
 // evenly; per CTA the elements whose p its matvec rows need (own range first,
 // then face neighbours) and the CTA-local column index of every block.
-static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
+static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 0) {
     const HostSetup& H = c->H;
-    const int G = c->n_sm, np = H.n_p;
+    const int np = H.n_p;
     P.grid = G;
     P.dtype = pc ? pc->precision : 0;
     const int esz = P.dtype == 0 ? 8 : P.dtype == 1 ? 4 : 2;
@@ -208,20 +250,33 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
                 max_ld = std::max<int64_t>(max_ld, pc->blocks[b].ld);
             }
     const int64_t n0 = (pc && pc->has_coarse) ? pc->n0 : 0;
-    // elements and neighbour lists
-    std::vector<int64_t> elem_ptr(G + 1);
+    // elements: an even split over the CTAs, each CTA's range cut into chunks of
+    // at most kChunk elements; per chunk the elements whose z its matvec rows need
+    // (the chunk first, then face neighbours outside it)
+    constexpr int64_t kChunk = 64;
+    std::vector<int64_t> elem_ptr(G + 1), chunk_elem;
+    std::vector<int32_t> cta_chunk(G + 1, 0);
     for (int g = 0; g <= G; ++g) elem_ptr[g] = (H.nc * g) / G;
-    std::vector<int32_t> need_ptr(G + 1, 0), need, col_local(H.col.size());
-    int max_need = 0;
     for (int g = 0; g < G; ++g) {
-        const int64_t e0 = elem_ptr[g], e1 = elem_ptr[g + 1];
+        cta_chunk[g] = (int32_t)chunk_elem.size();
+        const int64_t n_own = elem_ptr[g + 1] - elem_ptr[g];
+        const int64_t nch = (n_own + kChunk - 1) / kChunk;
+        for (int64_t k = 0; k < nch; ++k) chunk_elem.push_back(elem_ptr[g] + (n_own * k) / nch);
+    }
+    cta_chunk[G] = (int32_t)chunk_elem.size();
+    chunk_elem.push_back(H.nc);
+    const int n_chunks = cta_chunk[G];
+    std::vector<int32_t> need_ptr(n_chunks + 1, 0), need, col_local(H.col.size());
+    int max_need = 0;
+    for (int ch = 0; ch < n_chunks; ++ch) {
+        const int64_t e0 = chunk_elem[ch], e1 = chunk_elem[ch + 1];
         std::vector<int32_t> nb;
         for (int64_t e = e0; e < e1; ++e)
             for (int32_t bi = H.row_ptr[e]; bi < H.row_ptr[e + 1]; ++bi)
                 if (H.col[bi] < e0 || H.col[bi] >= e1) nb.push_back(H.col[bi]);
         std::sort(nb.begin(), nb.end());
         nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
-        need_ptr[g] = (int32_t)need.size();
+        need_ptr[ch] = (int32_t)need.size();
         for (int64_t e = e0; e < e1; ++e) need.push_back((int32_t)e);
         need.insert(need.end(), nb.begin(), nb.end());
         for (int64_t e = e0; e < e1; ++e)
@@ -233,7 +288,7 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
             }
         max_need = std::max(max_need, (int)((e1 - e0) + nb.size()));
     }
-    need_ptr[G] = (int32_t)need.size();
+    need_ptr[n_chunks] = (int32_t)need.size();
     // agglomerates touched by each CTA's needed elements (coarse rows it solves redundantly)
     const int nq = (pc && pc->has_coarse) ? pc->nq : 1;
     std::vector<int32_t> agg_internal(H.nc, 0);
@@ -245,12 +300,13 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
     std::vector<int32_t> need_aggl(need.size(), 0), need_agg_ptr(G + 1, 0), need_agg;
     int max_aggs = 0;
     for (int g = 0; g < G; ++g) {
+        const int32_t k0 = need_ptr[cta_chunk[g]], k1 = need_ptr[cta_chunk[g + 1]];
         std::vector<int32_t> js;
-        for (int32_t k = need_ptr[g]; k < need_ptr[g + 1]; ++k) js.push_back(agg_internal[need[k]]);
+        for (int32_t k = k0; k < k1; ++k) js.push_back(agg_internal[need[k]]);
         std::sort(js.begin(), js.end());
         js.erase(std::unique(js.begin(), js.end()), js.end());
         need_agg_ptr[g] = (int32_t)need_agg.size();
-        for (int32_t k = need_ptr[g]; k < need_ptr[g + 1]; ++k)
+        for (int32_t k = k0; k < k1; ++k)
             need_aggl[k] = (int32_t)(std::lower_bound(js.begin(), js.end(), agg_internal[need[k]]) - js.begin());
         need_agg.insert(need_agg.end(), js.begin(), js.end());
         max_aggs = std::max(max_aggs, (int)js.size());
@@ -263,26 +319,25 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
     // r0/q0, p of the needed elements
     auto r128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
     const size_t cap = 220 * 1024;
+    constexpr int kMaxRuns = 128;                // run descriptors (48 bytes) per CTA
+    const size_t td_reserve = r128(kMaxRuns * 48);
     const size_t fixed = r128((size_t)max_ld * xsz) + r128((size_t)max_ld * 8) + r128((size_t)n0 * 8) +
-                         r128((size_t)max_aggs * nq * 8) + r128((size_t)max_need * np * 8) +
-                         r128(kStages * 64 * 8);
-    if (fixed + kStages * (size_t)max_ld * esz > cap) {
+                         r128((size_t)max_aggs * nq * 8) + r128((size_t)max_need * np * 8) + td_reserve;
+    // per warp, as many one-row copy slots (up to kMaxWarpStages) as the rest leaves room for
+    const int NW = kPersistThreads / 32;
+    const size_t slot = pc ? r128((size_t)max_ld * esz) : 0;
+    const int64_t wst = (pc && fixed < cap) ? (int64_t)((cap - fixed) / (NW * slot)) : (pc ? 0 : 1);
+    if (wst < 1) {
         set_error("pcg: a subdomain or coarse space is too large for the shared-memory plan");
         return POLYDG_EINVAL;
     }
-    // tile rows: a multiple of the 16 warps, or a power of two that divides them (a row
-    // is then split over 16/rows warps); at most what kStages buffers leave room for
-    const size_t td_reserve = r128(64 * 64);   // descriptors of up to 64 tiles per CTA
-    const int64_t rmax = std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)((cap - fixed - td_reserve) / kStages / ((size_t)max_ld * esz))));
-    int rows = 1;
-    if (rmax >= 16) rows = (int)(rmax / 16 * 16);
-    else while (rows * 2 <= rmax) rows *= 2;
-    P.rows = rows;
-    P.buf_bytes = pc ? r128((size_t)rows * max_ld * esz) : 0;
-    P.xs_off = kStages * P.buf_bytes;
+    P.wstages = (int)std::min<int64_t>(kMaxWarpStages, wst);
+    P.slot_bytes = slot;
+    P.rows = 16;                                 // partition granularity (rows per tile)
+    const int rows = P.rows;
+    P.xs_off = (size_t)NW * P.wstages * slot;
     P.rp_off = P.xs_off + r128((size_t)max_ld * xsz);
-    P.zs_off = P.rp_off + r128((size_t)max_ld * 8);
-    P.r0_off = P.zs_off + r128(kStages * (size_t)rows * 8);
+    P.r0_off = P.rp_off + r128((size_t)max_ld * 8);
     P.y0_off = P.r0_off + r128((size_t)n0 * 8);
     P.pn_off = P.y0_off + r128((size_t)max_aggs * nq * 8);
     P.td_off = P.pn_off + r128((size_t)max_need * np * 8);
@@ -301,8 +356,8 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
     // the tile's bytes at the per-SM share of HBM bandwidth, a fixed per-tile cost,
     // a re-stage of r' whenever a run enters a new subdomain, and the restriction
     // rows for the run that holds a subdomain's first tile.
-    const double bw_sm = 6.0e12 / G;                     // bytes/s per SM (about HBM / SMs)
-    const double c_tile = 0.6e-6, c_stage = 1.5e-6, c_pair = 2.0e-6;
+    const double bw_sm = 6.0e12 / c->n_sm;               // bytes/s per SM (about HBM / SMs)
+    const double c_tile = 0.1e-6, c_stage = 1.5e-6, c_pair = 2.0e-6;
     std::vector<double> tcost(tiles.size()), tstage(tiles.size());
     for (size_t k = 0; k < tiles.size(); ++k) {
         const GemvBlock& B = pc->blocks[tiles[k].block];
@@ -336,54 +391,70 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, Plan& P) {
         if (pack(mid, nullptr) <= G) hi = mid; else lo = mid;
     }
     std::vector<int32_t> tile_ptr(G + 1, (int32_t)tiles.size());
-    const int runs = tiles.empty() ? 0 : pack(hi, &tile_ptr);
-    for (int g = runs; g <= G; ++g) tile_ptr[g] = (int32_t)tiles.size();
-    for (int g = 0; g < G; ++g)
-        if (tile_ptr[g + 1] - tile_ptr[g] > 64) {
-            set_error("pcg: more than 64 tiles per CTA; subdomains too large for this plan");
+    const int used = tiles.empty() ? 0 : pack(hi, &tile_ptr);
+    for (int g = used; g <= G; ++g) tile_ptr[g] = (int32_t)tiles.size();
+    P.est_seconds = tiles.empty() ? 0.0 : hi;
+    // each CTA's tiles as runs of consecutive rows of one block
+    std::vector<int32_t> run_ptr(G + 1, 0);
+    std::vector<GemvRun> runs;
+    for (int g = 0; g < G; ++g) {
+        run_ptr[g] = (int32_t)runs.size();
+        for (int32_t k = tile_ptr[g]; k < tile_ptr[g + 1]; ++k) {
+            const GemvTile& t = tiles[k];
+            const int32_t end = std::min<int32_t>(t.row0 + rows, pc->blocks[t.block].nrows);
+            if ((int32_t)runs.size() > run_ptr[g] && runs.back().block == t.block && runs.back().row_end == t.row0)
+                runs.back().row_end = end;
+            else
+                runs.push_back({t.block, t.row0, end, 0});
+        }
+        if ((int32_t)runs.size() - run_ptr[g] > kMaxRuns) {
+            set_error("pcg: a CTA would stream more than 128 subdomains; too many subdomains for the CTAs");
             return POLYDG_EINVAL;
         }
+    }
+    run_ptr[G] = (int32_t)runs.size();
     if (pc) sub_pairs = pc->sub_pairs;
     std::vector<int32_t> crow_ptr(G + 1);
     for (int g = 0; g <= G; ++g) crow_ptr[g] = (int32_t)((n0 * g) / G);
     int st;
-    if ((st = upload(&P.tile_ptr, tile_ptr)) || (st = upload(&P.tiles, tiles)) ||
+    if ((st = upload(&P.run_ptr, run_ptr)) || (st = upload(&P.runs, runs)) ||
         (st = upload(&P.sub_pairs, sub_pairs)) || (st = upload(&P.elem_ptr, elem_ptr)) ||
         (st = upload(&P.crow_ptr, crow_ptr)) || (st = upload(&P.need_ptr, need_ptr)) ||
         (st = upload(&P.need, need)) || (st = upload(&P.col_local, col_local)) ||
         (st = upload(&P.need_aggl, need_aggl)) || (st = upload(&P.need_agg_ptr, need_agg_ptr)) ||
-        (st = upload(&P.need_agg, need_agg)))
+        (st = upload(&P.need_agg, need_agg)) || (st = upload(&P.cta_chunk, cta_chunk)) ||
+        (st = upload(&P.chunk_elem, chunk_elem)))
         return st;
     int occ = 0;
-    CU(persistent_occupancy(P.dtype, np, P.smem, &occ));
+    CU(persistent_occupancy(P.dtype, np, P.smem, &occ, batched));
     if (occ < 1) { set_error("pcg: the persistent kernel does not fit on an SM"); return POLYDG_ECUDA; }
     return POLYDG_OK;
 }
 
-// Enqueue one persistent PCG solve of K x = b on the vectors of w (internal
-// order; x holds x0).  The scalars in w.sc must hold rtol2, maxit, flexible and done = 0.
-static int run_pcg(polydg_ctx* c, asm_ctx* pc, PcgWork& w, cudaStream_t s) {
-    const Plan& P = pc ? pc->plan : c->id_plan;
+// Arguments of one persistent PCG solve of K x = b on the vectors of w (internal
+// order; x holds x0) under plan P.
+static PersistArgs persist_args(polydg_ctx* c, asm_ctx* pc, const Plan& P, PcgWork& w) {
     const bool coarse = pc && pc->has_coarse;
     PersistArgs a = {};
     a.grid = P.grid;
-    a.rows = P.rows;
+    a.wstages = P.wstages;
     a.identity = pc ? 0 : 1;
     a.n0 = coarse ? (int)pc->n0 : 0;
     a.ld0 = coarse ? (int)pc->ld0 : 0;
     a.nq = coarse ? pc->nq : 1;
     a.nc = c->H.nc;
-    a.buf_bytes = P.buf_bytes;
+    a.slot_bytes = P.slot_bytes;
     a.redundant = P.redundant;
     a.xs_off = P.xs_off;
     a.rp_off = P.rp_off;
-    a.zs_off = P.zs_off;
     a.r0_off = P.r0_off;
     a.y0_off = P.y0_off;
     a.pn_off = P.pn_off;
     a.td_off = P.td_off;
     a.row_ptr = c->K.row_ptr;
     a.val = c->K.val;
+    a.cta_chunk = P.cta_chunk;
+    a.chunk_elem = P.chunk_elem;
     a.need_ptr = P.need_ptr;
     a.need = P.need;
     a.need_aggl = P.need_aggl;
@@ -392,8 +463,8 @@ static int run_pcg(polydg_ctx* c, asm_ctx* pc, PcgWork& w, cudaStream_t s) {
     a.col_local = P.col_local;
     a.elem_ptr = P.elem_ptr;
     a.blocks = pc ? pc->d_blocks : nullptr;
-    a.tiles = P.tiles;
-    a.tile_ptr = P.tile_ptr;
+    a.runs = P.runs;
+    a.run_ptr = P.run_ptr;
     a.sub_pairs = P.sub_pairs;
     a.store = pc ? (P.dtype == 0 ? (const void*)pc->st64 : P.dtype == 1 ? (const void*)pc->st32 : (const void*)pc->st16) : nullptr;
     a.st64 = pc ? pc->st64 : nullptr;
@@ -420,6 +491,14 @@ static int run_pcg(polydg_ctx* c, asm_ctx* pc, PcgWork& w, cudaStream_t s) {
     a.bcast = w.bcast;
     a.gs = w.gs;
     a.err = w.err;
+    return a;
+}
+
+// Enqueue one persistent PCG solve of K x = b on the vectors of w (internal
+// order; x holds x0).  The scalars in w.sc must hold rtol2, maxit, flexible and done = 0.
+static int run_pcg(polydg_ctx* c, asm_ctx* pc, PcgWork& w, cudaStream_t s) {
+    const Plan& P = pc ? pc->plan : c->id_plan;
+    const PersistArgs a = persist_args(c, pc, P, w);
     CU(cudaMemsetAsync(&w.gs->count, 0, sizeof(unsigned), s));
     CU(launch_pcg_persistent(P.dtype, c->H.n_p, a, P.smem, s));
     return POLYDG_OK;
@@ -479,8 +558,14 @@ int polydg_setup(const polydg_mesh* mesh, int p, const int32_t* subdomain_of_cel
         (st = upload(&c->d_zero_ptr, zero_ptr)) ||
         (st = upload(&c->d_to_caller, H.to_caller)) || (st = upload(&c->d_node_ptr, H.node_ptr)) ||
         (st = upload(&c->d_node_w, H.node_w)) || (st = upload(&c->d_node_phi, H.node_phi)) ||
-        (st = upload(&c->d_node_pos, H.node_to_caller_pos)))
+        (st = upload(&c->d_node_pos, H.node_to_caller_pos)) ||
+        (st = upload(&c->d_to_internal, H.to_internal)))
         return fail(st);
+    {
+        std::vector<double> diam(H.nc);
+        for (int64_t e = 0; e < H.nc; ++e) diam[e] = H.diam[H.to_caller[e]];
+        if ((st = upload(&c->d_diam, diam))) return fail(st);
+    }
     if ((st = c->work.alloc(H.nc * H.n_p))) return fail(st);
     if (cudaMallocHost((void**)&c->h_sc, sizeof(PcgScalars)) != cudaSuccess) {
         set_error("polydg_setup: pinned allocation failed");
@@ -491,7 +576,7 @@ int polydg_setup(const polydg_mesh* mesh, int p, const int32_t* subdomain_of_cel
         set_error("polydg_setup: cannot query the SM count");
         return fail(POLYDG_ECUDA);
     }
-    if ((st = build_plan(c, nullptr, c->id_plan))) return fail(st);
+    if ((st = build_plan(c, nullptr, c->n_sm, c->id_plan))) return fail(st);
     *out = c;
     return POLYDG_OK;
 }
@@ -746,7 +831,7 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
         (st = dalloc(&pc->d_err, 1)))
         return fail(st);
     if ((st = cu(cudaMemset(pc->d_err, 0, sizeof(int)), "memset"))) return fail(st);
-    if ((st = build_plan(c, pc, pc->plan))) return fail(st);
+    if ((st = build_plan(c, pc, c->n_sm, pc->plan))) return fail(st);
     *out = pc;
     return POLYDG_OK;
 }
@@ -766,7 +851,7 @@ int asm_get_info(const asm_ctx* pc, asm_info* out) {
     out->n_coarse = (int32_t)pc->n0;
     out->precision = pc->precision;
     out->grid = pc->plan.grid;
-    out->rows_per_tile = pc->plan.rows;
+    out->rows_per_tile = 1;                 // each bulk copy carries one row
     out->pad = 0;
     return POLYDG_OK;
 }
@@ -855,6 +940,7 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
     const int64_t n = H.nc * np, nn = (int64_t)H.node_w.size();
     int st;
     if ((st = sm->work.alloc(n)) || (st = dalloc(&sm->U, n)) || (st = dalloc(&sm->Uprev, n)) ||
+        (st = dalloc(&sm->Uprev2, n)) || (st = dalloc(&sm->xg, n)) ||
         (st = dalloc(&sm->I, n)) || (st = dalloc(&sm->y, 5 * nn)) || (st = dalloc(&sm->d_y0, 5)) ||
         (st = dalloc(&sm->d_ss, 1)))
         return fail(st);
@@ -888,6 +974,7 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
     sc.flexible = prm->flexible ? 1 : 0;
     if ((st = cu(cudaMemcpy(sm->U, U0.data(), n * sizeof(double), cudaMemcpyHostToDevice))) ||
         (st = cu(cudaMemcpy(sm->Uprev, U0.data(), n * sizeof(double), cudaMemcpyHostToDevice))) ||
+        (st = cu(cudaMemcpy(sm->Uprev2, U0.data(), n * sizeof(double), cudaMemcpyHostToDevice))) ||
         (st = cu(cudaMemcpy(sm->d_y0, y0, 5 * sizeof(double), cudaMemcpyHostToDevice))) ||
         (st = cu(launch_init_y(sm->y, nn, sm->d_y0, 0))) ||
         (st = cu(cudaMemcpy(sm->d_ss, &ss, sizeof(ss), cudaMemcpyHostToDevice))) ||
@@ -901,9 +988,24 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
 
 }  // extern "C"
 namespace polydg {
-// One Crank-Nicolson step (Eq. fully-discrete-1): ionic update at the nodes and
-// the ion-current load, right-hand side, x0 = U^k, PCG solve, rotation of U.
-static int enqueue_step(sim_ctx* sm, cudaStream_t s, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+// The parts of one Crank-Nicolson step (Eq. fully-discrete-1) before and after
+// its PCG solve: ionic update at the nodes and the ion-current load,
+// right-hand side, x0 = U^k; then the rotation of U and the step statistics.
+static GuessFeat guess_features(const polydg_ctx* c, const guess_model* g) {
+    GuessFeat f;
+    f.row_ptr = c->K.row_ptr;
+    f.col = c->K.col;
+    f.diam = c->d_diam;
+    f.u_rest = g->scales[0];
+    f.s_u = g->scales[1];
+    f.s_d = g->scales[2];
+    f.h_ref = g->scales[3];
+    f.dt_ref = g->scales[4];
+    f.dt = c->H.dt;
+    return f;
+}
+
+static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
     polydg_ctx* c = sm->ctx;
     const HostSetup& H = c->H;
     const int np = H.n_p;
@@ -915,12 +1017,67 @@ static int enqueue_step(sim_ctx* sm, cudaStream_t s, cudaEvent_t ev_begin, cudaE
                     H.nc, dt, sm->I, sm->d_ss, s));
     CU(launch_matvec(MODE_RHS, np, c->K, c->K.val_minus, sm->U, w.b, sm->I, sm->F, -H.chi_cm * dt,
                      dt, nullptr, nullptr, sm->d_ss, dt, sm->prm.stim_duration, nullptr, nullptr, s));
-    CU(launch_copy(sm->U, w.x[0], n, sm->d_ss, s));
-    if (ev_begin) CU(cudaEventRecord(ev_begin, s));
-    if (int st = run_pcg(c, sm->pc, w, s)) return st;
-    if (ev_end) CU(cudaEventRecord(ev_end, s));
-    CU(launch_step_finish(sm->U, sm->Uprev, w.x[0], w.x[1], n, w.sc, sm->d_ss, s));
+    if (sm->guess) {            // from k = 2 on: learned proposal, kept if its residual is smaller
+        const GuessFeat f = guess_features(c, sm->guess);
+        CU(launch_guess_propose(np, f, sm->guess->w16, sm->U, sm->Uprev, sm->Uprev2, sm->xg, H.nc,
+                                sm->d_ss, s));
+        CU(launch_guess_select(np, c->K, w.b, sm->xg, sm->U, w.partials, sm->d_ss, sm->guess_policy, s));
+        CU(launch_select_copy(sm->U, sm->xg, w.x[0], n, sm->d_ss, s));
+    } else {
+        CU(launch_copy(sm->U, w.x[0], n, sm->d_ss, s));
+    }
     return POLYDG_OK;
+}
+
+static int enqueue_step_post(sim_ctx* sm, cudaStream_t s) {
+    const int64_t n = sm->ctx->H.nc * sm->ctx->H.n_p;
+    PcgWork& w = sm->work;
+    CU(launch_step_finish(sm->U, sm->Uprev, sm->Uprev2, w.x[0], w.x[1], n, w.sc, sm->d_ss, s));
+    return POLYDG_OK;
+}
+
+static int enqueue_step(sim_ctx* sm, cudaStream_t s, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+    if (int st = enqueue_step_pre(sm, s)) return st;
+    if (ev_begin) CU(cudaEventRecord(ev_begin, s));
+    if (int st = run_pcg(sm->ctx, sm->pc, sm->work, s)) return st;
+    if (ev_end) CU(cudaEventRecord(ev_end, s));
+    return enqueue_step_post(sm, s);
+}
+
+// One step of every simulation of a batch: the per-simulation kernels before the
+// solves, one batched persistent launch for all solves, the kernels after.
+static int enqueue_batch_step(batch_ctx* bt, cudaStream_t s) {
+    for (sim_ctx* sm : bt->sims) {
+        if (int st = enqueue_step_pre(sm, s)) return st;
+        CU(cudaMemsetAsync(&sm->work.gs->count, 0, sizeof(unsigned), s));
+    }
+    CU(launch_pcg_batched(bt->dtype, bt->np, bt->d_args, bt->d_map, bt->n_cta, bt->smem, s));
+    for (sim_ctx* sm : bt->sims)
+        if (int st = enqueue_step_post(sm, s)) return st;
+    return POLYDG_OK;
+}
+
+// Zero the per-call counters of a simulation's scalars (host copy h).
+static int reset_step_counters(sim_ctx* sm, SimScalars& h, cudaStream_t s) {
+    CU(cudaMemcpyAsync(&h, sm->d_ss, sizeof(SimScalars), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    h.steps_done = 0;
+    h.total_its = 0;
+    h.max_its = 0;
+    h.last_relres = 0.0;
+    h.guesses_taken = 0;
+    CU(cudaMemcpyAsync(sm->d_ss, &h, sizeof(SimScalars), cudaMemcpyHostToDevice, s));
+    return POLYDG_OK;
+}
+
+static void fill_stats(const SimScalars& h, double seconds, step_stats* st) {
+    st->steps_done = h.steps_done;
+    st->total_iterations = h.total_its;
+    st->max_iterations = h.max_its;
+    st->status = h.status;
+    st->last_relres = h.last_relres;
+    st->pcg_seconds = seconds;
+    st->guesses_taken = h.guesses_taken;
 }
 }  // namespace polydg
 
@@ -931,13 +1088,7 @@ int monodomain_step(sim_ctx* sm, int nsteps, void* stream, step_stats* stats) {
     if (nsteps < 0) { set_error("monodomain_step: nsteps < 0"); return POLYDG_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     SimScalars& h = *sm->h_ss;
-    CU(cudaMemcpyAsync(&h, sm->d_ss, sizeof(SimScalars), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    h.steps_done = 0;
-    h.total_its = 0;
-    h.max_its = 0;
-    h.last_relres = 0.0;
-    CU(cudaMemcpyAsync(sm->d_ss, &h, sizeof(SimScalars), cudaMemcpyHostToDevice, s));
+    if (int st = reset_step_counters(sm, h, s)) return st;
     while ((int)sm->ev.size() < 2 * nsteps) {
         cudaEvent_t e;
         CU(cudaEventCreate(&e));
@@ -949,17 +1100,12 @@ int monodomain_step(sim_ctx* sm, int nsteps, void* stream, step_stats* stats) {
     CU(cudaStreamSynchronize(s));
     sm->k = h.k;
     if (stats) {
-        stats->steps_done = h.steps_done;
-        stats->total_iterations = h.total_its;
-        stats->max_iterations = h.max_its;
-        stats->status = h.status;
-        stats->last_relres = h.last_relres;
         double sec = 0.0;
         for (int i = 0; i < nsteps; ++i) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, sm->ev[2 * i], sm->ev[2 * i + 1]) == cudaSuccess) sec += 1e-3 * ms;
         }
-        stats->pcg_seconds = sec;
+        fill_stats(h, sec, stats);
     }
     if (h.status != 0) set_error("monodomain_step: a step's PCG solve failed");
     return h.status;
@@ -981,16 +1127,306 @@ int sim_set_potential(sim_ctx* sm, const double* u_dev, const double* uprev_dev,
     CU(launch_permute(u_dev, nullptr, sm->U, c->d_to_caller, c->H.nc, c->H.n_p, 1, nullptr, s));
     CU(launch_permute(uprev_dev ? uprev_dev : u_dev, nullptr, sm->Uprev, c->d_to_caller, c->H.nc,
                       c->H.n_p, 1, nullptr, s));
+    CU(cudaMemcpyAsync(sm->Uprev2, sm->Uprev, c->H.nc * c->H.n_p * sizeof(double),
+                       cudaMemcpyDeviceToDevice, s));
     return POLYDG_OK;
 }
 
 int64_t sim_step_index(const sim_ctx* sm) { return sm ? sm->k : -1; }
 
+int batch_create(sim_ctx* const* sims, int n, batch_ctx** out) {
+    if (!sims || n < 1 || !out) { set_error("batch_create: need n >= 1 simulations and an output pointer"); return POLYDG_EINVAL; }
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!sims[i] || !sims[i]->pc) { set_error("batch_create: every simulation needs a preconditioner"); return POLYDG_EINVAL; }
+        const sim_ctx* a = sims[i];
+        const sim_ctx* b = sims[0];
+        if (a->ctx->device != b->ctx->device || a->ctx->H.n_p != b->ctx->H.n_p ||
+            a->pc->precision != b->pc->precision) {
+            set_error("batch_create: simulations must share the device, the degree and the local precision");
+            return POLYDG_EINVAL;
+        }
+        for (int j = 0; j < i; ++j)
+            if (sims[j] == a || sims[j]->pc == a->pc) {
+                set_error("batch_create: simulations must be distinct and have their own preconditioners");
+                return POLYDG_EINVAL;
+            }
+    }
+    const int n_cta = sims[0]->ctx->n_sm;
+    if (n > n_cta) { set_error("batch_create: more simulations than SMs"); return POLYDG_EINVAL; }
+    batch_ctx* bt = new batch_ctx();
+    bt->sims.assign(sims, sims + n);
+    bt->n_cta = n_cta;
+    bt->dtype = sims[0]->pc->precision;
+    bt->np = sims[0]->ctx->H.n_p;
+    bt->device = sims[0]->ctx->device;
+    auto fail = [&](int code) { batch_destroy(bt); return code; };
+    // CTAs per simulation: minimise the largest per-CTA share of the bytes one
+    // iteration streams (local inverses + K_h), one CTA at a time to the
+    // simulation whose share is largest
+    std::vector<double> cost(n);
+    for (int i = 0; i < n; ++i) {
+        const sim_ctx* sm = sims[i];
+        const int np = sm->ctx->H.n_p;
+        cost[i] = (double)sm->pc->store_bytes + 8.0 * np * np * (double)sm->ctx->K.nblk +
+                  96.0 * (double)(sm->ctx->H.nc * np);
+    }
+    bt->group.assign(n, 1);
+    for (int k = n; k < n_cta; ++k) {
+        int best = 0;
+        for (int i = 1; i < n; ++i)
+            if (cost[i] / bt->group[i] > cost[best] / bt->group[best]) best = i;
+        ++bt->group[best];
+    }
+    bt->plans.resize(n);
+    std::vector<PersistArgs> args(n);
+    std::vector<int2> map;
+    for (int i = 0; i < n; ++i) {
+        sim_ctx* sm = sims[i];
+        if (int st = build_plan(sm->ctx, sm->pc, bt->group[i], bt->plans[i], 1)) return fail(st);
+        bt->smem = std::max(bt->smem, bt->plans[i].smem);
+        args[i] = persist_args(sm->ctx, sm->pc, bt->plans[i], sm->work);
+        for (int j = 0; j < bt->group[i]; ++j) map.push_back(make_int2(i, j));
+    }
+    int occ = 0;
+    if (persistent_occupancy(bt->dtype, bt->np, bt->smem, &occ, 1) != cudaSuccess || occ < 1) {
+        set_error("batch_create: the batched kernel does not fit on an SM");
+        return fail(POLYDG_ECUDA);
+    }
+    int st;
+    if ((st = upload(&bt->d_args, args))) return fail(st);
+    std::vector<int2> mp(map.begin(), map.end());
+    if ((st = dalloc(&bt->d_map, mp.size()))) return fail(st);
+    if (cudaMemcpy(bt->d_map, mp.data(), mp.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost((void**)&bt->h_ss, n * sizeof(SimScalars)) != cudaSuccess) {
+        set_error("batch_create: CUDA setup failed");
+        return fail(POLYDG_ECUDA);
+    }
+    *out = bt;
+    return POLYDG_OK;
+}
+
+int batch_get_groups(const batch_ctx* bt, int32_t* ctas_of_sim) {
+    if (!bt || !ctas_of_sim) { set_error("batch_get_groups: null argument"); return POLYDG_EINVAL; }
+    for (size_t i = 0; i < bt->group.size(); ++i) ctas_of_sim[i] = bt->group[i];
+    return POLYDG_OK;
+}
+
+int batch_step(batch_ctx* bt, int nsteps, void* stream, step_stats* per_sim, double* seconds) {
+    if (!bt) { set_error("batch_step: null batch"); return POLYDG_EINVAL; }
+    if (nsteps < 0) { set_error("batch_step: nsteps < 0"); return POLYDG_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)bt->sims.size();
+    for (int i = 0; i < n; ++i)
+        if (int st = reset_step_counters(bt->sims[i], bt->h_ss[i], s)) return st;
+    bool stale = !bt->exec;
+    for (int i = 0; i < n && !stale; ++i) stale = bt->versions[i] != bt->sims[i]->version;
+    if (stale) {                        // (re)capture one step of all simulations
+        if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
+        if (bt->graph) { cudaGraphDestroy(bt->graph); bt->graph = nullptr; }
+        bt->versions.resize(n);
+        for (int i = 0; i < n; ++i) bt->versions[i] = bt->sims[i]->version;
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal));
+        const int st = enqueue_batch_step(bt, bt->cap);
+        const cudaError_t e = cudaStreamEndCapture(bt->cap, &g);
+        if (st || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (!st) set_error(std::string("batch_step: graph capture failed: ") + cudaGetErrorString(e));
+            return st ? st : POLYDG_ECUDA;
+        }
+        bt->graph = g;
+        CU(cudaGraphInstantiate(&bt->exec, g, 0));
+    }
+    while ((int)bt->ev.size() < 2 * nsteps) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        bt->ev.push_back(e);
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        CU(cudaEventRecord(bt->ev[2 * k], s));
+        CU(cudaGraphLaunch(bt->exec, s));
+        CU(cudaEventRecord(bt->ev[2 * k + 1], s));
+    }
+    for (int i = 0; i < n; ++i)
+        CU(cudaMemcpyAsync(&bt->h_ss[i], bt->sims[i]->d_ss, sizeof(SimScalars), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    double sec = 0.0;
+    for (int k = 0; k < nsteps; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, bt->ev[2 * k], bt->ev[2 * k + 1]) == cudaSuccess) sec += 1e-3 * ms;
+    }
+    if (seconds) *seconds = sec;
+    int status = POLYDG_OK;
+    for (int i = 0; i < n; ++i) {
+        bt->sims[i]->k = bt->h_ss[i].k;
+        if (per_sim) fill_stats(bt->h_ss[i], sec, &per_sim[i]);
+        if (status == POLYDG_OK && bt->h_ss[i].status != 0) status = bt->h_ss[i].status;
+    }
+    if (status != POLYDG_OK) set_error("batch_step: a simulation's PCG solve failed");
+    return status;
+}
+
+// the training kernel's shared-memory image of the network fits for n_p <= 10 (p <= 3)
+static bool valid_np(int np) { return np == 3 || np == 6 || np == 10; }
+
+int guess_n_params(int n_p) {
+    if (!valid_np(n_p)) { set_error("guess_n_params: n_p must be 3, 6 or 10"); return POLYDG_EINVAL; }
+    return guess_param_count(n_p);
+}
+
+int guess_create(int n_p, const double* params, const double* scales, guess_model** out) {
+    if (!out || !params || !valid_np(n_p)) {
+        set_error("guess_create: need n_p in {3, 6, 10}, parameters and an output pointer");
+        return POLYDG_EINVAL;
+    }
+    *out = nullptr;
+    guess_model* g = new guess_model();
+    auto fail = [&](int code) { guess_destroy(g); return code; };
+    g->np = n_p;
+    g->P = guess_param_count(n_p);
+    if (scales) {
+        if (!(scales[1] > 0) || !(scales[2] > 0) || !(scales[3] > 0) || !(scales[4] > 0)) {
+            set_error("guess_create: the scales s_u, s_d, h_ref, dt_ref must be > 0");
+            return fail(POLYDG_EINVAL);
+        }
+        for (int k = 0; k < 5; ++k) g->scales[k] = scales[k];
+    }
+    if (cudaGetDevice(&g->device) != cudaSuccess) { set_error("guess_create: no CUDA device"); return fail(POLYDG_ECUDA); }
+    int n_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, g->device);
+    g->grid_max = std::max(1, 2 * n_sm);
+    std::vector<float> w(g->P);
+    for (int k = 0; k < g->P; ++k) w[k] = (float)params[k];
+    int st;
+    if ((st = upload(&g->w32, w)) || (st = dalloc(&g->m, g->P)) || (st = dalloc(&g->v, g->P)) ||
+        (st = dalloc(&g->w16, g->P)) || (st = dalloc(&g->part, (size_t)g->grid_max * g->P)) ||
+        (st = dalloc(&g->lpart, g->grid_max)) || (st = dalloc(&g->loss, 1)))
+        return fail(st);
+    CU(cudaMemset(g->m, 0, g->P * sizeof(float)));
+    CU(cudaMemset(g->v, 0, g->P * sizeof(float)));
+    CU(guess_prepare(n_p));
+    CU(launch_to_half(g->w32, g->w16, g->P, 0));
+    CU(cudaDeviceSynchronize());
+    *out = g;
+    return POLYDG_OK;
+}
+
+int guess_get_params(const guess_model* g, double* params, double* adam_m, double* adam_v,
+                     int64_t* adam_t) {
+    if (!g) { set_error("guess_get_params: null model"); return POLYDG_EINVAL; }
+    std::vector<float> h(g->P);
+    const float* src[3] = {g->w32, g->m, g->v};
+    double* dst[3] = {params, adam_m, adam_v};
+    for (int k = 0; k < 3; ++k) {
+        if (!dst[k]) continue;
+        CU(cudaMemcpy(h.data(), src[k], g->P * sizeof(float), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < g->P; ++i) dst[k][i] = h[i];
+    }
+    if (adam_t) *adam_t = g->t;
+    return POLYDG_OK;
+}
+
+int guess_set_scales(guess_model* g, const double* scales) {
+    if (!g || !scales || !(scales[1] > 0) || !(scales[2] > 0) || !(scales[3] > 0) || !(scales[4] > 0)) {
+        set_error("guess_set_scales: need a model and scales with s_u, s_d, h_ref, dt_ref > 0");
+        return POLYDG_EINVAL;
+    }
+    for (int k = 0; k < 5; ++k) g->scales[k] = scales[k];
+    return POLYDG_OK;
+}
+
+int guess_propose(guess_model* g, polydg_ctx* c, const double* uk, const double* uk1,
+                  const double* uk2, double* x_dev, void* stream) {
+    if (!g || !c || !uk || !uk1 || !uk2 || !x_dev) { set_error("guess_propose: null argument"); return POLYDG_EINVAL; }
+    if (g->np != c->H.n_p) { set_error("guess_propose: model and mesh differ in n_p"); return POLYDG_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = c->H.n_p;
+    PcgWork& w = c->work;
+    CU(launch_permute(uk, nullptr, w.r[0], c->d_to_caller, c->H.nc, np, 1, nullptr, s));
+    CU(launch_permute(uk1, nullptr, w.r[1], c->d_to_caller, c->H.nc, np, 1, nullptr, s));
+    CU(launch_permute(uk2, nullptr, w.b, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
+    CU(launch_guess_propose(np, guess_features(c, g), g->w16, w.r[0], w.r[1], w.b, w.z, c->H.nc,
+                            nullptr, s));
+    CU(launch_permute(w.z, nullptr, x_dev, c->d_to_caller, c->H.nc, np, 0, nullptr, s));
+    return POLYDG_OK;
+}
+
+int guess_train_step(guess_model* g, polydg_ctx* c, const double* traj_dev, int64_t n_states,
+                     const int64_t* samples, int64_t n_samples, double lr, double* loss,
+                     void* stream) {
+    if (!g || !c || !traj_dev || !samples || n_samples < 1 || !(lr >= 0)) {
+        set_error("guess_train_step: need a model, a context, a trajectory, samples and lr >= 0");
+        return POLYDG_EINVAL;
+    }
+    if (g->np != c->H.n_p) { set_error("guess_train_step: model and mesh differ in n_p"); return POLYDG_EINVAL; }
+    for (int64_t q = 0; q < n_samples; ++q)
+        if (samples[2 * q] < 2 || samples[2 * q] > n_states - 2 || samples[2 * q + 1] < 0 ||
+            samples[2 * q + 1] >= c->H.nc) {
+            set_error("guess_train_step: a sample needs 2 <= k <= n_states - 2 and a valid cell id");
+            return POLYDG_EINVAL;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_samples > g->sample_cap) {
+        dfree(g->samples);
+        if (int st = dalloc(&g->samples, 2 * (size_t)n_samples)) return st;
+        g->sample_cap = n_samples;
+    }
+    CU(cudaMemcpyAsync(g->samples, samples, 2 * n_samples * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    const int64_t tiles = (n_samples + 31) / 32;
+    const int grid = (int)std::min<int64_t>(tiles, g->grid_max);
+    const int np = c->H.n_p;
+    CU(launch_guess_train(np, guess_features(c, g), g->w32, traj_dev, c->H.nc * np, g->samples,
+                          n_samples, c->d_to_internal, c->d_to_caller, g->part, g->lpart, grid, s));
+    g->t += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 - std::pow(b1, (double)g->t)), c2 = (float)(1.0 - std::pow(b2, (double)g->t));
+    CU(launch_guess_adam(g->part, grid, g->P, g->w32, g->m, g->v, g->w16, (float)lr, (float)b1, (float)b2,
+                         1e-8f, c1, c2, g->lpart, 1.0 / ((double)n_samples * np), g->loss, s));
+    double l = 0.0;
+    CU(cudaMemcpyAsync(&l, g->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (loss) *loss = l;
+    return POLYDG_OK;
+}
+
+int sim_set_guess(sim_ctx* sm, guess_model* g, int policy) {
+    if (!sm) { set_error("sim_set_guess: null simulation"); return POLYDG_EINVAL; }
+    if (g && g->np != sm->ctx->H.n_p) { set_error("sim_set_guess: model and mesh differ in n_p"); return POLYDG_EINVAL; }
+    if (policy != 0 && policy != 1) { set_error("sim_set_guess: policy must be 0 or 1"); return POLYDG_EINVAL; }
+    if (sm->guess != g || sm->guess_policy != policy) {
+        sm->guess = g;
+        sm->guess_policy = policy;
+        sm->version += 1;
+    }
+    return POLYDG_OK;
+}
+
+void guess_destroy(guess_model* g) {
+    if (!g) return;
+    dfree(g->w32); dfree(g->m); dfree(g->v); dfree(g->w16); dfree(g->part); dfree(g->lpart);
+    dfree(g->loss); dfree(g->samples);
+    delete g;
+}
+
+void batch_destroy(batch_ctx* bt) {
+    if (!bt) return;
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    if (bt->cap) cudaStreamDestroy(bt->cap);
+    for (auto e : bt->ev) cudaEventDestroy(e);
+    for (auto& P : bt->plans) P.release();
+    dfree(bt->d_args); dfree(bt->d_map);
+    if (bt->h_ss) cudaFreeHost(bt->h_ss);
+    delete bt;
+}
+
 void sim_destroy(sim_ctx* sm) {
     if (!sm) return;
     for (auto e : sm->ev) cudaEventDestroy(e);
     sm->work.release();
-    dfree(sm->U); dfree(sm->Uprev); dfree(sm->I); dfree(sm->F); dfree(sm->y); dfree(sm->d_y0);
+    dfree(sm->U); dfree(sm->Uprev); dfree(sm->Uprev2); dfree(sm->xg); dfree(sm->I); dfree(sm->F); dfree(sm->y); dfree(sm->d_y0);
     dfree(sm->d_ss);
     if (sm->h_ss) cudaFreeHost(sm->h_ss);
     delete sm;
@@ -1011,7 +1447,7 @@ void polydg_destroy(polydg_ctx* c) {
     c->work.release();
     dfree(c->K.row_ptr); dfree(c->K.col); dfree(c->K.val); dfree(c->K.val_minus);
     dfree(c->d_to_caller); dfree(c->d_node_ptr); dfree(c->d_node_w); dfree(c->d_node_phi);
-    dfree(c->d_node_pos); dfree(c->d_id_blocks); dfree(c->d_id_tiles); dfree(c->d_zero_ptr);
+    dfree(c->d_node_pos); dfree(c->d_to_internal); dfree(c->d_diam); dfree(c->d_id_blocks); dfree(c->d_id_tiles); dfree(c->d_zero_ptr);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     delete c;
 }

@@ -63,6 +63,14 @@ struct GemvTile {
     int32_t row0;
 };
 
+// Rows [row_begin, row_end) of one LOCAL block, streamed by one CTA of the
+// persistent PCG kernel in tiles of `rows` rows.
+struct GemvRun {
+    int32_t block;
+    int32_t row_begin, row_end;
+    int32_t pad;
+};
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

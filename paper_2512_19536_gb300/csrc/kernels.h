@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "device.cuh"
 
@@ -19,8 +20,11 @@ struct SimScalars {
     int64_t steps_done;
     int64_t total_its;
     int32_t status;
-    int32_t pad;
+    int32_t use_guess;     // this step's PCG starts from the learned guess
     double last_relres;
+    int64_t guesses_taken; // steps (of this call) that started from the learned guess
+    uint32_t guess_ticket; // last-CTA ticket of the guess selection
+    uint32_t pad;
 };
 
 // Block-sparse K_h on the device (internal cell order).
@@ -75,16 +79,19 @@ struct GridSync {
 // Arguments of the persistent PCG kernel (kernels_pcg.cu).  Per-CTA work lists
 // are CSR arrays indexed by blockIdx.x.
 struct PersistArgs {
-    int grid, rows, identity, n0, ld0, nq, redundant;
+    int grid, wstages, identity, n0, ld0, nq, redundant;
     int64_t nc;
-    // shared-memory carve-up (byte offsets)
-    size_t buf_bytes, xs_off, rp_off, zs_off, r0_off, y0_off, pn_off, td_off;
-    // K_h (column-major blocks) and the per-CTA matvec plan: the elements whose
-    // z the CTA needs (its own range first, then face neighbours), their
-    // agglomerates, and per block of K_h the CTA-local index of its column element
+    // shared-memory carve-up (byte offsets): wstages copy slots of slot_bytes per warp
+    size_t slot_bytes, xs_off, rp_off, r0_off, y0_off, pn_off, td_off;
+    // K_h (column-major blocks) and the per-CTA matvec plan.  Each CTA's elements
+    // are cut into chunks; per chunk the elements whose z it needs (its own range
+    // first, then face neighbours) and their agglomerates, and per block of K_h the
+    // chunk-local index of its column element
     const int32_t* row_ptr;
     const double* val;
-    const int32_t* need_ptr;                   // [grid + 1]
+    const int32_t* cta_chunk;                  // [grid + 1] chunks of each CTA
+    const int64_t* chunk_elem;                 // [n_chunks + 1] element range of each chunk
+    const int32_t* need_ptr;                   // [n_chunks + 1]
     const int32_t* need;
     const int32_t* need_aggl;                  // per needed element: index into need_agg
     const int32_t* need_agg_ptr;               // [grid + 1]
@@ -93,8 +100,8 @@ struct PersistArgs {
     const int64_t* elem_ptr;                   // [grid + 1] own element ranges
     // preconditioner
     const GemvBlock* blocks;
-    const GemvTile* tiles;
-    const int32_t* tile_ptr;                   // [grid + 1]
+    const GemvRun* runs;                       // LOCAL row ranges streamed by each CTA
+    const int32_t* run_ptr;                    // [grid + 1]
     const int32_t* sub_pairs;                  // RESTRICT block ids grouped by subdomain
     const void* store;                         // store of the local inverses (dtype)
     const double* st64;                        // fp64 store (restriction rows)
@@ -118,11 +125,16 @@ struct PersistArgs {
     int* err;
 };
 
-constexpr int kStages = 3;                     // bulk-copy pipeline depth of the P phase
+constexpr int kMaxWarpStages = 4;              // copy slots per warp in the P phase
 
 cudaError_t launch_pcg_persistent(int dtype, int np, const PersistArgs& a, size_t smem,
                                   cudaStream_t s);
-cudaError_t persistent_occupancy(int dtype, int np, size_t smem, int* blocks_per_sm);
+// Several independent solves in one cooperative launch of n_cta CTAs: CTA b runs
+// as CTA map[b].y of the map[b].x-th solve, whose arguments are args[map[b].x]
+// (device arrays; args[i].grid = the CTAs mapped to solve i).
+cudaError_t launch_pcg_batched(int dtype, int np, const PersistArgs* args_dev, const int2* map_dev,
+                               int n_cta, size_t smem, cudaStream_t s);
+cudaError_t persistent_occupancy(int dtype, int np, size_t smem, int* blocks_per_sm, int batched);
 
 cudaError_t launch_matvec(int mode, int np, const DeviceMatrix& K, const double* val,
                           const double* x, double* y, const double* v1, const double* v2,
@@ -151,15 +163,46 @@ cudaError_t launch_chol_inverse(double* store, const int64_t* mat_off, const int
 cudaError_t launch_cast_store(const double* src, float* d32, __nv_bfloat16* d16, int64_t n,
                               cudaStream_t s);
 
+// Learned initial guess (kernels_guess.cu).  Features read K_h's block structure
+// (face neighbours), the cell diameters and the scales below.
+constexpr int kGuessHidden = 128;
+struct GuessFeat {
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const double* diam;        // [nc] internal order
+    double u_rest, s_u, s_d, h_ref, dt_ref, dt;
+};
+int guess_param_count(int np);
+size_t guess_propose_smem(int np);
+size_t guess_train_smem(int np);
+cudaError_t guess_prepare(int np);
+cudaError_t launch_guess_propose(int np, const GuessFeat& f, const __half* w16, const double* Uk,
+                                 const double* Uk1, const double* Uk2, double* xg, int64_t nc,
+                                 const SimScalars* ss, cudaStream_t s);
+cudaError_t launch_guess_select(int np, const DeviceMatrix& K, const double* b, const double* xg,
+                                const double* uk, double* partials, SimScalars* ss, int always,
+                                cudaStream_t s);
+cudaError_t launch_select_copy(const double* uk, const double* xg, double* x0, int64_t n,
+                               const SimScalars* ss, cudaStream_t s);
+cudaError_t launch_guess_train(int np, const GuessFeat& f, const float* w32, const double* traj,
+                               int64_t n_dofs, const int64_t* samples, int64_t n_samples,
+                               const int64_t* to_internal, const int64_t* to_caller, float* part,
+                               double* lpart, int grid, cudaStream_t s);
+cudaError_t launch_guess_adam(const float* part, int ncta, int P, float* w32, float* m, float* v,
+                              __half* w16, float lr, float b1, float b2, float eps, float c1, float c2,
+                              const double* lpart, double inv_count, double* loss, cudaStream_t s);
+cudaError_t launch_to_half(const float* w32, __half* w16, int P, cudaStream_t s);
+
 // Ionic update + ion-current load (Eq. fully-discrete-1).
 cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int64_t* node_ptr,
                          const double* node_w, const double* node_phi, double* y, int64_t nn,
                          int64_t nc, double dt, double* I, const SimScalars* ss, cudaStream_t s);
 cudaError_t launch_node_gather(const double* y_int, double* y_caller,
                                const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s);
-cudaError_t launch_step_finish(double* U, double* Uprev, const double* x0, const double* x1,
-                               int64_t n, const PcgScalars* sc, SimScalars* ss, cudaStream_t s);
-cudaError_t launch_step_begin(PcgScalars* sc, const SimScalars* ss, cudaStream_t s);
+cudaError_t launch_step_finish(double* U, double* Uprev, double* Uprev2, const double* x0,
+                               const double* x1, int64_t n, const PcgScalars* sc, SimScalars* ss,
+                               cudaStream_t s);
+cudaError_t launch_step_begin(PcgScalars* sc, SimScalars* ss, cudaStream_t s);
 cudaError_t launch_init_y(double* y, int64_t nn, const double* y0, cudaStream_t s);
 
 }  // namespace polydg

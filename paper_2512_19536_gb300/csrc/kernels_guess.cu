@@ -1,0 +1,526 @@
+// Learned PCG initial guess: per-element network, its training, and the safeguard.
+//
+// Features of element e from the last three solutions (own values, elementwise mean and
+// max over the face neighbours, cell size, time step, neighbour count: 9 n_p + 3 inputs),
+// two ReLU hidden layers of width kGuessHidden, a linear output of n_p values o; the
+// proposal is x0 = U^k + s_d o, kept only if |b - K x0|_2 < |b - K U^k|_2.  Training
+// minimises the mean squared error to (U^{k+1} - U^k) / s_d with Adam.
+//
+// Inference: fp16 weights staged in shared memory, fp32 activations and accumulation.
+// Training: fp32 weights (master copy), activations and gradients; per-CTA partial
+// gradients summed in CTA order (deterministic), then one Adam update per parameter.
+#include <algorithm>
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace polydg {
+
+constexpr int kGT = 32;                   // elements (samples) per tile
+constexpr int kGThreads = 256;
+constexpr int kH = kGuessHidden;          // 128
+constexpr int kHP = kH + 1;               // padded row stride of transposed weights
+
+__host__ __device__ constexpr int guess_inputs(int np) { return 9 * np + 3; }
+
+// Offsets of the parameter groups in the flat (canonical) layout.
+struct ParamOffsets {
+    int w1, b1, w2, b2, w3, b3, total;
+};
+__host__ __device__ inline ParamOffsets param_offsets(int np) {
+    const int F = guess_inputs(np);
+    ParamOffsets o;
+    o.w1 = 0;
+    o.b1 = o.w1 + kH * F;
+    o.w2 = o.b1 + kH;
+    o.b2 = o.w2 + kH * kH;
+    o.w3 = o.b2 + kH;
+    o.b3 = o.w3 + np * kH;
+    o.total = o.b3 + np;
+    return o;
+}
+
+int guess_param_count(int np) { return param_offsets(np).total; }
+
+// Shared-memory image of the weights: transposed, rows padded to kHP (conflict-free
+// both for the forward pass, thread j reading W[j][i], and the backward pass, thread i
+// reading W[j][i]):  W1t[i * kHP + j] = W1[j][i] (i < F),  W2t[i * kHP + j] = W2[j][i],
+// W3t[i * n_p + c] = W3[c][i]; biases as is.
+__host__ __device__ inline size_t guess_weights_bytes16(int np) {
+    const int F = guess_inputs(np);
+    return ((size_t)(F * kHP + kH * kHP + kH * np) * 2 + 15) / 16 * 16;
+}
+
+template <typename W, typename S>
+__device__ __forceinline__ void stage_weights(const S* __restrict__ src, int np, W* w1t, W* w2t, W* w3t,
+                                              float* b1, float* b2, float* b3) {
+    const ParamOffsets o = param_offsets(np);
+    const int F = guess_inputs(np);
+    for (int q = threadIdx.x; q < kH * F; q += blockDim.x) {      // W1[j][i], q = j F + i
+        const int j = q / F, i = q - j * F;
+        w1t[i * kHP + j] = (W)(float)src[o.w1 + q];
+    }
+    for (int q = threadIdx.x; q < kH * kH; q += blockDim.x) {
+        const int j = q / kH, i = q - j * kH;
+        w2t[i * kHP + j] = (W)(float)src[o.w2 + q];
+    }
+    for (int q = threadIdx.x; q < np * kH; q += blockDim.x) {     // W3[c][i]
+        const int c = q / kH, i = q - c * kH;
+        w3t[i * np + c] = (W)(float)src[o.w3 + q];
+    }
+    for (int q = threadIdx.x; q < kH; q += blockDim.x) {
+        b1[q] = (float)src[o.b1 + q];
+        b2[q] = (float)src[o.b2 + q];
+    }
+    for (int q = threadIdx.x; q < np; q += blockDim.x) b3[q] = (float)src[o.b3 + q];
+}
+
+// Features of element e into x[0 .. 9 NP + 3) (fp32), by one warp: lane l handles
+// component l of the own vector [a | d1 | d2] and its mean and max over the face
+// neighbours (the blocks of row e of K_h after the diagonal one).  off(c) is the
+// position of cell c's first coefficient in the U arrays.
+template <int NP, typename Off>
+__device__ __forceinline__ void element_features(const GuessFeat& f, const double* __restrict__ Uk,
+                                                 const double* __restrict__ Uk1,
+                                                 const double* __restrict__ Uk2, int64_t e, float* x,
+                                                 Off&& off) {
+    const int lane = threadIdx.x & 31;
+    auto own = [&](int64_t cell, int l) {
+        const int grp = l / NP, j = l - grp * NP;
+        const int64_t o = off(cell) + j;
+        if (grp == 0) return (Uk[o] - (j == 0 ? f.u_rest : 0.0)) / f.s_u;
+        if (grp == 1) return (Uk[o] - Uk1[o]) / f.s_d;
+        return (Uk1[o] - Uk2[o]) / f.s_d;
+    };
+    const int32_t b0 = f.row_ptr[e], b1 = f.row_ptr[e + 1];
+    const int cnt = b1 - b0 - 1;
+    for (int l = lane; l < 3 * NP; l += 32) {
+        x[l] = (float)own(e, l);
+        double sum = 0.0, mx = 0.0;
+        for (int32_t b = b0 + 1; b < b1; ++b) {
+            const double v = own(f.col[b], l);
+            sum += v;
+            mx = (b == b0 + 1) ? v : fmax(mx, v);
+        }
+        x[3 * NP + l] = cnt > 0 ? (float)(sum / cnt) : 0.f;
+        x[6 * NP + l] = cnt > 0 ? (float)mx : 0.f;
+    }
+    if (lane == 0) {
+        x[9 * NP] = (float)(f.diam[e] / f.h_ref);
+        x[9 * NP + 1] = (float)(f.dt / f.dt_ref);
+        x[9 * NP + 2] = (float)cnt / 10.f;
+    }
+}
+
+__device__ __forceinline__ void zero_row(float* x, int F) {
+    for (int l = threadIdx.x & 31; l < F; l += 32) x[l] = 0.f;
+}
+
+// Dense layer out[s][j] = act(b[j] + sum_i Wt[i * kHP + j] in[s][i]) for the tile's
+// kGT samples: thread (j, half) computes 16 samples of hidden unit j.
+template <typename W, bool RELU>
+__device__ __forceinline__ void hidden_layer(const W* wt, const float* b, const float* in, int n_in,
+                                             float* out) {
+    const int j = threadIdx.x & (kH - 1), s0 = (threadIdx.x >> 7) * 16;
+    float acc[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) acc[s] = b[j];
+    for (int i = 0; i < n_in; ++i) {
+        const float w = (float)wt[i * kHP + j];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) acc[s] = fmaf(w, in[(s0 + s) * n_in + i], acc[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < 16; ++s) out[(s0 + s) * kH + j] = RELU ? fmaxf(acc[s], 0.f) : acc[s];
+}
+
+// o[s * NP + c] = b3[c] + sum_i W3[c][i] h2[s][i].
+template <typename W, int NP>
+__device__ __forceinline__ void output_layer(const W* w3t, const float* b3, const float* h2, float* o) {
+    for (int q = threadIdx.x; q < kGT * NP; q += blockDim.x) {
+        const int s = q / NP, c = q - s * NP;
+        float acc = b3[c];
+        for (int i = 0; i < kH; ++i) acc = fmaf((float)w3t[i * NP + c], h2[s * kH + i], acc);
+        o[q] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ inference
+template <int NP>
+__global__ void __launch_bounds__(kGThreads)
+guess_propose_kernel(GuessFeat f, const __half* __restrict__ w16, const double* __restrict__ Uk,
+                     const double* __restrict__ Uk1, const double* __restrict__ Uk2,
+                     double* __restrict__ xg, int64_t nc, const SimScalars* ss) {
+    if (ss && (ss->failed || ss->k < 2)) return;
+    constexpr int F = guess_inputs(NP);
+    extern __shared__ __align__(16) unsigned char gsm[];
+    __half* w1t = reinterpret_cast<__half*>(gsm);
+    __half* w2t = w1t + F * kHP;
+    __half* w3t = w2t + kH * kHP;
+    float* b1 = reinterpret_cast<float*>(gsm + guess_weights_bytes16(NP));
+    float* b2 = b1 + kH;
+    float* b3 = b2 + kH;
+    float* xs = b3 + 16;
+    float* h1 = xs + kGT * F;
+    float* h2 = h1 + kGT * kH;
+    float* o = h2 + kGT * kH;
+    __shared__ int64_t elems[kGT];
+    stage_weights(w16, NP, w1t, w2t, w3t, b1, b2, b3);
+    for (int64_t t0 = (int64_t)blockIdx.x * kGT; t0 < nc; t0 += (int64_t)gridDim.x * kGT) {
+        const int n = (int)min((int64_t)kGT, nc - t0);
+        if (threadIdx.x < kGT) elems[threadIdx.x] = t0 + threadIdx.x;
+        __syncthreads();
+        for (int sm = threadIdx.x >> 5; sm < kGT; sm += blockDim.x >> 5) {
+            if (sm < n) element_features<NP>(f, Uk, Uk1, Uk2, elems[sm], xs + sm * F, [](int64_t e) { return e * NP; });
+            else zero_row(xs + sm * F, F);
+        }
+        __syncthreads();
+        hidden_layer<__half, true>(w1t, b1, xs, F, h1);
+        __syncthreads();
+        hidden_layer<__half, true>(w2t, b2, h1, kH, h2);
+        __syncthreads();
+        output_layer<__half, NP>(w3t, b3, h2, o);
+        __syncthreads();
+        for (int q = threadIdx.x; q < n * NP; q += blockDim.x) {
+            const int64_t t = t0 * NP + q;
+            xg[t] = Uk[t] + f.s_d * (double)o[q];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ safeguard
+// |b - K xg|^2 and |b - K U^k|^2 (warp per element, K_h read once), then the last CTA
+// (ticket) keeps the guess if its residual is strictly smaller.
+template <int NP>
+__global__ void __launch_bounds__(kBlock)
+guess_select_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                    const double* __restrict__ val, const double* __restrict__ b,
+                    const double* __restrict__ xg, const double* __restrict__ uk, int64_t nc,
+                    double* partials, SimScalars* ss, int always) {
+    if (ss->failed || ss->k < 2) return;
+    if (always) {                                 // policy: start from every proposal
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ss->use_guess = 1;
+            ss->guesses_taken += 1;
+        }
+        return;
+    }
+    __shared__ double sh[32];
+    __shared__ bool last;
+    constexpr int G = 32 / NP;
+    const int lane = threadIdx.x & 31;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int g = (lane < G * NP) ? lane / NP : G;
+    const int i = lane - (lane / NP) * NP;
+    double ag = 0.0, a0 = 0.0;
+    if (e < nc) {
+        const int32_t b0 = row_ptr[e];
+        const int ncol = (row_ptr[e + 1] - b0) * NP;
+        const double* V = val + (int64_t)b0 * NP * NP;
+        for (int c = g; c < ncol; c += G) {
+            const int sblk = c / NP;
+            const int64_t xi = (int64_t)__ldg(col + b0 + sblk) * NP + (c - sblk * NP);
+            const double v = __ldg(V + (int64_t)c * NP + i);
+            ag = fma(v, __ldg(xg + xi), ag);
+            a0 = fma(v, __ldg(uk + xi), a0);
+        }
+    }
+    double tg = ag, t0 = a0;
+#pragma unroll
+    for (int k = 1; k < G; ++k) {
+        tg += __shfl_down_sync(0xffffffffu, ag, k * NP);
+        t0 += __shfl_down_sync(0xffffffffu, a0, k * NP);
+    }
+    double dg = 0.0, d0 = 0.0;
+    if (e < nc && lane < NP) {
+        const double bv = b[e * NP + i];
+        dg = (bv - tg) * (bv - tg);
+        d0 = (bv - t0) * (bv - t0);
+    }
+    double s[2];
+    s[0] = block_sum(dg, sh);
+    s[1] = block_sum(d0, sh);
+    if (publish_partials(partials, s, 2, &ss->guess_ticket, &last)) {
+        const double rg = sum_partials(partials, gridDim.x, sh);
+        const double r0 = sum_partials(partials + kMaxPartials, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            ss->guess_ticket = 0;
+            ss->use_guess = (rg < r0) ? 1 : 0;
+            ss->guesses_taken += (rg < r0) ? 1 : 0;
+        }
+    }
+}
+
+// x0 = guess if it was kept, else U^k.
+__global__ void select_copy_kernel(const double* __restrict__ uk, const double* __restrict__ xg,
+                                   double* __restrict__ x0, int64_t n, const SimScalars* ss) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ss->failed || t >= n) return;
+    x0[t] = ss->use_guess ? xg[t] : uk[t];
+}
+
+// ------------------------------------------------------------------ training
+// One minibatch: forward, MSE loss and backward for tiles of kGT samples; CTA c adds
+// its tiles' gradients into part[c * P + .] (its first tile stores) and its loss sum
+// into lpart[c].  Sample q is (state k, caller cell id) in samples[2 q], [2 q + 1].
+template <int NP>
+__global__ void __launch_bounds__(kGThreads)
+guess_train_kernel(GuessFeat f, const float* __restrict__ w32, const double* __restrict__ traj,
+                   int64_t n_dofs, const int64_t* __restrict__ samples, int64_t n_samples,
+                   const int64_t* __restrict__ to_internal, const int64_t* __restrict__ to_caller,
+                   float* __restrict__ part, double* __restrict__ lpart) {
+    constexpr int F = guess_inputs(NP);
+    const ParamOffsets po = param_offsets(NP);
+    extern __shared__ __align__(16) unsigned char gsm[];
+    float* w1t = reinterpret_cast<float*>(gsm);
+    float* w2t = w1t + F * kHP;
+    float* w3t = w2t + kH * kHP;
+    float* b1 = w3t + kH * NP;
+    float* b2 = b1 + kH;
+    float* b3 = b2 + kH;
+    float* xs = b3 + 16;
+    float* h1 = xs + kGT * F;
+    float* h2 = h1 + kGT * kH;
+    float* dz2 = h2 + kGT * kH;
+    float* dz1 = dz2 + kGT * kH;
+    float* o = dz1 + kGT * kH;                 // then do
+    float* tg = o + kGT * NP;
+    __shared__ int64_t elems[kGT], kst[kGT];
+    __shared__ double lsh[32];
+    stage_weights(w32, NP, w1t, w2t, w3t, b1, b2, b3);
+    float* g = part + (size_t)blockIdx.x * po.total;
+    const float inv = 1.f / (float)((double)n_samples * NP);
+    double lsum = 0.0;
+    bool first = true;
+    const int64_t n_tiles = (n_samples + kGT - 1) / kGT;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t q0 = tile * kGT;
+        const int n = (int)min((int64_t)kGT, n_samples - q0);
+        if (threadIdx.x < kGT) {
+            const int s = threadIdx.x;
+            elems[s] = s < n ? to_internal[samples[2 * (q0 + s) + 1]] : 0;
+            kst[s] = s < n ? samples[2 * (q0 + s)] : 2;
+        }
+        __syncthreads();
+        // features (per sample its own state k) and targets
+        for (int s = threadIdx.x >> 5; s < kGT; s += blockDim.x >> 5) {
+            if (s < n) {
+                const double* Uk = traj + kst[s] * n_dofs;
+                element_features<NP>(f, Uk, Uk - n_dofs, Uk - 2 * n_dofs, elems[s], xs + s * F,
+                                     [&](int64_t c) { return to_caller[c] * NP; });
+            } else {
+                zero_row(xs + s * F, F);
+            }
+        }
+        for (int q = threadIdx.x; q < kGT * NP; q += blockDim.x) {
+            const int s = q / NP, c = q - s * NP;
+            float t = 0.f;
+            if (s < n) {
+                const int64_t o_ = to_caller[elems[s]] * NP + c;
+                const double* Uk = traj + kst[s] * n_dofs;
+                t = (float)((Uk[n_dofs + o_] - Uk[o_]) / f.s_d);
+            }
+            tg[q] = t;
+        }
+        __syncthreads();
+        hidden_layer<float, true>(w1t, b1, xs, F, h1);
+        __syncthreads();
+        hidden_layer<float, true>(w2t, b2, h1, kH, h2);
+        __syncthreads();
+        output_layer<float, NP>(w3t, b3, h2, o);
+        __syncthreads();
+        for (int q = threadIdx.x; q < kGT * NP; q += blockDim.x) {   // o <- dL/do
+            const int s = q / NP;
+            const float d = (s < n) ? o[q] - tg[q] : 0.f;
+            lsum += (double)d * d;
+            o[q] = 2.f * d * inv;
+        }
+        __syncthreads();
+        {   // dz2 = (do W3) * [h2 > 0]
+            const int j = threadIdx.x & (kH - 1), s0 = (threadIdx.x >> 7) * 16;
+            for (int s = s0; s < s0 + 16; ++s) {
+                float acc = 0.f;
+#pragma unroll
+                for (int c = 0; c < NP; ++c) acc = fmaf(o[s * NP + c], w3t[j * NP + c], acc);
+                dz2[s * kH + j] = h2[s * kH + j] > 0.f ? acc : 0.f;
+            }
+        }
+        __syncthreads();
+        {   // dz1 = (dz2 W2) * [h1 > 0]: dh1[s][i] = sum_j W2[j][i] dz2[s][j]
+            const int i = threadIdx.x & (kH - 1), s0 = (threadIdx.x >> 7) * 16;
+            float acc[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) acc[s] = 0.f;
+            for (int j = 0; j < kH; ++j) {
+                const float w = w2t[i * kHP + j];
+#pragma unroll
+                for (int s = 0; s < 16; ++s) acc[s] = fmaf(w, dz2[(s0 + s) * kH + j], acc[s]);
+            }
+#pragma unroll
+            for (int s = 0; s < 16; ++s) dz1[(s0 + s) * kH + i] = h1[(s0 + s) * kH + i] > 0.f ? acc[s] : 0.f;
+        }
+        __syncthreads();
+        // weight gradients of this tile, added into the CTA's partial (canonical layout)
+        auto put = [&](int idx, float v) { g[idx] = first ? v : g[idx] + v; };
+        for (int q = threadIdx.x; q < kH * F; q += blockDim.x) {     // W1[j][i]
+            const int j = q / F, i = q - j * F;
+            float acc = 0.f;
+            for (int s = 0; s < kGT; ++s) acc = fmaf(dz1[s * kH + j], xs[s * F + i], acc);
+            put(po.w1 + q, acc);
+        }
+        for (int q = threadIdx.x; q < kH * kH; q += blockDim.x) {    // W2[j][i]
+            const int j = q / kH, i = q - j * kH;
+            float acc = 0.f;
+            for (int s = 0; s < kGT; ++s) acc = fmaf(dz2[s * kH + j], h1[s * kH + i], acc);
+            put(po.w2 + q, acc);
+        }
+        for (int q = threadIdx.x; q < NP * kH; q += blockDim.x) {    // W3[c][i]
+            const int c = q / kH, i = q - c * kH;
+            float acc = 0.f;
+            for (int s = 0; s < kGT; ++s) acc = fmaf(o[s * NP + c], h2[s * kH + i], acc);
+            put(po.w3 + q, acc);
+        }
+        for (int q = threadIdx.x; q < kH; q += blockDim.x) {
+            float a1 = 0.f, a2 = 0.f;
+            for (int s = 0; s < kGT; ++s) { a1 += dz1[s * kH + q]; a2 += dz2[s * kH + q]; }
+            put(po.b1 + q, a1);
+            put(po.b2 + q, a2);
+        }
+        for (int q = threadIdx.x; q < NP; q += blockDim.x) {
+            float a3 = 0.f;
+            for (int s = 0; s < kGT; ++s) a3 += o[s * NP + q];
+            put(po.b3 + q, a3);
+        }
+        first = false;
+        __syncthreads();
+    }
+    const double lt = block_sum(lsum, lsh);
+    if (threadIdx.x == 0) lpart[blockIdx.x] = lt;
+}
+
+// grad = sum over CTAs of the partials (CTA order); one Adam step of the fp32 master
+// weights; fp16 copy for inference; loss = sum of the CTAs' loss sums / (samples n_p).
+__global__ void guess_adam_kernel(const float* __restrict__ part, int ncta, int P,
+                                  float* __restrict__ w32, float* __restrict__ m, float* __restrict__ v,
+                                  __half* __restrict__ w16, float lr, float b1, float b2, float eps,
+                                  float c1, float c2, const double* __restrict__ lpart, double inv_count,
+                                  double* loss) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) {
+        double l = 0.0;
+        for (int c = 0; c < ncta; ++c) l += lpart[c];
+        *loss = l * inv_count;
+    }
+    if (p >= P) return;
+    float gsum = 0.f;
+    for (int c = 0; c < ncta; ++c) gsum += part[(size_t)c * P + p];
+    const float mm = b1 * m[p] + (1.f - b1) * gsum;
+    const float vv = b2 * v[p] + (1.f - b2) * gsum * gsum;
+    m[p] = mm;
+    v[p] = vv;
+    const float w = w32[p] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+    w32[p] = w;
+    w16[p] = __float2half_rn(w);
+}
+
+__global__ void to_half_kernel(const float* __restrict__ w32, __half* __restrict__ w16, int P) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) w16[p] = __float2half_rn(w32[p]);
+}
+
+// ------------------------------------------------------------------ launchers
+size_t guess_propose_smem(int np) {
+    const int F = guess_inputs(np);
+    return guess_weights_bytes16(np) + (size_t)(2 * kH + 16 + kGT * F + 2 * kGT * kH + kGT * np) * sizeof(float);
+}
+
+size_t guess_train_smem(int np) {
+    const int F = guess_inputs(np);
+    return (size_t)(F * kHP + kH * kHP + kH * np + 2 * kH + 16 + kGT * F + 4 * kGT * kH + 2 * kGT * np) *
+           sizeof(float);
+}
+
+// n_p <= 10: the training kernel keeps the whole network in shared memory
+#define GUESS_NP_SWITCH(np, ...)                                \
+    switch (np) {                                               \
+        case 3: { constexpr int NP = 3; __VA_ARGS__; } break;   \
+        case 6: { constexpr int NP = 6; __VA_ARGS__; } break;   \
+        case 10: { constexpr int NP = 10; __VA_ARGS__; } break; \
+        default: return cudaErrorInvalidValue;                  \
+    }
+
+// Raise the shared-memory limits of the inference and training kernels for n_p (once,
+// before any launch, so that launches can be recorded into CUDA graphs).
+cudaError_t guess_prepare(int np) {
+    GUESS_NP_SWITCH(np, {
+        cudaError_t e = cudaFuncSetAttribute(guess_propose_kernel<NP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)guess_propose_smem(np));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(guess_train_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)guess_train_smem(np));
+        return e;
+    })
+    return cudaSuccess;
+}
+
+cudaError_t launch_guess_propose(int np, const GuessFeat& f, const __half* w16, const double* Uk,
+                                 const double* Uk1, const double* Uk2, double* xg, int64_t nc,
+                                 const SimScalars* ss, cudaStream_t s) {
+    const size_t smem = guess_propose_smem(np);
+    const unsigned grid = (unsigned)std::min<int64_t>((nc + kGT - 1) / kGT, 4 * 152);
+    if (grid == 0) return cudaSuccess;
+    GUESS_NP_SWITCH(np, {
+        guess_propose_kernel<NP><<<grid, kGThreads, smem, s>>>(f, w16, Uk, Uk1, Uk2, xg, nc, ss);
+    })
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guess_select(int np, const DeviceMatrix& K, const double* b, const double* xg,
+                                const double* uk, double* partials, SimScalars* ss, int always,
+                                cudaStream_t s) {
+    const unsigned grid = always ? 1u : (unsigned)((K.nc * 32 + kBlock - 1) / kBlock);
+    if (grid > (unsigned)kMaxPartials) return cudaErrorInvalidValue;
+    GUESS_NP_SWITCH(np, {
+        guess_select_kernel<NP><<<grid, kBlock, 0, s>>>(K.row_ptr, K.col, K.val, b, xg, uk, K.nc,
+                                                        partials, ss, always);
+    })
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_copy(const double* uk, const double* xg, double* x0, int64_t n,
+                               const SimScalars* ss, cudaStream_t s) {
+    select_copy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(uk, xg, x0, n, ss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guess_train(int np, const GuessFeat& f, const float* w32, const double* traj,
+                               int64_t n_dofs, const int64_t* samples, int64_t n_samples,
+                               const int64_t* to_internal, const int64_t* to_caller, float* part,
+                               double* lpart, int grid, cudaStream_t s) {
+    const size_t smem = guess_train_smem(np);
+    GUESS_NP_SWITCH(np, {
+        guess_train_kernel<NP><<<grid, kGThreads, smem, s>>>(f, w32, traj, n_dofs, samples, n_samples,
+                                                             to_internal, to_caller, part, lpart);
+    })
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guess_adam(const float* part, int ncta, int P, float* w32, float* m, float* v,
+                              __half* w16, float lr, float b1, float b2, float eps, float c1, float c2,
+                              const double* lpart, double inv_count, double* loss, cudaStream_t s) {
+    guess_adam_kernel<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(part, ncta, P, w32, m, v, w16, lr, b1,
+                                                                 b2, eps, c1, c2, lpart, inv_count, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_half(const float* w32, __half* w16, int P, cudaStream_t s) {
+    to_half_kernel<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(w32, w16, P);
+    return cudaGetLastError();
+}
+
+}  // namespace polydg

@@ -99,26 +99,30 @@ cudaError_t launch_init_y(double* y, int64_t nn, const double* y0, cudaStream_t 
 }
 
 // Reset the PCG scalars at the start of a step (no-op after a failed step).
-__global__ void step_begin_kernel(PcgScalars* sc, const SimScalars* ss) {
+__global__ void step_begin_kernel(PcgScalars* sc, SimScalars* ss) {
     if (threadIdx.x != 0) return;
     sc->done = ss->failed ? 1 : 0;
     sc->it = 0;
     sc->status = 0;
+    ss->use_guess = 0;
 }
 
-cudaError_t launch_step_begin(PcgScalars* sc, const SimScalars* ss, cudaStream_t s) {
+cudaError_t launch_step_begin(PcgScalars* sc, SimScalars* ss, cudaStream_t s) {
     step_begin_kernel<<<1, 32, 0, s>>>(sc, ss);
     return cudaGetLastError();
 }
 
-// U^{k-1} <- U^k, U^k <- x, k <- k + 1 and the step statistics.
+// U^{k-2} <- U^{k-1} (if kept), U^{k-1} <- U^k, U^k <- x, k <- k + 1 and the step
+// statistics.
 __global__ void step_finish_kernel(double* __restrict__ U, double* __restrict__ Uprev,
-                                   const double* __restrict__ x0, const double* __restrict__ x1,
-                                   int64_t n, const PcgScalars* sc, SimScalars* ss) {
+                                   double* __restrict__ Uprev2, const double* __restrict__ x0,
+                                   const double* __restrict__ x1, int64_t n, const PcgScalars* sc,
+                                   SimScalars* ss) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = !ss->failed;
     const double* x = (sc->pass & 1) ? x1 : x0;   // the iterate lives in buffer (pass & 1)
     if (ok && t < n) {
+        if (Uprev2) Uprev2[t] = Uprev[t];
         Uprev[t] = U[t];
         U[t] = x[t];
     }
@@ -137,9 +141,10 @@ __global__ void step_stats_kernel(const PcgScalars* sc, SimScalars* ss) {
     }
 }
 
-cudaError_t launch_step_finish(double* U, double* Uprev, const double* x0, const double* x1,
-                               int64_t n, const PcgScalars* sc, SimScalars* ss, cudaStream_t s) {
-    step_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, Uprev, x0, x1, n, sc, ss);
+cudaError_t launch_step_finish(double* U, double* Uprev, double* Uprev2, const double* x0,
+                               const double* x1, int64_t n, const PcgScalars* sc, SimScalars* ss,
+                               cudaStream_t s) {
+    step_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, Uprev, Uprev2, x0, x1, n, sc, ss);
     step_stats_kernel<<<1, 32, 0, s>>>(sc, ss);
     return cudaGetLastError();
 }

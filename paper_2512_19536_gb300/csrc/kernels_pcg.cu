@@ -107,18 +107,20 @@ __device__ __forceinline__ void block_sum_n(double (&v)[N]) {
     __syncthreads();
 }
 
-// Grid barrier over all CTAs of a cooperative launch.  gs->count starts at 0 for
-// the launch and only grows: barrier number k completes when it reaches
-// (k + 1) * gridDim.x, so no CTA has to reset or flip anything.  The arrive is a
+// Barrier over the G CTAs of one solve (all CTAs of a single-solve launch, or
+// one simulation's CTA group of a batched launch; the launch is cooperative, so
+// all of them are resident).  gs->count starts at 0 for the launch and only
+// grows: barrier number k completes when it reaches (k + 1) * G, so no CTA has
+// to reset or flip anything.  The arrive is a
 // fire-and-forget release reduction after a fence that publishes the CTA's
 // writes; waiters poll with acquire loads.  `target` lives in thread 0.
 // Returns false (and raises *err) if the other CTAs did not arrive in time.
-__device__ bool grid_barrier(GridSync* gs, unsigned& target, int* err) {
+__device__ bool grid_barrier(GridSync* gs, unsigned G, unsigned& target, int* err) {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        target += gridDim.x;
+        target += G;
         __threadfence();
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gs->count) : "memory");
         uint32_t k = 0;
@@ -135,18 +137,18 @@ __device__ bool grid_barrier(GridSync* gs, unsigned& target, int* err) {
 // block sums before the barrier and afterwards adds all CTAs' partials in CTA
 // order, so every CTA obtains the same bit-identical, deterministic sums.
 template <int N>
-__device__ bool barrier_sum(GridSync* gs, unsigned& gen, int* err, double* partials,
-                            double* /*bcast*/, double (&v)[N]) {
+__device__ bool barrier_sum(GridSync* gs, unsigned G, int cta, unsigned& gen, int* err,
+                            double* partials, double (&v)[N]) {
     block_sum_n<N>(v);
     if (threadIdx.x == 0)
 #pragma unroll
-        for (int k = 0; k < N; ++k) partials[(size_t)k * gridDim.x + blockIdx.x] = v[k];
-    const bool ok = grid_barrier(gs, gen, err);
+        for (int k = 0; k < N; ++k) partials[(size_t)k * G + cta] = v[k];
+    const bool ok = grid_barrier(gs, G, gen, err);
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+    for (int i = threadIdx.x; i < (int)G; i += blockDim.x)
 #pragma unroll
-        for (int k = 0; k < N; ++k) v[k] += __ldcg(partials + (size_t)k * gridDim.x + i);
+        for (int k = 0; k < N; ++k) v[k] += __ldcg(partials + (size_t)k * G + i);
     block_sum_n<N>(v);
     return ok;
 }
@@ -204,12 +206,13 @@ __device__ __forceinline__ double row_dot(const __nv_bfloat16* Ar, const float* 
     return (double)warp_sumf(a0 + a1);
 }
 
-// What the P phase needs of one tile, staged in shared memory at kernel start.
-struct TileDesc {
-    int64_t src_off;      // element offset of the tile's first row in the store
-    int64_t in_off;       // first DOF of the tile's subdomain
-    int32_t row0, nrt, ld, ncols, block, pair_begin, pair_count;
-    uint32_t bytes;       // bulk-copy size
+// What the P phase needs of one run (contiguous rows of one subdomain's local
+// inverse), staged in shared memory at kernel start.
+struct RunDesc {
+    int64_t mat_off;      // element offset of the block in the store
+    int64_t in_off;       // first DOF of the block's subdomain
+    int32_t row_begin, row_end, ld, ncols, block, pair_begin, pair_count;
+    int32_t ord;          // position of the run's first row in the CTA's row sequence
 };
 
 // Rows of the CTA's elements of y = K x, warp per element, with x read from the
@@ -258,16 +261,15 @@ __device__ __forceinline__ void local_rows(const int32_t* __restrict__ row_ptr,
     }
 }
 
+// The whole solve as seen by CTA `cta` of the G CTAs working on it.
 template <int DT, int NP>
-__global__ void __launch_bounds__(kPersistThreads, 1)
-pcg_persistent_kernel(PersistArgs a) {
+__device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int cta, const unsigned G,
+                                              unsigned char* smem) {
     using T = typename StoreType<DT>::T;
     using X = typename StoreType<DT>::X;
-    extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int S = kStages;
-    __shared__ __align__(8) uint64_t bars[S];
+    constexpr int NW = kPersistThreads / 32;
+    __shared__ __align__(8) uint64_t wbars[NW][kMaxWarpStages];
 
-    const int cta = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     PcgScalars* sc = a.sc;
     if (sc->done) return;             // a failed earlier step: nothing to do (uniform)
@@ -276,71 +278,105 @@ pcg_persistent_kernel(PersistArgs a) {
     const int maxit = sc->maxit;
     unsigned gen = 0;                 // barrier target of thread 0 (gs->count is 0 at launch)
 
-    auto buf = [&](int k) { return reinterpret_cast<T*>(smem + (size_t)k * a.buf_bytes); };
+    const int S = a.wstages;                                       // copy slots per warp
+    auto slot = [&](int w, int k) { return reinterpret_cast<T*>(smem + ((size_t)w * S + k) * a.slot_bytes); };
     X* xs = reinterpret_cast<X*>(smem + a.xs_off);                 // r' in the store's arithmetic
     double* rp = reinterpret_cast<double*>(smem + a.rp_off);       // r' (fp64)
-    double* zs = reinterpret_cast<double*>(smem + a.zs_off);       // [S][rows]
     double* r0s = reinterpret_cast<double*>(smem + a.r0_off);      // [n0]
     double* y0l = reinterpret_cast<double*>(smem + a.y0_off);      // y0 of the CTA's agglomerates
     double* pn = reinterpret_cast<double*>(smem + a.pn_off);       // x or z of the needed elements
-    TileDesc* td = reinterpret_cast<TileDesc*>(smem + a.td_off);   // this CTA's tiles
-    __shared__ double zpart[kPersistThreads / 32];                 // split-row partial dots
+    RunDesc* rd = reinterpret_cast<RunDesc*>(smem + a.td_off);     // this CTA's runs
 
     const int64_t e0 = a.elem_ptr[cta], e1 = a.elem_ptr[cta + 1];
     const int n_own = (int)(e1 - e0);
-    const int32_t* need = a.need + a.need_ptr[cta];
-    const int32_t* needj = a.need_aggl + a.need_ptr[cta];
-    const int n_need = a.need_ptr[cta + 1] - a.need_ptr[cta];
+    const int ch0 = a.cta_chunk[cta], ch1 = a.cta_chunk[cta + 1];
     const int32_t* aggs = a.need_agg + a.need_agg_ptr[cta];
     const int n_aggs = a.need_agg_ptr[cta + 1] - a.need_agg_ptr[cta];
-    const int t0 = a.tile_ptr[cta], nt = a.tile_ptr[cta + 1] - t0;
+    const int run0 = a.run_ptr[cta], nruns = a.run_ptr[cta + 1] - run0;
     const int c0 = a.crow_ptr[cta], c1 = a.crow_ptr[cta + 1];
     const bool coarse = a.n0 > 0;
 
     // ---- init: r = b - K x on own elements; p, q, z, w = 0; |b|^2, |r|^2
-    for (int idx = threadIdx.x; idx < n_need * NP; idx += blockDim.x) {
-        const int l = idx / NP;
-        pn[idx] = __ldcg(a.x + (int64_t)need[l] * NP + (idx - l * NP));
-    }
     for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) {
         a.p[0][t] = 0.0; a.p[1][t] = 0.0; a.q[0][t] = 0.0; a.q[1][t] = 0.0;
         a.z[t] = 0.0; a.w[t] = 0.0;
     }
-    __syncthreads();
     double v2[2] = {0.0, 0.0};
-    local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, e0, e1, [&](int64_t e, int i, double kx) {
-        const int64_t t = e * NP + i;
-        const double bv = a.b[t], rv = bv - kx;
-        a.r[0][t] = rv;
-        v2[0] = fma(bv, bv, v2[0]);
-        v2[1] = fma(rv, rv, v2[1]);
-    });
-    uint32_t seq = 0;                 // tiles consumed so far (all iterations)
-    for (int k = threadIdx.x; k < nt; k += blockDim.x) {
-        const GemvTile tl = a.tiles[t0 + k];
-        const GemvBlock B = a.blocks[tl.block];
-        TileDesc d;
-        d.src_off = B.mat_off + (int64_t)tl.row0 * B.ld;
-        d.in_off = B.in_off;
-        d.row0 = tl.row0;
-        d.nrt = min(a.rows, B.nrows - tl.row0);
-        d.ld = B.ld;
-        d.ncols = B.ncols;
-        d.block = tl.block;
-        d.pair_begin = B.pair_begin;
-        d.pair_count = B.pair_count;
-        d.bytes = (uint32_t)((size_t)d.nrt * B.ld * sizeof(T));
-        td[k] = d;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < S; ++k) mbar_init(&bars[k]);
-        for (int k = 0; k < S && nt > 0; ++k) {   // the inverses do not depend on the iterate
-            const TileDesc& d = td[k % nt];
-            bulk_load(buf(k), reinterpret_cast<const T*>(a.store) + d.src_off, d.bytes, &bars[k]);
+    for (int ch = ch0; ch < ch1; ++ch) {        // chunks of the CTA's elements
+        const int64_t ce0 = a.chunk_elem[ch], ce1 = a.chunk_elem[ch + 1];
+        const int32_t* need = a.need + a.need_ptr[ch];
+        const int n_need = a.need_ptr[ch + 1] - a.need_ptr[ch];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < n_need * NP; idx += blockDim.x) {
+            const int l = idx / NP;
+            pn[idx] = __ldcg(a.x + (int64_t)need[l] * NP + (idx - l * NP));
         }
+        __syncthreads();
+        local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, ce0, ce1, [&](int64_t e, int i, double kx) {
+            const int64_t t = e * NP + i;
+            const double bv = a.b[t], rv = bv - kx;
+            a.r[0][t] = rv;
+            v2[0] = fma(bv, bv, v2[0]);
+            v2[1] = fma(rv, rv, v2[1]);
+        });
     }
-    bool ok = barrier_sum<2>(a.gs, gen, a.err, a.partials, a.bcast, v2);
+    // The CTA's rows of the local inverses, run after run, are dealt to the warps in
+    // turn: warp w owns the rows at positions w, w + NW, ... of that sequence and
+    // streams them, one row per copy, through its own ring of S slots.
+    int n_rows = 0;
+    for (int k = 0; k < nruns; ++k) {
+        const GemvRun rn = a.runs[run0 + k];
+        if ((k & (blockDim.x - 1)) == (int)threadIdx.x) {
+            const GemvBlock B = a.blocks[rn.block];
+            RunDesc d;
+            d.mat_off = B.mat_off;
+            d.in_off = B.in_off;
+            d.row_begin = rn.row_begin;
+            d.row_end = rn.row_end;
+            d.ld = B.ld;
+            d.ncols = B.ncols;
+            d.block = rn.block;
+            d.pair_begin = B.pair_begin;
+            d.pair_count = B.pair_count;
+            d.ord = n_rows;
+            rd[k] = d;
+        }
+        n_rows += rn.row_end - rn.row_begin;
+    }
+    const bool has_rows = warp < n_rows;
+    uint32_t wseq = 0;                // rows this warp consumed so far (all iterations)
+    uint32_t n_done = 0, n_issued = 0;  // copies seen complete / issued (copy c: slot c % S)
+    bool wfail = false;               // a copy wait timed out: no more waits or copies
+    // issue side (lane 0): run and row of the warp's next copy; after the CTA's last
+    // run it starts over at the warp's first row (the inverses are constant)
+    int iss_run = 0, iss_row = 0, first_run = 0, first_row = 0;
+    __syncthreads();
+    if (has_rows) {
+        while (rd[first_run].ord + (rd[first_run].row_end - rd[first_run].row_begin) <= warp) ++first_run;
+        first_row = rd[first_run].row_begin + (warp - rd[first_run].ord);
+        iss_run = first_run;
+        iss_row = first_row;
+    }
+    auto issue = [&](int k) {
+        const RunDesc& d = rd[iss_run];
+        bulk_load(slot(warp, k), reinterpret_cast<const T*>(a.store) + d.mat_off + (int64_t)iss_row * d.ld,
+                  (uint32_t)((size_t)d.ld * sizeof(T)), &wbars[warp][k]);
+        iss_row += NW;
+        while (iss_row >= rd[iss_run].row_end) {
+            const int over = iss_row - rd[iss_run].row_end;
+            if (iss_run + 1 == nruns) { iss_run = first_run; iss_row = first_row; break; }
+            ++iss_run;
+            iss_row = rd[iss_run].row_begin + over;
+        }
+    };
+    if (has_rows) {
+        if (lane == 0) {
+            for (int k = 0; k < S; ++k) mbar_init(&wbars[warp][k]);
+            for (int k = 0; k < S; ++k) issue(k);
+        }
+        n_issued = S;
+    }
+    bool ok = barrier_sum<2>(a.gs, G, cta, gen, a.err, a.partials, v2);
     const double bb = v2[0];
     double rr = v2[1];
     int status = kOK, it = 0, done = 0, par = 0, pp = 0;
@@ -373,76 +409,33 @@ pcg_persistent_kernel(PersistArgs a) {
                 v1[0] = fma(r_, r_, v1[0]);
             }
         } else {
-            int staged = -1;
-            const int parts = (a.rows < nw && nw % a.rows == 0) ? nw / a.rows : 1;
-            for (int k = 0; k < nt; ++k, ++seq) {
-                const TileDesc& tl = td[k];
-                const int nrt = tl.nrt;
-                if (tl.block != staged) {
-                    __syncthreads();
-                    for (int j = threadIdx.x; j < tl.ld; j += blockDim.x) {
-                        double r_ = 0.0;
-                        if (j < tl.ncols) {
-                            const int64_t t = tl.in_off + j;
-                            const double qk = fma(be, __ldcg(qold + t), __ldcg(a.w + t));
-                            r_ = fma(-al, qk, __ldcg(rin + t));
+            for (int ri = 0; ri < nruns; ++ri) {
+                const RunDesc& rn = rd[ri];
+                // r' of the run's subdomain (all its DOFs: the product's input), and
+                // the commit of the run's own rows: p_k, q_k, x += alpha p_k, r'
+                __syncthreads();                  // the previous run's readers of xs / rp are done
+                for (int j = threadIdx.x; j < rn.ld; j += blockDim.x) {
+                    double r_ = 0.0;
+                    if (j < rn.ncols) {
+                        const int64_t t = rn.in_off + j;
+                        const double qk = fma(be, __ldcg(qold + t), __ldcg(a.w + t));
+                        r_ = fma(-al, qk, __ldcg(rin + t));
+                        if (j >= rn.row_begin && j < rn.row_end) {
+                            const double pk = fma(be, __ldcg(pold + t), __ldcg(a.z + t));
+                            pnew[t] = pk;
+                            qnew[t] = qk;
+                            a.x[t] = fma(al, pk, a.x[t]);
+                            rout[t] = r_;
+                            v1[0] = fma(r_, r_, v1[0]);
                         }
-                        rp[j] = r_;
-                        if (DT != 0) xs[j] = (X)r_;
                     }
-                    staged = tl.block;
-                    __syncthreads();
+                    rp[j] = r_;
+                    if (DT != 0) xs[j] = (X)r_;
                 }
-                // operands of the commit, fetched before the tile lands
-                const int64_t tr = tl.in_off + tl.row0 + threadIdx.x;
-                double zv = 0.0, wv = 0.0, pv = 0.0, qv = 0.0, xv = 0.0;
-                if ((int)threadIdx.x < nrt) {
-                    zv = __ldcg(a.z + tr); wv = __ldcg(a.w + tr);
-                    pv = __ldcg(pold + tr); qv = __ldcg(qold + tr);
-                    xv = a.x[tr];
-                }
-                const int bi = seq % S;
-                if (!mbar_wait(&bars[bi], (seq / S) & 1)) {
-                    if (threadIdx.x == 0) atomicExch(a.err, 1);
-                }
-                double* zt = zs + bi * a.rows;
-                const T* As = buf(bi);
-                const X* xin = (DT == 0) ? reinterpret_cast<const X*>(rp) : xs;
-                if (parts == 1) {
-                    for (int r_ = warp; r_ < nrt; r_ += nw) {
-                        const double zr = row_dot(As + (size_t)r_ * tl.ld, xin, tl.ld, lane, 0, 1);
-                        if (lane == 0) zt[r_] = zr;
-                    }
-                    __syncthreads();
-                } else {                  // rows < warps: each row split over `parts` warps
-                    const int r_ = warp % a.rows, part = warp / a.rows;
-                    const double zr = (r_ < nrt) ? row_dot(As + (size_t)r_ * tl.ld, xin, tl.ld, lane, part, parts) : 0.0;
-                    if (lane == 0) zpart[warp] = zr;
-                    __syncthreads();
-                    if ((int)threadIdx.x < nrt) {
-                        double sum = 0.0;
-                        for (int pt = 0; pt < parts; ++pt) sum += zpart[pt * a.rows + threadIdx.x];
-                        zt[threadIdx.x] = sum;
-                    }
-                    __syncthreads();
-                }
-                if (threadIdx.x == 0) {   // buffer bi is free: prefetch S tiles ahead (cyclic)
-                    const TileDesc& tn = td[(k + S) % nt];
-                    bulk_load(buf(bi), reinterpret_cast<const T*>(a.store) + tn.src_off, tn.bytes, &bars[bi]);
-                }
-                if ((int)threadIdx.x < nrt) {
-                    const double pk = fma(be, pv, zv), qk = fma(be, qv, wv);
-                    const double r_ = rp[tl.row0 + threadIdx.x];
-                    pnew[tr] = pk;
-                    qnew[tr] = qk;
-                    a.x[tr] = fma(al, pk, xv);
-                    rout[tr] = r_;
-                    a.zl[tr] = zt[threadIdx.x];
-                    v1[0] = fma(r_, r_, v1[0]);
-                }
-                if (tl.row0 == 0 && coarse) {   // this CTA stages the subdomain first: R_0 r'
-                    for (int pi = 0; pi < tl.pair_count; ++pi) {
-                        const GemvBlock R = a.blocks[a.sub_pairs[tl.pair_begin + pi]];
+                __syncthreads();
+                if (rn.row_begin == 0 && coarse) {   // this CTA streams the subdomain's first rows: R_0 r'
+                    for (int pi = 0; pi < rn.pair_count; ++pi) {
+                        const GemvBlock R = a.blocks[a.sub_pairs[rn.pair_begin + pi]];
                         const double* Rm = a.st64 + R.mat_off;
                         for (int row = warp; row < R.nrows; row += nw) {
                             const double* Rr = Rm + (int64_t)row * R.ld;
@@ -458,15 +451,35 @@ pcg_persistent_kernel(PersistArgs a) {
                         }
                     }
                 }
+                // this warp's rows of the run: z_loc = row . r'
+                const X* xin = (DT == 0) ? reinterpret_cast<const X*>(rp) : xs;
+                const int k0 = ((warp - rn.ord) % NW + NW) % NW;
+                for (int row = rn.row_begin + k0; row < rn.row_end; row += NW, ++wseq) {
+                    const int k = wseq % S;
+                    if (!wfail && !mbar_wait(&wbars[warp][k], (wseq / S) & 1)) {
+                        wfail = true;
+                        if (lane == 0) atomicExch(a.err, 1);
+                    }
+                    if (wfail) continue;          // the solve stops with an error at the next barrier
+                    ++n_done;
+                    const double zr = row_dot(slot(warp, k), xin, rn.ld, lane, 0, 1);
+                    __syncwarp();                 // every lane is done with the slot
+                    if (lane == 0) {
+                        a.zl[rn.in_off + row] = zr;
+                        issue(k);
+                    }
+                    ++n_issued;
+                }
             }
         }
-        if (threadIdx.x == 0 && n_own > 0) {     // K_h rows of the CM phase into L2
+        if (threadIdx.x == 0 && n_own > 0) {     // K_h rows of the CM phase's first chunk into L2
+            const int64_t pe1 = a.chunk_elem[ch0 + 1];
             const char* lo = reinterpret_cast<const char*>(a.val + (int64_t)a.row_ptr[e0] * NP * NP);
-            const char* hi = reinterpret_cast<const char*>(a.val + (int64_t)a.row_ptr[e1] * NP * NP);
+            const char* hi = reinterpret_cast<const char*>(a.val + (int64_t)a.row_ptr[pe1] * NP * NP);
             for (const char* c = lo; c < hi; c += 65536)
                 prefetch_l2(c, (uint32_t)min((int64_t)65536, (int64_t)(hi - c)));
         }
-        ok = barrier_sum<1>(a.gs, gen, a.err, a.partials, a.bcast, v1);
+        ok = barrier_sum<1>(a.gs, G, cta, gen, a.err, a.partials, v1);
         rr = v1[0];
         it += pending;
         pending = 0;
@@ -513,41 +526,50 @@ pcg_persistent_kernel(PersistArgs a) {
                     const double y = coarse_row(row);
                     if (lane == 0) a.y0[row] = y;
                 }
-                ok = grid_barrier(a.gs, gen, a.err);
+                ok = grid_barrier(a.gs, G, gen, a.err);
                 if (!ok) { status = kEDEVICE; break; }
             }
             __syncthreads();
         }
         // ---------------------------------------------------------------- CM
-        // z = z_loc + R_0^T y0 for own and neighbour elements; w = K z on own elements
-        for (int idx = threadIdx.x; idx < n_need * NP; idx += blockDim.x) {
-            const int l = idx / NP, j = idx - l * NP;
-            const int64_t e = need[l], t = e * NP + j;
-            double v = __ldcg(a.zl + t);
-            if (coarse) {
-                const double* Tr = a.T + t * a.nq;
-                if (a.redundant) {
-                    const double* y = y0l + needj[l] * a.nq;
-                    for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), y[kq], v);
-                } else {
-                    const double* y = a.y0 + (int64_t)a.agg[e] * a.nq;
-                    for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), __ldcg(y + kq), v);
-                }
-            }
-            pn[idx] = v;
-            if (l < n_own) a.z[t] = v;
-        }
-        __syncthreads();
+        // z = z_loc + R_0^T y0 for own and neighbour elements; w = K z on own elements,
+        // chunk by chunk of the CTA's elements
         double v3[3] = {0.0, 0.0, 0.0};           // r.z, z.q_k, z.w
-        local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, e0, e1, [&](int64_t e, int i, double kz) {
-            const int64_t t = e * NP + i;
-            const double zv = pn[(e - e0) * NP + i];
-            a.w[t] = kz;
-            v3[0] = fma(__ldcg(rk + t), zv, v3[0]);
-            v3[1] = fma(zv, __ldcg(qk + t), v3[1]);
-            v3[2] = fma(zv, kz, v3[2]);
-        });
-        ok = barrier_sum<3>(a.gs, gen, a.err, a.partials, a.bcast, v3);
+        for (int ch = ch0; ch < ch1; ++ch) {
+            const int64_t ce0 = a.chunk_elem[ch], ce1 = a.chunk_elem[ch + 1];
+            const int n_chunk = (int)(ce1 - ce0);
+            const int32_t* need = a.need + a.need_ptr[ch];
+            const int32_t* needj = a.need_aggl + a.need_ptr[ch];
+            const int n_need = a.need_ptr[ch + 1] - a.need_ptr[ch];
+            if (ch > ch0) __syncthreads();        // the previous chunk's readers of pn are done
+            for (int idx = threadIdx.x; idx < n_need * NP; idx += blockDim.x) {
+                const int l = idx / NP, j = idx - l * NP;
+                const int64_t e = need[l], t = e * NP + j;
+                double v = __ldcg(a.zl + t);
+                if (coarse) {
+                    const double* Tr = a.T + t * a.nq;
+                    if (a.redundant) {
+                        const double* y = y0l + needj[l] * a.nq;
+                        for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), y[kq], v);
+                    } else {
+                        const double* y = a.y0 + (int64_t)a.agg[e] * a.nq;
+                        for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), __ldcg(y + kq), v);
+                    }
+                }
+                pn[idx] = v;
+                if (l < n_chunk) a.z[t] = v;
+            }
+            __syncthreads();
+            local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, ce0, ce1, [&](int64_t e, int i, double kz) {
+                const int64_t t = e * NP + i;
+                const double zv = pn[(e - ce0) * NP + i];
+                a.w[t] = kz;
+                v3[0] = fma(__ldcg(rk + t), zv, v3[0]);
+                v3[1] = fma(zv, __ldcg(qk + t), v3[1]);
+                v3[2] = fma(zv, kz, v3[2]);
+            });
+        }
+        ok = barrier_sum<3>(a.gs, G, cta, gen, a.err, a.partials, v3);
         if (!ok) { status = kEDEVICE; break; }
         const double rz_new = v3[0], zq = v3[1], zw = v3[2];
         if (!isfinite(rz_new) || !isfinite(zq) || !isfinite(zw)) { status = kENONFINITE; break; }
@@ -568,8 +590,9 @@ pcg_persistent_kernel(PersistArgs a) {
         for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) a.x[t] = 0.0;
     }
     // wait (bounded) for this CTA's copies still in flight before leaving
-    if (!a.identity && nt > 0) {
-        for (uint32_t s2 = seq; s2 < seq + S; ++s2) mbar_wait(&bars[s2 % S], (s2 / S) & 1);
+    if (!a.identity && has_rows) {      // bounded wait for this warp's copies still in flight
+        for (uint32_t c = n_done; c < n_issued; ++c)
+            if (!mbar_wait(&wbars[warp][c % S], (c / S) & 1)) break;
     }
     if (cta == 0 && threadIdx.x == 0) {
         sc->bb = bb;
@@ -582,45 +605,83 @@ pcg_persistent_kernel(PersistArgs a) {
     }
 }
 
-template <int DT>
-static cudaError_t launch_dt(int np, const PersistArgs& a, size_t smem, cudaStream_t s) {
-    void* args[] = {(void*)&a};
-    const void* fn = nullptr;
-    switch (np) {
-        case 3: fn = (const void*)pcg_persistent_kernel<DT, 3>; break;
-        case 6: fn = (const void*)pcg_persistent_kernel<DT, 6>; break;
-        case 10: fn = (const void*)pcg_persistent_kernel<DT, 10>; break;
-        case 15: fn = (const void*)pcg_persistent_kernel<DT, 15>; break;
-        default: return cudaErrorInvalidValue;
+// One solve on all CTAs of the launch.
+template <int DT, int NP>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+pcg_persistent_kernel(const __grid_constant__ PersistArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    pcg_solve_cta<DT, NP>(a, blockIdx.x, gridDim.x, smem);
+}
+
+// Independent solves of several simulations in one launch: CTA b works on
+// simulation map[b].x as its CTA map[b].y of args[map[b].x].grid.  Each group
+// has its own scalars, barrier counter and stopping test, so a simulation that
+// converges early leaves the others undisturbed.
+template <int DT, int NP>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+pcg_batched_kernel(const PersistArgs* __restrict__ args, const int2* __restrict__ map) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(16) PersistArgs sa;
+    const int2 m = map[blockIdx.x];
+    {
+        static_assert(sizeof(PersistArgs) % 8 == 0, "PersistArgs is copied as 8-byte words");
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(args + m.x);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(&sa);
+        for (int k = threadIdx.x; k < (int)(sizeof(PersistArgs) / 8); k += blockDim.x) dst[k] = src[k];
     }
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel(fn, dim3(a.grid), dim3(kPersistThreads), args, smem, s);
+    __syncthreads();
+    pcg_solve_cta<DT, NP>(sa, m.y, (unsigned)sa.grid, smem);
+}
+
+template <int DT>
+static const void* kernel_fn(int np, bool batched) {
+    switch (np) {
+        case 3: return batched ? (const void*)pcg_batched_kernel<DT, 3> : (const void*)pcg_persistent_kernel<DT, 3>;
+        case 6: return batched ? (const void*)pcg_batched_kernel<DT, 6> : (const void*)pcg_persistent_kernel<DT, 6>;
+        case 10: return batched ? (const void*)pcg_batched_kernel<DT, 10> : (const void*)pcg_persistent_kernel<DT, 10>;
+        case 15: return batched ? (const void*)pcg_batched_kernel<DT, 15> : (const void*)pcg_persistent_kernel<DT, 15>;
+        default: return nullptr;
+    }
+}
+
+static const void* pick(int dtype, int np, bool batched) {
+    return dtype == 0 ? kernel_fn<0>(np, batched) : dtype == 1 ? kernel_fn<1>(np, batched)
+                                                              : kernel_fn<2>(np, batched);
 }
 
 cudaError_t launch_pcg_persistent(int dtype, int np, const PersistArgs& a, size_t smem,
                                   cudaStream_t s) {
     if (a.grid > kMaxPartials) return cudaErrorInvalidValue;
-    switch (dtype) {
-        case 0: return launch_dt<0>(np, a, smem, s);
-        case 1: return launch_dt<1>(np, a, smem, s);
-        default: return launch_dt<2>(np, a, smem, s);
-    }
+    const void* fn = pick(dtype, np, false);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&a};
+    return cudaLaunchCooperativeKernel(fn, dim3(a.grid), dim3(kPersistThreads), args, smem, s);
 }
 
-cudaError_t persistent_occupancy(int dtype, int np, size_t smem, int* blocks_per_sm) {
-    const void* fn = nullptr;
-#define PICK(DT)                                                               \
-    switch (np) {                                                              \
-        case 3: fn = (const void*)pcg_persistent_kernel<DT, 3>; break;         \
-        case 6: fn = (const void*)pcg_persistent_kernel<DT, 6>; break;         \
-        case 10: fn = (const void*)pcg_persistent_kernel<DT, 10>; break;       \
-        case 15: fn = (const void*)pcg_persistent_kernel<DT, 15>; break;       \
-        default: return cudaErrorInvalidValue;                                 \
+cudaError_t launch_pcg_batched(int dtype, int np, const PersistArgs* args_dev, const int2* map_dev,
+                               int n_cta, size_t smem, cudaStream_t s) {
+    // the shared-memory limit was raised by persistent_occupancy(.., batched = 1) at set-up
+    // (this launch may be recorded into a CUDA graph)
+    const void* fn = pick(dtype, np, true);
+    if (!fn || n_cta < 1) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&args_dev, (void*)&map_dev};
+    return cudaLaunchCooperativeKernel(fn, dim3(n_cta), dim3(kPersistThreads), args, smem, s);
+}
+
+cudaError_t persistent_occupancy(int dtype, int np, size_t smem, int* blocks_per_sm, int batched) {
+    const void* fn = pick(dtype, np, batched != 0);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (batched) {      // only ever raised, so every batch created earlier can still launch
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+        if ((size_t)fa.maxDynamicSharedSizeBytes < smem)
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    } else {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    if (dtype == 0) { PICK(0) } else if (dtype == 1) { PICK(1) } else { PICK(2) }
-#undef PICK
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kPersistThreads, smem);
 }

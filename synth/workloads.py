@@ -68,6 +68,37 @@ def voronoi4096_p3(n_cells: int = 4096, seed: int = 2, n_parts: int = 64,
                     rtol=1e-8, n_steps=n_steps, stimulus=stimulus_params(seed))
 
 
+def voronoi_batch(n_meshes: int = 8, sims_per_mesh: int = 4, seed: int = 4,
+                  cells: tuple = (1024, 16384), cells_per_subdomain: int = 64,
+                  n_steps: int = 100, p: int = 3) -> list:
+    """Independent simulations of uneven sizes: n_meshes Voronoi meshes (5 Lloyd
+    steps) whose cell counts are log-uniform in [cells[0], cells[1]], each carrying
+    sims_per_mesh simulations that differ in a scalar isotropic conductivity
+    sigma ~ U[0.5, 2] and a stimulus site uniform in [0.1, 0.9]^2; k-means
+    subdomains of about cells_per_subdomain cells = coarse cells; P3, dt = 0.05 ms.
+    Returns a list of n_meshes * sims_per_mesh Workloads (the sims of one mesh
+    share its Mesh and partition objects)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo, hi = np.log(cells[0]), np.log(cells[1])
+    counts = np.rint(np.exp(rng.uniform(lo, hi, n_meshes))).astype(int)
+    out = []
+    for m_id, nc in enumerate(counts):
+        mseed = int(1000 * seed + m_id)
+        mesh = voronoi_square(int(nc), mseed, lloyd=5)
+        parts = max(1, int(round(nc / cells_per_subdomain)))
+        part = kmeans_partition(mesh, parts, mseed)
+        for s_id in range(sims_per_mesh):
+            sig = float(rng.uniform(0.5, 2.0))
+            x0 = 0.1 + 0.8 * rng.random(2)
+            stim = {"x0": float(x0[0]), "y0": float(x0[1]), "amplitude": 250.0,
+                    "width": 0.05, "duration": 1.0}
+            out.append(Workload(f"batch{seed}_m{m_id}_s{s_id}", mesh, p=p, q=1,
+                                sigma=isotropic_conductivity(mesh.n_cells, sig),
+                                subdomain=part, coarse=part, eta0=10.0, dt=0.05,
+                                rtol=1e-8, n_steps=n_steps, stimulus=stim))
+    return out
+
+
 def make_workload(name: str, **kw) -> Workload:
     if name == "square16_p2":
         return square16_p2()
