@@ -6,11 +6,16 @@ Gaussian stimulus), every step solved by PCG with the two-level additive Schwarz
 preconditioner to |r|_2 <= 1e-8 |b|_2 on one GB300.
 
 A "step" is one Crank-Nicolson time step through the C ABI (monodomain_step):
-ionic update at the quadrature nodes, right-hand side, and the persistent PCG
-kernel.  Two forms are timed on the same trajectory setup:
-  * mixed: fp32 local inverses in flexible PCG (fp64 residual, dots, coarse solve
-    and matvec) -- the reported value;
-  * fp64 plain: fp64 local inverses in standard PCG -- reported beside it.
+ionic update at the quadrature nodes, right-hand side, initial guess, and the
+persistent PCG kernel.  By default the 3 warm-up and 197 timed steps together are the
+workload's 200 steps.  Three forms are timed on the same setup:
+  * mixed + learned: fp32 local inverses in flexible PCG (fp64 residual, dots, coarse
+    solve and matvec) with the learned initial guess (the network trained by
+    paper_2512_19536_gb300/guess_train.py on eight other meshes' trajectories, weights in
+    paper_2512_19536_gb300/guess_p3_voronoi4096.npz; kept per step only if its residual
+    is smaller than U^k's) -- the reported value;
+  * mixed: the same with x0 = U^k;
+  * fp64 plain: fp64 local inverses in standard PCG, x0 = U^k.
 The working set (fp32 store 112 MB + K_h 22.5 MB + vectors) exceeds the 126 MB
 L2, so no L2 flush is inserted between steps.
 
@@ -113,10 +118,26 @@ def algorithmic_bytes(ctx_info, pc_info, iterations, launches):
     return iterations * per_it + launches * (k_bytes + 4 * 8 * n)
 
 
-def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clocks=None):
-    pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision=precision)
+GUESS_WEIGHTS = os.path.join(ROOT, "paper_2512_19536_gb300", "guess_p3_voronoi4096.npz")
+
+
+def load_guess(pd):
+    """The trained guess model, or None if its weights file is missing."""
+    import numpy as np
+    if not os.path.exists(GUESS_WEIGHTS):
+        return None
+    z = np.load(GUESS_WEIGHTS)
+    return pd.guess_create(int(z["n_p"]), z["params"], z["scales"])
+
+
+def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clocks=None,
+              guess=None, pc=None):
+    if pc is None:
+        pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision=precision)
     sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-8, maxit=5000,
                         flexible=flexible)
+    if guess is not None:
+        pd.sim_set_guess(sim, guess, 0)
     pd.monodomain_step(sim, warmup, stream)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -135,11 +156,13 @@ def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clo
     return pc, sim, st, ms
 
 
-def time_e2e(pd, torch, w, ctx, pc, steps, stream):
+def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None):
     """Same metric with the potential crossing the host boundary every step: U^k and
     U^{k-1} copied in from pinned host memory, U^{k+1} copied back to pinned host."""
     sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-8, maxit=5000,
                         flexible=True)
+    if guess is not None:
+        pd.sim_set_guess(sim, guess, 0)
     n = ctx.n_dofs
     host_u = torch.empty(n, dtype=torch.float64).pin_memory()
     host_uprev = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -234,7 +257,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=197)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -261,20 +284,25 @@ def main():
                           w.subdomain, w.chi_cm, w.dt, w.eta0)
     peaks, peak_kind = measured_peaks()
 
-    # reported form: mixed precision (fp32 local inverses, flexible PCG)
+    # reported form: mixed precision (fp32 local inverses, flexible PCG) + learned guess
+    guess = load_guess(pd)
     clocks = ClockSampler(local)
     pc, sim, st, ms = time_form(pd, torch, w, ctx, "fp32", True, args.steps, args.warmup,
-                                stream, clocks)
+                                stream, clocks, guess=guess)
+    # the same without the learned guess (x0 = U^k)
+    _, _, st_ng, ms_ng = time_form(pd, torch, w, ctx, "fp32", True, args.steps, args.warmup,
+                                   stream, pc=pc)
     # fp64 plain form on the same workload, for the comparison the metric names
     pc64, sim64, st64, ms64 = time_form(pd, torch, w, ctx, "fp64", False, args.steps,
                                         args.warmup, stream)
-    t = torch.tensor([ms, ms64], dtype=torch.float64, device="cuda")
+    t = torch.tensor([ms, ms64, ms_ng], dtype=torch.float64, device="cuda")
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms, ms64 = float(t[0]), float(t[1])
+    ms, ms64, ms_ng = float(t[0]), float(t[1]), float(t[2])
     value = world * args.steps / (ms * 1e-3)
     value64 = world * args.steps / (ms64 * 1e-3)
-    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, max(5, args.steps // 4), stream)
+    value_ng = world * args.steps / (ms_ng * 1e-3)
+    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, max(5, args.steps // 8), stream, guess)
     if world > 1:
         te = torch.tensor([e2e_val], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MIN)
@@ -305,9 +333,15 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "mixed: fp32 local inverses, flexible PCG "
-                   "(learned initial guess not built; x0 = U^k)",
+        "config": {"workload": WORKLOAD,
+                   "form": ("mixed + learned: fp32 local inverses, flexible PCG, learned initial "
+                            "guess kept when its residual is smaller than U^k's")
+                   if guess is not None else
+                   "mixed: fp32 local inverses, flexible PCG (guess weights file missing; x0 = U^k)",
                    "rtol": 1e-8, "iterations_per_step": st["total_iterations"] / args.steps,
+                   "learned_guess_taken_steps": st.get("guesses_taken", 0),
+                   "mixed_without_guess_steps_per_s": value_ng,
+                   "mixed_without_guess_iterations_per_step": st_ng["total_iterations"] / args.steps,
                    "fp64_plain_steps_per_s": value64,
                    "fp64_plain_iterations_per_step": st64["total_iterations"] / args.steps,
                    "mixed_over_fp64": value / value64,
@@ -316,7 +350,7 @@ def main():
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_val, "unit": "time-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": (9 if guess is not None else 7) * args.steps,
         "roofline": roofline,
         "cpu_baseline": cpu,
     }
