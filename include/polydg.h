@@ -65,6 +65,7 @@ typedef struct asm_ctx asm_ctx;
 typedef struct sim_ctx sim_ctx;
 typedef struct batch_ctx batch_ctx;
 typedef struct guess_model guess_model;
+typedef struct shared_local shared_local;
 
 /* A 2D polygonal mesh (Sec. 3: T_h, disjoint polygons).  Cells are convex
  * polygons given as counter-clockwise vertex loops in CSR form; two cells
@@ -320,6 +321,37 @@ void guess_destroy(guess_model *model);
  *   `stream`.  Returns POLYDG_OK, POLYDG_ENOTSPD (a non-positive pivot; that
  *   matrix's contents are undefined), POLYDG_EINVAL or POLYDG_ECUDA. */
 int polydg_spd_inverse_static(double *mats_dev, int n, int ld, int batch, void *stream);
+
+/* ---- Local solves shared by simulations that differ only in a scalar conductivity.
+ * With Sigma_K = sigma I on every cell the SIP stiffness is linear in sigma (Eq. eta takes
+ * lambda_max(Sigma_K) = sigma, Eq. coer is linear in Sigma), so K_i(sigma) = chi_cm M_i +
+ * (dt sigma/2) A_i(1).  With M_i = L_i L_i^T (per element) and the eigendecomposition
+ * L_i^{-1} A_i(1) L_i^{-T} = Q_i diag(lam_i) Q_i^T, one factorisation gives
+ * K_i(sigma)^{-1} = L_i^{-T} Q_i diag(1/(chi_cm + dt sigma lam_i / 2)) Q_i^T L_i^{-1} for
+ * every sigma, and R simulations' right-hand sides take two passes over Q_i together. */
+
+/* Build the shared factors on the mesh and subdomains of ctx, whose conductivity must be
+ * the same scalar multiple of I on every cell (EINVAL otherwise).  Q_i is stored in
+ * POLYDG_FP32 or POLYDG_BF16; eigendecompositions on the host (polydg_sym_eig), one
+ * thread per hardware thread.  Errors: EINVAL, ENOTSPD, ENOTCONV, ENOMEM, ECUDA. */
+int shared_local_setup(polydg_ctx *ctx, int precision, shared_local **out);
+
+/* Bytes of the stored Q_i^T and Q_i, and the conductivity of the context it was built on. */
+int shared_local_info(const shared_local *sl, int64_t *store_bytes, double *sigma_ref);
+
+/* z_s = sum_i R_i^T K_i(sigmas[s])^{-1} R_i r_s for s < nrhs (1..4): r_dev / z_dev are host
+ * arrays of caller-order device vectors on the mesh of the context. */
+int shared_local_apply(shared_local *sl, int nrhs, const double *const *r_dev,
+                       double *const *z_dev, const double *sigmas, void *stream);
+
+void shared_local_destroy(shared_local *sl);
+
+/* Eigendecomposition of a symmetric n x n host matrix a (row-major; destroyed): the
+ * eigenvalues ascending in w[n], eigenvector k in qt[k*n .. k*n + n) (host arrays).
+ * Householder tridiagonalisation and implicit QR steps with Wilkinson shifts, float64,
+ * on the calling thread.  Used at setup by the shared local solves.  Returns POLYDG_OK,
+ * POLYDG_EINVAL or POLYDG_ENOTCONV. */
+int polydg_sym_eig(int n, double *a, double *w, double *qt);
 
 void sim_destroy(sim_ctx *sim);
 void asm_destroy(asm_ctx *pc);

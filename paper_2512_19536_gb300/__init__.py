@@ -9,11 +9,13 @@ from ._native import (PolyDG, ASM, Simulation, PolyDGError, load, polydg_setup, 
                       asm_apply, pcg_solve, sim_create, monodomain_step, sim_get_state,
                       sim_set_potential, spd_inverse_static, Batch, batch_create, batch_step,
                       GuessModel, guess_n_params, guess_create, guess_propose, guess_train_step,
-                      sim_set_guess, EXPORTS, LIB_PATH, POLYDG_OK, POLYDG_EINVAL, POLYDG_ENOMEM, POLYDG_ECUDA, POLYDG_ENOTSPD, POLYDG_ENOTCONV,
+                      sim_set_guess, SharedLocal, shared_local_setup, shared_local_apply,
+                      EXPORTS, LIB_PATH, POLYDG_OK, POLYDG_EINVAL, POLYDG_ENOMEM, POLYDG_ECUDA, POLYDG_ENOTSPD, POLYDG_ENOTCONV,
                       POLYDG_EBREAKDOWN, POLYDG_ENONFINITE)
 
 __all__ = ["PolyDG", "ASM", "Simulation", "PolyDGError", "load", "polydg_setup", "asm_setup",
            "asm_apply", "pcg_solve", "sim_create", "monodomain_step", "sim_get_state",
            "sim_set_potential", "spd_inverse_static", "Batch", "batch_create", "batch_step",
            "GuessModel", "guess_n_params", "guess_create", "guess_propose", "guess_train_step",
-           "sim_set_guess", "EXPORTS", "LIB_PATH"]
+           "sim_set_guess", "SharedLocal", "shared_local_setup", "shared_local_apply",
+           "EXPORTS", "LIB_PATH"]

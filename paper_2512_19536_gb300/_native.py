@@ -26,7 +26,8 @@ EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_get_info", "polydg_get_f
            "sim_destroy", "asm_destroy", "polydg_destroy", "polydg_spd_inverse_static",
            "batch_create", "batch_get_groups", "batch_step", "batch_destroy", "guess_n_params",
            "guess_create", "guess_get_params", "guess_set_scales", "guess_propose",
-           "guess_train_step", "sim_set_guess", "guess_destroy"]
+           "guess_train_step", "sim_set_guess", "guess_destroy", "polydg_sym_eig",
+           "shared_local_setup", "shared_local_info", "shared_local_apply", "shared_local_destroy"]
 
 
 class polydg_mesh(C.Structure):
@@ -112,6 +113,15 @@ def load() -> C.CDLL:
     L.guess_propose.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.guess_train_step.argtypes = [vp, vp, vp, i64, C.POINTER(C.c_int64), i64, dbl, pd_, vp]
     L.sim_set_guess.argtypes = [vp, vp, i32]
+    L.polydg_sym_eig.argtypes = [i32, pd_, pd_, pd_]
+    L.polydg_sym_eig.restype = i32
+    L.shared_local_setup.argtypes = [vp, i32, C.POINTER(vp)]
+    L.shared_local_info.argtypes = [vp, C.POINTER(C.c_int64), pd_]
+    L.shared_local_apply.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(vp), pd_, vp]
+    for name in ("shared_local_setup", "shared_local_info", "shared_local_apply"):
+        getattr(L, name).restype = i32
+    L.shared_local_destroy.argtypes = [vp]
+    L.shared_local_destroy.restype = None
     for name in ("guess_n_params", "guess_create", "guess_get_params", "guess_set_scales",
                  "guess_propose", "guess_train_step", "sim_set_guess"):
         getattr(L, name).restype = i32
@@ -436,3 +446,51 @@ def sim_set_guess(sim: Simulation, model, policy=0):
     """policy 0: start from the proposal only if its residual is smaller; 1: always."""
     _check(load().sim_set_guess(sim.h, model.h if model is not None else None, int(policy)))
     sim.guess = model
+
+
+def sym_eig(a):
+    """(w, Q) of a symmetric matrix on the host: a = Q diag(w) Q^T, w ascending."""
+    A = np.array(a, dtype=np.float64, order="C", copy=True)
+    n = A.shape[0]
+    w = np.empty(n)
+    qt = np.empty((n, n))
+    _check(load().polydg_sym_eig(int(n), _ptr(A, C.c_double), _ptr(w, C.c_double),
+                                 _ptr(qt, C.c_double)))
+    return w, qt.T.copy()
+
+
+class SharedLocal:
+    """Handle of a shared_local (local solves shared by scalar-conductivity simulations)."""
+
+    def __init__(self, ctx, handle):
+        self.ctx, self.h = ctx, handle
+
+    def info(self):
+        b, sref = C.c_int64(), C.c_double()
+        _check(load().shared_local_info(self.h, C.byref(b), C.byref(sref)))
+        return {"store_bytes": b.value, "sigma_ref": sref.value}
+
+    def close(self):
+        if self.h:
+            load().shared_local_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def shared_local_setup(ctx: PolyDG, precision="fp32") -> SharedLocal:
+    h = C.c_void_p()
+    _check(load().shared_local_setup(ctx.h, PRECISION[precision], C.byref(h)))
+    return SharedLocal(ctx, h)
+
+
+def shared_local_apply(sl: SharedLocal, rs, zs, sigmas, stream=None):
+    n = len(rs)
+    rp = (C.c_void_p * n)(*[_dev(r).value for r in rs])
+    zp = (C.c_void_p * n)(*[_dev(z).value for z in zs])
+    sg = np.ascontiguousarray(sigmas, np.float64)
+    _check(load().shared_local_apply(sl.h, n, rp, zp, _ptr(sg, C.c_double), _stream(stream)))

@@ -59,6 +59,10 @@ void eval_basis(int p, const double* box, double x, double y, double* val, doubl
 void element_rule(const HostSetup& S, int64_t caller_cell, int npts,
                   std::vector<double>& xy, std::vector<double>& w);
 
+// Symmetric eigendecomposition (host): a (n x n, row-major) is destroyed; w ascending,
+// qt[k * n + i] = component i of eigenvector k.  False if the iteration did not converge.
+bool sym_eig(int n, double* a, double* w, double* qt);
+
 // Coarse-space data (Sec. 4) computed on the host for asm_setup.
 struct CoarseSetup {
     int q = 0, n_q = 0, n_agg = 0;

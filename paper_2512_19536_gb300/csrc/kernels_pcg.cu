@@ -87,26 +87,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
-// Block-wide sums of N values at once (results valid in every thread).
-template <int N>
-__device__ __forceinline__ void block_sum_n(double (&v)[N]) {
-    __shared__ double shn[N][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < N; ++k) shn[k][w] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        double t = (lane < nw) ? shn[k][lane] : 0.0;
-        v[k] = warp_sum(t);
-    }
-    __syncthreads();
-}
-
 // Barrier over the G CTAs of one solve (all CTAs of a single-solve launch, or
 // one simulation's CTA group of a batched launch; the launch is cooperative, so
 // all of them are resident).  gs->count starts at 0 for the launch and only
@@ -133,23 +113,49 @@ __device__ bool grid_barrier(GridSync* gs, unsigned G, unsigned& target, int* er
     return ok_sh != 0;
 }
 
-// Grid barrier that also sums N values over all CTAs: every CTA publishes its
-// block sums before the barrier and afterwards adds all CTAs' partials in CTA
-// order, so every CTA obtains the same bit-identical, deterministic sums.
-template <int N>
+// Grid barrier that also sums N <= 3 values over the G CTAs.  Each thread's values go
+// to shared memory and warp 0 alone adds them (the fp64 pipe of this GPU is narrow: a
+// butterfly in all 16 warps would cost 5x more fp64 instructions); the CTA's sums are
+// published, and after the barrier warp 0 adds all G partials in the same order in every
+// CTA, so all CTAs obtain bit-identical, deterministic sums.  fin(sums) then runs in
+// thread 0 alone (scalar updates derived from the sums, written to shared memory) before
+// the closing CTA barrier; every thread returns with the sums in v.
+// red: shared scratch of 3 x blockDim.x doubles, outv: 3 shared doubles.
+template <int N, typename Fin>
 __device__ bool barrier_sum(GridSync* gs, unsigned G, int cta, unsigned& gen, int* err,
-                            double* partials, double (&v)[N]) {
-    block_sum_n<N>(v);
-    if (threadIdx.x == 0)
+                            double* partials, double (&v)[N], double* red, double* outv, Fin&& fin) {
+    static_assert(N >= 1 && N <= 3, "up to three sums");
+    const int t = threadIdx.x, lane = t & 31;
 #pragma unroll
-        for (int k = 0; k < N; ++k) partials[(size_t)k * G + cta] = v[k];
+    for (int k = 0; k < N; ++k) red[k * blockDim.x + t] = v[k];
+    __syncthreads();
+    if (t < 32) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            double s0 = 0.0;
+            for (int i = lane; i < (int)blockDim.x; i += 32) s0 += red[k * blockDim.x + i];
+            s0 = warp_sum(s0);
+            if (lane == 0) partials[(size_t)k * G + cta] = s0;
+        }
+    }
     const bool ok = grid_barrier(gs, G, gen, err);
+    if (t < 32) {
+        double sum[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = 0.0;
-    for (int i = threadIdx.x; i < (int)G; i += blockDim.x)
+        for (int k = 0; k < N; ++k) {
+            double s0 = 0.0;
+            for (int i = lane; i < (int)G; i += 32) s0 += __ldcg(partials + (size_t)k * G + i);
+            sum[k] = warp_sum(s0);
+        }
+        if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < N; ++k) v[k] += __ldcg(partials + (size_t)k * G + i);
-    block_sum_n<N>(v);
+            for (int k = 0; k < N; ++k) outv[k] = sum[k];
+            fin(sum);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = outv[k];
     return ok;
 }
 
@@ -161,7 +167,8 @@ struct StoreType {
 };
 
 // Row dot products from shared memory (row Ar of ld entries, staged input xs),
-// over the column chunks part, part + parts, ... of 32 lanes x vector width.
+// over the column chunks part, part + parts, ... of 32 lanes x vector width.  The
+// fp32/bf16 forms return the sum in lane 0 only.
 __device__ __forceinline__ double row_dot(const double* Ar, const double* xs, int ld, int lane,
                                           int part, int parts) {
     double a0 = 0.0, a1 = 0.0;
@@ -183,7 +190,8 @@ __device__ __forceinline__ double row_dot(const float* Ar, const float* xs, int 
         a0 = fmaf(u.x, v.x, a0); a1 = fmaf(u.y, v.y, a1);
         a0 = fmaf(u.z, v.z, a0); a1 = fmaf(u.w, v.w, a1);
     }
-    return (double)warp_sumf(a0 + a1);
+    const float sum = warp_sumf(a0 + a1);
+    return lane == 0 ? (double)sum : 0.0;   // only lane 0's value is used: one conversion per row
 }
 
 __device__ __forceinline__ double row_dot(const __nv_bfloat16* Ar, const float* xs, int ld, int lane,
@@ -203,7 +211,8 @@ __device__ __forceinline__ double row_dot(const __nv_bfloat16* Ar, const float* 
         f = __bfloat1622float2(h[3]);
         a0 = fmaf(f.x, x1.z, a0); a1 = fmaf(f.y, x1.w, a1);
     }
-    return (double)warp_sumf(a0 + a1);
+    const float sum = warp_sumf(a0 + a1);
+    return lane == 0 ? (double)sum : 0.0;
 }
 
 // What the P phase needs of one run (contiguous rows of one subdomain's local
@@ -269,6 +278,9 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
     using X = typename StoreType<DT>::X;
     constexpr int NW = kPersistThreads / 32;
     __shared__ __align__(8) uint64_t wbars[NW][kMaxWarpStages];
+    __shared__ double scal[3];            // alpha, beta, pq from thread 0
+    __shared__ int scode;                 // thread 0's verdict after a grid sum
+    __shared__ double red[3 * kPersistThreads], outv[3];   // grid-sum scratch
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     PcgScalars* sc = a.sc;
@@ -376,7 +388,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         }
         n_issued = S;
     }
-    bool ok = barrier_sum<2>(a.gs, G, cta, gen, a.err, a.partials, v2);
+    bool ok = barrier_sum<2>(a.gs, G, cta, gen, a.err, a.partials, v2, red, outv, [](const double*) {});
     const double bb = v2[0];
     double rr = v2[1];
     int status = kOK, it = 0, done = 0, par = 0, pp = 0;
@@ -479,17 +491,21 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
             for (const char* c = lo; c < hi; c += 65536)
                 prefetch_l2(c, (uint32_t)min((int64_t)65536, (int64_t)(hi - c)));
         }
-        ok = barrier_sum<1>(a.gs, G, cta, gen, a.err, a.partials, v1);
+        // stopping test by thread 0: 0 go on, 1 converged, 2 non-finite, 3 maxit
+        ok = barrier_sum<1>(a.gs, G, cta, gen, a.err, a.partials, v1, red, outv, [&](const double* sm) {
+            const double r2 = sm[0];
+            scode = !isfinite(r2) ? 2 : (r2 <= rtol2 * bb) ? 1 : (it + pending >= maxit) ? 3 : 0;
+        });
         rr = v1[0];
         it += pending;
         pending = 0;
         par ^= 1;
         pp ^= 1;
-        relres = sqrt(rr / bb);
+        const int code = scode;
         if (!ok) { status = kEDEVICE; break; }
-        if (!isfinite(rr)) { status = kENONFINITE; break; }
-        if (rr <= rtol2 * bb) { status = kOK; break; }
-        if (it >= maxit) { status = kENOTCONV; break; }
+        if (code == 2) { status = kENONFINITE; break; }
+        if (code == 1) { status = kOK; break; }
+        if (code == 3) { status = kENOTCONV; break; }
         const double* rk = a.r[par];              // r_{k+1}
         const double* qk = a.q[pp];               // q_k
         // ---------------------------------------------------------------- coarse
@@ -569,21 +585,29 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 v3[2] = fma(zv, kz, v3[2]);
             });
         }
-        ok = barrier_sum<3>(a.gs, G, cta, gen, a.err, a.partials, v3);
+        // beta, p.q and alpha by thread 0: code 0 go on, 2 non-finite, 4 breakdown
+        ok = barrier_sum<3>(a.gs, G, cta, gen, a.err, a.partials, v3, red, outv, [&](const double* sm) {
+            const double rz_new = sm[0], zq = sm[1], zw = sm[2];
+            if (!isfinite(rz_new) || !isfinite(zq) || !isfinite(zw)) { scode = 2; return; }
+            double bnew;
+            if (it == 0) bnew = 0.0;
+            else if (flexible) bnew = -alpha * zq / rz;   // z_{k+1}.(r_{k+1} - r_k) = -alpha_k z_{k+1}.q_k
+            else bnew = rz_new / rz;
+            const double pq_new = zw + 2.0 * bnew * zq + bnew * bnew * pq;
+            if (!isfinite(bnew) || rz_new == 0.0 || !(pq_new > 0.0) || !isfinite(pq_new)) { scode = 4; return; }
+            scal[0] = rz_new / pq_new;
+            scal[1] = bnew;
+            scal[2] = pq_new;
+            scode = 0;
+        });
         if (!ok) { status = kEDEVICE; break; }
-        const double rz_new = v3[0], zq = v3[1], zw = v3[2];
-        if (!isfinite(rz_new) || !isfinite(zq) || !isfinite(zw)) { status = kENONFINITE; break; }
-        double bnew;
-        if (it == 0) bnew = 0.0;
-        else if (flexible) bnew = -alpha * zq / rz;   // z_{k+1}.(r_{k+1} - r_k) = -alpha_k z_{k+1}.q_k
-        else bnew = rz_new / rz;
-        if (!isfinite(bnew) || rz_new == 0.0) { status = kEBREAKDOWN; break; }
-        const double pq_new = zw + 2.0 * bnew * zq + bnew * bnew * pq;
-        if (!(pq_new > 0.0) || !isfinite(pq_new)) { status = kEBREAKDOWN; break; }
-        beta = bnew;
-        rz = rz_new;
-        pq = pq_new;
-        alpha = rz / pq;
+        const int code3 = scode;
+        if (code3 == 2) { status = kENONFINITE; break; }
+        if (code3 == 4) { status = kEBREAKDOWN; break; }
+        rz = v3[0];
+        alpha = scal[0];
+        beta = scal[1];
+        pq = scal[2];
         pending = 1;
     }
     if (done == 2) {            // b = 0: the solution is x = 0
@@ -595,6 +619,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
             if (!mbar_wait(&wbars[warp][c % S], (c / S) & 1)) break;
     }
     if (cta == 0 && threadIdx.x == 0) {
+        relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
         sc->bb = bb;
         sc->rr = rr;
         sc->relres = relres;

@@ -1,0 +1,363 @@
+// Local solves shared by simulations that differ only in a scalar conductivity.
+//
+// On one mesh and partition with Sigma_K = sigma I, the SIP stiffness is linear in
+// sigma (Eq. eta takes lambda_max(Sigma_K) = sigma; Eq. coer is linear in Sigma), so
+// K_i(sigma) = chi_cm M_i + (dt sigma / 2) A_i with A_i the sigma = 1 stiffness.  With
+// M_i = L_i L_i^T (one Cholesky factor per element) and L_i^{-1} A_i L_i^{-T} =
+// Q_i diag(lam_i) Q_i^T,
+//     K_i(sigma)^{-1} = L_i^{-T} Q_i diag(1 / (chi_cm + c lam_i)) Q_i^T L_i^{-1},  c = dt sigma/2,
+// so one eigenbasis per subdomain serves every simulation on the mesh, and the R
+// right-hand sides of R simulations take two passes over Q_i (as Q_i^T rows, then Q_i
+// rows) instead of R passes over R different inverses.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <thread>
+#include <vector>
+
+#include "contexts.h"
+
+namespace polydg {
+
+struct SharedBlock {
+    int64_t q_off;        // element offset of Q_i^T (n x ld) in the store; Q_i follows
+    int64_t lam_off;      // offset of lam_i
+    int64_t in_off;       // first DOF (internal order)
+    int32_t n, ld, cell0, ncell;
+};
+
+constexpr int kMaxRhs = 4;
+
+struct RhsPtrs {
+    const double* r[kMaxRhs];
+    double* z[kMaxRhs];
+    double c[kMaxRhs];    // dt sigma_s / 2
+};
+
+template <typename T>
+__device__ __forceinline__ float to_f(T v) { return (float)v; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// One CTA per subdomain: X_s = L^{-1} r_s; Y_s = diag(1/(chi + c_s lam)) Q^T X_s;
+// z_s = L^{-T} Q Y_s.  Warp per row of Q^T (pass 1) and of Q (pass 2), R dots per row.
+template <typename T, int R>
+__global__ void __launch_bounds__(512)
+shared_local_apply_kernel(const SharedBlock* __restrict__ blocks, const T* __restrict__ q,
+                          const float* __restrict__ lam, const double* __restrict__ linv, int np,
+                          double chi, RhsPtrs p) {
+    extern __shared__ __align__(16) float sm[];
+    const SharedBlock B = blocks[blockIdx.x];
+    const int n = B.n, ld = B.ld;
+    float* X = sm;                 // [R][ld]
+    float* Y = sm + R * ld;        // [R][ld]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // X_s = L^{-1} r_s, element by element (L^{-1} lower triangular, row-major n_p x n_p)
+    for (int idx = threadIdx.x; idx < R * ld; idx += blockDim.x) {
+        const int s = idx / ld, k = idx - s * ld;
+        float v = 0.f;
+        if (k < n) {
+            const int el = k / np, i = k - el * np;
+            const double* Li = linv + ((int64_t)(B.cell0 + el) * np + i) * np;
+            const double* rs = p.r[s] + B.in_off + (int64_t)el * np;
+            double acc = 0.0;
+            for (int j = 0; j <= i; ++j) acc = fma(Li[j], rs[j], acc);
+            v = (float)acc;
+        }
+        X[idx] = v;
+    }
+    __syncthreads();
+    const T* Qt = q + B.q_off;
+    const T* Qr = Qt + (int64_t)n * ld;
+    const float* lm = lam + B.lam_off;
+    for (int j = warp; j < n; j += nw) {                 // pass 1: rows of Q^T
+        const T* row = Qt + (int64_t)j * ld;
+        float acc[R];
+#pragma unroll
+        for (int s = 0; s < R; ++s) acc[s] = 0.f;
+        for (int k = lane; k < n; k += 32) {
+            const float a = to_f(row[k]);
+#pragma unroll
+            for (int s = 0; s < R; ++s) acc[s] = fmaf(a, X[s * ld + k], acc[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            const float v = warp_sumf(acc[s]);
+            if (lane == 0) Y[s * ld + j] = (float)((double)v / (chi + p.c[s] * (double)lm[j]));
+        }
+    }
+    __syncthreads();
+    for (int k = warp; k < n; k += nw) {                 // pass 2: rows of Q, into X
+        const T* row = Qr + (int64_t)k * ld;
+        float acc[R];
+#pragma unroll
+        for (int s = 0; s < R; ++s) acc[s] = 0.f;
+        for (int j = lane; j < n; j += 32) {
+            const float a = to_f(row[j]);
+#pragma unroll
+            for (int s = 0; s < R; ++s) acc[s] = fmaf(a, Y[s * ld + j], acc[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            const float v = warp_sumf(acc[s]);
+            if (lane == 0) X[s * ld + k] = v;
+        }
+    }
+    __syncthreads();
+    // z_s = L^{-T} V_s: z[i] = sum_{j >= i} Linv[j][i] V[j] per element
+    for (int idx = threadIdx.x; idx < R * n; idx += blockDim.x) {
+        const int s = idx / n, k = idx - s * n;
+        const int el = k / np, i = k - el * np;
+        const double* L0 = linv + (int64_t)(B.cell0 + el) * np * np;
+        const float* V = X + s * ld + el * np;
+        double acc = 0.0;
+        for (int j = i; j < np; ++j) acc = fma(L0[j * np + i], (double)V[j], acc);
+        p.z[s][B.in_off + k] = acc;
+    }
+}
+
+}  // namespace polydg
+
+struct shared_local {
+    polydg_ctx* ctx = nullptr;
+    int precision = POLYDG_FP32;
+    double sigma_ref = 1.0;
+    int n_sub = 0;
+    int64_t max_ld = 0, store_bytes = 0;
+    std::vector<SharedBlock> hblocks;
+    SharedBlock* blocks = nullptr;
+    float* st32 = nullptr;
+    __nv_bfloat16* st16 = nullptr;
+    float* lam = nullptr;
+    double* linv = nullptr;
+    double* tmp[2 * kMaxRhs] = {};      // internal-order r and z of shared_local_apply
+};
+
+namespace polydg {
+
+// lower Cholesky factor of a small SPD matrix and its inverse (row-major n x n)
+static bool small_chol_inv(int n, const double* a, double* linv) {
+    std::vector<double> L(n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double d = a[j * n + j];
+        for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+        if (!(d > 0.0)) return false;
+        L[j * n + j] = std::sqrt(d);
+        for (int i = j + 1; i < n; ++i) {
+            double v = a[i * n + j];
+            for (int k = 0; k < j; ++k) v -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = v / L[j * n + j];
+        }
+    }
+    for (int i = 0; i < n * n; ++i) linv[i] = 0.0;
+    for (int c = 0; c < n; ++c) {                  // solve L x = e_c
+        for (int i = c; i < n; ++i) {
+            double v = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) v -= L[i * n + k] * linv[k * n + c];
+            linv[i * n + c] = v / L[i * n + i];
+        }
+    }
+    return true;
+}
+
+}  // namespace polydg
+
+extern "C" {
+
+int shared_local_setup(polydg_ctx* c, int precision, shared_local** out) {
+    if (!c || !out || (precision != POLYDG_FP32 && precision != POLYDG_BF16)) {
+        set_error("shared_local_setup: need a context, an output pointer and POLYDG_FP32 or POLYDG_BF16");
+        return POLYDG_EINVAL;
+    }
+    *out = nullptr;
+    const HostSetup& H = c->H;
+    const int np = H.n_p;
+    const double s0 = H.sigma[0];
+    for (int64_t k = 0; k < H.nc; ++k) {
+        const double* S = &H.sigma[4 * k];
+        if (S[1] != 0.0 || S[2] != 0.0 || S[0] != S[3] || S[0] != s0) {
+            set_error("shared_local_setup: the conductivity must be the same scalar multiple of I on every cell");
+            return POLYDG_EINVAL;
+        }
+    }
+    shared_local* sl = new shared_local();
+    sl->ctx = c;
+    sl->precision = precision;
+    sl->sigma_ref = s0;
+    sl->n_sub = H.n_sub;
+    auto fail = [&](int code) { shared_local_destroy(sl); return code; };
+    // per element L_K^{-1}
+    std::vector<double> linv((size_t)H.nc * np * np);
+    for (int64_t e = 0; e < H.nc; ++e)
+        if (!small_chol_inv(np, &H.Mblk[(size_t)e * np * np], &linv[(size_t)e * np * np])) {
+            set_error("shared_local_setup: an element mass matrix is not positive definite");
+            return fail(POLYDG_ENOTSPD);
+        }
+    // layout
+    int64_t q_total = 0, lam_total = 0;
+    sl->hblocks.resize(H.n_sub);
+    for (int i = 0; i < H.n_sub; ++i) {
+        SharedBlock& B = sl->hblocks[i];
+        B.cell0 = (int32_t)H.sub_ptr[i];
+        B.ncell = (int32_t)(H.sub_ptr[i + 1] - H.sub_ptr[i]);
+        B.n = B.ncell * np;
+        B.ld = (B.n + 7) / 8 * 8;
+        B.in_off = H.sub_ptr[i] * np;
+        B.q_off = q_total;
+        B.lam_off = lam_total;
+        q_total += 2 * (int64_t)B.n * B.ld;
+        lam_total += B.n;
+        sl->max_ld = std::max<int64_t>(sl->max_ld, B.ld);
+    }
+    const int esz = precision == POLYDG_FP32 ? 4 : 2;
+    sl->store_bytes = q_total * esz;
+    std::vector<float> q32(precision == POLYDG_FP32 ? q_total : 0), lam(lam_total);
+    std::vector<__nv_bfloat16> q16(precision == POLYDG_BF16 ? q_total : 0);
+    // C_i = L^{-1} A_i L^{-T} with A = (K - Kminus) / (dt sigma); eigendecomposition per subdomain
+    const double scale = 1.0 / (H.dt * s0);
+    std::atomic<int> next(0), bad(0);
+    auto work = [&]() {
+        std::vector<double> A, C, w, qt;
+        for (int i = next++; i < H.n_sub; i = next++) {
+            const SharedBlock& B = sl->hblocks[i];
+            const int n = B.n;
+            A.assign((size_t)n * n, 0.0);
+            for (int el = 0; el < B.ncell; ++el) {
+                const int64_t e = B.cell0 + el;
+                for (int32_t bi = H.row_ptr[e]; bi < H.row_ptr[e + 1]; ++bi) {
+                    const int64_t f = H.col[bi];
+                    if (f < B.cell0 || f >= B.cell0 + B.ncell) continue;
+                    const double* Kb = &H.Kval[(size_t)bi * np * np];
+                    const double* Km = &H.Kminus_val[(size_t)bi * np * np];
+                    for (int a = 0; a < np; ++a)
+                        for (int b = 0; b < np; ++b)
+                            A[(size_t)(el * np + a) * n + (f - B.cell0) * np + b] =
+                                (Kb[a * np + b] - Km[a * np + b]) * scale;
+                }
+            }
+            // C = Linv A Linv^T (block diagonal Linv): rows, then columns
+            C.assign((size_t)n * n, 0.0);
+            for (int el = 0; el < B.ncell; ++el) {
+                const double* Li = &linv[(size_t)(B.cell0 + el) * np * np];
+                for (int a = 0; a < np; ++a)
+                    for (int k = 0; k <= a; ++k) {
+                        const double l = Li[a * np + k];
+                        const double* src = &A[(size_t)(el * np + k) * n];
+                        double* dst = &C[(size_t)(el * np + a) * n];
+                        for (int j = 0; j < n; ++j) dst[j] += l * src[j];
+                    }
+            }
+            std::fill(A.begin(), A.end(), 0.0);
+            for (int r = 0; r < n; ++r)
+                for (int el = 0; el < B.ncell; ++el) {
+                    const double* Li = &linv[(size_t)(B.cell0 + el) * np * np];
+                    const double* src = &C[(size_t)r * n + el * np];
+                    double* dst = &A[(size_t)r * n + el * np];
+                    for (int b = 0; b < np; ++b) {
+                        double acc = 0.0;
+                        for (int k = 0; k <= b; ++k) acc += src[k] * Li[b * np + k];
+                        dst[b] = acc;
+                    }
+                }
+            for (int r = 0; r < n; ++r)                   // symmetrise the rounding
+                for (int j = 0; j < r; ++j) {
+                    const double v = 0.5 * (A[(size_t)r * n + j] + A[(size_t)j * n + r]);
+                    A[(size_t)r * n + j] = A[(size_t)j * n + r] = v;
+                }
+            w.resize(n);
+            qt.resize((size_t)n * n);
+            if (!sym_eig(n, A.data(), w.data(), qt.data())) { bad = 1; continue; }
+            for (int j = 0; j < n; ++j) lam[B.lam_off + j] = (float)w[j];
+            const int64_t ldq = B.ld;
+            for (int r = 0; r < n; ++r)
+                for (int k = 0; k < ldq; ++k) {
+                    const double vt = k < n ? qt[(size_t)r * n + k] : 0.0;   // Q^T[r][k]
+                    const double vq = k < n ? qt[(size_t)k * n + r] : 0.0;   // Q[r][k]
+                    const int64_t o1 = B.q_off + (int64_t)r * ldq + k;
+                    const int64_t o2 = B.q_off + (int64_t)n * ldq + (int64_t)r * ldq + k;
+                    if (precision == POLYDG_FP32) { q32[o1] = (float)vt; q32[o2] = (float)vq; }
+                    else { q16[o1] = __float2bfloat16_rn((float)vt); q16[o2] = __float2bfloat16_rn((float)vq); }
+                }
+        }
+    };
+    const int nthr = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), H.n_sub));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nthr; ++t) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+    if (bad) { set_error("shared_local_setup: an eigendecomposition did not converge"); return fail(POLYDG_ENOTCONV); }
+    int st;
+    if ((st = upload(&sl->blocks, sl->hblocks)) || (st = upload(&sl->lam, lam)) || (st = upload(&sl->linv, linv)))
+        return fail(st);
+    if (precision == POLYDG_FP32) { if ((st = upload(&sl->st32, q32))) return fail(st); }
+    else if ((st = upload(&sl->st16, q16))) return fail(st);
+    *out = sl;
+    return POLYDG_OK;
+}
+
+int shared_local_info(const shared_local* sl, int64_t* store_bytes, double* sigma_ref) {
+    if (!sl) { set_error("shared_local_info: null argument"); return POLYDG_EINVAL; }
+    if (store_bytes) *store_bytes = sl->store_bytes;
+    if (sigma_ref) *sigma_ref = sl->sigma_ref;
+    return POLYDG_OK;
+}
+
+int shared_local_apply(shared_local* sl, int nrhs, const double* const* r_dev, double* const* z_dev,
+                       const double* sigmas, void* stream) {
+    if (!sl || nrhs < 1 || nrhs > kMaxRhs || !r_dev || !z_dev || !sigmas) {
+        set_error("shared_local_apply: need 1 <= nrhs <= 4 vectors and conductivities");
+        return POLYDG_EINVAL;
+    }
+    polydg_ctx* c = sl->ctx;
+    const int np = c->H.n_p;
+    const int64_t n = c->H.nc * np;
+    cudaStream_t s = (cudaStream_t)stream;
+    RhsPtrs p = {};
+    for (int k = 0; k < nrhs; ++k) {
+        if (!(sigmas[k] > 0)) { set_error("shared_local_apply: conductivities must be > 0"); return POLYDG_EINVAL; }
+        for (int t = 0; t < 2; ++t)
+            if (!sl->tmp[2 * k + t])
+                if (int st = dalloc(&sl->tmp[2 * k + t], n)) return st;
+        CU(launch_permute(r_dev[k], nullptr, sl->tmp[2 * k], c->d_to_caller, c->H.nc, np, 1, nullptr, s));
+        p.r[k] = sl->tmp[2 * k];
+        p.z[k] = sl->tmp[2 * k + 1];
+        p.c[k] = 0.5 * c->H.dt * sigmas[k];
+    }
+    const size_t smem = 2 * (size_t)kMaxRhs * sl->max_ld * sizeof(float);
+    const unsigned grid = (unsigned)sl->n_sub;
+    const double chi = c->H.chi_cm;
+#define LAUNCH(T, R, Q)                                                                              \
+    {                                                                                                \
+        CU(cudaFuncSetAttribute(shared_local_apply_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        shared_local_apply_kernel<T, R><<<grid, 512, smem, s>>>(sl->blocks, Q, sl->lam, sl->linv, np, chi, p);     \
+    }
+    if (sl->precision == POLYDG_FP32) {
+        switch (nrhs) {
+            case 1: LAUNCH(float, 1, sl->st32) break;
+            case 2: LAUNCH(float, 2, sl->st32) break;
+            case 3: LAUNCH(float, 3, sl->st32) break;
+            default: LAUNCH(float, 4, sl->st32) break;
+        }
+    } else {
+        switch (nrhs) {
+            case 1: LAUNCH(__nv_bfloat16, 1, sl->st16) break;
+            case 2: LAUNCH(__nv_bfloat16, 2, sl->st16) break;
+            case 3: LAUNCH(__nv_bfloat16, 3, sl->st16) break;
+            default: LAUNCH(__nv_bfloat16, 4, sl->st16) break;
+        }
+    }
+#undef LAUNCH
+    CU(cudaGetLastError());
+    for (int k = 0; k < nrhs; ++k)
+        CU(launch_permute(sl->tmp[2 * k + 1], nullptr, z_dev[k], c->d_to_caller, c->H.nc, np, 0, nullptr, s));
+    return POLYDG_OK;
+}
+
+void shared_local_destroy(shared_local* sl) {
+    if (!sl) return;
+    dfree(sl->blocks); dfree(sl->st32); dfree(sl->st16); dfree(sl->lam); dfree(sl->linv);
+    for (auto& t : sl->tmp) dfree(t);
+    delete sl;
+}
+
+}  // extern "C"
