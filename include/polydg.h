@@ -344,6 +344,17 @@ int shared_local_info(const shared_local *sl, int64_t *store_bytes, double *sigm
 int shared_local_apply(shared_local *sl, int nrhs, const double *const *r_dev,
                        double *const *z_dev, const double *sigmas, void *stream);
 
+/* Let batch_step solve this simulation together with the other simulations of the batch
+ * that use the same shared_local: up to four of them run their PCG in lockstep in one CTA
+ * group, every local solve of every subdomain one two-pass sweep over the shared
+ * eigenbasis for all of them (each with its own conductivity, coarse solve, scalars and
+ * stopping test).  The simulation's mesh, subdomains, dt and chi_cm must be those of the
+ * shared_local's context, its conductivity one scalar multiple of I, and its
+ * preconditioner two-level (its coarse part is used; its local inverses are not).  Set it
+ * before batch_create (batch_step refuses a batch whose members changed); NULL detaches.
+ * monodomain_step is unaffected. */
+int sim_set_shared_local(sim_ctx *sim, shared_local *sl);
+
 void shared_local_destroy(shared_local *sl);
 
 /* Eigendecomposition of a symmetric n x n host matrix a (row-major; destroyed): the

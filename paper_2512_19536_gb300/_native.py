@@ -27,7 +27,8 @@ EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_get_info", "polydg_get_f
            "batch_create", "batch_get_groups", "batch_step", "batch_destroy", "guess_n_params",
            "guess_create", "guess_get_params", "guess_set_scales", "guess_propose",
            "guess_train_step", "sim_set_guess", "guess_destroy", "polydg_sym_eig",
-           "shared_local_setup", "shared_local_info", "shared_local_apply", "shared_local_destroy"]
+           "shared_local_setup", "shared_local_info", "shared_local_apply", "shared_local_destroy",
+           "sim_set_shared_local"]
 
 
 class polydg_mesh(C.Structure):
@@ -120,6 +121,8 @@ def load() -> C.CDLL:
     L.shared_local_apply.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(vp), pd_, vp]
     for name in ("shared_local_setup", "shared_local_info", "shared_local_apply"):
         getattr(L, name).restype = i32
+    L.sim_set_shared_local.argtypes = [vp, vp]
+    L.sim_set_shared_local.restype = i32
     L.shared_local_destroy.argtypes = [vp]
     L.shared_local_destroy.restype = None
     for name in ("guess_n_params", "guess_create", "guess_get_params", "guess_set_scales",
@@ -494,3 +497,9 @@ def shared_local_apply(sl: SharedLocal, rs, zs, sigmas, stream=None):
     zp = (C.c_void_p * n)(*[_dev(z).value for z in zs])
     sg = np.ascontiguousarray(sigmas, np.float64)
     _check(load().shared_local_apply(sl.h, n, rp, zp, _ptr(sg, C.c_double), _stream(stream)))
+
+
+def sim_set_shared_local(sim: Simulation, sl):
+    """Solve this simulation in lockstep with the batch's other users of `sl`."""
+    _check(load().sim_set_shared_local(sim.h, sl.h if sl is not None else None))
+    sim.shared = sl

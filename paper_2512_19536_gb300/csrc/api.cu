@@ -132,6 +132,8 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 
     // coarse rows solved redundantly per CTA while that costs little (<= 8k fp64 FMA per CTA);
     // otherwise distributed over the CTAs with one more grid barrier per iteration
     P.redundant = ((int64_t)max_aggs * nq * n0 <= 8192) ? 1 : 0;
+    P.max_need = max_need;
+    P.max_aggs = max_aggs;
     // shared memory: 2 tile buffers, staged r' (store type), r' and q (fp64), z (2 x rows),
     // r0/q0, p of the needed elements
     auto r128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
@@ -868,9 +870,158 @@ static int enqueue_batch_step(batch_ctx* bt, cudaStream_t s) {
         if (int st = enqueue_step_pre(sm, s)) return st;
         CU(cudaMemsetAsync(&sm->work.gs->count, 0, sizeof(unsigned), s));
     }
-    CU(launch_pcg_batched(bt->dtype, bt->np, bt->d_args, bt->d_map, bt->n_cta, bt->smem, s));
+    if (bt->n_cta > 0)
+        CU(launch_pcg_batched(bt->dtype, bt->np, bt->d_args, bt->d_map, bt->n_cta, bt->smem, s));
+    if (bt->g_cta > 0)
+        CU(launch_pcg_groups(bt->gq, bt->np, bt->d_gargs, bt->d_gmap, bt->g_cta, bt->gsmem, s));
     for (sim_ctx* sm : bt->sims)
         if (int st = enqueue_step_post(sm, s)) return st;
+    return POLYDG_OK;
+}
+
+// Cut costs[0..n) into at most G contiguous runs minimising the largest run sum
+// (bisection on the budget); ptr gets G + 1 boundaries (trailing runs empty).
+static std::vector<int32_t> linear_partition(const std::vector<double>& costs, int G) {
+    const int n = (int)costs.size();
+    auto pack = [&](double budget, std::vector<int32_t>* ptr) {
+        int runs = 0, k = 0;
+        while (k < n) {
+            if (ptr) (*ptr)[runs] = k;
+            ++runs;
+            double acc = 0.0;
+            const int first = k;
+            while (k < n && (k == first || acc + costs[k] <= budget)) acc += costs[k++];
+        }
+        return runs;
+    };
+    double lo = 0.0, hi = 0.0;
+    for (double c : costs) hi += c;
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (pack(mid, nullptr) <= G) hi = mid; else lo = mid;
+    }
+    std::vector<int32_t> ptr(G + 1, n);
+    const int used = n ? pack(hi, &ptr) : 0;
+    for (int g = used; g <= G; ++g) ptr[g] = n;
+    return ptr;
+}
+
+// CTAs per unit: one at a time to the unit with the largest cost per CTA.
+static std::vector<int> allocate_ctas(const std::vector<double>& cost, int n_cta) {
+    std::vector<int> g(cost.size(), 1);
+    for (int k = (int)cost.size(); k < n_cta; ++k) {
+        int best = 0;
+        for (int i = 1; i < (int)cost.size(); ++i)
+            if (cost[i] / g[i] > cost[best] / g[best]) best = i;
+        ++g[best];
+    }
+    return g;
+}
+
+// Plan and arguments of a lockstep group with `ctas` CTAs.
+static int build_group(batch_ctx* bt, BatchGroup& gr, GroupArgs& ga) {
+    sim_ctx* s0 = bt->sims[gr.members[0]];
+    polydg_ctx* c = s0->ctx;
+    asm_ctx* pc = s0->pc;
+    shared_local* sl = s0->shared;
+    const HostSetup& H = c->H;
+    const int np = H.n_p, G = gr.ctas, R = (int)gr.members.size();
+    if (int st = build_plan(c, pc, G, gr.plan, 1)) return st;
+    const Plan& P = gr.plan;
+    // whole subdomains per CTA, balanced by the bytes of Q_i^T and Q_i
+    const int esz = sl->precision == POLYDG_FP32 ? 4 : 2;
+    std::vector<double> cost(H.n_sub);
+    for (int i = 0; i < H.n_sub; ++i)
+        cost[i] = 2.0 * sl->hblocks[i].n * sl->hblocks[i].ld * esz + 2.0e-6 * 6.0e12 / c->n_sm;
+    std::vector<int32_t> cta_sub = linear_partition(cost, G);
+    int max_subs = 0;
+    for (int g = 0; g < G; ++g) max_subs = std::max(max_subs, cta_sub[g + 1] - cta_sub[g]);
+    if (2 * max_subs > 128) { set_error("batch_create: more than 64 subdomains per CTA in a group"); return POLYDG_EINVAL; }
+    std::vector<int32_t> pb(H.n_sub), pcnt(H.n_sub);
+    for (int i = 0; i < H.n_sub; ++i) { pb[i] = pc->blocks[i].pair_begin; pcnt[i] = pc->blocks[i].pair_count; }
+    int st;
+    if ((st = upload(&gr.d_cta_sub, cta_sub)) || (st = upload(&gr.d_pair_begin, pb)) ||
+        (st = upload(&gr.d_pair_count, pcnt)))
+        return st;
+    // shared memory: per-warp slots of one row of Q, r' (fp64) and X, Y (fp32) of R
+    // simulations, coarse and chunk staging, run descriptors
+    auto r128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
+    const size_t ldm = (size_t)sl->max_ld;
+    const int nq = pc->has_coarse ? pc->nq : 1;
+    const size_t n0 = pc->has_coarse ? pc->n0 : 0;
+    const size_t fixed = r128(kMaxRhs * ldm * 8) + 2 * r128(kMaxRhs * ldm * 4) + r128(n0 * 8) +
+                         r128((size_t)P.max_aggs * nq * 8) + r128((size_t)P.max_need * np * 8) +
+                         r128(128 * 48);
+    const size_t cap = 208 * 1024, slot = r128(ldm * esz);
+    const int NW = kPersistThreads / 32;
+    const int64_t wst = fixed < cap ? (int64_t)((cap - fixed) / (NW * slot)) : 0;
+    if (wst < 1) { set_error("batch_create: a subdomain is too large for the shared-memory plan of a group"); return POLYDG_EINVAL; }
+    ga = GroupArgs{};
+    ga.grid = G;
+    ga.R = R;
+    ga.wstages = (int)std::min<int64_t>(kMaxWarpStages, wst);
+    ga.n0 = (int)n0;
+    ga.ld0 = pc->has_coarse ? (int)pc->ld0 : 0;
+    ga.nq = nq;
+    ga.redundant = P.redundant;
+    ga.np_ = np;
+    ga.nc = H.nc;
+    ga.slot_bytes = slot;
+    ga.ld_max = ldm;
+    ga.rp_off = (size_t)NW * ga.wstages * slot;
+    ga.x_off = ga.rp_off + r128(kMaxRhs * ldm * 8);
+    ga.y_off = ga.x_off + r128(kMaxRhs * ldm * 4);
+    ga.r0_off = ga.y_off + r128(kMaxRhs * ldm * 4);
+    ga.y0_off = ga.r0_off + r128(n0 * 8);
+    ga.pn_off = ga.y0_off + r128((size_t)P.max_aggs * nq * 8);
+    ga.td_off = ga.pn_off + r128((size_t)P.max_need * np * 8);
+    const size_t smem = ga.td_off + r128(128 * 48);
+    bt->gsmem = std::max(bt->gsmem, smem);
+    ga.row_ptr = c->K.row_ptr;
+    ga.cta_chunk = P.cta_chunk;
+    ga.chunk_elem = P.chunk_elem;
+    ga.need_ptr = P.need_ptr;
+    ga.need = P.need;
+    ga.need_aggl = P.need_aggl;
+    ga.need_agg_ptr = P.need_agg_ptr;
+    ga.need_agg = P.need_agg;
+    ga.col_local = P.col_local;
+    ga.elem_ptr = P.elem_ptr;
+    ga.blocks = pc->d_blocks;
+    ga.sub_pairs = P.sub_pairs;
+    ga.pair_begin = gr.d_pair_begin;
+    ga.pair_count = gr.d_pair_count;
+    ga.st64 = pc->st64;
+    ga.pair_ptr = pc->has_coarse ? pc->d_pair_ptr : c->d_zero_ptr;
+    ga.T = pc->has_coarse ? pc->d_T : nullptr;
+    ga.agg = pc->has_coarse ? pc->d_agg : nullptr;
+    ga.crow_ptr = P.crow_ptr;
+    ga.sblocks = sl->blocks;
+    ga.qstore = sl->precision == POLYDG_FP32 ? (const void*)sl->st32 : (const void*)sl->st16;
+    ga.lam = sl->lam;
+    ga.linv = sl->linv;
+    ga.cta_sub = gr.d_cta_sub;
+    ga.chi = H.chi_cm;
+    for (int k = 0; k < R; ++k) {
+        sim_ctx* sm = bt->sims[gr.members[k]];
+        PcgWork& w = sm->work;
+        GroupSim& g = ga.sim[k];
+        g.val = sm->ctx->K.val;
+        g.K0inv = sm->pc->has_coarse ? sm->pc->st64 + sm->pc->off0 : nullptr;
+        g.c = 0.5 * H.dt * sm->sigma;
+        g.b = w.b;
+        g.x = w.x[0];
+        g.r[0] = w.r[0]; g.r[1] = w.r[1];
+        g.p[0] = w.p; g.p[1] = w.p2;
+        g.q[0] = w.q; g.q[1] = w.q2;
+        g.z = w.z; g.zl = w.zl; g.w = w.w;
+        g.r0p = sm->pc->d_r0p;
+        g.y0 = sm->pc->d_y0;
+        g.sc = w.sc;
+    }
+    ga.partials = s0->work.partials;
+    ga.gs = s0->work.gs;
+    ga.err = s0->work.err;
     return POLYDG_OK;
 }
 
@@ -958,9 +1109,8 @@ int batch_create(sim_ctx* const* sims, int n, batch_ctx** out) {
         if (!sims[i] || !sims[i]->pc) { set_error("batch_create: every simulation needs a preconditioner"); return POLYDG_EINVAL; }
         const sim_ctx* a = sims[i];
         const sim_ctx* b = sims[0];
-        if (a->ctx->device != b->ctx->device || a->ctx->H.n_p != b->ctx->H.n_p ||
-            a->pc->precision != b->pc->precision) {
-            set_error("batch_create: simulations must share the device, the degree and the local precision");
+        if (a->ctx->device != b->ctx->device || a->ctx->H.n_p != b->ctx->H.n_p) {
+            set_error("batch_create: simulations must share the device and the degree");
             return POLYDG_EINVAL;
         }
         for (int j = 0; j < i; ++j)
@@ -969,58 +1119,131 @@ int batch_create(sim_ctx* const* sims, int n, batch_ctx** out) {
                 return POLYDG_EINVAL;
             }
     }
-    const int n_cta = sims[0]->ctx->n_sm;
-    if (n > n_cta) { set_error("batch_create: more simulations than SMs"); return POLYDG_EINVAL; }
     batch_ctx* bt = new batch_ctx();
     bt->sims.assign(sims, sims + n);
-    bt->n_cta = n_cta;
-    bt->dtype = sims[0]->pc->precision;
+    for (int i = 0; i < n; ++i) bt->shared_at_create.push_back(sims[i]->shared);
     bt->np = sims[0]->ctx->H.n_p;
     bt->device = sims[0]->ctx->device;
+    bt->group.assign(n, 0);
     auto fail = [&](int code) { batch_destroy(bt); return code; };
-    // CTAs per simulation: minimise the largest per-CTA share of the bytes one
-    // iteration streams (local inverses + K_h), one CTA at a time to the
-    // simulation whose share is largest
-    std::vector<double> cost(n);
-    for (int i = 0; i < n; ++i) {
-        const sim_ctx* sm = sims[i];
-        const int np = sm->ctx->H.n_p;
-        cost[i] = (double)sm->pc->store_bytes + 8.0 * np * np * (double)sm->ctx->K.nblk +
-                  96.0 * (double)(sm->ctx->H.nc * np);
-    }
-    bt->group.assign(n, 1);
-    for (int k = n; k < n_cta; ++k) {
-        int best = 0;
-        for (int i = 1; i < n; ++i)
-            if (cost[i] / bt->group[i] > cost[best] / bt->group[best]) best = i;
-        ++bt->group[best];
-    }
-    bt->plans.resize(n);
-    std::vector<PersistArgs> args(n);
-    std::vector<int2> map;
+    const int n_sm = sims[0]->ctx->n_sm;
+    // simulations with shared local solves go into lockstep groups of <= kMaxRhs (in order)
     for (int i = 0; i < n; ++i) {
         sim_ctx* sm = sims[i];
-        if (int st = build_plan(sm->ctx, sm->pc, bt->group[i], bt->plans[i], 1)) return fail(st);
-        bt->smem = std::max(bt->smem, bt->plans[i].smem);
-        args[i] = persist_args(sm->ctx, sm->pc, bt->plans[i], sm->work);
-        for (int j = 0; j < bt->group[i]; ++j) map.push_back(make_int2(i, j));
+        if (!sm->shared) { bt->solo.push_back(i); continue; }
+        BatchGroup* g = nullptr;
+        for (auto& gg : bt->groups)
+            if (bt->sims[gg.members[0]]->shared == sm->shared && (int)gg.members.size() < kMaxRhs) g = &gg;
+        if (!g) { bt->groups.emplace_back(); g = &bt->groups.back(); }
+        g->members.push_back(i);
     }
-    int occ = 0;
-    if (persistent_occupancy(bt->dtype, bt->np, bt->smem, &occ, 1) != cudaSuccess || occ < 1) {
-        set_error("batch_create: the batched kernel does not fit on an SM");
-        return fail(POLYDG_ECUDA);
+    if ((int)bt->solo.size() > n_sm || (int)bt->groups.size() > n_sm) {
+        set_error("batch_create: more simulations (or groups) than SMs");
+        return fail(POLYDG_EINVAL);
     }
-    int st;
-    if ((st = upload(&bt->d_args, args))) return fail(st);
-    std::vector<int2> mp(map.begin(), map.end());
-    if ((st = dalloc(&bt->d_map, mp.size()))) return fail(st);
-    if (cudaMemcpy(bt->d_map, mp.data(), mp.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking) != cudaSuccess ||
+    for (auto& g : bt->groups) {
+        const int q = bt->sims[g.members[0]]->shared->precision == POLYDG_FP32 ? 1 : 2;
+        if (bt->gq && bt->gq != q) { set_error("batch_create: shared local solves of one batch need one precision"); return fail(POLYDG_EINVAL); }
+        bt->gq = q;
+    }
+    // solo simulations: the per-simulation launch
+    if (!bt->solo.empty()) {
+        bt->dtype = sims[bt->solo[0]]->pc->precision;
+        std::vector<double> cost;
+        for (int i : bt->solo) {
+            const sim_ctx* sm = sims[i];
+            if (sm->pc->precision != bt->dtype) { set_error("batch_create: simulations must share the local precision"); return fail(POLYDG_EINVAL); }
+            const int np = sm->ctx->H.n_p;
+            cost.push_back((double)sm->pc->store_bytes + 8.0 * np * np * (double)sm->ctx->K.nblk +
+                           96.0 * (double)(sm->ctx->H.nc * np));
+        }
+        const std::vector<int> g = allocate_ctas(cost, n_sm);
+        bt->n_cta = n_sm;
+        bt->plans.resize(bt->solo.size());
+        std::vector<PersistArgs> args(bt->solo.size());
+        std::vector<int2> map;
+        for (size_t k = 0; k < bt->solo.size(); ++k) {
+            sim_ctx* sm = sims[bt->solo[k]];
+            bt->group[bt->solo[k]] = g[k];
+            if (int st = build_plan(sm->ctx, sm->pc, g[k], bt->plans[k], 1)) return fail(st);
+            bt->smem = std::max(bt->smem, bt->plans[k].smem);
+            args[k] = persist_args(sm->ctx, sm->pc, bt->plans[k], sm->work);
+            for (int j = 0; j < g[k]; ++j) map.push_back(make_int2((int)k, j));
+        }
+        int occ = 0;
+        if (persistent_occupancy(bt->dtype, bt->np, bt->smem, &occ, 1) != cudaSuccess || occ < 1) {
+            set_error("batch_create: the batched kernel does not fit on an SM");
+            return fail(POLYDG_ECUDA);
+        }
+        int st;
+        if ((st = upload(&bt->d_args, args)) || (st = upload(&bt->d_map, map))) return fail(st);
+    }
+    // lockstep groups: the group launch
+    if (!bt->groups.empty()) {
+        std::vector<double> cost;
+        for (auto& gr : bt->groups) {
+            const sim_ctx* s0 = bt->sims[gr.members[0]];
+            const int np = s0->ctx->H.n_p;
+            cost.push_back((double)s0->shared->store_bytes +
+                           gr.members.size() * (8.0 * np * np * (double)s0->ctx->K.nblk +
+                                                96.0 * (double)(s0->ctx->H.nc * np)));
+        }
+        const std::vector<int> g = allocate_ctas(cost, n_sm);
+        std::vector<GroupArgs> gargs(bt->groups.size());
+        std::vector<int2> map;
+        for (size_t k = 0; k < bt->groups.size(); ++k) {
+            BatchGroup& gr = bt->groups[k];
+            gr.ctas = g[k];
+            for (int i : gr.members) bt->group[i] = g[k];
+            if (int st = build_group(bt, gr, gargs[k])) return fail(st);
+            for (int j = 0; j < g[k]; ++j) map.push_back(make_int2((int)k, j));
+        }
+        bt->g_cta = n_sm;
+        int occ = 0;
+        if (group_occupancy(bt->gq, bt->np, bt->gsmem, &occ) != cudaSuccess || occ < 1) {
+            set_error("batch_create: the group kernel does not fit on an SM");
+            return fail(POLYDG_ECUDA);
+        }
+        int st;
+        if ((st = upload(&bt->d_gargs, gargs)) || (st = upload(&bt->d_gmap, map))) return fail(st);
+    }
+    if (cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMallocHost((void**)&bt->h_ss, n * sizeof(SimScalars)) != cudaSuccess) {
         set_error("batch_create: CUDA setup failed");
         return fail(POLYDG_ECUDA);
     }
     *out = bt;
+    return POLYDG_OK;
+}
+
+int sim_set_shared_local(sim_ctx* sm, shared_local* sl) {
+    if (!sm) { set_error("sim_set_shared_local: null simulation"); return POLYDG_EINVAL; }
+    if (sl) {
+        const HostSetup& A = sm->ctx->H;
+        const HostSetup& B = sl->ctx->H;
+        if (A.nc != B.nc || A.n_p != B.n_p || A.sub_ptr != B.sub_ptr || A.to_caller != B.to_caller ||
+            A.dt != B.dt || A.chi_cm != B.chi_cm || A.row_ptr != B.row_ptr || A.col != B.col) {
+            set_error("sim_set_shared_local: the simulation's mesh, subdomains or time step differ");
+            return POLYDG_EINVAL;
+        }
+        if (!sm->pc || !sm->pc->has_coarse || !sl->ctx) {
+            set_error("sim_set_shared_local: the simulation needs a two-level preconditioner");
+            return POLYDG_EINVAL;
+        }
+        const double s0 = A.sigma[0];
+        for (int64_t k = 0; k < A.nc; ++k) {
+            const double* S = &A.sigma[4 * k];
+            if (S[1] != 0.0 || S[2] != 0.0 || S[0] != S[3] || S[0] != s0) {
+                set_error("sim_set_shared_local: the simulation's conductivity is not one scalar multiple of I");
+                return POLYDG_EINVAL;
+            }
+        }
+        sm->sigma = s0;
+    }
+    if (sm->shared != sl) {
+        sm->shared = sl;
+        sm->version += 1;
+    }
     return POLYDG_OK;
 }
 
@@ -1035,6 +1258,11 @@ int batch_step(batch_ctx* bt, int nsteps, void* stream, step_stats* per_sim, dou
     if (nsteps < 0) { set_error("batch_step: nsteps < 0"); return POLYDG_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)bt->sims.size();
+    for (int i = 0; i < n; ++i)
+        if (bt->sims[i]->shared != bt->shared_at_create[i]) {
+            set_error("batch_step: a simulation's shared local solves changed since batch_create");
+            return POLYDG_EINVAL;
+        }
     for (int i = 0; i < n; ++i)
         if (int st = reset_step_counters(bt->sims[i], bt->h_ss[i], s)) return st;
     bool stale = !bt->exec;
@@ -1234,7 +1462,8 @@ void batch_destroy(batch_ctx* bt) {
     if (bt->cap) cudaStreamDestroy(bt->cap);
     for (auto e : bt->ev) cudaEventDestroy(e);
     for (auto& P : bt->plans) P.release();
-    dfree(bt->d_args); dfree(bt->d_map);
+    for (auto& g : bt->groups) g.release();
+    dfree(bt->d_args); dfree(bt->d_map); dfree(bt->d_gargs); dfree(bt->d_gmap);
     if (bt->h_ss) cudaFreeHost(bt->h_ss);
     delete bt;
 }

@@ -92,6 +92,7 @@ struct Plan {
     GemvRun* runs = nullptr;
     int64_t* elem_ptr = nullptr;
     double est_seconds = 0.0;           // cost model: slowest CTA's P phase per iteration
+    int max_need = 0, max_aggs = 0;     // staged elements per chunk, agglomerates per CTA
     void release() {
         dfree(run_ptr); dfree(sub_pairs); dfree(crow_ptr); dfree(need_ptr); dfree(need);
         dfree(cta_chunk); dfree(chunk_elem);
@@ -175,6 +176,8 @@ struct sim_ctx {
     PcgWork work;
     guess_model* guess = nullptr;       // learned initial guess (nullptr: x0 = U^k)
     int guess_policy = 0;               // 0: keep the smaller residual, 1: always the proposal
+    shared_local* shared = nullptr;     // local solves shared with other simulations (batches)
+    double sigma = 0.0;                 // its scalar conductivity when `shared` is set
     int64_t version = 0;                // bumped when the step's kernel sequence changes
     double *Uprev2 = nullptr, *xg = nullptr;
     double *U = nullptr, *Uprev = nullptr, *I = nullptr, *F = nullptr, *y = nullptr;
@@ -187,14 +190,49 @@ struct sim_ctx {
 
 // Independent simulations advanced together: one cooperative launch per step in
 // which simulation i owns CTAs [cta_begin[i], cta_begin[i] + group[i]).
+// Local solves shared by simulations whose conductivity is a scalar multiple of I
+// (shared_local.cu): per subdomain Q_i^T and Q_i (fp32 or bf16), lam_i, per element L_K^{-1}.
+struct shared_local {
+    polydg_ctx* ctx = nullptr;
+    int precision = POLYDG_FP32;
+    double sigma_ref = 1.0;
+    int n_sub = 0;
+    int64_t max_ld = 0, store_bytes = 0;
+    std::vector<SharedBlock> hblocks;
+    SharedBlock* blocks = nullptr;
+    float* st32 = nullptr;
+    __nv_bfloat16* st16 = nullptr;
+    float* lam = nullptr;
+    double* linv = nullptr;
+    double* tmp[2 * kMaxRhs] = {};      // internal-order r and z of shared_local_apply
+};
+
+// A lockstep group of a batch: simulations that share one shared_local.
+struct BatchGroup {
+    std::vector<int> members;           // indices into batch_ctx::sims
+    Plan plan;                          // structure of the first member, for `ctas` CTAs
+    int ctas = 0;
+    int32_t *d_cta_sub = nullptr, *d_pair_begin = nullptr, *d_pair_count = nullptr;
+    void release() { plan.release(); dfree(d_cta_sub); dfree(d_pair_begin); dfree(d_pair_count); }
+};
+
 struct batch_ctx {
     std::vector<sim_ctx*> sims;
-    std::vector<Plan> plans;            // per simulation, for its CTA group
-    std::vector<int> group;             // CTAs per simulation
-    PersistArgs* d_args = nullptr;      // [n]
-    int2* d_map = nullptr;              // [n_cta] (simulation, CTA within its group)
+    // simulations with their own local inverses: one launch, a CTA group each
+    std::vector<int> solo;              // indices into sims
+    std::vector<Plan> plans;            // per solo simulation, for its CTA group
+    std::vector<int> group;             // CTAs per simulation (group members: the group's)
+    PersistArgs* d_args = nullptr;      // [solo]
+    int2* d_map = nullptr;              // [n_cta] (solo index, CTA within its group)
     int n_cta = 0, dtype = 0, np = 0, device = 0;
     size_t smem = 0;
+    // lockstep groups of simulations sharing local solves: a second launch
+    std::vector<BatchGroup> groups;
+    std::vector<shared_local*> shared_at_create;   // each simulation's shared local solves
+    GroupArgs* d_gargs = nullptr;
+    int2* d_gmap = nullptr;
+    int g_cta = 0, gq = 0;
+    size_t gsmem = 0;
     cudaStream_t cap = nullptr;         // stream the step is captured on
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

@@ -127,6 +127,70 @@ struct PersistArgs {
 
 constexpr int kMaxWarpStages = 4;              // copy slots per warp in the P phase
 
+// Shared local solves (shared_local.cu): one subdomain's eigenbasis in the store.
+struct SharedBlock {
+    int64_t q_off;        // element offset of Q_i^T (n x ld) in the store; Q_i follows
+    int64_t lam_off;      // offset of lam_i
+    int64_t in_off;       // first DOF (internal order)
+    int32_t n, ld, cell0, ncell;
+};
+
+constexpr int kMaxRhs = 4;                      // simulations sharing one eigenbasis pass
+
+// One simulation of a lockstep group (kernels_group.cu).
+struct GroupSim {
+    const double* val;                         // its K_h blocks
+    const double* K0inv;                       // its coarse inverse
+    double c;                                  // dt sigma / 2
+    const double* b;
+    double* x;
+    double* r[2];
+    double* p[2];
+    double* q[2];
+    double *z, *zl, *w;
+    double *r0p, *y0;
+    PcgScalars* sc;
+};
+
+// Arguments of the lockstep group solve: R <= kMaxRhs simulations on one mesh,
+// partition and coarse space whose local solves share one eigenbasis per subdomain.
+// Structure arrays (matvec chunks, coarse layout, restriction rows) are the first
+// simulation's; values and vectors are per simulation.
+struct GroupArgs {
+    int grid, R, wstages, n0, ld0, nq, redundant, np_;
+    int64_t nc;
+    size_t slot_bytes, rp_off, x_off, y_off, r0_off, y0_off, pn_off, td_off, ld_max;
+    const int32_t* row_ptr;
+    const int32_t* cta_chunk;
+    const int64_t* chunk_elem;
+    const int32_t* need_ptr;
+    const int32_t* need;
+    const int32_t* need_aggl;
+    const int32_t* need_agg_ptr;
+    const int32_t* need_agg;
+    const int32_t* col_local;
+    const int64_t* elem_ptr;
+    const GemvBlock* blocks;                   // first simulation's blocks (RESTRICT rows)
+    const int32_t* sub_pairs;
+    const int32_t* pair_begin;                 // [n_sub] first entry in sub_pairs
+    const int32_t* pair_count;                 // [n_sub]
+    const double* st64;                        // first simulation's fp64 store (rows of R_0)
+    const int64_t* pair_ptr;
+    const double* T;
+    const int32_t* agg;
+    const int32_t* crow_ptr;
+    const SharedBlock* sblocks;
+    const void* qstore;                        // Q_i^T, Q_i (bf16 or fp32)
+    const float* lam;
+    const double* linv;                        // per element L_K^{-1}
+    const int32_t* cta_sub;                    // [grid + 1] subdomains of each CTA
+    double chi;
+    GroupSim sim[kMaxRhs];
+    double* partials;
+    GridSync* gs;
+    int* err;
+};
+
 cudaError_t launch_pcg_persistent(int dtype, int np, const PersistArgs& a, size_t smem,
                                   cudaStream_t s);
 // Several independent solves in one cooperative launch of n_cta CTAs: CTA b runs
@@ -135,6 +199,11 @@ cudaError_t launch_pcg_persistent(int dtype, int np, const PersistArgs& a, size_
 cudaError_t launch_pcg_batched(int dtype, int np, const PersistArgs* args_dev, const int2* map_dev,
                                int n_cta, size_t smem, cudaStream_t s);
 cudaError_t persistent_occupancy(int dtype, int np, size_t smem, int* blocks_per_sm, int batched);
+// Lockstep groups (kernels_group.cu): one cooperative launch of n_cta CTAs, CTA b runs
+// as CTA map[b].y of group map[b].x (args on the device).  qdtype 1 fp32, 2 bf16 store.
+cudaError_t launch_pcg_groups(int qdtype, int np, const GroupArgs* args_dev, const int2* map_dev,
+                              int n_cta, size_t smem, cudaStream_t s);
+cudaError_t group_occupancy(int qdtype, int np, size_t smem, int* blocks_per_sm);
 
 cudaError_t launch_matvec(int mode, int np, const DeviceMatrix& K, const double* val,
                           const double* x, double* y, const double* v1, const double* v2,

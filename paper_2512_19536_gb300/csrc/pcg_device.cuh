@@ -96,29 +96,33 @@ __device__ __forceinline__ bool grid_barrier(GridSync* gs, unsigned G, unsigned&
     return ok_sh != 0;
 }
 
-// Grid barrier that also sums N <= 3 values over the G CTAs.  Each thread's values go
+// Grid barrier that also sums N <= 12 values over the G CTAs.  Each thread's values go
 // to shared memory and warp 0 alone adds them (the fp64 pipe of this GPU is narrow: a
 // butterfly in all 16 warps would cost 5x more fp64 instructions); the CTA's sums are
 // published, and after the barrier warp 0 adds all G partials in the same order in every
 // CTA, so all CTAs obtain bit-identical, deterministic sums.  fin(sums) then runs in
 // thread 0 alone (scalar updates derived from the sums, written to shared memory) before
 // the closing CTA barrier; every thread returns with the sums in v.
-// red: shared scratch of 3 x blockDim.x doubles, outv: 3 shared doubles.
+// red: shared scratch of 3 x blockDim.x doubles, outv: N shared doubles.
 template <int N, typename Fin>
 __device__ __forceinline__ bool barrier_sum(GridSync* gs, unsigned G, int cta, unsigned& gen, int* err,
                             double* partials, double (&v)[N], double* red, double* outv, Fin&& fin) {
-    static_assert(N >= 1 && N <= 3, "up to three sums");
+    static_assert(N >= 1 && N <= 12, "up to twelve sums (three at a time through red)");
     const int t = threadIdx.x, lane = t & 31;
 #pragma unroll
-    for (int k = 0; k < N; ++k) red[k * blockDim.x + t] = v[k];
-    __syncthreads();
-    if (t < 32) {
+    for (int c0 = 0; c0 < N; c0 += 3) {
+        if (c0 > 0) __syncthreads();              // warp 0 is done with the previous three
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-            double s0 = 0.0;
-            for (int i = lane; i < (int)blockDim.x; i += 32) s0 += red[k * blockDim.x + i];
-            s0 = warp_sum(s0);
-            if (lane == 0) partials[(size_t)k * G + cta] = s0;
+        for (int k = c0; k < N && k < c0 + 3; ++k) red[(k - c0) * blockDim.x + t] = v[k];
+        __syncthreads();
+        if (t < 32) {
+#pragma unroll
+            for (int k = c0; k < N && k < c0 + 3; ++k) {
+                double s0 = 0.0;
+                for (int i = lane; i < (int)blockDim.x; i += 32) s0 += red[(k - c0) * blockDim.x + i];
+                s0 = warp_sum(s0);
+                if (lane == 0) partials[(size_t)k * G + cta] = s0;
+            }
         }
     }
     const bool ok = grid_barrier(gs, G, gen, err);

@@ -19,15 +19,6 @@
 
 namespace polydg {
 
-struct SharedBlock {
-    int64_t q_off;        // element offset of Q_i^T (n x ld) in the store; Q_i follows
-    int64_t lam_off;      // offset of lam_i
-    int64_t in_off;       // first DOF (internal order)
-    int32_t n, ld, cell0, ncell;
-};
-
-constexpr int kMaxRhs = 4;
-
 struct RhsPtrs {
     const double* r[kMaxRhs];
     double* z[kMaxRhs];
@@ -117,21 +108,6 @@ shared_local_apply_kernel(const SharedBlock* __restrict__ blocks, const T* __res
 }
 
 }  // namespace polydg
-
-struct shared_local {
-    polydg_ctx* ctx = nullptr;
-    int precision = POLYDG_FP32;
-    double sigma_ref = 1.0;
-    int n_sub = 0;
-    int64_t max_ld = 0, store_bytes = 0;
-    std::vector<SharedBlock> hblocks;
-    SharedBlock* blocks = nullptr;
-    float* st32 = nullptr;
-    __nv_bfloat16* st16 = nullptr;
-    float* lam = nullptr;
-    double* linv = nullptr;
-    double* tmp[2 * kMaxRhs] = {};      // internal-order r and z of shared_local_apply
-};
 
 namespace polydg {
 
