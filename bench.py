@@ -24,11 +24,13 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 Under torchrun (N > 1) every rank runs an independent replica (the path has no
 exchange step); rank 0 prints one JSON line with the whole-job throughput.
 
---workload batch32 times the batched form instead: 32 independent simulations on 8
+--workload batch32 times the batched forms instead: 32 independent simulations on 8
 Voronoi meshes of 1024-16384 cells (log-uniform), 4 per mesh with scalar
-conductivities U[0.5, 2] and random stimulus sites, all solves of a step in one
-batched persistent launch (mixed precision), against the same simulations stepped one
-after another in fp64 plain form; the unit is simulation-steps/s.
+conductivities U[0.5, 2] and random stimulus sites.  Reported: the 4 simulations of each
+mesh in lockstep sharing one bf16 eigenbasis of every subdomain (all solves of a step in
+one persistent launch); beside it the batched form with each simulation's own fp32
+inverses and the fp64 plain form stepped one simulation after another; the unit is
+simulation-steps/s.
 """
 import argparse
 import json
@@ -362,11 +364,13 @@ def main():
 
 
 def bench_batch(args, pd, torch, stream, rank, world, local):
-    """Batched form: simulation-steps/s of 32 simulations of uneven sizes."""
+    """Batched forms: simulation-steps/s of 32 simulations of uneven sizes."""
     import numpy as np
     from synth import voronoi_batch
     ws = voronoi_batch()
     peaks, peak_kind = measured_peaks()
+    S = len(ws)
+    per_mesh = 4
 
     def make(prec, flex):
         out = []
@@ -378,29 +382,53 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
                                                rtol=1e-8, maxit=5000, flexible=flex)))
         return out
 
-    S = len(ws)
+    def timed_batch(trip, clocks=None):
+        sims = [x[2] for x in trip]
+        bt = pd.batch_create(sims)
+        pd.batch_step(bt, args.warmup, stream)
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if clocks is not None:
+            clocks.__enter__()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st, sec = pd.batch_step(bt, args.steps, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if clocks is not None:
+            clocks.__exit__(None, None, None)
+        return bt, st, sec, ev0.elapsed_time(ev1)
+
+    # candidate: one bf16 eigenbasis per mesh shared by its 4 simulations (lockstep groups)
     trip = make("fp32", True)
-    sims = [x[2] for x in trip]
-    bt = pd.batch_create(sims)
-    pd.batch_step(bt, args.warmup, stream)
-    if torch.distributed.is_initialized():
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    shared = []
+    for m0 in range(0, S, per_mesh):
+        sl = pd.shared_local_setup(trip[m0][0], "bf16")
+        shared.append(sl)
+        for k in range(m0, m0 + per_mesh):
+            pd.sim_set_shared_local(trip[k][2], sl)
+    t_eig = time.perf_counter() - t0
     clocks = ClockSampler(local)
-    clocks.__enter__()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    st, sec = pd.batch_step(bt, args.steps, stream)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    clocks.__exit__(None, None, None)
-    ms = ev0.elapsed_time(ev1)
-    # algorithmic bytes of all solves over the device time of the whole batched steps
+    bt, st, sec, ms = timed_batch(trip, clocks)
+    its = [s_["total_iterations"] / args.steps for s_ in st]
+    # algorithmic bytes: per group iteration the shared store once plus every member's K_h,
+    # coarse and vectors; group iterations >= the largest member's
     alg = 0.0
-    for (ctx, pc, _), s_ in zip(trip, st):
-        alg += algorithmic_bytes(ctx.info, pc.info(), s_["total_iterations"], s_["steps_done"])
+    for g, sl in enumerate(shared):
+        mem = range(g * per_mesh, (g + 1) * per_mesh)
+        g_its = max(st[k]["total_iterations"] for k in mem)
+        per_it = sl.info()["store_bytes"]
+        for k in mem:
+            ctx, pc, _ = trip[k]
+            inf = pc.info()
+            per_it += (8 * ctx.info.n_p ** 2 * ctx.info.n_blocks + inf["coarse_bytes"]
+                       + inf["restrict_bytes"] + 12 * 8 * ctx.n_dofs)
+        alg += g_its * per_it
     achieved = alg / (sec * 1e9)
     # e2e: every simulation's potential through pinned host memory each step
+    sims = [x[2] for x in trip]
     n_all = sum(ctx.n_dofs for ctx, _, _ in trip)
     hu = [torch.empty(ctx.n_dofs, dtype=torch.float64).pin_memory() for ctx, _, _ in trip]
     du = [torch.empty(ctx.n_dofs, dtype=torch.float64, device="cuda") for ctx, _, _ in trip]
@@ -420,16 +448,23 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
             h_.copy_(d_, non_blocking=True)
         torch.cuda.synchronize()
     e2e_val = world * S * e_steps / (time.perf_counter() - t0)
-    its = [s_["total_iterations"] / args.steps for s_ in st]
     groups = bt.groups().tolist()
     bt.close()
-    del trip, sims
+    del trip, sims, shared, du, hu
     torch.cuda.empty_cache()
-    # baseline: the same simulations in fp64 plain form, one simulation after another
+    # the same simulations with their own fp32 local inverses, one CTA group each
+    trip32 = make("fp32", True)
+    bt32, st32, _, ms32 = timed_batch(trip32)
+    its32 = [s_["total_iterations"] / args.steps for s_ in st32]
+    bt32.close()
+    del trip32
+    torch.cuda.empty_cache()
+    # baseline: fp64 plain form, one simulation after another
     trip64 = make("fp64", False)
     for _, _, s_ in trip64:
         pd.monodomain_step(s_, args.warmup, stream)
     torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     its64 = []
     for _, _, s_ in trip64:
@@ -437,11 +472,12 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
     ev1.record(stream)
     torch.cuda.synchronize()
     ms64 = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms, ms64], dtype=torch.float64, device="cuda")
+    t = torch.tensor([ms, ms32, ms64], dtype=torch.float64, device="cuda")
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms, ms64 = float(t[0]), float(t[1])
+    ms, ms32, ms64 = float(t[0]), float(t[1]), float(t[2])
     value = world * S * args.steps / (ms * 1e-3)
+    value32 = world * S * args.steps / (ms32 * 1e-3)
     value64 = world * S * args.steps / (ms64 * 1e-3)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -458,14 +494,20 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
         "metric": METRIC + " (batched form)", "value": value, "unit": "simulation-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD, "form": "batched: one persistent launch per step "
-                   "for all 32 solves (fp32 local inverses, flexible PCG), captured step graph",
-                   "cells": [w.mesh.n_cells for w in ws[::4]], "dofs": n_all,
+        "vs_baseline": None, "dtype": "f64+f32+bf16", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD,
+                   "form": "batched + shared eigenbasis: the 4 simulations of each mesh solve in "
+                           "lockstep, each subdomain's local solves one bf16 pass over Q_i^T and "
+                           "one over Q_i for all 4 (flexible PCG, fp64 residual/dots/coarse/matvec); "
+                           "one persistent launch per step, captured step graph",
+                   "cells": [w.mesh.n_cells for w in ws[::per_mesh]], "dofs": n_all,
                    "ctas_per_sim": groups, "iterations_per_step": its,
+                   "eigenbasis_setup_s": t_eig,
+                   "batched_fp32_inverses_sim_steps_per_s": value32,
+                   "batched_fp32_inverses_iterations_per_step": its32,
                    "fp64_plain_per_sim_launches_sim_steps_per_s": value64,
                    "fp64_plain_iterations_per_step": its64,
-                   "batched_over_fp64_plain": value / value64,
+                   "shared_over_fp64_plain": value / value64,
                    "l2": "working set > L2 (no flush needed)", "parallelism": f"replicas x{world}"},
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_val, "unit": "simulation-steps/s",
@@ -473,7 +515,7 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
         "gpu_launches": (6 * S + 1) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "kernel": "pcg_batched_kernel<fp32 store, n_p=10> (whole step time)",
+                     "kernel": "pcg_group_kernel<bf16 store, n_p=10> (whole step time)",
                      "peak_kind": peak_kind},
         "cpu_baseline": cpu,
     }
