@@ -928,21 +928,48 @@ static int build_group(batch_ctx* bt, BatchGroup& gr, GroupArgs& ga) {
     const int np = H.n_p, G = gr.ctas, R = (int)gr.members.size();
     if (int st = build_plan(c, pc, G, gr.plan, 1)) return st;
     const Plan& P = gr.plan;
-    // whole subdomains per CTA, balanced by the bytes of Q_i^T and Q_i
+    // element-aligned pieces of subdomains per CTA: tiles of two elements' rows, costed by
+    // the bytes of Q_i^T and Q_i they stream, split into G contiguous runs of equal cost
     const int esz = sl->precision == POLYDG_FP32 ? 4 : 2;
-    std::vector<double> cost(H.n_sub);
-    for (int i = 0; i < H.n_sub; ++i)
-        cost[i] = 2.0 * sl->hblocks[i].n * sl->hblocks[i].ld * esz + 2.0e-6 * 6.0e12 / c->n_sm;
-    std::vector<int32_t> cta_sub = linear_partition(cost, G);
-    int max_subs = 0;
-    for (int g = 0; g < G; ++g) max_subs = std::max(max_subs, cta_sub[g + 1] - cta_sub[g]);
-    if (2 * max_subs > 128) { set_error("batch_create: more than 64 subdomains per CTA in a group"); return POLYDG_EINVAL; }
+    struct QT { int sub, r0, r1; };
+    std::vector<QT> qt;
+    std::vector<double> cost;
+    const double bw_sm = 6.0e12 / c->n_sm;
+    for (int i = 0; i < H.n_sub; ++i) {
+        const SharedBlock& B = sl->hblocks[i];
+        for (int r0 = 0; r0 < B.n; r0 += 2 * np) {
+            const int r1 = std::min(B.n, r0 + 2 * np);
+            qt.push_back({i, r0, r1});
+            cost.push_back(2.0 * (r1 - r0) * B.ld * esz / bw_sm + 0.2e-6 + (r0 == 0 ? 3.0e-6 : 0.0));
+        }
+    }
+    const std::vector<int32_t> tptr = linear_partition(cost, G);
+    std::vector<GemvRun> pieces;
+    std::vector<int32_t> piece_ptr(G + 1, 0);
+    for (int g = 0; g < G; ++g) {
+        piece_ptr[g] = (int32_t)pieces.size();
+        for (int32_t k = tptr[g]; k < tptr[g + 1]; ++k) {
+            if ((int32_t)pieces.size() > piece_ptr[g] && pieces.back().block == qt[k].sub &&
+                pieces.back().row_end == qt[k].r0)
+                pieces.back().row_end = qt[k].r1;
+            else
+                pieces.push_back({qt[k].sub, qt[k].r0, qt[k].r1, 0});
+        }
+        if ((int32_t)pieces.size() - piece_ptr[g] > 64) {
+            set_error("batch_create: more than 64 subdomain pieces per CTA in a group");
+            return POLYDG_EINVAL;
+        }
+    }
+    piece_ptr[G] = (int32_t)pieces.size();
     std::vector<int32_t> pb(H.n_sub), pcnt(H.n_sub);
     for (int i = 0; i < H.n_sub; ++i) { pb[i] = pc->blocks[i].pair_begin; pcnt[i] = pc->blocks[i].pair_count; }
     int st;
-    if ((st = upload(&gr.d_cta_sub, cta_sub)) || (st = upload(&gr.d_pair_begin, pb)) ||
-        (st = upload(&gr.d_pair_count, pcnt)))
+    if ((st = upload(&gr.d_pieces, pieces)) || (st = upload(&gr.d_piece_ptr, piece_ptr)) ||
+        (st = upload(&gr.d_pair_begin, pb)) || (st = upload(&gr.d_pair_count, pcnt)))
         return st;
+    gr.yq.assign(R, nullptr);
+    for (int k = 0; k < R; ++k)
+        if ((st = dalloc(&gr.yq[k], (size_t)H.nc * np))) return st;
     // shared memory: per-warp slots of one row of Q, r' (fp64) and X, Y (fp32) of R
     // simulations, coarse and chunk staging, run descriptors
     auto r128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
@@ -950,8 +977,7 @@ static int build_group(batch_ctx* bt, BatchGroup& gr, GroupArgs& ga) {
     const int nq = pc->has_coarse ? pc->nq : 1;
     const size_t n0 = pc->has_coarse ? pc->n0 : 0;
     const size_t fixed = r128(kMaxRhs * ldm * 8) + 2 * r128(kMaxRhs * ldm * 4) + r128(n0 * 8) +
-                         r128((size_t)P.max_aggs * nq * 8) + r128((size_t)P.max_need * np * 8) +
-                         r128(128 * 48);
+                         r128((size_t)P.max_need * np * 8) + r128(128 * 48);
     const size_t cap = 208 * 1024, slot = r128(ldm * esz);
     const int NW = kPersistThreads / 32;
     const int64_t wst = fixed < cap ? (int64_t)((cap - fixed) / (NW * slot)) : 0;
@@ -973,7 +999,7 @@ static int build_group(batch_ctx* bt, BatchGroup& gr, GroupArgs& ga) {
     ga.y_off = ga.x_off + r128(kMaxRhs * ldm * 4);
     ga.r0_off = ga.y_off + r128(kMaxRhs * ldm * 4);
     ga.y0_off = ga.r0_off + r128(n0 * 8);
-    ga.pn_off = ga.y0_off + r128((size_t)P.max_aggs * nq * 8);
+    ga.pn_off = ga.y0_off;
     ga.td_off = ga.pn_off + r128((size_t)P.max_need * np * 8);
     const size_t smem = ga.td_off + r128(128 * 48);
     bt->gsmem = std::max(bt->gsmem, smem);
@@ -1000,7 +1026,8 @@ static int build_group(batch_ctx* bt, BatchGroup& gr, GroupArgs& ga) {
     ga.qstore = sl->precision == POLYDG_FP32 ? (const void*)sl->st32 : (const void*)sl->st16;
     ga.lam = sl->lam;
     ga.linv = sl->linv;
-    ga.cta_sub = gr.d_cta_sub;
+    ga.pieces = gr.d_pieces;
+    ga.piece_ptr = gr.d_piece_ptr;
     ga.chi = H.chi_cm;
     for (int k = 0; k < R; ++k) {
         sim_ctx* sm = bt->sims[gr.members[k]];
@@ -1017,6 +1044,7 @@ static int build_group(batch_ctx* bt, BatchGroup& gr, GroupArgs& ga) {
         g.z = w.z; g.zl = w.zl; g.w = w.w;
         g.r0p = sm->pc->d_r0p;
         g.y0 = sm->pc->d_y0;
+        g.yq = gr.yq[k];
         g.sc = w.sc;
     }
     ga.partials = s0->work.partials;

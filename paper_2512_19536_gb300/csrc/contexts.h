@@ -212,8 +212,13 @@ struct BatchGroup {
     std::vector<int> members;           // indices into batch_ctx::sims
     Plan plan;                          // structure of the first member, for `ctas` CTAs
     int ctas = 0;
-    int32_t *d_cta_sub = nullptr, *d_pair_begin = nullptr, *d_pair_count = nullptr;
-    void release() { plan.release(); dfree(d_cta_sub); dfree(d_pair_begin); dfree(d_pair_count); }
+    int32_t *d_piece_ptr = nullptr, *d_pair_begin = nullptr, *d_pair_count = nullptr;
+    GemvRun* d_pieces = nullptr;
+    std::vector<float*> yq;             // per member: pass-1 output (one float per DOF)
+    void release() {
+        plan.release(); dfree(d_piece_ptr); dfree(d_pair_begin); dfree(d_pair_count); dfree(d_pieces);
+        for (auto& y : yq) dfree(y);
+    }
 };
 
 struct batch_ctx {

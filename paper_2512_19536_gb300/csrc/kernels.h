@@ -149,6 +149,7 @@ struct GroupSim {
     double* q[2];
     double *z, *zl, *w;
     double *r0p, *y0;
+    float* yq;                                 // Q^T X of its subdomains (pass 1 -> pass 2)
     PcgScalars* sc;
 };
 
@@ -183,7 +184,8 @@ struct GroupArgs {
     const void* qstore;                        // Q_i^T, Q_i (bf16 or fp32)
     const float* lam;
     const double* linv;                        // per element L_K^{-1}
-    const int32_t* cta_sub;                    // [grid + 1] subdomains of each CTA
+    const GemvRun* pieces;                     // (subdomain, element-aligned row range) per CTA
+    const int32_t* piece_ptr;                  // [grid + 1]
     double chi;
     GroupSim sim[kMaxRhs];
     double* partials;

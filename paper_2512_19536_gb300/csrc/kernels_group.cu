@@ -2,13 +2,18 @@
 // and whose conductivities are scalar multiples of the identity (Sec. 4, Eq. prec), with
 // the local solves of every subdomain taken from one shared eigenbasis:
 //     K_i(sigma_s)^{-1} = L_i^{-T} Q_i diag(1 / (chi_cm + c_s lam_i)) Q_i^T L_i^{-1}.
-// One CTA group runs the R solves at once.  The iteration is the two-phase one of
-// kernels_pcg.cu, done for every simulation still solving; the P phase works on whole
-// subdomains: stage r'_s and commit the updates of every simulation, X_s = L^{-1} r'_s,
-// then stream the rows of Q_i^T (pass 1: Y_s = D_s Q_i^T X_s, R dot products per row)
-// and of Q_i (pass 2: V_s = Q_i Y_s) through per-warp copy rings, and z_loc,s =
-// L^{-T} V_s.  Each simulation keeps its own scalars and stopping test; one that has
-// converged drops out of the work while the others go on.
+// One CTA group runs the R solves at once; each CTA owns element-aligned row ranges
+// ("pieces") of subdomains.  Per iteration:
+//   P1  per piece: stage r'_s of the whole subdomain, commit the piece's rows of every
+//       simulation, X_s = L^{-1} r'_s, R_0 r'_s (piece at row 0), pass 1 over the piece's
+//       rows of Q_i^T: Y_s = D_s Q_i^T X_s (R dot products per streamed row) -> global
+//                                                        -> barrier, |r'|^2, tests
+//   P2  per piece: pass 2 over its rows of Q_i with the whole subdomain's Y_s, z_loc,s =
+//       L^{-T} V_s; the coarse solves                    -> barrier
+//   CM  z = z_loc + R_0^T y0, w = K_s z, dots per simulation   -> barrier, beta, alpha
+// The rows stream through per-warp copy rings prefetched across phases and iterations.
+// Each simulation keeps its own scalars and stopping test; one that has converged or
+// failed drops out of the work while the others go on.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -74,50 +79,58 @@ __device__ __forceinline__ void add_at(double (&v)[N], int s, double x) {
         if (k == s) v[k] += x;
 }
 
+// Per-simulation scalars of a group, uniform over the CTA: kept in shared memory
+// (thread 0 writes them between CTA barriers) rather than replicated in registers.
+struct GroupScalars {
+    double alpha[kMaxRhs], beta[kMaxRhs], rz[kMaxRhs], pq[kMaxRhs], bb[kMaxRhs], rr[kMaxRhs];
+    double rtol2[kMaxRhs];
+    int it[kMaxRhs], pending[kMaxRhs], status[kMaxRhs], maxit[kMaxRhs], flex[kMaxRhs];
+    int live, started;
+};
+
 template <typename T, int NP>
 __device__ __forceinline__ void pcg_group_cta(const GroupArgs& a, const int cta, const unsigned G,
                                               unsigned char* smem) {
     constexpr int NW = kPersistThreads / 32;
     constexpr int MR = kMaxRhs;
     __shared__ __align__(8) uint64_t wbars[NW][kMaxWarpStages];
-    __shared__ double scal[3 * MR];        // alpha, beta, pq per simulation from thread 0
-    __shared__ int scode[MR];
+    __shared__ GroupScalars gsc;
     __shared__ double red[3 * kPersistThreads], outv[3 * MR];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int R = a.R;
-    int live = 0;                          // simulations still solving (uniform over the group)
-    for (int s = 0; s < R; ++s)
-        if (!a.sim[s].sc->done) live |= 1 << s;
-    if (!live) return;
-    const int started = live;
-    bool flex[MR];
-    double rtol2[MR];
-    int maxit[MR];
-#pragma unroll
-    for (int s = 0; s < MR; ++s) {
-        flex[s] = s < R && a.sim[s].sc->flexible != 0;
-        rtol2[s] = s < R ? a.sim[s].sc->rtol2 : 0.0;
-        maxit[s] = s < R ? a.sim[s].sc->maxit : 0;
+    if (threadIdx.x == 0) {
+        int live = 0;
+        for (int s = 0; s < MR; ++s) {
+            const bool on = s < R && !a.sim[s].sc->done;
+            if (on) live |= 1 << s;
+            gsc.flex[s] = s < R && a.sim[s].sc->flexible != 0;
+            gsc.rtol2[s] = s < R ? a.sim[s].sc->rtol2 : 0.0;
+            gsc.maxit[s] = s < R ? a.sim[s].sc->maxit : 0;
+            gsc.alpha[s] = gsc.beta[s] = gsc.rz[s] = gsc.pq[s] = 0.0;
+            gsc.it[s] = gsc.pending[s] = 0;
+            gsc.status[s] = kOK;
+        }
+        gsc.live = live;
+        gsc.started = live;
     }
+    __syncthreads();
+    if (!gsc.live) return;
     unsigned gen = 0;
     const int S = a.wstages;
     const int ldm = (int)a.ld_max;
     auto slot = [&](int w, int k) { return reinterpret_cast<T*>(smem + ((size_t)w * S + k) * a.slot_bytes); };
     double* rp = reinterpret_cast<double*>(smem + a.rp_off);   // [MR][ldm] r' (fp64)
-    float* X = reinterpret_cast<float*>(smem + a.x_off);       // [MR][ldm]
-    float* Y = reinterpret_cast<float*>(smem + a.y_off);       // [MR][ldm]
+    float* X = reinterpret_cast<float*>(smem + a.x_off);       // [MR][ldm] L^{-1} r', then V
+    float* Y = reinterpret_cast<float*>(smem + a.y_off);       // [MR][ldm] Q^T X of the subdomain
     double* r0s = reinterpret_cast<double*>(smem + a.r0_off);  // [n0], one simulation at a time
-    double* y0l = reinterpret_cast<double*>(smem + a.y0_off);  // y0 of the CTA's agglomerates
     double* pn = reinterpret_cast<double*>(smem + a.pn_off);   // z or x of a chunk's needed elements
     RunDesc* rd = reinterpret_cast<RunDesc*>(smem + a.td_off);
 
     const int64_t e0 = a.elem_ptr[cta], e1 = a.elem_ptr[cta + 1];
     const int ch0 = a.cta_chunk[cta], ch1 = a.cta_chunk[cta + 1];
-    const int32_t* aggs = a.need_agg + a.need_agg_ptr[cta];
-    const int n_aggs = a.need_agg_ptr[cta + 1] - a.need_agg_ptr[cta];
     const int c0 = a.crow_ptr[cta], c1 = a.crow_ptr[cta + 1];
-    const int sub0 = a.cta_sub[cta], sub1 = a.cta_sub[cta + 1];
+    const int pc0 = a.piece_ptr[cta], npieces = a.piece_ptr[cta + 1] - pc0;
     const bool coarse = a.n0 > 0;
     const float chi_f = (float)a.chi;
 
@@ -125,55 +138,59 @@ __device__ __forceinline__ void pcg_group_cta(const GroupArgs& a, const int cta,
     double v2[2 * MR];
 #pragma unroll
     for (int k = 0; k < 2 * MR; ++k) v2[k] = 0.0;
+    {
+        const int live = gsc.live;
 #pragma unroll
-    for (int s = 0; s < MR; ++s) {
-        if (!((live >> s) & 1)) continue;
-        const GroupSim& sm = a.sim[s];
-        for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) {
-            sm.p[0][t] = 0.0; sm.p[1][t] = 0.0; sm.q[0][t] = 0.0; sm.q[1][t] = 0.0;
-            sm.z[t] = 0.0; sm.w[t] = 0.0;
-        }
-        for (int ch = ch0; ch < ch1; ++ch) {
-            const int64_t ce0 = a.chunk_elem[ch], ce1 = a.chunk_elem[ch + 1];
-            const int32_t* need = a.need + a.need_ptr[ch];
-            const int n_need = a.need_ptr[ch + 1] - a.need_ptr[ch];
-            __syncthreads();
-            for (int idx = threadIdx.x; idx < n_need * NP; idx += blockDim.x) {
-                const int l = idx / NP;
-                pn[idx] = __ldcg(sm.x + (int64_t)need[l] * NP + (idx - l * NP));
+        for (int s = 0; s < MR; ++s) {
+            if (!((live >> s) & 1)) continue;
+            const GroupSim& sm = a.sim[s];
+            for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) {
+                sm.p[0][t] = 0.0; sm.p[1][t] = 0.0; sm.q[0][t] = 0.0; sm.q[1][t] = 0.0;
+                sm.z[t] = 0.0; sm.w[t] = 0.0;
             }
-            __syncthreads();
-            local_rows<NP>(a.row_ptr, a.col_local, sm.val, pn, ce0, ce1, [&](int64_t e, int i, double kx) {
-                const int64_t t = e * NP + i;
-                const double bv = sm.b[t], rv = bv - kx;
-                sm.r[0][t] = rv;
-                v2[2 * s] = fma(bv, bv, v2[2 * s]);
-                v2[2 * s + 1] = fma(rv, rv, v2[2 * s + 1]);
-            });
+            for (int ch = ch0; ch < ch1; ++ch) {
+                const int64_t ce0 = a.chunk_elem[ch], ce1 = a.chunk_elem[ch + 1];
+                const int32_t* need = a.need + a.need_ptr[ch];
+                const int n_need = a.need_ptr[ch + 1] - a.need_ptr[ch];
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < n_need * NP; idx += blockDim.x) {
+                    const int l = idx / NP;
+                    pn[idx] = __ldcg(sm.x + (int64_t)need[l] * NP + (idx - l * NP));
+                }
+                __syncthreads();
+                local_rows<NP>(a.row_ptr, a.col_local, sm.val, pn, ce0, ce1, [&](int64_t e, int i, double kx) {
+                    const int64_t t = e * NP + i;
+                    const double bv = sm.b[t], rv = bv - kx;
+                    sm.r[0][t] = rv;
+                    v2[2 * s] = fma(bv, bv, v2[2 * s]);
+                    v2[2 * s + 1] = fma(rv, rv, v2[2 * s + 1]);
+                });
+            }
         }
     }
-    // ---- the CTA's rows: per subdomain a run over Q_i^T, then one over Q_i
-    const int nsub = sub1 - sub0;
+    // ---- the CTA's rows: its pieces' rows of Q^T (pass 1), then the same rows of Q (pass 2)
     int n_rows = 0;
-    for (int k = 0; k < 2 * nsub; ++k) {
-        const SharedBlock B = a.sblocks[sub0 + k / 2];
+    for (int k = 0; k < 2 * npieces; ++k) {
+        const int pi = k < npieces ? k : k - npieces;
+        const GemvRun pz = a.pieces[pc0 + pi];
+        const SharedBlock B = a.sblocks[pz.block];
         if ((k & (blockDim.x - 1)) == (int)threadIdx.x) {
             RunDesc d;
-            d.mat_off = B.q_off + ((k & 1) ? (int64_t)B.n * B.ld : 0);
+            d.mat_off = B.q_off + (k >= npieces ? (int64_t)B.n * B.ld : 0);
             d.in_off = B.in_off;
-            d.row_begin = 0;
-            d.row_end = B.n;
+            d.row_begin = pz.row_begin;
+            d.row_end = pz.row_end;
             d.ld = B.ld;
             d.ncols = B.n;
-            d.block = sub0 + k / 2;
+            d.block = pz.block;
             d.pair_begin = 0;
             d.pair_count = 0;
             d.ord = n_rows;
             rd[k] = d;
         }
-        n_rows += B.n;
+        n_rows += pz.row_end - pz.row_begin;
     }
-    const int nruns = 2 * nsub;
+    const int nruns = 2 * npieces;
     const bool has_rows = warp < n_rows;
     uint32_t wseq = 0, n_done = 0, n_issued = 0;
     bool wfail = false;
@@ -204,11 +221,11 @@ __device__ __forceinline__ void pcg_group_cta(const GroupArgs& a, const int cta,
         }
         n_issued = S;
     }
-    // consume this warp's rows of run ri: f(row, acc) with the R dot products of the row
-    auto rows_of = [&](int ri, const float* V, auto&& f) {
+    // this warp's rows of run ri: f(row, acc) with the R dot products of the row with V
+    auto rows_of = [&](int ri, const float* V, int live, auto&& f) {
         const RunDesc& rn = rd[ri];
         const int k0 = ((warp - rn.ord) % NW + NW) % NW;
-        for (int row = k0; row < rn.row_end; row += NW, ++wseq) {
+        for (int row = rn.row_begin + k0; row < rn.row_end; row += NW, ++wseq) {
             const int k = wseq % S;
             if (!wfail && !mbar_wait(&wbars[warp][k], (wseq / S) & 1)) {
                 wfail = true;
@@ -227,58 +244,62 @@ __device__ __forceinline__ void pcg_group_cta(const GroupArgs& a, const int cta,
         }
     };
 
-    bool ok = barrier_sum<2 * MR>(a.gs, G, cta, gen, a.err, a.partials, v2, red, outv, [](const double*) {});
-    double bb[MR], rr[MR], alpha[MR], beta[MR], rz[MR], pq[MR];
-    int it[MR], pending[MR], status[MR];
-#pragma unroll
-    for (int s = 0; s < MR; ++s) {
-        bb[s] = v2[2 * s];
-        rr[s] = v2[2 * s + 1];
-        alpha[s] = beta[s] = rz[s] = pq[s] = 0.0;
-        it[s] = pending[s] = 0;
-        status[s] = kOK;
-        if (!((live >> s) & 1)) continue;
-        if (!ok) { status[s] = kEDEVICE; live &= ~(1 << s); }
-        else if (!isfinite(bb[s]) || !isfinite(rr[s])) { status[s] = kENONFINITE; live &= ~(1 << s); }
-        else if (bb[s] == 0.0) {                 // b = 0: x = 0
-            for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) a.sim[s].x[t] = 0.0;
-            live &= ~(1 << s);
-        } else if (rr[s] <= rtol2[s] * bb[s]) live &= ~(1 << s);
+    bool ok = barrier_sum<2 * MR>(a.gs, G, cta, gen, a.err, a.partials, v2, red, outv, [&](const double* sm) {
+        int live = gsc.live;
+        for (int s = 0; s < MR; ++s) {
+            gsc.bb[s] = sm[2 * s];
+            gsc.rr[s] = sm[2 * s + 1];
+            if (!((live >> s) & 1)) continue;
+            if (!isfinite(sm[2 * s]) || !isfinite(sm[2 * s + 1])) { gsc.status[s] = kENONFINITE; live &= ~(1 << s); }
+            else if (sm[2 * s] == 0.0) live &= ~(1 << s);                 // b = 0: x = 0 below
+            else if (sm[2 * s + 1] <= gsc.rtol2[s] * sm[2 * s]) live &= ~(1 << s);
+        }
+        gsc.live = live;
+    });
+    if (!ok) {
+        if (threadIdx.x == 0) { for (int s = 0; s < MR; ++s) if ((gsc.live >> s) & 1) gsc.status[s] = kEDEVICE; gsc.live = 0; }
+        __syncthreads();
     }
+#pragma unroll
+    for (int s = 0; s < MR; ++s)                       // b = 0: the solution is x = 0
+        if (((gsc.started >> s) & 1) && gsc.bb[s] == 0.0)
+            for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) a.sim[s].x[t] = 0.0;
     int par = 0, pp = 0;
 
-    while (live) {
-        // ---------------------------------------------------------------- P
+    while (gsc.live) {
+        const int live = gsc.live;
+        // ---------------------------------------------------------------- P1
+        // per piece: stage r' of the whole subdomain, commit the piece's rows, X = L^{-1} r',
+        // R_0 r' (the piece that starts the subdomain), pass 1 over the piece's rows of Q^T
         double v1[MR];
 #pragma unroll
         for (int s = 0; s < MR; ++s) v1[s] = 0.0;
-        for (int i = sub0; i < sub1; ++i) {
-            const SharedBlock B = a.sblocks[i];
+        for (int pi = 0; pi < npieces; ++pi) {
+            const RunDesc& rn = rd[pi];
+            const SharedBlock B = a.sblocks[rn.block];
             const int n = B.n, ld = B.ld;
-            __syncthreads();                      // the previous subdomain's readers are done
+            __syncthreads();                      // the previous piece's readers are done
             for (int idx = threadIdx.x; idx < R * ld; idx += blockDim.x) {
                 const int s = idx / ld, j = idx - s * ld;
                 double r_ = 0.0;
                 if (((live >> s) & 1) && j < n) {
                     const GroupSim& sm = a.sim[s];
                     const int64_t t = B.in_off + j;
-                    double al = 0.0, be = 0.0;
-#pragma unroll
-                    for (int k = 0; k < MR; ++k)
-                        if (k == s) { al = pending[k] ? alpha[k] : 0.0; be = beta[k]; }
+                    const double al = gsc.pending[s] ? gsc.alpha[s] : 0.0, be = gsc.beta[s];
                     const double qk = fma(be, __ldcg(sm.q[pp] + t), __ldcg(sm.w + t));
                     r_ = fma(-al, qk, __ldcg(sm.r[par] + t));
-                    const double pk = fma(be, __ldcg(sm.p[pp] + t), __ldcg(sm.z + t));
-                    sm.p[pp ^ 1][t] = pk;
-                    sm.q[pp ^ 1][t] = qk;
-                    sm.x[t] = fma(al, pk, sm.x[t]);
-                    sm.r[par ^ 1][t] = r_;
-                    add_at(v1, s, r_ * r_);
+                    if (j >= rn.row_begin && j < rn.row_end) {
+                        const double pk = fma(be, __ldcg(sm.p[pp] + t), __ldcg(sm.z + t));
+                        sm.p[pp ^ 1][t] = pk;
+                        sm.q[pp ^ 1][t] = qk;
+                        sm.x[t] = fma(al, pk, sm.x[t]);
+                        sm.r[par ^ 1][t] = r_;
+                        add_at(v1, s, r_ * r_);
+                    }
                 }
                 rp[s * ldm + j] = r_;
             }
             __syncthreads();
-            // X_s = L^{-1} r'_s, element by element (L_K^{-1} lower triangular)
             for (int idx = threadIdx.x; idx < R * ld; idx += blockDim.x) {
                 const int s = idx / ld, k = idx - s * ld;
                 float v = 0.f;
@@ -291,17 +312,15 @@ __device__ __forceinline__ void pcg_group_cta(const GroupArgs& a, const int cta,
                     v = (float)acc;
                 }
                 X[s * ldm + k] = v;
-                if (k >= n) Y[s * ldm + k] = 0.f;     // pass 2 reads Y over the padded row
             }
-            // R_0 r'_s of this subdomain (fp64, from the staged r')
-            if (coarse) {
-                const int pb = a.pair_begin[i], pc = a.pair_count[i];
+            if (coarse && rn.row_begin == 0) {
+                const int pb = a.pair_begin[rn.block], pc = a.pair_count[rn.block];
                 const int items = R * pc * a.nq;
                 for (int w2 = warp; w2 < items; w2 += nw) {
                     const int s = w2 / (pc * a.nq), rem = w2 - s * pc * a.nq;
-                    const int pi = rem / a.nq, row = rem - pi * a.nq;
+                    const int pj = rem / a.nq, row = rem - pj * a.nq;
                     if (!((live >> s) & 1)) continue;
-                    const GemvBlock Rb = a.blocks[a.sub_pairs[pb + pi]];
+                    const GemvBlock Rb = a.blocks[a.sub_pairs[pb + pj]];
                     const double* Rr = a.st64 + Rb.mat_off + (int64_t)row * Rb.ld;
                     const double* r_ = rp + s * ldm;
                     double s0 = 0.0, s1 = 0.0;
@@ -316,26 +335,62 @@ __device__ __forceinline__ void pcg_group_cta(const GroupArgs& a, const int cta,
                 }
             }
             __syncthreads();
-            // pass 1: Y_s[j] = (Q^T row j . X_s) / (chi + c_s lam_j)
             const float* lm = a.lam + B.lam_off;
-            rows_of(2 * (i - sub0), X, [&](int row, const float (&acc)[MR]) {
+            rows_of(pi, X, live, [&](int row, const float (&acc)[MR]) {
                 const float l = lm[row];
 #pragma unroll
                 for (int s = 0; s < MR; ++s)
-                    if ((live >> s) & 1) Y[s * ldm + row] = acc[s] / (chi_f + (float)a.sim[s].c * l);
+                    if ((live >> s) & 1) a.sim[s].yq[B.in_off + row] = acc[s] / (chi_f + (float)a.sim[s].c * l);
             });
+        }
+        // stopping tests by thread 0 (0 go on, 1 converged, 2 non-finite, 3 maxit)
+        ok = barrier_sum<MR>(a.gs, G, cta, gen, a.err, a.partials, v1, red, outv, [&](const double* sm) {
+            int lv = gsc.live;
+            for (int s = 0; s < MR; ++s) {
+                if (!((lv >> s) & 1)) continue;
+                gsc.it[s] += gsc.pending[s];
+                gsc.pending[s] = 0;
+                gsc.rr[s] = sm[s];
+                const double r2 = sm[s];
+                const int code = !isfinite(r2) ? 2 : (r2 <= gsc.rtol2[s] * gsc.bb[s]) ? 1
+                                 : (gsc.it[s] >= gsc.maxit[s]) ? 3 : 0;
+                if (code == 2) { gsc.status[s] = kENONFINITE; lv &= ~(1 << s); }
+                else if (code == 1) { gsc.status[s] = kOK; lv &= ~(1 << s); }
+                else if (code == 3) { gsc.status[s] = kENOTCONV; lv &= ~(1 << s); }
+            }
+            gsc.live = lv;
+        });
+        par ^= 1;
+        pp ^= 1;
+        if (!ok) {
+            if (threadIdx.x == 0) { for (int s = 0; s < MR; ++s) if ((live >> s) & 1) gsc.status[s] = kEDEVICE; gsc.live = 0; }
             __syncthreads();
-            // pass 2: V_s[k] = Q row k . Y_s, into X
-            rows_of(2 * (i - sub0) + 1, Y, [&](int row, const float (&acc)[MR]) {
+            break;
+        }
+        const int live2 = gsc.live;
+        if (!live2) break;
+        // ---------------------------------------------------------------- P2 + coarse
+        // pass 2 over the pieces' rows of Q with the whole subdomain's Y; z_loc = L^{-T} V
+        for (int pi = 0; pi < npieces; ++pi) {
+            const RunDesc& rn = rd[npieces + pi];
+            const SharedBlock B = a.sblocks[rn.block];
+            const int n = B.n, ld = B.ld;
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < R * ld; idx += blockDim.x) {
+                const int s = idx / ld, j = idx - s * ld;
+                Y[s * ldm + j] = (((live2 >> s) & 1) && j < n) ? __ldcg(a.sim[s].yq + B.in_off + j) : 0.f;
+            }
+            __syncthreads();
+            rows_of(npieces + pi, Y, live2, [&](int row, const float (&acc)[MR]) {
 #pragma unroll
                 for (int s = 0; s < MR; ++s)
-                    if ((live >> s) & 1) X[s * ldm + row] = acc[s];
+                    if ((live2 >> s) & 1) X[s * ldm + row] = acc[s];
             });
             __syncthreads();
-            // z_loc,s = L^{-T} V_s
-            for (int idx = threadIdx.x; idx < R * n; idx += blockDim.x) {
-                const int s = idx / n, k = idx - s * n;
-                if (!((live >> s) & 1)) continue;
+            const int len = rn.row_end - rn.row_begin;    // element-aligned
+            for (int idx = threadIdx.x; idx < R * len; idx += blockDim.x) {
+                const int s = idx / len, k = rn.row_begin + (idx - s * len);
+                if (!((live2 >> s) & 1)) continue;
                 const int el = k / NP, ii = k - el * NP;
                 const double* L0 = a.linv + (int64_t)(B.cell0 + el) * NP * NP;
                 const float* V = X + s * ldm + el * NP;
@@ -344,84 +399,54 @@ __device__ __forceinline__ void pcg_group_cta(const GroupArgs& a, const int cta,
                 a.sim[s].zl[B.in_off + k] = acc;
             }
         }
-        // stopping tests by thread 0: per simulation 0 go on, 1 converged, 2 non-finite, 3 maxit
-        ok = barrier_sum<MR>(a.gs, G, cta, gen, a.err, a.partials, v1, red, outv, [&](const double* sm) {
-#pragma unroll
-            for (int s = 0; s < MR; ++s) {
-                if (!((live >> s) & 1)) { scode[s] = -1; continue; }
-                const double r2 = sm[s];
-                scode[s] = !isfinite(r2) ? 2 : (r2 <= rtol2[s] * bb[s]) ? 1 : (it[s] + pending[s] >= maxit[s]) ? 3 : 0;
-            }
-        });
-        par ^= 1;
-        pp ^= 1;
+        // coarse solves, each row once (rows [c0, c1) of this CTA, to global memory); the
+        // barrier below then completes y0 and the neighbours' z_loc for the CM phase
 #pragma unroll
         for (int s = 0; s < MR; ++s) {
-            if (!((live >> s) & 1)) continue;
-            it[s] += pending[s];
-            pending[s] = 0;
-            rr[s] = v1[s];
-            const int code = scode[s];
-            if (!ok) { status[s] = kEDEVICE; live &= ~(1 << s); }
-            else if (code == 2) { status[s] = kENONFINITE; live &= ~(1 << s); }
-            else if (code == 1) { status[s] = kOK; live &= ~(1 << s); }
-            else if (code == 3) { status[s] = kENOTCONV; live &= ~(1 << s); }
+            if (!coarse || !((live2 >> s) & 1) || c1 <= c0) continue;
+            const GroupSim& sm = a.sim[s];
+            __syncthreads();                      // r0s of the previous simulation is done
+            for (int idx = threadIdx.x; idx < a.n0; idx += blockDim.x) {
+                const int J = idx / a.nq, kq = idx - J * a.nq;
+                double s_r = 0.0;
+                for (int64_t p2 = a.pair_ptr[J]; p2 < a.pair_ptr[J + 1]; ++p2)
+                    s_r += __ldcg(sm.r0p + p2 * a.nq + kq);
+                r0s[idx] = s_r;
+            }
+            __syncthreads();
+            for (int row = c0 + warp; row < c1; row += nw) {
+                const double* Kr = sm.K0inv + (int64_t)row * a.ld0;
+                double s0 = 0.0, s1 = 0.0;
+                int c = lane;
+                for (; c + 32 < a.n0; c += 64) {
+                    s0 = fma(__ldg(Kr + c), r0s[c], s0);
+                    s1 = fma(__ldg(Kr + c + 32), r0s[c + 32], s1);
+                }
+                if (c < a.n0) s0 = fma(__ldg(Kr + c), r0s[c], s0);
+                const double y = warp_sum(s0 + s1);
+                if (lane == 0) sm.y0[row] = y;
+            }
         }
-        if (!live) break;
-        // ---------------------------------------------------------------- coarse + CM
+        ok = grid_barrier(a.gs, G, gen, a.err);
+        if (!ok) {
+            if (threadIdx.x == 0) { for (int s = 0; s < MR; ++s) if ((live2 >> s) & 1) gsc.status[s] = kEDEVICE; gsc.live = 0; }
+            __syncthreads();
+            break;
+        }
+        // ---------------------------------------------------------------- CM
         double v3[3 * MR];
 #pragma unroll
         for (int k = 0; k < 3 * MR; ++k) v3[k] = 0.0;
-        bool cm_ok = true;
 #pragma unroll
         for (int s = 0; s < MR; ++s) {
-            if (!((live >> s) & 1)) continue;
+            if (!((live2 >> s) & 1)) continue;
             const GroupSim& sm = a.sim[s];
             const double* rk = sm.r[par];
             const double* qk = sm.q[pp];
-            if (coarse) {
-                __syncthreads();
-                if (a.redundant || c1 > c0) {
-                    for (int idx = threadIdx.x; idx < a.n0; idx += blockDim.x) {
-                        const int J = idx / a.nq, kq = idx - J * a.nq;
-                        double s_r = 0.0;
-                        for (int64_t p2 = a.pair_ptr[J]; p2 < a.pair_ptr[J + 1]; ++p2)
-                            s_r += __ldcg(sm.r0p + p2 * a.nq + kq);
-                        r0s[idx] = s_r;
-                    }
-                    __syncthreads();
-                }
-                auto coarse_row = [&](int row) {
-                    const double* Kr = sm.K0inv + (int64_t)row * a.ld0;
-                    double s0 = 0.0, s1 = 0.0;
-                    int c = lane;
-                    for (; c + 32 < a.n0; c += 64) {
-                        s0 = fma(__ldg(Kr + c), r0s[c], s0);
-                        s1 = fma(__ldg(Kr + c + 32), r0s[c + 32], s1);
-                    }
-                    if (c < a.n0) s0 = fma(__ldg(Kr + c), r0s[c], s0);
-                    return warp_sum(s0 + s1);
-                };
-                if (a.redundant) {
-                    for (int w2 = warp; w2 < n_aggs * a.nq; w2 += nw) {
-                        const int jl = w2 / a.nq, kq = w2 - jl * a.nq;
-                        const double y = coarse_row(aggs[jl] * a.nq + kq);
-                        if (lane == 0) y0l[w2] = y;
-                    }
-                } else {
-                    for (int row = c0 + warp; row < c1; row += nw) {
-                        const double y = coarse_row(row);
-                        if (lane == 0) sm.y0[row] = y;
-                    }
-                    cm_ok = grid_barrier(a.gs, G, gen, a.err) && cm_ok;
-                }
-                __syncthreads();
-            }
             for (int ch = ch0; ch < ch1; ++ch) {
                 const int64_t ce0 = a.chunk_elem[ch], ce1 = a.chunk_elem[ch + 1];
                 const int n_chunk = (int)(ce1 - ce0);
                 const int32_t* need = a.need + a.need_ptr[ch];
-                const int32_t* needj = a.need_aggl + a.need_ptr[ch];
                 const int n_need = a.need_ptr[ch + 1] - a.need_ptr[ch];
                 __syncthreads();
                 for (int idx = threadIdx.x; idx < n_need * NP; idx += blockDim.x) {
@@ -430,13 +455,8 @@ __device__ __forceinline__ void pcg_group_cta(const GroupArgs& a, const int cta,
                     double v = __ldcg(sm.zl + t);
                     if (coarse) {
                         const double* Tr = a.T + t * a.nq;
-                        if (a.redundant) {
-                            const double* y = y0l + needj[l] * a.nq;
-                            for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), y[kq], v);
-                        } else {
-                            const double* y = sm.y0 + (int64_t)a.agg[e] * a.nq;
-                            for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), __ldcg(y + kq), v);
-                        }
+                        const double* y = sm.y0 + (int64_t)a.agg[e] * a.nq;
+                        for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), __ldcg(y + kq), v);
                     }
                     pn[idx] = v;
                     if (l < n_chunk) sm.z[t] = v;
@@ -452,40 +472,33 @@ __device__ __forceinline__ void pcg_group_cta(const GroupArgs& a, const int cta,
                 });
             }
         }
-        // beta, p.q, alpha per simulation by thread 0: code 0 go on, 2 non-finite, 4 breakdown
+        // beta, p.q, alpha per simulation by thread 0 (2 non-finite, 4 breakdown)
         ok = barrier_sum<3 * MR>(a.gs, G, cta, gen, a.err, a.partials, v3, red, outv, [&](const double* sm) {
-#pragma unroll
+            int lv = gsc.live;
             for (int s = 0; s < MR; ++s) {
-                if (!((live >> s) & 1)) { scode[s] = -1; continue; }
+                if (!((lv >> s) & 1)) continue;
                 const double rz_new = sm[3 * s], zq = sm[3 * s + 1], zw = sm[3 * s + 2];
-                if (!isfinite(rz_new) || !isfinite(zq) || !isfinite(zw)) { scode[s] = 2; continue; }
+                if (!isfinite(rz_new) || !isfinite(zq) || !isfinite(zw)) { gsc.status[s] = kENONFINITE; lv &= ~(1 << s); continue; }
                 double bnew;
-                if (it[s] == 0) bnew = 0.0;
-                else if (flex[s]) bnew = -alpha[s] * zq / rz[s];
-                else bnew = rz_new / rz[s];
-                const double pq_new = zw + 2.0 * bnew * zq + bnew * bnew * pq[s];
-                if (!isfinite(bnew) || rz_new == 0.0 || !(pq_new > 0.0) || !isfinite(pq_new)) { scode[s] = 4; continue; }
-                scal[3 * s] = rz_new / pq_new;
-                scal[3 * s + 1] = bnew;
-                scal[3 * s + 2] = pq_new;
-                scode[s] = 0;
+                if (gsc.it[s] == 0) bnew = 0.0;
+                else if (gsc.flex[s]) bnew = -gsc.alpha[s] * zq / gsc.rz[s];
+                else bnew = rz_new / gsc.rz[s];
+                const double pq_new = zw + 2.0 * bnew * zq + bnew * bnew * gsc.pq[s];
+                if (!isfinite(bnew) || rz_new == 0.0 || !(pq_new > 0.0) || !isfinite(pq_new)) {
+                    gsc.status[s] = kEBREAKDOWN; lv &= ~(1 << s); continue;
+                }
+                gsc.rz[s] = rz_new;
+                gsc.alpha[s] = rz_new / pq_new;
+                gsc.beta[s] = bnew;
+                gsc.pq[s] = pq_new;
+                gsc.pending[s] = 1;
             }
+            gsc.live = lv;
         });
-        ok = ok && cm_ok;
-#pragma unroll
-        for (int s = 0; s < MR; ++s) {
-            if (!((live >> s) & 1)) continue;
-            const int code = scode[s];
-            if (!ok) { status[s] = kEDEVICE; live &= ~(1 << s); }
-            else if (code == 2) { status[s] = kENONFINITE; live &= ~(1 << s); }
-            else if (code == 4) { status[s] = kEBREAKDOWN; live &= ~(1 << s); }
-            else {
-                rz[s] = v3[3 * s];
-                alpha[s] = scal[3 * s];
-                beta[s] = scal[3 * s + 1];
-                pq[s] = scal[3 * s + 2];
-                pending[s] = 1;
-            }
+        if (!ok) {
+            if (threadIdx.x == 0) { for (int s = 0; s < MR; ++s) if ((live2 >> s) & 1) gsc.status[s] = kEDEVICE; gsc.live = 0; }
+            __syncthreads();
+            break;
         }
     }
     if (has_rows) {                       // bounded wait for this warp's copies still in flight
@@ -493,15 +506,14 @@ __device__ __forceinline__ void pcg_group_cta(const GroupArgs& a, const int cta,
             if (!mbar_wait(&wbars[warp][c % S], (c / S) & 1)) break;
     }
     if (cta == 0 && threadIdx.x == 0) {
-#pragma unroll
         for (int s = 0; s < MR; ++s) {
-            if (!((started >> s) & 1)) continue;
+            if (!((gsc.started >> s) & 1)) continue;
             PcgScalars* sc = a.sim[s].sc;
-            sc->bb = bb[s];
-            sc->rr = rr[s];
-            sc->relres = bb[s] > 0.0 ? sqrt(rr[s] / bb[s]) : 0.0;
-            sc->it = it[s];
-            sc->status = status[s];
+            sc->bb = gsc.bb[s];
+            sc->rr = gsc.rr[s];
+            sc->relres = gsc.bb[s] > 0.0 ? sqrt(gsc.rr[s] / gsc.bb[s]) : 0.0;
+            sc->it = gsc.it[s];
+            sc->status = gsc.status[s];
             sc->done = 1;
             sc->pass = 0;                 // x is single-buffered here
         }
