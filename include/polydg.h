@@ -177,6 +177,16 @@ int asm_setup(polydg_ctx *ctx, const int32_t *coarse_of_cell, int q, int precisi
 
 int asm_get_info(const asm_ctx *pc, asm_info *out);
 
+/* Autotune the split of the local-inverse rows over the CTAs of pcg_solve and
+ * monodomain_step with this preconditioner: time `iterations` PCG iterations (a fixed
+ * right-hand side on the context's work vectors, default stream), read every CTA's
+ * P-phase cycle count, rescale the modelled cost of each CTA's tiles by its measured /
+ * modelled share, re-cut the tile sequence, and repeat `rounds` times; the fastest
+ * partition measured is kept.  *gain (may be NULL) = time before / time after.  Results of
+ * later solves change only by rounding (the per-CTA partial sums are grouped differently).
+ * Synchronises the device.  Errors: EINVAL, ECUDA. */
+int asm_autotune(asm_ctx *pc, int rounds, int iterations, double *gain);
+
 /* z = B_ad^{-1} r (Eq. prec).  r_dev and z_dev are caller-order device vectors
  * and must not alias. */
 int asm_apply(asm_ctx *pc, const double *r_dev, double *z_dev, void *stream);

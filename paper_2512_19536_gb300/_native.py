@@ -28,7 +28,7 @@ EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_get_info", "polydg_get_f
            "guess_create", "guess_get_params", "guess_set_scales", "guess_propose",
            "guess_train_step", "sim_set_guess", "guess_destroy", "polydg_sym_eig",
            "shared_local_setup", "shared_local_info", "shared_local_apply", "shared_local_destroy",
-           "sim_set_shared_local"]
+           "sim_set_shared_local", "asm_autotune"]
 
 
 class polydg_mesh(C.Structure):
@@ -121,6 +121,8 @@ def load() -> C.CDLL:
     L.shared_local_apply.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(vp), pd_, vp]
     for name in ("shared_local_setup", "shared_local_info", "shared_local_apply"):
         getattr(L, name).restype = i32
+    L.asm_autotune.argtypes = [vp, i32, i32, pd_]
+    L.asm_autotune.restype = i32
     L.sim_set_shared_local.argtypes = [vp, vp]
     L.sim_set_shared_local.restype = i32
     L.shared_local_destroy.argtypes = [vp]
@@ -251,6 +253,14 @@ def asm_setup(ctx: PolyDG, coarse_of_cell=None, q=1, precision="fp64") -> ASM:
         cptr = _ptr(coarse, C.c_int32)
     _check(load().asm_setup(ctx.h, cptr, int(q), PRECISION[precision], C.byref(h)))
     return ASM(ctx, h, precision)
+
+
+def asm_autotune(pc: ASM, rounds=3, iterations=60):
+    """Re-cut the local-inverse rows over the CTAs by measured per-CTA times; returns the
+    speed-up of a PCG iteration (time before / after)."""
+    g = C.c_double()
+    _check(load().asm_autotune(pc.h, int(rounds), int(iterations), C.byref(g)))
+    return g.value
 
 
 def asm_apply(pc: ASM, r, z, stream=None):

@@ -46,6 +46,65 @@ static K2Args k2_args(polydg_ctx* c, asm_ctx* pc, PcgScalars* sc, double* partia
     return a;
 }
 
+// Cut the plan's tile sequence into G contiguous runs of about equal cost (tile cost,
+// plus the stage cost of a tile that starts a subdomain within a run): greedy packing
+// under a per-CTA budget, the smallest budget that fits in G runs found by bisection.
+// Gives each CTA's tiles as runs of consecutive rows of one block.
+static int partition_tiles(Plan& P, const asm_ctx* pc, int G, const std::vector<double>& tcost,
+                           const std::vector<double>& tstage, std::vector<int32_t>& run_ptr,
+                           std::vector<GemvRun>& runs) {
+    const std::vector<GemvTile>& tiles = P.h_tiles;
+    const int rows = P.rows;
+    auto pack = [&](double budget, std::vector<int32_t>* ptr) {
+        int used = 0;
+        size_t k = 0;
+        while (k < tiles.size()) {
+            if (ptr) (*ptr)[used] = (int32_t)k;
+            ++used;
+            double acc = 0.0;
+            const size_t first = k;
+            while (k < tiles.size()) {
+                const bool stage = (k == first) || tiles[k].block != tiles[k - 1].block;
+                const double c = tcost[k] + (stage ? tstage[k] : 0.0);
+                if (k > first && acc + c > budget) break;
+                acc += c;
+                ++k;
+            }
+        }
+        return used;
+    };
+    double lo = 0.0, hi = 0.0;
+    for (size_t k = 0; k < tiles.size(); ++k) hi += tcost[k] + tstage[k];
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (pack(mid, nullptr) <= G) hi = mid; else lo = mid;
+    }
+    std::vector<int32_t> tile_ptr(G + 1, (int32_t)tiles.size());
+    const int used = tiles.empty() ? 0 : pack(hi, &tile_ptr);
+    for (int g = used; g <= G; ++g) tile_ptr[g] = (int32_t)tiles.size();
+    P.est_seconds = tiles.empty() ? 0.0 : hi;
+    P.h_tile_ptr = tile_ptr;
+    run_ptr.assign(G + 1, 0);
+    runs.clear();
+    for (int g = 0; g < G; ++g) {
+        run_ptr[g] = (int32_t)runs.size();
+        for (int32_t k = tile_ptr[g]; k < tile_ptr[g + 1]; ++k) {
+            const GemvTile& t = tiles[k];
+            const int32_t end = std::min<int32_t>(t.row0 + rows, pc->blocks[t.block].nrows);
+            if ((int32_t)runs.size() > run_ptr[g] && runs.back().block == t.block && runs.back().row_end == t.row0)
+                runs.back().row_end = end;
+            else
+                runs.push_back({t.block, t.row0, end, 0});
+        }
+        if ((int32_t)runs.size() - run_ptr[g] > 128) {
+            set_error("pcg: a CTA would stream more than 128 subdomains; too many subdomains for the CTAs");
+            return POLYDG_EINVAL;
+        }
+    }
+    run_ptr[G] = (int32_t)runs.size();
+    return POLYDG_OK;
+}
+
 // Split the work of one PCG iteration over `grid` CTAs: LOCAL tiles (rows of the
 // local inverses) as contiguous runs balanced by bytes, elements and coarse rows
 // evenly; per CTA the elements whose p its matvec rows need (own range first,
@@ -183,55 +242,12 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 
         tcost[k] = tbytes[k] / bw_sm + c_tile + (tiles[k].row0 == 0 ? c_pair * B.pair_count : 0.0);
         tstage[k] = c_stage;
     }
-    // greedy packing under a per-CTA budget; the smallest budget that fits in G runs
-    // (bisection) gives the partition with the smallest maximum estimated time
-    auto pack = [&](double budget, std::vector<int32_t>* ptr) {
-        int runs = 0;
-        size_t k = 0;
-        while (k < tiles.size()) {
-            if (ptr) (*ptr)[runs] = (int32_t)k;
-            ++runs;
-            double acc = 0.0;
-            const size_t first = k;
-            while (k < tiles.size()) {
-                const bool stage = (k == first) || tiles[k].block != tiles[k - 1].block;
-                const double c = tcost[k] + (stage ? tstage[k] : 0.0);
-                if (k > first && acc + c > budget) break;
-                acc += c;
-                ++k;
-            }
-        }
-        return runs;
-    };
-    double lo = 0.0, hi = 0.0;
-    for (size_t k = 0; k < tiles.size(); ++k) hi += tcost[k] + tstage[k];
-    for (int it = 0; it < 60; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (pack(mid, nullptr) <= G) hi = mid; else lo = mid;
-    }
-    std::vector<int32_t> tile_ptr(G + 1, (int32_t)tiles.size());
-    const int used = tiles.empty() ? 0 : pack(hi, &tile_ptr);
-    for (int g = used; g <= G; ++g) tile_ptr[g] = (int32_t)tiles.size();
-    P.est_seconds = tiles.empty() ? 0.0 : hi;
-    // each CTA's tiles as runs of consecutive rows of one block
-    std::vector<int32_t> run_ptr(G + 1, 0);
+    P.h_tiles = tiles;
+    P.h_cost = tcost;
+    P.h_stage = tstage;
+    std::vector<int32_t> run_ptr;
     std::vector<GemvRun> runs;
-    for (int g = 0; g < G; ++g) {
-        run_ptr[g] = (int32_t)runs.size();
-        for (int32_t k = tile_ptr[g]; k < tile_ptr[g + 1]; ++k) {
-            const GemvTile& t = tiles[k];
-            const int32_t end = std::min<int32_t>(t.row0 + rows, pc->blocks[t.block].nrows);
-            if ((int32_t)runs.size() > run_ptr[g] && runs.back().block == t.block && runs.back().row_end == t.row0)
-                runs.back().row_end = end;
-            else
-                runs.push_back({t.block, t.row0, end, 0});
-        }
-        if ((int32_t)runs.size() - run_ptr[g] > kMaxRuns) {
-            set_error("pcg: a CTA would stream more than 128 subdomains; too many subdomains for the CTAs");
-            return POLYDG_EINVAL;
-        }
-    }
-    run_ptr[G] = (int32_t)runs.size();
+    if (int st = partition_tiles(P, pc, G, tcost, tstage, run_ptr, runs)) return st;
     if (pc) sub_pairs = pc->sub_pairs;
     std::vector<int32_t> crow_ptr(G + 1);
     for (int g = 0; g <= G; ++g) crow_ptr[g] = (int32_t)((n0 * g) / G);
@@ -652,6 +668,108 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
     if ((st = cu(cudaMemset(pc->d_err, 0, sizeof(int)), "memset"))) return fail(st);
     if ((st = build_plan(c, pc, c->n_sm, pc->plan))) return fail(st);
     *out = pc;
+    return POLYDG_OK;
+}
+
+int asm_autotune(asm_ctx* pc, int rounds, int iterations, double* gain) {
+    if (!pc || rounds < 0 || iterations < 1) {
+        set_error("asm_autotune: need a preconditioner, rounds >= 0 and iterations >= 1");
+        return POLYDG_EINVAL;
+    }
+    polydg_ctx* c = pc->ctx;
+    Plan& P = pc->plan;
+    const int G = P.grid;
+    const int64_t n = c->H.nc * c->H.n_p;
+    PcgWork& w = c->work;
+    // a fixed right-hand side (the cost of an iteration does not depend on the data)
+    std::vector<double> hb(n);
+    uint64_t st_rng = 0x9E3779B97F4A7C15ull;
+    for (int64_t i = 0; i < n; ++i) {
+        st_rng = st_rng * 6364136223846793005ull + 1442695040888963407ull;
+        hb[i] = (double)(st_rng >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    }
+    long long* d_cyc = nullptr;
+    if (int st = dalloc(&d_cyc, 2 * (size_t)G)) return st;
+    struct Guard { long long*& p; ~Guard() { dfree(p); } } guard{d_cyc};
+    CU(cudaMemcpy(w.b, hb.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    std::vector<long long> cyc(2 * G);
+    // one solve of exactly `iterations` iterations under the current plan
+    auto run = [&](float* ms) -> int {
+        PcgScalars init = {};
+        init.rtol2 = 0.0;                     // never converges: runs to maxit
+        init.maxit = iterations;
+        init.flexible = pc->precision == POLYDG_FP64 ? 0 : 1;
+        CU(cudaMemcpy(w.sc, &init, sizeof(init), cudaMemcpyHostToDevice));
+        CU(cudaMemset(w.x[0], 0, n * sizeof(double)));
+        CU(cudaMemset(w.err, 0, sizeof(int)));
+        CU(cudaMemset(&w.gs->count, 0, sizeof(unsigned)));
+        PersistArgs a = persist_args(c, pc, P, w);
+        a.cta_cycles = d_cyc;
+        CU(cudaEventRecord(e0, 0));
+        CU(launch_pcg_persistent(P.dtype, c->H.n_p, a, P.smem, 0));
+        CU(cudaEventRecord(e1, 0));
+        CU(cudaEventSynchronize(e1));
+        CU(cudaEventElapsedTime(ms, e0, e1));
+        CU(cudaMemcpy(cyc.data(), d_cyc, 2 * G * sizeof(long long), cudaMemcpyDeviceToHost));
+        return POLYDG_OK;
+    };
+    float t0 = 0.f, t_best = 0.f;
+    if (int st = run(&t0)) return st;
+    if (int st = run(&t0)) return st;         // the first launch warms caches and code
+    t_best = t0;
+    std::vector<double> cost = P.h_cost, stage = P.h_stage;
+    std::vector<int32_t> best_ptr = P.h_tile_ptr;
+    std::vector<double> best_cost = cost, best_stage = stage;
+    for (int r = 0; r < rounds; ++r) {
+        // rescale every CTA's tile costs by its measured / modelled P-phase time
+        const std::vector<int32_t> tp = P.h_tile_ptr;
+        double tot_m = 0.0, tot_t = 0.0;
+        for (int g = 0; g < G; ++g) {
+            double m = 0.0;
+            for (int32_t k = tp[g]; k < tp[g + 1]; ++k) m += cost[k] + stage[k];
+            tot_m += m;
+            tot_t += (double)cyc[g];
+        }
+        if (tot_m <= 0.0 || tot_t <= 0.0) break;
+        for (int g = 0; g < G; ++g) {
+            double m = 0.0;
+            for (int32_t k = tp[g]; k < tp[g + 1]; ++k) m += cost[k] + stage[k];
+            if (m <= 0.0 || cyc[g] <= 0) continue;
+            const double f = ((double)cyc[g] / tot_t) / (m / tot_m);
+            for (int32_t k = tp[g]; k < tp[g + 1]; ++k) { cost[k] *= f; stage[k] *= f; }
+        }
+        std::vector<int32_t> run_ptr;
+        std::vector<GemvRun> runs;
+        if (int st = partition_tiles(P, pc, G, cost, stage, run_ptr, runs)) return st;
+        dfree(P.run_ptr);
+        dfree(P.runs);
+        if (int st = upload(&P.run_ptr, run_ptr)) return st;
+        if (int st = upload(&P.runs, runs)) return st;
+        float t = 0.f;
+        if (int st = run(&t)) return st;
+        if (t < t_best) {
+            t_best = t;
+            best_ptr = P.h_tile_ptr;
+            best_cost = cost;
+            best_stage = stage;
+        }
+    }
+    // keep the best partition measured
+    if (best_ptr != P.h_tile_ptr) {
+        std::vector<int32_t> run_ptr;
+        std::vector<GemvRun> runs;
+        if (int st = partition_tiles(P, pc, G, best_cost, best_stage, run_ptr, runs)) return st;
+        dfree(P.run_ptr);
+        dfree(P.runs);
+        if (int st = upload(&P.run_ptr, run_ptr)) return st;
+        if (int st = upload(&P.runs, runs)) return st;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (gain) *gain = t_best > 0.f ? (double)t0 / (double)t_best : 1.0;
     return POLYDG_OK;
 }
 

@@ -93,6 +93,9 @@ struct Plan {
     int64_t* elem_ptr = nullptr;
     double est_seconds = 0.0;           // cost model: slowest CTA's P phase per iteration
     int max_need = 0, max_aggs = 0;     // staged elements per chunk, agglomerates per CTA
+    std::vector<GemvTile> h_tiles;      // the tile sequence and its modelled costs (autotuning)
+    std::vector<double> h_cost, h_stage;
+    std::vector<int32_t> h_tile_ptr;
     void release() {
         dfree(run_ptr); dfree(sub_pairs); dfree(crow_ptr); dfree(need_ptr); dfree(need);
         dfree(cta_chunk); dfree(chunk_elem);

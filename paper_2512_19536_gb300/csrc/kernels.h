@@ -123,6 +123,7 @@ struct PersistArgs {
     double* bcast;
     GridSync* gs;
     int* err;
+    long long* cta_cycles;                     // [2 * grid] P and CM work cycles per CTA, or null
 };
 
 constexpr int kMaxWarpStages = 4;              // copy slots per warp in the P phase

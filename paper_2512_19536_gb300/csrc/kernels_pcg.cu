@@ -160,8 +160,13 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
     else if (bb == 0.0) { done = 2; }
     else { relres = sqrt(rr / bb); if (rr <= rtol2 * bb) done = 1; }
 
+    // per-CTA work time of the P and the coarse + CM phases (thread 0, SM cycles), for
+    // the tile-partition autotuner; the clock reads are skipped unless requested
+    const bool timing = a.cta_cycles != nullptr;
+    long long cyc_p = 0, cyc_cm = 0, t_mark = 0;
     while (!done) {
         // ---------------------------------------------------------------- P
+        if (timing && threadIdx.x == 0) t_mark = clock64();
         const double* rin = a.r[par];
         double* rout = a.r[par ^ 1];
         const double* pold = a.p[pp];
@@ -253,6 +258,10 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 prefetch_l2(c, (uint32_t)min((int64_t)65536, (int64_t)(hi - c)));
         }
         // stopping test by thread 0: 0 go on, 1 converged, 2 non-finite, 3 maxit
+        if (timing) {
+            __syncthreads();
+            if (threadIdx.x == 0) cyc_p += clock64() - t_mark;
+        }
         ok = barrier_sum<1>(a.gs, G, cta, gen, a.err, a.partials, v1, red, outv, [&](const double* sm) {
             const double r2 = sm[0];
             scode = !isfinite(r2) ? 2 : (r2 <= rtol2 * bb) ? 1 : (it + pending >= maxit) ? 3 : 0;
@@ -269,6 +278,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         if (code == 3) { status = kENOTCONV; break; }
         const double* rk = a.r[par];              // r_{k+1}
         const double* qk = a.q[pp];               // q_k
+        if (timing && threadIdx.x == 0) t_mark = clock64();
         // ---------------------------------------------------------------- coarse
         if (coarse) {
             if (a.redundant || c1 > c0) {
@@ -347,6 +357,10 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
             });
         }
         // beta, p.q and alpha by thread 0: code 0 go on, 2 non-finite, 4 breakdown
+        if (timing) {
+            __syncthreads();
+            if (threadIdx.x == 0) cyc_cm += clock64() - t_mark;
+        }
         ok = barrier_sum<3>(a.gs, G, cta, gen, a.err, a.partials, v3, red, outv, [&](const double* sm) {
             const double rz_new = sm[0], zq = sm[1], zw = sm[2];
             if (!isfinite(rz_new) || !isfinite(zq) || !isfinite(zw)) { scode = 2; return; }
@@ -378,6 +392,10 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
     if (!a.identity && has_rows) {      // bounded wait for this warp's copies still in flight
         for (uint32_t c = n_done; c < n_issued; ++c)
             if (!mbar_wait(&wbars[warp][c % S], (c / S) & 1)) break;
+    }
+    if (timing && threadIdx.x == 0) {
+        a.cta_cycles[cta] = cyc_p;
+        a.cta_cycles[G + cta] = cyc_cm;
     }
     if (cta == 0 && threadIdx.x == 0) {
         relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;

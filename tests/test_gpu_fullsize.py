@@ -113,3 +113,20 @@ def test_fullsize_200_coupled_steps_mixed_form(big):
     rest = np.zeros(d.n_dofs); rest[::d.n_p] = w.u_rest
     dev_ref = ref.U - rest
     assert np.sqrt((got - ref.U) @ (d.M @ (got - ref.U))) <= 1e-3 * np.sqrt(dev_ref @ (d.M @ dev_ref))
+
+
+@pytest.mark.parametrize("prec,flexible", [("fp32", True), ("fp64", False)])
+def test_fullsize_autotuned_partition_keeps_the_solution(big, prec, flexible):
+    """The autotuned split of the local-inverse rows only regroups the per-CTA partial
+    sums: the solution still matches the direct solve within the same bound."""
+    w, d, ctx = big
+    pd = lib()
+    pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision=prec)
+    gain = pd.asm_autotune(pc, rounds=3, iterations=30)
+    assert gain >= 1.0                       # the best measured partition is kept
+    b = np.random.default_rng(23).standard_normal(d.n_dofs)
+    x = dev(np.zeros(d.n_dofs))
+    st = pd.pcg_solve(ctx, pc, dev(b), x, rtol=1e-12, maxit=20000, flexible=flexible)
+    lu = cached(("splu", "voronoi4096"), lambda: spla.splu(d.K.tocsc()))
+    assert st["status"] == 0
+    assert mnorm_rel(d, host(x), lu.solve(b)) <= 1e-8
