@@ -302,7 +302,9 @@ int guess_train_step(guess_model *model, polydg_ctx *ctx, const double *traj_dev
 /* Use `model` (NULL: none) for the initial guess of the simulation's later steps: from
  * k = 2 on, each step computes the proposal x0 and starts PCG from it --
  *   policy 0: only if |b - K x0|_2 < |b - K U^k|_2 (else from U^k);
- *   policy 1: always.
+ *   policy 1: always;
+ *   policy 2: from U^k + theta (x0 - U^k) with theta minimising |b - K x|_2 on that line
+ *             (from the same pass over K_h; the residual never exceeds U^k's).
  * The FP64 stopping test decides convergence either way, so only iteration counts
  * change.  The model must outlive its use; it may be shared by several simulations. */
 int sim_set_guess(sim_ctx *sim, guess_model *model, int policy);

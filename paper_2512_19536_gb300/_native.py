@@ -456,7 +456,8 @@ def guess_train_step(model: GuessModel, ctx: PolyDG, traj, samples, lr, stream=N
 
 
 def sim_set_guess(sim: Simulation, model, policy=0):
-    """policy 0: start from the proposal only if its residual is smaller; 1: always."""
+    """policy 0: start from the proposal only if its residual is smaller; 1: always;
+    2: from U^k + theta (proposal - U^k), theta minimising the residual on that line."""
     _check(load().sim_set_guess(sim.h, model.h if model is not None else None, int(policy)))
     sim.guess = model
 

@@ -1585,7 +1585,7 @@ int guess_train_step(guess_model* g, polydg_ctx* c, const double* traj_dev, int6
 int sim_set_guess(sim_ctx* sm, guess_model* g, int policy) {
     if (!sm) { set_error("sim_set_guess: null simulation"); return POLYDG_EINVAL; }
     if (g && g->np != sm->ctx->H.n_p) { set_error("sim_set_guess: model and mesh differ in n_p"); return POLYDG_EINVAL; }
-    if (policy != 0 && policy != 1) { set_error("sim_set_guess: policy must be 0 or 1"); return POLYDG_EINVAL; }
+    if (policy < 0 || policy > 2) { set_error("sim_set_guess: policy must be 0, 1 or 2"); return POLYDG_EINVAL; }
     if (sm->guess != g || sm->guess_policy != policy) {
         sm->guess = g;
         sm->guess_policy = policy;

@@ -178,7 +178,7 @@ struct sim_ctx {
     sim_params prm{};
     PcgWork work;
     guess_model* guess = nullptr;       // learned initial guess (nullptr: x0 = U^k)
-    int guess_policy = 0;               // 0: keep the smaller residual, 1: always the proposal
+    int guess_policy = 0;               // 0 keep the smaller residual, 1 always, 2 damped
     shared_local* shared = nullptr;     // local solves shared with other simulations (batches)
     double sigma = 0.0;                 // its scalar conductivity when `shared` is set
     int64_t version = 0;                // bumped when the step's kernel sequence changes

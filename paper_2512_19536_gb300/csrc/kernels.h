@@ -25,6 +25,7 @@ struct SimScalars {
     int64_t guesses_taken; // steps (of this call) that started from the learned guess
     uint32_t guess_ticket; // last-CTA ticket of the guess selection
     uint32_t pad;
+    double theta;          // x0 = U^k + theta (guess - U^k) when use_guess
 };
 
 // Block-sparse K_h on the device (internal cell order).
@@ -252,7 +253,7 @@ cudaError_t launch_guess_propose(int np, const GuessFeat& f, const __half* w16, 
                                  const double* Uk1, const double* Uk2, double* xg, int64_t nc,
                                  const SimScalars* ss, cudaStream_t s);
 cudaError_t launch_guess_select(int np, const DeviceMatrix& K, const double* b, const double* xg,
-                                const double* uk, double* partials, SimScalars* ss, int always,
+                                const double* uk, double* partials, SimScalars* ss, int policy,
                                 cudaStream_t s);
 cudaError_t launch_select_copy(const double* uk, const double* xg, double* x0, int64_t n,
                                const SimScalars* ss, cudaStream_t s);

@@ -200,15 +200,17 @@ __global__ void __launch_bounds__(kBlock)
 guess_select_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                     const double* __restrict__ val, const double* __restrict__ b,
                     const double* __restrict__ xg, const double* __restrict__ uk, int64_t nc,
-                    double* partials, SimScalars* ss, int always) {
+                    double* partials, SimScalars* ss, int policy) {
     if (ss->failed || ss->k < 2) return;
-    if (always) {                                 // policy: start from every proposal
+    if (policy == 1) {                            // start from every proposal
         if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ss->theta = 1.0;
             ss->use_guess = 1;
             ss->guesses_taken += 1;
         }
         return;
     }
+    const bool damped = policy == 2;
     __shared__ double sh[32];
     __shared__ bool last;
     constexpr int G = 32 / NP;
@@ -235,32 +237,46 @@ guess_select_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restri
         tg += __shfl_down_sync(0xffffffffu, ag, k * NP);
         t0 += __shfl_down_sync(0xffffffffu, a0, k * NP);
     }
-    double dg = 0.0, d0 = 0.0;
+    double dg = 0.0, d0 = 0.0, dx = 0.0;
     if (e < nc && lane < NP) {
         const double bv = b[e * NP + i];
         dg = (bv - tg) * (bv - tg);
         d0 = (bv - t0) * (bv - t0);
+        dx = (bv - t0) * (bv - tg);
     }
-    double s[2];
+    double s[3];
     s[0] = block_sum(dg, sh);
     s[1] = block_sum(d0, sh);
-    if (publish_partials(partials, s, 2, &ss->guess_ticket, &last)) {
+    s[2] = block_sum(dx, sh);
+    if (publish_partials(partials, s, 3, &ss->guess_ticket, &last)) {
         const double rg = sum_partials(partials, gridDim.x, sh);
         const double r0 = sum_partials(partials + kMaxPartials, gridDim.x, sh);
+        const double rx = sum_partials(partials + 2 * kMaxPartials, gridDim.x, sh);
         if (threadIdx.x == 0) {
             ss->guess_ticket = 0;
-            ss->use_guess = (rg < r0) ? 1 : 0;
-            ss->guesses_taken += (rg < r0) ? 1 : 0;
+            if (damped) {
+                // x0 = U^k + theta (xg - U^k); with K d = r0 - rg the residual b - K x0 =
+                // r0 - theta K d is smallest at theta = r0.Kd / Kd.Kd (never above |r0|)
+                const double kd2 = r0 - 2.0 * rx + rg, r0kd = r0 - rx;
+                const double th = (kd2 > 0.0 && isfinite(kd2) && isfinite(r0kd)) ? r0kd / kd2 : 0.0;
+                ss->theta = th;
+                ss->use_guess = th != 0.0 ? 1 : 0;
+                ss->guesses_taken += th != 0.0 ? 1 : 0;
+            } else {
+                ss->theta = 1.0;
+                ss->use_guess = (rg < r0) ? 1 : 0;
+                ss->guesses_taken += (rg < r0) ? 1 : 0;
+            }
         }
     }
 }
 
-// x0 = guess if it was kept, else U^k.
+// x0 = U^k + theta (guess - U^k) if the guess was kept, else U^k.
 __global__ void select_copy_kernel(const double* __restrict__ uk, const double* __restrict__ xg,
                                    double* __restrict__ x0, int64_t n, const SimScalars* ss) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ss->failed || t >= n) return;
-    x0[t] = ss->use_guess ? xg[t] : uk[t];
+    x0[t] = ss->use_guess ? fma(ss->theta, xg[t] - uk[t], uk[t]) : uk[t];
 }
 
 // ------------------------------------------------------------------ training
@@ -481,13 +497,13 @@ cudaError_t launch_guess_propose(int np, const GuessFeat& f, const __half* w16, 
 }
 
 cudaError_t launch_guess_select(int np, const DeviceMatrix& K, const double* b, const double* xg,
-                                const double* uk, double* partials, SimScalars* ss, int always,
+                                const double* uk, double* partials, SimScalars* ss, int policy,
                                 cudaStream_t s) {
-    const unsigned grid = always ? 1u : (unsigned)((K.nc * 32 + kBlock - 1) / kBlock);
+    const unsigned grid = policy == 1 ? 1u : (unsigned)((K.nc * 32 + kBlock - 1) / kBlock);
     if (grid > (unsigned)kMaxPartials) return cudaErrorInvalidValue;
     GUESS_NP_SWITCH(np, {
         guess_select_kernel<NP><<<grid, kBlock, 0, s>>>(K.row_ptr, K.col, K.val, b, xg, uk, K.nc,
-                                                        partials, ss, always);
+                                                        partials, ss, policy);
     })
     return cudaGetLastError();
 }
