@@ -202,6 +202,21 @@ int asm_apply(asm_ctx *pc, const double *r_dev, double *z_dev, void *stream);
 int pcg_solve(polydg_ctx *ctx, asm_ctx *pc, const double *b_dev, double *x_dev,
               double rtol, int maxit, int flexible, void *stream, pcg_stats *stats);
 
+/* pcg_solve that also records alpha_k (k < capacity) and beta_k (the coefficient that
+ * forms p_{k+1}) into host arrays alphas[capacity], betas[capacity] (zeros past the last
+ * iteration).  With flexible = 0 they define the Lanczos tridiagonal of B_ad^{-1} K_h
+ * (Sec. 5: condition-number estimates; see pcg_lanczos_extremes). */
+int pcg_solve_trace(polydg_ctx *ctx, asm_ctx *pc, const double *b_dev, double *x_dev,
+                    double rtol, int maxit, int flexible, void *stream, pcg_stats *stats,
+                    double *alphas, double *betas, int capacity);
+
+/* Extreme eigenvalues of the Lanczos tridiagonal T of m PCG steps (host): T_kk =
+ * 1/alpha_k + beta_{k-1}/alpha_{k-1}, T_{k,k+1} = sqrt(beta_k)/alpha_k (Saad, Iterative
+ * Methods, Sec. 6.7.3); estimates of lambda_min, lambda_max of the preconditioned
+ * operator, kappa = lmax / lmin.  Returns POLYDG_OK, EINVAL or ENOTCONV. */
+int pcg_lanczos_extremes(const double *alphas, const double *betas, int m, double *lmin,
+                         double *lmax);
+
 /* Create a coupled simulation on ctx/pc (pc may be NULL for plain CG). */
 int sim_create(polydg_ctx *ctx, asm_ctx *pc, const sim_params *params, sim_ctx **out);
 

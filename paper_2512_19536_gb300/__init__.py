@@ -6,7 +6,7 @@ the package does not load the library; the first call does, and fails loudly
 if it has not been built.
 """
 from ._native import (PolyDG, ASM, Simulation, PolyDGError, load, polydg_setup, asm_setup,
-                      asm_apply, asm_autotune, pcg_solve, sim_create, monodomain_step, sim_get_state,
+                      asm_apply, asm_autotune, pcg_solve_trace, lanczos_extremes, pcg_solve, sim_create, monodomain_step, sim_get_state,
                       sim_set_potential, spd_inverse_static, Batch, batch_create, batch_step,
                       GuessModel, guess_n_params, guess_create, guess_propose, guess_train_step,
                       sim_set_guess, SharedLocal, shared_local_setup, shared_local_apply,
@@ -15,7 +15,7 @@ from ._native import (PolyDG, ASM, Simulation, PolyDGError, load, polydg_setup, 
                       POLYDG_EBREAKDOWN, POLYDG_ENONFINITE)
 
 __all__ = ["PolyDG", "ASM", "Simulation", "PolyDGError", "load", "polydg_setup", "asm_setup",
-           "asm_apply", "asm_autotune", "pcg_solve", "sim_create", "monodomain_step", "sim_get_state",
+           "asm_apply", "asm_autotune", "pcg_solve_trace", "lanczos_extremes", "pcg_solve", "sim_create", "monodomain_step", "sim_get_state",
            "sim_set_potential", "spd_inverse_static", "Batch", "batch_create", "batch_step",
            "GuessModel", "guess_n_params", "guess_create", "guess_propose", "guess_train_step",
            "sim_set_guess", "SharedLocal", "shared_local_setup", "shared_local_apply",

@@ -28,7 +28,7 @@ EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_get_info", "polydg_get_f
            "guess_create", "guess_get_params", "guess_set_scales", "guess_propose",
            "guess_train_step", "sim_set_guess", "guess_destroy", "polydg_sym_eig",
            "shared_local_setup", "shared_local_info", "shared_local_apply", "shared_local_destroy",
-           "sim_set_shared_local", "asm_autotune"]
+           "sim_set_shared_local", "asm_autotune", "pcg_solve_trace", "pcg_lanczos_extremes"]
 
 
 class polydg_mesh(C.Structure):
@@ -121,6 +121,10 @@ def load() -> C.CDLL:
     L.shared_local_apply.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(vp), pd_, vp]
     for name in ("shared_local_setup", "shared_local_info", "shared_local_apply"):
         getattr(L, name).restype = i32
+    L.pcg_solve_trace.argtypes = [vp, vp, vp, vp, dbl, i32, i32, vp, C.POINTER(pcg_stats), pd_, pd_, i32]
+    L.pcg_solve_trace.restype = i32
+    L.pcg_lanczos_extremes.argtypes = [pd_, pd_, i32, pd_, pd_]
+    L.pcg_lanczos_extremes.restype = i32
     L.asm_autotune.argtypes = [vp, i32, i32, pd_]
     L.asm_autotune.restype = i32
     L.sim_set_shared_local.argtypes = [vp, vp]
@@ -276,6 +280,32 @@ def pcg_solve(ctx: PolyDG, pc, b, x, rtol=1e-8, maxit=10000, flexible=False, str
     _check(status, allow)
     return {"iterations": st.iterations, "status": st.status, "relres": st.relres,
             "bnorm": st.bnorm}
+
+
+def pcg_solve_trace(ctx: PolyDG, pc, b, x, rtol=1e-8, maxit=10000, flexible=False, stream=None,
+                    allow=(POLYDG_ENOTCONV,)):
+    """pcg_solve that also returns (alphas, betas) of every iteration (numpy arrays)."""
+    st = pcg_stats()
+    cap = int(maxit)
+    al, be = np.zeros(cap), np.zeros(cap)
+    status = load().pcg_solve_trace(ctx.h, pc.h if pc is not None else None, _dev(b), _dev(x),
+                                    float(rtol), int(maxit), int(bool(flexible)), _stream(stream),
+                                    C.byref(st), _ptr(al, C.c_double), _ptr(be, C.c_double), cap)
+    _check(status, allow)
+    its = st.iterations
+    return ({"iterations": its, "status": st.status, "relres": st.relres, "bnorm": st.bnorm},
+            al[:its].copy(), be[:max(its - 1, 0)].copy())
+
+
+def lanczos_extremes(alphas, betas):
+    """(lambda_min, lambda_max) of the Lanczos tridiagonal of PCG coefficients."""
+    a = np.ascontiguousarray(alphas, np.float64)
+    b = np.zeros(max(len(a), 1))
+    b[:len(betas)] = betas
+    lo, hi = C.c_double(), C.c_double()
+    _check(load().pcg_lanczos_extremes(_ptr(a, C.c_double), _ptr(b, C.c_double), len(a),
+                                       C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
 
 
 class Simulation:

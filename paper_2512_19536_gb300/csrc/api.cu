@@ -331,9 +331,12 @@ static PersistArgs persist_args(polydg_ctx* c, asm_ctx* pc, const Plan& P, PcgWo
 
 // Enqueue one persistent PCG solve of K x = b on the vectors of w (internal
 // order; x holds x0).  The scalars in w.sc must hold rtol2, maxit, flexible and done = 0.
-static int run_pcg(polydg_ctx* c, asm_ctx* pc, PcgWork& w, cudaStream_t s) {
+static int run_pcg(polydg_ctx* c, asm_ctx* pc, PcgWork& w, cudaStream_t s, double* trace = nullptr,
+                   int trace_cap = 0) {
     const Plan& P = pc ? pc->plan : c->id_plan;
-    const PersistArgs a = persist_args(c, pc, P, w);
+    PersistArgs a = persist_args(c, pc, P, w);
+    a.trace = trace;
+    a.trace_cap = trace_cap;
     CU(cudaMemsetAsync(&w.gs->count, 0, sizeof(unsigned), s));
     CU(launch_pcg_persistent(P.dtype, c->H.n_p, a, P.smem, s));
     return POLYDG_OK;
@@ -820,12 +823,17 @@ int asm_apply(asm_ctx* pc, const double* r_dev, double* z_dev, void* stream) {
     return POLYDG_OK;
 }
 
-int pcg_solve(polydg_ctx* c, asm_ctx* pc, const double* b_dev, double* x_dev, double rtol,
-              int maxit, int flexible, void* stream, pcg_stats* stats) {
+int pcg_solve_trace(polydg_ctx* c, asm_ctx* pc, const double* b_dev, double* x_dev, double rtol,
+                    int maxit, int flexible, void* stream, pcg_stats* stats, double* alphas,
+                    double* betas, int capacity) {
+    if (capacity < 0 || (capacity > 0 && (!alphas || !betas))) {
+        set_error("pcg_solve_trace: capacity >= 0 and two host arrays of that length");
+        return POLYDG_EINVAL;
+    }
     if (int st = check_ctx(c, "pcg_solve")) return st;
-    if (!b_dev || !x_dev || b_dev == x_dev) { set_error("pcg_solve: null or aliased vectors"); return POLYDG_EINVAL; }
-    if (!(rtol > 0) || maxit < 1) { set_error("pcg_solve: rtol must be > 0 and maxit >= 1"); return POLYDG_EINVAL; }
-    if (pc && pc->ctx != c) { set_error("pcg_solve: preconditioner built on another context"); return POLYDG_EINVAL; }
+    if (!b_dev || !x_dev || b_dev == x_dev) { set_error("pcg_solve_trace: null or aliased vectors"); return POLYDG_EINVAL; }
+    if (!(rtol > 0) || maxit < 1) { set_error("pcg_solve_trace: rtol must be > 0 and maxit >= 1"); return POLYDG_EINVAL; }
+    if (pc && pc->ctx != c) { set_error("pcg_solve_trace: preconditioner built on another context"); return POLYDG_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     const int np = c->H.n_p;
     PcgScalars init = {};
@@ -837,10 +845,19 @@ int pcg_solve(polydg_ctx* c, asm_ctx* pc, const double* b_dev, double* x_dev, do
     CU(cudaMemsetAsync(c->work.err, 0, sizeof(int), s));
     CU(launch_permute(b_dev, nullptr, c->work.b, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
     CU(launch_permute(x_dev, nullptr, c->work.x[0], c->d_to_caller, c->H.nc, np, 1, nullptr, s));
-    if (int st = run_pcg(c, pc, c->work, s)) return st;
+    double* d_trace = nullptr;
+    if (capacity > 0)
+        if (int st = dalloc(&d_trace, 2 * (size_t)capacity)) return st;
+    struct Guard { double*& p; ~Guard() { dfree(p); } } guard{d_trace};
+    if (capacity > 0) CU(cudaMemsetAsync(d_trace, 0, 2 * (size_t)capacity * sizeof(double), s));
+    if (int st = run_pcg(c, pc, c->work, s, d_trace, capacity)) return st;
     CU(launch_permute(c->work.x[0], c->work.x[1], x_dev, c->d_to_caller, c->H.nc, np, 0, c->work.sc, s));
     CU(cudaMemcpyAsync(c->h_sc, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    if (capacity > 0) {
+        CU(cudaMemcpy(alphas, d_trace, capacity * sizeof(double), cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(betas, d_trace + capacity, capacity * sizeof(double), cudaMemcpyDeviceToHost));
+    }
     const PcgScalars& r = *c->h_sc;
     if (stats) {
         stats->iterations = r.it;
@@ -849,12 +866,45 @@ int pcg_solve(polydg_ctx* c, asm_ctx* pc, const double* b_dev, double* x_dev, do
         stats->bnorm = std::sqrt(r.bb);
     }
     if (r.status != 0) {
-        set_error(r.status == POLYDG_ECUDA ? "pcg_solve: a device-side wait timed out"
-                  : r.status == POLYDG_ENOTCONV ? "pcg_solve: maximum number of iterations reached"
-                  : r.status == POLYDG_EBREAKDOWN ? "pcg_solve: breakdown (p^T K p <= 0 or non-finite beta)"
-                                                  : "pcg_solve: non-finite value in b or the residual");
+        set_error(r.status == POLYDG_ECUDA ? "pcg_solve_trace: a device-side wait timed out"
+                  : r.status == POLYDG_ENOTCONV ? "pcg_solve_trace: maximum number of iterations reached"
+                  : r.status == POLYDG_EBREAKDOWN ? "pcg_solve_trace: breakdown (p^T K p <= 0 or non-finite beta)"
+                                                  : "pcg_solve_trace: non-finite value in b or the residual");
     }
     return r.status;
+}
+
+int pcg_solve(polydg_ctx* c, asm_ctx* pc, const double* b_dev, double* x_dev, double rtol,
+              int maxit, int flexible, void* stream, pcg_stats* stats) {
+    return pcg_solve_trace(c, pc, b_dev, x_dev, rtol, maxit, flexible, stream, stats, nullptr,
+                           nullptr, 0);
+}
+
+int pcg_lanczos_extremes(const double* alphas, const double* betas, int m, double* lmin, double* lmax) {
+    if (m < 1 || !alphas || !betas || !lmin || !lmax) {
+        set_error("pcg_lanczos_extremes: need m >= 1 coefficients and output pointers");
+        return POLYDG_EINVAL;
+    }
+    // T_kk = 1/alpha_k + beta_{k-1}/alpha_{k-1}, T_{k,k+1} = sqrt(beta_k)/alpha_k
+    std::vector<double> T((size_t)m * m, 0.0), w(m), q((size_t)m * m);
+    for (int k = 0; k < m; ++k) {
+        if (!(alphas[k] > 0.0) || (k < m - 1 && !(betas[k] >= 0.0))) {
+            set_error("pcg_lanczos_extremes: alphas must be > 0 and betas >= 0");
+            return POLYDG_EINVAL;
+        }
+        T[(size_t)k * m + k] = 1.0 / alphas[k] + (k > 0 ? betas[k - 1] / alphas[k - 1] : 0.0);
+        if (k < m - 1) {
+            const double e = std::sqrt(betas[k]) / alphas[k];
+            T[(size_t)k * m + k + 1] = T[(size_t)(k + 1) * m + k] = e;
+        }
+    }
+    if (!sym_eig(m, T.data(), w.data(), q.data())) {
+        set_error("pcg_lanczos_extremes: eigenvalue iteration did not converge");
+        return POLYDG_ENOTCONV;
+    }
+    *lmin = w[0];
+    *lmax = w[m - 1];
+    return POLYDG_OK;
 }
 
 int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out) {

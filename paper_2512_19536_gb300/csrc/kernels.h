@@ -125,6 +125,9 @@ struct PersistArgs {
     GridSync* gs;
     int* err;
     long long* cta_cycles;                     // [2 * grid] P and CM work cycles per CTA, or null
+    double* trace;                             // [2 * trace_cap]: alpha_k, then beta_k, or null
+    int trace_cap;
+    int pad_trace;
 };
 
 constexpr int kMaxWarpStages = 4;              // copy slots per warp in the P phase

@@ -303,10 +303,20 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 return warp_sum(s0 + s1);
             };
             if (a.redundant) {                    // y0 of this CTA's agglomerates only
-                for (int w2 = warp; w2 < n_aggs * a.nq; w2 += nw) {
-                    const int jl = w2 / a.nq, kq = w2 - jl * a.nq;
-                    const double y = coarse_row(aggs[jl] * a.nq + kq);
-                    if (lane == 0) y0l[w2] = y;
+                // eight rows per warp, four lanes per row: two shuffle levels per row
+                // instead of a 32-lane butterfly (fp64 adds are scarce on this GPU)
+                const int sub = lane >> 2, l4 = lane & 3, nrows = n_aggs * a.nq;
+                for (int base = warp * 8; base < nrows; base += nw * 8) {
+                    const int w2 = base + sub;
+                    double acc = 0.0;
+                    if (w2 < nrows) {
+                        const int jl = w2 / a.nq, kq = w2 - jl * a.nq;
+                        const double* Kr = a.K0inv + (int64_t)(aggs[jl] * a.nq + kq) * a.ld0;
+                        for (int c = l4; c < a.n0; c += 4) acc = fma(__ldg(Kr + c), r0s[c], acc);
+                    }
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                    if (l4 == 0 && w2 < nrows) y0l[w2] = acc;
                 }
             } else {                              // distributed coarse rows, then a barrier
                 for (int row = c0 + warp; row < c1; row += nw) {
@@ -374,6 +384,10 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
             scal[1] = bnew;
             scal[2] = pq_new;
             scode = 0;
+            if (a.trace && cta == 0) {            // alpha_k and beta_{k-1} for Lanczos estimates
+                if (it < a.trace_cap) a.trace[it] = scal[0];
+                if (it > 0 && it - 1 < a.trace_cap) a.trace[a.trace_cap + it - 1] = bnew;
+            }
         });
         if (!ok) { status = kEDEVICE; break; }
         const int code3 = scode;

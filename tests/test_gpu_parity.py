@@ -277,3 +277,27 @@ def test_coupled_steps_mixed_precision(vor):
     ref = oracle_coupled(w, d, steps)[-1]
     assert st["status"] == 0
     assert mnorm_rel(d, u, ref.U) <= 1e-8
+
+
+def test_traced_pcg_coefficients_and_condition_estimate(sq):
+    """alpha_k, beta_k of the GPU's plain fp64 PCG against the oracle's PCG with the
+    same preconditioner (the first coefficients agree to rounding, which grows slowly
+    along the iteration), and the Lanczos estimate of kappa(B_ad^{-1} K) from each."""
+    from oracle import schwarz
+    from oracle.pcg import pcg, lanczos_extremes
+    w, d, ctx = sq
+    pd = lib()
+    pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision="fp64")
+    from synth import random_rhs
+    b = random_rhs(d.n_dofs, 31)
+    x = dev(np.zeros(d.n_dofs))
+    st, al, be = pd.pcg_solve_trace(ctx, pc, dev(b), x, rtol=1e-10, maxit=500)
+    S = cached(("schwarz", w.name), lambda: schwarz.build(d, w.subdomain, w.coarse, w.q))
+    ref = pcg(d.K, b, prec=S.apply, rtol=1e-10, maxit=500)
+    assert st["status"] == 0 and abs(st["iterations"] - ref.iterations) <= 1
+    k = min(8, len(ref.alphas))
+    assert np.allclose(al[:k], ref.alphas[:k], rtol=1e-8)
+    assert np.allclose(be[:k - 1], ref.betas[:k - 1], rtol=1e-8)
+    lo, hi = pd.lanczos_extremes(al, be)
+    olo, ohi = lanczos_extremes(ref.alphas, ref.betas)
+    assert abs(hi / lo - ohi / olo) <= 1e-6 * (ohi / olo)
