@@ -52,6 +52,20 @@ BATCH_WORKLOAD = ("batch32: 32 coupled simulations, 8 Voronoi meshes 1024-16384 
 WORKLOAD = "voronoi4096_p3 coupled monodomain+Barreto-Cressman, 40960 DOFs, 64 subdomains, coarse P1"
 
 
+def reduce_over_ranks(torch, times_ms, rates, world, device):
+    """Replicas: every rank times its own copy of the workload; the job is as slow as
+    its slowest rank (max of the times) and its end-to-end rate that of the slowest
+    (min of the rates).  Returns (times_ms, rates) as lists of floats, identical on
+    every rank."""
+    if world <= 1:
+        return list(times_ms), list(rates)
+    t = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    r = torch.tensor(list(rates) if rates else [0.0], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(r, op=torch.distributed.ReduceOp.MIN)
+    return [float(x) for x in t], ([float(x) for x in r] if rates else [])
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -300,18 +314,12 @@ def main():
     # fp64 plain form on the same workload, for the comparison the metric names
     pc64, sim64, st64, ms64 = time_form(pd, torch, w, ctx, "fp64", False, args.steps,
                                         args.warmup, stream)
-    t = torch.tensor([ms, ms64, ms_ng], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms, ms64, ms_ng = float(t[0]), float(t[1]), float(t[2])
+    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, max(5, args.steps // 8), stream, guess)
+    (ms, ms64, ms_ng), (e2e_rank,) = reduce_over_ranks(torch, [ms, ms64, ms_ng], [e2e_val], world, "cuda")
     value = world * args.steps / (ms * 1e-3)
     value64 = world * args.steps / (ms64 * 1e-3)
     value_ng = world * args.steps / (ms_ng * 1e-3)
-    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, max(5, args.steps // 8), stream, guess)
-    if world > 1:
-        te = torch.tensor([e2e_val], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MIN)
-        e2e_val = world * float(te[0])
+    e2e_val = world * e2e_rank
 
     info = pc.info()
     launches = st["steps_done"]
@@ -450,7 +458,7 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
             pd.sim_get_state(s_, d_, stream=stream)
             h_.copy_(d_, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_val = world * S * e_steps / (time.perf_counter() - t0)
+    e2e_rate = S * e_steps / (time.perf_counter() - t0)
     groups = bt.groups().tolist()
     bt.close()
     del trip, sims, shared, du, hu
@@ -475,10 +483,8 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
     ev1.record(stream)
     torch.cuda.synchronize()
     ms64 = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms, ms32, ms64], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms, ms32, ms64 = float(t[0]), float(t[1]), float(t[2])
+    (ms, ms32, ms64), (e2e_rate,) = reduce_over_ranks(torch, [ms, ms32, ms64], [e2e_rate], world, "cuda")
+    e2e_val = world * e2e_rate
     value = world * S * args.steps / (ms * 1e-3)
     value32 = world * S * args.steps / (ms32 * 1e-3)
     value64 = world * S * args.steps / (ms64 * 1e-3)
