@@ -177,14 +177,15 @@ int asm_setup(polydg_ctx *ctx, const int32_t *coarse_of_cell, int q, int precisi
 
 int asm_get_info(const asm_ctx *pc, asm_info *out);
 
-/* Autotune the split of the local-inverse rows over the CTAs of pcg_solve and
- * monodomain_step with this preconditioner: time `iterations` PCG iterations (a fixed
- * right-hand side on the context's work vectors, default stream), read every CTA's
- * P-phase cycle count, rescale the modelled cost of each CTA's tiles by its measured /
- * modelled share, re-cut the tile sequence, and repeat `rounds` times; the fastest
- * partition measured is kept.  *gain (may be NULL) = time before / time after.  Results of
- * later solves change only by rounding (the per-CTA partial sums are grouped differently).
- * Synchronises the device.  Errors: EINVAL, ECUDA. */
+/* Autotune how pcg_solve and monodomain_step with this preconditioner split their work
+ * over the CTAs: time `iterations` PCG iterations (a fixed right-hand side on the
+ * context's work vectors, default stream) with per-CTA cycle counters, then alternate two
+ * moves `rounds` times each -- re-cut the rows of the local inverses with every CTA's
+ * tile costs rescaled by its measured / modelled P-phase share, and re-split the elements
+ * so that the CTAs' measured CM-phase cycles even out -- keeping a move only if the timed
+ * iterations got faster.  *gain (may be NULL) = time before / time after.  Later solves
+ * change only by rounding (the per-CTA partial sums are grouped differently).
+ * Synchronises the device.  Errors: EINVAL, ENOMEM, ECUDA. */
 int asm_autotune(asm_ctx *pc, int rounds, int iterations, double *gain);
 
 /* z = B_ad^{-1} r (Eq. prec).  r_dev and z_dev are caller-order device vectors

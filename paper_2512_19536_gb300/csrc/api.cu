@@ -109,7 +109,8 @@ static int partition_tiles(Plan& P, const asm_ctx* pc, int G, const std::vector<
 // local inverses) as contiguous runs balanced by bytes, elements and coarse rows
 // evenly; per CTA the elements whose p its matvec rows need (own range first,
 // then face neighbours) and the CTA-local column index of every block.
-static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 0) {
+static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 0,
+                      const std::vector<int64_t>* elem_split = nullptr) {
     const HostSetup& H = c->H;
     const int np = H.n_p;
     P.grid = G;
@@ -133,6 +134,7 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 
     std::vector<int64_t> elem_ptr(G + 1), chunk_elem;
     std::vector<int32_t> cta_chunk(G + 1, 0);
     for (int g = 0; g <= G; ++g) elem_ptr[g] = (H.nc * g) / G;
+    if (elem_split && (int)elem_split->size() == G + 1) elem_ptr = *elem_split;
     for (int g = 0; g < G; ++g) {
         cta_chunk[g] = (int32_t)chunk_elem.size();
         const int64_t n_own = elem_ptr[g + 1] - elem_ptr[g];
@@ -724,51 +726,87 @@ int asm_autotune(asm_ctx* pc, int rounds, int iterations, double* gain) {
     if (int st = run(&t0)) return st;         // the first launch warms caches and code
     t_best = t0;
     std::vector<double> cost = P.h_cost, stage = P.h_stage;
-    std::vector<int32_t> best_ptr = P.h_tile_ptr;
-    std::vector<double> best_cost = cost, best_stage = stage;
-    for (int r = 0; r < rounds; ++r) {
-        // rescale every CTA's tile costs by its measured / modelled P-phase time
+    std::vector<int64_t> split(G + 1);
+    CU(cudaMemcpy(split.data(), P.elem_ptr, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    // Moves alternate: (a) re-cut the tile sequence with every CTA's tile costs rescaled
+    // by its measured / modelled P-phase share; (b) re-split the elements so that every
+    // CTA's measured CM cycles, spread evenly over its elements, are equal.  A move is
+    // kept only if the timed iterations got faster; otherwise the previous plan returns
+    // and is timed again (its per-CTA cycles feed the next move).
+    for (int r = 0; r < 2 * rounds; ++r) {
+        const bool tiles_move = (r % 2) == 0;
+        Plan old = P;
+        Plan fresh;
+        std::vector<double> ncost = cost, nstage = stage;
+        std::vector<int64_t> nsplit = split;
         const std::vector<int32_t> tp = P.h_tile_ptr;
-        double tot_m = 0.0, tot_t = 0.0;
-        for (int g = 0; g < G; ++g) {
-            double m = 0.0;
-            for (int32_t k = tp[g]; k < tp[g + 1]; ++k) m += cost[k] + stage[k];
-            tot_m += m;
-            tot_t += (double)cyc[g];
+        if (tiles_move) {
+            double tot_m = 0.0, tot_t = 0.0;
+            std::vector<double> m(G, 0.0);
+            for (int g = 0; g < G; ++g) {
+                for (int32_t k = tp[g]; k < tp[g + 1]; ++k) m[g] += cost[k] + stage[k];
+                tot_m += m[g];
+                tot_t += (double)cyc[g];
+            }
+            if (!(tot_m > 0.0 && tot_t > 0.0)) continue;
+            for (int g = 0; g < G; ++g) {
+                if (m[g] <= 0.0 || cyc[g] <= 0) continue;
+                const double f = ((double)cyc[g] / tot_t) / (m[g] / tot_m);
+                for (int32_t k = tp[g]; k < tp[g + 1]; ++k) { ncost[k] *= f; nstage[k] *= f; }
+            }
+            fresh = P;                        // same arrays except the runs
+            std::vector<int32_t> run_ptr;
+            std::vector<GemvRun> runs;
+            if (int st = partition_tiles(fresh, pc, G, ncost, nstage, run_ptr, runs)) return st;
+            fresh.run_ptr = nullptr;
+            fresh.runs = nullptr;
+            if (int st = upload(&fresh.run_ptr, run_ptr)) return st;
+            if (int st = upload(&fresh.runs, runs)) { dfree(fresh.run_ptr); return st; }
+        } else {
+            std::vector<double> pre(c->H.nc + 1, 0.0);
+            for (int g = 0; g < G; ++g) {
+                const int64_t a0 = split[g], a1 = split[g + 1];
+                const double ce = (a1 > a0 && cyc[G + g] > 0) ? (double)cyc[G + g] / (double)(a1 - a0) : 0.0;
+                for (int64_t e = a0; e < a1; ++e) pre[e + 1] = pre[e] + ce;
+            }
+            if (!(pre[c->H.nc] > 0.0)) continue;
+            int64_t e = 0;
+            for (int g = 1; g < G; ++g) {
+                const double target = pre[c->H.nc] * g / G;
+                while (e < c->H.nc && pre[e + 1] <= target) ++e;
+                nsplit[g] = std::max<int64_t>(nsplit[g - 1], e);
+            }
+            nsplit[0] = 0;
+            nsplit[G] = c->H.nc;
+            if (int st = build_plan(c, pc, G, fresh, 0, &nsplit)) { fresh.release(); return st; }
+            std::vector<int32_t> run_ptr;
+            std::vector<GemvRun> runs;
+            if (int st = partition_tiles(fresh, pc, G, cost, stage, run_ptr, runs)) { fresh.release(); return st; }
+            fresh.h_cost = cost;
+            fresh.h_stage = stage;
+            dfree(fresh.run_ptr);
+            dfree(fresh.runs);
+            if (int st = upload(&fresh.run_ptr, run_ptr)) { fresh.release(); return st; }
+            if (int st = upload(&fresh.runs, runs)) { fresh.release(); return st; }
         }
-        if (tot_m <= 0.0 || tot_t <= 0.0) break;
-        for (int g = 0; g < G; ++g) {
-            double m = 0.0;
-            for (int32_t k = tp[g]; k < tp[g + 1]; ++k) m += cost[k] + stage[k];
-            if (m <= 0.0 || cyc[g] <= 0) continue;
-            const double f = ((double)cyc[g] / tot_t) / (m / tot_m);
-            for (int32_t k = tp[g]; k < tp[g + 1]; ++k) { cost[k] *= f; stage[k] *= f; }
-        }
-        std::vector<int32_t> run_ptr;
-        std::vector<GemvRun> runs;
-        if (int st = partition_tiles(P, pc, G, cost, stage, run_ptr, runs)) return st;
-        dfree(P.run_ptr);
-        dfree(P.runs);
-        if (int st = upload(&P.run_ptr, run_ptr)) return st;
-        if (int st = upload(&P.runs, runs)) return st;
+        P = fresh;
         float t = 0.f;
-        if (int st = run(&t)) return st;
-        if (t < t_best) {
+        const int st = run(&t);
+        if (st == POLYDG_OK && t < t_best) {   // keep the move: drop what the old plan alone owned
             t_best = t;
-            best_ptr = P.h_tile_ptr;
-            best_cost = cost;
-            best_stage = stage;
+            if (tiles_move) { dfree(old.run_ptr); dfree(old.runs); }
+            else old.release();
+            cost = ncost;
+            stage = nstage;
+            split = nsplit;
+        } else {                               // revert and re-time the kept plan
+            if (tiles_move) { dfree(fresh.run_ptr); dfree(fresh.runs); }
+            else fresh.release();
+            P = old;
+            if (st) return st;
+            float t2 = 0.f;
+            if (int st2 = run(&t2)) return st2;
         }
-    }
-    // keep the best partition measured
-    if (best_ptr != P.h_tile_ptr) {
-        std::vector<int32_t> run_ptr;
-        std::vector<GemvRun> runs;
-        if (int st = partition_tiles(P, pc, G, best_cost, best_stage, run_ptr, runs)) return st;
-        dfree(P.run_ptr);
-        dfree(P.runs);
-        if (int st = upload(&P.run_ptr, run_ptr)) return st;
-        if (int st = upload(&P.runs, runs)) return st;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
