@@ -16,8 +16,9 @@ workload's 200 steps.  Three forms are timed on the same setup:
     is smaller than U^k's) -- the reported value;
   * mixed: the same with x0 = U^k;
   * fp64 plain: fp64 local inverses in standard PCG, x0 = U^k.
-Each preconditioner's split of its local-inverse rows over the CTAs is autotuned at setup
-(asm_autotune: six rounds of 60 timed iterations), which is not part of the timed steps.
+Each preconditioner's split of its work over the CTAs is autotuned at setup
+(asm_autotune, six rounds: 26 solves of 60 timed iterations each), which is not part of
+the timed steps.
 The working set (fp32 store 112 MB + K_h 22.5 MB + vectors) exceeds the 126 MB
 L2, so no L2 flush is inserted between steps.
 

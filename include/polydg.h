@@ -183,7 +183,8 @@ int asm_get_info(const asm_ctx *pc, asm_info *out);
  * moves `rounds` times each -- re-cut the rows of the local inverses with every CTA's
  * tile costs rescaled by its measured / modelled P-phase share, and re-split the elements
  * so that the CTAs' measured CM-phase cycles even out -- keeping a move only if the timed
- * iterations got faster.  *gain (may be NULL) = time before / time after.  Later solves
+ * iterations got faster (always 2 + 4 rounds timed solves).  *gain (may be NULL) =
+ * time before / time after.  Later solves
  * change only by rounding (the per-CTA partial sums are grouped differently).
  * Synchronises the device.  Errors: EINVAL, ENOMEM, ECUDA. */
 int asm_autotune(asm_ctx *pc, int rounds, int iterations, double *gain);
