@@ -559,7 +559,7 @@ def profile_traffic(iterations_per_launch):
 def kernel_sha():
     import hashlib
     h = hashlib.sha256()
-    for name in ("kernels_pcg.cu", "kernels.h", "device.cuh"):
+    for name in ("kernels_pcg.cu", "kernels.h", "device.cuh", "pcg_device.cuh"):
         with open(os.path.join(ROOT, "paper_2512_19536_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

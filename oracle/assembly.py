@@ -56,8 +56,19 @@ class Discretisation:
 
 
 def element_rule(mesh, k, p):
-    """Element quadrature: polygon fan with n = p + 1 points per direction."""
+    """Element quadrature: polygon fan (2D) or polyhedron cone (3D) with n = p + 1."""
+    if mesh.dim == 3:
+        return quadrature.polyhedron_rule(mesh.vertices, mesh.facets(k), p + 1)
     return quadrature.polygon_rule(cell_polygon(mesh, k), p + 1)
+
+
+def face_rule(mesh, faces, f, p):
+    """Interior face quadrature: Gauss-Legendre on the edge (2D) or the collapsed
+    triangle rule (3D), n = p + 1."""
+    if mesh.dim == 3:
+        V = mesh.vertices
+        return quadrature.triangle_rule_3d(V[faces.va[f]], V[faces.vb[f]], V[faces.vc[f]], p + 1)
+    return quadrature.segment_rule(mesh.vertices[faces.va[f]], mesh.vertices[faces.vb[f]], p + 1)
 
 
 def penalty(eta0, p, sigma, diameter, faces):
@@ -71,7 +82,7 @@ def penalty(eta0, p, sigma, diameter, faces):
 
 def assemble(mesh, p, sigma, eta0, chi_cm, dt) -> Discretisation:
     nc = mesh.n_cells
-    n_p = len(basis.modes(p))
+    n_p = len(basis.modes(p, mesh.dim))
     geom = geometry(mesh)
     faces = interior_faces(mesh)
     eta = penalty(eta0, p, sigma, geom.diameter, faces)
@@ -82,7 +93,7 @@ def assemble(mesh, p, sigma, eta0, chi_cm, dt) -> Discretisation:
         x, w = element_rule(mesh, k, p)
         V, G = basis.eval_basis(p, geom.bbox[k], x)
         M_blocks[k] = V.T @ (w[:, None] * V)
-        SG = G @ sigma[k]                               # [nq, n_p, 2] = Sigma grad phi
+        SG = G @ sigma[k]                               # [nq, n_p, dim] = Sigma grad phi
         A_diag[k] = np.einsum("q,qid,qjd->ij", w, G, SG)
 
     A_off = np.zeros((len(faces.plus), n_p, n_p))
@@ -90,8 +101,7 @@ def assemble(mesh, p, sigma, eta0, chi_cm, dt) -> Discretisation:
     for f in range(len(faces.plus)):
         kp, km = faces.plus[f], faces.minus[f]
         n = faces.normal[f]
-        x, w = quadrature.segment_rule(mesh.vertices[faces.va[f]],
-                                       mesh.vertices[faces.vb[f]], p + 1)
+        x, w = face_rule(mesh, faces, f, p)
         Vs, Fs = [], []
         for k in (kp, km):
             V, G = basis.eval_basis(p, geom.bbox[k], x)
@@ -144,7 +154,7 @@ def _assemble_sparse(diag, off, faces, n_p):
 
 
 def load_vector(disc: Discretisation, g):
-    """b_i = int_Omega g phi_i for a vectorised function g(x [nq, 2]) -> [nq]."""
+    """b_i = int_Omega g phi_i for a vectorised function g(x [nq, dim]) -> [nq]."""
     out = np.zeros((disc.mesh.n_cells, disc.n_p))
     for k in range(disc.mesh.n_cells):
         x, w = element_rule(disc.mesh, k, disc.p)

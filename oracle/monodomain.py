@@ -32,7 +32,7 @@ from .pcg import pcg
 @dataclass
 class Nodes:
     cell: np.ndarray      # [nn] element of each node
-    x: np.ndarray         # [nn, 2]
+    x: np.ndarray         # [nn, dim]
     w: np.ndarray         # [nn]
     phi: np.ndarray       # [nn, n_p] basis values of the node's element
 
@@ -62,7 +62,7 @@ def project_nodal(nodes: Nodes, g, n_cells, n_p):
 def stimulus_load(disc, stim):
     """Spatial profile int A exp(-|x-x0|^2/(2w^2)) phi_i (time switch applied by the caller)."""
     A, w = stim["amplitude"], stim["width"]
-    x0 = np.array([stim["x0"], stim["y0"]])
+    x0 = np.array([stim["x0"], stim["y0"]] + ([stim["z0"]] if disc.mesh.dim == 3 else []))
     return load_vector(disc, lambda x: A * np.exp(-((x - x0) ** 2).sum(1) / (2.0 * w * w)))
 
 

@@ -1,4 +1,5 @@
-"""Quadrature rules on segments, triangles and convex polygons (FP64).
+"""Quadrature rules on segments, triangles, convex polygons, tetrahedra and
+star-shaped polyhedra (FP64).
 
 The paper does not fix a quadrature (Sec. 3 only says the forms are integrated
 on polytopal elements).  The rules here: Gauss-Legendre on segments; on a
@@ -8,9 +9,17 @@ with Jacobian 2|T| s; on a convex polygon the fan of triangles
 polynomials of total degree 2n-2 exactly; n = p + 1 makes the mass, stiffness
 and coarse-transfer integrands exact.
 
-Pins (tests/test_oracle_quadrature.py): exact monomial integrals over
-polygons via the divergence theorem, and Gauss-Legendre nodes against the
-closed forms for n = 1..3.
+In 3D a tetrahedron ABCD takes x(s,t,u) = A + s(B-A) + s t(C-B) + s t u(D-C)
+with Jacobian 6|T| s^2 t; a monomial of degree d becomes a polynomial of degree
+d+2 in s, d+1 in t and d in u, so n+1 Gauss points in s and n in t and u
+integrate total degree 2n-2 exactly (n = p + 1: degree 2p).  A polyhedron given
+by outward triangle facets is the cone of tetrahedra (apex, a, b, c) from the
+average of its vertices (the jittered hexahedra are star-shaped about it); a
+triangle facet in space takes the 2D collapsed rule with Jacobian |(B-A) x (C-A)| s.
+
+Pins (tests/test_oracle_quadrature.py, tests/test_oracle_3d.py): exact monomial
+integrals over polygons and polyhedra via the divergence theorem, and
+Gauss-Legendre nodes against the closed forms for n = 1..3.
 """
 import numpy as np
 
@@ -50,6 +59,47 @@ def polygon_rule(P, n: int):
     pts, wts = [], []
     for k in range(1, len(P) - 1):
         x, w = triangle_rule(P[0], P[k], P[k + 1], n)
+        pts.append(x)
+        wts.append(w)
+    return np.concatenate(pts), np.concatenate(wts)
+
+
+def triangle_rule_3d(A, B, C, n: int):
+    """Collapsed rule with n x n points on a triangle ABC in space."""
+    s, ws = gauss_legendre_01(n)
+    A, B, C = (np.asarray(v, float) for v in (A, B, C))
+    twice_area = np.linalg.norm(np.cross(B - A, C - A))
+    pts, wts = [], []
+    for i in range(n):
+        for j in range(n):
+            pts.append(A + s[i] * (B - A) + s[i] * s[j] * (C - B))
+            wts.append(ws[i] * ws[j] * s[i] * twice_area)
+    return np.asarray(pts), np.asarray(wts)
+
+
+def tet_rule(A, B, C, D, n: int):
+    """Collapsed rule on tetrahedron ABCD: n+1 points in s, n in t and u."""
+    s, ws = gauss_legendre_01(n + 1)
+    t, wt = gauss_legendre_01(n)
+    A, B, C, D = (np.asarray(v, float) for v in (A, B, C, D))
+    six_vol = abs(np.linalg.det(np.stack([B - A, C - A, D - A])))
+    pts, wts = [], []
+    for i in range(n + 1):
+        for j in range(n):
+            for k in range(n):
+                pts.append(A + s[i] * (B - A) + s[i] * t[j] * (C - B)
+                           + s[i] * t[j] * t[k] * (D - C))
+                wts.append(ws[i] * wt[j] * wt[k] * s[i] ** 2 * t[j] * six_vol)
+    return np.asarray(pts), np.asarray(wts)
+
+
+def polyhedron_rule(vertices, facets, n: int):
+    """Cone rule on a polyhedron with outward triangle facets [m, 3] (vertex ids)."""
+    V = np.asarray(vertices, float)
+    apex = V[np.unique(facets)].mean(axis=0)
+    pts, wts = [], []
+    for a, b, c in facets:
+        x, w = tet_rule(apex, V[a], V[b], V[c], n)
         pts.append(x)
         wts.append(w)
     return np.concatenate(pts), np.concatenate(wts)

@@ -52,13 +52,14 @@ class Schwarz:
 
 def agglomerate_bbox(mesh, cells):
     V = mesh.vertices[np.concatenate([mesh.cell(k) for k in cells])]
-    return (V[:, 0].min(), V[:, 0].max(), V[:, 1].min(), V[:, 1].max())
+    lo, hi = V.min(0), V.max(0)
+    return tuple(v for d in range(mesh.dim) for v in (lo[d], hi[d]))
 
 
 def coarse_prolongation(disc, coarse, q):
     """Matrix of R_0^T: block (K, J(K)) = T_K = M_K^{-1} int_K phi_K psi_J^T."""
     mesh, p, n_p = disc.mesh, disc.p, disc.n_p
-    n_q = len(basis.modes(q))
+    n_q = len(basis.modes(q, mesh.dim))
     n_agg = int(coarse.max()) + 1
     boxes = [agglomerate_bbox(mesh, np.flatnonzero(coarse == J)) for J in range(n_agg)]
     rows, cols, vals = [], [], []

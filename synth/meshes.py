@@ -236,3 +236,87 @@ def fibre_conductivity(mesh: Mesh, sigma_l: float, sigma_t: float, seed: int,
     l = np.stack([np.cos(theta), np.sin(theta)], 1)
     S = sigma_t * np.eye(2)[None] + (sigma_l - sigma_t) * l[:, :, None] * l[:, None, :]
     return S
+
+
+# ------------------------------------------------------------------ 3D meshes
+@dataclass
+class PolyMesh3D:
+    """Polyhedral mesh: each cell is a closed surface of triangle facets.
+
+    Facets are given per cell in CSR form (``cell_face_ptr`` int64 [nc+1] over
+    ``face_vtx`` int32 [n_facets, 3]); every facet is oriented so that
+    (b - a) x (c - a) points out of its cell.  Two cells share an interior face
+    exactly when a facet's three vertex ids appear in both, in opposite
+    orientation.
+    """
+    vertices: np.ndarray      # [nv, 3] float64
+    cell_face_ptr: np.ndarray  # [nc+1] int64
+    face_vtx: np.ndarray      # [n_facets, 3] int32
+    dim: int = 3
+
+    @property
+    def n_cells(self) -> int:
+        return len(self.cell_face_ptr) - 1
+
+    def facets(self, k: int) -> np.ndarray:
+        return self.face_vtx[self.cell_face_ptr[k]:self.cell_face_ptr[k + 1]]
+
+    def cell(self, k: int) -> np.ndarray:
+        """The cell's vertex ids, ascending."""
+        return np.unique(self.facets(k))
+
+
+# outward-oriented corner loops of the six faces of the unit hex, corners (di, dj, dk)
+_HEX_FACES = (
+    ((0, 0, 0), (0, 0, 1), (0, 1, 1), (0, 1, 0)),   # x = 0
+    ((1, 0, 0), (1, 1, 0), (1, 1, 1), (1, 0, 1)),   # x = 1
+    ((0, 0, 0), (1, 0, 0), (1, 0, 1), (0, 0, 1)),   # y = 0
+    ((0, 1, 0), (0, 1, 1), (1, 1, 1), (1, 1, 0)),   # y = 1
+    ((0, 0, 0), (0, 1, 0), (1, 1, 0), (1, 0, 0)),   # z = 0
+    ((0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)),   # z = 1
+)
+
+
+def jittered_hex_cube(n: int, seed: int, jitter: float = 0.1) -> PolyMesh3D:
+    """n^3 hexahedra on [0,1]^3 with seeded vertex jitter, as 12-facet polyhedra.
+
+    Vertex (i, j, k) -> id (k (n+1) + j)(n+1) + i, moved by U[-jitter h, jitter h]
+    (h = 1/n) along every axis in which it is not on the cube's boundary
+    (boundary vertices move only tangentially; corners stay).  Each quadrilateral
+    face is split into two triangles along the diagonal through its smallest
+    vertex id, so both cells sharing a face split it the same way.  Cell (i, j, k)
+    -> id (k n + j) n + i.
+    """
+    m = n + 1
+    idx = np.arange(m)
+    K, J, I = np.meshgrid(idx, idx, idx, indexing="ij")
+    grid = np.stack([I.ravel(), J.ravel(), K.ravel()], 1)          # [nv, 3] ids along x, y, z
+    h = 1.0 / n
+    d = _rng(seed).uniform(-1.0, 1.0, grid.shape) * (jitter * h)
+    d[(grid == 0) | (grid == n)] = 0.0
+    verts = grid * h + d
+
+    def vid(i, j, k):
+        return (k * m + j) * m + i
+
+    tris = []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                for quad in _HEX_FACES:
+                    q = [vid(i + a, j + b, k + c) for a, b, c in quad]
+                    s = int(np.argmin(q))
+                    q = q[s:] + q[:s]
+                    tris.append((q[0], q[1], q[2]))
+                    tris.append((q[0], q[2], q[3]))
+    face_vtx = np.asarray(tris, dtype=np.int32)
+    cell_face_ptr = np.arange(0, 12 * n ** 3 + 1, 12, dtype=np.int64)
+    return PolyMesh3D(verts, cell_face_ptr, face_vtx)
+
+
+def block_partition_3d(n: int, b: int) -> np.ndarray:
+    """Partition of the n^3 hex mesh into (n/b)^3 blocks of b^3 cells."""
+    m = n // b
+    c = np.arange(n)
+    K, J, I = np.meshgrid(c, c, c, indexing="ij")
+    return (((K // b) * m + J // b) * m + I // b).ravel().astype(np.int32)

@@ -11,7 +11,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from .meshes import (Mesh, cartesian_square, voronoi_square, block_partition,
-                     kmeans_partition, fibre_conductivity, isotropic_conductivity)
+                     kmeans_partition, fibre_conductivity, isotropic_conductivity,
+                     jittered_hex_cube, block_partition_3d)
 
 
 @dataclass
@@ -20,7 +21,7 @@ class Workload:
     mesh: Mesh
     p: int                     # fine polynomial degree
     q: int                     # coarse polynomial degree
-    sigma: np.ndarray          # [nc, 2, 2] per-cell conductivity
+    sigma: np.ndarray          # [nc, dim, dim] per-cell conductivity
     subdomain: np.ndarray      # [nc] int32 subdomain id per cell
     coarse: np.ndarray         # [nc] int32 coarse agglomerate id per cell
     eta0: float = 10.0
@@ -38,11 +39,15 @@ def random_rhs(n: int, seed: int) -> np.ndarray:
 
 
 def stimulus_params(seed: int, amplitude: float = 250.0, width: float = 0.05,
-                    duration: float = 1.0) -> dict:
-    """Gaussian external current I = A exp(-|x-x0|^2 / (2 w^2)) while t < duration."""
-    x0 = 0.25 + 0.5 * np.random.Generator(np.random.PCG64(seed)).random(2)
-    return {"x0": float(x0[0]), "y0": float(x0[1]), "amplitude": amplitude,
-            "width": width, "duration": duration}
+                    duration: float = 1.0, dim: int = 2) -> dict:
+    """Gaussian external current I = A exp(-|x-x0|^2 / (2 w^2)) while t < duration,
+    centred at a seeded point of [0.25, 0.75]^dim."""
+    x0 = 0.25 + 0.5 * np.random.Generator(np.random.PCG64(seed)).random(dim)
+    out = {"x0": float(x0[0]), "y0": float(x0[1]), "amplitude": amplitude,
+           "width": width, "duration": duration}
+    if dim == 3:
+        out["z0"] = float(x0[2])
+    return out
 
 
 def square16_p2() -> Workload:
@@ -99,9 +104,24 @@ def voronoi_batch(n_meshes: int = 8, sims_per_mesh: int = 4, seed: int = 4,
     return out
 
 
+def hex_cube_p2(n: int = 48, block: int = 4, seed: int = 3, n_steps: int = 50,
+                p: int = 2) -> Workload:
+    """n^3 jittered hexahedra on [0,1]^3 (10 % jitter, 12-facet polyhedra), P2
+    (10 DOF per cell), isotropic sigma = 1, subdomains = coarse cells = blocks of
+    block^3 cells, coarse P1, dt = 0.05 ms, n_steps coupled steps."""
+    mesh = jittered_hex_cube(n, seed)
+    part = block_partition_3d(n, block)
+    return Workload(f"hex{n}_p{p}", mesh, p=p, q=1,
+                    sigma=isotropic_conductivity(mesh.n_cells, 1.0, dim=3),
+                    subdomain=part, coarse=part.copy(), eta0=10.0, dt=0.05,
+                    rtol=1e-8, n_steps=n_steps, stimulus=stimulus_params(seed, dim=3))
+
+
 def make_workload(name: str, **kw) -> Workload:
     if name == "square16_p2":
         return square16_p2()
     if name.startswith("voronoi"):
         return voronoi4096_p3(**kw)
+    if name.startswith("hex"):
+        return hex_cube_p2(**kw)
     raise KeyError(name)
