@@ -6,7 +6,8 @@
  *
  *   polydg_setup     Sec. 3 (Eq. eta, Eq. coer): SIP-DG assembly of M_h, A_h and
  *                    K_h = chi_m C_m M_h + dt/2 A_h on a polygonal mesh, plus the
- *                    subdomain partition T_S of Sec. 4.
+ *                    subdomain partition T_S of Sec. 4 (polydg_setup3d: the same on
+ *                    a polyhedral mesh).
  *   asm_setup        Sec. 4: local matrices K_i = R_i K_h R_i^T, the coarse space
  *                    V_0 = P^q on the agglomerates of T_H with R_0^T the L2
  *                    projection, K_0 = R_0 K_h R_0^T, and their factorisations.
@@ -28,7 +29,10 @@
  *   - Basis (the paper fixes none): on cell c with axis-aligned bounding box
  *     [x0,x1]x[y0,y1], phi_(a,b) = L_a(xi) L_b(eta), a + b <= p, L_n the Legendre
  *     polynomials, xi = (2x-x0-x1)/(x1-x0), eta likewise; ordered by total
- *     degree, then by increasing b.  n_p = (p+1)(p+2)/2.
+ *     degree, then by increasing b.  n_p = (p+1)(p+2)/2.  In 3D (box
+ *     [x0,x1]x[y0,y1]x[z0,z1]) phi_(a,b,c) = L_a(xi) L_b(eta) L_c(zeta),
+ *     a + b + c <= p, ordered by total degree, then by increasing c, then by
+ *     increasing b; n_p = (p+1)(p+2)(p+3)/6.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *     Work is enqueued on it; calls that return statistics synchronise it.
  *   - Every function returns POLYDG_OK (0) or a negative status; the text of
@@ -82,6 +86,27 @@ typedef struct {
     const double  *sigma;      /* [n_cells * 4] host                         */
 } polydg_mesh;
 
+/* A 3D polyhedral mesh (Sec. 3: T_h, disjoint polyhedra).  Each cell is a
+ * closed surface of triangle facets, listed in CSR form: cell c owns facets
+ * cell_face_ptr[c] .. cell_face_ptr[c+1]-1, facet f being the vertex ids
+ * face_vtx[3f], face_vtx[3f+1], face_vtx[3f+2], ordered so that
+ * (b - a) x (c - a) points out of the cell.  Every cell must be star-shaped
+ * about the average of its vertices (its element quadrature is the cone of
+ * tetrahedra from that point over its facets).  Two cells share an interior
+ * face exactly when a facet's three vertex ids appear in both, in opposite
+ * orientation; facets of one cell only are boundary faces (homogeneous
+ * Neumann).  A planar quadrilateral face is two facets; both neighbours must
+ * split it along the same diagonal.  sigma holds Sigma_K of each cell,
+ * row-major 3x3, symmetric positive definite. */
+typedef struct {
+    int64_t        n_vertices;
+    const double  *vertices;      /* [n_vertices * 3] host, (x, y, z)           */
+    int64_t        n_cells;
+    const int64_t *cell_face_ptr; /* [n_cells + 1] host, cell_face_ptr[0] = 0   */
+    const int32_t *face_vtx;      /* [cell_face_ptr[n_cells] * 3] host          */
+    const double  *sigma;         /* [n_cells * 9] host                         */
+} polydg_mesh3d;
+
 typedef struct {
     int64_t n_cells;
     int64_t n_dofs;            /* n_cells * n_p                              */
@@ -113,6 +138,7 @@ typedef struct {
     double  rtol;
     int32_t maxit;
     int32_t flexible;          /* 1: flexible PCG (required with FP32/BF16 local inverses) */
+    double  stim_z0;           /* stimulus centre's z (3D meshes; ignored in 2D) */
 } sim_params;
 
 typedef struct {
@@ -153,6 +179,18 @@ const char *polydg_last_error(void);
  * ENOMEM, ECUDA. */
 int polydg_setup(const polydg_mesh *mesh, int p, const int32_t *subdomain_of_cell,
                  double chi_cm, double dt, double eta0, polydg_ctx **out);
+
+/* polydg_setup on a polyhedral mesh (degree p = 2, n_p = 10: the device kernels are
+ * instantiated for n_p in {3, 6, 10, 15}, and only P2 maps to one of them in 3D).  Element integrals use
+ * the cone of tetrahedra from each cell's vertex average, each with a collapsed
+ * Gauss rule of p + 2 points along the collapsed direction and p + 1 along the
+ * others (exact for polynomials of degree 2p); face integrals use the collapsed
+ * rule with (p + 1)^2 points per facet.  The quadrature-node tables (ionic state)
+ * follow the same element rule.  Errors as polydg_setup, plus EINVAL for a facet
+ * shared by more than two cells or without opposite orientation, and for a cell
+ * that is not star-shaped about its vertex average. */
+int polydg_setup3d(const polydg_mesh3d *mesh, int p, const int32_t *subdomain_of_cell,
+                   double chi_cm, double dt, double eta0, polydg_ctx **out);
 
 int polydg_get_info(const polydg_ctx *ctx, polydg_info *out);
 

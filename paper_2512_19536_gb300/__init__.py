@@ -5,7 +5,8 @@ ABI of ``include/polydg.h``); this package is its ctypes binding.  Importing
 the package does not load the library; the first call does, and fails loudly
 if it has not been built.
 """
-from ._native import (PolyDG, ASM, Simulation, PolyDGError, load, polydg_setup, asm_setup,
+from ._native import (PolyDG, ASM, Simulation, PolyDGError, load, polydg_setup, polydg_setup3d,
+                      setup_mesh, asm_setup,
                       asm_apply, asm_autotune, pcg_solve_trace, lanczos_extremes, pcg_solve, sim_create, monodomain_step, sim_get_state,
                       sim_set_potential, spd_inverse_static, Batch, batch_create, batch_step,
                       GuessModel, guess_n_params, guess_create, guess_propose, guess_train_step,
@@ -14,7 +15,8 @@ from ._native import (PolyDG, ASM, Simulation, PolyDGError, load, polydg_setup, 
                       EXPORTS, LIB_PATH, POLYDG_OK, POLYDG_EINVAL, POLYDG_ENOMEM, POLYDG_ECUDA, POLYDG_ENOTSPD, POLYDG_ENOTCONV,
                       POLYDG_EBREAKDOWN, POLYDG_ENONFINITE)
 
-__all__ = ["PolyDG", "ASM", "Simulation", "PolyDGError", "load", "polydg_setup", "asm_setup",
+__all__ = ["PolyDG", "ASM", "Simulation", "PolyDGError", "load", "polydg_setup", "polydg_setup3d",
+           "setup_mesh", "asm_setup",
            "asm_apply", "asm_autotune", "pcg_solve_trace", "lanczos_extremes", "pcg_solve", "sim_create", "monodomain_step", "sim_get_state",
            "sim_set_potential", "spd_inverse_static", "Batch", "batch_create", "batch_step",
            "GuessModel", "guess_n_params", "guess_create", "guess_propose", "guess_train_step",

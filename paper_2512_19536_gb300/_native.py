@@ -20,7 +20,7 @@ POLYDG_ENOTSPD, POLYDG_ENOTCONV, POLYDG_EBREAKDOWN, POLYDG_ENONFINITE = -4, -5, 
 POLYDG_FP64, POLYDG_FP32, POLYDG_BF16 = 0, 1, 2
 PRECISION = {"fp64": POLYDG_FP64, "fp32": POLYDG_FP32, "bf16": POLYDG_BF16}
 
-EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_get_info", "polydg_get_faces",
+EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_setup3d", "polydg_get_info", "polydg_get_faces",
            "polydg_matvec", "asm_setup", "asm_get_info", "asm_apply", "pcg_solve", "sim_create",
            "monodomain_step", "sim_get_state", "sim_set_potential", "sim_step_index",
            "sim_destroy", "asm_destroy", "polydg_destroy", "polydg_spd_inverse_static",
@@ -35,6 +35,12 @@ class polydg_mesh(C.Structure):
     _fields_ = [("n_vertices", C.c_int64), ("vertices", C.POINTER(C.c_double)),
                 ("n_cells", C.c_int64), ("cell_ptr", C.POINTER(C.c_int64)),
                 ("cell_vtx", C.POINTER(C.c_int32)), ("sigma", C.POINTER(C.c_double))]
+
+
+class polydg_mesh3d(C.Structure):
+    _fields_ = [("n_vertices", C.c_int64), ("vertices", C.POINTER(C.c_double)),
+                ("n_cells", C.c_int64), ("cell_face_ptr", C.POINTER(C.c_int64)),
+                ("face_vtx", C.POINTER(C.c_int32)), ("sigma", C.POINTER(C.c_double))]
 
 
 class polydg_info(C.Structure):
@@ -53,7 +59,7 @@ class sim_params(C.Structure):
     _fields_ = [("u0", C.c_double), ("stim_x0", C.c_double), ("stim_y0", C.c_double),
                 ("stim_amplitude", C.c_double), ("stim_width", C.c_double),
                 ("stim_duration", C.c_double), ("rtol", C.c_double), ("maxit", C.c_int32),
-                ("flexible", C.c_int32)]
+                ("flexible", C.c_int32), ("stim_z0", C.c_double)]
 
 
 class step_stats(C.Structure):
@@ -86,6 +92,8 @@ def load() -> C.CDLL:
     L.polydg_last_error.restype = C.c_char_p
     L.polydg_setup.argtypes = [C.POINTER(polydg_mesh), i32, C.POINTER(C.c_int32), dbl, dbl, dbl,
                                C.POINTER(vp)]
+    L.polydg_setup3d.argtypes = [C.POINTER(polydg_mesh3d), i32, C.POINTER(C.c_int32), dbl, dbl,
+                                 dbl, C.POINTER(vp)]
     L.polydg_get_info.argtypes = [vp, C.POINTER(polydg_info)]
     L.polydg_get_faces.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.polydg_matvec.argtypes = [vp, vp, vp, vp]
@@ -225,6 +233,31 @@ def polydg_setup(vertices, cell_ptr, cell_vtx, sigma, p, subdomain_of_cell, chi_
     return PolyDG(h)
 
 
+def polydg_setup3d(vertices, cell_face_ptr, face_vtx, sigma, p, subdomain_of_cell, chi_cm=1.0,
+                   dt=0.1, eta0=10.0) -> PolyDG:
+    """polydg_setup3d on a polyhedral mesh given by outward triangle facets per cell."""
+    v = np.ascontiguousarray(vertices, np.float64)
+    fp = np.ascontiguousarray(cell_face_ptr, np.int64)
+    fv = np.ascontiguousarray(face_vtx, np.int32).reshape(-1)
+    sg = np.ascontiguousarray(sigma, np.float64).reshape(-1)
+    sub = np.ascontiguousarray(subdomain_of_cell, np.int32)
+    m = polydg_mesh3d(len(v), _ptr(v, C.c_double), len(fp) - 1, _ptr(fp, C.c_int64),
+                      _ptr(fv, C.c_int32), _ptr(sg, C.c_double))
+    h = C.c_void_p()
+    _check(load().polydg_setup3d(C.byref(m), int(p), _ptr(sub, C.c_int32), float(chi_cm),
+                                 float(dt), float(eta0), C.byref(h)))
+    return PolyDG(h)
+
+
+def setup_mesh(mesh, sigma, p, subdomain_of_cell, chi_cm=1.0, dt=0.1, eta0=10.0) -> PolyDG:
+    """polydg_setup or polydg_setup3d, by the mesh's dimension."""
+    if getattr(mesh, "dim", 2) == 3:
+        return polydg_setup3d(mesh.vertices, mesh.cell_face_ptr, mesh.face_vtx, sigma, p,
+                              subdomain_of_cell, chi_cm, dt, eta0)
+    return polydg_setup(mesh.vertices, mesh.cell_ptr, mesh.cell_vtx, sigma, p, subdomain_of_cell,
+                        chi_cm, dt, eta0)
+
+
 class ASM:
     """Handle of an asm_ctx (two-level additive Schwarz preconditioner)."""
 
@@ -334,7 +367,7 @@ def sim_create(ctx: PolyDG, pc, u0=-67.0, stimulus=None, rtol=1e-8, maxit=10000,
                flexible=False) -> Simulation:
     s = stimulus or {"x0": 0.5, "y0": 0.5, "amplitude": 0.0, "width": 1.0, "duration": 0.0}
     prm = sim_params(float(u0), s["x0"], s["y0"], s["amplitude"], s["width"], s["duration"],
-                     float(rtol), int(maxit), int(bool(flexible)))
+                     float(rtol), int(maxit), int(bool(flexible)), float(s.get("z0", 0.0)))
     h = C.c_void_p()
     _check(load().sim_create(ctx.h, pc.h if pc is not None else None, C.byref(prm), C.byref(h)))
     return Simulation(ctx, pc, h)

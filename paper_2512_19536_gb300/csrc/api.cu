@@ -350,6 +350,8 @@ static int check_ctx(const polydg_ctx* c, const char* fn) {
 }
 
 static inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+// coarse spaces larger than this are factorised and inverted on the host threads
+constexpr int64_t kHostCoarseDofs = 2048;
 
 }  // namespace polydg
 
@@ -358,13 +360,9 @@ extern "C" {
 
 const char* polydg_last_error(void) { return g_error.c_str(); }
 
-int polydg_setup(const polydg_mesh* mesh, int p, const int32_t* subdomain_of_cell,
-                 double chi_cm, double dt, double eta0, polydg_ctx** out) {
-    if (!out) { set_error("polydg_setup: null output"); return POLYDG_EINVAL; }
-    *out = nullptr;
-    polydg_ctx* c = new polydg_ctx();
-    int st = host_setup(mesh, p, subdomain_of_cell, chi_cm, dt, eta0, c->H);
-    if (st) { delete c; return st; }
+// Device side of polydg_setup / polydg_setup3d once c->H holds the host assembly.
+static int setup_device(polydg_ctx* c, polydg_ctx** out) {
+    int st;
     auto fail = [&](int code) { polydg_destroy(c); return code; };
     if (cudaGetDevice(&c->device) != cudaSuccess) { set_error("polydg_setup: no CUDA device"); return fail(POLYDG_ECUDA); }
     const HostSetup& H = c->H;
@@ -421,6 +419,26 @@ int polydg_setup(const polydg_mesh* mesh, int p, const int32_t* subdomain_of_cel
     return POLYDG_OK;
 }
 
+
+int polydg_setup(const polydg_mesh* mesh, int p, const int32_t* subdomain_of_cell,
+                 double chi_cm, double dt, double eta0, polydg_ctx** out) {
+    if (!out) { set_error("polydg_setup: null output"); return POLYDG_EINVAL; }
+    *out = nullptr;
+    polydg_ctx* c = new polydg_ctx();
+    int st = host_setup(mesh, p, subdomain_of_cell, chi_cm, dt, eta0, c->H);
+    if (st) { delete c; return st; }
+    return setup_device(c, out);
+}
+
+int polydg_setup3d(const polydg_mesh3d* mesh, int p, const int32_t* subdomain_of_cell,
+                   double chi_cm, double dt, double eta0, polydg_ctx** out) {
+    if (!out) { set_error("polydg_setup3d: null output"); return POLYDG_EINVAL; }
+    *out = nullptr;
+    polydg_ctx* c = new polydg_ctx();
+    int st = host_setup3d(mesh, p, subdomain_of_cell, chi_cm, dt, eta0, c->H);
+    if (st) { delete c; return st; }
+    return setup_device(c, out);
+}
 int polydg_get_info(const polydg_ctx* c, polydg_info* out) {
     if (int st = check_ctx(c, "polydg_get_info")) return st;
     if (!out) { set_error("polydg_get_info: null output"); return POLYDG_EINVAL; }
@@ -469,7 +487,10 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
     CoarseSetup C;
     if (coarse_of_cell) {
         if (int st = coarse_setup(H, coarse_of_cell, q, C)) return st;
-        if (C.n_q != 3 && C.n_q != 6 && C.n_q != 10) { set_error("asm_setup: coarse degree q must be 1..3"); return POLYDG_EINVAL; }
+        if (C.n_q != 3 && C.n_q != 4 && C.n_q != 6 && C.n_q != 10) {
+            set_error("asm_setup: coarse degree q must be 1..3 (2D) or 1..2 (3D)");
+            return POLYDG_EINVAL;
+        }
     }
     asm_ctx* pc = new asm_ctx();
     pc->ctx = c;
@@ -493,7 +514,7 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
         const int64_t ld = round_up(n0, 8), wld = round_up(n0, 32);
         mats.push_back({n0, ld, off, wld, woff});
         off += n0 * ld;
-        woff += wld * wld;
+        if (n0 <= kHostCoarseDofs) woff += wld * wld;
         max_n = std::max(max_n, n0);
     }
     const int nmat = (int)mats.size();
@@ -525,22 +546,38 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
         set_error(std::string("asm_setup: ") + what + ": " + cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? POLYDG_ENOMEM : POLYDG_ECUDA;
     };
+    // A large coarse matrix (3D: thousands of coarse DOFs) is inverted on the host
+    // threads: the batched kernel gives each matrix one CTA.
+    const bool coarse_on_host = pc->has_coarse && n0 > kHostCoarseDofs;
+    const int nmat_dev = coarse_on_host ? nmat - 1 : nmat;
+    int64_t max_n_dev = 0;
+    for (int m = 0; m < nmat_dev; ++m) max_n_dev = std::max(max_n_dev, mats[m].n);
+    std::vector<double> K0inv;
+    if (coarse_on_host) {
+        K0inv.resize((size_t)n0 * n0);
+        if (!spd_inverse(n0, C.K0.data(), K0inv.data())) {
+            cleanup();
+            set_error("asm_setup: the coarse matrix K_0 is not positive definite");
+            return fail(POLYDG_ENOTSPD);
+        }
+    }
+    const double* coarse_src = coarse_on_host ? K0inv.data() : C.K0.data();
     if ((st = cu(cudaMemset(pc->st64, 0, off * sizeof(double)), "memset")) ||
         (st = cu(cudaMemset(work, 0, woff * sizeof(double)), "memset")) ||
         (st = cu(launch_extract_local(c->K, d_subptr, H.n_sub, d_off, d_ld, pc->st64, np, 0), "extract")) ||
         (pc->has_coarse &&
-         (st = cu(cudaMemcpy2D(pc->st64 + mats.back().off, mats.back().ld * sizeof(double), C.K0.data(),
+         (st = cu(cudaMemcpy2D(pc->st64 + mats.back().off, mats.back().ld * sizeof(double), coarse_src,
                                n0 * sizeof(double), n0 * sizeof(double), n0, cudaMemcpyHostToDevice),
                   "coarse upload"))) ||
-        (st = cu(launch_chol_inverse(pc->st64, d_off, d_n, d_ld, work, d_woff, d_wld, d_status, nmat,
-                                     (int)max_n, 0), "cholesky")) ||
+        (st = cu(launch_chol_inverse(pc->st64, d_off, d_n, d_ld, work, d_woff, d_wld, d_status, nmat_dev,
+                                     (int)max_n_dev, 0), "cholesky")) ||
         (st = cu(cudaDeviceSynchronize(), "cholesky sync"))) {
         cleanup();
         return fail(st);
     }
     {
-        std::vector<int> hs(nmat);
-        cudaMemcpy(hs.data(), d_status, nmat * sizeof(int), cudaMemcpyDeviceToHost);
+        std::vector<int> hs(nmat, 0);
+        cudaMemcpy(hs.data(), d_status, nmat_dev * sizeof(int), cudaMemcpyDeviceToHost);
         for (int m = 0; m < nmat; ++m)
             if (hs[m] != 0) {
                 cleanup();
@@ -991,8 +1028,10 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
     for (int64_t e = 0; e < H.nc; ++e) {
         U0[e * np] = prm->u0;   // constant u0: only the (0,0) mode
         for (int64_t qn = H.node_ptr[e]; qn < H.node_ptr[e + 1]; ++qn) {
-            const double dx = H.node_xy[2 * qn] - prm->stim_x0, dy = H.node_xy[2 * qn + 1] - prm->stim_y0;
-            const double g = H.node_w[qn] * prm->stim_amplitude * std::exp(-(dx * dx + dy * dy) / s2);
+            const double* xq = &H.node_x[(size_t)H.dim * qn];
+            const double dx = xq[0] - prm->stim_x0, dy = xq[1] - prm->stim_y0;
+            const double dz = H.dim == 3 ? xq[2] - prm->stim_z0 : 0.0;
+            const double g = H.node_w[qn] * prm->stim_amplitude * std::exp(-(dx * dx + dy * dy + dz * dz) / s2);
             for (int i = 0; i < np; ++i) F[e * np + i] += g * H.node_phi[qn * np + i];
         }
     }

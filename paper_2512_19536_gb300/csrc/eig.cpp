@@ -4,9 +4,11 @@
 // the orthogonal factor.  The factor is kept transposed (row k = column k of Q), so
 // every update touches contiguous rows.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -125,6 +127,94 @@ bool sym_eig(int n, double* a, double* w, double* qt) {
         std::copy(qt + (size_t)idx[k] * n, qt + (size_t)idx[k] * n + n, tmp.begin() + (size_t)k * n);
     }
     std::copy(tmp.begin(), tmp.end(), qt);
+    return true;
+}
+
+// ------------------------------------------------ dense SPD inverse on the host
+// For coarse matrices too large for one CTA's factorisation: Cholesky A = L L^T by
+// column panels (rows below a panel in parallel) inside the envelope of A (row i of L
+// starts at row i's first nonzero of A: no fill left of it), W = L^{-1} transposed
+// (rows in parallel: row k of W is column k of L^{-1}, zero before k), then
+// A^{-1} = W^T-products: A^{-1}_ij = sum_{m >= max(i,j)} W_im W_jm (rows in parallel).
+// Every dot product runs in a fixed order, so the result does not depend on the
+// thread count.
+static double dot4(const double* a, const double* b, int64_t n) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t k = 0;
+    for (; k + 4 <= n; k += 4) {
+        s0 += a[k] * b[k];
+        s1 += a[k + 1] * b[k + 1];
+        s2 += a[k + 2] * b[k + 2];
+        s3 += a[k + 3] * b[k + 3];
+    }
+    for (; k < n; ++k) s0 += a[k] * b[k];
+    return (s0 + s1) + (s2 + s3);
+}
+
+template <class F>
+static void host_parallel(int64_t n, F body) {
+    const int64_t T = std::max<int64_t>(1, std::min<int64_t>(std::min<unsigned>(std::thread::hardware_concurrency(), 64u), n));
+    if (T <= 1) { for (int64_t i = 0; i < n; ++i) body(i); return; }
+    std::atomic<int64_t> next{0};
+    std::vector<std::thread> th;
+    for (int64_t t = 0; t < T; ++t)
+        th.emplace_back([&] {
+            for (int64_t i; (i = next.fetch_add(1)) < n;) body(i);
+        });
+    for (auto& x : th) x.join();
+}
+
+bool spd_inverse(int64_t n, const double* A, double* Ainv) {
+    // envelope: row i of L is zero left of the first nonzero of row i of A
+    std::vector<int64_t> first(n);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t f = i;
+        for (int64_t j = 0; j < i; ++j)
+            if (A[(size_t)i * n + j] != 0.0) { f = j; break; }
+        first[i] = f;
+    }
+    std::vector<double> L((size_t)n * n, 0.0);
+    auto entry = [&](int64_t i, int64_t j) {        // L[i][j], j < i, j >= first[i]
+        const double* Li = &L[(size_t)i * n];
+        const double* Lj = &L[(size_t)j * n];
+        const int64_t m0 = std::max(first[i], first[j]);
+        return (A[(size_t)i * n + j] - dot4(Li + m0, Lj + m0, j - m0)) / Lj[j];
+    };
+    const int64_t nb = 64;
+    for (int64_t j0 = 0; j0 < n; j0 += nb) {
+        const int64_t j1 = std::min(n, j0 + nb);
+        for (int64_t j = j0; j < j1; ++j) {
+            double* Lj = &L[(size_t)j * n];
+            for (int64_t jj = std::max(j0, first[j]); jj < j; ++jj) Lj[jj] = entry(j, jj);
+            const double d = A[(size_t)j * n + j] - dot4(Lj + first[j], Lj + first[j], j - first[j]);
+            if (!(d > 0)) return false;
+            Lj[j] = std::sqrt(d);
+        }
+        host_parallel(n - j1, [&](int64_t r) {
+            const int64_t i = j1 + r;
+            double* Li = &L[(size_t)i * n];
+            for (int64_t j = std::max(j0, first[i]); j < j1; ++j) Li[j] = entry(i, j);
+        });
+    }
+    std::vector<double> W((size_t)n * n, 0.0);           // W[k][i] = (L^{-1})[i][k]
+    host_parallel(n, [&](int64_t k) {
+        double* Wk = &W[(size_t)k * n];
+        Wk[k] = 1.0 / L[(size_t)k * n + k];
+        for (int64_t i = k + 1; i < n; ++i) {
+            const double* Li = &L[(size_t)i * n];
+            const int64_t m0 = std::max(k, first[i]);
+            Wk[i] = m0 < i ? -dot4(Li + m0, Wk + m0, i - m0) / Li[i] : 0.0;
+        }
+    });
+    host_parallel(n, [&](int64_t i) {
+        const double* Wi = &W[(size_t)i * n];
+        for (int64_t j = i; j < n; ++j) {
+            const double* Wj = &W[(size_t)j * n];
+            Ainv[(size_t)i * n + j] = dot4(Wi + j, Wj + j, n - j);
+        }
+    });
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < i; ++j) Ainv[(size_t)i * n + j] = Ainv[(size_t)j * n + i];
     return true;
 }
 

@@ -1,16 +1,33 @@
 // Host-side setup of libpolydg: connectivity, geometry, quadrature, modal basis
 // and the symmetric interior-penalty assembly of Sec. 3 (Eq. eta, Eq. coer),
-// plus the coarse-space transfer and Galerkin matrix of Sec. 4.  Runs once per
-// mesh; the per-step work runs in the CUDA kernels.
+// plus the coarse-space transfer and Galerkin matrix of Sec. 4, for polygonal (2D)
+// and polyhedral (3D) meshes.  Runs once per mesh; the per-step work runs in the
+// CUDA kernels.  Loops over cells and faces run on all host threads; every cell
+// and face writes only its own outputs, so the result does not depend on the
+// thread count.
 #include <algorithm>
+#include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 #include <tuple>
 
 #include "internal.h"
 
 namespace polydg {
+
+// Runs body(i0, i1) on contiguous chunks of [0, n) on the host's threads.
+template <class F>
+static void parallel_chunks(int64_t n, F body) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t T = std::min<int64_t>(std::min<unsigned>(hw, 64u), std::max<int64_t>(1, n / 64));
+    if (T <= 1) { body(int64_t(0), n); return; }
+    std::vector<std::thread> th;
+    for (int64_t t = 0; t < T; ++t) th.emplace_back([&, t] { body(n * t / T, n * (t + 1) / T); });
+    for (auto& x : th) x.join();
+}
 
 // --------------------------------------------------------------- quadrature
 // Gauss-Legendre: roots of L_n by Newton's method from the Chebyshev-like
@@ -39,7 +56,9 @@ void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
     }
 }
 
-int n_modes(int p) { return (p + 1) * (p + 2) / 2; }
+int n_modes(int p, int dim) {
+    return dim == 3 ? (p + 1) * (p + 2) * (p + 3) / 6 : (p + 1) * (p + 2) / 2;
+}
 
 // Legendre values and derivatives L_0..L_p at t.
 static void legendre(int p, double t, double* L, double* D) {
@@ -52,54 +71,354 @@ static void legendre(int p, double t, double* L, double* D) {
     }
 }
 
-// phi_(a,b)(x,y) = L_a(xi) L_b(eta) on box = {x0, x1, y0, y1}; order: total degree d,
-// then b = 0..d.  grad (optional) receives [n_p][2].
-void eval_basis(int p, const double* box, double x, double y, double* val, double* grad) {
-    double Lx[16], Dx[16], Ly[16], Dy[16];
-    const double sx = 2.0 / (box[1] - box[0]), sy = 2.0 / (box[3] - box[2]);
-    const double xi = sx * x - (box[0] + box[1]) / (box[1] - box[0]);
-    const double eta = sy * y - (box[2] + box[3]) / (box[3] - box[2]);
-    legendre(p, xi, Lx, Dx);
-    legendre(p, eta, Ly, Dy);
+// 2D: phi_(a,b) = L_a(xi) L_b(eta), order: total degree d, then b = 0..d.
+// 3D: phi_(a,b,c) = L_a(xi) L_b(eta) L_c(zeta), order: total degree d, then c = 0..d,
+// then b = 0..d-c.  box = {x0, x1, y0, y1[, z0, z1]}; grad (optional) is [n_p][dim].
+void eval_basis(int dim, int p, const double* box, const double* x, double* val, double* grad) {
+    double L[3][16], D[3][16], s[3];
+    for (int d = 0; d < dim; ++d) {
+        const double lo = box[2 * d], hi = box[2 * d + 1];
+        s[d] = 2.0 / (hi - lo);
+        legendre(p, s[d] * x[d] - (lo + hi) / (hi - lo), L[d], D[d]);
+    }
     int j = 0;
-    for (int d = 0; d <= p; ++d)
-        for (int b = 0; b <= d; ++b, ++j) {
-            const int a = d - b;
-            val[j] = Lx[a] * Ly[b];
-            if (grad) {
-                grad[2 * j] = sx * Dx[a] * Ly[b];
-                grad[2 * j + 1] = sy * Lx[a] * Dy[b];
+    if (dim == 2) {
+        for (int d = 0; d <= p; ++d)
+            for (int b = 0; b <= d; ++b, ++j) {
+                const int a = d - b;
+                val[j] = L[0][a] * L[1][b];
+                if (grad) {
+                    grad[2 * j] = s[0] * D[0][a] * L[1][b];
+                    grad[2 * j + 1] = s[1] * L[0][a] * D[1][b];
+                }
             }
-        }
+        return;
+    }
+    for (int d = 0; d <= p; ++d)
+        for (int c = 0; c <= d; ++c)
+            for (int b = 0; b <= d - c; ++b, ++j) {
+                const int a = d - b - c;
+                val[j] = L[0][a] * L[1][b] * L[2][c];
+                if (grad) {
+                    grad[3 * j] = s[0] * D[0][a] * L[1][b] * L[2][c];
+                    grad[3 * j + 1] = s[1] * L[0][a] * D[1][b] * L[2][c];
+                    grad[3 * j + 2] = s[2] * L[0][a] * L[1][b] * D[2][c];
+                }
+            }
 }
 
-// Fan of triangles (v0, v_k, v_{k+1}); on each the collapsed rule
+// Apex of a polyhedron's cone rule: the average of its distinct vertices.
+static void cell_apex3d(const HostSetup& S, int64_t c, double* apex) {
+    std::vector<int32_t> ids(S.cell_vtx.begin() + S.cell_ptr[c], S.cell_vtx.begin() + S.cell_ptr[c + 1]);
+    std::sort(ids.begin(), ids.end());
+    ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+    apex[0] = apex[1] = apex[2] = 0.0;
+    for (int32_t v : ids)
+        for (int d = 0; d < 3; ++d) apex[d] += S.verts[3 * v + d];
+    for (int d = 0; d < 3; ++d) apex[d] /= (double)ids.size();
+}
+
+// 2D: fan of triangles (v0, v_k, v_{k+1}); on each the collapsed rule
 // x(s,t) = A + s (B - A) + s t (C - B), weight w_s w_t s |(B-A) x (C-A)|.
-void element_rule(const HostSetup& S, int64_t c, int npts, std::vector<double>& xy,
+// 3D: cone of tetrahedra (apex, a, b, c) over the outward facets; on each
+// x(s,t,u) = A + s (B-A) + s t (C-B) + s t u (D-C), weight w_s w_t w_u s^2 t 6|T|,
+// with npts + 1 points in s and npts in t and u (exact to degree 2 npts - 2).
+void element_rule(const HostSetup& S, int64_t c, int npts, std::vector<double>& xs,
                   std::vector<double>& w) {
     std::vector<double> g, gw;
     gauss_legendre01(npts, g, gw);
-    const int64_t b = S.cell_ptr[c], m = S.cell_ptr[c + 1] - b;
     const double* V = S.verts.data();
-    xy.clear();
+    xs.clear();
     w.clear();
-    const double ax = V[2 * S.cell_vtx[b]], ay = V[2 * S.cell_vtx[b] + 1];
-    for (int64_t k = 1; k + 1 < m; ++k) {
-        const double bx = V[2 * S.cell_vtx[b + k]], by = V[2 * S.cell_vtx[b + k] + 1];
-        const double cx = V[2 * S.cell_vtx[b + k + 1]], cy = V[2 * S.cell_vtx[b + k + 1] + 1];
-        const double jac = std::fabs((bx - ax) * (cy - ay) - (by - ay) * (cx - ax));
-        for (int i = 0; i < npts; ++i)
-            for (int j = 0; j < npts; ++j) {
-                const double s = g[i], t = g[j];
-                xy.push_back(ax + s * (bx - ax) + s * t * (cx - bx));
-                xy.push_back(ay + s * (by - ay) + s * t * (cy - by));
-                w.push_back(gw[i] * gw[j] * s * jac);
-            }
+    if (S.dim == 2) {
+        const int64_t b = S.cell_ptr[c], m = S.cell_ptr[c + 1] - b;
+        const double ax = V[2 * S.cell_vtx[b]], ay = V[2 * S.cell_vtx[b] + 1];
+        for (int64_t k = 1; k + 1 < m; ++k) {
+            const double bx = V[2 * S.cell_vtx[b + k]], by = V[2 * S.cell_vtx[b + k] + 1];
+            const double cx = V[2 * S.cell_vtx[b + k + 1]], cy = V[2 * S.cell_vtx[b + k + 1] + 1];
+            const double jac = std::fabs((bx - ax) * (cy - ay) - (by - ay) * (cx - ax));
+            for (int i = 0; i < npts; ++i)
+                for (int j = 0; j < npts; ++j) {
+                    const double s = g[i], t = g[j];
+                    xs.push_back(ax + s * (bx - ax) + s * t * (cx - bx));
+                    xs.push_back(ay + s * (by - ay) + s * t * (cy - by));
+                    w.push_back(gw[i] * gw[j] * s * jac);
+                }
+        }
+        return;
+    }
+    std::vector<double> gs, gsw;
+    gauss_legendre01(npts + 1, gs, gsw);
+    double A[3];
+    cell_apex3d(S, c, A);
+    for (int64_t k = S.cell_ptr[c]; k < S.cell_ptr[c + 1]; k += 3) {
+        const double* B = V + 3 * S.cell_vtx[k];
+        const double* C = V + 3 * S.cell_vtx[k + 1];
+        const double* D = V + 3 * S.cell_vtx[k + 2];
+        double e1[3], e2[3], e3[3];
+        for (int d = 0; d < 3; ++d) { e1[d] = B[d] - A[d]; e2[d] = C[d] - A[d]; e3[d] = D[d] - A[d]; }
+        const double six_vol = std::fabs(e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) -
+                                         e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+                                         e1[2] * (e2[0] * e3[1] - e2[1] * e3[0]));
+        for (int i = 0; i <= npts; ++i)
+            for (int j = 0; j < npts; ++j)
+                for (int l = 0; l < npts; ++l) {
+                    const double s = gs[i], t = g[j], u = g[l];
+                    for (int d = 0; d < 3; ++d)
+                        xs.push_back(A[d] + s * (B[d] - A[d]) + s * t * (C[d] - B[d]) + s * t * u * (D[d] - C[d]));
+                    w.push_back(gsw[i] * gw[j] * gw[l] * s * s * t * six_vol);
+                }
     }
 }
 
+static int64_t element_rule_size(const HostSetup& S, int64_t c, int npts) {
+    const int64_t m = S.cell_ptr[c + 1] - S.cell_ptr[c];
+    return S.dim == 2 ? (m - 2) * npts * npts : (m / 3) * (npts + 1) * npts * npts;
+}
+
+// ---------------------------------------------------------------- geometry
+static void cross3(const double* a, const double* b, double* out) {
+    out[0] = a[1] * b[2] - a[2] * b[1];
+    out[1] = a[2] * b[0] - a[0] * b[2];
+    out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Checks each cell, fills bbox, diameter and area/volume (caller order).
+static int cell_geometry(HostSetup& S) {
+    const int64_t nc = S.nc;
+    const int dim = S.dim;
+    const double* V = S.verts.data();
+    S.bbox.assign(2 * dim * nc, 0.0);
+    S.diam.assign(nc, 0.0);
+    S.area.assign(nc, 0.0);
+    if (dim == 2) {
+        for (int64_t c = 0; c < nc; ++c) {
+            const int64_t b = S.cell_ptr[c], n = S.cell_ptr[c + 1] - b;
+            double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300, a2 = 0.0, d2 = 0.0;
+            for (int64_t k = 0; k < n; ++k) {
+                const int32_t i = S.cell_vtx[b + k];
+                x0 = std::min(x0, V[2 * i]); x1 = std::max(x1, V[2 * i]);
+                y0 = std::min(y0, V[2 * i + 1]); y1 = std::max(y1, V[2 * i + 1]);
+            }
+            const double ext = (x1 - x0) + (y1 - y0);
+            for (int64_t k = 0; k < n; ++k) {
+                const int32_t i = S.cell_vtx[b + k], j = S.cell_vtx[b + (k + 1) % n],
+                              l = S.cell_vtx[b + (k + 2) % n];
+                const double xi = V[2 * i], yi = V[2 * i + 1];
+                a2 += xi * V[2 * j + 1] - V[2 * j] * yi;
+                const double cr = (V[2 * j] - xi) * (V[2 * l + 1] - V[2 * j + 1]) -
+                                  (V[2 * j + 1] - yi) * (V[2 * l] - V[2 * j]);
+                if (cr < -1e-14 * ext * ext) {
+                    set_error("polydg_setup: cell is not convex with counter-clockwise vertices");
+                    return POLYDG_EINVAL;
+                }
+                for (int64_t k2 = k + 1; k2 < n; ++k2) {
+                    const int32_t o = S.cell_vtx[b + k2];
+                    const double dx = V[2 * o] - xi, dy = V[2 * o + 1] - yi;
+                    d2 = std::max(d2, dx * dx + dy * dy);
+                }
+            }
+            if (!(a2 > 0)) { set_error("polydg_setup: cell with non-positive area (clockwise?)"); return POLYDG_EINVAL; }
+            S.area[c] = 0.5 * a2;
+            S.diam[c] = std::sqrt(d2);
+            double* bb = &S.bbox[4 * c];
+            bb[0] = x0; bb[1] = x1; bb[2] = y0; bb[3] = y1;
+        }
+        return POLYDG_OK;
+    }
+    std::atomic<int> bad{0};
+    parallel_chunks(nc, [&](int64_t c0, int64_t c1) {
+        for (int64_t c = c0; c < c1; ++c) {
+            const int64_t b = S.cell_ptr[c], e = S.cell_ptr[c + 1];
+            double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, d2 = 0.0;
+            for (int64_t k = b; k < e; ++k)
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = std::min(lo[d], V[3 * S.cell_vtx[k] + d]);
+                    hi[d] = std::max(hi[d], V[3 * S.cell_vtx[k] + d]);
+                }
+            for (int64_t k = b; k < e; ++k)
+                for (int64_t k2 = k + 1; k2 < e; ++k2) {
+                    double s = 0.0;
+                    for (int d = 0; d < 3; ++d) {
+                        const double t = V[3 * S.cell_vtx[k] + d] - V[3 * S.cell_vtx[k2] + d];
+                        s += t * t;
+                    }
+                    d2 = std::max(d2, s);
+                }
+            const double ext = (hi[0] - lo[0]) + (hi[1] - lo[1]) + (hi[2] - lo[2]);
+            double apex[3], vol6 = 0.0;
+            cell_apex3d(S, c, apex);
+            for (int64_t k = b; k < e; k += 3) {
+                double a[3], bb[3], cc[3], cr[3];
+                for (int d = 0; d < 3; ++d) {
+                    a[d] = V[3 * S.cell_vtx[k] + d] - apex[d];
+                    bb[d] = V[3 * S.cell_vtx[k + 1] + d] - apex[d];
+                    cc[d] = V[3 * S.cell_vtx[k + 2] + d] - apex[d];
+                }
+                cross3(bb, cc, cr);
+                const double det = a[0] * cr[0] + a[1] * cr[1] + a[2] * cr[2];   // 6 vol of the cone tet
+                if (det < -1e-13 * ext * ext * ext) bad = 1;
+                vol6 += det;
+            }
+            if (!(vol6 > 0)) bad = 1;
+            S.area[c] = vol6 / 6.0;
+            S.diam[c] = std::sqrt(d2);
+            double* bx = &S.bbox[6 * c];
+            for (int d = 0; d < 3; ++d) { bx[2 * d] = lo[d]; bx[2 * d + 1] = hi[d]; }
+        }
+    });
+    if (bad) {
+        set_error("polydg_setup3d: a cell is not star-shaped about its vertex average, or has inward facets");
+        return POLYDG_EINVAL;
+    }
+    return POLYDG_OK;
+}
+
+// Interior faces: (K+, K-, vertices in K+'s orientation), sorted by (K+, K-, vertices).
+struct Face { int64_t kp, km; std::array<int32_t, 3> v; };
+
+static int match_faces(const HostSetup& S, std::vector<Face>& faces) {
+    faces.clear();
+    if (S.dim == 2) {
+        struct Edge { uint64_t key; int64_t cell; int32_t a, b; };
+        std::vector<Edge> edges;
+        edges.reserve(S.cell_vtx.size());
+        for (int64_t c = 0; c < S.nc; ++c) {
+            const int64_t b = S.cell_ptr[c], n = S.cell_ptr[c + 1] - b;
+            for (int64_t k = 0; k < n; ++k) {
+                const int32_t va = S.cell_vtx[b + k], vb = S.cell_vtx[b + (k + 1) % n];
+                const uint64_t lo = (uint64_t)std::min(va, vb), hi = (uint64_t)std::max(va, vb);
+                edges.push_back({(lo << 32) | hi, c, va, vb});
+            }
+        }
+        std::sort(edges.begin(), edges.end(), [](const Edge& x, const Edge& y) {
+            return std::tie(x.key, x.cell) < std::tie(y.key, y.cell);
+        });
+        for (size_t i = 0; i < edges.size();) {
+            size_t j = i + 1;
+            while (j < edges.size() && edges[j].key == edges[i].key) ++j;
+            if (j - i > 2) { set_error("polydg_setup: an edge is shared by more than two cells"); return POLYDG_EINVAL; }
+            if (j - i == 2) {
+                const Edge& e0 = edges[i];   // lower cell id (sorted by cell)
+                const Edge& e1 = edges[i + 1];
+                if (e0.cell == e1.cell || e0.a != e1.b || e0.b != e1.a) {
+                    set_error("polydg_setup: shared edge without opposite orientation");
+                    return POLYDG_EINVAL;
+                }
+                faces.push_back({e0.cell, e1.cell, {e0.a, e0.b, -1}});
+            }
+            i = j;
+        }
+    } else {
+        struct Tri { std::array<int32_t, 3> key; int64_t cell; std::array<int32_t, 3> v; };
+        std::vector<Tri> tris;
+        tris.reserve(S.cell_vtx.size() / 3);
+        for (int64_t c = 0; c < S.nc; ++c)
+            for (int64_t k = S.cell_ptr[c]; k < S.cell_ptr[c + 1]; k += 3) {
+                Tri t;
+                t.v = {S.cell_vtx[k], S.cell_vtx[k + 1], S.cell_vtx[k + 2]};
+                t.key = t.v;
+                std::sort(t.key.begin(), t.key.end());
+                t.cell = c;
+                tris.push_back(t);
+            }
+        std::sort(tris.begin(), tris.end(), [](const Tri& x, const Tri& y) {
+            return std::tie(x.key, x.cell) < std::tie(y.key, y.cell);
+        });
+        for (size_t i = 0; i < tris.size();) {
+            size_t j = i + 1;
+            while (j < tris.size() && tris[j].key == tris[i].key) ++j;
+            if (j - i > 2) { set_error("polydg_setup3d: a facet is shared by more than two cells"); return POLYDG_EINVAL; }
+            if (j - i == 2) {
+                const Tri& t0 = tris[i];
+                const Tri& t1 = tris[i + 1];
+                // t1 must run through the same vertices in the opposite cyclic order
+                const std::array<int32_t, 3> r = {t0.v[0], t0.v[2], t0.v[1]};
+                const bool opp = t1.v == r || t1.v == std::array<int32_t, 3>{r[1], r[2], r[0]} ||
+                                 t1.v == std::array<int32_t, 3>{r[2], r[0], r[1]};
+                if (t0.cell == t1.cell || !opp) {
+                    set_error("polydg_setup3d: shared facet without opposite orientation");
+                    return POLYDG_EINVAL;
+                }
+                faces.push_back({t0.cell, t1.cell, t0.v});
+            }
+            i = j;
+        }
+    }
+    std::sort(faces.begin(), faces.end(), [](const Face& x, const Face& y) {
+        return std::tie(x.kp, x.km, x.v) < std::tie(y.kp, y.km, y.v);
+    });
+    return POLYDG_OK;
+}
+
+// Quadrature of an interior face: points [n * dim], weights, unit normal out of K+.
+static void face_rule(const HostSetup& S, const Face& F, const std::vector<double>& g,
+                      const std::vector<double>& gw, std::vector<double>& xs, std::vector<double>& w,
+                      double* normal) {
+    const double* V = S.verts.data();
+    const int nq = (int)g.size();
+    xs.clear();
+    w.clear();
+    if (S.dim == 2) {
+        const double ax = V[2 * F.v[0]], ay = V[2 * F.v[0] + 1], bx = V[2 * F.v[1]], by = V[2 * F.v[1] + 1];
+        const double len = std::sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+        normal[0] = (by - ay) / len;
+        normal[1] = -(bx - ax) / len;
+        for (int k = 0; k < nq; ++k) {
+            xs.push_back(ax + g[k] * (bx - ax));
+            xs.push_back(ay + g[k] * (by - ay));
+            w.push_back(gw[k] * len);
+        }
+        return;
+    }
+    const double* A = V + 3 * F.v[0];
+    const double* B = V + 3 * F.v[1];
+    const double* C = V + 3 * F.v[2];
+    double e1[3], e2[3], cr[3];
+    for (int d = 0; d < 3; ++d) { e1[d] = B[d] - A[d]; e2[d] = C[d] - A[d]; }
+    cross3(e1, e2, cr);
+    const double twice_area = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    for (int d = 0; d < 3; ++d) normal[d] = cr[d] / twice_area;
+    for (int i = 0; i < nq; ++i)
+        for (int j = 0; j < nq; ++j) {
+            const double s = g[i], t = g[j];
+            for (int d = 0; d < 3; ++d) xs.push_back(A[d] + s * (B[d] - A[d]) + s * t * (C[d] - B[d]));
+            w.push_back(gw[i] * gw[j] * s * twice_area);
+        }
+}
+
 // --------------------------------------------------------------- validation
-static int validate(const polydg_mesh* m, int p, const int32_t* sub) {
+static int validate_sigma(int dim, const double* sigma, int64_t nc) {
+    for (int64_t c = 0; c < nc; ++c) {
+        const double* s = sigma + dim * dim * c;
+        double scale = 0.0;
+        for (int i = 0; i < dim * dim; ++i) scale += std::fabs(s[i]);
+        bool ok = scale > 0 && std::isfinite(scale);
+        for (int i = 0; i < dim && ok; ++i)
+            for (int j = i + 1; j < dim; ++j)
+                if (std::fabs(s[i * dim + j] - s[j * dim + i]) > 1e-13 * scale) ok = false;
+        // positive definite: the Cholesky pivots of the (symmetric part) are positive
+        double L[9] = {0};
+        for (int j = 0; j < dim && ok; ++j) {
+            double d = s[j * dim + j];
+            for (int k = 0; k < j; ++k) d -= L[j * 3 + k] * L[j * 3 + k];
+            if (!(d > 0)) { ok = false; break; }
+            L[j * 3 + j] = std::sqrt(d);
+            for (int i = j + 1; i < dim; ++i) {
+                double t = s[i * dim + j];
+                for (int k = 0; k < j; ++k) t -= L[i * 3 + k] * L[j * 3 + k];
+                L[i * 3 + j] = t / L[j * 3 + j];
+            }
+        }
+        if (!ok) {
+            set_error("polydg_setup: sigma of a cell is not symmetric positive definite");
+            return POLYDG_EINVAL;
+        }
+    }
+    return POLYDG_OK;
+}
+
+static int validate2d(const polydg_mesh* m, int p, const int32_t* sub) {
     if (!m || !m->vertices || !m->cell_ptr || !m->cell_vtx || !m->sigma || !sub) {
         set_error("polydg_setup: null mesh array");
         return POLYDG_EINVAL;
@@ -117,33 +436,39 @@ static int validate(const polydg_mesh* m, int p, const int32_t* sub) {
                 set_error("polydg_setup: vertex id out of range");
                 return POLYDG_EINVAL;
             }
-        const double* s = m->sigma + 4 * c;
-        const double scale = std::fabs(s[0]) + std::fabs(s[1]) + std::fabs(s[2]) + std::fabs(s[3]);
-        if (!(s[0] > 0) || !(s[0] * s[3] - s[1] * s[2] > 0) || std::fabs(s[1] - s[2]) > 1e-13 * scale) {
-            set_error("polydg_setup: sigma of a cell is not symmetric positive definite");
-            return POLYDG_EINVAL;
-        }
     }
-    return POLYDG_OK;
+    return validate_sigma(2, m->sigma, m->n_cells);
 }
 
-// ---------------------------------------------------------------- assembly
-int host_setup(const polydg_mesh* m, int p, const int32_t* sub, double chi_cm, double dt,
-               double eta0, HostSetup& S) {
-    int st = validate(m, p, sub);
-    if (st) return st;
-    if (!(chi_cm > 0) || !(dt > 0) || !(eta0 > 0)) {
-        set_error("polydg_setup: chi_cm, dt and eta0 must be positive");
+static int validate3d(const polydg_mesh3d* m, int p, const int32_t* sub) {
+    if (!m || !m->vertices || !m->cell_face_ptr || !m->face_vtx || !m->sigma || !sub) {
+        set_error("polydg_setup3d: null mesh array");
         return POLYDG_EINVAL;
     }
-    const int64_t nc = m->n_cells;
-    const int np = n_modes(p);
-    S.p = p; S.n_p = np; S.nc = nc; S.chi_cm = chi_cm; S.dt = dt; S.eta0 = eta0;
-    S.verts.assign(m->vertices, m->vertices + 2 * m->n_vertices);
-    S.cell_ptr.assign(m->cell_ptr, m->cell_ptr + nc + 1);
-    S.cell_vtx.assign(m->cell_vtx, m->cell_vtx + m->cell_ptr[nc]);
-    S.sigma.assign(m->sigma, m->sigma + 4 * nc);
-    const double* V = S.verts.data();
+    // the device kernels are instantiated for n_p in {3, 6, 10, 15}; in 3D only p = 2 (n_p = 10) maps
+    if (p != 2) { set_error("polydg_setup3d: degree p must be 2 (n_p = 10)"); return POLYDG_EINVAL; }
+    if (m->n_cells < 1 || m->n_vertices < 4 || m->cell_face_ptr[0] != 0) {
+        set_error("polydg_setup3d: empty mesh or cell_face_ptr[0] != 0");
+        return POLYDG_EINVAL;
+    }
+    for (int64_t c = 0; c < m->n_cells; ++c) {
+        const int64_t b = m->cell_face_ptr[c], e = m->cell_face_ptr[c + 1];
+        if (e - b < 4) { set_error("polydg_setup3d: cell with fewer than 4 facets"); return POLYDG_EINVAL; }
+        for (int64_t k = 3 * b; k < 3 * e; ++k)
+            if (m->face_vtx[k] < 0 || m->face_vtx[k] >= m->n_vertices) {
+                set_error("polydg_setup3d: vertex id out of range");
+                return POLYDG_EINVAL;
+            }
+    }
+    return validate_sigma(3, m->sigma, m->n_cells);
+}
+
+// --------------------------------------------------------------- assembly
+// Everything after the mesh copy: subdomain renumbering, geometry, faces,
+// element and face blocks (Eq. coer, Eq. eta), K_h and the quadrature-node tables.
+static int assemble(HostSetup& S, const int32_t* sub) {
+    const int64_t nc = S.nc;
+    const int dim = S.dim, p = S.p, np = S.n_p;
 
     // subdomains: ids dense in [0, n_sub)
     int32_t smax = -1;
@@ -168,172 +493,135 @@ int host_setup(const polydg_mesh* m, int p, const int32_t* sub, double chi_cm, d
             S.to_internal[c] = e;
         }
     }
-
-    // geometry (caller order) and convexity / orientation check
-    S.bbox.resize(4 * nc);
-    S.diam.resize(nc);
-    S.area.resize(nc);
-    for (int64_t c = 0; c < nc; ++c) {
-        const int64_t b = S.cell_ptr[c], n = S.cell_ptr[c + 1] - b;
-        double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300, a2 = 0.0, d2 = 0.0;
-        for (int64_t k = 0; k < n; ++k) {
-            const int32_t i = S.cell_vtx[b + k];
-            x0 = std::min(x0, V[2 * i]); x1 = std::max(x1, V[2 * i]);
-            y0 = std::min(y0, V[2 * i + 1]); y1 = std::max(y1, V[2 * i + 1]);
-        }
-        const double ext = (x1 - x0) + (y1 - y0);
-        for (int64_t k = 0; k < n; ++k) {
-            const int32_t i = S.cell_vtx[b + k], j = S.cell_vtx[b + (k + 1) % n],
-                          l = S.cell_vtx[b + (k + 2) % n];
-            const double xi = V[2 * i], yi = V[2 * i + 1];
-            a2 += xi * V[2 * j + 1] - V[2 * j] * yi;
-            const double cr = (V[2 * j] - xi) * (V[2 * l + 1] - V[2 * j + 1]) -
-                              (V[2 * j + 1] - yi) * (V[2 * l] - V[2 * j]);
-            if (cr < -1e-14 * ext * ext) {
-                set_error("polydg_setup: cell is not convex with counter-clockwise vertices");
-                return POLYDG_EINVAL;
-            }
-            for (int64_t k2 = k + 1; k2 < n; ++k2) {
-                const int32_t o = S.cell_vtx[b + k2];
-                const double dx = V[2 * o] - xi, dy = V[2 * o + 1] - yi;
-                d2 = std::max(d2, dx * dx + dy * dy);
-            }
-        }
-        if (!(a2 > 0)) { set_error("polydg_setup: cell with non-positive area (clockwise?)"); return POLYDG_EINVAL; }
-        S.area[c] = 0.5 * a2;
-        S.diam[c] = std::sqrt(d2);
-        double* bb = &S.bbox[4 * c];
-        bb[0] = x0; bb[1] = x1; bb[2] = y0; bb[3] = y1;
-    }
-
-    // connectivity: sort all edges by their sorted vertex pair
-    struct Edge { uint64_t key; int64_t cell; int32_t a, b; };
-    std::vector<Edge> edges;
-    edges.reserve(S.cell_vtx.size());
-    for (int64_t c = 0; c < nc; ++c) {
-        const int64_t b = S.cell_ptr[c], n = S.cell_ptr[c + 1] - b;
-        for (int64_t k = 0; k < n; ++k) {
-            const int32_t va = S.cell_vtx[b + k], vb = S.cell_vtx[b + (k + 1) % n];
-            const uint64_t lo = (uint64_t)std::min(va, vb), hi = (uint64_t)std::max(va, vb);
-            edges.push_back({(lo << 32) | hi, c, va, vb});
-        }
-    }
-    std::sort(edges.begin(), edges.end(), [](const Edge& x, const Edge& y) {
-        return std::tie(x.key, x.cell) < std::tie(y.key, y.cell);
-    });
-    struct Face { int64_t kp, km; int32_t a, b; };
+    if (int st = cell_geometry(S)) return st;
     std::vector<Face> faces;
-    for (size_t i = 0; i < edges.size();) {
-        size_t j = i + 1;
-        while (j < edges.size() && edges[j].key == edges[i].key) ++j;
-        if (j - i > 2) { set_error("polydg_setup: an edge is shared by more than two cells"); return POLYDG_EINVAL; }
-        if (j - i == 2) {
-            const Edge& e0 = edges[i];   // lower cell id (sorted by cell)
-            const Edge& e1 = edges[i + 1];
-            if (e0.cell == e1.cell || e0.a != e1.b || e0.b != e1.a) {
-                set_error("polydg_setup: shared edge without opposite orientation");
-                return POLYDG_EINVAL;
-            }
-            faces.push_back({e0.cell, e1.cell, e0.a, e0.b});
-        }
-        i = j;
-    }
-    std::sort(faces.begin(), faces.end(), [](const Face& x, const Face& y) {
-        return std::tie(x.kp, x.km, x.a) < std::tie(y.kp, y.km, y.a);
-    });
+    if (int st = match_faces(S, faces)) return st;
     const int64_t nf = (int64_t)faces.size();
     S.f_plus.resize(nf);
     S.f_minus.resize(nf);
     for (int64_t f = 0; f < nf; ++f) { S.f_plus[f] = faces[f].kp; S.f_minus[f] = faces[f].km; }
 
-    // spectral norm of each Sigma_K (2x2 symmetric): (a+c)/2 + sqrt(((a-c)/2)^2 + b^2)
+    // spectral norm of each Sigma_K
     std::vector<double> lam(nc);
     for (int64_t c = 0; c < nc; ++c) {
-        const double* s = &S.sigma[4 * c];
-        const double h = 0.5 * (s[0] - s[3]);
-        lam[c] = 0.5 * (s[0] + s[3]) + std::sqrt(h * h + s[1] * s[1]);
+        const double* s = &S.sigma[dim * dim * c];
+        if (dim == 2) {      // 2x2 symmetric: (a+c)/2 + sqrt(((a-c)/2)^2 + b^2)
+            const double h = 0.5 * (s[0] - s[3]);
+            lam[c] = 0.5 * (s[0] + s[3]) + std::sqrt(h * h + s[1] * s[1]);
+        } else {
+            double a[9], w[3], qt[9];
+            for (int i = 0; i < 9; ++i) a[i] = s[i];
+            if (!sym_eig(3, a, w, qt)) { set_error("polydg_setup3d: eigenvalues of sigma did not converge"); return POLYDG_EINVAL; }
+            lam[c] = w[2];
+        }
     }
 
     const int nq = p + 1;
     const int nn2 = np * np;
     // element blocks, caller order
     std::vector<double> Mc(nc * nn2, 0.0), Ac(nc * nn2, 0.0);
-    std::vector<double> xy, w, val(np), grad(2 * np);
-    std::vector<double> phis, grads;
-    for (int64_t c = 0; c < nc; ++c) {
-        element_rule(S, c, nq, xy, w);
-        const size_t nqp = w.size();
-        phis.resize(nqp * np);
-        grads.resize(nqp * 2 * np);
-        for (size_t k = 0; k < nqp; ++k)
-            eval_basis(p, &S.bbox[4 * c], xy[2 * k], xy[2 * k + 1], &phis[k * np], &grads[k * 2 * np]);
-        const double* s = &S.sigma[4 * c];
-        double* M = &Mc[c * nn2];
-        double* A = &Ac[c * nn2];
-        for (int i = 0; i < np; ++i)
-            for (int j = i; j < np; ++j) {
-                double mij = 0.0, aij = 0.0;
-                for (size_t k = 0; k < nqp; ++k) {
-                    const double* gi = &grads[k * 2 * np + 2 * i];
-                    const double* gj = &grads[k * 2 * np + 2 * j];
-                    mij += w[k] * phis[k * np + i] * phis[k * np + j];
-                    const double sgx = s[0] * gj[0] + s[1] * gj[1];
-                    const double sgy = s[2] * gj[0] + s[3] * gj[1];
-                    aij += w[k] * (gi[0] * sgx + gi[1] * sgy);
+    parallel_chunks(nc, [&](int64_t c0, int64_t c1) {
+        std::vector<double> xs, w, phis, grads;
+        for (int64_t c = c0; c < c1; ++c) {
+            element_rule(S, c, nq, xs, w);
+            const size_t nqp = w.size();
+            phis.resize(nqp * np);
+            grads.resize(nqp * dim * np);
+            for (size_t k = 0; k < nqp; ++k)
+                eval_basis(dim, p, &S.bbox[2 * dim * c], &xs[dim * k], &phis[k * np], &grads[k * dim * np]);
+            const double* s = &S.sigma[dim * dim * c];
+            double* M = &Mc[c * nn2];
+            double* A = &Ac[c * nn2];
+            for (int i = 0; i < np; ++i)
+                for (int j = i; j < np; ++j) {
+                    double mij = 0.0, aij = 0.0;
+                    for (size_t k = 0; k < nqp; ++k) {
+                        const double* gi = &grads[(k * np + i) * dim];
+                        const double* gj = &grads[(k * np + j) * dim];
+                        mij += w[k] * phis[k * np + i] * phis[k * np + j];
+                        double e = 0.0;
+                        for (int r = 0; r < dim; ++r) {
+                            double sg = 0.0;
+                            for (int t = 0; t < dim; ++t) sg += s[r * dim + t] * gj[t];
+                            e += gi[r] * sg;
+                        }
+                        aij += w[k] * e;
+                    }
+                    M[i * np + j] = M[j * np + i] = mij;
+                    A[i * np + j] = A[j * np + i] = aij;
                 }
-                M[i * np + j] = M[j * np + i] = mij;
-                A[i * np + j] = A[j * np + i] = aij;
-            }
-    }
+        }
+    });
 
-    // interior face terms of Eq. coer; sides: 0 = K+, 1 = K-
+    // interior face terms of Eq. coer; sides: 0 = K+, 1 = K-.  Faces are computed in
+    // parallel chunks; their self blocks are then added to the element blocks in face
+    // order, so the sums do not depend on the thread count.
     std::vector<double> gx, gw;
     gauss_legendre01(nq, gx, gw);
     std::vector<double> Aoff(nf * nn2, 0.0);
-    std::vector<double> Vs[2], Fs[2];
-    for (int s = 0; s < 2; ++s) { Vs[s].resize(nq * np); Fs[s].resize(nq * np); }
-    for (int64_t f = 0; f < nf; ++f) {
-        const Face& F = faces[f];
-        const double ax = V[2 * F.a], ay = V[2 * F.a + 1], bx = V[2 * F.b], by = V[2 * F.b + 1];
-        const double len = std::sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
-        const double nx = (by - ay) / len, ny = -(bx - ax) / len;   // out of K+
-        const double h = 2.0 * S.diam[F.kp] * S.diam[F.km] / (S.diam[F.kp] + S.diam[F.km]);
-        const double eta = eta0 * 0.5 * (lam[F.kp] + lam[F.km]) * p * p / h;
-        const int64_t cells[2] = {F.kp, F.km};
-        for (int s = 0; s < 2; ++s) {
-            const double* sg = &S.sigma[4 * cells[s]];
-            const double snx = sg[0] * nx + sg[1] * ny, sny = sg[2] * nx + sg[3] * ny;  // Sigma n
-            for (int k = 0; k < nq; ++k) {
-                const double x = ax + gx[k] * (bx - ax), y = ay + gx[k] * (by - ay);
-                eval_basis(p, &S.bbox[4 * cells[s]], x, y, val.data(), grad.data());
-                for (int j = 0; j < np; ++j) {
-                    Vs[s][k * np + j] = val[j];
-                    Fs[s][k * np + j] = grad[2 * j] * snx + grad[2 * j + 1] * sny;
-                }
-            }
-        }
-        const double sgn[2] = {1.0, -1.0};
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) {
-                if (b < a) continue;
-                double* out = (a == b) ? &Ac[cells[a] * nn2] : &Aoff[f * nn2];
-                for (int i = 0; i < np; ++i)
-                    for (int j = (a == b ? i : 0); j < np; ++j) {
-                        double acc = 0.0;
-                        for (int k = 0; k < nq; ++k) {
-                            const double wk = gw[k] * len;
-                            acc += wk * (-0.5 * sgn[a] * Vs[a][k * np + i] * Fs[b][k * np + j]
-                                         - 0.5 * sgn[b] * Fs[a][k * np + i] * Vs[b][k * np + j]
-                                         + eta * sgn[a] * sgn[b] * Vs[a][k * np + i] * Vs[b][k * np + j]);
-                        }
-                        if (a == b) {
-                            out[i * np + j] += acc;
-                            if (j != i) out[j * np + i] += acc;
-                        } else {
-                            out[i * np + j] = acc;
+    const int64_t fchunk = 1 << 15;
+    std::vector<double> self((size_t)std::min<int64_t>(fchunk, std::max<int64_t>(nf, 1)) * 2 * nn2);
+    for (int64_t f0 = 0; f0 < nf; f0 += fchunk) {
+        const int64_t f1 = std::min(nf, f0 + fchunk);
+        parallel_chunks(f1 - f0, [&](int64_t i0, int64_t i1) {
+            std::vector<double> xs, w, val(np), grad(dim * np), Vs[2], Fs[2];
+            for (int64_t f = f0 + i0; f < f0 + i1; ++f) {
+                const Face& F = faces[f];
+                double nrm[3];
+                face_rule(S, F, gx, gw, xs, w, nrm);
+                const int nfq = (int)w.size();
+                const double h = 2.0 * S.diam[F.kp] * S.diam[F.km] / (S.diam[F.kp] + S.diam[F.km]);
+                const double eta = S.eta0 * 0.5 * (lam[F.kp] + lam[F.km]) * p * p / h;
+                const int64_t cells[2] = {F.kp, F.km};
+                for (int sd = 0; sd < 2; ++sd) {
+                    Vs[sd].resize(nfq * np);
+                    Fs[sd].resize(nfq * np);
+                    const double* sg = &S.sigma[dim * dim * cells[sd]];
+                    double sn[3];                                     // Sigma n
+                    for (int r = 0; r < dim; ++r) {
+                        sn[r] = 0.0;
+                        for (int t = 0; t < dim; ++t) sn[r] += sg[r * dim + t] * nrm[t];
+                    }
+                    for (int k = 0; k < nfq; ++k) {
+                        eval_basis(dim, p, &S.bbox[2 * dim * cells[sd]], &xs[dim * k], val.data(), grad.data());
+                        for (int j = 0; j < np; ++j) {
+                            Vs[sd][k * np + j] = val[j];
+                            double fl = 0.0;
+                            for (int r = 0; r < dim; ++r) fl += grad[j * dim + r] * sn[r];
+                            Fs[sd][k * np + j] = fl;
                         }
                     }
+                }
+                const double sgn[2] = {1.0, -1.0};
+                double* sp = &self[(size_t)(f - f0) * 2 * nn2];
+                std::fill(sp, sp + 2 * nn2, 0.0);
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b) {
+                        if (b < a) continue;
+                        double* out = (a == b) ? sp + a * nn2 : &Aoff[f * nn2];
+                        for (int i = 0; i < np; ++i)
+                            for (int j = (a == b ? i : 0); j < np; ++j) {
+                                double acc = 0.0;
+                                for (int k = 0; k < nfq; ++k)
+                                    acc += w[k] * (-0.5 * sgn[a] * Vs[a][k * np + i] * Fs[b][k * np + j]
+                                                   - 0.5 * sgn[b] * Fs[a][k * np + i] * Vs[b][k * np + j]
+                                                   + eta * sgn[a] * sgn[b] * Vs[a][k * np + i] * Vs[b][k * np + j]);
+                                if (a == b) {
+                                    out[i * np + j] += acc;
+                                    if (j != i) out[j * np + i] += acc;
+                                } else {
+                                    out[i * np + j] = acc;
+                                }
+                            }
+                    }
             }
+        });
+        for (int64_t f = f0; f < f1; ++f) {
+            const double* sp = &self[(size_t)(f - f0) * 2 * nn2];
+            double* Ap = &Ac[faces[f].kp * nn2];
+            double* Am = &Ac[faces[f].km * nn2];
+            for (int t = 0; t < nn2; ++t) { Ap[t] += sp[t]; Am[t] += sp[nn2 + t]; }
+        }
     }
 
     // block-sparse K_h and (chi_cm M - dt/2 A), internal order, rows: diag first then
@@ -366,6 +654,7 @@ int host_setup(const polydg_mesh* m, int p, const int32_t* sub, double chi_cm, d
     S.Kval.assign(nblk * nn2, 0.0);
     S.Kminus_val.assign(nblk * nn2, 0.0);
     S.Mblk.assign(nc * nn2, 0.0);
+    const double chi_cm = S.chi_cm, dt = S.dt;
     for (int64_t e = 0; e < nc; ++e) {
         const int64_t c = S.to_caller[e];
         for (int32_t bi = S.row_ptr[e]; bi < S.row_ptr[e + 1]; ++bi) {
@@ -396,28 +685,67 @@ int host_setup(const polydg_mesh* m, int p, const int32_t* sub, double chi_cm, d
 
     // element quadrature nodes (ionic state and load vectors), internal cell order
     std::vector<int64_t> caller_node_ptr(nc + 1, 0);
-    {
-        for (int64_t c = 0; c < nc; ++c) {
-            const int64_t ntri = S.cell_ptr[c + 1] - S.cell_ptr[c] - 2;
-            caller_node_ptr[c + 1] = caller_node_ptr[c] + ntri * nq * nq;
-        }
-    }
+    for (int64_t c = 0; c < nc; ++c) caller_node_ptr[c + 1] = caller_node_ptr[c] + element_rule_size(S, c, nq);
     S.node_ptr.assign(nc + 1, 0);
-    S.node_w.clear(); S.node_xy.clear(); S.node_phi.clear(); S.node_to_caller_pos.clear();
-    for (int64_t e = 0; e < nc; ++e) {
-        const int64_t c = S.to_caller[e];
-        element_rule(S, c, nq, xy, w);
-        for (size_t k = 0; k < w.size(); ++k) {
-            eval_basis(p, &S.bbox[4 * c], xy[2 * k], xy[2 * k + 1], val.data(), nullptr);
-            S.node_w.push_back(w[k]);
-            S.node_xy.push_back(xy[2 * k]);
-            S.node_xy.push_back(xy[2 * k + 1]);
-            S.node_phi.insert(S.node_phi.end(), val.begin(), val.end());
-            S.node_to_caller_pos.push_back(caller_node_ptr[c] + (int64_t)k);
+    for (int64_t e = 0; e < nc; ++e) S.node_ptr[e + 1] = S.node_ptr[e] + element_rule_size(S, S.to_caller[e], nq);
+    const int64_t nn = S.node_ptr[nc];
+    S.node_w.assign(nn, 0.0);
+    S.node_x.assign(nn * dim, 0.0);
+    S.node_phi.assign(nn * np, 0.0);
+    S.node_to_caller_pos.assign(nn, 0);
+    parallel_chunks(nc, [&](int64_t e0, int64_t e1) {
+        std::vector<double> xs, w;
+        for (int64_t e = e0; e < e1; ++e) {
+            const int64_t c = S.to_caller[e];
+            element_rule(S, c, nq, xs, w);
+            const int64_t q0 = S.node_ptr[e];
+            for (size_t k = 0; k < w.size(); ++k) {
+                const int64_t qn = q0 + (int64_t)k;
+                eval_basis(dim, p, &S.bbox[2 * dim * c], &xs[dim * k], &S.node_phi[qn * np], nullptr);
+                S.node_w[qn] = w[k];
+                for (int d = 0; d < dim; ++d) S.node_x[qn * dim + d] = xs[dim * k + d];
+                S.node_to_caller_pos[qn] = caller_node_ptr[c] + (int64_t)k;
+            }
         }
-        S.node_ptr[e + 1] = (int64_t)S.node_w.size();
+    });
+    return POLYDG_OK;
+}
+
+static int check_scalars(double chi_cm, double dt, double eta0) {
+    if (!(chi_cm > 0) || !(dt > 0) || !(eta0 > 0)) {
+        set_error("polydg_setup: chi_cm, dt and eta0 must be positive");
+        return POLYDG_EINVAL;
     }
     return POLYDG_OK;
+}
+
+int host_setup(const polydg_mesh* m, int p, const int32_t* sub, double chi_cm, double dt,
+               double eta0, HostSetup& S) {
+    if (int st = validate2d(m, p, sub)) return st;
+    if (int st = check_scalars(chi_cm, dt, eta0)) return st;
+    const int64_t nc = m->n_cells;
+    S.dim = 2;
+    S.p = p; S.n_p = n_modes(p, 2); S.nc = nc; S.chi_cm = chi_cm; S.dt = dt; S.eta0 = eta0;
+    S.verts.assign(m->vertices, m->vertices + 2 * m->n_vertices);
+    S.cell_ptr.assign(m->cell_ptr, m->cell_ptr + nc + 1);
+    S.cell_vtx.assign(m->cell_vtx, m->cell_vtx + m->cell_ptr[nc]);
+    S.sigma.assign(m->sigma, m->sigma + 4 * nc);
+    return assemble(S, sub);
+}
+
+int host_setup3d(const polydg_mesh3d* m, int p, const int32_t* sub, double chi_cm, double dt,
+                 double eta0, HostSetup& S) {
+    if (int st = validate3d(m, p, sub)) return st;
+    if (int st = check_scalars(chi_cm, dt, eta0)) return st;
+    const int64_t nc = m->n_cells;
+    S.dim = 3;
+    S.p = p; S.n_p = n_modes(p, 3); S.nc = nc; S.chi_cm = chi_cm; S.dt = dt; S.eta0 = eta0;
+    S.verts.assign(m->vertices, m->vertices + 3 * m->n_vertices);
+    S.cell_ptr.resize(nc + 1);
+    for (int64_t c = 0; c <= nc; ++c) S.cell_ptr[c] = 3 * m->cell_face_ptr[c];
+    S.cell_vtx.assign(m->face_vtx, m->face_vtx + S.cell_ptr[nc]);
+    S.sigma.assign(m->sigma, m->sigma + 9 * nc);
+    return assemble(S, sub);
 }
 
 // ------------------------------------------------------------ coarse space
@@ -456,24 +784,27 @@ int coarse_setup(const HostSetup& S, const int32_t* coarse, int q, CoarseSetup& 
     if (!coarse) { set_error("asm_setup: null coarse partition"); return POLYDG_EINVAL; }
     if (q < 1 || q > S.p) { set_error("asm_setup: coarse degree q must be in 1..p"); return POLYDG_EINVAL; }
     const int64_t nc = S.nc;
-    const int np = S.n_p, nqm = n_modes(q);
+    const int dim = S.dim, np = S.n_p, nqm = n_modes(q, dim);
     int32_t amax = -1;
     for (int64_t c = 0; c < nc; ++c) {
         if (coarse[c] < 0) { set_error("asm_setup: negative agglomerate id"); return POLYDG_EINVAL; }
         amax = std::max(amax, coarse[c]);
     }
     C.q = q; C.n_q = nqm; C.n_agg = amax + 1;
-    std::vector<double> abox(4 * C.n_agg);
-    for (int J = 0; J < C.n_agg; ++J) { abox[4*J] = 1e300; abox[4*J+1] = -1e300; abox[4*J+2] = 1e300; abox[4*J+3] = -1e300; }
+    std::vector<double> abox(2 * dim * (size_t)C.n_agg);
+    for (int J = 0; J < C.n_agg; ++J)
+        for (int d = 0; d < dim; ++d) { abox[2 * dim * J + 2 * d] = 1e300; abox[2 * dim * J + 2 * d + 1] = -1e300; }
     std::vector<int64_t> cnt(C.n_agg, 0);
     for (int64_t c = 0; c < nc; ++c) {
         const int J = coarse[c];
         cnt[J]++;
-        for (int64_t k = S.cell_ptr[c]; k < S.cell_ptr[c + 1]; ++k) {
-            const double x = S.verts[2 * S.cell_vtx[k]], y = S.verts[2 * S.cell_vtx[k] + 1];
-            abox[4*J] = std::min(abox[4*J], x); abox[4*J+1] = std::max(abox[4*J+1], x);
-            abox[4*J+2] = std::min(abox[4*J+2], y); abox[4*J+3] = std::max(abox[4*J+3], y);
-        }
+        double* bx = &abox[2 * dim * J];
+        for (int64_t k = S.cell_ptr[c]; k < S.cell_ptr[c + 1]; ++k)
+            for (int d = 0; d < dim; ++d) {
+                const double x = S.verts[dim * S.cell_vtx[k] + d];
+                bx[2 * d] = std::min(bx[2 * d], x);
+                bx[2 * d + 1] = std::max(bx[2 * d + 1], x);
+            }
     }
     for (int J = 0; J < C.n_agg; ++J)
         if (!cnt[J]) { set_error("asm_setup: unused agglomerate id"); return POLYDG_EINVAL; }
@@ -489,22 +820,26 @@ int coarse_setup(const HostSetup& S, const int32_t* coarse, int q, CoarseSetup& 
     }
     // T_K per internal cell
     C.T.assign(nc * np * nqm, 0.0);
-    std::vector<double> xy, w, v(np), psi(nqm);
-    for (int64_t e = 0; e < nc; ++e) {
-        const int64_t c = S.to_caller[e];
-        const int J = C.agg_of_cell[e];
-        element_rule(S, c, S.p + 1, xy, w);
-        double* T = &C.T[e * np * nqm];
-        for (size_t k = 0; k < w.size(); ++k) {
-            eval_basis(S.p, &S.bbox[4 * c], xy[2 * k], xy[2 * k + 1], v.data(), nullptr);
-            eval_basis(q, &abox[4 * J], xy[2 * k], xy[2 * k + 1], psi.data(), nullptr);
-            for (int i = 0; i < np; ++i)
-                for (int a = 0; a < nqm; ++a) T[i * nqm + a] += w[k] * v[i] * psi[a];
+    std::atomic<int> bad{0};
+    parallel_chunks(nc, [&](int64_t e0, int64_t e1) {
+        std::vector<double> xs, w, v(np), psi(nqm);
+        for (int64_t e = e0; e < e1; ++e) {
+            const int64_t c = S.to_caller[e];
+            const int J = C.agg_of_cell[e];
+            element_rule(S, c, S.p + 1, xs, w);
+            double* T = &C.T[e * np * nqm];
+            for (size_t k = 0; k < w.size(); ++k) {
+                eval_basis(dim, S.p, &S.bbox[2 * dim * c], &xs[dim * k], v.data(), nullptr);
+                eval_basis(dim, q, &abox[2 * dim * J], &xs[dim * k], psi.data(), nullptr);
+                for (int i = 0; i < np; ++i)
+                    for (int a = 0; a < nqm; ++a) T[i * nqm + a] += w[k] * v[i] * psi[a];
+            }
+            if (!cholesky_solve_small(np, &S.Mblk[e * np * np], T, nqm)) bad = 1;
         }
-        if (!cholesky_solve_small(np, &S.Mblk[e * np * np], T, nqm)) {
-            set_error("asm_setup: element mass matrix not positive definite");
-            return POLYDG_ENOTSPD;
-        }
+    });
+    if (bad) {
+        set_error("asm_setup: element mass matrix not positive definite");
+        return POLYDG_ENOTSPD;
     }
     // K_0 = sum over blocks (e, f): T_e^T K_ef T_f into (J(e), J(f))
     const int64_t n0 = (int64_t)C.n_agg * nqm;

@@ -15,6 +15,7 @@ void set_error(const std::string& msg);
 // Everything computed on the host once per mesh (Sec. 3 assembly), in the
 // library's internal cell order (cells sorted by subdomain, stable).
 struct HostSetup {
+    int dim = 2;                       // 2: polygons, 3: polyhedra of triangle facets
     int p = 0, n_p = 0;
     int64_t nc = 0;
     double chi_cm = 1.0, dt = 0.0, eta0 = 0.0;
@@ -25,11 +26,13 @@ struct HostSetup {
     int n_sub = 0;
     std::vector<int64_t> sub_ptr;      // [n_sub+1] internal cell ranges
     // geometry, caller order
-    std::vector<double> bbox;          // [nc*4] x0 x1 y0 y1
-    std::vector<double> diam, area;
-    std::vector<double> sigma;         // [nc*4]
-    // mesh copy (caller numbering), for agglomerate boxes and quadrature
-    std::vector<double> verts;
+    std::vector<double> bbox;          // [nc*2*dim] x0 x1 y0 y1 (z0 z1)
+    std::vector<double> diam, area;    // area: the cell's area (2D) or volume (3D)
+    std::vector<double> sigma;         // [nc*dim*dim]
+    // mesh copy (caller numbering), for agglomerate boxes and quadrature.  2D:
+    // cell_vtx[cell_ptr[c]..] is the CCW vertex loop; 3D: it lists the cell's
+    // outward triangle facets, three vertex ids each.
+    std::vector<double> verts;         // [n_vertices*dim]
     std::vector<int64_t> cell_ptr;
     std::vector<int32_t> cell_vtx;
     // interior faces, caller ids, K+ < K-, sorted
@@ -42,26 +45,33 @@ struct HostSetup {
     // element quadrature nodes, internal cell order
     std::vector<int64_t> node_ptr;          // [nc+1]
     std::vector<double> node_w;             // [nn]
-    std::vector<double> node_xy;            // [nn*2]
+    std::vector<double> node_x;             // [nn*dim]
     std::vector<double> node_phi;           // [nn*n_p]
     std::vector<int64_t> node_to_caller_pos;// [nn] position of internal node in caller node order
 };
 
 int host_setup(const polydg_mesh* mesh, int p, const int32_t* sub, double chi_cm,
                double dt, double eta0, HostSetup& out);
+int host_setup3d(const polydg_mesh3d* mesh, int p, const int32_t* sub, double chi_cm,
+                 double dt, double eta0, HostSetup& out);
 
 // Gauss-Legendre nodes/weights on [0,1], ascending.
 void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
-// Modal basis values (and gradients if grad != nullptr) at (x, y) for a box.
-int n_modes(int p);
-void eval_basis(int p, const double* box, double x, double y, double* val, double* grad);
-// Element rule (vertex-0 fan, collapsed Gauss rule with n = p+1 points per direction).
+// Modal basis values (and gradients [n_p][dim] if grad != nullptr) at x[dim] for a box.
+int n_modes(int p, int dim);
+void eval_basis(int dim, int p, const double* box, const double* x, double* val, double* grad);
+// Element rule: 2D vertex-0 fan, 3D cone from the vertex average over the facets;
+// collapsed Gauss rules with n = npts points per direction (npts + 1 along the
+// collapsed direction of a tetrahedron).  xs receives dim coordinates per point.
 void element_rule(const HostSetup& S, int64_t caller_cell, int npts,
-                  std::vector<double>& xy, std::vector<double>& w);
+                  std::vector<double>& xs, std::vector<double>& w);
 
 // Symmetric eigendecomposition (host): a (n x n, row-major) is destroyed; w ascending,
 // qt[k * n + i] = component i of eigenvector k.  False if the iteration did not converge.
 bool sym_eig(int n, double* a, double* w, double* qt);
+// Inverse of a dense SPD matrix (n x n row-major) on the host threads; false if a
+// Cholesky pivot is not positive.
+bool spd_inverse(int64_t n, const double* A, double* Ainv);
 
 // Coarse-space data (Sec. 4) computed on the host for asm_setup.
 struct CoarseSetup {

@@ -149,9 +149,13 @@ int shared_local_setup(polydg_ctx* c, int precision, shared_local** out) {
     const HostSetup& H = c->H;
     const int np = H.n_p;
     const double s0 = H.sigma[0];
+    const int d = H.dim;
     for (int64_t k = 0; k < H.nc; ++k) {
-        const double* S = &H.sigma[4 * k];
-        if (S[1] != 0.0 || S[2] != 0.0 || S[0] != S[3] || S[0] != s0) {
+        const double* S = &H.sigma[(size_t)d * d * k];
+        bool scalar = true;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) scalar = scalar && S[i * d + j] == (i == j ? s0 : 0.0);
+        if (!scalar) {
             set_error("shared_local_setup: the conductivity must be the same scalar multiple of I on every cell");
             return POLYDG_EINVAL;
         }
