@@ -10,9 +10,10 @@ polynomials of total degree 2n-2 exactly; n = p + 1 makes the mass, stiffness
 and coarse-transfer integrands exact.
 
 In 3D a tetrahedron ABCD takes x(s,t,u) = A + s(B-A) + s t(C-B) + s t u(D-C)
-with Jacobian 6|T| s^2 t; a monomial of degree d becomes a polynomial of degree
-d+2 in s, d+1 in t and d in u, so n+1 Gauss points in s and n in t and u
-integrate total degree 2n-2 exactly (n = p + 1: degree 2p).  A polyhedron given
+with Jacobian 6|T| s^2 t; a monomial of degree d becomes a polynomial of degree at
+most d in each of s, t and u, and the Jacobian's s^2 t is taken as the weight of
+Gauss-Jacobi rules in s (weight s^2) and t (weight t), with Gauss-Legendre in u:
+n points per direction integrate total degree 2n-1 exactly (n = p + 1: 2p + 1).  A polyhedron given
 by outward triangle facets is the cone of tetrahedra (apex, a, b, c) from the
 average of its vertices (the jittered hexahedra are star-shaped about it); a
 triangle facet in space takes the 2D collapsed rule with Jacobian |(B-A) x (C-A)| s.
@@ -77,19 +78,28 @@ def triangle_rule_3d(A, B, C, n: int):
     return np.asarray(pts), np.asarray(wts)
 
 
+def gauss_jacobi_01(n: int, power: int):
+    """n-point Gauss rule on [0, 1] for the weight s**power (library routine)."""
+    from scipy.special import roots_jacobi
+    x, w = roots_jacobi(n, 0.0, float(power))       # weight (1 + x)^power on [-1, 1]
+    return 0.5 * (x + 1.0), w / 2.0 ** (power + 1)
+
+
 def tet_rule(A, B, C, D, n: int):
-    """Collapsed rule on tetrahedron ABCD: n+1 points in s, n in t and u."""
-    s, ws = gauss_legendre_01(n + 1)
-    t, wt = gauss_legendre_01(n)
+    """Collapsed rule on tetrahedron ABCD: n Gauss-Jacobi points in s (weight s^2) and
+    t (weight t), n Gauss-Legendre points in u."""
+    s, ws = gauss_jacobi_01(n, 2)
+    t, wt = gauss_jacobi_01(n, 1)
+    u, wu = gauss_legendre_01(n)
     A, B, C, D = (np.asarray(v, float) for v in (A, B, C, D))
     six_vol = abs(np.linalg.det(np.stack([B - A, C - A, D - A])))
     pts, wts = [], []
-    for i in range(n + 1):
+    for i in range(n):
         for j in range(n):
             for k in range(n):
                 pts.append(A + s[i] * (B - A) + s[i] * t[j] * (C - B)
-                           + s[i] * t[j] * t[k] * (D - C))
-                wts.append(ws[i] * wt[j] * wt[k] * s[i] ** 2 * t[j] * six_vol)
+                           + s[i] * t[j] * u[k] * (D - C))
+                wts.append(ws[i] * wt[j] * wu[k] * six_vol)
     return np.asarray(pts), np.asarray(wts)
 
 

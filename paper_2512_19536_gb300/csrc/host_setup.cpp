@@ -56,6 +56,32 @@ void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
     }
 }
 
+// Gauss-Jacobi on [0, 1] for the weight s^power (power >= 1), by Golub-Welsch: the
+// nodes are the eigenvalues of the Jacobi matrix of the monic polynomials orthogonal
+// for (1 + x)^power on [-1, 1] (recurrence a_k = b^2 / ((2k+b)(2k+b+2)),
+// beta_k = 4k^2(k+b)^2 / ((2k+b)^2 (2k+b+1)(2k+b-1)), b = power), the weights mu_0 times
+// the squared first eigenvector components, mu_0 = 2^(b+1)/(b+1); then s = (1 + x)/2.
+static void gauss_jacobi01(int n, int power, std::vector<double>& x, std::vector<double>& w) {
+    const double b = power;
+    std::vector<double> J((size_t)n * n, 0.0), ev(n), vec((size_t)n * n);
+    for (int k = 0; k < n; ++k) {
+        J[(size_t)k * n + k] = b * b / ((2 * k + b) * (2 * k + b + 2));
+        if (k >= 1) {
+            const double t = 2 * k + b;
+            const double off = std::sqrt(4.0 * k * k * (k + b) * (k + b) / (t * t * (t + 1) * (t - 1)));
+            J[(size_t)k * n + k - 1] = J[(size_t)(k - 1) * n + k] = off;
+        }
+    }
+    sym_eig(n, J.data(), ev.data(), vec.data());
+    const double mu0 = std::pow(2.0, b + 1) / (b + 1);
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        x[i] = 0.5 * (ev[i] + 1.0);
+        w[i] = mu0 * vec[(size_t)i * n] * vec[(size_t)i * n] / std::pow(2.0, b + 1);
+    }
+}
+
 int n_modes(int p, int dim) {
     return dim == 3 ? (p + 1) * (p + 2) * (p + 3) / 6 : (p + 1) * (p + 2) / 2;
 }
@@ -121,8 +147,9 @@ static void cell_apex3d(const HostSetup& S, int64_t c, double* apex) {
 // 2D: fan of triangles (v0, v_k, v_{k+1}); on each the collapsed rule
 // x(s,t) = A + s (B - A) + s t (C - B), weight w_s w_t s |(B-A) x (C-A)|.
 // 3D: cone of tetrahedra (apex, a, b, c) over the outward facets; on each
-// x(s,t,u) = A + s (B-A) + s t (C-B) + s t u (D-C), weight w_s w_t w_u s^2 t 6|T|,
-// with npts + 1 points in s and npts in t and u (exact to degree 2 npts - 2).
+// x(s,t,u) = A + s (B-A) + s t (C-B) + s t u (D-C) with Jacobian 6|T| s^2 t, taken as
+// the weights of npts-point Gauss-Jacobi rules in s (s^2) and t (t), Gauss-Legendre in
+// u: exact to total degree 2 npts - 1.
 void element_rule(const HostSetup& S, int64_t c, int npts, std::vector<double>& xs,
                   std::vector<double>& w) {
     std::vector<double> g, gw;
@@ -147,8 +174,9 @@ void element_rule(const HostSetup& S, int64_t c, int npts, std::vector<double>& 
         }
         return;
     }
-    std::vector<double> gs, gsw;
-    gauss_legendre01(npts + 1, gs, gsw);
+    std::vector<double> gs, gsw, gt, gtw;
+    gauss_jacobi01(npts, 2, gs, gsw);
+    gauss_jacobi01(npts, 1, gt, gtw);
     double A[3];
     cell_apex3d(S, c, A);
     for (int64_t k = S.cell_ptr[c]; k < S.cell_ptr[c + 1]; k += 3) {
@@ -160,20 +188,20 @@ void element_rule(const HostSetup& S, int64_t c, int npts, std::vector<double>& 
         const double six_vol = std::fabs(e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) -
                                          e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
                                          e1[2] * (e2[0] * e3[1] - e2[1] * e3[0]));
-        for (int i = 0; i <= npts; ++i)
+        for (int i = 0; i < npts; ++i)
             for (int j = 0; j < npts; ++j)
                 for (int l = 0; l < npts; ++l) {
-                    const double s = gs[i], t = g[j], u = g[l];
+                    const double s = gs[i], t = gt[j], u = g[l];
                     for (int d = 0; d < 3; ++d)
                         xs.push_back(A[d] + s * (B[d] - A[d]) + s * t * (C[d] - B[d]) + s * t * u * (D[d] - C[d]));
-                    w.push_back(gsw[i] * gw[j] * gw[l] * s * s * t * six_vol);
+                    w.push_back(gsw[i] * gtw[j] * gw[l] * six_vol);
                 }
     }
 }
 
 static int64_t element_rule_size(const HostSetup& S, int64_t c, int npts) {
     const int64_t m = S.cell_ptr[c + 1] - S.cell_ptr[c];
-    return S.dim == 2 ? (m - 2) * npts * npts : (m / 3) * (npts + 1) * npts * npts;
+    return S.dim == 2 ? (m - 2) * npts * npts : (m / 3) * npts * npts * npts;
 }
 
 // ---------------------------------------------------------------- geometry

@@ -11,24 +11,32 @@ namespace polydg {
 // Warp per cell: nodes of cell e are node_ptr[e]..node_ptr[e+1]-1.  Per node:
 //   u^k(x_q), y^{k+1} = y^k + dt y'(u^k, y^k),  u~ = 3/2 U^k - 1/2 U^{k-1} (U^0 at k = 0),
 //   I_e[i] = sum_q w_q f(u~(x_q), y^{k+1}_q) phi_i(x_q).
+// The cell's coefficient vectors sit in shared memory (broadcast reads), so a thread
+// keeps only its node's basis values and the NP partial sums in registers: two
+// 256-thread blocks fit on an SM, which the fp64-latency-bound node update needs.
+constexpr int kIonicThreads = 256;
+
 template <int NP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kIonicThreads, 2)
 ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
              const int64_t* __restrict__ node_ptr, const double* __restrict__ node_w,
              const double* __restrict__ node_phi, double* __restrict__ y, int64_t nn, int64_t nc,
-             double dt, double* __restrict__ I, const SimScalars* ss) {
+             double dt, double* __restrict__ I, const SimScalars* ss, const bc::NodeConsts kc) {
+    __shared__ double su[kIonicThreads / 32][2][NP];
     if (ss->failed) return;
     const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     if (e >= nc) return;
     const bool first = (ss->k == 0);
-    double Ue[NP], Ux[NP], acc[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        Ue[j] = U[e * NP + j];
-        Ux[j] = first ? Ue[j] : 1.5 * Ue[j] - 0.5 * Uprev[e * NP + j];
-        acc[j] = 0.0;
+    if (lane < NP) {
+        const double ue = U[e * NP + lane];
+        su[wl][0][lane] = ue;
+        su[wl][1][lane] = first ? ue : 1.5 * ue - 0.5 * Uprev[e * NP + lane];
     }
+    __syncwarp();
+    double acc[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) acc[j] = 0.0;
     const int64_t q1 = node_ptr[e + 1];
     for (int64_t q = node_ptr[e] + lane; q < q1; q += 32) {
         const double* ph = node_phi + q * NP;
@@ -36,15 +44,14 @@ ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
         double uk = 0.0, ux = 0.0;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            phv[j] = ph[j];
-            uk = fma(phv[j], Ue[j], uk);
-            ux = fma(phv[j], Ux[j], ux);
+            phv[j] = __ldg(ph + j);
+            uk = fma(phv[j], su[wl][0][j], uk);
+            ux = fma(phv[j], su[wl][1][j], ux);
         }
         double n = y[q], h = y[nn + q], Ko = y[2 * nn + q], Nai = y[3 * nn + q], Cai = y[4 * nn + q];
-        bc::euler(uk, dt, n, h, Ko, Nai, Cai);    // explicit Euler with u^k
+        bc::euler(kc, uk, dt, n, h, Ko, Nai, Cai);    // explicit Euler with u^k
         y[q] = n; y[nn + q] = h; y[2 * nn + q] = Ko; y[3 * nn + q] = Nai; y[4 * nn + q] = Cai;
-        const bc::Currents c = bc::currents(ux, n, h, Ko, Nai, Cai);
-        const double wf = node_w[q] * (c.INa + c.IK + c.ICl);
+        const double wf = node_w[q] * bc::total_current(kc, ux, n, h, Ko, Nai, Cai);
 #pragma unroll
         for (int j = 0; j < NP; ++j) acc[j] = fma(wf, phv[j], acc[j]);
     }
@@ -58,12 +65,13 @@ ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
 cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int64_t* node_ptr,
                          const double* node_w, const double* node_phi, double* y, int64_t nn,
                          int64_t nc, double dt, double* I, const SimScalars* ss, cudaStream_t s) {
-    const unsigned g = (unsigned)((nc * 32 + 255) / 256);
+    const unsigned g = (unsigned)((nc * 32 + kIonicThreads - 1) / kIonicThreads);
+    static const bc::NodeConsts kc = bc::node_consts();
     switch (np) {
-        case 3: ionic_kernel<3><<<g, 256, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss); break;
-        case 6: ionic_kernel<6><<<g, 256, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss); break;
-        case 10: ionic_kernel<10><<<g, 256, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss); break;
-        case 15: ionic_kernel<15><<<g, 256, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss); break;
+        case 3: ionic_kernel<3><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss, kc); break;
+        case 6: ionic_kernel<6><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss, kc); break;
+        case 10: ionic_kernel<10><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss, kc); break;
+        case 15: ionic_kernel<15><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss, kc); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

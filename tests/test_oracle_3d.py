@@ -49,17 +49,28 @@ def test_triangle_rule_in_space_barycentric_moments():
         assert np.isclose(got, want, rtol=1e-13), (a, b, c)
 
 
-def test_tet_rule_barycentric_moments_to_degree_2n_minus_2():
+def test_gauss_jacobi_weights_and_exactness():
+    # sum w = 1/(power+1); the rule integrates s^k s^power exactly for k <= 2n - 1
+    for power in (1, 2):
+        for n in (1, 2, 3, 4):
+            s, w = quadrature.gauss_jacobi_01(n, power)
+            for k in range(2 * n):
+                assert np.isclose(np.sum(w * s ** k), 1.0 / (k + power + 1), rtol=1e-13), (power, n, k)
+            assert not np.isclose(np.sum(w * s ** (2 * n)), 1.0 / (2 * n + power + 1), rtol=1e-9)
+
+
+def test_tet_rule_barycentric_moments_to_degree_2n_minus_1():
     # int_T l1^a l2^b l3^c l4^d dV = 6|T| a! b! c! d! / (a + b + c + d + 3)!
     rng = np.random.default_rng(1)
     P = rng.standard_normal((4, 3))
     vol = abs(np.linalg.det(P[1:] - P[0])) / 6.0
     for n in (2, 3):
         x, w = quadrature.tet_rule(*P, n)
+        assert len(w) == n ** 3
         Lb = np.linalg.solve(np.vstack([P.T, np.ones(4)]), np.vstack([x.T, np.ones(len(x))]))
         for e in [(0, 0, 0, 0), (1, 0, 0, 0), (0, 0, 0, 2), (1, 1, 0, 0), (0, 1, 1, 1),
-                  (2 * n - 2, 0, 0, 0), (0, 0, 0, 2 * n - 2), (0, n - 1, 0, n - 1)]:
-            if sum(e) > 2 * n - 2:
+                  (2 * n - 1, 0, 0, 0), (0, 0, 0, 2 * n - 1), (0, n - 1, 0, n), (1, 1, 1, 2 * n - 4)]:
+            if sum(e) > 2 * n - 1 or min(e) < 0:
                 continue
             got = np.sum(w * np.prod([Lb[i] ** e[i] for i in range(4)], axis=0))
             want = 6 * vol * np.prod([math.factorial(k) for k in e]) / math.factorial(sum(e) + 3)
