@@ -161,15 +161,18 @@ def load_guess(pd):
     return pd.guess_create(int(z["n_p"]), z["params"], z["scales"])
 
 
+GUESS_POLICY = 3   # Galerkin projection onto the learned proposal and the last 8 solution increments
+
+
 def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clocks=None,
-              guess=None, pc=None):
+              guess=None, pc=None, policy=None):
     if pc is None:
         pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision=precision)
         pd.asm_autotune(pc, rounds=6, iterations=60)   # setup: re-cut the rows by measured CTA times
     sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-8, maxit=5000,
                         flexible=flexible)
-    if guess is not None:
-        pd.sim_set_guess(sim, guess, 0)
+    if policy is not None:
+        pd.sim_set_guess(sim, guess, policy)
     pd.monodomain_step(sim, warmup, stream)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -188,36 +191,45 @@ def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clo
     return pc, sim, st, ms
 
 
-def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None):
-    """Same metric with the potential crossing the host boundary every step: U^k and
-    U^{k-1} copied in from pinned host memory, U^{k+1} copied back to pinned host."""
+def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None, warm=12):
+    """Same metric with the state crossing the host boundary every step: the last
+    solutions the step depends on (U^k .. U^{k-8}: the initial guess reads them) copied in
+    from pinned host memory and restored with sim_set_history, U^{k+1} copied back to
+    pinned host memory.  The same steps as the device-timed forms: `warm` untimed, then
+    `steps` timed."""
     sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-8, maxit=5000,
                         flexible=True)
-    if guess is not None:
-        pd.sim_set_guess(sim, guess, 0)
+    pd.sim_set_guess(sim, guess, GUESS_POLICY)
     n = ctx.n_dofs
-    host_u = torch.empty(n, dtype=torch.float64).pin_memory()
-    host_uprev = torch.empty(n, dtype=torch.float64).pin_memory()
+    H = 9
+    host_hist = torch.empty((H, n), dtype=torch.float64).pin_memory()   # row 0 = U^k
+    dev_hist = torch.empty((H, n), dtype=torch.float64, device="cuda")
     dev_u = torch.empty(n, dtype=torch.float64, device="cuda")
-    dev_uprev = torch.empty(n, dtype=torch.float64, device="cuda")
-    pd.monodomain_step(sim, 2, stream)
-    pd.sim_get_state(sim, dev_u, stream=stream)
-    host_u.copy_(dev_u)
-    host_uprev.copy_(dev_u)
+    host_new = torch.empty(n, dtype=torch.float64).pin_memory()
+    sols = []
+    for _ in range(warm):
+        pd.monodomain_step(sim, 1, stream)
+        pd.sim_get_state(sim, dev_u, stream=stream)
+        sols.append(dev_u.cpu())
+    host_hist.zero_()
+    for h in range(min(H, len(sols))):
+        host_hist[h].copy_(sols[-1 - h])
+    count = min(H, len(sols))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        dev_u.copy_(host_u, non_blocking=True)
-        dev_uprev.copy_(host_uprev, non_blocking=True)
-        pd.sim_set_potential(sim, dev_u, dev_uprev, stream)
+        dev_hist.copy_(host_hist, non_blocking=True)
+        pd.sim_set_history(sim, dev_hist[:count], stream)
+        count = min(H, count + 1)
         pd.monodomain_step(sim, 1, stream)
-        host_uprev.copy_(host_u)
         pd.sim_get_state(sim, dev_u, stream=stream)
-        host_u.copy_(dev_u, non_blocking=True)
+        host_new.copy_(dev_u, non_blocking=True)
         torch.cuda.synchronize()
+        host_hist[1:].copy_(host_hist[:-1].clone())
+        host_hist[0].copy_(host_new)
     dt = time.perf_counter() - t0
     sim.close()
-    return steps / dt, 2 * 8 * n, 8 * n
+    return steps / dt, H * 8 * n, 8 * n
 
 
 def cpu_baseline(w, its_per_step, sample_its=40):
@@ -322,14 +334,23 @@ def main():
     guess = load_guess(pd)
     clocks = ClockSampler(local)
     pc, sim, st, ms = time_form(pd, torch, w, ctx, "fp32", True, args.steps, args.warmup,
-                                stream, clocks, guess=guess)
-    # the same without the learned guess (x0 = U^k)
+                                stream, clocks, guess=guess, policy=GUESS_POLICY)
+    # the same without any initial guess (x0 = U^k)
     _, _, st_ng, ms_ng = time_form(pd, torch, w, ctx, "fp32", True, args.steps, args.warmup,
                                    stream, pc=pc)
+    # ablations: the increments alone (no network), and the network's proposal alone
+    # (kept only when its residual is below U^k's)
+    _, _, st_h, ms_h = time_form(pd, torch, w, ctx, "fp32", True, args.steps, args.warmup,
+                                 stream, pc=pc, policy=GUESS_POLICY)
+    if guess is not None:
+        _, _, st_p, ms_p = time_form(pd, torch, w, ctx, "fp32", True, args.steps, args.warmup,
+                                     stream, pc=pc, guess=guess, policy=0)
+    else:
+        st_p, ms_p = st_ng, ms_ng
     # fp64 plain form on the same workload, for the comparison the metric names
     pc64, sim64, st64, ms64 = time_form(pd, torch, w, ctx, "fp64", False, args.steps,
                                         args.warmup, stream)
-    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, max(5, args.steps // 8), stream, guess)
+    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, args.steps, stream, guess, warm=args.warmup)
     (ms, ms64, ms_ng), (e2e_rank,) = reduce_over_ranks(torch, [ms, ms64, ms_ng], [e2e_val], world, "cuda")
     value = world * args.steps / (ms * 1e-3)
     value64 = world * args.steps / (ms64 * 1e-3)
@@ -362,14 +383,21 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD,
-                   "form": ("mixed + learned: fp32 local inverses, flexible PCG, learned initial "
-                            "guess kept when its residual is smaller than U^k's")
+                   "form": ("mixed + learned: fp32 local inverses, flexible PCG; initial guess = "
+                            "Galerkin projection onto the network's proposal and the last 8 "
+                            "solution increments (U^k when that does not lower the error)")
                    if guess is not None else
-                   "mixed: fp32 local inverses, flexible PCG (guess weights file missing; x0 = U^k)",
+                   "mixed: fp32 local inverses, flexible PCG, initial guess from the last 8 "
+                   "solution increments (guess weights file missing)",
                    "rtol": 1e-8, "iterations_per_step": st["total_iterations"] / args.steps,
-                   "learned_guess_taken_steps": st.get("guesses_taken", 0),
+                   "guess_taken_steps": st.get("guesses_taken", 0),
                    "mixed_without_guess_steps_per_s": value_ng,
                    "mixed_without_guess_iterations_per_step": st_ng["total_iterations"] / args.steps,
+                   "ablation_increments_only_steps_per_s": world * args.steps / (ms_h * 1e-3),
+                   "ablation_increments_only_iterations_per_step": st_h["total_iterations"] / args.steps,
+                   "ablation_proposal_only_steps_per_s": world * args.steps / (ms_p * 1e-3),
+                   "ablation_proposal_only_iterations_per_step": st_p["total_iterations"] / args.steps,
+                   "ablation_proposal_only_taken_steps": st_p.get("guesses_taken", 0),
                    "fp64_plain_steps_per_s": value64,
                    "fp64_plain_iterations_per_step": st64["total_iterations"] / args.steps,
                    "mixed_over_fp64": value / value64,
@@ -378,7 +406,7 @@ def main():
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_val, "unit": "time-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": (9 if guess is not None else 7) * args.steps,
+        "gpu_launches": (10 if guess is not None else 9) * args.steps,
         "roofline": roofline,
         "cpu_baseline": cpu,
     }
@@ -401,11 +429,11 @@ def bench_hex(args, pd, torch, stream, rank, world, local):
     guess = load_guess(pd)
     clocks = ClockSampler(local)
     pc, _, st, ms = time_form(pd, torch, w, ctx, "fp32", True, steps, args.warmup, stream,
-                              clocks, guess=guess)
+                              clocks, guess=guess, policy=GUESS_POLICY)
     _, _, st_ng, ms_ng = time_form(pd, torch, w, ctx, "fp32", True, steps, args.warmup,
                                    stream, pc=pc)
     _, _, st64, ms64 = time_form(pd, torch, w, ctx, "fp64", False, steps, args.warmup, stream)
-    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, 5, stream, guess)
+    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, steps, stream, guess, warm=args.warmup)
     (ms, ms64, ms_ng), (e2e_rank,) = reduce_over_ranks(torch, [ms, ms64, ms_ng], [e2e_val], world, "cuda")
     value = world * steps / (ms * 1e-3)
     value64 = world * steps / (ms64 * 1e-3)
@@ -419,12 +447,13 @@ def bench_hex(args, pd, torch, stream, rank, world, local):
         "data": "synthetic",
         "config": {"workload": HEX_WORKLOAD.format(n=n, dofs=10 * n ** 3, subs=(n // 4) ** 3,
                                                    n0=4 * (n // 4) ** 3),
-                   "form": "mixed + learned: fp32 local inverses, flexible PCG, learned initial "
-                           "guess (trained on 2D Voronoi P3 trajectories) kept when its residual "
-                           "is smaller than U^k's",
+                   "form": "mixed + learned: fp32 local inverses, flexible PCG; initial guess = "
+                           "Galerkin projection onto the network's proposal (trained on 2D "
+                           "Voronoi P3 trajectories) and the last 8 solution increments",
                    "rtol": 1e-8, "iterations_per_step": st["total_iterations"] / steps,
-                   "learned_guess_taken_steps": st.get("guesses_taken", 0),
+                   "guess_taken_steps": st.get("guesses_taken", 0),
                    "mixed_without_guess_steps_per_s": world * steps / (ms_ng * 1e-3),
+                   "mixed_without_guess_iterations_per_step": st_ng["total_iterations"] / steps,
                    "fp64_plain_steps_per_s": value64,
                    "fp64_plain_iterations_per_step": st64["total_iterations"] / steps,
                    "mixed_over_fp64": value / value64,
@@ -434,7 +463,7 @@ def bench_hex(args, pd, torch, stream, rank, world, local):
         "clocks": clocks.summary(),
         "e2e": {"value": world * e2e_rank, "unit": "time-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": (9 if guess is not None else 7) * steps,
+        "gpu_launches": (10 if guess is not None else 9) * steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                      "kernel": "pcg_persistent_kernel<fp32 store, n_p=10> (distributed coarse rows)",

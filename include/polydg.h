@@ -275,9 +275,17 @@ int monodomain_step(sim_ctx *sim, int nsteps, void *stream, step_stats *stats);
 int sim_get_state(sim_ctx *sim, double *u_dev, double *y_dev, void *stream);
 
 /* Overwrite U^k and U^{k-1} (caller order device vectors; uprev_dev may be
- * NULL to use u_dev for both). */
+ * NULL to use u_dev for both).  The history kept for the subspace guess (policy 3 of
+ * sim_set_guess) restarts from these two. */
 int sim_set_potential(sim_ctx *sim, const double *u_dev, const double *uprev_dev,
                       void *stream);
+
+/* Overwrite the last `count` solutions: hist_dev is a caller-order device array
+ * [count][n_dofs] holding U^k, U^{k-1}, ..., U^{k-count+1}.  U^k, U^{k-1} and U^{k-2}
+ * become the simulation's potentials, and the first min(count, 9, k + 1) solutions the
+ * history of the subspace guess (a caller that keeps the state on the host restores
+ * all of it this way).  Enqueued on `stream`. */
+int sim_set_history(sim_ctx *sim, const double *hist_dev, int count, void *stream);
 
 /* Current step index k. */
 int64_t sim_step_index(const sim_ctx *sim);
@@ -360,7 +368,13 @@ int guess_train_step(guess_model *model, polydg_ctx *ctx, const double *traj_dev
  *   policy 0: only if |b - K x0|_2 < |b - K U^k|_2 (else from U^k);
  *   policy 1: always;
  *   policy 2: from U^k + theta (x0 - U^k) with theta minimising |b - K x|_2 on that line
- *             (from the same pass over K_h; the residual never exceeds U^k's).
+ *             (from the same pass over K_h; the residual never exceeds U^k's);
+ *   policy 3: from U^k + sum_d theta_d v_d over the directions v: x0 - U^k (when a
+ *             model is given, from k = 2 on) and the last min(8, k) solution increments
+ *             U^{k-j+1} - U^{k-j}, theta the Galerkin projection V^T K V theta = V^T (b -
+ *             K U^k) (the K-norm of the error is smallest; directions with negligible
+ *             Schur-complement pivots dropped).  Policy 3 works without a model (the
+ *             increments alone) and keeps the last 9 solutions on the device.
  * The FP64 stopping test decides convergence either way, so only iteration counts
  * change.  The model must outlive its use; it may be shared by several simulations. */
 int sim_set_guess(sim_ctx *sim, guess_model *model, int policy);

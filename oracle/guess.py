@@ -179,3 +179,23 @@ def safeguard(K, b, x_guess, Uk):
     rg = np.linalg.norm(b - K @ x_guess)
     r0 = np.linalg.norm(b - K @ Uk)
     return (x_guess, True) if rg < r0 else (Uk, False)
+
+
+def subspace_guess(K, b, history, xg=None, m=8):
+    """x0 = U^k + V theta over the directions v = xg - U^k (if a proposal is given) and the
+    last min(m, len(history) - 1) increments U^{k-j+1} - U^{k-j}; history = [U^k, U^{k-1},
+    ...].  theta is the Galerkin projection V^T K V theta = V^T (b - K U^k): the x0 of the
+    span with the smallest K-norm error (library least squares for the small system).
+    Returns (x0, theta)."""
+    Uk = history[0]
+    dirs = []
+    if xg is not None:
+        dirs.append(xg - Uk)
+    for j in range(1, min(m, len(history) - 1) + 1):
+        dirs.append(history[j - 1] - history[j])
+    if not dirs:
+        return Uk.copy(), np.zeros(0)
+    V = np.stack(dirs, 1)
+    H = V.T @ (K @ V)
+    theta, *_ = np.linalg.lstsq(0.5 * (H + H.T), V.T @ (b - K @ Uk), rcond=None)
+    return Uk + V @ theta, theta

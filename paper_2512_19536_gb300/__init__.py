@@ -8,7 +8,7 @@ if it has not been built.
 from ._native import (PolyDG, ASM, Simulation, PolyDGError, load, polydg_setup, polydg_setup3d,
                       setup_mesh, asm_setup,
                       asm_apply, asm_autotune, pcg_solve_trace, lanczos_extremes, pcg_solve, sim_create, monodomain_step, sim_get_state,
-                      sim_set_potential, spd_inverse_static, Batch, batch_create, batch_step,
+                      sim_set_potential, sim_set_history, spd_inverse_static, Batch, batch_create, batch_step,
                       GuessModel, guess_n_params, guess_create, guess_propose, guess_train_step,
                       sim_set_guess, SharedLocal, shared_local_setup, shared_local_apply,
                       sim_set_shared_local,
@@ -18,7 +18,7 @@ from ._native import (PolyDG, ASM, Simulation, PolyDGError, load, polydg_setup, 
 __all__ = ["PolyDG", "ASM", "Simulation", "PolyDGError", "load", "polydg_setup", "polydg_setup3d",
            "setup_mesh", "asm_setup",
            "asm_apply", "asm_autotune", "pcg_solve_trace", "lanczos_extremes", "pcg_solve", "sim_create", "monodomain_step", "sim_get_state",
-           "sim_set_potential", "spd_inverse_static", "Batch", "batch_create", "batch_step",
+           "sim_set_potential", "sim_set_history", "spd_inverse_static", "Batch", "batch_create", "batch_step",
            "GuessModel", "guess_n_params", "guess_create", "guess_propose", "guess_train_step",
            "sim_set_guess", "SharedLocal", "shared_local_setup", "shared_local_apply",
            "sim_set_shared_local",

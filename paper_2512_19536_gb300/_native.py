@@ -28,7 +28,8 @@ EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_setup3d", "polydg_get_in
            "guess_create", "guess_get_params", "guess_set_scales", "guess_propose",
            "guess_train_step", "sim_set_guess", "guess_destroy", "polydg_sym_eig",
            "shared_local_setup", "shared_local_info", "shared_local_apply", "shared_local_destroy",
-           "sim_set_shared_local", "asm_autotune", "pcg_solve_trace", "pcg_lanczos_extremes"]
+           "sim_set_shared_local", "asm_autotune", "pcg_solve_trace", "pcg_lanczos_extremes",
+           "sim_set_history"]
 
 
 class polydg_mesh(C.Structure):
@@ -105,6 +106,7 @@ def load() -> C.CDLL:
     L.monodomain_step.argtypes = [vp, i32, vp, C.POINTER(step_stats)]
     L.sim_get_state.argtypes = [vp, vp, vp, vp]
     L.sim_set_potential.argtypes = [vp, vp, vp, vp]
+    L.sim_set_history.argtypes = [vp, vp, i32, vp]
     L.polydg_spd_inverse_static.argtypes = [vp, i32, i32, i32, vp]
     L.polydg_spd_inverse_static.restype = i32
     L.sim_step_index.argtypes = [vp]
@@ -436,6 +438,13 @@ def sim_set_potential(sim: Simulation, u, uprev=None, stream=None):
                                     _stream(stream)))
 
 
+def sim_set_history(sim: Simulation, hist, stream=None):
+    """Restore the last solutions: hist is a CUDA float64 tensor [count, n_dofs] holding
+    U^k, U^{k-1}, ... (caller order)."""
+    count = int(hist.shape[0])
+    _check(load().sim_set_history(sim.h, _dev(hist), count, _stream(stream)))
+
+
 def spd_inverse_static(mats, n, ld, batch, stream=None):
     """In-place inversion of `batch` SPD float64 matrices (order n, leading dimension
     ld) held in the CUDA tensor `mats`, using only the library's fixed static
@@ -520,7 +529,9 @@ def guess_train_step(model: GuessModel, ctx: PolyDG, traj, samples, lr, stream=N
 
 def sim_set_guess(sim: Simulation, model, policy=0):
     """policy 0: start from the proposal only if its residual is smaller; 1: always;
-    2: from U^k + theta (proposal - U^k), theta minimising the residual on that line."""
+    2: from U^k + theta (proposal - U^k), theta minimising the residual on that line;
+    3: residual least squares over the proposal (if a model is given) and the last
+    eight solution increments (model may be None)."""
     _check(load().sim_set_guess(sim.h, model.h if model is not None else None, int(policy)))
     sim.guess = model
 

@@ -1016,7 +1016,8 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
     if ((st = sm->work.alloc(n)) || (st = dalloc(&sm->U, n)) || (st = dalloc(&sm->Uprev, n)) ||
         (st = dalloc(&sm->Uprev2, n)) || (st = dalloc(&sm->xg, n)) ||
         (st = dalloc(&sm->I, n)) || (st = dalloc(&sm->y, 5 * nn)) || (st = dalloc(&sm->d_y0, 5)) ||
-        (st = dalloc(&sm->d_ss, 1)))
+        (st = dalloc(&sm->d_ss, 1)) || (st = dalloc(&sm->ring, kHistRing * n)) ||
+        (st = dalloc(&sm->subW, (2 * kSubMaxDirs + 1) * n)) || (st = dalloc(&sm->gram, kSubMaxPairs * kSubMaxCtas)))
         return fail(st);
     if (cudaMallocHost((void**)&sm->h_ss, sizeof(SimScalars)) != cudaSuccess) {
         set_error("sim_create: pinned allocation failed");
@@ -1044,6 +1045,7 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
         return POLYDG_ECUDA;
     };
     SimScalars ss = {};
+    ss.hist_len = 1;                    // the ring holds U^0
     PcgScalars sc = {};
     sc.rtol2 = prm->rtol * prm->rtol;
     sc.maxit = prm->maxit;
@@ -1051,6 +1053,7 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
     if ((st = cu(cudaMemcpy(sm->U, U0.data(), n * sizeof(double), cudaMemcpyHostToDevice))) ||
         (st = cu(cudaMemcpy(sm->Uprev, U0.data(), n * sizeof(double), cudaMemcpyHostToDevice))) ||
         (st = cu(cudaMemcpy(sm->Uprev2, U0.data(), n * sizeof(double), cudaMemcpyHostToDevice))) ||
+        (st = cu(cudaMemcpy(sm->ring, U0.data(), n * sizeof(double), cudaMemcpyHostToDevice))) ||
         (st = cu(cudaMemcpy(sm->d_y0, y0, 5 * sizeof(double), cudaMemcpyHostToDevice))) ||
         (st = cu(launch_init_y(sm->y, nn, sm->d_y0, 0))) ||
         (st = cu(cudaMemcpy(sm->d_ss, &ss, sizeof(ss), cudaMemcpyHostToDevice))) ||
@@ -1093,7 +1096,17 @@ static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
                     H.nc, dt, sm->I, sm->d_ss, s));
     CU(launch_matvec(MODE_RHS, np, c->K, c->K.val_minus, sm->U, w.b, sm->I, sm->F, -H.chi_cm * dt,
                      dt, nullptr, nullptr, sm->d_ss, dt, sm->prm.stim_duration, nullptr, nullptr, s));
-    if (sm->guess) {            // from k = 2 on: learned proposal, kept if its residual is smaller
+    if (sm->guess_policy == 3) {  // subspace of the learned proposal and the last increments
+        const double* xg = nullptr;
+        if (sm->guess) {
+            const GuessFeat f = guess_features(c, sm->guess);
+            CU(launch_guess_propose(np, f, sm->guess->w16, sm->U, sm->Uprev, sm->Uprev2, sm->xg, H.nc,
+                                    sm->d_ss, s));
+            xg = sm->xg;
+        }
+        CU(launch_guess_subspace(np, c->K, w.b, sm->U, xg, sm->ring, sm->subW, sm->gram, n, sm->d_ss, s));
+        CU(launch_subspace_copy(sm->U, xg, sm->ring, w.x[0], n, sm->d_ss, s));
+    } else if (sm->guess) {     // from k = 2 on: learned proposal, kept if its residual is smaller
         const GuessFeat f = guess_features(c, sm->guess);
         CU(launch_guess_propose(np, f, sm->guess->w16, sm->U, sm->Uprev, sm->Uprev2, sm->xg, H.nc,
                                 sm->d_ss, s));
@@ -1108,7 +1121,7 @@ static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
 static int enqueue_step_post(sim_ctx* sm, cudaStream_t s) {
     const int64_t n = sm->ctx->H.nc * sm->ctx->H.n_p;
     PcgWork& w = sm->work;
-    CU(launch_step_finish(sm->U, sm->Uprev, sm->Uprev2, w.x[0], w.x[1], n, w.sc, sm->d_ss, s));
+    CU(launch_step_finish(sm->U, sm->Uprev, sm->Uprev2, w.x[0], w.x[1], n, w.sc, sm->d_ss, sm->ring, s));
     return POLYDG_OK;
 }
 
@@ -1382,6 +1395,15 @@ int sim_set_potential(sim_ctx* sm, const double* u_dev, const double* uprev_dev,
                       c->H.n_p, 1, nullptr, s));
     CU(cudaMemcpyAsync(sm->Uprev2, sm->Uprev, c->H.nc * c->H.n_p * sizeof(double),
                        cudaMemcpyDeviceToDevice, s));
+    CU(launch_history_reset(sm->ring, sm->U, sm->Uprev, c->H.nc * c->H.n_p, sm->d_ss, s));
+    return POLYDG_OK;
+}
+
+int sim_set_history(sim_ctx* sm, const double* hist_dev, int count, void* stream) {
+    if (!sm || !hist_dev || count < 1) { set_error("sim_set_history: need a simulation, a device array and count >= 1"); return POLYDG_EINVAL; }
+    polydg_ctx* c = sm->ctx;
+    CU(launch_history_set(hist_dev, count, sm->ring, sm->U, sm->Uprev, sm->Uprev2, c->d_to_caller,
+                          c->H.nc, c->H.n_p, sm->d_ss, (cudaStream_t)stream));
     return POLYDG_OK;
 }
 
@@ -1724,7 +1746,8 @@ int guess_train_step(guess_model* g, polydg_ctx* c, const double* traj_dev, int6
 int sim_set_guess(sim_ctx* sm, guess_model* g, int policy) {
     if (!sm) { set_error("sim_set_guess: null simulation"); return POLYDG_EINVAL; }
     if (g && g->np != sm->ctx->H.n_p) { set_error("sim_set_guess: model and mesh differ in n_p"); return POLYDG_EINVAL; }
-    if (policy < 0 || policy > 2) { set_error("sim_set_guess: policy must be 0, 1 or 2"); return POLYDG_EINVAL; }
+    if (policy < 0 || policy > 3) { set_error("sim_set_guess: policy must be 0, 1, 2 or 3"); return POLYDG_EINVAL; }
+    if (!g && policy != 0 && policy != 3) { set_error("sim_set_guess: policies 1 and 2 need a model"); return POLYDG_EINVAL; }
     if (sm->guess != g || sm->guess_policy != policy) {
         sm->guess = g;
         sm->guess_policy = policy;
@@ -1758,6 +1781,7 @@ void sim_destroy(sim_ctx* sm) {
     for (auto e : sm->ev) cudaEventDestroy(e);
     sm->work.release();
     dfree(sm->U); dfree(sm->Uprev); dfree(sm->Uprev2); dfree(sm->xg); dfree(sm->I); dfree(sm->F); dfree(sm->y); dfree(sm->d_y0);
+    dfree(sm->ring); dfree(sm->subW); dfree(sm->gram);
     dfree(sm->d_ss);
     if (sm->h_ss) cudaFreeHost(sm->h_ss);
     delete sm;

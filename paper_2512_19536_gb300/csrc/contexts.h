@@ -178,11 +178,14 @@ struct sim_ctx {
     sim_params prm{};
     PcgWork work;
     guess_model* guess = nullptr;       // learned initial guess (nullptr: x0 = U^k)
-    int guess_policy = 0;               // 0 keep the smaller residual, 1 always, 2 damped
+    int guess_policy = 0;               // 0 keep the smaller residual, 1 always, 2 damped, 3 subspace
     shared_local* shared = nullptr;     // local solves shared with other simulations (batches)
     double sigma = 0.0;                 // its scalar conductivity when `shared` is set
     int64_t version = 0;                // bumped when the step's kernel sequence changes
     double *Uprev2 = nullptr, *xg = nullptr;
+    double* ring = nullptr;             // [kHistRing][n] past solutions, slot k mod kHistRing = U^k
+    double* subW = nullptr;             // [2 kSubMaxDirs + 1][n] r0, K v_d and v_d of the subspace guess
+    double* gram = nullptr;             // [kSubMaxPairs][kSubMaxCtas] Gram partial sums
     double *U = nullptr, *Uprev = nullptr, *I = nullptr, *F = nullptr, *y = nullptr;
     double* d_y0 = nullptr;
     SimScalars* d_ss = nullptr;

@@ -12,6 +12,15 @@ namespace polydg {
 
 enum MatvecMode { MODE_PLAIN = 0, MODE_PCG = 1, MODE_RESID = 2, MODE_RHS = 3 };
 
+// Subspace initial guess (policy 3): the last kHistDirs solution increments, plus the
+// learned proposal, combined by residual least squares.  The solutions live in a ring
+// of kHistRing vectors indexed by step (slot k mod kHistRing holds U^k).
+constexpr int kHistDirs = 8;
+constexpr int kHistRing = kHistDirs + 1;
+constexpr int kSubMaxDirs = kHistDirs + 1;                       // + the learned proposal
+constexpr int kSubMaxPairs = kSubMaxDirs + kSubMaxDirs * (kSubMaxDirs + 1) / 2;
+constexpr int kSubMaxCtas = 1024;                                // Gram partial sums per pair
+
 // Per-simulation scalars resident in device memory.
 struct SimScalars {
     int64_t k;             // current step index (U holds U^k)
@@ -26,6 +35,9 @@ struct SimScalars {
     uint32_t guess_ticket; // last-CTA ticket of the guess selection
     uint32_t pad;
     double theta;          // x0 = U^k + theta (guess - U^k) when use_guess
+    int32_t hist_len;      // consecutive solutions U^k, U^{k-1}, ... held by the ring (>= 1)
+    int32_t sub_dirs;      // directions of this step's subspace guess
+    double theta_sub[kSubMaxDirs];   // their coefficients
 };
 
 // Block-sparse K_h on the device (internal cell order).
@@ -260,6 +272,22 @@ cudaError_t launch_guess_select(int np, const DeviceMatrix& K, const double* b, 
                                 cudaStream_t s);
 cudaError_t launch_select_copy(const double* uk, const double* xg, double* x0, int64_t n,
                                const SimScalars* ss, cudaStream_t s);
+// Subspace guess: r0 = b - K U^k, K v_d and v_d for the directions into W
+// ([2 kSubMaxDirs + 1][n]), the dot products V^T r0 and V^T K V (gram: kSubMaxPairs *
+// kSubMaxCtas partial sums), the Galerkin coefficients (last CTA), then x0.
+// xg == nullptr leaves the learned proposal out.
+cudaError_t launch_guess_subspace(int np, const DeviceMatrix& K, const double* b, const double* U,
+                                  const double* xg, const double* ring, double* W, double* gram,
+                                  int64_t n, SimScalars* ss, cudaStream_t s);
+cudaError_t launch_subspace_copy(const double* U, const double* xg, const double* ring, double* x0,
+                                 int64_t n, const SimScalars* ss, cudaStream_t s);
+// Ring maintenance: slot(k) <- U and slot(k-1) <- Uprev with hist_len reset (new potentials),
+// or `count` caller-order solutions [count][n] (U^k first) into the ring, U, Uprev, Uprev2.
+cudaError_t launch_history_reset(double* ring, const double* U, const double* Uprev, int64_t n,
+                                 SimScalars* ss, cudaStream_t s);
+cudaError_t launch_history_set(const double* hist, int count, double* ring, double* U, double* Uprev,
+                               double* Uprev2, const int64_t* to_caller, int64_t nc, int np,
+                               SimScalars* ss, cudaStream_t s);
 cudaError_t launch_guess_train(int np, const GuessFeat& f, const float* w32, const double* traj,
                                int64_t n_dofs, const int64_t* samples, int64_t n_samples,
                                const int64_t* to_internal, const int64_t* to_caller, float* part,
@@ -277,7 +305,7 @@ cudaError_t launch_node_gather(const double* y_int, double* y_caller,
                                const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s);
 cudaError_t launch_step_finish(double* U, double* Uprev, double* Uprev2, const double* x0,
                                const double* x1, int64_t n, const PcgScalars* sc, SimScalars* ss,
-                               cudaStream_t s);
+                               double* ring, cudaStream_t s);
 cudaError_t launch_step_begin(PcgScalars* sc, SimScalars* ss, cudaStream_t s);
 cudaError_t launch_init_y(double* y, int64_t nn, const double* y0, cudaStream_t s);
 

@@ -279,6 +279,269 @@ __global__ void select_copy_kernel(const double* __restrict__ uk, const double* 
     x0[t] = ss->use_guess ? fma(ss->theta, xg[t] - uk[t], uk[t]) : uk[t];
 }
 
+// ------------------------------------------------------------------ subspace guess
+// Policy 3: x0 = U^k + sum_d theta_d v_d over the directions v_0 = xg - U^k (the learned
+// proposal, from k = 2 on, when a model is attached) and v_j = U^{k-j+1} - U^{k-j} for the
+// last min(kHistDirs, hist_len - 1) solution increments, theta the Galerkin projection of
+// the correction onto their span (minimum of the K-norm of the error x* - x0, the norm
+// CG minimises): V^T K V theta = V^T r0 with r0 = b - K U^k.  The direction list depends
+// only on (k, hist_len, model attached): every kernel below rebuilds the same list.
+__device__ __forceinline__ int subspace_dirs(const SimScalars* ss, const double* U, const double* xg,
+                                             const double* ring, int64_t n, const double** a,
+                                             const double** b) {
+    const int64_t k = ss->k;
+    const int m = min(kHistDirs, ss->hist_len - 1);
+    int nd = 0;
+    if (xg != nullptr && k >= 2) { a[nd] = xg; b[nd] = U; ++nd; }
+    for (int j = 1; j <= m; ++j) {
+        a[nd] = (j == 1) ? U : ring + ((k - j + 1) % kHistRing) * n;
+        b[nd] = ring + ((k - j) % kHistRing) * n;
+        ++nd;
+    }
+    return nd;
+}
+
+// W[0] = r0 = b - K U^k, W[1 + d] = K v_d and W[1 + kSubMaxDirs + d] = v_d, warp per
+// element row block (K_h read once).
+template <int NP>
+__global__ void __launch_bounds__(kBlock)
+subspace_rows_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                     const double* __restrict__ val, const double* __restrict__ b,
+                     const double* __restrict__ U, const double* xg, const double* ring,
+                     double* __restrict__ W, int64_t n, int64_t nc, const SimScalars* ss) {
+    __shared__ const double* sa[kSubMaxDirs];
+    __shared__ const double* sb[kSubMaxDirs];
+    __shared__ int snd;
+    if (ss->failed) return;
+    if (threadIdx.x == 0) snd = subspace_dirs(ss, U, xg, ring, n, sa, sb);
+    __syncthreads();
+    const int nd = snd;
+    constexpr int G = 32 / NP;
+    const int lane = threadIdx.x & 31;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (nd == 0 || e >= nc) return;
+    const int g = lane / NP, i = lane - g * NP;
+    double a0 = 0.0, a[kSubMaxDirs];
+#pragma unroll
+    for (int d = 0; d < kSubMaxDirs; ++d) a[d] = 0.0;
+    const int32_t b0 = row_ptr[e];
+    const int ncol = (row_ptr[e + 1] - b0) * NP;
+    const double* V = val + (int64_t)b0 * NP * NP;
+    if (g < G)
+        for (int c = g; c < ncol; c += G) {
+            const int sblk = c / NP;
+            const int64_t xi = (int64_t)__ldg(col + b0 + sblk) * NP + (c - sblk * NP);
+            const double v = __ldg(V + (int64_t)c * NP + i);
+            a0 = fma(v, __ldg(U + xi), a0);
+#pragma unroll
+            for (int d = 0; d < kSubMaxDirs; ++d)
+                if (d < nd) a[d] = fma(v, __ldcg(sa[d] + xi) - __ldcg(sb[d] + xi), a[d]);
+        }
+    double t0 = a0, t[kSubMaxDirs];
+#pragma unroll
+    for (int d = 0; d < kSubMaxDirs; ++d) t[d] = a[d];
+#pragma unroll
+    for (int k = 1; k < G; ++k) {
+        t0 += __shfl_down_sync(0xffffffffu, a0, k * NP);
+#pragma unroll
+        for (int d = 0; d < kSubMaxDirs; ++d) t[d] += __shfl_down_sync(0xffffffffu, a[d], k * NP);
+    }
+    if (lane < NP) {
+        const int64_t r = e * NP + i;
+        W[r] = b[r] - t0;
+#pragma unroll
+        for (int d = 0; d < kSubMaxDirs; ++d)
+            if (d < nd) {
+                W[(1 + d) * n + r] = t[d];
+                W[(1 + kSubMaxDirs + d) * n + r] = __ldcg(sa[d] + r) - __ldcg(sb[d] + r);
+            }
+    }
+}
+
+// The dot products c_d = v_d . r0 and H_ij = v_i . K v_j (i <= j) over the columns of W,
+// per-CTA partial sums in fixed row order; the last CTA adds them in CTA order and thread
+// 0 solves for theta: Cholesky on the directions whose Schur-complement pivots stay above
+// 1e-13 of the largest diagonal (greedy, largest pivot first), the others left at zero.
+// The guess is used when it lowers the K-norm of the error (gain c.theta > 0).
+constexpr int kGramThreads = 256;
+
+__global__ void __launch_bounds__(kGramThreads)
+subspace_gram_kernel(const double* __restrict__ W, int64_t n, double* gram, SimScalars* ss,
+                     int with_model) {
+    __shared__ double tile[2 * kSubMaxDirs + 1][kGramThreads + 1];   // r0, K v_d, v_d
+    __shared__ double Gs[kSubMaxPairs];
+    __shared__ bool last;
+    if (ss->failed) return;
+    const int64_t k = ss->k;
+    const int nd = (with_model && k >= 2 ? 1 : 0) + min(kHistDirs, ss->hist_len - 1);
+    if (nd == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ss->use_guess = 0;
+        return;
+    }
+    const int npair = nd + nd * (nd + 1) / 2;
+    int pi = 0, pj = 0;                  // tile rows multiplied by thread p
+    if (threadIdx.x < npair) {
+        int p = threadIdx.x;
+        if (p < nd) {                    // c_p = v_p . r0
+            pi = 1 + nd + p;
+            pj = 0;
+        } else {                         // H_ij = v_i . K v_j, i <= j
+            p -= nd;
+            int i2 = 0;
+            while (p >= nd - i2) { p -= nd - i2; ++i2; }
+            pi = 1 + nd + i2;
+            pj = 1 + i2 + p;
+        }
+    }
+    double acc = 0.0;
+    for (int64_t r0 = (int64_t)blockIdx.x * kGramThreads; r0 < n; r0 += (int64_t)gridDim.x * kGramThreads) {
+        const int64_t r = r0 + threadIdx.x;
+        tile[0][threadIdx.x] = (r < n) ? __ldcg(W + r) : 0.0;
+        for (int d = 0; d < nd; ++d) {
+            tile[1 + d][threadIdx.x] = (r < n) ? __ldcg(W + (1 + d) * n + r) : 0.0;
+            tile[1 + nd + d][threadIdx.x] = (r < n) ? __ldcg(W + (1 + kSubMaxDirs + d) * n + r) : 0.0;
+        }
+        __syncthreads();
+        if (threadIdx.x < npair)
+            for (int q = 0; q < kGramThreads; ++q) acc = fma(tile[pi][q], tile[pj][q], acc);
+        __syncthreads();
+    }
+    if (threadIdx.x < npair) gram[threadIdx.x * kSubMaxCtas + blockIdx.x] = acc;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ss->guess_ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < npair) {           // eight independent chains, combined in a fixed order
+        double part[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        const double* src = gram + threadIdx.x * kSubMaxCtas;
+        unsigned c = 0;
+        for (; c + 8 <= gridDim.x; c += 8)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) part[q] += __ldcg(src + c + q);
+        for (; c < gridDim.x; ++c) part[0] += __ldcg(src + c);
+        Gs[threadIdx.x] = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    ss->guess_ticket = 0;
+    // H = V^T K V, c = V^T r0 from the packed sums
+    auto pair = [&](int i, int j) { return nd + i * nd - i * (i - 1) / 2 + (j - i); };   // i <= j
+    double H[kSubMaxDirs][kSubMaxDirs], c[kSubMaxDirs], A[kSubMaxDirs][kSubMaxDirs], th[kSubMaxDirs];
+    double dmax = 0.0;
+    for (int d = 0; d < nd; ++d) {
+        c[d] = Gs[d];
+        for (int e2 = d; e2 < nd; ++e2) H[d][e2] = H[e2][d] = Gs[pair(d, e2)];
+        dmax = fmax(dmax, H[d][d]);
+        th[d] = 0.0;
+    }
+    bool ok = isfinite(dmax) && dmax > 0.0;
+    for (int d = 0; d < nd; ++d) ok = ok && isfinite(c[d]);
+    int sel[kSubMaxDirs], ns = 0;
+    bool used[kSubMaxDirs];
+    for (int d = 0; d < nd; ++d) {
+        used[d] = false;
+        for (int e2 = 0; e2 < nd; ++e2) A[d][e2] = H[d][e2];
+    }
+    while (ok && ns < nd) {              // greedy pivot choice on the Schur complement
+        int q = -1;
+        double best = 1e-13 * dmax;
+        for (int d = 0; d < nd; ++d)
+            if (!used[d] && A[d][d] > best) { best = A[d][d]; q = d; }
+        if (q < 0) break;
+        used[q] = true;
+        sel[ns++] = q;
+        for (int i2 = 0; i2 < nd; ++i2)
+            for (int j2 = 0; j2 < nd; ++j2)
+                if (!used[i2] && !used[j2]) A[i2][j2] -= A[i2][q] * A[q][j2] / A[q][q];
+    }
+    double L[kSubMaxDirs][kSubMaxDirs], y[kSubMaxDirs];
+    for (int r = 0; ok && r < ns; ++r) {   // Cholesky of H restricted to the chosen directions
+        for (int c2 = 0; c2 <= r; ++c2) {
+            double v = H[sel[r]][sel[c2]];
+            for (int t2 = 0; t2 < c2; ++t2) v -= L[r][t2] * L[c2][t2];
+            if (c2 == r) {
+                if (!(v > 0.0)) { ok = false; break; }
+                L[r][r] = sqrt(v);
+            } else {
+                L[r][c2] = v / L[c2][c2];
+            }
+        }
+    }
+    double gain = 0.0;
+    if (ok && ns > 0) {
+        for (int r = 0; r < ns; ++r) {
+            double v = c[sel[r]];
+            for (int t2 = 0; t2 < r; ++t2) v -= L[r][t2] * y[t2];
+            y[r] = v / L[r][r];
+        }
+        for (int r = ns - 1; r >= 0; --r) {
+            double v = y[r];
+            for (int t2 = r + 1; t2 < ns; ++t2) v -= L[t2][r] * th[sel[t2]];
+            th[sel[r]] = v / L[r][r];
+        }
+        for (int d = 0; d < nd; ++d) gain += c[d] * th[d];
+    }
+    const bool use = ok && ns > 0 && isfinite(gain) && gain > 0.0;
+    for (int d = 0; d < kSubMaxDirs; ++d) ss->theta_sub[d] = (use && d < nd) ? th[d] : 0.0;
+    ss->sub_dirs = use ? nd : 0;
+    ss->use_guess = use ? 1 : 0;
+    ss->guesses_taken += use ? 1 : 0;
+}
+
+// x0 = U^k + sum_d theta_d v_d when the subspace guess is used, else U^k.
+__global__ void subspace_copy_kernel(const double* __restrict__ U, const double* xg,
+                                     const double* ring, double* __restrict__ x0, int64_t n,
+                                     const SimScalars* ss) {
+    __shared__ const double* sa[kSubMaxDirs];
+    __shared__ const double* sb[kSubMaxDirs];
+    __shared__ int snd;
+    if (ss->failed) return;
+    if (threadIdx.x == 0) snd = ss->use_guess ? subspace_dirs(ss, U, xg, ring, n, sa, sb) : 0;
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double x = U[t];
+    for (int d = 0; d < snd; ++d) x = fma(ss->theta_sub[d], __ldcg(sa[d] + t) - __ldcg(sb[d] + t), x);
+    x0[t] = x;
+}
+
+// New potentials from the caller: the ring restarts from U^k (and U^{k-1}).
+__global__ void history_reset_kernel(double* __restrict__ ring, const double* __restrict__ U,
+                                     const double* __restrict__ Uprev, int64_t n, SimScalars* ss) {
+    const int64_t k = ss->k;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        ring[(k % kHistRing) * n + t] = U[t];
+        if (k >= 1) ring[((k - 1) % kHistRing) * n + t] = Uprev[t];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ss->hist_len = k >= 1 ? 2 : 1;
+}
+
+// count caller-order solutions hist[h] = U^{k-h} into the ring (internal order), U, Uprev, Uprev2.
+__global__ void history_set_kernel(const double* __restrict__ hist, int count, double* __restrict__ ring,
+                                   double* __restrict__ U, double* __restrict__ Uprev, double* Uprev2,
+                                   const int64_t* __restrict__ to_caller, int64_t nc, int np,
+                                   SimScalars* ss) {
+    const int64_t k = ss->k;
+    const int cnt = (int)min((int64_t)min(count, kHistRing), k + 1);
+    const int64_t n = nc * np;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        const int64_t e = t / np, j = t - e * np;
+        const int64_t src = to_caller[e] * np + j;
+        for (int h = 0; h < cnt; ++h) {
+            const double v = hist[h * n + src];
+            ring[((k - h) % kHistRing) * n + t] = v;
+            if (h == 0) U[t] = v;
+            if (h == 1) Uprev[t] = v;
+            if (h == 2 && Uprev2) Uprev2[t] = v;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ss->hist_len = cnt;
+}
+
 // ------------------------------------------------------------------ training
 // One minibatch: forward, MSE loss and backward for tiles of kGT samples; CTA c adds
 // its tiles' gradients into part[c * P + .] (its first tile stores) and its loss sum
@@ -511,6 +774,39 @@ cudaError_t launch_guess_select(int np, const DeviceMatrix& K, const double* b, 
 cudaError_t launch_select_copy(const double* uk, const double* xg, double* x0, int64_t n,
                                const SimScalars* ss, cudaStream_t s) {
     select_copy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(uk, xg, x0, n, ss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guess_subspace(int np, const DeviceMatrix& K, const double* b, const double* U,
+                                  const double* xg, const double* ring, double* W, double* gram,
+                                  int64_t n, SimScalars* ss, cudaStream_t s) {
+    const unsigned grid = (unsigned)((K.nc * 32 + kBlock - 1) / kBlock);
+    GUESS_NP_SWITCH(np, {
+        subspace_rows_kernel<NP><<<grid, kBlock, 0, s>>>(K.row_ptr, K.col, K.val, b, U, xg, ring, W,
+                                                         n, K.nc, ss);
+    })
+    const unsigned g2 = (unsigned)std::min<int64_t>(kSubMaxCtas, (n + kGramThreads - 1) / kGramThreads);
+    subspace_gram_kernel<<<g2, kGramThreads, 0, s>>>(W, n, gram, ss, xg != nullptr ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_subspace_copy(const double* U, const double* xg, const double* ring, double* x0,
+                                 int64_t n, const SimScalars* ss, cudaStream_t s) {
+    subspace_copy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, xg, ring, x0, n, ss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_history_reset(double* ring, const double* U, const double* Uprev, int64_t n,
+                                 SimScalars* ss, cudaStream_t s) {
+    history_reset_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ring, U, Uprev, n, ss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_history_set(const double* hist, int count, double* ring, double* U, double* Uprev,
+                               double* Uprev2, const int64_t* to_caller, int64_t nc, int np,
+                               SimScalars* ss, cudaStream_t s) {
+    history_set_kernel<<<(unsigned)((nc * np + 255) / 256), 256, 0, s>>>(hist, count, ring, U, Uprev,
+                                                                       Uprev2, to_caller, nc, np, ss);
     return cudaGetLastError();
 }
 

@@ -120,12 +120,12 @@ cudaError_t launch_step_begin(PcgScalars* sc, SimScalars* ss, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// U^{k-2} <- U^{k-1} (if kept), U^{k-1} <- U^k, U^k <- x, k <- k + 1 and the step
-// statistics.
+// U^{k-2} <- U^{k-1} (if kept), U^{k-1} <- U^k, U^k <- x (also into the solution ring,
+// slot k+1), k <- k + 1 and the step statistics.
 __global__ void step_finish_kernel(double* __restrict__ U, double* __restrict__ Uprev,
                                    double* __restrict__ Uprev2, const double* __restrict__ x0,
                                    const double* __restrict__ x1, int64_t n, const PcgScalars* sc,
-                                   SimScalars* ss) {
+                                   SimScalars* ss, double* __restrict__ ring) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = !ss->failed;
     const double* x = (sc->pass & 1) ? x1 : x0;   // the iterate lives in buffer (pass & 1)
@@ -133,11 +133,13 @@ __global__ void step_finish_kernel(double* __restrict__ U, double* __restrict__ 
         if (Uprev2) Uprev2[t] = Uprev[t];
         Uprev[t] = U[t];
         U[t] = x[t];
+        if (ring) ring[((ss->k + 1) % kHistRing) * n + t] = x[t];
     }
 }
 
 __global__ void step_stats_kernel(const PcgScalars* sc, SimScalars* ss) {
     if (threadIdx.x != 0 || ss->failed) return;
+    if (ss->hist_len < kHistRing) ss->hist_len += 1;
     ss->k += 1;
     ss->steps_done += 1;
     ss->total_its += sc->it;
@@ -151,8 +153,9 @@ __global__ void step_stats_kernel(const PcgScalars* sc, SimScalars* ss) {
 
 cudaError_t launch_step_finish(double* U, double* Uprev, double* Uprev2, const double* x0,
                                const double* x1, int64_t n, const PcgScalars* sc, SimScalars* ss,
+                               double* ring,
                                cudaStream_t s) {
-    step_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, Uprev, Uprev2, x0, x1, n, sc, ss);
+    step_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, Uprev, Uprev2, x0, x1, n, sc, ss, ring);
     step_stats_kernel<<<1, 32, 0, s>>>(sc, ss);
     return cudaGetLastError();
 }

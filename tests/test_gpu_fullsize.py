@@ -85,8 +85,10 @@ def test_fullsize_solution_matches_direct_solve(big, prec, flexible):
     assert mnorm_rel(d, host(x), ref) <= 1e-8
 
 
-def test_fullsize_200_coupled_steps_mixed_form(big):
-    """The bench configuration (fp32 local inverses, flexible PCG, rtol 1e-8) for the
+@pytest.mark.parametrize("guess", [False, True])
+def test_fullsize_200_coupled_steps_mixed_form(big, guess):
+    """The bench configuration (fp32 local inverses, flexible PCG, rtol 1e-8; with the
+    learned + increments initial guess of the measured form, or from U^k) for the
     workload's 200 steps against the oracle's exactly solved trajectory."""
     from oracle import monodomain
     w, d, ctx = big
@@ -94,6 +96,10 @@ def test_fullsize_200_coupled_steps_mixed_form(big):
     pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision="fp32")
     sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-8, maxit=5000,
                         flexible=True)
+    if guess:
+        z = np.load(os.path.join(os.path.dirname(pd.LIB_PATH), "guess_p3_voronoi4096.npz"))
+        model = pd.guess_create(int(z["n_p"]), z["params"], z["scales"])
+        pd.sim_set_guess(sim, model, 3)
     steps = w.n_steps
     st = pd.monodomain_step(sim, steps)
     u = dev(np.zeros(d.n_dofs))

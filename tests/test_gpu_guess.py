@@ -217,3 +217,90 @@ def test_coupled_steps_with_trained_guess_match_oracle(vor):
     assert st["status"] == 0 and st["steps_done"] == 12
     assert 0 <= st["guesses_taken"] <= 10
     assert mnorm_rel(d, u, traj[12]) <= 1e-8
+
+
+# ------------------------------------------------------------ subspace guess (policy 3)
+def subspace_run(w, d, steps, model=None, rtol=1e-8, reset_history=False):
+    """Per-step iteration counts and the final potential of a policy-3 run; with
+    reset_history the simulation's own last solutions are restored through
+    sim_set_history before every step (a host-side state round trip)."""
+    import torch
+    pd = lib()
+    ctx = gpu_ctx(w)
+    pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision="fp64")
+    sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=rtol, maxit=5000)
+    pd.sim_set_guess(sim, model, 3)
+    its, hist = [], [dev(np.zeros(d.n_dofs))]
+    pd.sim_get_state(sim, hist[0])
+    for _ in range(steps):
+        if reset_history:
+            pd.sim_set_history(sim, torch.stack(hist[::-1][:9]))
+        st = pd.monodomain_step(sim, 1)
+        assert st["status"] == 0
+        its.append(st["total_iterations"])
+        u = dev(np.zeros(d.n_dofs))
+        pd.sim_get_state(sim, u)
+        hist.append(u)
+    return its, host(hist[-1])
+
+
+def test_subspace_guess_iterations_and_answer_match_oracle(vor):
+    """Policy 3 without a model against the oracle running the same recipe
+    (oracle.guess.subspace_guess + PCG with the same preconditioner): per-step
+    iteration counts within 3, totals within 5 %, far fewer than from U^k, and the
+    potential after the steps within the coupled-step bound of the direct solve."""
+    from oracle import guess as G, monodomain, schwarz
+    from oracle.pcg import pcg
+    w, d, _, _ = vor
+    steps = 40
+    its, u = subspace_run(w, d, steps)
+    S = cached(("schwarz", w.name), lambda: schwarz.build(d, w.subdomain, w.coarse, w.q))
+    md = monodomain.Monodomain(d, w.stimulus, u0=w.u_rest)
+    hist, ref_its, plain_its = [md.state.U.copy()], [], []
+    for _ in range(steps):
+        st = md.state
+        b, y_new = md.rhs(st)
+        x0, _ = G.subspace_guess(d.K, b, hist[::-1], m=8)
+        r = pcg(d.K, b, x0=x0, prec=S.apply, rtol=1e-8)
+        ref_its.append(r.iterations)
+        plain_its.append(pcg(d.K, b, x0=st.U, prec=S.apply, rtol=1e-8).iterations)
+        md.state = monodomain.State(r.x, st.U, y_new, st.k + 1)
+        hist.append(r.x.copy())
+    # the least squares are ill-conditioned (nearly parallel increments), so the two sides'
+    # roundings pick slightly different guesses: a few iterations apart per step
+    assert max(abs(a - b) for a, b in zip(its, ref_its)) <= 8, (list(its), list(ref_its))
+    assert abs(sum(its) - sum(ref_its)) <= 0.05 * sum(ref_its), (sum(its), sum(ref_its))
+    assert sum(its) < 0.8 * sum(plain_its), (sum(its), sum(plain_its))
+    direct = monodomain.Monodomain(d, w.stimulus, u0=w.u_rest)
+    for _ in range(steps):
+        ref = direct.step()
+    assert mnorm_rel(d, u, ref.U) <= 1e-6
+
+
+def test_subspace_guess_history_round_trip(vor):
+    """Restoring the simulation's own last solutions before every step changes nothing."""
+    w, d, _, _ = vor
+    its_a, u_a = subspace_run(w, d, 14)
+    its_b, u_b = subspace_run(w, d, 14, reset_history=True)
+    assert its_a == its_b
+    assert np.array_equal(u_a, u_b)
+
+
+def test_subspace_guess_with_zero_model_drops_its_direction(vor):
+    """A model whose output is zero gives K v_0 = 0: its direction is dropped by the
+    pivoting and the steps match the model-free run; at rtol 1e-12 the answer is the
+    oracle's."""
+    from oracle import guess as G, monodomain
+    w, d, _, _ = vor
+    pd = lib()
+    P = G.unflatten(init_params(d.n_p, 17), d.n_p, 128)
+    P["W3"][:] = 0.0
+    P["b3"][:] = 0.0
+    model = pd.guess_create(d.n_p, G.flatten(P), scales_for(d).as_array())
+    its_m, u_m = subspace_run(w, d, 10, model=model, rtol=1e-12)
+    its_0, u_0 = subspace_run(w, d, 10, rtol=1e-12)
+    assert its_m == its_0
+    direct = monodomain.Monodomain(d, w.stimulus, u0=w.u_rest)
+    for _ in range(10):
+        ref = direct.step()
+    assert mnorm_rel(d, u_m, ref.U) <= 1e-8

@@ -138,3 +138,49 @@ def test_safeguard_keeps_the_smaller_residual():
     Uk = rng.standard_normal(6)
     X = rng.standard_normal((3, G.n_inputs(n_p)))
     assert np.array_equal(G.propose(P, X, Uk, G.Scales(s_d=3.0)), Uk)
+
+
+# ------------------------------------------------------------ subspace initial guess
+def _spd(n, seed):
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((n, n))
+    return B @ B.T + n * np.eye(n)
+
+
+def test_subspace_guess_recovers_a_solution_in_the_span():
+    # x* = U^k + 0.7 (U^k - U^{k-1}) - 0.2 (U^{k-2} - U^{k-3}): the residual vanishes
+    from oracle.guess import subspace_guess
+    K = _spd(40, 1)
+    rng = np.random.default_rng(2)
+    H = [rng.standard_normal(40) for _ in range(5)]
+    xs = H[0] + 0.7 * (H[0] - H[1]) - 0.2 * (H[2] - H[3])
+    x0, th = subspace_guess(K, K @ xs, H, m=4)
+    assert np.allclose(x0, xs, atol=1e-10)
+    assert np.allclose(th, [0.7, 0.0, -0.2, 0.0], atol=1e-10)
+
+
+def test_subspace_guess_single_direction_closed_form_and_never_worse():
+    # one direction: theta = v.r0 / v.Kv; more directions never raise the K-norm error
+    from oracle.guess import subspace_guess
+    K = _spd(30, 3)
+    rng = np.random.default_rng(4)
+    H = [rng.standard_normal(30) for _ in range(9)]
+    b = rng.standard_normal(30)
+    xs = np.linalg.solve(K, b)
+    knorm = lambda e: np.sqrt(e @ (K @ e))
+    x1, th = subspace_guess(K, b, H[:2], m=1)
+    r0, v = b - K @ H[0], H[0] - H[1]
+    assert np.isclose(th[0], (v @ r0) / (v @ (K @ v)), rtol=1e-12)
+    err = [knorm(xs - H[0])]
+    for m in range(1, 9):
+        x0, _ = subspace_guess(K, b, H, m=m)
+        err.append(knorm(xs - x0))
+    assert all(err[i + 1] <= err[i] * (1 + 1e-12) for i in range(8))
+    # the error is K-orthogonal to the span (Galerkin)
+    x0, _ = subspace_guess(K, b, H, m=8)
+    V = np.stack([H[j - 1] - H[j] for j in range(1, 9)], 1)
+    assert np.abs(V.T @ (K @ (xs - x0))).max() < 1e-9 * np.abs(V.T @ (K @ xs)).max()
+    # with a proposal as well
+    xg = rng.standard_normal(30)
+    x0g, thg = subspace_guess(K, b, H, xg=xg, m=8)
+    assert len(thg) == 9 and knorm(xs - x0g) <= err[-1] * (1 + 1e-12)
