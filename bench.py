@@ -161,7 +161,7 @@ def load_guess(pd):
     return pd.guess_create(int(z["n_p"]), z["params"], z["scales"])
 
 
-GUESS_POLICY = 3   # Galerkin projection onto the learned proposal and the last 8 solution increments
+GUESS_POLICY = 3   # Galerkin projection onto the learned proposal and the last 16 solution increments
 
 
 def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clocks=None,
@@ -193,7 +193,7 @@ def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clo
 
 def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None, warm=12):
     """Same metric with the state crossing the host boundary every step: the last
-    solutions the step depends on (U^k .. U^{k-8}: the initial guess reads them) copied in
+    solutions the step depends on (U^k .. U^{k-16}: the initial guess reads them) copied in
     from pinned host memory and restored with sim_set_history, U^{k+1} copied back to
     pinned host memory.  The same steps as the device-timed forms: `warm` untimed, then
     `steps` timed."""
@@ -201,7 +201,7 @@ def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None, warm=12):
                         flexible=True)
     pd.sim_set_guess(sim, guess, GUESS_POLICY)
     n = ctx.n_dofs
-    H = 9
+    H = 17
     host_hist = torch.empty((H, n), dtype=torch.float64).pin_memory()   # row 0 = U^k
     dev_hist = torch.empty((H, n), dtype=torch.float64, device="cuda")
     dev_u = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -384,10 +384,10 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD,
                    "form": ("mixed + learned: fp32 local inverses, flexible PCG; initial guess = "
-                            "Galerkin projection onto the network's proposal and the last 8 "
+                            "Galerkin projection onto the network's proposal and the last 16 "
                             "solution increments (U^k when that does not lower the error)")
                    if guess is not None else
-                   "mixed: fp32 local inverses, flexible PCG, initial guess from the last 8 "
+                   "mixed: fp32 local inverses, flexible PCG, initial guess from the last 16 "
                    "solution increments (guess weights file missing)",
                    "rtol": 1e-8, "iterations_per_step": st["total_iterations"] / args.steps,
                    "guess_taken_steps": st.get("guesses_taken", 0),
@@ -401,6 +401,7 @@ def main():
                    "fp64_plain_steps_per_s": value64,
                    "fp64_plain_iterations_per_step": st64["total_iterations"] / args.steps,
                    "mixed_over_fp64": value / value64,
+                   "l2_keep_fraction": info["l2_keep_permille"] / 1000.0,
                    "l2": "working set > L2 (no flush needed)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks.summary(),
@@ -449,7 +450,7 @@ def bench_hex(args, pd, torch, stream, rank, world, local):
                                                    n0=4 * (n // 4) ** 3),
                    "form": "mixed + learned: fp32 local inverses, flexible PCG; initial guess = "
                            "Galerkin projection onto the network's proposal (trained on 2D "
-                           "Voronoi P3 trajectories) and the last 8 solution increments",
+                           "Voronoi P3 trajectories) and the last 16 solution increments",
                    "rtol": 1e-8, "iterations_per_step": st["total_iterations"] / steps,
                    "guess_taken_steps": st.get("guesses_taken", 0),
                    "mixed_without_guess_steps_per_s": world * steps / (ms_ng * 1e-3),

@@ -162,7 +162,8 @@ typedef struct {
     int32_t precision;           /* POLYDG_FP64/FP32/BF16                       */
     int32_t grid;                /* CTAs of the persistent PCG kernel           */
     int32_t rows_per_tile;       /* rows of K_i^{-1} per bulk copy (1)          */
-    int32_t pad;
+    int32_t l2_keep_permille;    /* share of the K_i^{-1} cache lines kept in L2 across
+                                    iterations (evict-last), per mille (asm_autotune) */
 } asm_info;
 
 /* Text of the last error raised on the calling thread ("" if none). */
@@ -222,8 +223,10 @@ int asm_get_info(const asm_ctx *pc, asm_info *out);
  * moves `rounds` times each -- re-cut the rows of the local inverses with every CTA's
  * tile costs rescaled by its measured / modelled P-phase share, and re-split the elements
  * so that the CTAs' measured CM-phase cycles even out -- keeping a move only if the timed
- * iterations got faster (always 2 + 4 rounds timed solves).  *gain (may be NULL) =
- * time before / time after.  Later solves
+ * iterations got faster.  Before the moves it times five fractions (0, 1/4, 1/2, 3/4, 1)
+ * of the local-inverse cache lines kept in L2 across iterations (evict-last; the rest
+ * streams evict-first) and keeps the fastest (always 8 + 4 rounds timed solves).
+ * *gain (may be NULL) = time before / time after.  Later solves
  * change only by rounding (the per-CTA partial sums are grouped differently).
  * Synchronises the device.  Errors: EINVAL, ENOMEM, ECUDA. */
 int asm_autotune(asm_ctx *pc, int rounds, int iterations, double *gain);
@@ -282,7 +285,7 @@ int sim_set_potential(sim_ctx *sim, const double *u_dev, const double *uprev_dev
 
 /* Overwrite the last `count` solutions: hist_dev is a caller-order device array
  * [count][n_dofs] holding U^k, U^{k-1}, ..., U^{k-count+1}.  U^k, U^{k-1} and U^{k-2}
- * become the simulation's potentials, and the first min(count, 9, k + 1) solutions the
+ * become the simulation's potentials, and the first min(count, 17, k + 1) solutions the
  * history of the subspace guess (a caller that keeps the state on the host restores
  * all of it this way).  Enqueued on `stream`. */
 int sim_set_history(sim_ctx *sim, const double *hist_dev, int count, void *stream);
@@ -370,11 +373,11 @@ int guess_train_step(guess_model *model, polydg_ctx *ctx, const double *traj_dev
  *   policy 2: from U^k + theta (x0 - U^k) with theta minimising |b - K x|_2 on that line
  *             (from the same pass over K_h; the residual never exceeds U^k's);
  *   policy 3: from U^k + sum_d theta_d v_d over the directions v: x0 - U^k (when a
- *             model is given, from k = 2 on) and the last min(8, k) solution increments
+ *             model is given, from k = 2 on) and the last min(16, k) solution increments
  *             U^{k-j+1} - U^{k-j}, theta the Galerkin projection V^T K V theta = V^T (b -
  *             K U^k) (the K-norm of the error is smallest; directions with negligible
  *             Schur-complement pivots dropped).  Policy 3 works without a model (the
- *             increments alone) and keeps the last 9 solutions on the device.
+ *             increments alone) and keeps the last 17 solutions on the device.
  * The FP64 stopping test decides convergence either way, so only iteration counts
  * change.  The model must outlive its use; it may be shared by several simulations. */
 int sim_set_guess(sim_ctx *sim, guess_model *model, int policy);

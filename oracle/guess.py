@@ -181,7 +181,7 @@ def safeguard(K, b, x_guess, Uk):
     return (x_guess, True) if rg < r0 else (Uk, False)
 
 
-def subspace_guess(K, b, history, xg=None, m=8):
+def subspace_guess(K, b, history, xg=None, m=16):
     """x0 = U^k + V theta over the directions v = xg - U^k (if a proposal is given) and the
     last min(m, len(history) - 1) increments U^{k-j+1} - U^{k-j}; history = [U^k, U^{k-1},
     ...].  theta is the Galerkin projection V^T K V theta = V^T (b - K U^k): the x0 of the

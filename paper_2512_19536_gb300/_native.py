@@ -74,7 +74,7 @@ class asm_info(C.Structure):
     _fields_ = [("local_store_bytes", C.c_int64), ("coarse_bytes", C.c_int64),
                 ("restrict_bytes", C.c_int64), ("n_subdomains", C.c_int32),
                 ("n_coarse", C.c_int32), ("precision", C.c_int32), ("grid", C.c_int32),
-                ("rows_per_tile", C.c_int32), ("pad", C.c_int32)]
+                ("rows_per_tile", C.c_int32), ("l2_keep_permille", C.c_int32)]
 
 
 _lib = None
@@ -269,7 +269,7 @@ class ASM:
     def info(self):
         inf = asm_info()
         _check(load().asm_get_info(self.h, C.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in asm_info._fields_ if k != "pad"}
+        return {k: getattr(inf, k) for k, _ in asm_info._fields_}
 
     def close(self):
         if self.h:
@@ -530,8 +530,8 @@ def guess_train_step(model: GuessModel, ctx: PolyDG, traj, samples, lr, stream=N
 def sim_set_guess(sim: Simulation, model, policy=0):
     """policy 0: start from the proposal only if its residual is smaller; 1: always;
     2: from U^k + theta (proposal - U^k), theta minimising the residual on that line;
-    3: residual least squares over the proposal (if a model is given) and the last
-    eight solution increments (model may be None)."""
+    3: Galerkin projection onto the proposal (if a model is given) and the last
+    sixteen solution increments (model may be None)."""
     _check(load().sim_set_guess(sim.h, model.h if model is not None else None, int(policy)))
     sim.guess = model
 

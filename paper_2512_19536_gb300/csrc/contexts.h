@@ -83,6 +83,7 @@ struct Plan {
     int grid = 0, rows = 1, dtype = 0;
     int redundant = 1;
     int wstages = 1;
+    float l2_keep = 0.f;                // fraction of the local-inverse lines kept in L2
     size_t smem = 0, slot_bytes = 0, xs_off = 0, rp_off = 0, r0_off = 0, y0_off = 0,
            pn_off = 0, td_off = 0;
     int32_t *run_ptr = nullptr, *sub_pairs = nullptr, *crow_ptr = nullptr, *cta_chunk = nullptr;

@@ -13,9 +13,9 @@ namespace polydg {
 enum MatvecMode { MODE_PLAIN = 0, MODE_PCG = 1, MODE_RESID = 2, MODE_RHS = 3 };
 
 // Subspace initial guess (policy 3): the last kHistDirs solution increments, plus the
-// learned proposal, combined by residual least squares.  The solutions live in a ring
+// learned proposal, combined by a Galerkin projection.  The solutions live in a ring
 // of kHistRing vectors indexed by step (slot k mod kHistRing holds U^k).
-constexpr int kHistDirs = 8;
+constexpr int kHistDirs = 16;
 constexpr int kHistRing = kHistDirs + 1;
 constexpr int kSubMaxDirs = kHistDirs + 1;                       // + the learned proposal
 constexpr int kSubMaxPairs = kSubMaxDirs + kSubMaxDirs * (kSubMaxDirs + 1) / 2;
@@ -93,6 +93,7 @@ struct GridSync {
 // are CSR arrays indexed by blockIdx.x.
 struct PersistArgs {
     int grid, wstages, identity, n0, ld0, nq, redundant;
+    float l2_keep;                             // fraction of the local-inverse lines kept in L2
     int64_t nc;
     // shared-memory carve-up (byte offsets): wstages copy slots of slot_bytes per warp
     size_t slot_bytes, xs_off, rp_off, r0_off, y0_off, pn_off, td_off;

@@ -205,7 +205,7 @@ __device__ __forceinline__ void pcg_group_cta(const GroupArgs& a, const int cta,
     auto issue = [&](int k) {
         const RunDesc& d = rd[iss_run];
         bulk_load(slot(warp, k), reinterpret_cast<const T*>(a.qstore) + d.mat_off + (int64_t)iss_row * d.ld,
-                  (uint32_t)((size_t)d.ld * sizeof(T)), &wbars[warp][k]);
+                  (uint32_t)((size_t)d.ld * sizeof(T)), &wbars[warp][k], evict_first_policy());
         iss_row += NW;
         while (iss_row >= rd[iss_run].row_end) {
             const int over = iss_row - rd[iss_run].row_end;

@@ -359,16 +359,17 @@ subspace_rows_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restr
 }
 
 // The dot products c_d = v_d . r0 and H_ij = v_i . K v_j (i <= j) over the columns of W,
-// per-CTA partial sums in fixed row order; the last CTA adds them in CTA order and thread
-// 0 solves for theta: Cholesky on the directions whose Schur-complement pivots stay above
+// per-CTA partial sums in fixed row order; the last CTA adds them in CTA order and solves
+// for theta by elimination on the directions whose Schur-complement pivots stay above
 // 1e-13 of the largest diagonal (greedy, largest pivot first), the others left at zero.
 // The guess is used when it lowers the K-norm of the error (gain c.theta > 0).
 constexpr int kGramThreads = 256;
+constexpr int kGramRows = 128;           // rows per shared-memory tile
 
 __global__ void __launch_bounds__(kGramThreads)
 subspace_gram_kernel(const double* __restrict__ W, int64_t n, double* gram, SimScalars* ss,
                      int with_model) {
-    __shared__ double tile[2 * kSubMaxDirs + 1][kGramThreads + 1];   // r0, K v_d, v_d
+    __shared__ double tile[2 * kSubMaxDirs + 1][kGramRows + 1];   // r0, K v_d, v_d
     __shared__ double Gs[kSubMaxPairs];
     __shared__ bool last;
     if (ss->failed) return;
@@ -394,16 +395,17 @@ subspace_gram_kernel(const double* __restrict__ W, int64_t n, double* gram, SimS
         }
     }
     double acc = 0.0;
-    for (int64_t r0 = (int64_t)blockIdx.x * kGramThreads; r0 < n; r0 += (int64_t)gridDim.x * kGramThreads) {
-        const int64_t r = r0 + threadIdx.x;
-        tile[0][threadIdx.x] = (r < n) ? __ldcg(W + r) : 0.0;
-        for (int d = 0; d < nd; ++d) {
-            tile[1 + d][threadIdx.x] = (r < n) ? __ldcg(W + (1 + d) * n + r) : 0.0;
-            tile[1 + nd + d][threadIdx.x] = (r < n) ? __ldcg(W + (1 + kSubMaxDirs + d) * n + r) : 0.0;
+    const int nrow = 1 + 2 * nd;
+    for (int64_t r0 = (int64_t)blockIdx.x * kGramRows; r0 < n; r0 += (int64_t)gridDim.x * kGramRows) {
+        for (int idx = threadIdx.x; idx < nrow * kGramRows; idx += kGramThreads) {
+            const int v = idx / kGramRows, q = idx - v * kGramRows;
+            const int64_t r = r0 + q;
+            const int64_t col = v == 0 ? 0 : (v <= nd ? v : 1 + kSubMaxDirs + (v - 1 - nd));
+            tile[v][q] = (r < n) ? __ldcg(W + col * n + r) : 0.0;
         }
         __syncthreads();
         if (threadIdx.x < npair)
-            for (int q = 0; q < kGramThreads; ++q) acc = fma(tile[pi][q], tile[pj][q], acc);
+            for (int q = 0; q < kGramRows; ++q) acc = fma(tile[pi][q], tile[pj][q], acc);
         __syncthreads();
     }
     if (threadIdx.x < npair) gram[threadIdx.x * kSubMaxCtas + blockIdx.x] = acc;
@@ -424,66 +426,70 @@ subspace_gram_kernel(const double* __restrict__ W, int64_t n, double* gram, SimS
         Gs[threadIdx.x] = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    ss->guess_ticket = 0;
-    // H = V^T K V, c = V^T r0 from the packed sums
+    // Symmetric elimination with greedy diagonal pivoting on H = V^T K V, c = V^T r0, all
+    // threads sharing each pivot's rank-one update; the pivot rows as eliminated give
+    // theta by back substitution.  Directions never chosen as pivots keep theta = 0.
+    __shared__ double sA[kSubMaxDirs][kSubMaxDirs + 1], sR[kSubMaxDirs][kSubMaxDirs + 1];
+    __shared__ double sc[kSubMaxDirs], sc0[kSubMaxDirs], sD[kSubMaxDirs], sdmax;
+    __shared__ int ssel[kSubMaxDirs], sused[kSubMaxDirs], sq, sok;
     auto pair = [&](int i, int j) { return nd + i * nd - i * (i - 1) / 2 + (j - i); };   // i <= j
-    double H[kSubMaxDirs][kSubMaxDirs], c[kSubMaxDirs], A[kSubMaxDirs][kSubMaxDirs], th[kSubMaxDirs];
-    double dmax = 0.0;
-    for (int d = 0; d < nd; ++d) {
-        c[d] = Gs[d];
-        for (int e2 = d; e2 < nd; ++e2) H[d][e2] = H[e2][d] = Gs[pair(d, e2)];
-        dmax = fmax(dmax, H[d][d]);
-        th[d] = 0.0;
+    for (int idx = threadIdx.x; idx < nd * nd; idx += blockDim.x) {
+        const int i = idx / nd, j = idx - i * nd;
+        sA[i][j] = Gs[i <= j ? pair(i, j) : pair(j, i)];
     }
-    bool ok = isfinite(dmax) && dmax > 0.0;
-    for (int d = 0; d < nd; ++d) ok = ok && isfinite(c[d]);
-    int sel[kSubMaxDirs], ns = 0;
-    bool used[kSubMaxDirs];
-    for (int d = 0; d < nd; ++d) {
-        used[d] = false;
-        for (int e2 = 0; e2 < nd; ++e2) A[d][e2] = H[d][e2];
+    if (threadIdx.x < nd) {
+        sc[threadIdx.x] = sc0[threadIdx.x] = Gs[threadIdx.x];
+        sused[threadIdx.x] = 0;
     }
-    while (ok && ns < nd) {              // greedy pivot choice on the Schur complement
-        int q = -1;
-        double best = 1e-13 * dmax;
-        for (int d = 0; d < nd; ++d)
-            if (!used[d] && A[d][d] > best) { best = A[d][d]; q = d; }
-        if (q < 0) break;
-        used[q] = true;
-        sel[ns++] = q;
-        for (int i2 = 0; i2 < nd; ++i2)
-            for (int j2 = 0; j2 < nd; ++j2)
-                if (!used[i2] && !used[j2]) A[i2][j2] -= A[i2][q] * A[q][j2] / A[q][q];
-    }
-    double L[kSubMaxDirs][kSubMaxDirs], y[kSubMaxDirs];
-    for (int r = 0; ok && r < ns; ++r) {   // Cholesky of H restricted to the chosen directions
-        for (int c2 = 0; c2 <= r; ++c2) {
-            double v = H[sel[r]][sel[c2]];
-            for (int t2 = 0; t2 < c2; ++t2) v -= L[r][t2] * L[c2][t2];
-            if (c2 == r) {
-                if (!(v > 0.0)) { ok = false; break; }
-                L[r][r] = sqrt(v);
-            } else {
-                L[r][c2] = v / L[c2][c2];
-            }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ss->guess_ticket = 0;
+        double dmax = 0.0;
+        bool ok = true;
+        for (int d = 0; d < nd; ++d) {
+            dmax = fmax(dmax, sA[d][d]);
+            ok = ok && isfinite(sA[d][d]) && isfinite(sc[d]);
         }
+        sdmax = dmax;
+        sok = (ok && isfinite(dmax) && dmax > 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    int ns = 0;
+    while (sok && ns < nd) {
+        if (threadIdx.x == 0) {
+            int q = -1;
+            double best = 1e-13 * sdmax;
+            for (int d = 0; d < nd; ++d)
+                if (!sused[d] && sA[d][d] > best) { best = sA[d][d]; q = d; }
+            sq = q;
+            if (q >= 0) { sused[q] = 1; ssel[ns] = q; sD[ns] = sA[q][q]; }
+        }
+        __syncthreads();
+        const int q = sq;
+        if (q < 0) break;
+        for (int j = threadIdx.x; j < nd; j += blockDim.x) sR[ns][j] = sA[q][j];
+        __syncthreads();
+        const double inv = 1.0 / sD[ns], cq = sc[q];
+        for (int idx = threadIdx.x; idx < nd * nd; idx += blockDim.x) {
+            const int i = idx / nd, j = idx - i * nd;
+            if (!sused[i] && !sused[j]) sA[i][j] -= sR[ns][i] * sR[ns][j] * inv;
+        }
+        if (threadIdx.x < nd && !sused[threadIdx.x]) sc[threadIdx.x] -= sR[ns][threadIdx.x] * cq * inv;
+        ++ns;
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double th[kSubMaxDirs];
+    for (int d = 0; d < kSubMaxDirs; ++d) th[d] = 0.0;
+    for (int t = ns - 1; t >= 0; --t) {
+        const int q = ssel[t];
+        double v = sc[q];
+        for (int u = t + 1; u < ns; ++u) v -= sR[t][ssel[u]] * th[ssel[u]];
+        th[q] = v / sD[t];
     }
     double gain = 0.0;
-    if (ok && ns > 0) {
-        for (int r = 0; r < ns; ++r) {
-            double v = c[sel[r]];
-            for (int t2 = 0; t2 < r; ++t2) v -= L[r][t2] * y[t2];
-            y[r] = v / L[r][r];
-        }
-        for (int r = ns - 1; r >= 0; --r) {
-            double v = y[r];
-            for (int t2 = r + 1; t2 < ns; ++t2) v -= L[t2][r] * th[sel[t2]];
-            th[sel[r]] = v / L[r][r];
-        }
-        for (int d = 0; d < nd; ++d) gain += c[d] * th[d];
-    }
-    const bool use = ok && ns > 0 && isfinite(gain) && gain > 0.0;
+    for (int d = 0; d < nd; ++d) gain += sc0[d] * th[d];
+    const bool use = sok && ns > 0 && isfinite(gain) && gain > 0.0;
     for (int d = 0; d < kSubMaxDirs; ++d) ss->theta_sub[d] = (use && d < nd) ? th[d] : 0.0;
     ss->sub_dirs = use ? nd : 0;
     ss->use_guess = use ? 1 : 0;
@@ -785,7 +791,7 @@ cudaError_t launch_guess_subspace(int np, const DeviceMatrix& K, const double* b
         subspace_rows_kernel<NP><<<grid, kBlock, 0, s>>>(K.row_ptr, K.col, K.val, b, U, xg, ring, W,
                                                          n, K.nc, ss);
     })
-    const unsigned g2 = (unsigned)std::min<int64_t>(kSubMaxCtas, (n + kGramThreads - 1) / kGramThreads);
+    const unsigned g2 = (unsigned)std::min<int64_t>(kSubMaxCtas, (n + kGramRows - 1) / kGramRows);
     subspace_gram_kernel<<<g2, kGramThreads, 0, s>>>(W, n, gram, ss, xg != nullptr ? 1 : 0);
     return cudaGetLastError();
 }

@@ -9,7 +9,8 @@
 //   P   p_k, q_k, x += alpha p_k, r' = r - alpha q_k (r, p, q double-buffered);
 //       z_loc = K_i^{-1} r'_i on the CTA's rows of the local inverses, streamed by
 //       cp.async.bulk into a shared-memory ring prefetched across phases and
-//       iterations (the inverses are constant); R_0 r' for the subdomains the
+//       iterations (the inverses are constant; a fraction of their lines, chosen by
+//       the plan, stays in L2 as evict-last); R_0 r' for the subdomains the
 //       CTA stages first; partial |r'|^2                     -> barrier, test
 //   CM  y0 = K_0^{-1} R_0 r' for the agglomerates the CTA's elements touch
 //       (redundantly per CTA; a distributed coarse phase with one more barrier
@@ -130,10 +131,11 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         iss_run = first_run;
         iss_row = first_row;
     }
+    const uint64_t l2pol = stream_policy(a.l2_keep);
     auto issue = [&](int k) {
         const RunDesc& d = rd[iss_run];
         bulk_load(slot(warp, k), reinterpret_cast<const T*>(a.store) + d.mat_off + (int64_t)iss_row * d.ld,
-                  (uint32_t)((size_t)d.ld * sizeof(T)), &wbars[warp][k]);
+                  (uint32_t)((size_t)d.ld * sizeof(T)), &wbars[warp][k], l2pol);
         iss_row += NW;
         while (iss_row >= rd[iss_run].row_end) {
             const int over = iss_row - rd[iss_run].row_end;

@@ -38,8 +38,20 @@ __device__ __forceinline__ uint64_t evict_first_policy() {
     return pol;
 }
 
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    const uint64_t pol = evict_first_policy();
+// L2 policy for the local inverses: a fraction `keep` of their lines evict-last (they
+// stay in L2 from one iteration to the next), the rest evict-first (streamed from HBM
+// without pushing K_h, the vectors and the coarse data out).  keep <= 0: all evict-first.
+__device__ __forceinline__ uint64_t stream_policy(float keep) {
+    if (!(keep > 0.f)) return evict_first_policy();
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.L2::evict_first.b64 %0, %1;"
+                 : "=l"(pol)
+                 : "f"(fminf(keep, 1.f)));
+    return pol;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                          uint64_t pol) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                  "r"(bytes)

@@ -234,7 +234,7 @@ def subspace_run(w, d, steps, model=None, rtol=1e-8, reset_history=False):
     pd.sim_get_state(sim, hist[0])
     for _ in range(steps):
         if reset_history:
-            pd.sim_set_history(sim, torch.stack(hist[::-1][:9]))
+            pd.sim_set_history(sim, torch.stack(hist[::-1][:17]))
         st = pd.monodomain_step(sim, 1)
         assert st["status"] == 0
         its.append(st["total_iterations"])
@@ -260,7 +260,7 @@ def test_subspace_guess_iterations_and_answer_match_oracle(vor):
     for _ in range(steps):
         st = md.state
         b, y_new = md.rhs(st)
-        x0, _ = G.subspace_guess(d.K, b, hist[::-1], m=8)
+        x0, _ = G.subspace_guess(d.K, b, hist[::-1], m=16)
         r = pcg(d.K, b, x0=x0, prec=S.apply, rtol=1e-8)
         ref_its.append(r.iterations)
         plain_its.append(pcg(d.K, b, x0=st.U, prec=S.apply, rtol=1e-8).iterations)
