@@ -1044,7 +1044,7 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
         (st = dalloc(&sm->Uprev2, n)) || (st = dalloc(&sm->xg, n)) ||
         (st = dalloc(&sm->I, n)) || (st = dalloc(&sm->y, 5 * nn)) || (st = dalloc(&sm->d_y0, 5)) ||
         (st = dalloc(&sm->d_ss, 1)) || (st = dalloc(&sm->ring, kHistRing * n)) ||
-        (st = dalloc(&sm->subW, (2 * kSubMaxDirs + 1) * n)) || (st = dalloc(&sm->gram, kSubMaxPairs * kSubMaxCtas)))
+        (st = dalloc(&sm->kuring, kHistRing * n)) || (st = dalloc(&sm->subW, 2 * n)) || (st = dalloc(&sm->gram, kSubMaxPairs * kSubMaxCtas)))
         return fail(st);
     if (cudaMallocHost((void**)&sm->h_ss, sizeof(SimScalars)) != cudaSuccess) {
         set_error("sim_create: pinned allocation failed");
@@ -1073,6 +1073,7 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
     };
     SimScalars ss = {};
     ss.hist_len = 1;                    // the ring holds U^0
+    ss.kd_step = -2;                    // no increment products yet
     PcgScalars sc = {};
     sc.rtol2 = prm->rtol * prm->rtol;
     sc.maxit = prm->maxit;
@@ -1131,8 +1132,9 @@ static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
                                     sm->d_ss, s));
             xg = sm->xg;
         }
-        CU(launch_guess_subspace(np, c->K, w.b, sm->U, xg, sm->ring, sm->subW, sm->gram, n, sm->d_ss, s));
-        CU(launch_subspace_copy(sm->U, xg, sm->ring, w.x[0], n, sm->d_ss, s));
+        CU(launch_guess_subspace(np, c->K, w.b, sm->U, xg, sm->ring, sm->kuring, sm->subW, sm->gram, n,
+                                 sm->d_ss, s));
+        CU(launch_subspace_copy(sm->U, xg, sm->ring, sm->kuring, sm->subW, w.x[0], n, sm->d_ss, s));
     } else if (sm->guess) {     // from k = 2 on: learned proposal, kept if its residual is smaller
         const GuessFeat f = guess_features(c, sm->guess);
         CU(launch_guess_propose(np, f, sm->guess->w16, sm->U, sm->Uprev, sm->Uprev2, sm->xg, H.nc,
@@ -1422,15 +1424,16 @@ int sim_set_potential(sim_ctx* sm, const double* u_dev, const double* uprev_dev,
                       c->H.n_p, 1, nullptr, s));
     CU(cudaMemcpyAsync(sm->Uprev2, sm->Uprev, c->H.nc * c->H.n_p * sizeof(double),
                        cudaMemcpyDeviceToDevice, s));
-    CU(launch_history_reset(sm->ring, sm->U, sm->Uprev, c->H.nc * c->H.n_p, sm->d_ss, s));
+    CU(launch_history_reset(c->H.n_p, c->K, sm->ring, sm->kuring, sm->U, sm->Uprev, c->H.nc * c->H.n_p,
+                            sm->d_ss, s));
     return POLYDG_OK;
 }
 
 int sim_set_history(sim_ctx* sm, const double* hist_dev, int count, void* stream) {
     if (!sm || !hist_dev || count < 1) { set_error("sim_set_history: need a simulation, a device array and count >= 1"); return POLYDG_EINVAL; }
     polydg_ctx* c = sm->ctx;
-    CU(launch_history_set(hist_dev, count, sm->ring, sm->U, sm->Uprev, sm->Uprev2, c->d_to_caller,
-                          c->H.nc, c->H.n_p, sm->d_ss, (cudaStream_t)stream));
+    CU(launch_history_set(c->K, hist_dev, count, sm->ring, sm->kuring, sm->U, sm->Uprev, sm->Uprev2,
+                          c->d_to_caller, c->H.nc, c->H.n_p, sm->d_ss, (cudaStream_t)stream));
     return POLYDG_OK;
 }
 
@@ -1808,7 +1811,7 @@ void sim_destroy(sim_ctx* sm) {
     for (auto e : sm->ev) cudaEventDestroy(e);
     sm->work.release();
     dfree(sm->U); dfree(sm->Uprev); dfree(sm->Uprev2); dfree(sm->xg); dfree(sm->I); dfree(sm->F); dfree(sm->y); dfree(sm->d_y0);
-    dfree(sm->ring); dfree(sm->subW); dfree(sm->gram);
+    dfree(sm->ring); dfree(sm->kuring); dfree(sm->subW); dfree(sm->gram);
     dfree(sm->d_ss);
     if (sm->h_ss) cudaFreeHost(sm->h_ss);
     delete sm;

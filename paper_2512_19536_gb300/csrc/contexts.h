@@ -185,7 +185,8 @@ struct sim_ctx {
     int64_t version = 0;                // bumped when the step's kernel sequence changes
     double *Uprev2 = nullptr, *xg = nullptr;
     double* ring = nullptr;             // [kHistRing][n] past solutions, slot k mod kHistRing = U^k
-    double* subW = nullptr;             // [2 kSubMaxDirs + 1][n] r0, K v_d and v_d of the subspace guess
+    double* kuring = nullptr;           // [kHistRing][n] products K (U^j - U^{j-1}), same slots as ring
+    double* subW = nullptr;             // [2][n] r0 = b - K U^k and K (xg - U^k) of the subspace guess
     double* gram = nullptr;             // [kSubMaxPairs][kSubMaxCtas] Gram partial sums
     double *U = nullptr, *Uprev = nullptr, *I = nullptr, *F = nullptr, *y = nullptr;
     double* d_y0 = nullptr;

@@ -38,6 +38,9 @@ struct SimScalars {
     int32_t hist_len;      // consecutive solutions U^k, U^{k-1}, ... held by the ring (>= 1)
     int32_t sub_dirs;      // directions of this step's subspace guess
     double theta_sub[kSubMaxDirs];   // their coefficients
+    int32_t kd_len;        // consecutive increment products K D_j held by their ring, up to kd_step
+    int32_t pad2;
+    int64_t kd_step;
 };
 
 // Block-sparse K_h on the device (internal cell order).
@@ -273,22 +276,27 @@ cudaError_t launch_guess_select(int np, const DeviceMatrix& K, const double* b, 
                                 cudaStream_t s);
 cudaError_t launch_select_copy(const double* uk, const double* xg, double* x0, int64_t n,
                                const SimScalars* ss, cudaStream_t s);
-// Subspace guess: r0 = b - K U^k, K v_d and v_d for the directions into W
-// ([2 kSubMaxDirs + 1][n]), the dot products V^T r0 and V^T K V (gram: kSubMaxPairs *
-// kSubMaxCtas partial sums), the Galerkin coefficients (last CTA), then x0.
-// xg == nullptr leaves the learned proposal out.
+// Subspace guess: r0 = b - K U^k into W[0], K (U^k - U^{k-1}) into the increment-product
+// ring kuring (same slots as the solution ring), K (xg - U^k) into W[1] (with a model);
+// then the dot products V^T r0 and
+// V^T K V (gram: kSubMaxPairs * kSubMaxCtas partial sums), the Galerkin coefficients (last
+// CTA), and x0.  xg == nullptr leaves the learned proposal out.
 cudaError_t launch_guess_subspace(int np, const DeviceMatrix& K, const double* b, const double* U,
-                                  const double* xg, const double* ring, double* W, double* gram,
-                                  int64_t n, SimScalars* ss, cudaStream_t s);
-cudaError_t launch_subspace_copy(const double* U, const double* xg, const double* ring, double* x0,
-                                 int64_t n, const SimScalars* ss, cudaStream_t s);
-// Ring maintenance: slot(k) <- U and slot(k-1) <- Uprev with hist_len reset (new potentials),
-// or `count` caller-order solutions [count][n] (U^k first) into the ring, U, Uprev, Uprev2.
-cudaError_t launch_history_reset(double* ring, const double* U, const double* Uprev, int64_t n,
-                                 SimScalars* ss, cudaStream_t s);
-cudaError_t launch_history_set(const double* hist, int count, double* ring, double* U, double* Uprev,
-                               double* Uprev2, const int64_t* to_caller, int64_t nc, int np,
-                               SimScalars* ss, cudaStream_t s);
+                                  const double* xg, const double* ring, double* kuring, double* W,
+                                  double* gram, int64_t n, SimScalars* ss, cudaStream_t s);
+cudaError_t launch_subspace_copy(const double* U, const double* xg, const double* ring,
+                                 const double* kuring, const double* W, double* x0, int64_t n,
+                                 const SimScalars* ss, cudaStream_t s);
+// Ring maintenance: slot(k) <- U and slot(k-1) <- Uprev (new potentials), or `count`
+// caller-order solutions [count][n] (U^k first) into the ring, U, Uprev, Uprev2; either way
+// the products of the restored increments into the increment-product ring.
+cudaError_t launch_history_reset(int np, const DeviceMatrix& K, double* ring, double* kuring,
+                                 const double* U, const double* Uprev, int64_t n, SimScalars* ss,
+                                 cudaStream_t s);
+cudaError_t launch_history_set(const DeviceMatrix& K, const double* hist, int count, double* ring,
+                               double* kuring, double* U, double* Uprev, double* Uprev2,
+                               const int64_t* to_caller, int64_t nc, int np, SimScalars* ss,
+                               cudaStream_t s);
 cudaError_t launch_guess_train(int np, const GuessFeat& f, const float* w32, const double* traj,
                                int64_t n_dofs, const int64_t* samples, int64_t n_samples,
                                const int64_t* to_internal, const int64_t* to_caller, float* part,

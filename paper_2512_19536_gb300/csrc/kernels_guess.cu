@@ -281,49 +281,52 @@ __global__ void select_copy_kernel(const double* __restrict__ uk, const double* 
 
 // ------------------------------------------------------------------ subspace guess
 // Policy 3: x0 = U^k + sum_d theta_d v_d over the directions v_0 = xg - U^k (the learned
-// proposal, from k = 2 on, when a model is attached) and v_j = U^{k-j+1} - U^{k-j} for the
-// last min(kHistDirs, hist_len - 1) solution increments, theta the Galerkin projection of
-// the correction onto their span (minimum of the K-norm of the error x* - x0, the norm
-// CG minimises): V^T K V theta = V^T r0 with r0 = b - K U^k.  The direction list depends
-// only on (k, hist_len, model attached): every kernel below rebuilds the same list.
+// proposal, from k = 2 on, when a model is attached) and v_j = D_{k-j+1} for the last m
+// solution increments D_i = U^i - U^{i-1}, theta the Galerkin projection of the correction
+// onto their span (minimum of the K-norm of the error x* - x0, the norm CG minimises):
+// V^T K V theta = V^T r0 with r0 = b - K U^k.  K v_j needs no pass over K_h: each step
+// multiplies its newest increment D_k once and keeps K D_k in a second ring (slot k mod
+// kHistRing, like U^k).  The increment is formed exactly (the difference of two nearby
+// doubles), so its product carries only the product's own rounding, unlike a difference
+// of the products K U^i.  m = min(kHistDirs, hist_len - 1, kd_len).  The direction list
+// depends only on (k, hist_len, kd_len, model attached): every kernel after the ring
+// update rebuilds the same list.
+struct SubDirs {
+    const double* a[kSubMaxDirs];        // v_d = a_d - b_d
+    const double* b[kSubMaxDirs];
+    const double* kv[kSubMaxDirs];       // K v_d
+};
+
 __device__ __forceinline__ int subspace_dirs(const SimScalars* ss, const double* U, const double* xg,
-                                             const double* ring, int64_t n, const double** a,
-                                             const double** b) {
+                                             const double* ring, const double* kdring, const double* kxg,
+                                             int64_t n, SubDirs& D) {
     const int64_t k = ss->k;
-    const int m = min(kHistDirs, ss->hist_len - 1);
+    const int m = min(min(kHistDirs, ss->hist_len - 1), ss->kd_len);
     int nd = 0;
-    if (xg != nullptr && k >= 2) { a[nd] = xg; b[nd] = U; ++nd; }
+    if (xg != nullptr && k >= 2) { D.a[nd] = xg; D.b[nd] = U; D.kv[nd] = kxg; ++nd; }
     for (int j = 1; j <= m; ++j) {
-        a[nd] = (j == 1) ? U : ring + ((k - j + 1) % kHistRing) * n;
-        b[nd] = ring + ((k - j) % kHistRing) * n;
+        D.a[nd] = (j == 1) ? U : ring + ((k - j + 1) % kHistRing) * n;
+        D.b[nd] = ring + ((k - j) % kHistRing) * n;
+        D.kv[nd] = kdring + ((k - j + 1) % kHistRing) * n;
         ++nd;
     }
     return nd;
 }
 
-// W[0] = r0 = b - K U^k, W[1 + d] = K v_d and W[1 + kSubMaxDirs + d] = v_d, warp per
-// element row block (K_h read once).
-template <int NP>
-__global__ void __launch_bounds__(kBlock)
-subspace_rows_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                     const double* __restrict__ val, const double* __restrict__ b,
-                     const double* __restrict__ U, const double* xg, const double* ring,
-                     double* __restrict__ W, int64_t n, int64_t nc, const SimScalars* ss) {
-    __shared__ const double* sa[kSubMaxDirs];
-    __shared__ const double* sb[kSubMaxDirs];
-    __shared__ int snd;
-    if (ss->failed) return;
-    if (threadIdx.x == 0) snd = subspace_dirs(ss, U, xg, ring, n, sa, sb);
-    __syncthreads();
-    const int nd = snd;
+// y_v = K (x_v - w_v) for up to NV vectors (w_v may be null), warp per element row block;
+// the differences are formed per entry before the product.
+template <int NP, int NV>
+__device__ __forceinline__ void multi_matvec_row(const int32_t* __restrict__ row_ptr,
+                                                 const int32_t* __restrict__ col,
+                                                 const double* __restrict__ val, int64_t e,
+                                                 const double* const* x, const double* const* w,
+                                                 int nv, double* t) {
     constexpr int G = 32 / NP;
     const int lane = threadIdx.x & 31;
-    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (nd == 0 || e >= nc) return;
     const int g = lane / NP, i = lane - g * NP;
-    double a0 = 0.0, a[kSubMaxDirs];
+    double a[NV];
 #pragma unroll
-    for (int d = 0; d < kSubMaxDirs; ++d) a[d] = 0.0;
+    for (int v = 0; v < NV; ++v) a[v] = 0.0;
     const int32_t b0 = row_ptr[e];
     const int ncol = (row_ptr[e + 1] - b0) * NP;
     const double* V = val + (int64_t)b0 * NP * NP;
@@ -331,50 +334,111 @@ subspace_rows_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restr
         for (int c = g; c < ncol; c += G) {
             const int sblk = c / NP;
             const int64_t xi = (int64_t)__ldg(col + b0 + sblk) * NP + (c - sblk * NP);
-            const double v = __ldg(V + (int64_t)c * NP + i);
-            a0 = fma(v, __ldg(U + xi), a0);
+            const double kv = __ldg(V + (int64_t)c * NP + i);
 #pragma unroll
-            for (int d = 0; d < kSubMaxDirs; ++d)
-                if (d < nd) a[d] = fma(v, __ldcg(sa[d] + xi) - __ldcg(sb[d] + xi), a[d]);
+            for (int v = 0; v < NV; ++v)
+                if (v < nv) a[v] = fma(kv, __ldcg(x[v] + xi) - (w[v] ? __ldcg(w[v] + xi) : 0.0), a[v]);
         }
-    double t0 = a0, t[kSubMaxDirs];
 #pragma unroll
-    for (int d = 0; d < kSubMaxDirs; ++d) t[d] = a[d];
+    for (int v = 0; v < NV; ++v) {
+        double s = a[v];
 #pragma unroll
-    for (int k = 1; k < G; ++k) {
-        t0 += __shfl_down_sync(0xffffffffu, a0, k * NP);
-#pragma unroll
-        for (int d = 0; d < kSubMaxDirs; ++d) t[d] += __shfl_down_sync(0xffffffffu, a[d], k * NP);
-    }
-    if (lane < NP) {
-        const int64_t r = e * NP + i;
-        W[r] = b[r] - t0;
-#pragma unroll
-        for (int d = 0; d < kSubMaxDirs; ++d)
-            if (d < nd) {
-                W[(1 + d) * n + r] = t[d];
-                W[(1 + kSubMaxDirs + d) * n + r] = __ldcg(sa[d] + r) - __ldcg(sb[d] + r);
-            }
+        for (int k = 1; k < G; ++k) s += __shfl_down_sync(0xffffffffu, a[v], k * NP);
+        t[v] = s;
     }
 }
 
-// The dot products c_d = v_d . r0 and H_ij = v_i . K v_j (i <= j) over the columns of W,
-// per-CTA partial sums in fixed row order; the last CTA adds them in CTA order and solves
-// for theta by elimination on the directions whose Schur-complement pivots stay above
-// 1e-13 of the largest diagonal (greedy, largest pivot first), the others left at zero.
-// The guess is used when it lowers the K-norm of the error (gain c.theta > 0).
+// W[0] = r0 = b - K U^k, K D_k = K (U^k - U^{k-1}) into the increment-product ring (slot k,
+// from k = 1 on), W[1] = K (xg - U^k) (with a model).
+template <int NP>
+__global__ void __launch_bounds__(kBlock)
+subspace_rows_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                     const double* __restrict__ val, const double* __restrict__ b,
+                     const double* __restrict__ U, const double* xg, const double* ring,
+                     double* __restrict__ kdring, double* __restrict__ W, int64_t n, int64_t nc,
+                     SimScalars* ss) {
+    if (ss->failed) return;
+    const int64_t k = ss->k;
+    const bool inc = ss->hist_len >= 2;          // U^{k-1} is in the ring
+    const int lane = threadIdx.x & 31;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (e < nc) {
+        const double* Um1 = ring + ((k + kHistRing - 1) % kHistRing) * n;
+        const double* x[3] = {U, inc ? U : U, xg};
+        const double* w[3] = {nullptr, inc ? Um1 : nullptr, U};
+        int nv = 1;
+        double t[3];
+        if (inc) nv = 2;
+        if (xg != nullptr) { x[nv] = xg; w[nv] = U; ++nv; }
+        multi_matvec_row<NP, 3>(row_ptr, col, val, e, x, w, nv, t);
+        if (lane < NP) {
+            const int64_t r = e * NP + lane;
+            W[r] = b[r] - t[0];
+            if (inc) kdring[(k % kHistRing) * n + r] = t[1];
+            if (xg != nullptr) W[n + r] = t[nv - 1];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {      // the product ring now reaches step k
+        ss->kd_len = !inc ? 0 : (ss->kd_step == k - 1 ? min(ss->kd_len + 1, kHistDirs) : 1);
+        ss->kd_step = k;
+    }
+}
+
+// Restored history: K D_{k-h} = K (U^{k-h} - U^{k-h-1}) for h = 1 .. hist_len - 2 into the
+// increment-product ring (the step's own rows kernel adds K D_k).
+template <int NP>
+__global__ void __launch_bounds__(kBlock)
+history_products_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                        const double* __restrict__ val, const double* __restrict__ ring,
+                        double* __restrict__ kdring, int64_t n, int64_t nc, SimScalars* ss) {
+    const int64_t k = ss->k;
+    const int np_ = max(0, ss->hist_len - 2);      // increments D_{k-1} .. D_{k-np_}
+    const int lane = threadIdx.x & 31;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (e < nc && np_ > 0) {
+        const double* x[kHistDirs];
+        const double* w[kHistDirs];
+        for (int h = 0; h < kHistDirs; ++h) {
+            const int hh = 1 + min(h, np_ - 1);
+            x[h] = ring + ((k - hh) % kHistRing) * n;
+            w[h] = ring + ((k - hh - 1) % kHistRing) * n;
+        }
+        double t[kHistDirs];
+        multi_matvec_row<NP, kHistDirs>(row_ptr, col, val, e, x, w, np_, t);
+        if (lane < NP) {
+            const int64_t r = e * NP + lane;
+#pragma unroll
+            for (int h = 0; h < kHistDirs; ++h)
+                if (h < np_) kdring[((k - 1 - h) % kHistRing) * n + r] = t[h];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // as if steps k-np_ .. k-1 had stored theirs
+        ss->kd_len = np_;
+        ss->kd_step = k - 1;
+    }
+}
+
+// The dot products c_d = v_d . r0 and H_ij = v_i . K v_j (i <= j), per-CTA partial sums in
+// fixed row order; the last CTA adds them in CTA order and solves for theta by elimination
+// on the directions whose Schur-complement pivots stay above 1e-13 of the largest diagonal
+// (greedy, largest pivot first), the others left at zero.  The guess is used when it
+// lowers the K-norm of the error (gain c.theta > 0).
 constexpr int kGramThreads = 256;
 constexpr int kGramRows = 128;           // rows per shared-memory tile
 
 __global__ void __launch_bounds__(kGramThreads)
-subspace_gram_kernel(const double* __restrict__ W, int64_t n, double* gram, SimScalars* ss,
-                     int with_model) {
+subspace_gram_kernel(const double* __restrict__ W, const double* U, const double* xg,
+                     const double* ring, const double* kdring, int64_t n, double* gram,
+                     SimScalars* ss) {
     __shared__ double tile[2 * kSubMaxDirs + 1][kGramRows + 1];   // r0, K v_d, v_d
     __shared__ double Gs[kSubMaxPairs];
+    __shared__ SubDirs D;
+    __shared__ int snd;
     __shared__ bool last;
     if (ss->failed) return;
-    const int64_t k = ss->k;
-    const int nd = (with_model && k >= 2 ? 1 : 0) + min(kHistDirs, ss->hist_len - 1);
+    if (threadIdx.x == 0) snd = subspace_dirs(ss, U, xg, ring, kdring, W + n, n, D);
+    __syncthreads();
+    const int nd = snd;
     if (nd == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0) ss->use_guess = 0;
         return;
@@ -400,8 +464,13 @@ subspace_gram_kernel(const double* __restrict__ W, int64_t n, double* gram, SimS
         for (int idx = threadIdx.x; idx < nrow * kGramRows; idx += kGramThreads) {
             const int v = idx / kGramRows, q = idx - v * kGramRows;
             const int64_t r = r0 + q;
-            const int64_t col = v == 0 ? 0 : (v <= nd ? v : 1 + kSubMaxDirs + (v - 1 - nd));
-            tile[v][q] = (r < n) ? __ldcg(W + col * n + r) : 0.0;
+            double x = 0.0;
+            if (r < n) {
+                if (v == 0) x = __ldcg(W + r);
+                else if (v <= nd) x = __ldcg(D.kv[v - 1] + r);
+                else x = __ldcg(D.a[v - 1 - nd] + r) - __ldcg(D.b[v - 1 - nd] + r);
+            }
+            tile[v][q] = x;
         }
         __syncthreads();
         if (threadIdx.x < npair)
@@ -498,18 +567,17 @@ subspace_gram_kernel(const double* __restrict__ W, int64_t n, double* gram, SimS
 
 // x0 = U^k + sum_d theta_d v_d when the subspace guess is used, else U^k.
 __global__ void subspace_copy_kernel(const double* __restrict__ U, const double* xg,
-                                     const double* ring, double* __restrict__ x0, int64_t n,
-                                     const SimScalars* ss) {
-    __shared__ const double* sa[kSubMaxDirs];
-    __shared__ const double* sb[kSubMaxDirs];
+                                     const double* ring, const double* kdring, const double* kxg,
+                                     double* __restrict__ x0, int64_t n, const SimScalars* ss) {
+    __shared__ SubDirs D;
     __shared__ int snd;
     if (ss->failed) return;
-    if (threadIdx.x == 0) snd = ss->use_guess ? subspace_dirs(ss, U, xg, ring, n, sa, sb) : 0;
+    if (threadIdx.x == 0) snd = ss->use_guess ? subspace_dirs(ss, U, xg, ring, kdring, kxg, n, D) : 0;
     __syncthreads();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     double x = U[t];
-    for (int d = 0; d < snd; ++d) x = fma(ss->theta_sub[d], __ldcg(sa[d] + t) - __ldcg(sb[d] + t), x);
+    for (int d = 0; d < snd; ++d) x = fma(ss->theta_sub[d], __ldcg(D.a[d] + t) - __ldcg(D.b[d] + t), x);
     x0[t] = x;
 }
 
@@ -784,35 +852,48 @@ cudaError_t launch_select_copy(const double* uk, const double* xg, double* x0, i
 }
 
 cudaError_t launch_guess_subspace(int np, const DeviceMatrix& K, const double* b, const double* U,
-                                  const double* xg, const double* ring, double* W, double* gram,
-                                  int64_t n, SimScalars* ss, cudaStream_t s) {
+                                  const double* xg, const double* ring, double* kuring, double* W,
+                                  double* gram, int64_t n, SimScalars* ss, cudaStream_t s) {
     const unsigned grid = (unsigned)((K.nc * 32 + kBlock - 1) / kBlock);
     GUESS_NP_SWITCH(np, {
-        subspace_rows_kernel<NP><<<grid, kBlock, 0, s>>>(K.row_ptr, K.col, K.val, b, U, xg, ring, W,
-                                                         n, K.nc, ss);
+        subspace_rows_kernel<NP><<<grid, kBlock, 0, s>>>(K.row_ptr, K.col, K.val, b, U, xg, ring, kuring,
+                                                         W, n, K.nc, ss);
     })
     const unsigned g2 = (unsigned)std::min<int64_t>(kSubMaxCtas, (n + kGramRows - 1) / kGramRows);
-    subspace_gram_kernel<<<g2, kGramThreads, 0, s>>>(W, n, gram, ss, xg != nullptr ? 1 : 0);
+    subspace_gram_kernel<<<g2, kGramThreads, 0, s>>>(W, U, xg, ring, kuring, n, gram, ss);
     return cudaGetLastError();
 }
 
-cudaError_t launch_subspace_copy(const double* U, const double* xg, const double* ring, double* x0,
-                                 int64_t n, const SimScalars* ss, cudaStream_t s) {
-    subspace_copy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, xg, ring, x0, n, ss);
+cudaError_t launch_subspace_copy(const double* U, const double* xg, const double* ring,
+                                 const double* kuring, const double* W, double* x0, int64_t n,
+                                 const SimScalars* ss, cudaStream_t s) {
+    subspace_copy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, xg, ring, kuring, W + n, x0, n, ss);
     return cudaGetLastError();
 }
 
-cudaError_t launch_history_reset(double* ring, const double* U, const double* Uprev, int64_t n,
-                                 SimScalars* ss, cudaStream_t s) {
+cudaError_t launch_history_reset(int np, const DeviceMatrix& K, double* ring, double* kuring,
+                                 const double* U, const double* Uprev, int64_t n, SimScalars* ss,
+                                 cudaStream_t s) {
     history_reset_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ring, U, Uprev, n, ss);
+    const unsigned grid = (unsigned)((K.nc * 32 + kBlock - 1) / kBlock);
+    GUESS_NP_SWITCH(np, {
+        history_products_kernel<NP><<<grid, kBlock, 0, s>>>(K.row_ptr, K.col, K.val, ring, kuring, n,
+                                                            K.nc, ss);
+    })
     return cudaGetLastError();
 }
 
-cudaError_t launch_history_set(const double* hist, int count, double* ring, double* U, double* Uprev,
-                               double* Uprev2, const int64_t* to_caller, int64_t nc, int np,
-                               SimScalars* ss, cudaStream_t s) {
+cudaError_t launch_history_set(const DeviceMatrix& K, const double* hist, int count, double* ring,
+                               double* kuring, double* U, double* Uprev, double* Uprev2,
+                               const int64_t* to_caller, int64_t nc, int np, SimScalars* ss,
+                               cudaStream_t s) {
     history_set_kernel<<<(unsigned)((nc * np + 255) / 256), 256, 0, s>>>(hist, count, ring, U, Uprev,
                                                                        Uprev2, to_caller, nc, np, ss);
+    const unsigned grid = (unsigned)((K.nc * 32 + kBlock - 1) / kBlock);
+    GUESS_NP_SWITCH(np, {
+        history_products_kernel<NP><<<grid, kBlock, 0, s>>>(K.row_ptr, K.col, K.val, ring, kuring,
+                                                            nc * np, K.nc, ss);
+    })
     return cudaGetLastError();
 }
 
