@@ -488,15 +488,20 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
     peaks, peak_kind = measured_peaks()
     S = len(ws)
     per_mesh = 4
+    steps = min(args.steps, ws[0].n_steps - args.warmup)     # the workload's steps
+    guess = load_guess(pd)
 
-    def make(prec, flex):
+    def make(prec, flex, with_guess):
         out = []
         for w in ws:
             ctx = pd.polydg_setup(w.mesh.vertices, w.mesh.cell_ptr, w.mesh.cell_vtx, w.sigma,
                                   w.p, w.subdomain, w.chi_cm, w.dt, w.eta0)
             pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision=prec)
-            out.append((ctx, pc, pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus,
-                                               rtol=1e-8, maxit=5000, flexible=flex)))
+            sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-8,
+                                maxit=5000, flexible=flex)
+            if with_guess:
+                pd.sim_set_guess(sim, guess, GUESS_POLICY)
+            out.append((ctx, pc, sim))
         return out
 
     def timed_batch(trip, clocks=None):
@@ -510,7 +515,7 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
             clocks.__enter__()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        st, sec = pd.batch_step(bt, args.steps, stream)
+        st, sec = pd.batch_step(bt, steps, stream)
         ev1.record(stream)
         torch.cuda.synchronize()
         if clocks is not None:
@@ -518,7 +523,7 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
         return bt, st, sec, ev0.elapsed_time(ev1)
 
     # candidate: one bf16 eigenbasis per mesh shared by its 4 simulations (lockstep groups)
-    trip = make("fp32", True)
+    trip = make("fp32", True, True)
     t0 = time.perf_counter()
     shared = []
     for m0 in range(0, S, per_mesh):
@@ -529,7 +534,7 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
     t_eig = time.perf_counter() - t0
     clocks = ClockSampler(local)
     bt, st, sec, ms = timed_batch(trip, clocks)
-    its = [s_["total_iterations"] / args.steps for s_ in st]
+    its = [s_["total_iterations"] / steps for s_ in st]
     # algorithmic bytes: per group iteration the shared store once plus every member's K_h,
     # coarse and vectors; group iterations >= the largest member's
     alg = 0.0
@@ -544,40 +549,61 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
                        + inf["restrict_bytes"] + 12 * 8 * ctx.n_dofs)
         alg += g_its * per_it
     achieved = alg / (sec * 1e9)
-    # e2e: every simulation's potential through pinned host memory each step
+    # e2e: every simulation's state (the last 17 solutions the initial guess reads) through
+    # pinned host memory each step, the new potential back
     sims = [x[2] for x in trip]
     n_all = sum(ctx.n_dofs for ctx, _, _ in trip)
-    hu = [torch.empty(ctx.n_dofs, dtype=torch.float64).pin_memory() for ctx, _, _ in trip]
+    H = 17
+    hh = [torch.zeros((H, ctx.n_dofs), dtype=torch.float64).pin_memory() for ctx, _, _ in trip]
+    dh = [torch.empty((H, ctx.n_dofs), dtype=torch.float64, device="cuda") for ctx, _, _ in trip]
     du = [torch.empty(ctx.n_dofs, dtype=torch.float64, device="cuda") for ctx, _, _ in trip]
-    for s_, d_, h_ in zip(sims, du, hu):
-        pd.sim_get_state(s_, d_, stream=stream)
-        h_.copy_(d_)
+    hn = [torch.empty(ctx.n_dofs, dtype=torch.float64).pin_memory() for ctx, _, _ in trip]
+    # a fresh batch of the same form, its warm-up steps recorded on the host
+    del bt
+    trip_e = make("fp32", True, True)
+    for m0 in range(0, S, per_mesh):
+        for k in range(m0, m0 + per_mesh):
+            pd.sim_set_shared_local(trip_e[k][2], shared[m0 // per_mesh])
+    sims = [x[2] for x in trip_e]
+    bt = pd.batch_create(sims)
+    count = 0
+    for _ in range(args.warmup):
+        pd.batch_step(bt, 1, stream)
+        for s_, d_, h_ in zip(sims, du, hh):
+            pd.sim_get_state(s_, d_, stream=stream)
+            h_[1:].copy_(h_[:-1].clone())
+            h_[0].copy_(d_)
+        count = min(H, count + 1)
     torch.cuda.synchronize()
-    e_steps = max(2, args.steps // 4)
+    e_steps = steps
     t0 = time.perf_counter()
     for _ in range(e_steps):
-        for s_, d_, h_ in zip(sims, du, hu):
+        for s_, d_, h_ in zip(sims, dh, hh):
             d_.copy_(h_, non_blocking=True)
-            pd.sim_set_potential(s_, d_, None, stream)
+            pd.sim_set_history(s_, d_[:count], stream)
         pd.batch_step(bt, 1, stream)
-        for s_, d_, h_ in zip(sims, du, hu):
+        for s_, d_, h_ in zip(sims, du, hn):
             pd.sim_get_state(s_, d_, stream=stream)
             h_.copy_(d_, non_blocking=True)
         torch.cuda.synchronize()
+        for h_, n_ in zip(hh, hn):
+            h_[1:].copy_(h_[:-1].clone())
+            h_[0].copy_(n_)
+        count = min(H, count + 1)
     e2e_rate = S * e_steps / (time.perf_counter() - t0)
     groups = bt.groups().tolist()
     bt.close()
-    del trip, sims, shared, du, hu
+    del trip, trip_e, sims, shared, du, dh, hh, hn
     torch.cuda.empty_cache()
     # the same simulations with their own fp32 local inverses, one CTA group each
-    trip32 = make("fp32", True)
+    trip32 = make("fp32", True, True)
     bt32, st32, _, ms32 = timed_batch(trip32)
-    its32 = [s_["total_iterations"] / args.steps for s_ in st32]
+    its32 = [s_["total_iterations"] / steps for s_ in st32]
     bt32.close()
     del trip32
     torch.cuda.empty_cache()
     # baseline: fp64 plain form, one simulation after another
-    trip64 = make("fp64", False)
+    trip64 = make("fp64", False, False)
     for _, _, s_ in trip64:
         pd.monodomain_step(s_, args.warmup, stream)
     torch.cuda.synchronize()
@@ -585,15 +611,15 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
     ev0.record(stream)
     its64 = []
     for _, _, s_ in trip64:
-        its64.append(pd.monodomain_step(s_, args.steps, stream)["total_iterations"] / args.steps)
+        its64.append(pd.monodomain_step(s_, steps, stream)["total_iterations"] / steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms64 = ev0.elapsed_time(ev1)
     (ms, ms32, ms64), (e2e_rate,) = reduce_over_ranks(torch, [ms, ms32, ms64], [e2e_rate], world, "cuda")
     e2e_val = world * e2e_rate
-    value = world * S * args.steps / (ms * 1e-3)
-    value32 = world * S * args.steps / (ms32 * 1e-3)
-    value64 = world * S * args.steps / (ms64 * 1e-3)
+    value = world * S * steps / (ms * 1e-3)
+    value32 = world * S * steps / (ms32 * 1e-3)
+    value64 = world * S * steps / (ms64 * 1e-3)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # oracle on the smallest mesh's first simulation, scaled by DOFs to all 32
@@ -607,14 +633,16 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
                          f"{its64[k]:.0f} iterations), scaled by DOFs to all 32 simulations"}
     line = {
         "metric": METRIC + " (batched form)", "value": value, "unit": "simulation-steps/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32+bf16", "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD,
-                   "form": "batched + shared eigenbasis: the 4 simulations of each mesh solve in "
-                           "lockstep, each subdomain's local solves one bf16 pass over Q_i^T and "
-                           "one over Q_i for all 4 (flexible PCG, fp64 residual/dots/coarse/matvec); "
-                           "one persistent launch per step, captured step graph",
+                   "form": "batched + shared eigenbasis + learned: the 4 simulations of each mesh "
+                           "solve in lockstep, each subdomain's local solves one bf16 pass over Q_i^T "
+                           "and one over Q_i for all 4 (flexible PCG, fp64 residual/dots/coarse/"
+                           "matvec); every simulation's initial guess the Galerkin projection onto "
+                           "the network's proposal and its last 16 solution increments; one "
+                           "persistent launch per step, captured step graph",
                    "cells": [w.mesh.n_cells for w in ws[::per_mesh]], "dofs": n_all,
                    "ctas_per_sim": groups, "iterations_per_step": its,
                    "eigenbasis_setup_s": t_eig,
@@ -626,8 +654,8 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
                    "l2": "working set > L2 (no flush needed)", "parallelism": f"replicas x{world}"},
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_val, "unit": "simulation-steps/s",
-                "h2d_bytes_per_step": 8 * n_all, "d2h_bytes_per_step": 8 * n_all},
-        "gpu_launches": (6 * S + 1) * args.steps,
+                "h2d_bytes_per_step": 17 * 8 * n_all, "d2h_bytes_per_step": 8 * n_all},
+        "gpu_launches": ((9 if guess is not None else 8) * S + 1) * steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                      "kernel": "pcg_group_kernel<bf16 store, n_p=10> (whole step time)",
