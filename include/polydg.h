@@ -386,11 +386,10 @@ void guess_destroy(guess_model *model);
 
 /* Invert `batch` symmetric positive definite float64 matrices in place, without
  * allocating any device memory.  The paper has no counterpart: this serves callers
- * that cannot call cudaMalloc -- code running while a CUDA graph is being captured
- * (allocation is not allowed during capture), processes whose device memory belongs
- * to another allocator (a framework's caching allocator, a fixed arena in an
- * embedded or real-time runtime), and code that must not fail on allocation in the
- * middle of a time step.  It runs the same Cholesky-based kernel that asm_setup
+ * that cannot call cudaMalloc -- processes whose device memory belongs to another
+ * allocator (a framework's caching allocator, or a fixed arena reserved up front by an
+ * embedded or real-time runtime, where a stray cudaMalloc would take memory the arena
+ * counted on), and code that must not fail on allocation in the middle of a time step.  It runs the same Cholesky-based kernel that asm_setup
  * uses for K_i^{-1} and K_0^{-1}.
  *   mats_dev: device pointer to batch row-major matrices of order n with leading
  *             dimension ld, matrix m starting at mats_dev + m * n * ld; overwritten

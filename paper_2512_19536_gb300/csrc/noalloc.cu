@@ -1,11 +1,11 @@
 // polydg_spd_inverse_static: in-place inversion of a batch of symmetric positive
 // definite float64 matrices, for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being
-// captured (allocation is not allowed there), processes whose device memory is
-// owned by another allocator (a framework's caching allocator, a fixed arena in
-// an embedded or real-time runtime), or code that must not fail on allocation in
-// the middle of a time step.  This entry point needs nothing from them but the
+// Some callers cannot call cudaMalloc: processes whose device memory is owned by
+// another allocator (a framework's caching allocator, or a fixed arena reserved up
+// front by an embedded or real-time runtime, where a stray cudaMalloc would take
+// memory the arena counted on), or code that must not fail on allocation in the
+// middle of a time step.  This entry point needs nothing from them but the
 // matrices: the kernel's workspace lives in one file-scope static device array
 // of fixed size, set aside when the library is loaded.
 //

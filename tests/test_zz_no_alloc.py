@@ -1,8 +1,8 @@
 """polydg_spd_inverse_static: batched SPD inversion that allocates no device memory.
 
-Some callers of this library cannot call cudaMalloc: code running inside CUDA graph
-capture, processes whose device memory belongs to another allocator, code that must
-not fail on allocation mid-step.  This entry point keeps its workspace in one fixed
+Some callers of this library cannot call cudaMalloc: processes whose device memory
+belongs to another allocator (a caching allocator, a fixed arena reserved up front),
+and code that must not fail on allocation mid-step.  This entry point keeps its workspace in one fixed
 static device array.  Its output is checked, on two calls in a row, against the
 library's existing inverse path: with one subdomain and no coarse space, asm_apply
 applies K^{-1} (formed by asm_setup with the same Cholesky kernel), so asm_apply on
