@@ -74,3 +74,54 @@ def test_preconditioned_spectrum_real_positive():
     BK = np.stack([S.apply(col) for col in d.K.toarray().T], 1)
     ev = np.linalg.eigvals(BK)
     assert np.abs(ev.imag).max() < 1e-8 and ev.real.min() > 0
+
+
+# ---- the massively parallel case of Sec. 4: every subdomain one fine element (T_S = T_h)
+
+def test_massively_parallel_with_fine_coarse_space_closed_form():
+    # T_S = T_h and the coarse cells are the fine elements with q = p: psi_J is the
+    # fine modal basis on the same bounding box, so T_K = M_K^{-1} M_K = I, R_0^T = I,
+    # K_0 = K and B_ad^{-1} = blockdiag(K_KK)^{-1} + K^{-1} (Eq. prec written out).
+    m, d = small()
+    cells = np.arange(m.n_cells, dtype=np.int32)
+    S = schwarz.build(d, cells, cells, d.p)
+    assert np.allclose(S.R0T.toarray(), np.eye(d.n_dofs), atol=1e-12)
+    r = np.random.default_rng(11).standard_normal(d.n_dofs)
+    Kd = d.K.toarray()
+    n = d.n_p
+    local = np.concatenate([sla.solve(Kd[k * n:(k + 1) * n, k * n:(k + 1) * n], r[k * n:(k + 1) * n])
+                            for k in range(m.n_cells)])
+    expect = local + np.linalg.solve(Kd, r)
+    assert np.allclose(S.apply(r), expect, rtol=1e-10, atol=1e-13)
+
+
+def test_massively_parallel_coarse_correction_is_k_orthogonal_projection(voronoi256):
+    # Q = R_0^T K_0^{-1} R_0 K with K_0 = R_0 K R_0^T: Q^2 = Q and K Q symmetric, for a
+    # coarse space of degree 1 and of degree q = p on the k-means agglomerates, with
+    # every fine element its own subdomain.  A transposed R_0 or a wrong K_0 breaks both.
+    w, d = voronoi256
+    cells = np.arange(w.mesh.n_cells, dtype=np.int32)
+    K = d.K.toarray()
+    for q in (1, d.p):
+        S = schwarz.build(d, cells, w.coarse, q)
+        R0T = S.R0T.toarray()
+        Q = R0T @ sla.cho_solve(S.K0_chol, R0T.T @ K)
+        assert np.abs(Q @ Q - Q).max() <= 1e-8 * np.abs(Q).max()
+        KQ = K @ Q
+        assert np.abs(KQ - KQ.T).max() <= 1e-8 * np.abs(KQ).max()
+
+
+def test_massively_parallel_spectrum_bounded_by_colouring():
+    # Non-overlapping element subspaces on a Cartesian mesh are two-colourable (elements
+    # of one colour share no face, so their K-projections are mutually K-orthogonal and
+    # sum to a projection): lambda_max(B K) <= 2 + 1 (coarse projection).  The lower
+    # end is positive (B SPD).  Block Jacobi alone is bounded by 2.
+    m, d = small()
+    cells = np.arange(m.n_cells, dtype=np.int32)
+    K = d.K.toarray()
+    for coarse, bound in ((None, 2.0), (block_partition(4, 2), 3.0)):
+        S = schwarz.build(d, cells, coarse, d.p if coarse is not None else 1)
+        BK = np.stack([S.apply(col) for col in K.T], 1)
+        ev = np.linalg.eigvals(BK)
+        assert np.abs(ev.imag).max() < 1e-8
+        assert 0 < ev.real.min() and ev.real.max() <= bound + 1e-10
