@@ -257,7 +257,8 @@ int pcg_solve_trace(polydg_ctx *ctx, asm_ctx *pc, const double *b_dev, double *x
 /* Extreme eigenvalues of the Lanczos tridiagonal T of m PCG steps (host): T_kk =
  * 1/alpha_k + beta_{k-1}/alpha_{k-1}, T_{k,k+1} = sqrt(beta_k)/alpha_k (Saad, Iterative
  * Methods, Sec. 6.7.3); estimates of lambda_min, lambda_max of the preconditioned
- * operator, kappa = lmax / lmin.  Returns POLYDG_OK, EINVAL or ENOTCONV. */
+ * operator, kappa = lmax / lmin, found by bisection on Sturm counts of T (O(m) memory
+ * and work per bisection step).  Returns POLYDG_OK or EINVAL. */
 int pcg_lanczos_extremes(const double *alphas, const double *betas, int m, double *lmin,
                          double *lmax);
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <string>
 #include <utility>
@@ -994,30 +995,65 @@ int pcg_solve(polydg_ctx* c, asm_ctx* pc, const double* b_dev, double* x_dev, do
                            nullptr, 0);
 }
 
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x: the negative
+// pivots of the LDL^T factorisation of T - x I (Sylvester's law of inertia), with a
+// zero pivot replaced by -pivmin.
+static int sturm_count(const std::vector<double>& d, const std::vector<double>& e2, double x,
+                       double pivmin) {
+    int neg = 0;
+    double q = d[0] - x;
+    if (std::fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++neg;
+    for (size_t k = 1; k < d.size(); ++k) {
+        q = d[k] - x - e2[k - 1] / q;
+        if (std::fabs(q) < pivmin) q = -pivmin;
+        if (q < 0.0) ++neg;
+    }
+    return neg;
+}
+
 int pcg_lanczos_extremes(const double* alphas, const double* betas, int m, double* lmin, double* lmax) {
     if (m < 1 || !alphas || !betas || !lmin || !lmax) {
         set_error("pcg_lanczos_extremes: need m >= 1 coefficients and output pointers");
         return POLYDG_EINVAL;
     }
     // T_kk = 1/alpha_k + beta_{k-1}/alpha_{k-1}, T_{k,k+1} = sqrt(beta_k)/alpha_k
-    std::vector<double> T((size_t)m * m, 0.0), w(m), q((size_t)m * m);
+    std::vector<double> d(m), e2(m > 1 ? m - 1 : 1, 0.0);
     for (int k = 0; k < m; ++k) {
-        if (!(alphas[k] > 0.0) || (k < m - 1 && !(betas[k] >= 0.0))) {
+        if (!(alphas[k] > 0.0) || (k < m - 1 && !(betas[k] >= 0.0)) || !std::isfinite(alphas[k])) {
             set_error("pcg_lanczos_extremes: alphas must be > 0 and betas >= 0");
             return POLYDG_EINVAL;
         }
-        T[(size_t)k * m + k] = 1.0 / alphas[k] + (k > 0 ? betas[k - 1] / alphas[k - 1] : 0.0);
-        if (k < m - 1) {
-            const double e = std::sqrt(betas[k]) / alphas[k];
-            T[(size_t)k * m + k + 1] = T[(size_t)(k + 1) * m + k] = e;
+        d[k] = 1.0 / alphas[k] + (k > 0 ? betas[k - 1] / alphas[k - 1] : 0.0);
+        if (k < m - 1) e2[k] = betas[k] / (alphas[k] * alphas[k]);
+    }
+    // the two extreme eigenvalues by bisection on Sturm counts inside the Gershgorin
+    // interval: O(m) per step, accurate to a few ulps of |T| (the tridiagonal is never
+    // formed densely, so traces of many thousand iterations cost milliseconds)
+    double lo = d[0], hi = d[0], tmax = 0.0;
+    for (int k = 0; k < m; ++k) {
+        const double r = (k > 0 ? std::sqrt(e2[k - 1]) : 0.0) + (k < m - 1 ? std::sqrt(e2[k]) : 0.0);
+        lo = std::min(lo, d[k] - r);
+        hi = std::max(hi, d[k] + r);
+        tmax = std::max(tmax, std::fabs(d[k]) + r);
+    }
+    if (!std::isfinite(lo) || !std::isfinite(hi)) {
+        set_error("pcg_lanczos_extremes: non-finite coefficients");
+        return POLYDG_EINVAL;
+    }
+    const double eps = std::numeric_limits<double>::epsilon();
+    const double pivmin = std::max(std::numeric_limits<double>::min(), eps * eps * tmax * tmax);
+    auto bisect = [&](int target) {       // smallest x with count(x) >= target
+        double a = lo - eps * tmax, b = hi + eps * tmax;
+        for (int it = 0; it < 200 && b - a > 2.0 * eps * std::max(std::fabs(a), std::fabs(b)); ++it) {
+            const double mid = 0.5 * (a + b);
+            if (mid <= a || mid >= b) break;
+            if (sturm_count(d, e2, mid, pivmin) >= target) b = mid; else a = mid;
         }
-    }
-    if (!sym_eig(m, T.data(), w.data(), q.data())) {
-        set_error("pcg_lanczos_extremes: eigenvalue iteration did not converge");
-        return POLYDG_ENOTCONV;
-    }
-    *lmin = w[0];
-    *lmax = w[m - 1];
+        return 0.5 * (a + b);
+    };
+    *lmin = bisect(1);
+    *lmax = bisect(m);
     return POLYDG_OK;
 }
 

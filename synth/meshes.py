@@ -195,7 +195,11 @@ def cell_points(mesh: Mesh) -> np.ndarray:
 
 def kmeans_partition(mesh: Mesh, k: int, seed: int, iters: int = 30) -> np.ndarray:
     """Seeded k-means of cell vertex-averages; ties go to the lowest cluster id."""
-    pts = cell_points(mesh)
+    return kmeans_points(cell_points(mesh), k, seed, iters)
+
+
+def kmeans_points(pts: np.ndarray, k: int, seed: int, iters: int = 30) -> np.ndarray:
+    """Seeded k-means labels of points [n, dim], dense ids by first appearance."""
     rng = _rng(seed)
     centres = pts[rng.choice(len(pts), size=k, replace=False)].copy()
     lab = np.zeros(len(pts), dtype=np.int32)

@@ -20,3 +20,25 @@ def test_lanczos_extremes_match_oracle_and_spectrum():
     olo, ohi = oracle_extremes(r.alphas, r.betas)
     assert abs(lo - olo) <= 1e-10 * abs(olo) and abs(hi - ohi) <= 1e-10 * abs(ohi)
     assert abs(lo - 0.5) <= 1e-6 and abs(hi - 40.0) <= 1e-6
+
+
+def test_lanczos_extremes_long_traces_match_tridiagonal_eigensolver():
+    # traces of tens of thousands of iterations (unpreconditioned CG at p = 4): the
+    # library's extremes against LAPACK's tridiagonal bisection on the same T
+    import time
+    import scipy.linalg as sla
+    ensure_built()
+    from paper_2512_19536_gb300._native import lanczos_extremes
+    rng = np.random.default_rng(12)
+    m = 40000
+    al = rng.uniform(1e-6, 1.0, m)
+    be = rng.uniform(0.0, 0.99, m - 1)
+    d = 1.0 / al + np.concatenate([[0.0], be / al[:-1]])
+    e = np.sqrt(be) / al[:-1]
+    t0 = time.time()
+    lo, hi = lanczos_extremes(al, be)
+    assert time.time() - t0 < 5.0
+    ref_lo = sla.eigvalsh_tridiagonal(d, e, select="i", select_range=(0, 0))[0]
+    ref_hi = sla.eigvalsh_tridiagonal(d, e, select="i", select_range=(m - 1, m - 1))[0]
+    assert abs(hi - ref_hi) <= 1e-12 * abs(ref_hi)
+    assert abs(lo - ref_lo) <= 1e-12 * abs(ref_hi)        # absolute accuracy ~ eps |T|
