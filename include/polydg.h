@@ -206,8 +206,8 @@ int polydg_matvec(polydg_ctx *ctx, const double *x_dev, double *y_dev, void *str
 /* Build the two-level additive Schwarz preconditioner of Eq. prec on the
  * subdomains given to polydg_setup.  coarse_of_cell (host, [n_cells]) assigns
  * every cell to an agglomerate of T_H (ids 0..N_0-1, all used); NULL builds
- * the one-level operator (no coarse space).  q (1 <= q <= p) is the coarse
- * degree.  The local inverses K_i^{-1} are formed in float64 on the device by
+ * the one-level operator (no coarse space).  q (1 <= q <= p; at most 4 in 2D and 2
+ * in 3D) is the coarse degree.  The local inverses K_i^{-1} are formed in float64 on the device by
  * Cholesky factorisation and stored in `precision` (POLYDG_FP64/FP32/BF16);
  * the coarse inverse K_0^{-1} is always float64.  R_0 is the Euclidean
  * transpose of R_0^T, so B_ad is symmetric.  Errors: EINVAL, ENOTSPD, ENOMEM,

@@ -97,7 +97,7 @@ static int partition_tiles(Plan& P, const asm_ctx* pc, int G, const std::vector<
             else
                 runs.push_back({t.block, t.row0, end, 0});
         }
-        if ((int32_t)runs.size() - run_ptr[g] > 128) {
+        if (!P.small && (int32_t)runs.size() - run_ptr[g] > 128) {
             set_error("pcg: a CTA would stream more than 128 subdomains; too many subdomains for the CTAs");
             return POLYDG_EINVAL;
         }
@@ -214,7 +214,19 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 
     }
     P.wstages = (int)std::min<int64_t>(kMaxWarpStages, wst);
     P.slot_bytes = slot;
-    P.rows = 16;                                 // partition granularity (rows per tile)
+    // subdomains of at most 32 DOFs (one element each in the massively parallel case,
+    // T_S = T_h): whole subdomains go to warps, one lane per row, and the CTA reads its
+    // runs from global memory (no shared-memory run table, no bulk row copies)
+    P.small = 0;
+    if (pc && !local_ids.empty()) {
+        int max_rows = 0;
+        for (int b : local_ids) max_rows = std::max(max_rows, (int)pc->blocks[b].nrows);
+        P.small = max_rows <= 32 ? 1 : 0;
+    }
+    P.pair_lanes = 1;
+    if (pc && pc->has_coarse)
+        while (P.pair_lanes < 32 && P.pair_lanes < pc->max_pairs) P.pair_lanes *= 2;
+    P.rows = P.small ? 32 : 16;                  // partition granularity (rows per tile)
     const int rows = P.rows;
     P.xs_off = (size_t)NW * P.wstages * slot;
     P.rp_off = P.xs_off + r128((size_t)max_ld * xsz);
@@ -293,6 +305,8 @@ static PersistArgs persist_args(polydg_ctx* c, asm_ctx* pc, const Plan& P, PcgWo
     a.nc = c->H.nc;
     a.slot_bytes = P.slot_bytes;
     a.redundant = P.redundant;
+    a.small = P.small;
+    a.pair_lanes = P.pair_lanes;
     a.l2_keep = P.l2_keep;
     a.xs_off = P.xs_off;
     a.rp_off = P.rp_off;
@@ -499,8 +513,8 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
     CoarseSetup C;
     if (coarse_of_cell) {
         if (int st = coarse_setup(H, coarse_of_cell, q, C)) return st;
-        if (C.n_q != 3 && C.n_q != 4 && C.n_q != 6 && C.n_q != 10) {
-            set_error("asm_setup: coarse degree q must be 1..3 (2D) or 1..2 (3D)");
+        if (C.n_q != 3 && C.n_q != 4 && C.n_q != 6 && C.n_q != 10 && !(C.n_q == 15 && H.dim == 2)) {
+            set_error("asm_setup: coarse degree q must be 1..4 (2D) or 1..2 (3D)");
             return POLYDG_EINVAL;
         }
     }
@@ -673,6 +687,7 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
                         R[(int64_t)a * B.ld + c0 + kk] = C.T[(e * np + kk) * C.n_q + a];
             }
         }
+        for (int J = 0; J < C.n_agg; ++J) pc->max_pairs = std::max(pc->max_pairs, (int)pair_ptr[J + 1]);
         for (int J = 0; J < C.n_agg; ++J) pair_ptr[J + 1] += pair_ptr[J];
         pc->n_pairs = (int)rblocks.size();
         // grow st64 to hold the R blocks

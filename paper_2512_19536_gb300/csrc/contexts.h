@@ -83,6 +83,8 @@ struct Plan {
     int grid = 0, rows = 1, dtype = 0;
     int redundant = 1;
     int wstages = 1;
+    int small = 0;                      // every subdomain <= 32 DOFs: one warp per subdomain
+    int pair_lanes = 1;                 // lanes summing one coarse DOF's pair partials
     float l2_keep = 0.f;                // fraction of the local-inverse lines kept in L2
     size_t smem = 0, slot_bytes = 0, xs_off = 0, rp_off = 0, r0_off = 0, y0_off = 0,
            pn_off = 0, td_off = 0;
@@ -150,6 +152,7 @@ struct asm_ctx {
     double* d_T = nullptr;
     int32_t* d_agg = nullptr;
     int64_t* d_pair_ptr = nullptr;
+    int max_pairs = 0;                  // most (agglomerate, subdomain) pairs of one agglomerate
     double* d_r0p = nullptr;
     double* d_q0p = nullptr;
     double* d_y0 = nullptr;

@@ -96,6 +96,8 @@ struct GridSync {
 // are CSR arrays indexed by blockIdx.x.
 struct PersistArgs {
     int grid, wstages, identity, n0, ld0, nq, redundant;
+    int small;                                 // every subdomain <= 32 DOFs: a warp per subdomain
+    int pair_lanes;                            // lanes (power of 2) summing one coarse DOF's pairs
     float l2_keep;                             // fraction of the local-inverse lines kept in L2
     int64_t nc;
     // shared-memory carve-up (byte offsets): wstages copy slots of slot_bytes per warp

@@ -806,6 +806,17 @@ size_t guess_train_smem(int np) {
         default: return cudaErrorInvalidValue;                  \
     }
 
+// the K_h row kernels (history products, subspace rows) hold no network: every n_p of
+// the block-sparse operator, including n_p = 15 (2D P4)
+#define KROW_NP_SWITCH(np, ...)                                 \
+    switch (np) {                                               \
+        case 3: { constexpr int NP = 3; __VA_ARGS__; } break;   \
+        case 6: { constexpr int NP = 6; __VA_ARGS__; } break;   \
+        case 10: { constexpr int NP = 10; __VA_ARGS__; } break; \
+        case 15: { constexpr int NP = 15; __VA_ARGS__; } break; \
+        default: return cudaErrorInvalidValue;                  \
+    }
+
 // Raise the shared-memory limits of the inference and training kernels for n_p (once,
 // before any launch, so that launches can be recorded into CUDA graphs).
 cudaError_t guess_prepare(int np) {
@@ -855,7 +866,7 @@ cudaError_t launch_guess_subspace(int np, const DeviceMatrix& K, const double* b
                                   const double* xg, const double* ring, double* kuring, double* W,
                                   double* gram, int64_t n, SimScalars* ss, cudaStream_t s) {
     const unsigned grid = (unsigned)((K.nc * 32 + kBlock - 1) / kBlock);
-    GUESS_NP_SWITCH(np, {
+    KROW_NP_SWITCH(np, {
         subspace_rows_kernel<NP><<<grid, kBlock, 0, s>>>(K.row_ptr, K.col, K.val, b, U, xg, ring, kuring,
                                                          W, n, K.nc, ss);
     })
@@ -876,7 +887,7 @@ cudaError_t launch_history_reset(int np, const DeviceMatrix& K, double* ring, do
                                  cudaStream_t s) {
     history_reset_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ring, U, Uprev, n, ss);
     const unsigned grid = (unsigned)((K.nc * 32 + kBlock - 1) / kBlock);
-    GUESS_NP_SWITCH(np, {
+    KROW_NP_SWITCH(np, {
         history_products_kernel<NP><<<grid, kBlock, 0, s>>>(K.row_ptr, K.col, K.val, ring, kuring, n,
                                                             K.nc, ss);
     })
@@ -890,7 +901,7 @@ cudaError_t launch_history_set(const DeviceMatrix& K, const double* hist, int co
     history_set_kernel<<<(unsigned)((nc * np + 255) / 256), 256, 0, s>>>(hist, count, ring, U, Uprev,
                                                                        Uprev2, to_caller, nc, np, ss);
     const unsigned grid = (unsigned)((K.nc * 32 + kBlock - 1) / kBlock);
-    GUESS_NP_SWITCH(np, {
+    KROW_NP_SWITCH(np, {
         history_products_kernel<NP><<<grid, kBlock, 0, s>>>(K.row_ptr, K.col, K.val, ring, kuring,
                                                             nc * np, K.nc, ss);
     })

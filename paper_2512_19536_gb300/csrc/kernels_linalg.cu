@@ -763,6 +763,7 @@ cudaError_t launch_direction(int nq, double* p, const double* zl, const double* 
         case 4: direction_kernel<4><<<g, kBlock, 0, s>>>(p, zl, T, agg, y0, nc, np, sc, out); break;
         case 6: direction_kernel<6><<<g, kBlock, 0, s>>>(p, zl, T, agg, y0, nc, np, sc, out); break;
         case 10: direction_kernel<10><<<g, kBlock, 0, s>>>(p, zl, T, agg, y0, nc, np, sc, out); break;
+        case 15: direction_kernel<15><<<g, kBlock, 0, s>>>(p, zl, T, agg, y0, nc, np, sc, out); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

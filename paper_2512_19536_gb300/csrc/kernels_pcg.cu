@@ -98,7 +98,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
     // turn: warp w owns the rows at positions w, w + NW, ... of that sequence and
     // streams them, one row per copy, through its own ring of S slots.
     int n_rows = 0;
-    for (int k = 0; k < nruns; ++k) {
+    for (int k = 0; k < (a.small ? 0 : nruns); ++k) {   // small subdomains: no run table, no copies
         const GemvRun rn = a.runs[run0 + k];
         if ((k & (blockDim.x - 1)) == (int)threadIdx.x) {
             const GemvBlock B = a.blocks[rn.block];
@@ -188,6 +188,41 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 a.zl[t] = r_;
                 v1[0] = fma(r_, r_, v1[0]);
             }
+        } else if (a.small) {
+            // whole subdomains of at most 32 DOFs, one per warp at a time: lane j commits
+            // DOF j (p_k, q_k, x, r'), then computes row j of K_i^{-1} r' and row j of each
+            // restriction block with r' broadcast by shuffles (no CTA barrier, no copies)
+            for (int k = warp; k < nruns; k += nw) {
+                const GemvRun rn = a.runs[run0 + k];
+                const GemvBlock B = a.blocks[rn.block];
+                const int n = B.ncols;
+                const int64_t t = B.in_off + lane;
+                double r_ = 0.0;
+                if (lane < n) {
+                    const double qk = fma(be, __ldcg(qold + t), __ldcg(a.w + t));
+                    r_ = fma(-al, qk, __ldcg(rin + t));
+                    const double pk = fma(be, __ldcg(pold + t), __ldcg(a.z + t));
+                    pnew[t] = pk;
+                    qnew[t] = qk;
+                    a.x[t] = fma(al, pk, a.x[t]);
+                    rout[t] = r_;
+                    v1[0] = fma(r_, r_, v1[0]);
+                }
+                const X xr = (X)r_;
+                const T* Ar = reinterpret_cast<const T*>(a.store) + B.mat_off + (int64_t)min(lane, n - 1) * B.ld;
+                X acc = (X)0;
+                for (int c = 0; c < n; ++c) acc = fma_x(store_elem(Ar + c), __shfl_sync(0xffffffffu, xr, c), acc);
+                if (lane < n) a.zl[t] = (double)acc;
+                if (coarse) {
+                    for (int pi = 0; pi < B.pair_count; ++pi) {
+                        const GemvBlock R = a.blocks[a.sub_pairs[B.pair_begin + pi]];
+                        const double* Rr = a.st64 + R.mat_off + (int64_t)min(lane, R.nrows - 1) * R.ld;
+                        double sv = 0.0;
+                        for (int c = 0; c < R.ncols; ++c) sv = fma(__ldg(Rr + c), __shfl_sync(0xffffffffu, r_, c), sv);
+                        if (lane < R.nrows) a.r0p[R.out_off + lane] = sv;
+                    }
+                }
+            }
         } else {
             for (int ri = 0; ri < nruns; ++ri) {
                 const RunDesc& rn = rd[ri];
@@ -254,10 +289,13 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         }
         if (threadIdx.x == 0 && n_own > 0) {     // K_h rows of the CM phase's first chunk into L2
             const int64_t pe1 = a.chunk_elem[ch0 + 1];
-            const char* lo = reinterpret_cast<const char*>(a.val + (int64_t)a.row_ptr[e0] * NP * NP);
-            const char* hi = reinterpret_cast<const char*>(a.val + (int64_t)a.row_ptr[pe1] * NP * NP);
-            for (const char* c = lo; c < hi; c += 65536)
-                prefetch_l2(c, (uint32_t)min((int64_t)65536, (int64_t)(hi - c)));
+            // a bulk prefetch takes a 16-byte aligned address and a multiple of 16 bytes;
+            // an n_p x n_p fp64 block is 8 bytes short of that for odd n_p (3, 15), so both
+            // ends are rounded down (val itself is 256-byte aligned: lo stays inside it)
+            const uintptr_t lo = reinterpret_cast<uintptr_t>(a.val + (int64_t)a.row_ptr[e0] * NP * NP) & ~(uintptr_t)15;
+            const uintptr_t hi = reinterpret_cast<uintptr_t>(a.val + (int64_t)a.row_ptr[pe1] * NP * NP) & ~(uintptr_t)15;
+            for (uintptr_t c = lo; c < hi; c += 65536)
+                prefetch_l2(reinterpret_cast<const void*>(c), (uint32_t)min((uintptr_t)65536, hi - c));
         }
         // stopping test by thread 0: 0 go on, 1 converged, 2 non-finite, 3 maxit
         if (timing) {
@@ -284,12 +322,22 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         // ---------------------------------------------------------------- coarse
         if (coarse) {
             if (a.redundant || c1 > c0) {
-                for (int idx = threadIdx.x; idx < a.n0; idx += blockDim.x) {
-                    const int J = idx / a.nq, kq = idx - J * a.nq;
+                // R_0 r' = the pair partials summed per coarse DOF, by groups of L lanes
+                // (L = pair_lanes, a power of 2 covering the largest agglomerate's pair
+                // count, up to 32) and a shuffle tree: the same order in every CTA, so
+                // every CTA holds the same bits
+                const int L = a.pair_lanes, gl = lane & (L - 1);
+                const int per_pass = (int)blockDim.x / L;
+                for (int base = 0; base < a.n0; base += per_pass) {
+                    const int idx = base + (int)threadIdx.x / L;
                     double s_r = 0.0;
-                    for (int64_t p2 = a.pair_ptr[J]; p2 < a.pair_ptr[J + 1]; ++p2)
-                        s_r += __ldcg(a.r0p + p2 * a.nq + kq);
-                    r0s[idx] = s_r;
+                    if (idx < a.n0) {
+                        const int J = idx / a.nq, kq = idx - J * a.nq;
+                        for (int64_t p2 = a.pair_ptr[J] + gl; p2 < a.pair_ptr[J + 1]; p2 += L)
+                            s_r += __ldcg(a.r0p + p2 * a.nq + kq);
+                    }
+                    for (int o = L >> 1; o > 0; o >>= 1) s_r += __shfl_xor_sync(0xffffffffu, s_r, o);
+                    if (idx < a.n0 && gl == 0) r0s[idx] = s_r;
                 }
                 __syncthreads();
             }

@@ -214,6 +214,14 @@ __device__ __forceinline__ double row_dot(const __nv_bfloat16* Ar, const float* 
     return lane == 0 ? (double)sum : 0.0;
 }
 
+// One element of a stored local-inverse row, in the store's arithmetic (the same
+// rounding as the row_dot forms above: fp64, or fp32 for the fp32 and bf16 stores).
+__device__ __forceinline__ double store_elem(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float store_elem(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float store_elem(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ double fma_x(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_x(float a, float b, float c) { return fmaf(a, b, c); }
+
 // What the P phase needs of one run (contiguous rows of one subdomain's local
 // inverse), staged in shared memory at kernel start.
 struct RunDesc {

@@ -1,0 +1,138 @@
+"""Parity of the massively parallel Schwarz case with the FP64 oracle, on a GB300.
+
+Sec. 4 investigates subdomains of a single fine element (T_S = T_h) with the coarse
+correction on agglomerates of T_H, at p = q (Table 1).  Through the C ABI that is
+polydg_setup with one subdomain per cell and asm_setup with the agglomerates; the
+persistent kernel then streams one n_p x n_p inverse per element.  Cases: the
+anisotropic 256-cell Voronoi P3 mesh with 6 k-means agglomerates at q = 1 and q = 3,
+a 16 x 16 Cartesian P1 mesh with 4 x 4-cell agglomerates (H = 4h), and an 8 x 8
+Cartesian P4 mesh with 2 x 2-cell agglomerates (H = 2h), q = p.
+
+Tolerances as in test_gpu_parity.py: B_ad r within 1e-9 (fp64 store) and 1e-4 (fp32
+store) relative; solutions at rtol 1e-12 within 1e-8 of a direct solve in the function
+L2 norm; iteration counts at the paper's tolerance 1e-9 within max(3, its / 50) of the
+oracle's PCG (these solves take up to ~500 iterations, along which the two sides'
+rounding drifts apart); the largest Ritz value within 1e-8 of the oracle's (it
+converges within the first iterations), the condition estimate within 1e-3: at the
+tolerance 1e-9 the smallest Ritz value has not converged yet (0.3 % above the smallest
+eigenvalue on the Voronoi q = 1 case, from the dense spectrum), and an unconverged
+Ritz value after ~500 iterations moves with the summation order by ~1e-4.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from conftest import cached
+from test_gpu_parity import lib, dev, host, mnorm_rel, gpu_ctx, oracle_coupled
+
+pytestmark = pytest.mark.gpu
+
+CASES = ["vor_q1", "vor_q3", "sq_p1", "sq8_p4"]
+
+
+def make_case(name, voronoi256):
+    from synth import Workload
+    from synth.meshes import cartesian_square, block_partition, isotropic_conductivity
+    from oracle import assembly
+
+    def build():
+        if name.startswith("vor"):
+            w, d = voronoi256
+            q = 1 if name == "vor_q1" else w.p
+        else:
+            n, p, blk = (16, 1, 4) if name == "sq_p1" else (8, 4, 2)
+            m = cartesian_square(n)
+            part = block_partition(n, blk)
+            w = Workload(f"cart{n}_p{p}", m, p, p, isotropic_conductivity(m.n_cells, 1.0),
+                         part, part.copy(), eta0=10.0, dt=0.1, rtol=1e-9)
+            d = assembly.assemble(m, p, w.sigma, w.eta0, w.chi_cm, w.dt)
+            q = p if p > 1 else 1
+        cells = np.arange(w.mesh.n_cells, dtype=np.int32)
+        wm = dataclasses.replace(w, subdomain=cells, q=q)
+        return wm, d
+    return cached(("mp", name), build)
+
+
+def case_ctx(name, voronoi256):
+    wm, d = make_case(name, voronoi256)
+    ctx = cached(("mp_ctx", name), lambda: gpu_ctx(wm))
+    return wm, d, ctx
+
+
+def oracle_schwarz(name, wm, d):
+    from oracle import schwarz
+    return cached(("mp_schwarz", name), lambda: schwarz.build(d, wm.subdomain, wm.coarse, wm.q))
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_mp_asm_apply(case, voronoi256):
+    pd = lib()
+    wm, d, ctx = case_ctx(case, voronoi256)
+    S = oracle_schwarz(case, wm, d)
+    r = np.random.default_rng(51).standard_normal(d.n_dofs)
+    ref = S.apply(r)
+    for prec, tol in (("fp64", 1e-9), ("fp32", 1e-4)):
+        pc = pd.asm_setup(ctx, wm.coarse, q=wm.q, precision=prec)
+        assert pc.info()["n_subdomains"] == wm.mesh.n_cells
+        z = dev(np.zeros(d.n_dofs))
+        pd.asm_apply(pc, dev(r), z)
+        assert np.linalg.norm(host(z) - ref) <= tol * np.linalg.norm(ref), prec
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_mp_pcg_solution(case, voronoi256):
+    pd = lib()
+    wm, d, ctx = case_ctx(case, voronoi256)
+    b = np.random.default_rng(52).standard_normal(d.n_dofs)
+    ref = cached(("mp_direct", case), lambda: spla.spsolve(d.K.tocsc(), b))
+    for prec, flexible in (("fp64", False), ("fp32", True)):
+        pc = pd.asm_setup(ctx, wm.coarse, q=wm.q, precision=prec)
+        x = dev(np.zeros(d.n_dofs))
+        st = pd.pcg_solve(ctx, pc, dev(b), x, rtol=1e-12, maxit=20000, flexible=flexible)
+        assert st["status"] == 0 and st["relres"] <= 1e-12, (prec, st)
+        assert mnorm_rel(d, host(x), ref) <= 1e-8, prec
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_mp_iterations_and_condition_estimate(case, voronoi256):
+    from oracle.pcg import pcg, lanczos_extremes
+    from synth import random_rhs
+    pd = lib()
+    wm, d, ctx = case_ctx(case, voronoi256)
+    S = oracle_schwarz(case, wm, d)
+    b = random_rhs(d.n_dofs, 41)
+    pc = pd.asm_setup(ctx, wm.coarse, q=wm.q, precision="fp64")
+    x = dev(np.zeros(d.n_dofs))
+    st, al, be = pd.pcg_solve_trace(ctx, pc, dev(b), x, rtol=1e-9, maxit=5000)
+    ref = pcg(d.K, b, prec=S.apply, rtol=1e-9, maxit=5000)
+    assert st["status"] == 0 and ref.converged
+    assert abs(st["iterations"] - ref.iterations) <= max(3, ref.iterations // 50), (st, ref.iterations)
+    lo, hi = pd.lanczos_extremes(al, be)
+    olo, ohi = lanczos_extremes(ref.alphas, ref.betas)
+    assert abs(hi - ohi) <= 1e-8 * ohi, (hi, ohi)
+    assert abs(hi / lo - ohi / olo) <= 1e-3 * (ohi / olo), (hi / lo, ohi / olo)
+
+
+def test_mp_coupled_steps(voronoi256):
+    """20 coupled steps with one-element subdomains and the degree-3 coarse space:
+    the potential within 1e-8 of the oracle's exactly solved trajectory, the ionic
+    state within 1e-9 (the preconditioner changes iterations, not the answer)."""
+    from oracle import monodomain
+    pd = lib()
+    w, d = voronoi256
+    wm, _, ctx = case_ctx("vor_q3", voronoi256)
+    steps = 20
+    pc = pd.asm_setup(ctx, wm.coarse, q=wm.q, precision="fp32")
+    sim = pd.sim_create(ctx, pc, u0=wm.u_rest, stimulus=wm.stimulus, rtol=1e-12, maxit=20000,
+                        flexible=True)
+    st = pd.monodomain_step(sim, steps)
+    u = dev(np.zeros(d.n_dofs))
+    nodes = cached(("nodes", w.name), lambda: monodomain.quadrature_nodes(d))
+    y = dev(np.zeros(5 * len(nodes.w)))
+    pd.sim_get_state(sim, u, y)
+    ref = oracle_coupled(w, d, steps)[-1]
+    assert st["status"] == 0 and st["steps_done"] == steps
+    assert mnorm_rel(d, host(u), ref.U) <= 1e-8
+    assert np.allclose(host(y).reshape(5, -1), ref.y, rtol=1e-9, atol=1e-12)
