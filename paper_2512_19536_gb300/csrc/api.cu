@@ -223,9 +223,18 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 
         for (int b : local_ids) max_rows = std::max(max_rows, (int)pc->blocks[b].nrows);
         P.small = max_rows <= 32 ? 1 : 0;
     }
+    // R_0 r' = per coarse DOF, the sum of its pairs' partials.  Lane groups of L (a power
+    // of 2) split each sum so that no lane adds more than 16 partials in sequence; the
+    // shuffle tree costs L log2 L fp64 adds per coarse DOF, so L stays as small as that
+    // allows.  When all the sums together exceed 8192 adds, the CTAs sum slices of the
+    // coarse DOFs into a global vector behind one more grid barrier instead of every
+    // CTA adding all of them (GB300's fp64 pipe retires ~2 FMA per clock per SM).
     P.pair_lanes = 1;
-    if (pc && pc->has_coarse)
-        while (P.pair_lanes < 32 && P.pair_lanes < pc->max_pairs) P.pair_lanes *= 2;
+    P.r0_split = 0;
+    if (pc && pc->has_coarse) {
+        while (P.pair_lanes < 32 && P.pair_lanes * 16 < pc->max_pairs) P.pair_lanes *= 2;
+        P.r0_split = (int64_t)pc->n_pairs * pc->nq > 8192 ? 1 : 0;
+    }
     P.rows = P.small ? 32 : 16;                  // partition granularity (rows per tile)
     const int rows = P.rows;
     P.xs_off = (size_t)NW * P.wstages * slot;
@@ -307,6 +316,8 @@ static PersistArgs persist_args(polydg_ctx* c, asm_ctx* pc, const Plan& P, PcgWo
     a.redundant = P.redundant;
     a.small = P.small;
     a.pair_lanes = P.pair_lanes;
+    a.r0_split = P.r0_split;
+    a.r0g = coarse ? pc->d_r0g : nullptr;
     a.l2_keep = P.l2_keep;
     a.xs_off = P.xs_off;
     a.rp_off = P.rp_off;
@@ -730,7 +741,7 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
         return fail(st);
     const int64_t npairs = std::max<int64_t>(pc->n_pairs, 1) * std::max(pc->nq, 1);
     if ((st = dalloc(&pc->d_r0p, npairs)) || (st = dalloc(&pc->d_q0p, npairs)) ||
-        (st = dalloc(&pc->d_y0, std::max<int64_t>(n0, 1))) || (st = dalloc(&pc->d_rin, H.nc * np)) ||
+        (st = dalloc(&pc->d_y0, std::max<int64_t>(n0, 1))) || (st = dalloc(&pc->d_r0g, std::max<int64_t>(n0, 1))) || (st = dalloc(&pc->d_rin, H.nc * np)) ||
         (st = dalloc(&pc->d_zloc, H.nc * np)) || (st = dalloc(&pc->d_zout, H.nc * np)) ||
         (st = dalloc(&pc->d_err, 1)))
         return fail(st);
@@ -1873,7 +1884,7 @@ void asm_destroy(asm_ctx* pc) {
     pc->plan.release();
     dfree(pc->d_blocks); dfree(pc->d_tiles); dfree(pc->st64); dfree(pc->st32); dfree(pc->st16);
     dfree(pc->d_T); dfree(pc->d_agg); dfree(pc->d_pair_ptr); dfree(pc->d_r0p); dfree(pc->d_q0p);
-    dfree(pc->d_y0); dfree(pc->d_rin); dfree(pc->d_zloc); dfree(pc->d_zout); dfree(pc->d_err);
+    dfree(pc->d_y0); dfree(pc->d_r0g); dfree(pc->d_rin); dfree(pc->d_zloc); dfree(pc->d_zout); dfree(pc->d_err);
     delete pc;
 }
 

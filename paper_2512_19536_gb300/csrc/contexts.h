@@ -85,6 +85,7 @@ struct Plan {
     int wstages = 1;
     int small = 0;                      // every subdomain <= 32 DOFs: one warp per subdomain
     int pair_lanes = 1;                 // lanes summing one coarse DOF's pair partials
+    int r0_split = 0;                   // pair partials summed by slices, one more barrier
     float l2_keep = 0.f;                // fraction of the local-inverse lines kept in L2
     size_t smem = 0, slot_bytes = 0, xs_off = 0, rp_off = 0, r0_off = 0, y0_off = 0,
            pn_off = 0, td_off = 0;
@@ -153,6 +154,7 @@ struct asm_ctx {
     int32_t* d_agg = nullptr;
     int64_t* d_pair_ptr = nullptr;
     int max_pairs = 0;                  // most (agglomerate, subdomain) pairs of one agglomerate
+    double* d_r0g = nullptr;            // R_0 r' summed by slices of the CTAs (split mode)
     double* d_r0p = nullptr;
     double* d_q0p = nullptr;
     double* d_y0 = nullptr;

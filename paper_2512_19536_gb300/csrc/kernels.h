@@ -98,6 +98,8 @@ struct PersistArgs {
     int grid, wstages, identity, n0, ld0, nq, redundant;
     int small;                                 // every subdomain <= 32 DOFs: a warp per subdomain
     int pair_lanes;                            // lanes (power of 2) summing one coarse DOF's pairs
+    int r0_split;                              // R_0 r' summed by slices into r0g, then a barrier
+    double* r0g;                               // [n0] (r0_split)
     float l2_keep;                             // fraction of the local-inverse lines kept in L2
     int64_t nc;
     // shared-memory carve-up (byte offsets): wstages copy slots of slot_bytes per warp

@@ -321,24 +321,36 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         if (timing && threadIdx.x == 0) t_mark = clock64();
         // ---------------------------------------------------------------- coarse
         if (coarse) {
-            if (a.redundant || c1 > c0) {
-                // R_0 r' = the pair partials summed per coarse DOF, by groups of L lanes
-                // (L = pair_lanes, a power of 2 covering the largest agglomerate's pair
-                // count, up to 32) and a shuffle tree: the same order in every CTA, so
-                // every CTA holds the same bits
-                const int L = a.pair_lanes, gl = lane & (L - 1);
-                const int per_pass = (int)blockDim.x / L;
-                for (int base = 0; base < a.n0; base += per_pass) {
+            // R_0 r' = the pair partials summed per coarse DOF, by groups of L lanes (L =
+            // pair_lanes, a power of 2) and a shuffle tree, in one fixed order (the same
+            // bits wherever a sum is formed).  Split mode: this CTA sums its slice of the
+            // coarse DOFs into r0g, a grid barrier, then the CTAs that need R_0 r' load it;
+            // otherwise every such CTA sums all of them.
+            const int L = a.pair_lanes, gl = lane & (L - 1);
+            const int per_pass = (int)blockDim.x / L;
+            auto pair_sums = [&](int i0, int i1, double* out) {
+                for (int base = i0; base < i1; base += per_pass) {
                     const int idx = base + (int)threadIdx.x / L;
                     double s_r = 0.0;
-                    if (idx < a.n0) {
+                    if (idx < i1) {
                         const int J = idx / a.nq, kq = idx - J * a.nq;
                         for (int64_t p2 = a.pair_ptr[J] + gl; p2 < a.pair_ptr[J + 1]; p2 += L)
                             s_r += __ldcg(a.r0p + p2 * a.nq + kq);
                     }
                     for (int o = L >> 1; o > 0; o >>= 1) s_r += __shfl_xor_sync(0xffffffffu, s_r, o);
-                    if (idx < a.n0 && gl == 0) r0s[idx] = s_r;
+                    if (idx < i1 && gl == 0) out[idx] = s_r;
                 }
+            };
+            if (a.r0_split) {
+                pair_sums((int)(((int64_t)a.n0 * cta) / G), (int)(((int64_t)a.n0 * (cta + 1)) / G), a.r0g);
+                ok = grid_barrier(a.gs, G, gen, a.err);
+                if (!ok) { status = kEDEVICE; break; }
+                if (a.redundant || c1 > c0) {
+                    for (int idx = threadIdx.x; idx < a.n0; idx += blockDim.x) r0s[idx] = __ldcg(a.r0g + idx);
+                    __syncthreads();
+                }
+            } else if (a.redundant || c1 > c0) {
+                pair_sums(0, a.n0, r0s);
                 __syncthreads();
             }
             auto coarse_row = [&](int row) {

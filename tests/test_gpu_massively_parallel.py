@@ -5,8 +5,11 @@ correction on agglomerates of T_H, at p = q (Table 1).  Through the C ABI that i
 polydg_setup with one subdomain per cell and asm_setup with the agglomerates; the
 persistent kernel then streams one n_p x n_p inverse per element.  Cases: the
 anisotropic 256-cell Voronoi P3 mesh with 6 k-means agglomerates at q = 1 and q = 3,
-a 16 x 16 Cartesian P1 mesh with 4 x 4-cell agglomerates (H = 4h), and an 8 x 8
-Cartesian P4 mesh with 2 x 2-cell agglomerates (H = 2h), q = p.
+a 16 x 16 Cartesian P1 mesh with 4 x 4-cell agglomerates (H = 4h), an 8 x 8
+Cartesian P4 mesh with 2 x 2-cell agglomerates (H = 2h), q = p, and a 24 x 24 Cartesian
+P4 mesh with 6 x 6-cell agglomerates (576 pairs x 15 coarse modes: the kernel sums the
+restriction partials by slices of the CTAs behind an extra grid barrier, 4 lanes per
+coarse DOF).
 
 Tolerances as in test_gpu_parity.py: B_ad r within 1e-9 (fp64 store) and 1e-4 (fp32
 store) relative; solutions at rtol 1e-12 within 1e-8 of a direct solve in the function
@@ -29,7 +32,7 @@ from test_gpu_parity import lib, dev, host, mnorm_rel, gpu_ctx, oracle_coupled
 
 pytestmark = pytest.mark.gpu
 
-CASES = ["vor_q1", "vor_q3", "sq_p1", "sq8_p4"]
+CASES = ["vor_q1", "vor_q3", "sq_p1", "sq8_p4", "sq24_p4"]
 
 
 def make_case(name, voronoi256):
@@ -42,7 +45,7 @@ def make_case(name, voronoi256):
             w, d = voronoi256
             q = 1 if name == "vor_q1" else w.p
         else:
-            n, p, blk = (16, 1, 4) if name == "sq_p1" else (8, 4, 2)
+            n, p, blk = {"sq_p1": (16, 1, 4), "sq8_p4": (8, 4, 2), "sq24_p4": (24, 4, 6)}[name]
             m = cartesian_square(n)
             part = block_partition(n, blk)
             w = Workload(f"cart{n}_p{p}", m, p, p, isotropic_conductivity(m.n_cells, 1.0),
