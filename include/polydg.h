@@ -265,6 +265,23 @@ int pcg_lanczos_extremes(const double *alphas, const double *betas, int m, doubl
 /* Create a coupled simulation on ctx/pc (pc may be NULL for plain CG). */
 int sim_create(polydg_ctx *ctx, asm_ctx *pc, const sim_params *params, sim_ctx **out);
 
+/* ---- representation of the ionic state (sim_set_ionic_form) ------------------ */
+#define POLYDG_IONIC_NODAL 0    /* per quadrature node, explicit Euler there (default)   */
+#define POLYDG_IONIC_MODAL 1    /* in the DG basis: the second line of Eq.
+                                   fully-discrete-1, M_h Y^{k+1} = M_h Y^k - dt G^k     */
+
+/* Choose how the simulation's ionic state is represented, before its first step
+ * (EINVAL after it).  NODAL keeps the five states at the element quadrature nodes and
+ * advances each node by explicit Euler with u^k there.  MODAL keeps, per cell and
+ * state l, the n_p coefficients Y_l of the DG basis, starting from the rest state as
+ * a constant, and advances them by Eq. fully-discrete-1 (second line): G_l collects
+ * sum_q w_q m_l(u^k(x_q), y_h^k(x_q)) phi(x_q) over the cell's quadrature nodes and
+ * Y_l^{k+1} = Y_l^k - dt M_K^{-1} G_l (M_h is block diagonal); the ion current I^{k+1}
+ * then uses y_h^{k+1} at the nodes.  In both forms sim_get_state returns the states
+ * at the nodes (for MODAL, y_h^{k+1}(x_q)).  Allocates 5 n doubles for Y and, once per
+ * context, the inverse mass blocks (n_c n_p^2 doubles).  Errors: EINVAL, ENOMEM, ECUDA. */
+int sim_set_ionic_form(sim_ctx *sim, int form);
+
 /* Advance nsteps Crank-Nicolson steps (Eq. fully-discrete-1).  Per step:
  * y^{k+1} = y^k - dt m(u^k, y^k) at every quadrature node; I^{k+1} from
  * u~ = 3/2 U^k - 1/2 U^{k-1} (U^0 on the first step) and y^{k+1}; b =

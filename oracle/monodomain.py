@@ -10,7 +10,13 @@ with the ionic state advanced explicitly.  Readings (listed with the others):
     Crank-Nicolson midpoint (u~ = U^0 on the first step);
   * F^{k+1}_i = int I_ext(x, t^{k+1/2}) phi_i with the Gaussian stimulus
     I_ext = A exp(-|x - x0|^2 / (2 w^2)) switched on while t < duration;
-  * chi_m C_m = chi_cm and C_m = 1, so chi_m = chi_cm.
+  * chi_m C_m = chi_cm and C_m = 1, so chi_m = chi_cm;
+  * ionic_form="modal" takes the second line of Eq. fully-discrete-1 as printed
+    instead: per state l the DG coefficients Y_l, M_h Y_l^{k+1} = M_h Y_l^k - dt G_l^k
+    with G_l = int m_l(u_h^k, y_h^k) phi (element quadrature), so
+    Y_l^{k+1} = Y_l^k + M_K^{-1} sum_q w_q dt y'_l(x_q) phi(x_q) cell by cell, and
+    I^{k+1} uses y_h^{k+1} at the nodes.  The initial state is the rest state as a
+    constant (coefficient of the constant mode, phi_0 = 1).
 The linear solve is either a direct sparse factorisation (the definition:
 the method's PCG converges to that solution) or PCG with B_ad (Eq. prec).
 
@@ -70,13 +76,14 @@ def stimulus_load(disc, stim):
 class State:
     U: np.ndarray
     U_prev: np.ndarray
-    y: np.ndarray          # [5, nn]
+    y: np.ndarray          # [5, nn] the states at the nodes
     k: int = 0
+    Y: np.ndarray = None   # [5, n_dofs] DG coefficients of the states (modal form)
 
 
 class Monodomain:
     def __init__(self, disc, stimulus, u0=-67.0, solver="direct", prec=None, rtol=1e-8,
-                 flexible=False, ion=True):
+                 flexible=False, ion=True, ionic_form="nodal"):
         self.disc = disc
         self.nodes = quadrature_nodes(disc)
         self.stim = stimulus
@@ -87,15 +94,28 @@ class Monodomain:
         self.lu = spla.splu(disc.K.tocsc()) if solver == "direct" else None
         U0 = np.zeros(disc.n_dofs)
         U0[::disc.n_p] = u0                      # constant u0: only the (0,0) mode
-        y0 = np.repeat(ionic.rest_state(u0)[:, None], len(self.nodes.w), axis=1)
-        self.state = State(U0, U0.copy(), y0, 0)
+        rest = ionic.rest_state(u0)
+        y0 = np.repeat(rest[:, None], len(self.nodes.w), axis=1)
+        self.ionic_form = ionic_form
+        Y0 = None
+        if ionic_form == "modal":
+            Y0 = np.zeros((5, disc.n_dofs))
+            Y0[:, ::disc.n_p] = rest[:, None]
+        elif ionic_form != "nodal":
+            raise ValueError(ionic_form)
+        self.state = State(U0, U0.copy(), y0, 0, Y0)
         self.iterations = []
 
     def rhs(self, st: State):
         d = self.disc
         dt = d.dt
         u_nodes = nodal_values(self.nodes, st.U, d.n_p)
-        y_new = ionic.euler_step(u_nodes, st.y, dt)
+        Y_new = None
+        if self.ionic_form == "modal":
+            Y_new = self.modal_update(u_nodes, st.Y)
+            y_new = np.stack([nodal_values(self.nodes, Y_new[l], d.n_p) for l in range(5)])
+        else:
+            y_new = ionic.euler_step(u_nodes, st.y, dt)
         U_ext = st.U if st.k == 0 else 1.5 * st.U - 0.5 * st.U_prev
         if self.ion:
             f = ionic.f_ion(nodal_values(self.nodes, U_ext, d.n_p), y_new)
@@ -105,7 +125,19 @@ class Monodomain:
         t_half = (st.k + 0.5) * dt
         on = 1.0 if (self.stim and t_half < self.stim["duration"]) else 0.0
         b = self.Kminus @ st.U - d.chi_cm * dt * I + dt * on * self.F
+        self._Y_new = Y_new
         return b, y_new
+
+    def modal_update(self, u_nodes, Y):
+        """Y_l + M_K^{-1} sum_q w_q dt y'_l(u^k(x_q), y_h^k(x_q)) phi(x_q), cell by cell."""
+        d, nc, n_p = self.disc, self.disc.mesh.n_cells, self.disc.n_p
+        yq = np.stack([nodal_values(self.nodes, Y[l], n_p) for l in range(5)])
+        incr = d.dt * ionic.dydt(u_nodes, yq)
+        out = np.empty_like(Y)
+        for l in range(5):
+            G = project_nodal(self.nodes, incr[l], nc, n_p).reshape(nc, n_p, 1)
+            out[l] = Y[l] + np.linalg.solve(d.M_blocks, G).ravel()
+        return out
 
     def step(self):
         st = self.state
@@ -118,5 +150,5 @@ class Monodomain:
                       flexible=self.flexible)
             U_new = res.x
             self.iterations.append(res.iterations)
-        self.state = State(U_new, st.U, y_new, st.k + 1)
+        self.state = State(U_new, st.U, y_new, st.k + 1, self._Y_new)
         return self.state

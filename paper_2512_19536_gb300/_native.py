@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libpolydg.so")
 POLYDG_OK, POLYDG_EINVAL, POLYDG_ENOMEM, POLYDG_ECUDA = 0, -1, -2, -3
 POLYDG_ENOTSPD, POLYDG_ENOTCONV, POLYDG_EBREAKDOWN, POLYDG_ENONFINITE = -4, -5, -6, -7
 POLYDG_FP64, POLYDG_FP32, POLYDG_BF16 = 0, 1, 2
+POLYDG_IONIC_NODAL, POLYDG_IONIC_MODAL = 0, 1
+IONIC_FORM = {"nodal": POLYDG_IONIC_NODAL, "modal": POLYDG_IONIC_MODAL}
 PRECISION = {"fp64": POLYDG_FP64, "fp32": POLYDG_FP32, "bf16": POLYDG_BF16}
 
 EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_setup3d", "polydg_get_info", "polydg_get_faces",
@@ -29,7 +31,7 @@ EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_setup3d", "polydg_get_in
            "guess_train_step", "sim_set_guess", "guess_destroy", "polydg_sym_eig",
            "shared_local_setup", "shared_local_info", "shared_local_apply", "shared_local_destroy",
            "sim_set_shared_local", "asm_autotune", "pcg_solve_trace", "pcg_lanczos_extremes",
-           "sim_set_history"]
+           "sim_set_history", "sim_set_ionic_form"]
 
 
 class polydg_mesh(C.Structure):
@@ -139,6 +141,8 @@ def load() -> C.CDLL:
     L.asm_autotune.restype = i32
     L.sim_set_shared_local.argtypes = [vp, vp]
     L.sim_set_shared_local.restype = i32
+    L.sim_set_ionic_form.argtypes = [vp, i32]
+    L.sim_set_ionic_form.restype = i32
     L.shared_local_destroy.argtypes = [vp]
     L.shared_local_destroy.restype = None
     for name in ("guess_n_params", "guess_create", "guess_get_params", "guess_set_scales",
@@ -373,6 +377,12 @@ def sim_create(ctx: PolyDG, pc, u0=-67.0, stimulus=None, rtol=1e-8, maxit=10000,
     h = C.c_void_p()
     _check(load().sim_create(ctx.h, pc.h if pc is not None else None, C.byref(prm), C.byref(h)))
     return Simulation(ctx, pc, h)
+
+
+def sim_set_ionic_form(sim: Simulation, form="modal"):
+    """Ionic state per quadrature node ("nodal", the default) or in the DG basis ("modal");
+    chosen before the first step."""
+    _check(load().sim_set_ionic_form(sim.h, IONIC_FORM[form]))
 
 
 def _stats(st):

@@ -1083,6 +1083,42 @@ int pcg_lanczos_extremes(const double* alphas, const double* betas, int m, doubl
     return POLYDG_OK;
 }
 
+int sim_set_ionic_form(sim_ctx* sm, int form) {
+    if (!sm || (form != POLYDG_IONIC_NODAL && form != POLYDG_IONIC_MODAL)) {
+        set_error("sim_set_ionic_form: need a simulation and form 0 (nodal) or 1 (modal)");
+        return POLYDG_EINVAL;
+    }
+    if (sm->k != 0) {
+        set_error("sim_set_ionic_form: the form is chosen before the first step");
+        return POLYDG_EINVAL;
+    }
+    polydg_ctx* c = sm->ctx;
+    const HostSetup& H = c->H;
+    const int np = H.n_p;
+    if (form == POLYDG_IONIC_NODAL) {
+        if (sm->Ym) { dfree(sm->Ym); sm->Ym = nullptr; ++sm->version; }
+        return POLYDG_OK;
+    }
+    if (sm->Ym) return POLYDG_OK;
+    int st;
+    if (!c->d_Minv) {
+        std::vector<double> minv;
+        if ((st = mass_inverse_blocks(H, minv))) return st;
+        if ((st = upload(&c->d_Minv, minv))) return st;
+    }
+    if ((st = dalloc(&sm->Ym, 5 * H.nc * np))) return st;
+    cudaError_t e = launch_init_modal(sm->Ym, H.nc, np, sm->d_y0, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+        dfree(sm->Ym);
+        sm->Ym = nullptr;
+        set_error(std::string("sim_set_ionic_form: ") + cudaGetErrorString(e));
+        return POLYDG_ECUDA;
+    }
+    ++sm->version;                      // batches re-record their step graph
+    return POLYDG_OK;
+}
+
 int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out) {
     if (int st = check_ctx(c, "sim_create")) return st;
     if (!prm || !out) { set_error("sim_create: null argument"); return POLYDG_EINVAL; }
@@ -1182,8 +1218,12 @@ static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
     PcgWork& w = sm->work;
     const double dt = H.dt;
     CU(launch_step_begin(w.sc, sm->d_ss, s));
-    CU(launch_ionic(np, sm->U, sm->Uprev, c->d_node_ptr, c->d_node_w, c->d_node_phi, sm->y, nn,
-                    H.nc, dt, sm->I, sm->d_ss, s));
+    if (sm->Ym)
+        CU(launch_ionic_modal(np, sm->U, sm->Uprev, c->d_node_ptr, c->d_node_w, c->d_node_phi, c->d_Minv,
+                              sm->Ym, sm->y, nn, H.nc, dt, sm->I, sm->d_ss, s));
+    else
+        CU(launch_ionic(np, sm->U, sm->Uprev, c->d_node_ptr, c->d_node_w, c->d_node_phi, sm->y, nn,
+                        H.nc, dt, sm->I, sm->d_ss, s));
     CU(launch_matvec(MODE_RHS, np, c->K, c->K.val_minus, sm->U, w.b, sm->I, sm->F, -H.chi_cm * dt,
                      dt, nullptr, nullptr, sm->d_ss, dt, sm->prm.stim_duration, nullptr, nullptr, s));
     if (sm->guess_policy == 3) {  // subspace of the learned proposal and the last increments
@@ -1873,6 +1913,7 @@ void sim_destroy(sim_ctx* sm) {
     for (auto e : sm->ev) cudaEventDestroy(e);
     sm->work.release();
     dfree(sm->U); dfree(sm->Uprev); dfree(sm->Uprev2); dfree(sm->xg); dfree(sm->I); dfree(sm->F); dfree(sm->y); dfree(sm->d_y0);
+    dfree(sm->Ym);
     dfree(sm->ring); dfree(sm->kuring); dfree(sm->subW); dfree(sm->gram);
     dfree(sm->d_ss);
     if (sm->h_ss) cudaFreeHost(sm->h_ss);
@@ -1893,7 +1934,7 @@ void polydg_destroy(polydg_ctx* c) {
     c->id_plan.release();
     c->work.release();
     dfree(c->K.row_ptr); dfree(c->K.col); dfree(c->K.val); dfree(c->K.val_minus);
-    dfree(c->d_to_caller); dfree(c->d_node_ptr); dfree(c->d_node_w); dfree(c->d_node_phi);
+    dfree(c->d_to_caller); dfree(c->d_node_ptr); dfree(c->d_node_w); dfree(c->d_node_phi); dfree(c->d_Minv);
     dfree(c->d_node_pos); dfree(c->d_to_internal); dfree(c->d_diam); dfree(c->d_id_blocks); dfree(c->d_id_tiles); dfree(c->d_zero_ptr);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     delete c;

@@ -120,6 +120,7 @@ struct polydg_ctx {
     int64_t* d_node_ptr = nullptr;
     double* d_node_w = nullptr;
     double* d_node_phi = nullptr;
+    double* d_Minv = nullptr;           // [nc][n_p][n_p] inverse mass blocks (modal ionic state)
     int64_t* d_node_pos = nullptr;
     int64_t* d_to_internal = nullptr;   // caller -> internal cell id
     double* d_diam = nullptr;           // cell diameters, internal order
@@ -195,6 +196,7 @@ struct sim_ctx {
     double* gram = nullptr;             // [kSubMaxPairs][kSubMaxCtas] Gram partial sums
     double *U = nullptr, *Uprev = nullptr, *I = nullptr, *F = nullptr, *y = nullptr;
     double* d_y0 = nullptr;
+    double* Ym = nullptr;               // [5][n] modal ionic state (sim_set_ionic_form 1), or null
     SimScalars* d_ss = nullptr;
     SimScalars* h_ss = nullptr;         // pinned
     int64_t k = 0;

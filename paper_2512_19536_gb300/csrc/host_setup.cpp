@@ -808,6 +808,21 @@ static bool cholesky_solve_small(int n, const double* A, double* B, int nrhs) {
     return true;
 }
 
+// M_K^{-1} of every cell (row-major, internal order), by the Cholesky solve above with
+// the identity as right-hand side.
+int mass_inverse_blocks(const HostSetup& S, std::vector<double>& out) {
+    const int np = S.n_p;
+    out.assign((size_t)S.nc * np * np, 0.0);
+    int bad = 0;
+    for (int64_t e = 0; e < S.nc; ++e) {
+        double* B = &out[(size_t)e * np * np];
+        for (int i = 0; i < np; ++i) B[i * np + i] = 1.0;
+        if (!cholesky_solve_small(np, &S.Mblk[(size_t)e * np * np], B, np)) bad = 1;
+    }
+    if (bad) { set_error("mass matrix of a cell is not positive definite"); return POLYDG_ENOTSPD; }
+    return POLYDG_OK;
+}
+
 int coarse_setup(const HostSetup& S, const int32_t* coarse, int q, CoarseSetup& C) {
     if (!coarse) { set_error("asm_setup: null coarse partition"); return POLYDG_EINVAL; }
     if (q < 1 || q > S.p) { set_error("asm_setup: coarse degree q must be in 1..p"); return POLYDG_EINVAL; }

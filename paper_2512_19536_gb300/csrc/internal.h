@@ -83,5 +83,6 @@ struct CoarseSetup {
     std::vector<double> K0;               // [n0 * n0] dense, n0 = n_agg * n_q
 };
 int coarse_setup(const HostSetup& S, const int32_t* coarse_of_cell, int q, CoarseSetup& out);
+int mass_inverse_blocks(const HostSetup& S, std::vector<double>& out);
 
 }  // namespace polydg

@@ -94,9 +94,9 @@ BC_HD double total_current(const NodeConsts& k, double V, double n, double h, do
     return INa + IK + gClL * (V - k.ECl);
 }
 
-// One explicit Euler step y <- y + dt y'(V, y) (Sec. 2 model, per quadrature node).
-BC_HD void euler(const NodeConsts& k, double V, double dt, double& n, double& h, double& Ko,
-                 double& Nai, double& Cai) {
+// y'(V, y) of the Sec. 2 model (= -m(u, y)) at one point: d[0..4] for n, h, K_o, Na_i, Ca_i.
+BC_HD void rates(const NodeConsts& k, double V, double n, double h, double Ko, double Nai, double Cai,
+                 double* d) {
     const double E = exp(-V * kInv80);
     const double E2 = E * E, E4 = E2 * E2, E8 = E4 * E4, E16 = E8 * E8, E32 = E16 * E16;
     const double an = 0.01 * lin_exp_given(V + 34.0, 10.0, k.an * E8);
@@ -119,11 +119,23 @@ BC_HD void euler(const NodeConsts& k, double V, double dt, double& n, double& h,
     const double dKo = (gamma * beta * IK - 2.0 * beta * pump - glia - diff) * kInvTau;
     const double dNa = (-gamma * INa - 3.0 * pump) * kInvTau;
     const double dCa = -0.002 * gCa * (V - ECa) / (1.0 + k.ca * E32) - Cai * kInv80;
-    n += dt * dn;
-    h += dt * dh;
-    Ko += dt * dKo;
-    Nai += dt * dNa;
-    Cai += dt * dCa;
+    d[0] = dn;
+    d[1] = dh;
+    d[2] = dKo;
+    d[3] = dNa;
+    d[4] = dCa;
+}
+
+// One explicit Euler step y <- y + dt y'(V, y) (Sec. 2 model, per quadrature node).
+BC_HD void euler(const NodeConsts& k, double V, double dt, double& n, double& h, double& Ko,
+                 double& Nai, double& Cai) {
+    double d[5];
+    rates(k, V, n, h, Ko, Nai, Cai, d);
+    n += dt * d[0];
+    h += dt * d[1];
+    Ko += dt * d[2];
+    Nai += dt * d[3];
+    Cai += dt * d[4];
 }
 
 // Rest state at potential V0: gates at steady state, K_o = 4, Na_i = 18, Ca_i = 0.

@@ -314,6 +314,13 @@ cudaError_t launch_to_half(const float* w32, __half* w16, int P, cudaStream_t s)
 cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int64_t* node_ptr,
                          const double* node_w, const double* node_phi, double* y, int64_t nn,
                          int64_t nc, double dt, double* I, const SimScalars* ss, cudaStream_t s);
+// Modal ionic state (the second line of Eq. fully-discrete-1 in the DG basis): Ym is
+// [5][nc n_p], Minv the per-cell inverse mass blocks [nc][n_p][n_p] (row-major).
+cudaError_t launch_ionic_modal(int np, const double* U, const double* Uprev, const int64_t* node_ptr,
+                               const double* node_w, const double* node_phi, const double* Minv,
+                               double* Ym, double* y, int64_t nn, int64_t nc, double dt, double* I,
+                               const SimScalars* ss, cudaStream_t s);
+cudaError_t launch_init_modal(double* Ym, int64_t nc, int np, const double* y0, cudaStream_t s);
 cudaError_t launch_node_gather(const double* y_int, double* y_caller,
                                const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s);
 cudaError_t launch_step_finish(double* U, double* Uprev, double* Uprev2, const double* x0,

@@ -1,5 +1,7 @@
 // Per-quadrature-node ionic update and ion-current load of one Crank-Nicolson
 // step (Eq. fully-discrete-1), plus the per-step bookkeeping kernels.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -74,6 +76,143 @@ cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int
         case 15: ionic_kernel<15><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss, kc); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+// The ionic state in the DG basis (Eq. fully-discrete-1, second line: M_h Y^{k+1} =
+// M_h Y^k - dt G^k, M_h block diagonal).  Warp per cell, Y_l the cell's n_p coefficients
+// of state l (Ym[l][c n_p + j]):
+//   pass 1, per node:  d_l(x_q) = dt y'_l(u^k(x_q), y_h^k(x_q))  (into the node buffer y),
+//   pass 2, per state: G_l = sum_q w_q d_l(x_q) phi(x_q),  Y_l += M_K^{-1} G_l,
+//   pass 3, per node:  y_h^{k+1}(x_q) into y, and I_e = sum_q w_q f(u~(x_q), y_h^{k+1}(x_q)) phi(x_q).
+// The node buffer then holds the modal state's values at the nodes.
+template <int NP>
+__global__ void __launch_bounds__(kIonicThreads, 2)
+ionic_modal_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
+                   const int64_t* __restrict__ node_ptr, const double* __restrict__ node_w,
+                   const double* __restrict__ node_phi, const double* __restrict__ Minv,
+                   double* __restrict__ Ym, double* __restrict__ y, int64_t nn, int64_t nc, double dt,
+                   double* __restrict__ I, const SimScalars* ss, const bc::NodeConsts kc) {
+    constexpr int W = kIonicThreads / 32;
+    __shared__ double su[W][2][NP];
+    __shared__ double sy[W][5][NP];
+    __shared__ double sg[W][5][NP];
+    if (ss->failed) return;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    if (e >= nc) return;
+    const bool first = (ss->k == 0);
+    const int64_t n = nc * NP;
+    if (lane < NP) {
+        const double ue = U[e * NP + lane];
+        su[wl][0][lane] = ue;
+        su[wl][1][lane] = first ? ue : 1.5 * ue - 0.5 * Uprev[e * NP + lane];
+#pragma unroll
+        for (int l = 0; l < 5; ++l) sy[wl][l][lane] = Ym[l * n + e * NP + lane];
+    }
+    __syncwarp();
+    const int64_t q0 = node_ptr[e], q1 = node_ptr[e + 1];
+    for (int64_t q = q0 + lane; q < q1; q += 32) {          // pass 1
+        const double* ph = node_phi + q * NP;
+        double uk = 0.0, yv[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            const double pv = __ldg(ph + j);
+            uk = fma(pv, su[wl][0][j], uk);
+#pragma unroll
+            for (int l = 0; l < 5; ++l) yv[l] = fma(pv, sy[wl][l][j], yv[l]);
+        }
+        double d[5];
+        bc::rates(kc, uk, yv[0], yv[1], yv[2], yv[3], yv[4], d);
+#pragma unroll
+        for (int l = 0; l < 5; ++l) y[l * nn + q] = dt * d[l];
+    }
+    __syncwarp();
+    for (int l = 0; l < 5; ++l) {                           // pass 2
+        double acc[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[j] = 0.0;
+        for (int64_t q = q0 + lane; q < q1; q += 32) {
+            const double* ph = node_phi + q * NP;
+            const double wd = node_w[q] * y[l * nn + q];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) acc[j] = fma(wd, __ldg(ph + j), acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            const double sum = warp_sum(acc[j]);
+            if (lane == j) sg[wl][l][j] = sum;
+        }
+    }
+    __syncwarp();
+    if (lane < NP) {
+        const double* Mr = Minv + (e * NP + lane) * NP;     // row `lane` of M_K^{-1}
+#pragma unroll
+        for (int l = 0; l < 5; ++l) {
+            double v = sy[wl][l][lane];
+#pragma unroll
+            for (int c = 0; c < NP; ++c) v = fma(__ldg(Mr + c), sg[wl][l][c], v);
+            Ym[l * n + e * NP + lane] = v;
+            sy[wl][l][lane] = v;                            // read back after the warp sync
+        }
+    }
+    __syncwarp();
+    double acc[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) acc[j] = 0.0;
+    for (int64_t q = q0 + lane; q < q1; q += 32) {          // pass 3
+        const double* ph = node_phi + q * NP;
+        double phv[NP];
+        double ux = 0.0, yv[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            phv[j] = __ldg(ph + j);
+            ux = fma(phv[j], su[wl][1][j], ux);
+#pragma unroll
+            for (int l = 0; l < 5; ++l) yv[l] = fma(phv[j], sy[wl][l][j], yv[l]);
+        }
+#pragma unroll
+        for (int l = 0; l < 5; ++l) y[l * nn + q] = yv[l];
+        const double wf = node_w[q] * bc::total_current(kc, ux, yv[0], yv[1], yv[2], yv[3], yv[4]);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[j] = fma(wf, phv[j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const double sum = warp_sum(acc[j]);
+        if (lane == 0) I[e * NP + j] = sum;
+    }
+}
+
+cudaError_t launch_ionic_modal(int np, const double* U, const double* Uprev, const int64_t* node_ptr,
+                               const double* node_w, const double* node_phi, const double* Minv,
+                               double* Ym, double* y, int64_t nn, int64_t nc, double dt, double* I,
+                               const SimScalars* ss, cudaStream_t s) {
+    const unsigned g = (unsigned)((nc * 32 + kIonicThreads - 1) / kIonicThreads);
+    static const bc::NodeConsts kc = bc::node_consts();
+    switch (np) {
+        case 3: ionic_modal_kernel<3><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, Minv, Ym, y, nn, nc, dt, I, ss, kc); break;
+        case 6: ionic_modal_kernel<6><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, Minv, Ym, y, nn, nc, dt, I, ss, kc); break;
+        case 10: ionic_modal_kernel<10><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, Minv, Ym, y, nn, nc, dt, I, ss, kc); break;
+        case 15: ionic_modal_kernel<15><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, Minv, Ym, y, nn, nc, dt, I, ss, kc); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Modal initial state: Y_l = y0_l times the constant mode (phi_0 = 1), other modes 0.
+__global__ void init_modal_kernel(double* Ym, int64_t nc, int np, const double* y0) {
+    const int64_t n = nc * np;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 5 * n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = t / n, r = t - l * n;
+        Ym[t] = (r % np == 0) ? y0[l] : 0.0;
+    }
+}
+
+cudaError_t launch_init_modal(double* Ym, int64_t nc, int np, const double* y0, cudaStream_t s) {
+    const int64_t total = 5 * nc * np;
+    const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+    init_modal_kernel<<<g, 256, 0, s>>>(Ym, nc, np, y0);
     return cudaGetLastError();
 }
 
