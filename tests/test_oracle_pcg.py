@@ -60,3 +60,45 @@ def test_flexible_equals_standard_with_fixed_spd_preconditioner():
     r2 = pcg(A, b, prec=lambda v: D @ v, rtol=1e-10, flexible=True)
     assert abs(r1.iterations - r2.iterations) <= 1
     assert np.allclose(r1.x, r2.x, rtol=1e-7)
+
+
+# ---- pipelined PCG: the same iteration with one reduction per step
+
+def test_pipelined_matches_textbook_coefficients_and_iterates():
+    # exact arithmetic gives identical alpha_k, beta_k and x_k; rounding separates them
+    # slowly on a well-conditioned system, so the first iterations agree closely
+    from oracle.pcg import pcg_pipelined
+    A = spd_with_spectrum(np.linspace(1, 50, 40), 5)
+    Dinv = 1.0 / np.diag(A)
+    b = np.random.default_rng(6).standard_normal(40)
+    prec = lambda v: Dinv * v
+    ref = pcg(A, b, prec=prec, rtol=1e-300, maxit=10)
+    got = pcg_pipelined(A, b, prec=prec, rtol=1e-300, maxit=10)
+    assert np.allclose(got.alphas, ref.alphas, rtol=1e-10)
+    # at maxit the textbook loop has already formed the next beta; the pipelined one
+    # forms it at the start of the following iteration
+    assert np.allclose(got.betas, ref.betas[:len(got.betas)], rtol=1e-10) and len(got.betas) == 9
+    assert np.allclose(got.x, ref.x, rtol=1e-9, atol=1e-12)
+    # the recurrence residual (the stopping test reads it) is the true residual: the
+    # coefficients do not depend on r, so only this catches an error in its recurrence
+    true_rel = np.linalg.norm(b - A @ got.x) / np.linalg.norm(b)
+    assert abs(got.relres - true_rel) <= 1e-12 and abs(got.relres - ref.relres) <= 1e-12
+
+
+def test_pipelined_reaches_direct_solution_with_schwarz(square16):
+    # on the 16 x 16 P2 case with the two-level preconditioner: the direct solution,
+    # iteration counts within 2 of the textbook PCG, recurrence residual near the true one
+    import scipy.sparse.linalg as spla
+    from oracle import schwarz
+    from oracle.pcg import pcg_pipelined
+    w, d = square16
+    S = schwarz.build(d, w.subdomain, w.coarse, w.q)
+    b = np.random.default_rng(7).standard_normal(d.n_dofs)
+    got = pcg_pipelined(d.K, b, prec=S.apply, rtol=1e-10)
+    ref = pcg(d.K, b, prec=S.apply, rtol=1e-10)
+    x = spla.spsolve(d.K.tocsc(), b)
+    assert got.converged and abs(got.iterations - ref.iterations) <= 2
+    assert np.linalg.norm(got.x - x) <= 1e-8 * np.linalg.norm(x)
+    true_rel = np.linalg.norm(b - d.K @ got.x) / np.linalg.norm(b)
+    assert true_rel <= 1e-9
+
