@@ -24,8 +24,10 @@ m(u, y) of Eq. monodomain is -dy/dt.
 PARITY UNPINNED as physics: the cited publications are not available to
 check these constants against.  What is pinned (tests/test_oracle_ionic.py):
 the rest state at the paper's u0 = -67 mV is close to equilibrium, gating
-steady states lie in (0, 1), and the rate functions' removable singularities
-are evaluated by their limits.
+steady states lie in (0, 1), the rate functions' removable singularities are
+evaluated by their limits, and each current vanishes at its Nernst reversal
+potential.  The coupling of f and of the state update into the time step is
+pinned there too, with currents whose discrete solution has a closed form.
 """
 import numpy as np
 

@@ -23,7 +23,13 @@ the method's PCG converges to that solution) or PCG with B_ad (Eq. prec).
 Pins (tests/test_oracle_monodomain.py): with f = 0 and no stimulus the
 scheme conserves int u (Neumann) exactly; on a single eigenmode of the
 generalised problem A v = lambda M v the amplification factor is
-(1 - dt lambda/2)/(1 + dt lambda/2).
+(1 - dt lambda/2)/(1 + dt lambda/2).  The ion term (tests/test_oracle_ionic.py):
+a linear current g u on an eigenmode follows the closed-form two-step recurrence
+(chi + dt lambda/2) a_{k+1} = (chi - dt lambda/2) a_k - chi dt g u~_k; an affine
+current on the constant mode and a current of the updated state likewise; with a
+frozen state a uniform field converges at second order in dt to the exact solution
+of u' = -f(u), and with the explicit state update at first order; the stimulus
+enters as dt F while t^{k+1/2} < duration.
 """
 from dataclasses import dataclass
 

@@ -38,25 +38,6 @@ def test_eigenmode_amplification_factor():
     assert np.allclose(st.U, g * v, atol=1e-10 * np.abs(v).max())
 
 
-def test_rest_state_is_near_equilibrium():
-    y0 = ionic.rest_state(-67.0)
-    assert 0 < y0[0] < 1 and 0 < y0[1] < 1
-    f = ionic.f_ion(np.array([-67.0]), y0[:, None])[0]
-    assert abs(f) < 0.01                                   # uA/cm^2
-    dy = ionic.dydt(np.array([-67.0]), y0[:, None])[:, 0]
-    assert abs(dy[0]) < 1e-12 and abs(dy[1]) < 1e-12       # gates at steady state
-    assert abs(dy[2]) < 1e-3 and abs(dy[3]) < 1e-3         # slow concentration drift
-
-
-def test_rate_singularities_are_continuous():
-    for v0 in (-30.0, -34.0):                              # removable points of alpha_m, alpha_n
-        V = np.array([v0 - 1e-4, v0, v0 + 1e-4])
-        am, _, an, _, _, _ = ionic.gating_rates(V)
-        a = am if v0 == -30.0 else an
-        assert np.all(np.isfinite(a))
-        assert abs(a[1] - 0.5 * (a[0] + a[2])) < 1e-6
-
-
 def test_first_step_uses_initial_state_for_extrapolation():
     d = small()
     md = monodomain.Monodomain(d, None)
