@@ -232,8 +232,23 @@ int asm_get_info(const asm_ctx *pc, asm_info *out);
 int asm_autotune(asm_ctx *pc, int rounds, int iterations, double *gain);
 
 /* z = B_ad^{-1} r (Eq. prec).  r_dev and z_dev are caller-order device vectors
- * and must not alias. */
+ * and must not alias.  Runs one launch of the persistent PCG kernel in its
+ * one-application mode (the local solves, restriction, coarse solve and prolongation
+ * of one PCG iteration, with the same work split and arithmetic as pcg_solve), on the
+ * context's work vectors (so not concurrently with pcg_solve on the same context).
+ * Synchronises `stream`.  Returns POLYDG_OK, POLYDG_ENONFINITE (NaN/Inf in r),
+ * POLYDG_ECUDA (a device-side wait timed out, or a CUDA error), POLYDG_EINVAL. */
 int asm_apply(asm_ctx *pc, const double *r_dev, double *z_dev, void *stream);
+
+/* Number of polls a grid barrier of the persistent PCG kernels makes before it gives
+ * up (default 2^22, about a second); polls < 0 restores the default.  Process-wide; it
+ * applies to launches whose arguments are built afterwards (pcg_solve, asm_apply,
+ * monodomain_step, and batches created afterwards).  When a barrier gives up, the
+ * kernel waits for its own copies in flight (with the default limit), stops, and the
+ * call returns POLYDG_ECUDA ("a device-side wait timed out"); the context stays
+ * usable.  A small limit is a way to exercise that path without a fault.
+ * Returns POLYDG_OK or POLYDG_EINVAL. */
+int polydg_set_wait_limit(int64_t polls);
 
 /* Solve K_h x = b by PCG (Saad Alg. 9.1) with B_ad^{-1} (pc != NULL) or without
  * preconditioner (pc == NULL: plain CG).  x_dev holds x0 on entry and the
@@ -307,6 +322,22 @@ int sim_set_potential(sim_ctx *sim, const double *u_dev, const double *uprev_dev
  * history of the subspace guess (a caller that keeps the state on the host restores
  * all of it this way).  Enqueued on `stream`. */
 int sim_set_history(sim_ctx *sim, const double *hist_dev, int count, void *stream);
+
+/* Restore a simulation's ionic state and step index k >= 0 (checkpoint / resume; with
+ * sim_set_history for the potentials, a resumed run continues bit for bit).  Nodal form:
+ * y_dev is [5][n_nodes] in sim_get_state's node order (required).  Modal form
+ * (sim_set_ionic_form, chosen before this call): Y_dev is [5][n_dofs], per state the
+ * caller-order DG coefficients as sim_get_ionic_coeffs returns them (required); y_dev, if
+ * given, restores the states at the nodes that sim_get_state reports until the next step.
+ * The index k sets the time t^k = k dt of the stimulus and the first-step extrapolation
+ * (k = 0), and bounds the history sim_set_history keeps (min(count, 17, k + 1)
+ * solutions), so call this before sim_set_history.  Clears a failed flag of an earlier
+ * step.  Enqueued on `stream`.  Errors: EINVAL, ECUDA. */
+int sim_set_state(sim_ctx *sim, const double *y_dev, const double *Y_dev, int64_t k, void *stream);
+
+/* Modal form only: copy the DG coefficients of the five ionic states to Y_dev
+ * ([5][n_dofs], per state caller order).  EINVAL for the nodal form. */
+int sim_get_ionic_coeffs(sim_ctx *sim, double *Y_dev, void *stream);
 
 /* Current step index k. */
 int64_t sim_step_index(const sim_ctx *sim);

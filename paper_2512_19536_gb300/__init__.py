@@ -11,7 +11,8 @@ from ._native import (PolyDG, ASM, Simulation, PolyDGError, load, polydg_setup, 
                       sim_set_potential, sim_set_history, spd_inverse_static, Batch, batch_create, batch_step,
                       GuessModel, guess_n_params, guess_create, guess_propose, guess_train_step,
                       sim_set_guess, SharedLocal, shared_local_setup, shared_local_apply,
-                      sim_set_shared_local, sim_set_ionic_form,
+                      sim_set_shared_local, sim_set_ionic_form, sim_set_state, sim_get_ionic_coeffs,
+                      set_wait_limit,
                       EXPORTS, LIB_PATH, POLYDG_OK, POLYDG_EINVAL, POLYDG_ENOMEM, POLYDG_ECUDA, POLYDG_ENOTSPD, POLYDG_ENOTCONV,
                       POLYDG_EBREAKDOWN, POLYDG_ENONFINITE)
 
@@ -21,5 +22,5 @@ __all__ = ["PolyDG", "ASM", "Simulation", "PolyDGError", "load", "polydg_setup",
            "sim_set_potential", "sim_set_history", "spd_inverse_static", "Batch", "batch_create", "batch_step",
            "GuessModel", "guess_n_params", "guess_create", "guess_propose", "guess_train_step",
            "sim_set_guess", "SharedLocal", "shared_local_setup", "shared_local_apply",
-           "sim_set_shared_local", "sim_set_ionic_form",
-           "EXPORTS", "LIB_PATH"]
+           "sim_set_shared_local", "sim_set_ionic_form", "sim_set_state", "sim_get_ionic_coeffs",
+           "set_wait_limit", "EXPORTS", "LIB_PATH"]

@@ -31,7 +31,8 @@ EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_setup3d", "polydg_get_in
            "guess_train_step", "sim_set_guess", "guess_destroy", "polydg_sym_eig",
            "shared_local_setup", "shared_local_info", "shared_local_apply", "shared_local_destroy",
            "sim_set_shared_local", "asm_autotune", "pcg_solve_trace", "pcg_lanczos_extremes",
-           "sim_set_history", "sim_set_ionic_form"]
+           "sim_set_history", "sim_set_ionic_form", "polydg_set_wait_limit", "sim_set_state",
+           "sim_get_ionic_coeffs"]
 
 
 class polydg_mesh(C.Structure):
@@ -145,6 +146,12 @@ def load() -> C.CDLL:
     L.sim_set_ionic_form.restype = i32
     L.shared_local_destroy.argtypes = [vp]
     L.shared_local_destroy.restype = None
+    L.polydg_set_wait_limit.argtypes = [i64]
+    L.polydg_set_wait_limit.restype = i32
+    L.sim_set_state.argtypes = [vp, vp, vp, i64, vp]
+    L.sim_set_state.restype = i32
+    L.sim_get_ionic_coeffs.argtypes = [vp, vp, vp]
+    L.sim_get_ionic_coeffs.restype = i32
     for name in ("guess_n_params", "guess_create", "guess_get_params", "guess_set_scales",
                  "guess_propose", "guess_train_step", "sim_set_guess"):
         getattr(L, name).restype = i32
@@ -455,6 +462,23 @@ def sim_set_history(sim: Simulation, hist, stream=None):
     _check(load().sim_set_history(sim.h, _dev(hist), count, _stream(stream)))
 
 
+def sim_set_state(sim: Simulation, k, y=None, Y=None, stream=None):
+    """Restore the ionic state (nodal form: y [5, n_nodes]; modal form: Y [5, n_dofs]) and
+    the step index k; call before sim_set_history."""
+    _check(load().sim_set_state(sim.h, _dev(y) if y is not None else None,
+                                _dev(Y) if Y is not None else None, int(k), _stream(stream)))
+
+
+def sim_get_ionic_coeffs(sim: Simulation, Y, stream=None):
+    """Modal form: the DG coefficients of the five ionic states into Y [5, n_dofs]."""
+    _check(load().sim_get_ionic_coeffs(sim.h, _dev(Y), _stream(stream)))
+
+
+def set_wait_limit(polls):
+    """Polls of a grid barrier before the persistent kernels give up (< 0: default)."""
+    _check(load().polydg_set_wait_limit(int(polls)))
+
+
 def spd_inverse_static(mats, n, ld, batch, stream=None):
     """In-place inversion of `batch` SPD float64 matrices (order n, leading dimension
     ld) held in the CUDA tensor `mats`, using only the library's fixed static
@@ -463,8 +487,12 @@ def spd_inverse_static(mats, n, ld, batch, stream=None):
         raise ValueError("expected a contiguous float64 CUDA tensor")
     if mats.numel() < batch * n * ld:
         raise ValueError("tensor smaller than batch * n * ld")
-    _check(load().polydg_spd_inverse_static(C.c_void_p(mats.data_ptr()), int(n), int(ld),
-                                            int(batch), _stream(stream)))
+    import torch
+    with torch.cuda.device(mats.device):      # the call runs on the device holding mats
+        if stream is None:
+            stream = torch.cuda.current_stream(mats.device)
+        _check(load().polydg_spd_inverse_static(C.c_void_p(mats.data_ptr()), int(n), int(ld),
+                                                int(batch), _stream(stream)))
 
 
 class GuessModel:

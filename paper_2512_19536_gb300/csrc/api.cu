@@ -1,6 +1,7 @@
 // C ABI of libpolydg (include/polydg.h): contexts, device buffers, the work
 // plan of the persistent PCG kernel and the launch sequence of a time step.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,28 +25,16 @@ namespace polydg {
 static thread_local std::string g_error;
 void set_error(const std::string& msg) { g_error = msg; }
 
+// Polls of a grid barrier of the persistent PCG kernels before they give up
+// (polydg_set_wait_limit); read when a launch's arguments are built.
+constexpr uint32_t kDefaultWaitPolls = 1u << 22;
+static std::atomic<uint32_t> g_wait_limit{kDefaultWaitPolls};
+
 }  // namespace polydg
 
 using namespace polydg;
 
 namespace polydg {
-
-// ---------------------------------------------------------- preconditioner plumbing
-static K2Args k2_args(polydg_ctx* c, asm_ctx* pc, PcgScalars* sc, double* partials) {
-    K2Args a = {};
-    a.K0inv = (pc && pc->has_coarse) ? pc->st64 + pc->off0 : nullptr;
-    a.n0 = (pc && pc->has_coarse) ? (int)pc->n0 : 0;
-    a.ld0 = (pc && pc->has_coarse) ? (int)pc->ld0 : 0;
-    a.nq = (pc && pc->has_coarse) ? pc->nq : 1;
-    a.rows_per_cta = 32;
-    a.pair_ptr = (pc && pc->has_coarse) ? pc->d_pair_ptr : c->d_zero_ptr;
-    a.r0p = pc ? pc->d_r0p : nullptr;
-    a.q0p = pc ? pc->d_q0p : nullptr;
-    a.y0 = pc ? pc->d_y0 : nullptr;
-    a.sc = sc;
-    a.partials = partials;
-    return a;
-}
 
 // Cut the plan's tile sequence into G contiguous runs of about equal cost (tile cost,
 // plus the stage cost of a tile that starts a subdomain within a run): greedy packing
@@ -365,6 +354,7 @@ static PersistArgs persist_args(polydg_ctx* c, asm_ctx* pc, const Plan& P, PcgWo
     a.bcast = w.bcast;
     a.gs = w.gs;
     a.err = w.err;
+    a.wait_limit = g_wait_limit.load();
     return a;
 }
 
@@ -509,7 +499,7 @@ int polydg_matvec(polydg_ctx* c, const double* x_dev, double* y_dev, void* strea
     const int np = c->H.n_p;
     CU(launch_permute(x_dev, nullptr, c->work.p, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
     CU(launch_matvec(MODE_PLAIN, np, c->K, c->K.val, c->work.p, c->work.q, nullptr, nullptr, 0, 0,
-                     nullptr, nullptr, nullptr, 0, 0, nullptr, nullptr, s));
+                     nullptr, 0, 0, s));
     CU(launch_permute(c->work.q, nullptr, y_dev, c->d_to_caller, c->H.nc, np, 0, nullptr, s));
     return POLYDG_OK;
 }
@@ -634,13 +624,7 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
         if ((st = cu(launch_cast_store(pc->st64, nullptr, pc->st16, local_elems, 0), "cast"))) return fail(st);
     }
     const int esz = precision == POLYDG_FP64 ? 8 : precision == POLYDG_FP32 ? 4 : 2;
-    // rows per tile: the tile's rows of K_i^{-1} (one bulk copy) fill <= 96 KB of
-    // shared memory, so two tiles fit on an SM
-    int64_t max_ld = 8;
-    for (int m = 0; m < H.n_sub; ++m) max_ld = std::max(max_ld, mats[m].ld);
-    pc->rows = (int)std::max<int64_t>(8, std::min<int64_t>(64, (96 * 1024 / (max_ld * esz)) / 8 * 8));
-    // LOCAL blocks and tiles
-    std::vector<GemvTile> tiles;
+    // LOCAL blocks: the dense K_i^{-1} of each subdomain
     for (int m = 0; m < H.n_sub; ++m) {
         GemvBlock B = {};
         B.mat_off = mats[m].off;
@@ -650,12 +634,7 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
         B.dtype = precision;
         B.in_off = B.out_off = H.sub_ptr[m] * np;
         pc->blocks.push_back(B);
-        for (int r0 = 0; r0 < B.nrows; r0 += pc->rows) tiles.push_back({m, r0});
         pc->store_bytes += (int64_t)B.nrows * B.ld * esz;
-        const size_t xsz = precision == POLYDG_FP64 ? 8 : 4;
-        const size_t need = (((size_t)pc->rows * B.ld * esz + 15) & ~(size_t)15) +
-                            (((size_t)B.ld * xsz + 15) & ~(size_t)15) + (size_t)pc->rows * 8;
-        pc->k1_smem = std::max(pc->k1_smem, need);
     }
     // RESTRICT blocks: rows of R_0 on the DOFs of each (agglomerate, subdomain)
     // pair, fp64, stored after the inverses in st64
@@ -712,10 +691,8 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
         dfree(pc->st64);
         pc->st64 = grown;
         for (auto& B : rblocks) {
-            tiles.push_back({(int32_t)pc->blocks.size(), 0});
             pc->blocks.push_back(B);
             pc->store_bytes += (int64_t)B.nrows * B.ld * 8;
-            pc->k1_smem = std::max(pc->k1_smem, (size_t)2 * B.ld * 8);
         }
         pc->store_bytes += n0 * mats.back().ld * 8;
         if ((st = upload(&pc->d_pair_ptr, pair_ptr)) || (st = upload(&pc->d_T, C.T)) ||
@@ -732,20 +709,11 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
         B.pair_count = (int32_t)pc->sub_pairs.size() - B.pair_begin;
     }
     pc->n_blocks = (int)pc->blocks.size();
-    pc->ntiles = (int)tiles.size();
-    pc->k2_smem = 2 * (size_t)n0 * sizeof(double);
-    if ((st = upload(&pc->d_blocks, pc->blocks)) || (st = upload(&pc->d_tiles, tiles)))
-        return fail(st);
-    if ((st = cu(set_precond_smem(pc->k1_smem), "precond smem")) ||
-        (st = cu(set_coarse_smem(pc->k2_smem), "coarse smem")))
-        return fail(st);
+    if ((st = upload(&pc->d_blocks, pc->blocks))) return fail(st);
     const int64_t npairs = std::max<int64_t>(pc->n_pairs, 1) * std::max(pc->nq, 1);
-    if ((st = dalloc(&pc->d_r0p, npairs)) || (st = dalloc(&pc->d_q0p, npairs)) ||
-        (st = dalloc(&pc->d_y0, std::max<int64_t>(n0, 1))) || (st = dalloc(&pc->d_r0g, std::max<int64_t>(n0, 1))) || (st = dalloc(&pc->d_rin, H.nc * np)) ||
-        (st = dalloc(&pc->d_zloc, H.nc * np)) || (st = dalloc(&pc->d_zout, H.nc * np)) ||
-        (st = dalloc(&pc->d_err, 1)))
+    if ((st = dalloc(&pc->d_r0p, npairs)) || (st = dalloc(&pc->d_y0, std::max<int64_t>(n0, 1))) ||
+        (st = dalloc(&pc->d_r0g, std::max<int64_t>(n0, 1))))
         return fail(st);
-    if ((st = cu(cudaMemset(pc->d_err, 0, sizeof(int)), "memset"))) return fail(st);
     if ((st = build_plan(c, pc, c->n_sm, pc->plan))) return fail(st);
     *out = pc;
     return POLYDG_OK;
@@ -943,24 +911,31 @@ int asm_apply(asm_ctx* pc, const double* r_dev, double* z_dev, void* stream) {
     polydg_ctx* c = pc->ctx;
     cudaStream_t s = (cudaStream_t)stream;
     const int np = c->H.n_p;
-    CU(launch_permute(r_dev, nullptr, pc->d_rin, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
-    K1Args a = {};
-    a.blocks = pc->d_blocks;
-    a.tiles = pc->d_tiles;
-    a.rows = pc->rows;
-    a.st64 = pc->st64; a.st32 = pc->st32; a.st16 = pc->st16;
-    a.x[0] = a.x[1] = nullptr;
-    a.r[0] = a.r[1] = pc->d_rin;
-    a.z = pc->d_zloc;
-    a.r0p = pc->d_r0p;
-    a.q0p = pc->d_q0p;
-    a.err = pc->d_err;
-    CU(launch_precond(a, pc->precision, pc->ntiles, pc->k1_smem, s));
-    if (pc->has_coarse) CU(launch_coarse(k2_args(c, pc, nullptr, nullptr), s));
-    CU(launch_direction(pc->has_coarse ? pc->nq : 3, nullptr, pc->d_zloc,
-                        pc->has_coarse ? pc->d_T : nullptr, pc->has_coarse ? pc->d_agg : nullptr,
-                        pc->d_y0, c->H.nc, np, nullptr, pc->d_zout, s));
-    CU(launch_permute(pc->d_zout, nullptr, z_dev, c->d_to_caller, c->H.nc, np, 0, nullptr, s));
+    // one launch of the persistent PCG kernel in its one-application mode: the P phase
+    // and the coarse + z part of the CM phase of an iteration, on r = the input
+    PcgScalars init = {};
+    init.maxit = 1;
+    *c->h_sc = init;
+    CU(cudaMemcpyAsync(c->work.sc, c->h_sc, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
+    CU(cudaMemsetAsync(c->work.err, 0, sizeof(int), s));
+    CU(launch_permute(r_dev, nullptr, c->work.b, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
+    PersistArgs a = persist_args(c, pc, pc->plan, c->work);
+    a.apply_only = 1;
+    CU(cudaMemsetAsync(&c->work.gs->count, 0, sizeof(unsigned), s));
+    CU(launch_pcg_persistent(pc->plan.dtype, np, a, pc->plan.smem, s));
+    CU(launch_permute(c->work.z, nullptr, z_dev, c->d_to_caller, c->H.nc, np, 0, nullptr, s));
+    CU(cudaMemcpyAsync(c->h_sc, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const int st = c->h_sc->status;
+    if (st != 0)
+        set_error(st == POLYDG_ECUDA ? "asm_apply: a device-side wait timed out"
+                                     : "asm_apply: non-finite value in r");
+    return st;
+}
+
+int polydg_set_wait_limit(int64_t polls) {
+    if (polls > (int64_t)UINT32_MAX) { set_error("polydg_set_wait_limit: at most 2^32 - 1 polls"); return POLYDG_EINVAL; }
+    g_wait_limit.store(polls < 0 ? kDefaultWaitPolls : (uint32_t)polls);
     return POLYDG_OK;
 }
 
@@ -1225,7 +1200,7 @@ static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
         CU(launch_ionic(np, sm->U, sm->Uprev, c->d_node_ptr, c->d_node_w, c->d_node_phi, sm->y, nn,
                         H.nc, dt, sm->I, sm->d_ss, s));
     CU(launch_matvec(MODE_RHS, np, c->K, c->K.val_minus, sm->U, w.b, sm->I, sm->F, -H.chi_cm * dt,
-                     dt, nullptr, nullptr, sm->d_ss, dt, sm->prm.stim_duration, nullptr, nullptr, s));
+                     dt, sm->d_ss, dt, sm->prm.stim_duration, s));
     if (sm->guess_policy == 3) {  // subspace of the learned proposal and the last increments
         const double* xg = nullptr;
         if (sm->guess) {
@@ -1536,6 +1511,37 @@ int sim_set_history(sim_ctx* sm, const double* hist_dev, int count, void* stream
     polydg_ctx* c = sm->ctx;
     CU(launch_history_set(c->K, hist_dev, count, sm->ring, sm->kuring, sm->U, sm->Uprev, sm->Uprev2,
                           c->d_to_caller, c->H.nc, c->H.n_p, sm->d_ss, (cudaStream_t)stream));
+    return POLYDG_OK;
+}
+
+int sim_set_state(sim_ctx* sm, const double* y_dev, const double* Y_dev, int64_t k, void* stream) {
+    if (!sm || k < 0) { set_error("sim_set_state: need a simulation and k >= 0"); return POLYDG_EINVAL; }
+    if (sm->Ym ? !Y_dev : !y_dev) {
+        set_error(sm->Ym ? "sim_set_state: the modal form needs the coefficients Y"
+                         : "sim_set_state: the nodal form needs the nodal states y");
+        return POLYDG_EINVAL;
+    }
+    polydg_ctx* c = sm->ctx;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nn = (int64_t)c->H.node_w.size(), n = c->H.nc * c->H.n_p;
+    if (y_dev) CU(launch_node_scatter(y_dev, sm->y, c->d_node_pos, nn, s));
+    if (sm->Ym)
+        for (int l = 0; l < bc::kStates; ++l)
+            CU(launch_permute(Y_dev + l * n, nullptr, sm->Ym + l * n, c->d_to_caller, c->H.nc, c->H.n_p, 1,
+                              nullptr, s));
+    CU(launch_set_step(sm->d_ss, k, s));
+    sm->k = k;
+    return POLYDG_OK;
+}
+
+int sim_get_ionic_coeffs(sim_ctx* sm, double* Y_dev, void* stream) {
+    if (!sm || !Y_dev) { set_error("sim_get_ionic_coeffs: null argument"); return POLYDG_EINVAL; }
+    if (!sm->Ym) { set_error("sim_get_ionic_coeffs: the simulation keeps its ionic state at the nodes"); return POLYDG_EINVAL; }
+    polydg_ctx* c = sm->ctx;
+    const int64_t n = c->H.nc * c->H.n_p;
+    for (int l = 0; l < bc::kStates; ++l)
+        CU(launch_permute(sm->Ym + l * n, nullptr, Y_dev + l * n, c->d_to_caller, c->H.nc, c->H.n_p, 0,
+                          nullptr, (cudaStream_t)stream));
     return POLYDG_OK;
 }
 
@@ -1923,9 +1929,9 @@ void sim_destroy(sim_ctx* sm) {
 void asm_destroy(asm_ctx* pc) {
     if (!pc) return;
     pc->plan.release();
-    dfree(pc->d_blocks); dfree(pc->d_tiles); dfree(pc->st64); dfree(pc->st32); dfree(pc->st16);
-    dfree(pc->d_T); dfree(pc->d_agg); dfree(pc->d_pair_ptr); dfree(pc->d_r0p); dfree(pc->d_q0p);
-    dfree(pc->d_y0); dfree(pc->d_r0g); dfree(pc->d_rin); dfree(pc->d_zloc); dfree(pc->d_zout); dfree(pc->d_err);
+    dfree(pc->d_blocks); dfree(pc->st64); dfree(pc->st32); dfree(pc->st16);
+    dfree(pc->d_T); dfree(pc->d_agg); dfree(pc->d_pair_ptr); dfree(pc->d_r0p);
+    dfree(pc->d_y0); dfree(pc->d_r0g);
     delete pc;
 }
 

@@ -140,13 +140,10 @@ struct asm_ctx {
     int precision = POLYDG_FP64;
     int has_coarse = 0, q = 0, nq = 0, n_agg = 0, n_pairs = 0;
     int64_t n0 = 0, ld0 = 0, off0 = 0;
-    int n_blocks = 0, ntiles = 0, rows = 32;
-    int* d_err = nullptr;               // device-wait timeout flag of asm_apply
+    int n_blocks = 0;
     Plan plan;                          // persistent-kernel plan with this preconditioner
     std::vector<int32_t> sub_pairs;     // RESTRICT block ids grouped by subdomain
-    size_t k1_smem = 0, k2_smem = 0;
     GemvBlock* d_blocks = nullptr;
-    GemvTile* d_tiles = nullptr;
     std::vector<GemvBlock> blocks;
     double* st64 = nullptr;
     float* st32 = nullptr;
@@ -157,11 +154,7 @@ struct asm_ctx {
     int max_pairs = 0;                  // most (agglomerate, subdomain) pairs of one agglomerate
     double* d_r0g = nullptr;            // R_0 r' summed by slices of the CTAs (split mode)
     double* d_r0p = nullptr;
-    double* d_q0p = nullptr;
     double* d_y0 = nullptr;
-    double* d_rin = nullptr;
-    double* d_zloc = nullptr;
-    double* d_zout = nullptr;
     int64_t store_bytes = 0;            // bytes of the dense stores read per apply
 };
 

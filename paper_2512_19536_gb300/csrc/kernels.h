@@ -10,7 +10,7 @@
 
 namespace polydg {
 
-enum MatvecMode { MODE_PLAIN = 0, MODE_PCG = 1, MODE_RESID = 2, MODE_RHS = 3 };
+enum MatvecMode { MODE_PLAIN = 0, MODE_RHS = 3 };
 
 // Subspace initial guess (policy 3): the last kHistDirs solution increments, plus the
 // learned proposal, combined by a Galerkin projection.  The solutions live in a ring
@@ -50,40 +50,6 @@ struct DeviceMatrix {
     int32_t* col = nullptr;
     double* val = nullptr;        // K_h
     double* val_minus = nullptr;  // chi_cm M - dt/2 A
-};
-
-// Arguments of the preconditioner kernel K1 (see kernels_linalg.cu).
-struct K1Args {
-    const GemvBlock* blocks;
-    const GemvTile* tiles;
-    int rows;
-    int use_cond;
-    const double* st64;
-    const float* st32;
-    const __nv_bfloat16* st16;
-    double* x[2];              // parity buffers of the iterate
-    double* r[2];              // parity buffers of the residual
-    const double* p;
-    const double* q;           // K p of the previous iteration (nullptr: alpha = 0)
-    double* z;                 // z_loc
-    double* r0p;               // per-(agglomerate, subdomain) partial R_0 r
-    double* q0p;               // per-(agglomerate, subdomain) partial R_0 q
-    PcgScalars* sc;            // nullptr: apply only (no commit, no dots)
-    double* partials;
-    int* err;                  // set to 1 if a bulk copy did not complete in time
-    cudaGraphConditionalHandle cond;
-};
-
-// Arguments of the coarse kernel K2.
-struct K2Args {
-    const double* K0inv;
-    int n0, ld0, nq, rows_per_cta;
-    const int64_t* pair_ptr;   // [n_agg + 1] pairs of each agglomerate
-    const double* r0p;
-    const double* q0p;
-    double* y0;
-    PcgScalars* sc;
-    double* partials;
 };
 
 // Grid-barrier state of a cooperative launch (count returns to 0 after each barrier).
@@ -147,7 +113,9 @@ struct PersistArgs {
     long long* cta_cycles;                     // [2 * grid] P and CM work cycles per CTA, or null
     double* trace;                             // [2 * trace_cap]: alpha_k, then beta_k, or null
     int trace_cap;
-    int pad_trace;
+    int apply_only;                            // 1: z = B_ad^{-1} b once (r = b, no solve)
+    uint32_t wait_limit;                       // polls of a grid barrier before it gives up
+    int pad_wait;
 };
 
 constexpr int kMaxWarpStages = 4;              // copy slots per warp in the P phase
@@ -234,16 +202,8 @@ cudaError_t group_occupancy(int qdtype, int np, size_t smem, int* blocks_per_sm)
 
 cudaError_t launch_matvec(int mode, int np, const DeviceMatrix& K, const double* val,
                           const double* x, double* y, const double* v1, const double* v2,
-                          double c1, double c2, PcgScalars* sc, double* partials,
-                          const SimScalars* ss, double dt, double stim_duration, double* zero1,
-                          double* zero2, cudaStream_t s);
-cudaError_t launch_precond(const K1Args& a, int dtype, int ntiles, size_t smem, cudaStream_t s);
-cudaError_t set_precond_smem(size_t smem);
-cudaError_t launch_coarse(const K2Args& a, cudaStream_t s);
-cudaError_t set_coarse_smem(size_t smem);
-cudaError_t launch_direction(int nq, double* p, const double* zl, const double* T,
-                             const int32_t* agg, const double* y0, int64_t nc, int np,
-                             const PcgScalars* sc, double* out, cudaStream_t s);
+                          double c1, double c2, const SimScalars* ss, double dt,
+                          double stim_duration, cudaStream_t s);
 cudaError_t launch_permute(const double* src, const double* src_odd, double* dst,
                            const int64_t* to_caller, int64_t nc, int np, int to_internal,
                            const PcgScalars* sc, cudaStream_t s);
@@ -328,5 +288,9 @@ cudaError_t launch_step_finish(double* U, double* Uprev, double* Uprev2, const d
                                double* ring, cudaStream_t s);
 cudaError_t launch_step_begin(PcgScalars* sc, SimScalars* ss, cudaStream_t s);
 cudaError_t launch_init_y(double* y, int64_t nn, const double* y0, cudaStream_t s);
+cudaError_t launch_node_scatter(const double* y_caller, double* y_int,
+                                const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s);
+// Step index k of a simulation (and its failed flag cleared), for a restored state.
+cudaError_t launch_set_step(SimScalars* ss, int64_t k, cudaStream_t s);
 
 }  // namespace polydg

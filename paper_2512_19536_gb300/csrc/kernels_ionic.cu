@@ -233,6 +233,33 @@ cudaError_t launch_node_gather(const double* y_int, double* y_caller,
     return cudaGetLastError();
 }
 
+// The reverse of node_gather_kernel: caller node order -> internal node order.
+__global__ void node_scatter_kernel(const double* __restrict__ yc, double* __restrict__ yi,
+                                    const int64_t* __restrict__ pos, int64_t nn) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nn) return;
+    const int64_t d = pos[q];
+#pragma unroll
+    for (int s = 0; s < 5; ++s) yi[s * nn + q] = yc[s * nn + d];
+}
+
+cudaError_t launch_node_scatter(const double* y_caller, double* y_int,
+                                const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s) {
+    node_scatter_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(y_caller, y_int,
+                                                                    node_to_caller_pos, nn);
+    return cudaGetLastError();
+}
+
+__global__ void set_step_kernel(SimScalars* ss, int64_t k) {
+    ss->k = k;
+    ss->failed = 0;
+}
+
+cudaError_t launch_set_step(SimScalars* ss, int64_t k, cudaStream_t s) {
+    set_step_kernel<<<1, 1, 0, s>>>(ss, k);
+    return cudaGetLastError();
+}
+
 __global__ void init_y_kernel(double* y, int64_t nn, const double* y0) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nn) return;

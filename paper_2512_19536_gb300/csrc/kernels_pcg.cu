@@ -20,7 +20,11 @@
 // Every CTA sums the per-CTA partials in the same order, so all CTAs hold
 // bit-identical scalars and take the same branches; the result is deterministic.
 // Waits (grid barriers, mbarriers) are bounded: on timeout the kernel raises an
-// error flag, waits (bounded) for its own copies in flight and stops.
+// error flag, waits (bounded) for its own copies in flight and stops.  A grid
+// barrier gives up after a.wait_limit polls.
+// With a.apply_only the launch applies the preconditioner once, z = B_ad^{-1} b: r = b,
+// one P phase (alpha = beta = 0, so r' = r), the coarse solve and the z part of the CM
+// phase, then it stops -- the same code that every PCG iteration runs.
 #include <type_traits>
 
 #include <cuda_runtime.h>
@@ -50,6 +54,8 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
     const bool flexible = sc->flexible != 0;
     const double rtol2 = sc->rtol2;
     const int maxit = sc->maxit;
+    const bool apply = a.apply_only != 0;
+    const uint32_t wl = a.wait_limit;
     unsigned gen = 0;                 // barrier target of thread 0 (gs->count is 0 at launch)
 
     const int S = a.wstages;                                       // copy slots per warp
@@ -76,7 +82,15 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         a.z[t] = 0.0; a.w[t] = 0.0;
     }
     double v2[2] = {0.0, 0.0};
-    for (int ch = ch0; ch < ch1; ++ch) {        // chunks of the CTA's elements
+    if (apply) {                                // r = b: the preconditioner's input
+        for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) {
+            const double bv = a.b[t];
+            a.r[0][t] = bv;
+            v2[0] = fma(bv, bv, v2[0]);
+        }
+        v2[1] = v2[0];
+    }
+    for (int ch = ch0; ch < (apply ? ch0 : ch1); ++ch) {        // chunks of the CTA's elements
         const int64_t ce0 = a.chunk_elem[ch], ce1 = a.chunk_elem[ch + 1];
         const int32_t* need = a.need + a.need_ptr[ch];
         const int n_need = a.need_ptr[ch + 1] - a.need_ptr[ch];
@@ -151,7 +165,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         }
         n_issued = S;
     }
-    bool ok = barrier_sum<2>(a.gs, G, cta, gen, a.err, a.partials, v2, red, outv, [](const double*) {});
+    bool ok = barrier_sum<2>(a.gs, G, cta, gen, a.err, a.partials, v2, red, outv, [](const double*) {}, wl);
     const double bb = v2[0];
     double rr = v2[1];
     int status = kOK, it = 0, done = 0, par = 0, pp = 0;
@@ -159,6 +173,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
     int pending = 0;                  // alpha p_k / alpha q_k not yet committed to x, r
     if (!ok) { status = kEDEVICE; done = 1; }
     else if (!isfinite(bb) || !isfinite(rr)) { status = kENONFINITE; done = 1; }
+    else if (apply) { relres = 1.0; }          // one application: no stopping test
     else if (bb == 0.0) { done = 2; }
     else { relres = sqrt(rr / bb); if (rr <= rtol2 * bb) done = 1; }
 
@@ -304,8 +319,8 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         }
         ok = barrier_sum<1>(a.gs, G, cta, gen, a.err, a.partials, v1, red, outv, [&](const double* sm) {
             const double r2 = sm[0];
-            scode = !isfinite(r2) ? 2 : (r2 <= rtol2 * bb) ? 1 : (it + pending >= maxit) ? 3 : 0;
-        });
+            scode = !isfinite(r2) ? 2 : apply ? 0 : (r2 <= rtol2 * bb) ? 1 : (it + pending >= maxit) ? 3 : 0;
+        }, wl);
         rr = v1[0];
         it += pending;
         pending = 0;
@@ -343,7 +358,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
             };
             if (a.r0_split) {
                 pair_sums((int)(((int64_t)a.n0 * cta) / G), (int)(((int64_t)a.n0 * (cta + 1)) / G), a.r0g);
-                ok = grid_barrier(a.gs, G, gen, a.err);
+                ok = grid_barrier(a.gs, G, gen, a.err, wl);
                 if (!ok) { status = kEDEVICE; break; }
                 if (a.redundant || c1 > c0) {
                     for (int idx = threadIdx.x; idx < a.n0; idx += blockDim.x) r0s[idx] = __ldcg(a.r0g + idx);
@@ -385,7 +400,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                     const double y = coarse_row(row);
                     if (lane == 0) a.y0[row] = y;
                 }
-                ok = grid_barrier(a.gs, G, gen, a.err);
+                ok = grid_barrier(a.gs, G, gen, a.err, wl);
                 if (!ok) { status = kEDEVICE; break; }
             }
             __syncthreads();
@@ -419,6 +434,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 if (l < n_chunk) a.z[t] = v;
             }
             __syncthreads();
+            if (apply) continue;                  // z is the result: no matvec
             local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, ce0, ce1, [&](int64_t e, int i, double kz) {
                 const int64_t t = e * NP + i;
                 const double zv = pn[(e - ce0) * NP + i];
@@ -428,6 +444,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 v3[2] = fma(zv, kz, v3[2]);
             });
         }
+        if (apply) break;                         // status kOK: z = B_ad^{-1} b is complete
         // beta, p.q and alpha by thread 0: code 0 go on, 2 non-finite, 4 breakdown
         if (timing) {
             __syncthreads();
@@ -450,7 +467,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 if (it < a.trace_cap) a.trace[it] = scal[0];
                 if (it > 0 && it - 1 < a.trace_cap) a.trace[a.trace_cap + it - 1] = bnew;
             }
-        });
+        }, wl);
         if (!ok) { status = kEDEVICE; break; }
         const int code3 = scode;
         if (code3 == 2) { status = kENONFINITE; break; }

@@ -89,6 +89,15 @@ extern "C" int polydg_spd_inverse_static(double* mats_dev, int n, int ld, int ba
         set_error("polydg_spd_inverse_static: no CUDA device");
         return POLYDG_ECUDA;
     }
+    // the matrices must live on the current device: the kernel runs there, and a pointer
+    // to another GPU's (or host) memory would be read through the wrong address space
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, mats_dev) != cudaSuccess ||
+        (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) || attr.device != dev) {
+        cudaGetLastError();
+        set_error("polydg_spd_inverse_static: mats_dev is not device memory of the current device");
+        return POLYDG_EINVAL;
+    }
     unsigned char* base = nullptr;
     if (int st = static_scratch(dev, &base)) return st;
     double* work = reinterpret_cast<double*>(base);

@@ -13,7 +13,7 @@
 
 namespace polydg {
 
-constexpr uint32_t kSpinLimit = 1u << 22;     // bounded polls for every wait
+constexpr uint32_t kSpinLimit = 1u << 22;     // bounded polls for every wait (default)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -89,8 +89,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // to reset or flip anything.  The arrive is a
 // fire-and-forget release reduction after a fence that publishes the CTA's
 // writes; waiters poll with acquire loads.  `target` lives in thread 0.
-// Returns false (and raises *err) if the other CTAs did not arrive in time.
-__device__ __forceinline__ bool grid_barrier(GridSync* gs, unsigned G, unsigned& target, int* err) {
+// Returns false (and raises *err) if the other CTAs did not arrive within `limit` polls.
+__device__ __forceinline__ bool grid_barrier(GridSync* gs, unsigned G, unsigned& target, int* err,
+                                             uint32_t limit = kSpinLimit) {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -100,7 +101,7 @@ __device__ __forceinline__ bool grid_barrier(GridSync* gs, unsigned G, unsigned&
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gs->count) : "memory");
         uint32_t k = 0;
         while ((int)(ld_acquire(&gs->count) - target) < 0) {
-            if (++k > kSpinLimit) { ok = 0; atomicExch(err, 1); break; }
+            if (++k > limit) { ok = 0; atomicExch(err, 1); break; }
         }
         ok_sh = ok && (*((volatile int*)err) == 0);
     }
@@ -118,7 +119,8 @@ __device__ __forceinline__ bool grid_barrier(GridSync* gs, unsigned G, unsigned&
 // red: shared scratch of 3 x blockDim.x doubles, outv: N shared doubles.
 template <int N, typename Fin>
 __device__ __forceinline__ bool barrier_sum(GridSync* gs, unsigned G, int cta, unsigned& gen, int* err,
-                            double* partials, double (&v)[N], double* red, double* outv, Fin&& fin) {
+                            double* partials, double (&v)[N], double* red, double* outv, Fin&& fin,
+                            uint32_t limit = kSpinLimit) {
     static_assert(N >= 1 && N <= 12, "up to twelve sums (three at a time through red)");
     const int t = threadIdx.x, lane = t & 31;
 #pragma unroll
@@ -137,7 +139,7 @@ __device__ __forceinline__ bool barrier_sum(GridSync* gs, unsigned G, int cta, u
             }
         }
     }
-    const bool ok = grid_barrier(gs, G, gen, err);
+    const bool ok = grid_barrier(gs, G, gen, err, limit);
     if (t < 32) {
         double sum[N];
 #pragma unroll

@@ -11,8 +11,8 @@ P4 mesh with 6 x 6-cell agglomerates (576 pairs x 15 coarse modes: the kernel su
 restriction partials by slices of the CTAs behind an extra grid barrier, 4 lanes per
 coarse DOF).
 
-Tolerances as in test_gpu_parity.py: B_ad r within 1e-9 (fp64 store) and 1e-4 (fp32
-store) relative; solutions at rtol 1e-12 within 1e-8 of a direct solve in the function
+Tolerances as in test_gpu_parity.py: B_ad r within 1e-9 (fp64 store), 1e-4 (fp32
+store) and 5e-2 (bf16 store) relative, in the 2-norm and entry by entry; solutions at rtol 1e-12 within 1e-8 of a direct solve in the function
 L2 norm; iteration counts at the paper's tolerance 1e-9 within max(3, its / 50) of the
 oracle's PCG (these solves take up to ~500 iterations, along which the two sides'
 rounding drifts apart); the largest Ritz value within 1e-8 of the oracle's (it
@@ -76,12 +76,14 @@ def test_mp_asm_apply(case, voronoi256):
     S = oracle_schwarz(case, wm, d)
     r = np.random.default_rng(51).standard_normal(d.n_dofs)
     ref = S.apply(r)
-    for prec, tol in (("fp64", 1e-9), ("fp32", 1e-4)):
+    for prec, tol in (("fp64", 1e-9), ("fp32", 1e-4), ("bf16", 5e-2)):
         pc = pd.asm_setup(ctx, wm.coarse, q=wm.q, precision=prec)
         assert pc.info()["n_subdomains"] == wm.mesh.n_cells
         z = dev(np.zeros(d.n_dofs))
         pd.asm_apply(pc, dev(r), z)
-        assert np.linalg.norm(host(z) - ref) <= tol * np.linalg.norm(ref), prec
+        got = host(z)
+        assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), prec
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), prec
 
 
 @pytest.mark.parametrize("case", CASES)

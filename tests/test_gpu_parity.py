@@ -96,6 +96,7 @@ def test_asm_apply_fp64(case, request):
     pd.asm_apply(pc, dev(r), z)
     got, ref = host(z), S.apply(r)
     assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()        # entry by entry
 
 
 def test_asm_apply_one_level(vor):
@@ -107,7 +108,9 @@ def test_asm_apply_one_level(vor):
     r = np.random.default_rng(5).standard_normal(d.n_dofs)
     z = dev(np.zeros(d.n_dofs))
     pd.asm_apply(pc, dev(r), z)
-    assert np.linalg.norm(host(z) - S.apply(r)) <= 1e-9 * np.linalg.norm(S.apply(r))
+    ref = S.apply(r)
+    assert np.linalg.norm(host(z) - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert np.abs(host(z) - ref).max() <= 1e-9 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -125,6 +128,33 @@ def test_asm_apply_reduced_precision_error_bound(vor, prec):
     ref = S.apply(r)
     tol = 1e-4 if prec == "fp32" else 5e-2
     assert np.linalg.norm(host(z) - ref) <= tol * np.linalg.norm(ref)
+    assert np.abs(host(z) - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_asm_apply_edge_cases(vor):
+    # r = 0 gives z = 0 exactly; a NaN in r is reported, and the context stays usable
+    w, d, ctx = vor
+    pd = lib()
+    pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision="fp32")
+    z = dev(np.full(d.n_dofs, 7.0))
+    pd.asm_apply(pc, dev(np.zeros(d.n_dofs)), z)
+    assert np.array_equal(host(z), np.zeros(d.n_dofs))
+    r = np.random.default_rng(8).standard_normal(d.n_dofs)
+    r[17] = np.nan
+    with pytest.raises(pd.PolyDGError) as e:
+        pd.asm_apply(pc, dev(r), z)
+    assert e.value.status == pd.POLYDG_ENONFINITE
+    r[17] = 0.5
+    pd.asm_apply(pc, dev(r), z)
+    assert np.all(np.isfinite(host(z)))
+    # the application is linear and deterministic: B (2r) = 2 B r bit for bit (a power of
+    # two scales every rounding exactly), and two calls agree bit for bit
+    z2 = dev(np.zeros(d.n_dofs))
+    pd.asm_apply(pc, dev(2.0 * r), z2)
+    assert np.array_equal(host(z2), 2.0 * host(z))
+    z3 = dev(np.zeros(d.n_dofs))
+    pd.asm_apply(pc, dev(r), z3)
+    assert np.array_equal(host(z3), host(z))
 
 
 @pytest.mark.parametrize("case", ["sq", "vor"])
