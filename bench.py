@@ -1,39 +1,44 @@
 #!/usr/bin/env python3
 """Benchmark: ASM-PCG time-steps/s on the coupled PolyDG monodomain + Barreto-Cressman
-workload (4096-cell Voronoi mesh of the unit square, P3, anisotropic fibre
-conductivity, 64 k-means subdomains = coarse agglomerates, coarse P1, dt = 0.05 ms,
-Gaussian stimulus), every step solved by PCG with the two-level additive Schwarz
-preconditioner to |r|_2 <= 1e-8 |b|_2 on one GB300.
+step, every step solved by PCG with the two-level additive Schwarz preconditioner to
+|r|_2 <= 1e-8 |b|_2 on one GB300.
 
-A "step" is one Crank-Nicolson time step through the C ABI (monodomain_step):
-ionic update at the quadrature nodes, right-hand side, initial guess, and the
-persistent PCG kernel.  By default the 3 warm-up and 197 timed steps together are the
-workload's 200 steps.  Three forms are timed on the same setup:
-  * mixed + learned: fp32 local inverses in flexible PCG (fp64 residual, dots, coarse
-    solve and matvec) with the learned initial guess (the network trained by
-    paper_2512_19536_gb300/guess_train.py on eight other meshes' trajectories, weights in
-    paper_2512_19536_gb300/guess_p3_voronoi4096.npz; kept per step only if its residual
-    is smaller than U^k's) -- the reported value;
-  * mixed: the same with x0 = U^k;
+Default workload (the largest single-GPU configuration): the unit cube in 48^3 jittered
+hexahedra (12-facet polyhedra), P2, 1,105,920 DOFs, 1728 subdomains of 4^3 cells = coarse
+agglomerates, coarse P1 (6912 DOFs), isotropic sigma = 1, dt = 0.05 ms, Gaussian
+stimulus; the workload's 50 steps cover the warm-up and the timed steps.
+
+A "step" is one Crank-Nicolson time step through the C ABI (monodomain_step): ionic
+update at the quadrature nodes, right-hand side, initial guess, and the persistent PCG
+kernel.  Forms timed on the same setup:
+  * mixed + learned (reported): fp32 local inverses in flexible PCG (fp64 residual, dots,
+    coarse solve and matvec); initial guess = Galerkin projection onto the learned
+    proposal (weights in paper_2512_19536_gb300/guess_p3_voronoi4096.npz) and the last 16
+    solution increments;
+  * the increments alone (no network), and x0 = U^k, as ablations;
   * fp64 plain: fp64 local inverses in standard PCG, x0 = U^k.
 Each preconditioner's split of its work over the CTAs is autotuned at setup
-(asm_autotune, six rounds: 26 solves of 60 timed iterations each), which is not part of
-the timed steps.
-The working set (fp32 store 112 MB + K_h 22.5 MB + vectors) exceeds the 126 MB
-L2, so no L2 flush is inserted between steps.
+(asm_autotune), which is not part of the timed steps.  The 4096-cell Voronoi P3 workload
+(the 2D configuration) is timed in the same run and reported under config.voronoi4096.
+The working sets (fp32 store 2.8 GB + K_h 608 MB at 48^3) exceed the 126 MB L2, so no L2
+flush is inserted between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload voronoi4096|batch32]
+                       [--workload hex48|voronoi4096|batch32|hex32|hex24]
+                       [--ionic-form nodal|modal]
 Under torchrun (N > 1) every rank runs an independent replica (the path has no
 exchange step); rank 0 prints one JSON line with the whole-job throughput.
 
---workload batch32 times the batched forms instead: 32 independent simulations on 8
-Voronoi meshes of 1024-16384 cells (log-uniform), 4 per mesh with scalar
-conductivities U[0.5, 2] and random stimulus sites.  Reported: the 4 simulations of each
-mesh in lockstep sharing one bf16 eigenbasis of every subdomain (all solves of a step in
-one persistent launch); beside it the batched form with each simulation's own fp32
-inverses and the fp64 plain form stepped one simulation after another; the unit is
-simulation-steps/s.
+--workload voronoi4096 reports the 2D workload alone (200 steps); --workload batch32
+the batched forms: 32 independent simulations on 8 Voronoi meshes of 1024-16384 cells,
+4 per mesh, the 4 simulations of each mesh in lockstep sharing one bf16 eigenbasis (unit:
+simulation-steps/s).  --ionic-form modal keeps the ionic state in the DG basis (the
+second line of Eq. fully-discrete-1) in every timed form.
+
+The CPU baseline (and --impl reference) is the float64 oracle (oracle/) on the host
+cores, timed on whole time steps of a stated sub-problem of the same recipe (the 8^3
+cube for the 3D workload) and scaled to the workload by its DOFs (and, in the CPU
+baseline, by the GPU's iteration count); the scaling is stated in the line.
 """
 import argparse
 import json
@@ -165,12 +170,14 @@ GUESS_POLICY = 3   # Galerkin projection onto the learned proposal and the last 
 
 
 def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clocks=None,
-              guess=None, pc=None, policy=None):
+              guess=None, pc=None, policy=None, ionic_form="nodal"):
     if pc is None:
         pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision=precision)
         pd.asm_autotune(pc, rounds=6, iterations=60)   # setup: re-cut the rows by measured CTA times
     sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-8, maxit=5000,
                         flexible=flexible)
+    if ionic_form != "nodal":
+        pd.sim_set_ionic_form(sim, ionic_form)
     if policy is not None:
         pd.sim_set_guess(sim, guess, policy)
     pd.monodomain_step(sim, warmup, stream)
@@ -191,7 +198,7 @@ def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clo
     return pc, sim, st, ms
 
 
-def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None, warm=12):
+def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None, warm=12, ionic_form="nodal"):
     """Same metric with the state crossing the host boundary every step: the last
     solutions the step depends on (U^k .. U^{k-16}: the initial guess reads them) copied in
     from pinned host memory and restored with sim_set_history, U^{k+1} copied back to
@@ -199,6 +206,8 @@ def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None, warm=12):
     `steps` timed."""
     sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-8, maxit=5000,
                         flexible=True)
+    if ionic_form != "nodal":
+        pd.sim_set_ionic_form(sim, ionic_form)
     pd.sim_set_guess(sim, guess, GUESS_POLICY)
     n = ctx.n_dofs
     H = 17
@@ -232,67 +241,124 @@ def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None, warm=12):
     return steps / dt, H * 8 * n, 8 * n
 
 
-def cpu_baseline(w, its_per_step, sample_its=40):
-    """The oracle (oracle.monodomain with oracle.pcg and oracle.schwarz, float64 on
-    the host cores) timed on a bounded sample: one right-hand side (ionic update and
-    load) and `sample_its` ASM-PCG iterations, extrapolated to `its_per_step`."""
-    import numpy as np
-    from oracle import assembly, schwarz, monodomain
-    from oracle.pcg import pcg
-    d = assembly.assemble(w.mesh, w.p, w.sigma, w.eta0, w.chi_cm, w.dt)
-    S = schwarz.build(d, w.subdomain, w.coarse, w.q)
-    md = monodomain.Monodomain(d, w.stimulus, u0=w.u_rest, solver="pcg", prec=S.apply, rtol=1e-8)
-    t0 = time.perf_counter()
-    b, _ = md.rhs(md.state)
-    t_rhs = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    pcg(d.K, b, x0=np.zeros_like(b), prec=S.apply, rtol=1e-30, maxit=sample_its)
-    t_it = (time.perf_counter() - t0) / sample_its
-    t_step = t_rhs + its_per_step * t_it
-    return t_step, t_rhs, t_it
+class Oracle:
+    """Whole time steps of the float64 oracle (oracle.monodomain with oracle.pcg and the
+    two-level oracle.schwarz preconditioner, rtol 1e-8, x0 = U^k) on workload w."""
+
+    def __init__(self, w, ionic_form="nodal"):
+        from oracle import assembly, schwarz, monodomain
+        self.w = w
+        self.d = assembly.assemble(w.mesh, w.p, w.sigma, w.eta0, w.chi_cm, w.dt)
+        S = schwarz.build(self.d, w.subdomain, w.coarse, w.q)
+        self.md = monodomain.Monodomain(self.d, w.stimulus, u0=w.u_rest, solver="pcg",
+                                        prec=S.apply, rtol=1e-8, ionic_form=ionic_form)
+
+    def steps(self, k):
+        """k timed steps: (seconds per step, seconds of the ionic update + right-hand side
+        per step, PCG iterations per step).  The right-hand side is timed by one extra
+        evaluation before each step (it has no side effect on the state)."""
+        t_step, t_rhs = 0.0, 0.0
+        for _ in range(k):
+            t0 = time.perf_counter()
+            self.md.rhs(self.md.state)
+            t1 = time.perf_counter()
+            self.md.step()
+            t2 = time.perf_counter()
+            t_rhs += t1 - t0
+            t_step += t2 - t1
+        return t_step / k, t_rhs / k, sum(self.md.iterations[-k:]) / k
+
+
+def on_cores(n, fn):
+    """fn() with this process pinned to its first n allowed cores (None: all of them);
+    returns (fn(), cores used)."""
+    allowed = sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None
+    if n is None or allowed is None:
+        return fn(), (len(allowed) if allowed else os.cpu_count())
+    try:
+        os.sched_setaffinity(0, set(allowed[:n]))
+        return fn(), min(n, len(allowed))
+    finally:
+        os.sched_setaffinity(0, set(allowed))
+
+
+def sub_workload(name):
+    """The oracle's sub-problem of a workload: the same recipe on a smaller mesh."""
+    if name.startswith("hex"):
+        from synth import hex_cube_p2
+        return hex_cube_p2(n=8)
+    from synth import voronoi4096_p3
+    return voronoi4096_p3(n_cells=1024, n_parts=16)
+
+
+def cpu_baseline(name, w_full, n_full, its_gpu, steps=3, warm=1, ionic_form="nodal"):
+    """The oracle timed on whole steps of the workload's sub-problem (the same recipe on a
+    smaller mesh), on one core and on all cores, and scaled to the workload: by the DOF
+    ratio (the oracle's work per step grows linearly with the cells at a fixed iteration
+    count) and, for the PCG part, by the ratio of the GPU's iteration count at full size
+    to the oracle's on the sub-problem."""
+    w = sub_workload(name)
+    o = Oracle(w, ionic_form)
+    o.steps(warm)
+    n_sub = o.d.n_dofs
+    (t1, r1, it1), c1 = on_cores(1, lambda: o.steps(steps))
+    (ta, ra, ita), ca = on_cores(None, lambda: o.steps(steps))
+    scale = n_full / n_sub
+
+    def est(t, r, it):
+        return scale * (r + (t - r) * its_gpu / max(it, 1e-9))
+
+    sample = (f"{steps} whole oracle steps (after {warm} warm-up) of the same recipe on "
+              f"{w.name} ({w.mesh.n_cells} cells, {n_sub} DOFs, {len(set(w.subdomain.tolist()))} "
+              f"subdomains): {ta:.3f} s/step on {ca} cores ({ra:.3f} s ionic update + RHS, "
+              f"{ita:.1f} PCG iterations), {t1:.3f} s/step on 1 core; scaled by the DOF ratio "
+              f"{scale:.1f} and, for the PCG part, by {its_gpu:.1f}/{ita:.1f} iterations "
+              f"(the fp64 plain GPU form's at full size over the oracle's)")
+    return {"value": 1.0 / est(ta, ra, ita), "unit": "time-steps/s", "cores": ca, "kind": "oracle",
+            "sample": sample,
+            "one_core": {"value": 1.0 / est(t1, r1, it1), "unit": "time-steps/s", "cores": c1},
+            "sub_problem_steps_per_s": {"all_cores": 1.0 / ta, "one_core": 1.0 / t1}}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle of the same method on the same workload."""
+    """Reference arm: the float64 CPU oracle of the same method, whole time steps of the
+    workload's stated sub-problem, scaled to the workload by the DOF ratio."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    w = build_case()
-    import numpy as np
-    from oracle import assembly, schwarz, monodomain
-    from oracle.pcg import pcg
-    d = assembly.assemble(w.mesh, w.p, w.sigma, w.eta0, w.chi_cm, w.dt)
-    S = schwarz.build(d, w.subdomain, w.coarse, w.q)
-    md = monodomain.Monodomain(d, w.stimulus, u0=w.u_rest, solver="pcg", prec=S.apply, rtol=1e-8)
-    sample_its = 10
-    # one full step fixes the iteration count that each sampled step is scaled to
-    b, _ = md.rhs(md.state)
-    full = pcg(d.K, b, x0=md.state.U, prec=S.apply, rtol=1e-8)
-    its = full.iterations
-    times = []
-    for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        b, _ = md.rhs(md.state)
-        t_rhs = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        pcg(d.K, b, x0=md.state.U, prec=S.apply, rtol=1e-30, maxit=sample_its)
-        t_it = (time.perf_counter() - t0) / sample_its
-        if k >= args.warmup:
-            times.append(t_rhs + its * t_it)
-    total = sum(times)
-    value = len(times) / total
-    cores = os.cpu_count()
-    line = {"metric": METRIC, "value": value, "unit": "time-steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+    if args.workload == "batch32":
+        name, n_full, label = "voronoi", None, BATCH_WORKLOAD
+    elif args.workload.startswith("hex"):
+        n = int(args.workload[3:])
+        name, n_full = args.workload, 10 * n ** 3
+        label = HEX_WORKLOAD.format(n=n, dofs=n_full, subs=(n // 4) ** 3, n0=4 * (n // 4) ** 3)
+    else:
+        name, n_full, label = "voronoi4096", 40960, WORKLOAD
+    if n_full is None:                       # batch32: all simulations' DOFs
+        from synth import voronoi_batch
+        n_full = sum(10 * w.mesh.n_cells for w in voronoi_batch())
+    o = Oracle(sub_workload(name), args.ionic_form)
+    o.steps(args.warmup)
+    t_step, t_rhs, its = o.steps(args.steps)
+    scale = n_full / o.d.n_dofs
+    value = 1.0 / (t_step * scale)
+    if args.workload == "batch32":
+        value *= 32                          # simulation-steps/s of the 32 simulations
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    w = o.w
+    sample = (f"per timed step one whole oracle time step of the same recipe on {w.name} "
+              f"({w.mesh.n_cells} cells, {o.d.n_dofs} DOFs; {t_step:.3f} s, {its:.1f} PCG "
+              f"iterations), scaled to the workload by the DOF ratio {scale:.1f}")
+    unit = "simulation-steps/s" if args.workload == "batch32" else "time-steps/s"
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "form": "FP64 oracle, plain ASM-PCG"},
-            "cpu_baseline": {"value": value, "unit": "time-steps/s", "cores": cores,
-                             "kind": "oracle",
-                             "sample": f"per step: ionic update + RHS and {sample_its} ASM-PCG "
-                                       f"iterations, scaled to the {its} iterations of a full "
-                                       "step solved once beforehand"},
-            "e2e": {"value": value, "unit": "time-steps/s", "h2d_bytes_per_step": 0,
+            "config": {"workload": label, "form": "FP64 oracle, plain ASM-PCG, x0 = U^k",
+                       "ms_per_step_is": "the measured time of one sampled (sub-problem) step"},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -301,14 +367,20 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=197)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the workload's steps minus the warm-up)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["voronoi4096", "batch32", "hex48", "hex32", "hex24"], default="voronoi4096")
+    ap.add_argument("--workload", choices=["hex48", "voronoi4096", "batch32", "hex32", "hex24", "hex16"],
+                    default="hex48")
+    ap.add_argument("--ionic-form", choices=["nodal", "modal"], default="nodal")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.steps is None:
+        args.steps = (200 if args.workload == "voronoi4096" else 100 if args.workload == "batch32"
+                      else 50) - args.warmup
     if args.impl == "reference":
         return run_reference(args)
 
@@ -325,92 +397,8 @@ def main():
         return bench_batch(args, pd, torch, stream, rank, world, local)
     if args.workload.startswith("hex"):
         return bench_hex(args, pd, torch, stream, rank, world, local)
-    w = build_case()
-    ctx = pd.polydg_setup(w.mesh.vertices, w.mesh.cell_ptr, w.mesh.cell_vtx, w.sigma, w.p,
-                          w.subdomain, w.chi_cm, w.dt, w.eta0)
-    peaks, peak_kind = measured_peaks()
-
-    # reported form: mixed precision (fp32 local inverses, flexible PCG) + learned guess
-    guess = load_guess(pd)
-    clocks = ClockSampler(local)
-    pc, sim, st, ms = time_form(pd, torch, w, ctx, "fp32", True, args.steps, args.warmup,
-                                stream, clocks, guess=guess, policy=GUESS_POLICY)
-    # the same without any initial guess (x0 = U^k)
-    _, _, st_ng, ms_ng = time_form(pd, torch, w, ctx, "fp32", True, args.steps, args.warmup,
-                                   stream, pc=pc)
-    # ablations: the increments alone (no network), and the network's proposal alone
-    # (kept only when its residual is below U^k's)
-    _, _, st_h, ms_h = time_form(pd, torch, w, ctx, "fp32", True, args.steps, args.warmup,
-                                 stream, pc=pc, policy=GUESS_POLICY)
-    if guess is not None:
-        _, _, st_p, ms_p = time_form(pd, torch, w, ctx, "fp32", True, args.steps, args.warmup,
-                                     stream, pc=pc, guess=guess, policy=0)
-    else:
-        st_p, ms_p = st_ng, ms_ng
-    # fp64 plain form on the same workload, for the comparison the metric names
-    pc64, sim64, st64, ms64 = time_form(pd, torch, w, ctx, "fp64", False, args.steps,
-                                        args.warmup, stream)
-    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, args.steps, stream, guess, warm=args.warmup)
-    (ms, ms64, ms_ng), (e2e_rank,) = reduce_over_ranks(torch, [ms, ms64, ms_ng], [e2e_val], world, "cuda")
-    value = world * args.steps / (ms * 1e-3)
-    value64 = world * args.steps / (ms64 * 1e-3)
-    value_ng = world * args.steps / (ms_ng * 1e-3)
-    e2e_val = world * e2e_rank
-
-    info = pc.info()
-    launches = st["steps_done"]
-    alg = algorithmic_bytes(ctx.info, info, st["total_iterations"], launches)
-    achieved = alg / st["pcg_seconds"] / 1e9
-    traffic = profile_traffic(st["total_iterations"] / max(1, launches))
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "pcg_persistent_kernel<fp32 store, n_p=10>",
-                "peak_kind": peak_kind}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        its64 = st64["total_iterations"] / max(1, st64["steps_done"])
-        t_step, t_rhs, t_it = cpu_baseline(w, its64)
-        cpu = {"value": 1.0 / t_step, "unit": "time-steps/s", "cores": os.cpu_count(),
-               "kind": "oracle",
-               "sample": f"one ionic update + RHS ({t_rhs:.2f} s) and 40 ASM-PCG iterations "
-                         f"({t_it * 1e3:.1f} ms each) of the float64 oracle, scaled to "
-                         f"{its64:.1f} iterations/step (the fp64 plain form's mean)"}
-
-    line = {
-        "metric": METRIC, "value": value, "unit": "time-steps/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD,
-                   "form": ("mixed + learned: fp32 local inverses, flexible PCG; initial guess = "
-                            "Galerkin projection onto the network's proposal and the last 16 "
-                            "solution increments (U^k when that does not lower the error)")
-                   if guess is not None else
-                   "mixed: fp32 local inverses, flexible PCG, initial guess from the last 16 "
-                   "solution increments (guess weights file missing)",
-                   "rtol": 1e-8, "iterations_per_step": st["total_iterations"] / args.steps,
-                   "guess_taken_steps": st.get("guesses_taken", 0),
-                   "mixed_without_guess_steps_per_s": value_ng,
-                   "mixed_without_guess_iterations_per_step": st_ng["total_iterations"] / args.steps,
-                   "ablation_increments_only_steps_per_s": world * args.steps / (ms_h * 1e-3),
-                   "ablation_increments_only_iterations_per_step": st_h["total_iterations"] / args.steps,
-                   "ablation_proposal_only_steps_per_s": world * args.steps / (ms_p * 1e-3),
-                   "ablation_proposal_only_iterations_per_step": st_p["total_iterations"] / args.steps,
-                   "ablation_proposal_only_taken_steps": st_p.get("guesses_taken", 0),
-                   "fp64_plain_steps_per_s": value64,
-                   "fp64_plain_iterations_per_step": st64["total_iterations"] / args.steps,
-                   "mixed_over_fp64": value / value64,
-                   "l2_keep_fraction": info["l2_keep_permille"] / 1000.0,
-                   "l2": "working set > L2 (no flush needed)",
-                   "parallelism": f"replicas x{world}"},
-        "clocks": clocks.summary(),
-        "e2e": {"value": e2e_val, "unit": "time-steps/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": (10 if guess is not None else 9) * args.steps,
-        "roofline": roofline,
-        "cpu_baseline": cpu,
-    }
+    line = bench_voronoi(args, pd, torch, stream, rank, world, local,
+                         with_cpu=rank == 0 and world == 1 and not args.no_cpu_baseline)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -418,47 +406,72 @@ def main():
     return 0
 
 
-def bench_hex(args, pd, torch, stream, rank, world, local):
-    """The 3D workload: its 50 coupled steps (warm-up included) in the mixed + learned,
-    mixed and fp64 plain forms."""
-    from synth import hex_cube_p2
-    n = int(args.workload[3:])
-    w = hex_cube_p2(n=n)
-    steps = min(args.steps, w.n_steps - args.warmup)
-    ctx = pd.setup_mesh(w.mesh, w.sigma, w.p, w.subdomain, w.chi_cm, w.dt, w.eta0)
+def bench_voronoi(args, pd, torch, stream, rank, world, local, with_cpu, steps=None, clocks=None):
+    """The 2D workload (4096-cell Voronoi, P3): its forms, roofline and CPU baseline."""
+    steps = steps or args.steps
+    w = build_case()
+    ctx = pd.polydg_setup(w.mesh.vertices, w.mesh.cell_ptr, w.mesh.cell_vtx, w.sigma, w.p,
+                          w.subdomain, w.chi_cm, w.dt, w.eta0)
     peaks, peak_kind = measured_peaks()
+    form = args.ionic_form
     guess = load_guess(pd)
-    clocks = ClockSampler(local)
-    pc, _, st, ms = time_form(pd, torch, w, ctx, "fp32", True, steps, args.warmup, stream,
-                              clocks, guess=guess, policy=GUESS_POLICY)
+    clocks = clocks or ClockSampler(local)
+    pc, sim, st, ms = time_form(pd, torch, w, ctx, "fp32", True, steps, args.warmup,
+                                stream, clocks, guess=guess, policy=GUESS_POLICY, ionic_form=form)
     _, _, st_ng, ms_ng = time_form(pd, torch, w, ctx, "fp32", True, steps, args.warmup,
-                                   stream, pc=pc)
-    _, _, st64, ms64 = time_form(pd, torch, w, ctx, "fp64", False, steps, args.warmup, stream)
-    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, steps, stream, guess, warm=args.warmup)
+                                   stream, pc=pc, ionic_form=form)
+    _, _, st_h, ms_h = time_form(pd, torch, w, ctx, "fp32", True, steps, args.warmup,
+                                 stream, pc=pc, policy=GUESS_POLICY, ionic_form=form)
+    if guess is not None:
+        _, _, st_p, ms_p = time_form(pd, torch, w, ctx, "fp32", True, steps, args.warmup,
+                                     stream, pc=pc, guess=guess, policy=0, ionic_form=form)
+    else:
+        st_p, ms_p = st_ng, ms_ng
+    pc64, sim64, st64, ms64 = time_form(pd, torch, w, ctx, "fp64", False, steps,
+                                        args.warmup, stream, ionic_form=form)
+    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, steps, stream, guess, warm=args.warmup,
+                                 ionic_form=form)
     (ms, ms64, ms_ng), (e2e_rank,) = reduce_over_ranks(torch, [ms, ms64, ms_ng], [e2e_val], world, "cuda")
     value = world * steps / (ms * 1e-3)
     value64 = world * steps / (ms64 * 1e-3)
+    value_ng = world * steps / (ms_ng * 1e-3)
     info = pc.info()
-    alg = algorithmic_bytes(ctx.info, info, st["total_iterations"], st["steps_done"])
+    launches = st["steps_done"]
+    alg = algorithmic_bytes(ctx.info, info, st["total_iterations"], launches)
     achieved = alg / st["pcg_seconds"] / 1e9
-    line = {
-        "metric": METRIC + " (3D workload)", "value": value, "unit": "time-steps/s",
-        "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
+    traffic = profile_traffic("pcg_persistent_voronoi4096_fp32.txt",
+                              st["total_iterations"] / max(1, launches), 1.0)
+    cpu = None
+    if with_cpu:
+        its64 = st64["total_iterations"] / max(1, st64["steps_done"])
+        cpu = cpu_baseline("voronoi4096", w, ctx.n_dofs, its64, steps=2, warm=1, ionic_form=form)
+    return {
+        "metric": METRIC, "value": value, "unit": "time-steps/s", "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
         "data": "synthetic",
-        "config": {"workload": HEX_WORKLOAD.format(n=n, dofs=10 * n ** 3, subs=(n // 4) ** 3,
-                                                   n0=4 * (n // 4) ** 3),
-                   "form": "mixed + learned: fp32 local inverses, flexible PCG; initial guess = "
-                           "Galerkin projection onto the network's proposal (trained on 2D "
-                           "Voronoi P3 trajectories) and the last 16 solution increments",
+        "config": {"workload": WORKLOAD,
+                   "form": ("mixed + learned: fp32 local inverses, flexible PCG; initial guess = "
+                            "Galerkin projection onto the network's proposal and the last 16 "
+                            "solution increments") if guess is not None else
+                   "mixed: fp32 local inverses, flexible PCG, initial guess from the last 16 "
+                   "solution increments (guess weights file missing)",
+                   "ionic_form": form,
                    "rtol": 1e-8, "iterations_per_step": st["total_iterations"] / steps,
                    "guess_taken_steps": st.get("guesses_taken", 0),
-                   "mixed_without_guess_steps_per_s": world * steps / (ms_ng * 1e-3),
+                   "pcg_ms_per_step": 1e3 * st["pcg_seconds"] / steps,
+                   "non_pcg_ms_per_step": (ms - 1e3 * st["pcg_seconds"]) / steps,
+                   "mixed_without_guess_steps_per_s": value_ng,
                    "mixed_without_guess_iterations_per_step": st_ng["total_iterations"] / steps,
+                   "ablation_increments_only_steps_per_s": world * steps / (ms_h * 1e-3),
+                   "ablation_increments_only_iterations_per_step": st_h["total_iterations"] / steps,
+                   "ablation_proposal_only_steps_per_s": world * steps / (ms_p * 1e-3),
+                   "ablation_proposal_only_iterations_per_step": st_p["total_iterations"] / steps,
+                   "ablation_proposal_only_taken_steps": st_p.get("guesses_taken", 0),
                    "fp64_plain_steps_per_s": value64,
                    "fp64_plain_iterations_per_step": st64["total_iterations"] / steps,
                    "mixed_over_fp64": value / value64,
-                   "pcg_share_of_step": st["pcg_seconds"] * 1e3 / ms,
+                   "l2_keep_fraction": info["l2_keep_permille"] / 1000.0,
                    "l2": "working set > L2 (no flush needed)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks.summary(),
@@ -466,12 +479,104 @@ def bench_hex(args, pd, torch, stream, rank, world, local):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": (10 if guess is not None else 9) * steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "kernel": "pcg_persistent_kernel<fp32 store, n_p=10>",
+                     "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+    }
+
+
+def bench_hex(args, pd, torch, stream, rank, world, local):
+    """The 3D workload (default 48^3 jittered hexahedra, P2): its 50 coupled steps (warm-up
+    included) in the mixed + learned, increments-only, x0 = U^k and fp64 plain forms; then
+    the 2D workload's forms for config.voronoi4096."""
+    from synth import hex_cube_p2
+    n = int(args.workload[3:])
+    w = hex_cube_p2(n=n)
+    steps = min(args.steps, w.n_steps - args.warmup)
+    form = args.ionic_form
+    t0 = time.perf_counter()
+    ctx = pd.setup_mesh(w.mesh, w.sigma, w.p, w.subdomain, w.chi_cm, w.dt, w.eta0)
+    t_setup = time.perf_counter() - t0
+    peaks, peak_kind = measured_peaks()
+    guess = load_guess(pd)
+    clocks = ClockSampler(local)
+    t0 = time.perf_counter()
+    pc, _, st, ms = time_form(pd, torch, w, ctx, "fp32", True, steps, args.warmup, stream,
+                              clocks, guess=guess, policy=GUESS_POLICY, ionic_form=form)
+    t_form = time.perf_counter() - t0
+    _, _, st_h, ms_h = time_form(pd, torch, w, ctx, "fp32", True, steps, args.warmup,
+                                 stream, pc=pc, policy=GUESS_POLICY, ionic_form=form)
+    _, _, st_ng, ms_ng = time_form(pd, torch, w, ctx, "fp32", True, steps, args.warmup,
+                                   stream, pc=pc, ionic_form=form)
+    e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, steps, stream, guess, warm=args.warmup,
+                                 ionic_form=form)
+    info = pc.info()
+    pc.close()
+    torch.cuda.empty_cache()
+    pc64, _, st64, ms64 = time_form(pd, torch, w, ctx, "fp64", False, steps, args.warmup, stream,
+                                    ionic_form=form)
+    pc64.close()
+    (ms, ms64, ms_ng, ms_h), (e2e_rank,) = reduce_over_ranks(torch, [ms, ms64, ms_ng, ms_h], [e2e_val],
+                                                             world, "cuda")
+    value = world * steps / (ms * 1e-3)
+    value64 = world * steps / (ms64 * 1e-3)
+    its = st["total_iterations"] / max(1, st["steps_done"])
+    alg = algorithmic_bytes(ctx.info, info, st["total_iterations"], st["steps_done"])
+    achieved = alg / st["pcg_seconds"] / 1e9
+    traffic = profile_traffic(f"pcg_persistent_hex{n}_fp32.txt", its, 1.0)
+    cpu = None
+    its64 = st64["total_iterations"] / max(1, st64["steps_done"])
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, w, ctx.n_dofs, its64, ionic_form=form)
+    ctx.close()
+    torch.cuda.empty_cache()
+    # the 2D workload in the same run
+    vor = bench_voronoi(args, pd, torch, stream, rank, world, local, with_cpu=False, steps=20)
+    pcg_ms = 1e3 * st["pcg_seconds"] / steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "time-steps/s",
+        "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": HEX_WORKLOAD.format(n=n, dofs=10 * n ** 3, subs=(n // 4) ** 3,
+                                                   n0=4 * (n // 4) ** 3),
+                   "form": "mixed + learned: fp32 local inverses, flexible PCG (fp64 residual, dots, "
+                           "coarse solve, matvec); initial guess = Galerkin projection onto the "
+                           "network's proposal (trained on 2D Voronoi P3 trajectories) and the last "
+                           "16 solution increments",
+                   "ionic_form": form,
+                   "rtol": 1e-8, "iterations_per_step": its,
+                   "guess_taken_steps": st.get("guesses_taken", 0),
+                   "pcg_ms_per_step": pcg_ms,
+                   "non_pcg_ms_per_step": ms / steps - pcg_ms,
+                   "ablation_increments_only_steps_per_s": world * steps / (ms_h * 1e-3),
+                   "ablation_increments_only_iterations_per_step": st_h["total_iterations"] / steps,
+                   "mixed_without_guess_steps_per_s": world * steps / (ms_ng * 1e-3),
+                   "mixed_without_guess_iterations_per_step": st_ng["total_iterations"] / steps,
+                   "fp64_plain_steps_per_s": value64,
+                   "fp64_plain_iterations_per_step": its64,
+                   "mixed_over_fp64": value / value64,
+                   "setup_s": {"polydg_setup3d": t_setup,
+                               "asm_setup_autotune_and_first_form": t_form},
+                   "l2": "working set > L2 (no flush needed)",
+                   "parallelism": f"replicas x{world}",
+                   "voronoi4096": {k: vor[k] for k in ("value", "ms_per_step", "e2e", "roofline")}
+                   | {k: vor["config"][k] for k in ("workload", "iterations_per_step",
+                                                    "fp64_plain_steps_per_s",
+                                                    "fp64_plain_iterations_per_step",
+                                                    "ablation_increments_only_steps_per_s",
+                                                    "mixed_without_guess_steps_per_s",
+                                                    "guess_taken_steps")}},
+        "clocks": clocks.summary(),
+        "e2e": {"value": world * e2e_rank, "unit": "time-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": (10 if guess is not None else 9) * steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "kernel": "pcg_persistent_kernel<fp32 store, n_p=10> (distributed coarse rows)",
                      "peak_kind": peak_kind},
-        "cpu_baseline": None,
-        "cpu_baseline_note": "the float64 oracle needs minutes per step at 1.1 M DOFs; its "
-                             "parity is checked on the 4^3 and 10^3 cases and on sampled rows",
+        "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -622,15 +727,12 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
     value64 = world * S * steps / (ms64 * 1e-3)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # oracle on the smallest mesh's first simulation, scaled by DOFs to all 32
-        k = int(np.argmin([w.mesh.n_cells for w in ws]))
-        t_step, t_rhs, t_it = cpu_baseline(ws[k], its64[k], sample_its=10)
-        scale = n_all / (ws[k].mesh.n_cells * 10)
-        cpu = {"value": 1.0 / (t_step * scale) * S, "unit": "simulation-steps/s",
-               "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"one step of the {ws[k].mesh.n_cells}-cell simulation (ionic update + "
-                         f"RHS and 10 ASM-PCG iterations of the float64 oracle, scaled to "
-                         f"{its64[k]:.0f} iterations), scaled by DOFs to all 32 simulations"}
+        # whole oracle steps of the 1024-cell recipe, scaled by DOFs to all 32 simulations
+        cpu = cpu_baseline("voronoi", None, n_all, float(np.mean(its64)), steps=2, warm=1)
+        for key in ("value",):
+            cpu[key] *= S
+        cpu["one_core"]["value"] *= S
+        cpu["unit"] = cpu["one_core"]["unit"] = "simulation-steps/s"
     line = {
         "metric": METRIC + " (batched form)", "value": value, "unit": "simulation-steps/s",
         "n_gpus": world, "steps": steps, "warmup": args.warmup,
@@ -669,11 +771,12 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
     return 0
 
 
-def profile_traffic(iterations_per_launch):
-    """DRAM bytes per launch of the persistent kernel from the committed ncu summary,
-    scaled to this run's iterations per launch; None if the kernel source changed
-    since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "pcg_persistent_voronoi4096_fp32.txt")
+def profile_traffic(fname, iterations_per_launch, scale=1.0):
+    """DRAM bytes per launch of the persistent kernel from a committed ncu summary
+    (profiles/<fname>: dram_bytes_per_iteration), times this run's iterations per launch;
+    None if the summary is missing or the kernel source changed since the counters were
+    taken."""
+    path = os.path.join(ROOT, "profiles", fname)
     try:
         kv = {}
         with open(path) as f:
@@ -683,8 +786,7 @@ def profile_traffic(iterations_per_launch):
                     kv[k.strip()] = v.strip()
         if kv.get("kernel_source_sha") != kernel_sha():
             return None
-        per_it = float(kv["dram_bytes_per_iteration"])
-        return per_it * iterations_per_launch
+        return float(kv["dram_bytes_per_iteration"]) * iterations_per_launch * scale
     except (OSError, KeyError, ValueError):
         return None
 

@@ -12,8 +12,10 @@
 // with K_i = 140 + (18 - Na_i), Na_o = 144 - beta (Na_i - 18) and Nernst
 // potentials E = 26.64 ln(c_out / c_in).  The model's m(u, y) is -y'.
 // The device forms below evaluate the same expressions with the exponentials of V
-// and of K_o regrouped (exp(a + b) = exp(a) exp(b)) and divisions by constants taken
-// as products with reciprocals; results differ from the plain forms by rounding only.
+// and of K_o regrouped (exp(a + b) = exp(a) exp(b), one exponential per potential),
+// the reciprocals of a node batched into one division, and the Nernst potentials after
+// an Euler step updated from the old ones; results differ from the plain forms by
+// rounding only.
 #pragma once
 
 #include <cmath>
@@ -50,24 +52,81 @@ BC_HD Rates gate_rates(double V) {
     return r;
 }
 
-// Constants of the per-node update that do not depend on the state (host-computed):
-// the membrane-potential exponentials of the rates are all exp(-(V + c)/s) with
-// s in {10, 20, 80, 2.5} -- integer divisors of 80 -- except beta_m (s = 18), so with
-// E = exp(-V/80) they are exp(-c/s) E^(80/s); likewise the pump's exp(5.5 - K_o) and
-// the glial exp((18 - K_o)/2.5) are e^5.5 X^5 and e^7.2 X^2 with X = exp(-K_o/5).
+// Constants of the per-node update that do not depend on the state (host-computed).
+// Every membrane-potential exponential of the rates is exp(-(V + c)/s) with s in
+// {10, 18, 20, 80, 2.5}, all of which divide 720 into integers (72, 40, 36, 9, 288), so
+// with B = exp(-V/720) they are exp(-c/s) B^(720/s): one exponential per potential, the
+// powers by repeated squaring (relative error <= ~300 ulp, far below the model's use).
+// Likewise the pump's exp(5.5 - K_o) and the glial exp((18 - K_o)/2.5) are e^5.5 X^5 and
+// e^7.2 X^2 with X = exp(-K_o/5).
 struct NodeConsts {
-    double an, bn, ah, bh, am, ca;   // exp(-3.4), 0.125 exp(-0.55), 0.07 exp(-2.2), exp(-1.4), exp(-3), exp(-10)
-    double pump, glia;               // exp(5.5), exp(7.2)
-    double ECl;                      // RTF ln(Cl_i / Cl_o)
+    double an, bn, ah, bh, am, bm, ca;   // exp(-3.4), 0.125 exp(-0.55), 0.07 exp(-2.2), exp(-1.4),
+                                         // exp(-3), 4 exp(-55/18), exp(-10)
+    double pump, glia;                   // exp(5.5), exp(7.2)
+    double ECl;                          // RTF ln(Cl_i / Cl_o)
 };
 
 inline NodeConsts node_consts() {
     NodeConsts k;
     k.an = std::exp(-3.4); k.bn = 0.125 * std::exp(-0.55); k.ah = 0.07 * std::exp(-2.2);
-    k.bh = std::exp(-1.4); k.am = std::exp(-3.0); k.ca = std::exp(-10.0);
+    k.bh = std::exp(-1.4); k.am = std::exp(-3.0); k.bm = 4.0 * std::exp(-55.0 / 18.0);
+    k.ca = std::exp(-10.0);
     k.pump = std::exp(5.5); k.glia = std::exp(7.2);
     k.ECl = RTF * std::log(Cli / Clo);
     return k;
+}
+
+// exp(-V/s) for s = 10, 18, 20, 80, 2.5 from B = exp(-V/720).
+struct VPowers { double e10, e18, e20, e80, e25; };
+
+BC_HD VPowers vpowers(double V) {
+    const double B = exp(-V * (1.0 / 720.0));
+    const double B2 = B * B, B4 = B2 * B2, B8 = B4 * B4, B16 = B8 * B8, B32 = B16 * B16;
+    const double B64 = B32 * B32, B256 = (B64 * B64) * (B64 * B64);
+    VPowers p;
+    p.e80 = B8 * B;
+    p.e20 = B32 * B4;
+    p.e18 = B32 * B8;
+    p.e10 = B64 * B8;
+    p.e25 = B256 * B32;
+    return p;
+}
+
+// exp(-V/10) and exp(-V/18) only (the sodium gate of the current).
+BC_HD void vpowers_m(double V, double& e10, double& e18) {
+    const double B = exp(-V * (1.0 / 720.0));
+    const double B2 = B * B, B4 = B2 * B2, B8 = B4 * B4, B16 = B8 * B8, B32 = B16 * B16;
+    e18 = B32 * B8;
+    e10 = (B32 * B32) * B8;
+}
+
+// Reciprocals of M nonzero values with one division: prefix products, the reciprocal
+// of the last one, then backwards (Montgomery's batch inversion); each result is within
+// a few ulps of 1/x_i.  The fp64 pipe, not memory, bounds the node update, and a
+// division costs several times a product there.
+template <int M>
+BC_HD void batch_reciprocal(const double (&x)[M], double (&inv)[M]) {
+    double pre[M];
+    pre[0] = x[0];
+#pragma unroll
+    for (int i = 1; i < M; ++i) pre[i] = pre[i - 1] * x[i];
+    double r = 1.0 / pre[M - 1];
+#pragma unroll
+    for (int i = M - 1; i > 0; --i) {
+        inv[i] = r * pre[i - 1];
+        r *= x[i];
+    }
+    inv[0] = r;
+}
+
+// ln(1 + a): the Taylor series for |a| < 2^-10 (six terms: relative error < a^6 / 7 <
+// 2e-19), else the library function.
+BC_HD double log1p_small(double a) {
+    if (fabs(a) < 0x1p-10) {
+        const double a2 = a * a;
+        return a - a2 * (0.5 - a * (1.0 / 3.0 - a * (0.25 - a * (0.2 - a * (1.0 / 6.0)))));
+    }
+    return log1p(a);
 }
 
 // x / (1 - ex) for ex = exp(-x/s) given; the removable point x = 0 takes its limit.
@@ -76,54 +135,105 @@ BC_HD double lin_exp_given(double x, double s, double ex) {
     return x / (1.0 - ex);
 }
 
-// Divisions by constants are multiplications by their reciprocals, and the pump's two
-// denominators share one division: the fp64 pipe, not memory, bounds the node update.
-constexpr double kInv80 = 1.0 / 80.0, kInv18 = 1.0 / 18.0, kInv3 = 1.0 / 3.0, kInv5 = 1.0 / 5.0;
-constexpr double kInvTau = 1.0 / tau, kInv10 = 1.0 / 10.0;
+constexpr double kInv80 = 1.0 / 80.0, kInv3 = 1.0 / 3.0, kInv5 = 1.0 / 5.0;
+constexpr double kInvTau = 1.0 / tau;
+
+// Nernst potentials and the reciprocals of the concentrations they came from (for the
+// update of the potentials after an Euler step, see current_after_step).
+struct Nernst { double ENa, EK, iNao, iNai, iKo, iKi; };
+
+// y'(V, y) of the Sec. 2 model (= -m(u, y)) at one point: d[0..4] for n, h, K_o, Na_i,
+// Ca_i; also the Nernst potentials of the state in *ne (may be null).
+BC_HD void rates(const NodeConsts& k, double V, double n, double h, double Ko, double Nai, double Cai,
+                 double* d, Nernst* ne = nullptr) {
+    const VPowers p = vpowers(V);
+    const double xn = V + 34.0, xm = V + 30.0;
+    const bool sn = fabs(xn) < 1e-5, sm = fabs(xm) < 1e-5;       // |x| < 1e-6 s, s = 10
+    const double exn = k.an * p.e10, exm = k.am * p.e10;
+    const double bm = k.bm * p.e18;
+    // m_inf = am / (am + bm), am = 0.1 xm / (1 - exm): 0.1 xm / (0.1 xm + bm (1 - exm))
+    const double am_num = sm ? 0.1 * (10.0 + 0.5 * xm) : 0.1 * xm;
+    const double am_den = sm ? 1.0 : 1.0 - exm;
+    const double Ki = 140.0 + (18.0 - Nai);
+    const double Nao = 144.0 - beta * (Nai - 18.0);
+    const double X = exp(-Ko * kInv5), X2 = X * X, X5 = X2 * X2 * X;
+    const double ep = exp((25.0 - Nai) * kInv3);
+    double den[11] = {sn ? 1.0 : 1.0 - exn,                  // alpha_n
+                      1.0 + k.bh * p.e10,                    // beta_h
+                      am_num + bm * am_den,                  // m_inf
+                      1.0 + Cai,                             // g_AHP term
+                      (1.0 + ep) * (1.0 + k.pump * X5),      // pump
+                      1.0 + k.glia * X2,                     // glia
+                      1.0 + k.ca * p.e25,                    // calcium
+                      Nai, Ki, Nao, Ko};
+    double inv[11];
+    batch_reciprocal(den, inv);
+    const double an = sn ? 0.01 * (10.0 + 0.5 * xn) : 0.01 * xn * inv[0];
+    const double bn = k.bn * p.e80;
+    const double ah = k.ah * p.e20;
+    const double bh = inv[1];
+    const double minf = am_num * inv[2];
+    const double ENa = RTF * log(Nao * inv[7]);
+    const double EK = RTF * log(Ko * inv[8]);
+    const double INa = (gNa * minf * minf * minf * h + gNaL) * (V - ENa);
+    const double IK = (gK * (n * n) * (n * n) + gAHP * Cai * inv[3] + gKL) * (V - EK);
+    const double pump = rho * inv[4];
+    const double glia = Gglia * inv[5];
+    const double diff = eps * (Ko - kbath);
+    d[0] = phi * (an * (1.0 - n) - bn * n);
+    d[1] = phi * (ah * (1.0 - h) - bh * h);
+    d[2] = (gamma * beta * IK - 2.0 * beta * pump - glia - diff) * kInvTau;
+    d[3] = (-gamma * INa - 3.0 * pump) * kInvTau;
+    d[4] = -0.002 * gCa * (V - ECa) * inv[6] - Cai * kInv80;
+    if (ne) {
+        ne->ENa = ENa; ne->EK = EK;
+        ne->iNai = inv[7]; ne->iKi = inv[8]; ne->iNao = inv[9]; ne->iKo = inv[10];
+    }
+}
+
+// Sodium gate m_inf(V) = num / den (the division is left to the caller's batch).
+BC_HD void minf_parts(const NodeConsts& k, double V, double& num, double& den) {
+    double e10, e18;
+    vpowers_m(V, e10, e18);
+    const double xm = V + 30.0;
+    const bool sm = fabs(xm) < 1e-5;
+    const double exm = k.am * e10, bm = k.bm * e18;
+    num = sm ? 0.1 * (10.0 + 0.5 * xm) : 0.1 * xm;
+    den = num + bm * (sm ? 1.0 : 1.0 - exm);
+}
 
 // I_Na + I_K + I_Cl at potential V for state (n, h, K_o, Na_i, Ca_i).
 BC_HD double total_current(const NodeConsts& k, double V, double n, double h, double Ko, double Nai,
                            double Cai) {
-    const double am = 0.1 * lin_exp_given(V + 30.0, 10.0, exp(-(V + 30.0) * kInv10));
-    const double bm = 4.0 * exp(-(V + 55.0) * kInv18);
-    const double minf = am / (am + bm);
+    double num, den;
+    minf_parts(k, V, num, den);
     const double Ki = 140.0 + (18.0 - Nai);
     const double Nao = 144.0 - beta * (Nai - 18.0);
-    const double INa = (gNa * minf * minf * minf * h + gNaL) * (V - RTF * log(Nao / Nai));
-    const double IK = (gK * (n * n) * (n * n) + gAHP * Cai / (1.0 + Cai) + gKL) * (V - RTF * log(Ko / Ki));
+    double dd[4] = {den, 1.0 + Cai, Nai, Ki}, inv[4];
+    batch_reciprocal(dd, inv);
+    const double minf = num * inv[0];
+    const double INa = (gNa * minf * minf * minf * h + gNaL) * (V - RTF * log(Nao * inv[2]));
+    const double IK = (gK * (n * n) * (n * n) + gAHP * Cai * inv[1] + gKL) * (V - RTF * log(Ko * inv[3]));
     return INa + IK + gClL * (V - k.ECl);
 }
 
-// y'(V, y) of the Sec. 2 model (= -m(u, y)) at one point: d[0..4] for n, h, K_o, Na_i, Ca_i.
-BC_HD void rates(const NodeConsts& k, double V, double n, double h, double Ko, double Nai, double Cai,
-                 double* d) {
-    const double E = exp(-V * kInv80);
-    const double E2 = E * E, E4 = E2 * E2, E8 = E4 * E4, E16 = E8 * E8, E32 = E16 * E16;
-    const double an = 0.01 * lin_exp_given(V + 34.0, 10.0, k.an * E8);
-    const double bn = k.bn * E;
-    const double ah = k.ah * E4;
-    const double bh = 1.0 / (1.0 + k.bh * E8);
-    const double am = 0.1 * lin_exp_given(V + 30.0, 10.0, k.am * E8);
-    const double bm = 4.0 * exp(-(V + 55.0) * kInv18);
-    const double minf = am / (am + bm);
-    const double Ki = 140.0 + (18.0 - Nai);
-    const double Nao = 144.0 - beta * (Nai - 18.0);
-    const double INa = (gNa * minf * minf * minf * h + gNaL) * (V - RTF * log(Nao / Nai));
-    const double IK = (gK * (n * n) * (n * n) + gAHP * Cai / (1.0 + Cai) + gKL) * (V - RTF * log(Ko / Ki));
-    const double X = exp(-Ko * kInv5), X2 = X * X, X5 = X2 * X2 * X;
-    const double pump = rho / ((1.0 + exp((25.0 - Nai) * kInv3)) * (1.0 + k.pump * X5));
-    const double glia = Gglia / (1.0 + k.glia * X2);
-    const double diff = eps * (Ko - kbath);
-    const double dn = phi * (an * (1.0 - n) - bn * n);
-    const double dh = phi * (ah * (1.0 - h) - bh * h);
-    const double dKo = (gamma * beta * IK - 2.0 * beta * pump - glia - diff) * kInvTau;
-    const double dNa = (-gamma * INa - 3.0 * pump) * kInvTau;
-    const double dCa = -0.002 * gCa * (V - ECa) / (1.0 + k.ca * E32) - Cai * kInv80;
-    d[0] = dn;
-    d[1] = dh;
-    d[2] = dKo;
-    d[3] = dNa;
-    d[4] = dCa;
+// The current at (V, y + dy) for a state y whose Nernst potentials ne rates() gave:
+// with dNa = dy[3] (Na_o falls by beta dNa, K_i by dNa) and dK = dy[2],
+//   E_Na' = E_Na + RTF (ln(1 - beta dNa / Na_o) - ln(1 + dNa / Na_i)),
+//   E_K'  = E_K  + RTF (ln(1 + dK / K_o) - ln(1 - dNa / K_i)),
+// logarithms of numbers within ~1e-3 of 1 (a short series) instead of two full ones.
+BC_HD double current_after_step(const NodeConsts& k, double V, double n, double h, double Ko,
+                                double Nai, double Cai, const Nernst& ne, double dK, double dNa) {
+    double num, den;
+    minf_parts(k, V, num, den);
+    double dd[2] = {den, 1.0 + Cai}, inv[2];
+    batch_reciprocal(dd, inv);
+    const double minf = num * inv[0];
+    const double ENa = ne.ENa + RTF * (log1p_small(-beta * dNa * ne.iNao) - log1p_small(dNa * ne.iNai));
+    const double EK = ne.EK + RTF * (log1p_small(dK * ne.iKo) - log1p_small(-dNa * ne.iKi));
+    const double INa = (gNa * minf * minf * minf * h + gNaL) * (V - ENa);
+    const double IK = (gK * (n * n) * (n * n) + gAHP * Cai * inv[1] + gKL) * (V - EK);
+    return INa + IK + gClL * (V - k.ECl);
 }
 
 // One explicit Euler step y <- y + dt y'(V, y) (Sec. 2 model, per quadrature node).
@@ -136,6 +246,23 @@ BC_HD void euler(const NodeConsts& k, double V, double dt, double& n, double& h,
     Ko += dt * d[2];
     Nai += dt * d[3];
     Cai += dt * d[4];
+}
+
+// The Euler step at potential V followed by the current at potential Vx and the new
+// state (the per-node work of one time step), the new state's Nernst potentials taken
+// from the old ones.  Returns f(Vx, y^{k+1}).
+BC_HD double euler_and_current(const NodeConsts& k, double V, double Vx, double dt, double& n,
+                               double& h, double& Ko, double& Nai, double& Cai) {
+    double d[5];
+    Nernst ne;
+    rates(k, V, n, h, Ko, Nai, Cai, d, &ne);
+    const double dK = dt * d[2], dNa = dt * d[3];
+    n += dt * d[0];
+    h += dt * d[1];
+    Ko += dK;
+    Nai += dNa;
+    Cai += dt * d[4];
+    return current_after_step(k, Vx, n, h, Ko, Nai, Cai, ne, dK, dNa);
 }
 
 // Rest state at potential V0: gates at steady state, K_o = 4, Na_i = 18, Ca_i = 0.

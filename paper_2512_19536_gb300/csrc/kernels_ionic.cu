@@ -42,20 +42,22 @@ ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
     const int64_t q1 = node_ptr[e + 1];
     for (int64_t q = node_ptr[e] + lane; q < q1; q += 32) {
         const double* ph = node_phi + q * NP;
-        double phv[NP];
         double uk = 0.0, ux = 0.0;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            phv[j] = __ldg(ph + j);
-            uk = fma(phv[j], su[wl][0][j], uk);
-            ux = fma(phv[j], su[wl][1][j], ux);
+            const double pv = __ldg(ph + j);
+            uk = fma(pv, su[wl][0][j], uk);
+            ux = fma(pv, su[wl][1][j], ux);
         }
         double n = y[q], h = y[nn + q], Ko = y[2 * nn + q], Nai = y[3 * nn + q], Cai = y[4 * nn + q];
-        bc::euler(kc, uk, dt, n, h, Ko, Nai, Cai);    // explicit Euler with u^k
+        // explicit Euler with u^k, then f(u~, y^{k+1})
+        const double f = bc::euler_and_current(kc, uk, ux, dt, n, h, Ko, Nai, Cai);
         y[q] = n; y[nn + q] = h; y[2 * nn + q] = Ko; y[3 * nn + q] = Nai; y[4 * nn + q] = Cai;
-        const double wf = node_w[q] * bc::total_current(kc, ux, n, h, Ko, Nai, Cai);
+        const double wf = node_w[q] * f;
+        // the basis values again (L1 hits): keeping them in registers across the node
+        // update would spill
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc[j] = fma(wf, phv[j], acc[j]);
+        for (int j = 0; j < NP; ++j) acc[j] = fma(wf, __ldg(ph + j), acc[j]);
     }
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
