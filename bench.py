@@ -429,6 +429,8 @@ def bench_voronoi(args, pd, torch, stream, rank, world, local, with_cpu, steps=N
         st_p, ms_p = st_ng, ms_ng
     pc64, sim64, st64, ms64 = time_form(pd, torch, w, ctx, "fp64", False, steps,
                                         args.warmup, stream, ionic_form=form)
+    _, _, stpp, mspp = time_form(pd, torch, w, ctx, "fp64", 2, steps, args.warmup, stream, pc=pc64,
+                                 ionic_form=form)
     e2e_val, h2d, d2h = time_e2e(pd, torch, w, ctx, pc, steps, stream, guess, warm=args.warmup,
                                  ionic_form=form)
     (ms, ms64, ms_ng), (e2e_rank,) = reduce_over_ranks(torch, [ms, ms64, ms_ng], [e2e_val], world, "cuda")
@@ -470,6 +472,10 @@ def bench_voronoi(args, pd, torch, stream, rank, world, local, with_cpu, steps=N
                    "ablation_proposal_only_taken_steps": st_p.get("guesses_taken", 0),
                    "fp64_plain_steps_per_s": value64,
                    "fp64_plain_iterations_per_step": st64["total_iterations"] / steps,
+                   "fp64_pipelined_steps_per_s": world * steps / (mspp * 1e-3),
+                   "fp64_pipelined_iterations_per_step": stpp["total_iterations"] / steps,
+                   "fp64_pipelined_pcg_ms_per_step": 1e3 * stpp["pcg_seconds"] / steps,
+                   "fp64_plain_pcg_ms_per_step": 1e3 * st64["pcg_seconds"] / steps,
                    "mixed_over_fp64": value / value64,
                    "l2_keep_fraction": info["l2_keep_permille"] / 1000.0,
                    "l2": "working set > L2 (no flush needed)",
@@ -516,6 +522,8 @@ def bench_hex(args, pd, torch, stream, rank, world, local):
     torch.cuda.empty_cache()
     pc64, _, st64, ms64 = time_form(pd, torch, w, ctx, "fp64", False, steps, args.warmup, stream,
                                     ionic_form=form)
+    _, _, stpp, mspp = time_form(pd, torch, w, ctx, "fp64", 2, steps, args.warmup, stream, pc=pc64,
+                                 ionic_form=form)
     pc64.close()
     (ms, ms64, ms_ng, ms_h), (e2e_rank,) = reduce_over_ranks(torch, [ms, ms64, ms_ng, ms_h], [e2e_val],
                                                              world, "cuda")
@@ -556,6 +564,10 @@ def bench_hex(args, pd, torch, stream, rank, world, local):
                    "mixed_without_guess_iterations_per_step": st_ng["total_iterations"] / steps,
                    "fp64_plain_steps_per_s": value64,
                    "fp64_plain_iterations_per_step": its64,
+                   "fp64_pipelined_steps_per_s": world * steps / (mspp * 1e-3),
+                   "fp64_pipelined_iterations_per_step": stpp["total_iterations"] / steps,
+                   "fp64_pipelined_pcg_ms_per_step": 1e3 * stpp["pcg_seconds"] / steps,
+                   "fp64_plain_pcg_ms_per_step": 1e3 * st64["pcg_seconds"] / steps,
                    "mixed_over_fp64": value / value64,
                    "setup_s": {"polydg_setup3d": t_setup,
                                "asm_setup_autotune_and_first_form": t_form},
@@ -565,6 +577,9 @@ def bench_hex(args, pd, torch, stream, rank, world, local):
                    | {k: vor["config"][k] for k in ("workload", "iterations_per_step",
                                                     "fp64_plain_steps_per_s",
                                                     "fp64_plain_iterations_per_step",
+                                                    "fp64_pipelined_steps_per_s",
+                                                    "fp64_plain_pcg_ms_per_step",
+                                                    "fp64_pipelined_pcg_ms_per_step",
                                                     "ablation_increments_only_steps_per_s",
                                                     "mixed_without_guess_steps_per_s",
                                                     "guess_taken_steps")}},

@@ -137,7 +137,8 @@ typedef struct {
     double  stim_x0, stim_y0, stim_amplitude, stim_width, stim_duration;
     double  rtol;
     int32_t maxit;
-    int32_t flexible;          /* 1: flexible PCG (required with FP32/BF16 local inverses) */
+    int32_t flexible;          /* 0: standard PCG; 1: flexible PCG (required with FP32/BF16
+                                  local inverses); 2: pipelined PCG (as pcg_solve)          */
     double  stim_z0;           /* stimulus centre's z (3D meshes; ignored in 2D) */
 } sim_params;
 
@@ -253,6 +254,12 @@ int polydg_set_wait_limit(int64_t polls);
 /* Solve K_h x = b by PCG (Saad Alg. 9.1) with B_ad^{-1} (pc != NULL) or without
  * preconditioner (pc == NULL: plain CG).  x_dev holds x0 on entry and the
  * solution on exit.  flexible = 1 takes beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k).
+ * flexible = 2 runs pipelined PCG (Ghysels and Vanroose): the same Krylov iterates as the
+ * standard form in exact arithmetic, with the auxiliary recurrences u = B r, w = K u, m = B w,
+ * n = K m, so that gamma = r.u, delta = w.u and |r|^2 are one reduction per iteration (the
+ * other grid barrier of the iteration carries no sums); standard beta, for FP64 local
+ * inverses (with FP32/BF16 ones use flexible = 1).  Sims and batches take the same flag
+ * through sim_params.flexible (lockstep groups of shared local solves run flexible PCG).
  * The whole iteration runs in one cooperative (persistent) kernel launch with
  * one CTA per SM and grid barriers between its phases; the call synchronises
  * `stream` and fills *stats (may be NULL).
@@ -472,8 +479,13 @@ int shared_local_setup(polydg_ctx *ctx, int precision, shared_local **out);
 /* Bytes of the stored Q_i^T and Q_i, and the conductivity of the context it was built on. */
 int shared_local_info(const shared_local *sl, int64_t *store_bytes, double *sigma_ref);
 
-/* z_s = sum_i R_i^T K_i(sigmas[s])^{-1} R_i r_s for s < nrhs (1..4): r_dev / z_dev are host
- * arrays of caller-order device vectors on the mesh of the context. */
+/* z_s = sum_i R_i^T K_i(sigmas[s])^{-1} R_i r_s for s < nrhs: r_dev / z_dev are host
+ * arrays of caller-order device vectors on the mesh of the context.  BF16 store: 1..16
+ * right-hand sides, both passes over Q_i as tcgen05 BF16 GEMMs with FP32 accumulation (one
+ * CTA per subdomain; the inputs enter as two BF16 parts each, so the error is that of the
+ * BF16 eigenbasis); subdomains of at most 1024 DOFs.  FP32 store: 1..4, SIMT FP32.
+ * Synchronises `stream` (BF16).  Errors: EINVAL, ENOMEM, ECUDA (including a device-side wait
+ * that timed out). */
 int shared_local_apply(shared_local *sl, int nrhs, const double *const *r_dev,
                        double *const *z_dev, const double *sigmas, void *stream);
 

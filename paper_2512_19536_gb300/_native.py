@@ -189,6 +189,13 @@ def _dev(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _method(flexible):
+    """The PCG variant flag of the C ABI: False/0 standard, True/1 flexible, "pipelined"/2."""
+    if flexible == "pipelined" or (not isinstance(flexible, bool) and flexible == 2):
+        return 2
+    return int(bool(flexible))
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -321,7 +328,7 @@ def pcg_solve(ctx: PolyDG, pc, b, x, rtol=1e-8, maxit=10000, flexible=False, str
               allow=(POLYDG_ENOTCONV,)):
     st = pcg_stats()
     status = load().pcg_solve(ctx.h, pc.h if pc is not None else None, _dev(b), _dev(x),
-                              float(rtol), int(maxit), int(bool(flexible)), _stream(stream),
+                              float(rtol), int(maxit), _method(flexible), _stream(stream),
                               C.byref(st))
     _check(status, allow)
     return {"iterations": st.iterations, "status": st.status, "relres": st.relres,
@@ -335,7 +342,7 @@ def pcg_solve_trace(ctx: PolyDG, pc, b, x, rtol=1e-8, maxit=10000, flexible=Fals
     cap = int(maxit)
     al, be = np.zeros(cap), np.zeros(cap)
     status = load().pcg_solve_trace(ctx.h, pc.h if pc is not None else None, _dev(b), _dev(x),
-                                    float(rtol), int(maxit), int(bool(flexible)), _stream(stream),
+                                    float(rtol), int(maxit), _method(flexible), _stream(stream),
                                     C.byref(st), _ptr(al, C.c_double), _ptr(be, C.c_double), cap)
     _check(status, allow)
     its = st.iterations
@@ -380,7 +387,7 @@ def sim_create(ctx: PolyDG, pc, u0=-67.0, stimulus=None, rtol=1e-8, maxit=10000,
                flexible=False) -> Simulation:
     s = stimulus or {"x0": 0.5, "y0": 0.5, "amplitude": 0.0, "width": 1.0, "duration": 0.0}
     prm = sim_params(float(u0), s["x0"], s["y0"], s["amplitude"], s["width"], s["duration"],
-                     float(rtol), int(maxit), int(bool(flexible)), float(s.get("z0", 0.0)))
+                     float(rtol), int(maxit), _method(flexible), float(s.get("z0", 0.0)))
     h = C.c_void_p()
     _check(load().sim_create(ctx.h, pc.h if pc is not None else None, C.byref(prm), C.byref(h)))
     return Simulation(ctx, pc, h)

@@ -955,7 +955,7 @@ int pcg_solve_trace(polydg_ctx* c, asm_ctx* pc, const double* b_dev, double* x_d
     PcgScalars init = {};
     init.rtol2 = rtol * rtol;
     init.maxit = maxit;
-    init.flexible = flexible ? 1 : 0;
+    init.flexible = flexible == 2 ? 2 : flexible ? 1 : 0;   // 2: pipelined
     *c->h_sc = init;
     CU(cudaMemcpyAsync(c->work.sc, c->h_sc, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
     CU(cudaMemsetAsync(c->work.err, 0, sizeof(int), s));
@@ -1150,7 +1150,7 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
     PcgScalars sc = {};
     sc.rtol2 = prm->rtol * prm->rtol;
     sc.maxit = prm->maxit;
-    sc.flexible = prm->flexible ? 1 : 0;
+    sc.flexible = prm->flexible == 2 ? 2 : prm->flexible ? 1 : 0;   // 2: pipelined
     if ((st = cu(cudaMemcpy(sm->U, U0.data(), n * sizeof(double), cudaMemcpyHostToDevice))) ||
         (st = cu(cudaMemcpy(sm->Uprev, U0.data(), n * sizeof(double), cudaMemcpyHostToDevice))) ||
         (st = cu(cudaMemcpy(sm->Uprev2, U0.data(), n * sizeof(double), cudaMemcpyHostToDevice))) ||

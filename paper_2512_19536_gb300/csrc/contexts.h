@@ -212,7 +212,14 @@ struct shared_local {
     __nv_bfloat16* st16 = nullptr;
     float* lam = nullptr;
     double* linv = nullptr;
-    double* tmp[2 * kMaxRhs] = {};      // internal-order r and z of shared_local_apply
+    double* tmp[2 * kMaxTcRhs] = {};    // internal-order r and z of shared_local_apply
+    // tensor-core tiles (BF16 store only): Q_i^T then Q_i of every subdomain, 16 KB tiles
+    std::vector<TcBlock> htc;
+    TcBlock* tc = nullptr;
+    unsigned char* tiles = nullptr;
+    int64_t tile_bytes = 0;
+    int max_kpad = 0;
+    int* d_err = nullptr;
 };
 
 // A lockstep group of a batch: simulations that share one shared_local.

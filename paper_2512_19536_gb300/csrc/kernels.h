@@ -130,6 +130,28 @@ struct SharedBlock {
 
 constexpr int kMaxRhs = 4;                      // simulations sharing one eigenbasis pass
 
+// Tensor-core form of the shared local solves (shared_local_tc.cu): per subdomain the
+// 128 x 64 BF16 tiles of Q_i^T (pass 1) and then of Q_i (pass 2), each 16 KB in the
+// core-matrix layout of tcgen05.mma, starting at byte tile_off of the tile store.
+struct TcBlock {
+    int64_t tile_off;      // bytes
+    int64_t in_off;        // first DOF (internal order)
+    int64_t lam_off;
+    int32_t n, mt, kt, cell0;   // order, 128-row tiles, 64-column tiles, first cell
+};
+constexpr int kMaxTcRhs = 16;                   // right-hand sides of one tensor-core pass
+struct TcRhs {
+    const double* r[kMaxTcRhs];
+    double* z[kMaxTcRhs];
+    double c[kMaxTcRhs];                        // dt sigma_s / 2
+    int nrhs;
+    int pad;
+};
+size_t shared_tc_smem(int max_kpad, int nb);
+cudaError_t launch_shared_tc(const TcBlock* blocks, int n_blocks, const unsigned char* tiles,
+                             const float* lam, const double* linv, int np, double chi,
+                             const TcRhs& p, int max_kpad, int* err, cudaStream_t s);
+
 // One simulation of a lockstep group (kernels_group.cu).
 struct GroupSim {
     const double* val;                         // its K_h blocks

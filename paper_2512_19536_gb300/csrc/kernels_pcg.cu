@@ -56,6 +56,17 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
     const int maxit = sc->maxit;
     const bool apply = a.apply_only != 0;
     const uint32_t wl = a.wait_limit;
+    // Pipelined PCG (sc->flexible == 2; Ghysels and Vanroose's rearrangement): per iteration
+    // the P phase applies the local solves to w and sums gamma = r.u, delta = w.u and |r|^2 in
+    // the same pass (the one reduction, at the first barrier: stopping test, alpha, beta);
+    // the CM phase forms m = B w, n = K m and updates z = n + beta z, q = m + beta q,
+    // s = w + beta s, p = u + beta p, x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z
+    // on its own rows, then a plain barrier.  The first pass forms u = B r and w = K u.
+    // Roles of the buffers: r = r[0], u = r[1], w = w, p = p[0], s = p[1], q = q[0],
+    // z = q[1], B's local part = zl.
+    const bool pipe = sc->flexible == 2 && !apply;
+    bool pinit = pipe;
+    double gam_old = 0.0, alp_old = 0.0;        // thread 0: gamma and alpha of the last iteration
     unsigned gen = 0;                 // barrier target of thread 0 (gs->count is 0 at launch)
 
     const int S = a.wstages;                                       // copy slots per warp
@@ -192,7 +203,20 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         double* qnew = a.q[pp ^ 1];
         const double al = pending ? alpha : 0.0, be = beta;
         double v1[1] = {0.0};                     // |r'|^2
-        if (a.identity) {
+        double vp[3] = {0.0, 0.0, 0.0};           // pipelined: r.u, w.u, r.r on own rows
+        const double* vin = pinit ? a.r[0] : a.w; // pipelined: the input of the local solves
+        auto pdots = [&](int64_t t) {
+            const double rt = __ldcg(a.r[0] + t), ut = __ldcg(a.r[1] + t), wt = __ldcg(a.w + t);
+            vp[0] = fma(rt, ut, vp[0]);
+            vp[1] = fma(wt, ut, vp[1]);
+            vp[2] = fma(rt, rt, vp[2]);
+        };
+        if (a.identity && pipe) {
+            for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) {
+                a.zl[t] = __ldcg(vin + t);
+                if (!pinit) pdots(t);
+            }
+        } else if (a.identity) {
             for (int64_t t = e0 * NP + threadIdx.x; t < e1 * NP; t += blockDim.x) {
                 const double pk = fma(be, pold[t], a.z[t]), qk = fma(be, qold[t], a.w[t]);
                 pnew[t] = pk;
@@ -213,7 +237,10 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 const int n = B.ncols;
                 const int64_t t = B.in_off + lane;
                 double r_ = 0.0;
-                if (lane < n) {
+                if (lane < n && pipe) {
+                    r_ = __ldcg(vin + t);
+                    if (!pinit) pdots(t);
+                } else if (lane < n) {
                     const double qk = fma(be, __ldcg(qold + t), __ldcg(a.w + t));
                     r_ = fma(-al, qk, __ldcg(rin + t));
                     const double pk = fma(be, __ldcg(pold + t), __ldcg(a.z + t));
@@ -246,7 +273,11 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 __syncthreads();                  // the previous run's readers of xs / rp are done
                 for (int j = threadIdx.x; j < rn.ld; j += blockDim.x) {
                     double r_ = 0.0;
-                    if (j < rn.ncols) {
+                    if (j < rn.ncols && pipe) {
+                        const int64_t t = rn.in_off + j;
+                        r_ = __ldcg(vin + t);
+                        if (!pinit && j >= rn.row_begin && j < rn.row_end) pdots(t);
+                    } else if (j < rn.ncols) {
                         const int64_t t = rn.in_off + j;
                         const double qk = fma(be, __ldcg(qold + t), __ldcg(a.w + t));
                         r_ = fma(-al, qk, __ldcg(rin + t));
@@ -317,20 +348,53 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
             __syncthreads();
             if (threadIdx.x == 0) cyc_p += clock64() - t_mark;
         }
-        ok = barrier_sum<1>(a.gs, G, cta, gen, a.err, a.partials, v1, red, outv, [&](const double* sm) {
-            const double r2 = sm[0];
-            scode = !isfinite(r2) ? 2 : apply ? 0 : (r2 <= rtol2 * bb) ? 1 : (it + pending >= maxit) ? 3 : 0;
-        }, wl);
-        rr = v1[0];
-        it += pending;
-        pending = 0;
-        par ^= 1;
-        pp ^= 1;
-        const int code = scode;
+        int code = 0;
+        if (pipe && pinit) {
+            ok = grid_barrier(a.gs, G, gen, a.err, wl);
+        } else if (pipe) {
+            // the iteration's one reduction: stopping test on |r_k|, then beta and alpha
+            ok = barrier_sum<3>(a.gs, G, cta, gen, a.err, a.partials, vp, red, outv, [&](const double* sm) {
+                const double gam = sm[0], del = sm[1], r2 = sm[2];
+                if (!isfinite(gam) || !isfinite(del) || !isfinite(r2)) { scode = 2; return; }
+                if (r2 <= rtol2 * bb) { scode = 1; return; }
+                if (it >= maxit) { scode = 3; return; }
+                double bt = 0.0, den = del;
+                if (it > 0) {
+                    bt = gam / gam_old;
+                    den = del - bt * gam / alp_old;
+                }
+                const double al_ = gam / den;
+                if (!(den > 0.0) || !isfinite(al_) || !isfinite(bt) || gam == 0.0) { scode = 4; return; }
+                scal[0] = al_;
+                scal[1] = bt;
+                scode = 0;
+                if (a.trace && cta == 0) {        // alpha_k and beta_{k-1}, as the textbook form's
+                    if (it < a.trace_cap) a.trace[it] = al_;
+                    if (it > 0 && it - 1 < a.trace_cap) a.trace[a.trace_cap + it - 1] = bt;
+                }
+                gam_old = gam;
+                alp_old = al_;
+            }, wl);
+            rr = vp[2];
+            code = scode;
+        } else {
+            ok = barrier_sum<1>(a.gs, G, cta, gen, a.err, a.partials, v1, red, outv, [&](const double* sm) {
+                const double r2 = sm[0];
+                scode = !isfinite(r2) ? 2 : apply ? 0 : (r2 <= rtol2 * bb) ? 1 : (it + pending >= maxit) ? 3 : 0;
+            }, wl);
+            rr = v1[0];
+            it += pending;
+            pending = 0;
+            par ^= 1;
+            pp ^= 1;
+            code = scode;
+        }
         if (!ok) { status = kEDEVICE; break; }
         if (code == 2) { status = kENONFINITE; break; }
         if (code == 1) { status = kOK; break; }
         if (code == 3) { status = kENOTCONV; break; }
+        if (code == 4) { status = kEBREAKDOWN; break; }
+        const double pal = pipe ? scal[0] : 0.0, pbe = pipe ? scal[1] : 0.0;
         const double* rk = a.r[par];              // r_{k+1}
         const double* qk = a.q[pp];               // q_k
         if (timing && threadIdx.x == 0) t_mark = clock64();
@@ -438,6 +502,26 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
             local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, ce0, ce1, [&](int64_t e, int i, double kz) {
                 const int64_t t = e * NP + i;
                 const double zv = pn[(e - ce0) * NP + i];
+                if (pipe) {                       // zv = m (u on the first pass), kz = K m
+                    if (pinit) {
+                        a.r[1][t] = zv;
+                        a.w[t] = kz;
+                        return;
+                    }
+                    const double zn = fma(pbe, a.q[1][t], kz);
+                    const double qn = fma(pbe, a.q[0][t], zv);
+                    const double sn = fma(pbe, a.p[1][t], a.w[t]);
+                    const double pn_ = fma(pbe, a.p[0][t], a.r[1][t]);
+                    a.q[1][t] = zn;
+                    a.q[0][t] = qn;
+                    a.p[1][t] = sn;
+                    a.p[0][t] = pn_;
+                    a.x[t] = fma(pal, pn_, a.x[t]);
+                    a.r[0][t] = fma(-pal, sn, a.r[0][t]);
+                    a.r[1][t] = fma(-pal, qn, a.r[1][t]);
+                    a.w[t] = fma(-pal, zn, a.w[t]);
+                    return;
+                }
                 a.w[t] = kz;
                 v3[0] = fma(__ldcg(rk + t), zv, v3[0]);
                 v3[1] = fma(zv, __ldcg(qk + t), v3[1]);
@@ -449,6 +533,13 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         if (timing) {
             __syncthreads();
             if (threadIdx.x == 0) cyc_cm += clock64() - t_mark;
+        }
+        if (pipe) {                               // the own rows are updated: a plain barrier
+            ok = grid_barrier(a.gs, G, gen, a.err, wl);
+            if (!ok) { status = kEDEVICE; break; }
+            if (!pinit) ++it;
+            pinit = false;
+            continue;
         }
         ok = barrier_sum<3>(a.gs, G, cta, gen, a.err, a.partials, v3, red, outv, [&](const double* sm) {
             const double rz_new = sm[0], zq = sm[1], zw = sm[2];

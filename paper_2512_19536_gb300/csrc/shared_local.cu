@@ -20,9 +20,9 @@
 namespace polydg {
 
 struct RhsPtrs {
-    const double* r[kMaxRhs];
-    double* z[kMaxRhs];
-    double c[kMaxRhs];    // dt sigma_s / 2
+    const double* r[kMaxTcRhs];
+    double* z[kMaxTcRhs];
+    double c[kMaxTcRhs];    // dt sigma_s / 2
 };
 
 template <typename T>
@@ -267,6 +267,60 @@ int shared_local_setup(polydg_ctx* c, int precision, shared_local** out) {
     for (auto& t : pool) t.join();
     if (bad) { set_error("shared_local_setup: an eigendecomposition did not converge"); return fail(POLYDG_ENOTCONV); }
     int st;
+    if (precision == POLYDG_BF16) {
+        // tiles of tcgen05.mma: per subdomain the 128 x 64 tiles of Q^T (row j, column k) and
+        // then of Q (row k, column j), zero-padded to 128 rows and 64 columns, element (r, c)
+        // of a tile at byte (r/8) 1024 + (c/8) 128 + (r%8) 16 + (c%8) 2
+        int64_t total = 0;
+        sl->htc.resize(H.n_sub);
+        for (int i = 0; i < H.n_sub; ++i) {
+            const SharedBlock& B = sl->hblocks[i];
+            TcBlock& T = sl->htc[i];
+            T.n = B.n;
+            T.mt = (B.n + 127) / 128;
+            T.kt = (B.n + 63) / 64;
+            T.cell0 = B.cell0;
+            T.in_off = B.in_off;
+            T.lam_off = B.lam_off;
+            T.tile_off = total;
+            total += 2 * (int64_t)T.mt * T.kt * 16384;
+            sl->max_kpad = std::max(sl->max_kpad, T.kt * 64);
+        }
+    }
+    if (precision == POLYDG_BF16 && sl->max_kpad <= 1024) {   // larger subdomains: SIMT passes only
+        const int64_t total = sl->htc.back().tile_off + 2 * (int64_t)sl->htc.back().mt * sl->htc.back().kt * 16384;
+        std::vector<__nv_bfloat16> tiles(total / 2, __float2bfloat16_rn(0.f));
+        std::atomic<int> nx(0);
+        auto tile_work = [&]() {
+            for (int i = nx++; i < H.n_sub; i = nx++) {
+                const SharedBlock& B = sl->hblocks[i];
+                const TcBlock& T = sl->htc[i];
+                for (int pass = 0; pass < 2; ++pass) {
+                    const int64_t qbase = B.q_off + (pass ? (int64_t)B.n * B.ld : 0);   // Q^T, then Q
+                    for (int row = 0; row < B.n; ++row)
+                        for (int col = 0; col < B.n; ++col) {
+                            const int mt = row / 128, kt = col / 64, r = row % 128, c = col % 64;
+                            const int64_t tile = (int64_t)pass * T.mt * T.kt + (int64_t)mt * T.kt + kt;
+                            const int64_t byte = T.tile_off + tile * 16384 + (r / 8) * 1024 + (c / 8) * 128 +
+                                                 (r % 8) * 16 + (c % 8) * 2;
+                            tiles[byte / 2] = q16[qbase + (int64_t)row * B.ld + col];
+                        }
+                }
+            }
+        };
+        std::vector<std::thread> tpool;
+        for (int tt = 1; tt < nthr; ++tt) tpool.emplace_back(tile_work);
+        tile_work();
+        for (auto& th : tpool) th.join();
+        sl->tile_bytes = total;
+        if ((st = upload(&sl->tc, sl->htc)) || (st = dalloc(&sl->d_err, 1))) return fail(st);
+        if ((st = dalloc(&sl->tiles, total))) return fail(st);
+        if (cudaMemcpy(sl->tiles, tiles.data(), total, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(sl->d_err, 0, sizeof(int)) != cudaSuccess) {
+            set_error("shared_local_setup: tile upload failed");
+            return fail(POLYDG_ECUDA);
+        }
+    }
     if ((st = upload(&sl->blocks, sl->hblocks)) || (st = upload(&sl->lam, lam)) || (st = upload(&sl->linv, linv)))
         return fail(st);
     if (precision == POLYDG_FP32) { if ((st = upload(&sl->st32, q32))) return fail(st); }
@@ -284,8 +338,10 @@ int shared_local_info(const shared_local* sl, int64_t* store_bytes, double* sigm
 
 int shared_local_apply(shared_local* sl, int nrhs, const double* const* r_dev, double* const* z_dev,
                        const double* sigmas, void* stream) {
-    if (!sl || nrhs < 1 || nrhs > kMaxRhs || !r_dev || !z_dev || !sigmas) {
-        set_error("shared_local_apply: need 1 <= nrhs <= 4 vectors and conductivities");
+    const int max_rhs = (sl && sl->tiles) ? kMaxTcRhs : kMaxRhs;
+    if (!sl || nrhs < 1 || nrhs > max_rhs || !r_dev || !z_dev || !sigmas) {
+        set_error("shared_local_apply: need 1 <= nrhs <= 16 (BF16, subdomains <= 1024 DOFs) or 4 "
+                  "vectors and conductivities");
         return POLYDG_EINVAL;
     }
     polydg_ctx* c = sl->ctx;
@@ -303,9 +359,27 @@ int shared_local_apply(shared_local* sl, int nrhs, const double* const* r_dev, d
         p.z[k] = sl->tmp[2 * k + 1];
         p.c[k] = 0.5 * c->H.dt * sigmas[k];
     }
+    const double chi = c->H.chi_cm;
+    if (sl->tiles) {                         // tensor cores: both passes as tcgen05 BF16 GEMMs
+        TcRhs tp = {};
+        tp.nrhs = nrhs;
+        for (int k = 0; k < nrhs; ++k) { tp.r[k] = p.r[k]; tp.z[k] = p.z[k]; tp.c[k] = p.c[k]; }
+        int h_err = 0;
+        CU(launch_shared_tc(sl->tc, sl->n_sub, sl->tiles, sl->lam, sl->linv, np, chi, tp, sl->max_kpad,
+                            sl->d_err, s));
+        CU(cudaMemcpyAsync(&h_err, sl->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (h_err) {
+            cudaMemsetAsync(sl->d_err, 0, sizeof(int), s);
+            set_error("shared_local_apply: a device-side wait timed out");
+            return POLYDG_ECUDA;
+        }
+        for (int k = 0; k < nrhs; ++k)
+            CU(launch_permute(sl->tmp[2 * k + 1], nullptr, z_dev[k], c->d_to_caller, c->H.nc, np, 0, nullptr, s));
+        return POLYDG_OK;
+    }
     const size_t smem = 2 * (size_t)kMaxRhs * sl->max_ld * sizeof(float);
     const unsigned grid = (unsigned)sl->n_sub;
-    const double chi = c->H.chi_cm;
 #define LAUNCH(T, R, Q)                                                                              \
     {                                                                                                \
         CU(cudaFuncSetAttribute(shared_local_apply_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
@@ -336,6 +410,7 @@ int shared_local_apply(shared_local* sl, int nrhs, const double* const* r_dev, d
 void shared_local_destroy(shared_local* sl) {
     if (!sl) return;
     dfree(sl->blocks); dfree(sl->st32); dfree(sl->st16); dfree(sl->lam); dfree(sl->linv);
+    dfree(sl->tc); dfree(sl->tiles); dfree(sl->d_err);
     for (auto& t : sl->tmp) dfree(t);
     delete sl;
 }

@@ -1,0 +1,292 @@
+// Local solves shared by up to 16 simulations of one mesh, on the 5th-generation tensor
+// cores (tcgen05): the two passes over the eigenbasis of every subdomain,
+//     Y = diag(1/(chi + c_s lam)) Q_i^T X,   V = Q_i Y,   X = L_i^{-1} r_s, z_s = L_i^{-T} V,
+// are [n_i x n_i] x [n_i x 2R] BF16 products with FP32 accumulation (Sec. 4, Eq. prec:
+// K_i(sigma)^{-1} = L_i^{-T} Q_i diag(1/(chi_cm + c lam_i)) Q_i^T L_i^{-1}, c = dt sigma/2).
+//
+// The right-hand sides enter as two BF16 parts each, hi = bf16(x) and lo = bf16(x - hi),
+// so the inputs keep ~16 bits and the result's error is that of the BF16 eigenbasis
+// alone.  One CTA of 128 threads per subdomain:
+//   * thread 0 streams the 128 x 64 tiles of Q_i^T, then of Q_i (16 KB each, stored
+//     pre-tiled in the core-matrix layout the MMA reads: 8-row x 16-byte core matrices,
+//     K-adjacent ones 128 B apart, 8-row groups 1024 B apart) through a ring of shared-memory
+//     stages with cp.async.bulk (mbarrier completion), and issues tcgen05.mma (M = 128,
+//     N = 16 or 32, K = 16; four per tile) into one TMEM accumulator per 128-row tile;
+//     each stage's commit frees it for the next copy;
+//   * the four warps read the accumulators back with tcgen05.ld (warp w owns TMEM lanes
+//     32w..32w+31), form Y (pass 1) or V (pass 2) and write the next B operand.
+// Every wait is bounded; on a timeout the CTA raises *err, waits (bounded) for its copies
+// and MMAs in flight, frees its TMEM and leaves.
+#include <cstdint>
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "device.cuh"
+#include "kernels.h"
+#include "pcg_device.cuh"
+
+namespace polydg {
+
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTcStages = 6;                   // ring of 16 KB A tiles
+constexpr uint32_t kTileBytes = 128 * 64 * 2;  // one 128 x 64 BF16 tile
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;      // K-adjacent core matrices
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;      // adjacent 8-row groups
+    d |= (uint64_t)1 << 46;                             // descriptor version of tcgen05
+    return d;                                           // base offset 0, no swizzle
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: D fp32, A and B bf16, both K-major,
+// M = 128, N = NB.
+template <int NB>
+__device__ __forceinline__ uint32_t instr_desc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NB >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_addr(bar)) : "memory");
+}
+
+// NB fp32 columns of this thread's TMEM lane (32x32b shape: thread t of warp w reads lane
+// 32 (w % 4) + t), starting at column col.
+template <int NB>
+__device__ __forceinline__ void tmem_load_row(uint32_t taddr, float* out) {
+#pragma unroll
+    for (int c0 = 0; c0 < NB; c0 += 16) {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr + (uint32_t)c0) : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int k = 0; k < 16; ++k) out[c0 + k] = __uint_as_float(r[k]);
+    }
+}
+
+// Byte offset of element (row, k) of an operand stored as 8-row x 16-byte core matrices,
+// K-adjacent core matrices 128 B apart and 8-row groups `sbo` bytes apart.
+__device__ __forceinline__ uint32_t core_off(int row, int k, uint32_t sbo) {
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u +
+           (uint32_t)(k & 7) * 2u;
+}
+
+}  // namespace
+
+template <int NB>
+__global__ void __launch_bounds__(kTcThreads, 1)
+shared_tc_kernel(const TcBlock* __restrict__ blocks, const unsigned char* __restrict__ tiles,
+                 const float* __restrict__ lam, const double* __restrict__ linv, int np, double chi,
+                 TcRhs p, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int fail_sh;
+    const TcBlock B = blocks[blockIdx.x];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int R = p.nrhs, n = B.n, MT = B.mt, KT = B.kt;
+    const int kpad = KT * 64, npad = MT * 128;
+    const uint32_t bsbo = (uint32_t)(kpad / 8) * 128u;      // B operand: 8-row groups apart
+    unsigned char* ring = smem;                              // kTcStages x 16 KB
+    unsigned char* bop = smem + kTcStages * kTileBytes;      // NB x kpad bf16, core matrices
+    float* vst = reinterpret_cast<float*>(smem);             // V staging (reuses the ring)
+    int cols = 32;                                           // TMEM columns: a power of 2
+    while (cols < MT * NB) cols *= 2;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_addr(&tmem_slot)), "r"(cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    if (t == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&empty[s])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fail_sh = 0;
+    }
+    // X_s = L^{-1} r_s (fp64) as hi + lo bf16 parts: B-operand rows s and R + s
+    for (int idx = t; idx < NB * kpad; idx += kTcThreads) {
+        const int row = idx / kpad, k = idx - row * kpad;
+        float v = 0.f;
+        if (k < n && row < 2 * R) {
+            const int s = row < R ? row : row - R;
+            const int el = k / np, i = k - el * np;
+            const double* Li = linv + ((int64_t)(B.cell0 + el) * np + i) * np;
+            const double* rs = p.r[s] + B.in_off + (int64_t)el * np;
+            double acc = 0.0;
+            for (int j = 0; j <= i; ++j) acc = fma(Li[j], rs[j], acc);
+            const float x = (float)acc;
+            const float hi = __bfloat162float(__float2bfloat16_rn(x));
+            v = row < R ? hi : x - hi;
+        }
+        *reinterpret_cast<__nv_bfloat16*>(bop + core_off(row, k, bsbo)) = __float2bfloat16_rn(v);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const int T = MT * KT;                                   // tiles per pass; tile g < 2T overall
+    const unsigned char* src = tiles + B.tile_off;
+    const uint32_t idesc = instr_desc<NB>();
+
+    // thread 0: copy tile g into stage g % S (the stage's previous MMAs have completed)
+    auto copy_tile = [&](int g) {
+        const int s = g % kTcStages;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     ::"r"(smem_addr(&full[s])), "r"(kTileBytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(smem_addr(ring + (size_t)s * kTileBytes)), "l"(src + (size_t)g * kTileBytes),
+                       "r"(kTileBytes), "r"(smem_addr(&full[s])) : "memory");
+    };
+    // thread 0's bookkeeping: copies issued, tiles whose copy was seen complete, commits
+    // of the `done` barrier (one per pass)
+    int issued = 0, consumed = 0, commits = 0;
+    bool ok = true;
+    // thread 0: the MMAs of pass `pass` (tiles pass*T .. pass*T + T - 1), refilling the ring
+    // one tile behind (the stage of tile g - 1 is free once its MMAs, committed one tile
+    // earlier, have completed), then one commit of `done` for the whole pass
+    auto run_pass = [&](int pass) {
+        for (int g = pass * T; g < (pass + 1) * T; ++g) {
+            const int s = g % kTcStages;
+            if (!mbar_wait(&full[s], (g / kTcStages) & 1)) { ok = false; break; }
+            ++consumed;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int tt = g - pass * T, mt = tt / KT, kt = tt - mt * KT;
+            const uint32_t abase = smem_addr(ring + (size_t)s * kTileBytes);
+            const uint32_t bbase = smem_addr(bop) + (uint32_t)kt * 8u * 128u;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_bf16(tmem + (uint32_t)(mt * NB), smem_desc(abase + kk * 256u, 128u, 1024u),
+                         smem_desc(bbase + kk * 256u, 128u, bsbo), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+            if (g >= 1 && issued < 2 * T) {
+                const int gp = g - 1;
+                if (!mbar_wait(&empty[gp % kTcStages], (gp / kTcStages) & 1)) { ok = false; break; }
+                copy_tile(issued++);
+            }
+        }
+        mma_commit(&done);
+        ++commits;
+    };
+    if (t == 0) {
+        while (issued < kTcStages && issued < 2 * T) copy_tile(issued++);
+        run_pass(0);
+        if (!ok) fail_sh = 1;
+    }
+    if (!mbar_wait(&done, 0)) fail_sh = 1;                   // pass 1 complete
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    const bool fail1 = fail_sh != 0;
+    if (!fail1) {
+        // Y_s = (D hi + D lo) / (chi + c_s lam): hi/lo parts into the B operand of pass 2
+        for (int mt = 0; mt < MT; ++mt) {
+            float d[NB];
+            tmem_load_row<NB>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(mt * NB), d);
+            const int j = mt * 128 + 32 * warp + lane;
+            if (j < kpad) {
+                const double lj = j < n ? (double)lam[B.lam_off + j] : 0.0;
+                for (int row = 0; row < NB; ++row) {
+                    float v = 0.f;
+                    if (j < n && row < 2 * R) {
+                        const int s = row < R ? row : row - R;
+                        const float y = (float)((double)(d[s] + d[R + s]) / (chi + p.c[s] * lj));
+                        const float hi = __bfloat162float(__float2bfloat16_rn(y));
+                        v = row < R ? hi : y - hi;
+                    }
+                    *reinterpret_cast<__nv_bfloat16*>(bop + core_off(row, j, bsbo)) = __float2bfloat16_rn(v);
+                }
+            }
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (t == 0 && !fail1) {
+        run_pass(1);
+        if (!ok) fail_sh = 1;
+    }
+    if (!fail1 && !mbar_wait(&done, 1)) fail_sh = 1;          // pass 2 complete
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    const bool fail2 = fail_sh != 0;
+    if (!fail2) {
+        // V_s = D hi + D lo (rows k of Q_i Y), staged as fp32 in the ring
+        for (int mt = 0; mt < MT; ++mt) {
+            float d[NB];
+            tmem_load_row<NB>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(mt * NB), d);
+            const int k = mt * 128 + 32 * warp + lane;
+            if (k < n)
+                for (int s = 0; s < R; ++s) vst[(size_t)s * npad + k] = d[s] + d[R + s];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!fail2) {
+        // z_s = L^{-T} V_s per element: z[i] = sum_{j >= i} Linv[j][i] V[j]
+        for (int idx = t; idx < R * n; idx += kTcThreads) {
+            const int s = idx / n, k = idx - s * n;
+            const int el = k / np, i = k - el * np;
+            const double* L0 = linv + (int64_t)(B.cell0 + el) * np * np;
+            const float* V = vst + (size_t)s * npad + el * np;
+            double acc = 0.0;
+            for (int j = i; j < np; ++j) acc = fma(L0[j * np + i], (double)V[j], acc);
+            p.z[s][B.in_off + k] = acc;
+        }
+    }
+    if (fail2 && t == 0) {
+        atomicExch(err, 1);
+        // bounded drain: the copies issued and not seen complete, then the last commit of
+        // `done` (which covers every MMA issued)
+        for (int g = consumed; g < issued; ++g)
+            if (!mbar_wait(&full[g % kTcStages], (g / kTcStages) & 1)) break;
+        if (commits > 0) mbar_wait(&done, (commits - 1) & 1);
+    }
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols) : "memory");
+}
+
+size_t shared_tc_smem(int max_kpad, int nb) {
+    const size_t ring = (size_t)kTcStages * kTileBytes;
+    const size_t bop = (size_t)nb * max_kpad * 2;
+    return ring + bop;
+}
+
+cudaError_t launch_shared_tc(const TcBlock* blocks, int n_blocks, const unsigned char* tiles,
+                             const float* lam, const double* linv, int np, double chi,
+                             const TcRhs& p, int max_kpad, int* err, cudaStream_t s) {
+    const int nb = 2 * p.nrhs <= 16 ? 16 : 32;
+    const size_t smem = shared_tc_smem(max_kpad, nb);
+    const void* fn = nb == 16 ? (const void*)shared_tc_kernel<16> : (const void*)shared_tc_kernel<32>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (nb == 16)
+        shared_tc_kernel<16><<<n_blocks, kTcThreads, smem, s>>>(blocks, tiles, lam, linv, np, chi, p, err);
+    else
+        shared_tc_kernel<32><<<n_blocks, kTcThreads, smem, s>>>(blocks, tiles, lam, linv, np, chi, p, err);
+    return cudaGetLastError();
+}
+
+}  // namespace polydg

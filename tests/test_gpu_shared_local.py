@@ -99,3 +99,47 @@ def test_anisotropic_conductivity_is_rejected(case):
     with pytest.raises(pd.PolyDGError) as e:
         pd.shared_local_setup(ctx, "fp32")
     assert e.value.status == pd.POLYDG_EINVAL
+
+
+@pytest.mark.parametrize("nrhs", [5, 16])
+def test_tensor_core_passes_for_many_right_hand_sides(case, nrhs):
+    """BF16 store: both passes run as tcgen05 BF16 GEMMs (FP32 accumulate) for up to 16
+    right-hand sides at once; each one against the oracle's exact local solve with its own
+    conductivity (3e-2, the BF16 bound above), and against the FP32-eigenbasis form in
+    groups of four (the two differ by the BF16 rounding of Q alone: 3e-2).  The subdomains
+    here have ~375 DOFs: three 128-row tiles, the last one ragged, six 64-column tiles."""
+    from oracle import multirhs
+    m, part, d1, S = case
+    pd = lib()
+    ctx = gpu_ctx(m, part, 1.0)
+    sl = pd.shared_local_setup(ctx, "bf16")
+    sl32 = pd.shared_local_setup(ctx, "fp32")
+    rng = np.random.default_rng(40 + nrhs)
+    sigmas = list(rng.uniform(0.5, 2.0, nrhs))
+    rs = [rng.standard_normal(d1.n_dofs) for _ in range(nrhs)]
+    zs = [dev(np.zeros(d1.n_dofs)) for _ in range(nrhs)]
+    pd.shared_local_apply(sl, [dev(r) for r in rs], zs, sigmas)
+    z32 = [dev(np.zeros(d1.n_dofs)) for _ in range(nrhs)]
+    for k0 in range(0, nrhs, 4):
+        k1 = min(nrhs, k0 + 4)
+        pd.shared_local_apply(sl32, [dev(r) for r in rs[k0:k1]], z32[k0:k1], sigmas[k0:k1])
+    for r, z, zf, sg in zip(rs, zs, z32, sigmas):
+        ref = multirhs.apply_local(S, r, sg, 1.0, 0.05)
+        got = host(z)
+        assert np.linalg.norm(got - ref) <= 3e-2 * np.linalg.norm(ref), sg
+        assert np.linalg.norm(got - host(zf)) <= 3e-2 * np.linalg.norm(ref), sg
+    # the same right-hand side in two slots gives the same result (columns are independent)
+    z1, z2 = dev(np.zeros(d1.n_dofs)), dev(np.zeros(d1.n_dofs))
+    pd.shared_local_apply(sl, [dev(rs[0]), dev(rs[0])], [z1, z2], [sigmas[0], sigmas[0]])
+    assert np.array_equal(host(z1), host(z2))
+
+
+def test_tensor_core_rhs_limit(case):
+    m, part, d1, S = case
+    pd = lib()
+    ctx = gpu_ctx(m, part, 1.0)
+    sl = pd.shared_local_setup(ctx, "bf16")
+    r = [dev(np.zeros(d1.n_dofs)) for _ in range(17)]
+    with pytest.raises(pd.PolyDGError) as e:
+        pd.shared_local_apply(sl, r, r, [1.0] * 17)
+    assert e.value.status == pd.POLYDG_EINVAL
