@@ -551,8 +551,11 @@ def bench_hex(args, pd, torch, stream, rank, world, local):
                                                    n0=4 * (n // 4) ** 3),
                    "form": "mixed + learned: fp32 local inverses, flexible PCG (fp64 residual, dots, "
                            "coarse solve, matvec); initial guess = Galerkin projection onto the "
-                           "network's proposal (trained on 2D Voronoi P3 trajectories) and the last "
-                           "16 solution increments",
+                           "network's proposal (trained on 2D Voronoi P3 trajectories of the plain "
+                           "solver, seeds 0-7) and the last 16 solution increments; the gain over "
+                           "fp64 plain is the fp32 inverses' and the increments' (see the "
+                           "increments-only ablation: the network's direction does not help on this "
+                           "mesh)",
                    "ionic_form": form,
                    "rtol": 1e-8, "iterations_per_step": its,
                    "guess_taken_steps": st.get("guesses_taken", 0),
@@ -807,11 +810,21 @@ def profile_traffic(fname, iterations_per_launch, scale=1.0):
 
 
 def kernel_sha():
+    """Hash of what the persistent PCG kernel is compiled from: its source, its device
+    helpers and the argument structures it reads (the rest of kernels.h declares other
+    launchers and does not change the kernel)."""
     import hashlib
+    import re
     h = hashlib.sha256()
-    for name in ("kernels_pcg.cu", "kernels.h", "device.cuh", "pcg_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2512_19536_gb300", "csrc", name), "rb") as f:
+    csrc = os.path.join(ROOT, "paper_2512_19536_gb300", "csrc")
+    for name in ("kernels_pcg.cu", "device.cuh", "pcg_device.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
+    with open(os.path.join(csrc, "kernels.h")) as f:
+        text = f.read()
+    for struct in ("GridSync", "PersistArgs"):
+        m = re.search(r"struct %s \{.*?\n\};" % struct, text, flags=re.S)
+        h.update(m.group(0).encode() if m else b"")
     return h.hexdigest()[:16]
 
 

@@ -377,7 +377,7 @@ static int check_ctx(const polydg_ctx* c, const char* fn) {
 }
 
 static inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
-// coarse spaces larger than this are factorised and inverted on the host threads
+// coarse spaces larger than this are factorised and inverted by the blocked tile kernels
 constexpr int64_t kHostCoarseDofs = 2048;
 
 }  // namespace polydg
@@ -573,24 +573,16 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
         set_error(std::string("asm_setup: ") + what + ": " + cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? POLYDG_ENOMEM : POLYDG_ECUDA;
     };
-    // A large coarse matrix (3D: thousands of coarse DOFs) is inverted on the host
-    // threads: the batched kernel gives each matrix one CTA.
-    const bool coarse_on_host = pc->has_coarse && n0 > kHostCoarseDofs;
-    const int nmat_dev = coarse_on_host ? nmat - 1 : nmat;
+    // A large coarse matrix (3D: thousands of coarse DOFs) is factorised and inverted by
+    // the blocked tile kernels (chol_blocked.cu): the batched kernel gives each matrix one CTA.
+    const bool coarse_blocked = pc->has_coarse && n0 > kHostCoarseDofs;
+    const int nmat_dev = coarse_blocked ? nmat - 1 : nmat;
     int64_t max_n_dev = 0;
     for (int m = 0; m < nmat_dev; ++m) max_n_dev = std::max(max_n_dev, mats[m].n);
-    std::vector<double> K0inv;
-    if (coarse_on_host) {
-        K0inv.resize((size_t)n0 * n0);
-        if (!spd_inverse(n0, C.K0.data(), K0inv.data())) {
-            cleanup();
-            set_error("asm_setup: the coarse matrix K_0 is not positive definite");
-            return fail(POLYDG_ENOTSPD);
-        }
-    }
-    const double* coarse_src = coarse_on_host ? K0inv.data() : C.K0.data();
+    const double* coarse_src = C.K0.data();
     if ((st = cu(cudaMemset(pc->st64, 0, off * sizeof(double)), "memset")) ||
         (st = cu(cudaMemset(work, 0, woff * sizeof(double)), "memset")) ||
+        (st = cu(cudaMemset(d_status, 0, nmat * sizeof(int)), "memset")) ||
         (st = cu(launch_extract_local(c->K, d_subptr, H.n_sub, d_off, d_ld, pc->st64, np, 0), "extract")) ||
         (pc->has_coarse &&
          (st = cu(cudaMemcpy2D(pc->st64 + mats.back().off, mats.back().ld * sizeof(double), coarse_src,
@@ -602,9 +594,19 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
         cleanup();
         return fail(st);
     }
+    if (coarse_blocked) {                    // status slot nmat - 1 belongs to K_0
+        double* bw = nullptr;
+        if ((st = dalloc(&bw, chol_blocked_work_doubles((int)n0)))) { cleanup(); return fail(st); }
+        double* K0 = pc->st64 + mats.back().off;
+        st = cu(launch_chol_blocked_inverse(K0, mats.back().ld, (int)n0, K0, mats.back().ld, bw,
+                                            d_status + (nmat - 1), 0), "coarse cholesky");
+        if (!st) st = cu(cudaDeviceSynchronize(), "coarse cholesky sync");
+        dfree(bw);
+        if (st) { cleanup(); return fail(st); }
+    }
     {
         std::vector<int> hs(nmat, 0);
-        cudaMemcpy(hs.data(), d_status, nmat_dev * sizeof(int), cudaMemcpyDeviceToHost);
+        cudaMemcpy(hs.data(), d_status, nmat * sizeof(int), cudaMemcpyDeviceToHost);
         for (int m = 0; m < nmat; ++m)
             if (hs[m] != 0) {
                 cleanup();

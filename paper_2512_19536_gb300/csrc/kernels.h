@@ -238,6 +238,12 @@ cudaError_t launch_chol_inverse(double* store, const int64_t* mat_off, const int
                                 const int32_t* ld, double* work, const int64_t* work_off,
                                 const int32_t* wld, int* status, int nmat, int max_n,
                                 cudaStream_t s);
+// Blocked FP64 Cholesky inversion of one SPD matrix (chol_blocked.cu): out = A^{-1} (out
+// may be A); work holds chol_blocked_work_doubles(n) doubles; *status = 1 on a
+// non-positive pivot.
+int64_t chol_blocked_work_doubles(int n);
+cudaError_t launch_chol_blocked_inverse(const double* A, int64_t lda, int n, double* out, int64_t ldo,
+                                        double* work, int* status, cudaStream_t s);
 cudaError_t launch_cast_store(const double* src, float* d32, __nv_bfloat16* d16, int64_t n,
                               cudaStream_t s);
 

@@ -238,3 +238,58 @@ def test_hex48_fp32_and_fp64_solves_and_coupled_run(hex48):
     assert e <= 1e-6, e
     eu = np.linalg.norm(sols["fp32_u"] - sols["fp64_u"]) / np.linalg.norm(sols["fp64_u"])
     assert eu <= 1e-6, eu
+
+
+def test_one_element_subdomains_3d(hex4):
+    """T_S = T_h on a polyhedral mesh (one subdomain per cell, the small-subdomain P phase)
+    with the 2^3-cell agglomerates as the coarse space: B_ad r and PCG against the oracle."""
+    from oracle import schwarz
+    import dataclasses
+    w, d, _ = hex4
+    pd = lib()
+    wm = dataclasses.replace(w, subdomain=np.arange(w.mesh.n_cells, dtype=np.int32))
+    ctx = ctx_of(wm)
+    S = schwarz.build(d, wm.subdomain, wm.coarse, wm.q)
+    r = np.random.default_rng(35).standard_normal(d.n_dofs)
+    for prec, tol in (("fp64", 1e-9), ("fp32", 1e-4), ("bf16", 5e-2)):
+        pc = pd.asm_setup(ctx, wm.coarse, q=wm.q, precision=prec)
+        assert pc.info()["n_subdomains"] == w.mesh.n_cells
+        z = dev(np.zeros(d.n_dofs))
+        pd.asm_apply(pc, dev(r), z)
+        ref = S.apply(r)
+        assert np.linalg.norm(host(z) - ref) <= tol * np.linalg.norm(ref), prec
+    pc = pd.asm_setup(ctx, wm.coarse, q=wm.q, precision="fp64")
+    b = np.random.default_rng(36).standard_normal(d.n_dofs)
+    x = dev(np.zeros(d.n_dofs))
+    st = pd.pcg_solve(ctx, pc, dev(b), x, rtol=1e-12, maxit=5000)
+    assert st["status"] == 0
+    assert mnorm_rel(d, host(x), spla.spsolve(d.K.tocsc(), b)) <= 1e-8
+
+
+@pytest.mark.slow
+def test_hex12_coupled_run_in_the_measured_form_vs_oracle():
+    """The 48^3 workload's recipe on a 12^3 mesh the oracle assembles (27 subdomains of 4^3
+    cells = coarse agglomerates, coarse P1, isotropic sigma, the same stimulus recipe): 8
+    coupled steps in the measured form -- fp32 local inverses, flexible PCG, the subspace
+    initial guess -- at rtol 1e-12 against the oracle's exactly solved trajectory."""
+    from oracle import monodomain
+    from synth import hex_cube_p2
+    from oracle import assembly
+    w = hex_cube_p2(n=12)
+    d = cached(("hex12", "disc"), lambda: assembly.assemble(w.mesh, w.p, w.sigma, w.eta0, w.chi_cm, w.dt))
+    pd = lib()
+    steps = 8
+    ctx = ctx_of(w)
+    pc = pd.asm_setup(ctx, w.coarse, q=w.q, precision="fp32")
+    sim = pd.sim_create(ctx, pc, u0=w.u_rest, stimulus=w.stimulus, rtol=1e-12, maxit=5000, flexible=True)
+    pd.sim_set_guess(sim, None, 3)
+    st = pd.monodomain_step(sim, steps)
+    assert st["status"] == 0 and st["steps_done"] == steps
+    nodes = monodomain.quadrature_nodes(d)
+    u, y = dev(np.zeros(d.n_dofs)), dev(np.zeros(5 * len(nodes.w)))
+    pd.sim_get_state(sim, u, y)
+    md = monodomain.Monodomain(d, w.stimulus, u0=w.u_rest)
+    for _ in range(steps):
+        ref = md.step()
+    assert mnorm_rel(d, host(u), ref.U) <= 1e-8
+    assert np.allclose(host(y).reshape(5, -1), ref.y, rtol=1e-9, atol=1e-12)

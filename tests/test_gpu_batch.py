@@ -187,3 +187,24 @@ def test_batch_rejects_invalid_groups(small_batch):
     with pytest.raises(pd.PolyDGError) as e:      # mixed local precisions
         pd.batch_create([s1, s3])
     assert e.value.status == pd.POLYDG_EINVAL
+
+
+def test_batch_one_element_subdomains_match_oracle(small_batch):
+    """The massively parallel case inside the batched launch: every simulation of the
+    batch with one subdomain per cell (the small-subdomain P phase of pcg_batched_kernel)
+    and its k-means agglomerates as the coarse space, fp64 and the fp32 store (flexible),
+    each against the oracle's exactly solved trajectory."""
+    import dataclasses
+    ws, ds = small_batch
+    pd = lib()
+    wm = [dataclasses.replace(w, subdomain=np.arange(w.mesh.n_cells, dtype=np.int32)) for w in ws]
+    for precision, flexible, tol in (("fp64", False, 1e-8), ("fp32", True, 1e-8)):
+        sims = make_sims(wm, precision=precision, flexible=flexible)
+        bt = pd.batch_create(sims)
+        stats, _ = pd.batch_step(bt, STEPS)
+        for sim, st, w, d in zip(sims, stats, ws, ds):
+            assert st["status"] == 0 and st["steps_done"] == STEPS, (precision, st)
+            u, _ = state(sim, d)
+            ref = oracle_run(w, d, STEPS)
+            assert mnorm_rel(d, u, ref.U) <= tol, precision
+        bt.close()
