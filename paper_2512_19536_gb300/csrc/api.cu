@@ -183,6 +183,10 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 
     // coarse rows solved redundantly per CTA while that costs little (<= 8k fp64 FMA per CTA);
     // otherwise distributed over the CTAs with one more grid barrier per iteration
     P.redundant = ((int64_t)max_aggs * nq * n0 <= 8192) ? 1 : 0;
+    // distributed coarse rows: per needed element its agglomerate itself (read beside the
+    // element id instead of through it)
+    if (!P.redundant)
+        for (size_t k = 0; k < need.size(); ++k) need_aggl[k] = agg_internal[need[k]];
     P.max_need = max_need;
     P.max_aggs = max_aggs;
     // shared memory: 2 tile buffers, staged r' (store type), r' and q (fp64), z (2 x rows),

@@ -80,7 +80,8 @@ struct PersistArgs {
     const int64_t* chunk_elem;                 // [n_chunks + 1] element range of each chunk
     const int32_t* need_ptr;                   // [n_chunks + 1]
     const int32_t* need;
-    const int32_t* need_aggl;                  // per needed element: index into need_agg
+    const int32_t* need_aggl;                  // per needed element: index into need_agg (redundant
+                                               // coarse rows), else its agglomerate
     const int32_t* need_agg_ptr;               // [grid + 1]
     const int32_t* need_agg;                   // agglomerates of the needed elements
     const int32_t* col_local;                  // [n_blocks of K_h]

@@ -489,8 +489,8 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                     if (a.redundant) {
                         const double* y = y0l + needj[l] * a.nq;
                         for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), y[kq], v);
-                    } else {
-                        const double* y = a.y0 + (int64_t)a.agg[e] * a.nq;
+                    } else {                      // needj: the element's agglomerate
+                        const double* y = a.y0 + (int64_t)needj[l] * a.nq;
                         for (int kq = 0; kq < a.nq; ++kq) v = fma(__ldg(Tr + kq), __ldcg(y + kq), v);
                     }
                 }

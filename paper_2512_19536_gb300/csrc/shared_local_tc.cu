@@ -6,15 +6,19 @@
 //
 // The right-hand sides enter as two BF16 parts each, hi = bf16(x) and lo = bf16(x - hi),
 // so the inputs keep ~16 bits and the result's error is that of the BF16 eigenbasis
-// alone.  One CTA of 128 threads per subdomain:
+// alone.  One CTA of 512 threads per subdomain:
 //   * thread 0 streams the 128 x 64 tiles of Q_i^T, then of Q_i (16 KB each, stored
 //     pre-tiled in the core-matrix layout the MMA reads: 8-row x 16-byte core matrices,
 //     K-adjacent ones 128 B apart, 8-row groups 1024 B apart) through a ring of shared-memory
 //     stages with cp.async.bulk (mbarrier completion), and issues tcgen05.mma (M = 128,
 //     N = 16 or 32, K = 16; four per tile) into one TMEM accumulator per 128-row tile;
 //     each stage's commit frees it for the next copy;
-//   * the four warps read the accumulators back with tcgen05.ld (warp w owns TMEM lanes
-//     32w..32w+31), form Y (pass 1) or V (pass 2) and write the next B operand.
+//   * the 16 warps read the accumulators back with tcgen05.ld (warp w reads TMEM lanes
+//     32 (w % 4)..32 (w % 4) + 31 of the tiles mt = w / 4, w / 4 + 4, ...), form Y (pass 1) or
+//     V (pass 2) and write the next B operand;
+//   * the FP64 work around the GEMMs (X = L^{-1} r, z = L^{-T} V, element by element with
+//     the element's block of L^{-1} read once per right-hand side) is spread over the CTA,
+//     while the first tiles are already streaming in.
 // Every wait is bounded; on a timeout the CTA raises *err, waits (bounded) for its copies
 // and MMAs in flight, frees its TMEM and leaves.
 #include <cstdint>
@@ -30,7 +34,7 @@ namespace polydg {
 
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 512;                // 16 warps: warp w reads TMEM lanes 32 (w % 4)..
 constexpr int kTcStages = 6;                   // ring of 16 KB A tiles
 constexpr uint32_t kTileBytes = 128 * 64 * 2;  // one 128 x 64 BF16 tile
 
@@ -90,11 +94,12 @@ __device__ __forceinline__ uint32_t core_off(int row, int k, uint32_t sbo) {
 
 }  // namespace
 
-template <int NB>
+template <int NB, int NP>
 __global__ void __launch_bounds__(kTcThreads, 1)
 shared_tc_kernel(const TcBlock* __restrict__ blocks, const unsigned char* __restrict__ tiles,
-                 const float* __restrict__ lam, const double* __restrict__ linv, int np, double chi,
+                 const float* __restrict__ lam, const double* __restrict__ linv, double chi,
                  TcRhs p, int* err) {
+    constexpr int np = NP;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], done;
     __shared__ uint32_t tmem_slot;
@@ -125,27 +130,7 @@ shared_tc_kernel(const TcBlock* __restrict__ blocks, const unsigned char* __rest
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fail_sh = 0;
     }
-    // X_s = L^{-1} r_s (fp64) as hi + lo bf16 parts: B-operand rows s and R + s
-    for (int idx = t; idx < NB * kpad; idx += kTcThreads) {
-        const int row = idx / kpad, k = idx - row * kpad;
-        float v = 0.f;
-        if (k < n && row < 2 * R) {
-            const int s = row < R ? row : row - R;
-            const int el = k / np, i = k - el * np;
-            const double* Li = linv + ((int64_t)(B.cell0 + el) * np + i) * np;
-            const double* rs = p.r[s] + B.in_off + (int64_t)el * np;
-            double acc = 0.0;
-            for (int j = 0; j <= i; ++j) acc = fma(Li[j], rs[j], acc);
-            const float x = (float)acc;
-            const float hi = __bfloat162float(__float2bfloat16_rn(x));
-            v = row < R ? hi : x - hi;
-        }
-        *reinterpret_cast<__nv_bfloat16*>(bop + core_off(row, k, bsbo)) = __float2bfloat16_rn(v);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_slot;
+    __syncthreads();                                         // barriers initialised
     const int T = MT * KT;                                   // tiles per pass; tile g < 2T overall
     const unsigned char* src = tiles + B.tile_off;
     const uint32_t idesc = instr_desc<NB>();
@@ -159,9 +144,41 @@ shared_tc_kernel(const TcBlock* __restrict__ blocks, const unsigned char* __rest
                      ::"r"(smem_addr(ring + (size_t)s * kTileBytes)), "l"(src + (size_t)g * kTileBytes),
                        "r"(kTileBytes), "r"(smem_addr(&full[s])) : "memory");
     };
-    // thread 0's bookkeeping: copies issued, tiles whose copy was seen complete, commits
-    // of the `done` barrier (one per pass)
-    int issued = 0, consumed = 0, commits = 0;
+    int issued = 0, consumed = 0, commits = 0;               // thread 0's bookkeeping
+    if (t == 0)                                              // the first tiles stream during X
+        while (issued < kTcStages && issued < 2 * T) copy_tile(issued++);
+
+    // X_s = L^{-1} r_s (fp64) as hi + lo bf16 parts: B-operand rows s and R + s (rows >= 2R
+    // and columns >= n are zero)
+    for (int q = t; q < NB * kpad / 8; q += kTcThreads)
+        reinterpret_cast<uint4*>(bop)[q] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    const int ncell = n / np;
+    for (int q = t; q < ncell * R; q += kTcThreads) {
+        const int el = q / R, s = q - el * R;
+        const double* Le = linv + (int64_t)(B.cell0 + el) * np * np;    // row-major, lower
+        const double* rs = p.r[s] + B.in_off + (int64_t)el * np;
+        double rv[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) rv[j] = __ldg(rs + j);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            double acc = 0.0;
+#pragma unroll
+            for (int j = 0; j <= i; ++j) acc = fma(__ldg(Le + i * NP + j), rv[j], acc);
+            const float x = (float)acc;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            const int k = el * np + i;
+            *reinterpret_cast<__nv_bfloat16*>(bop + core_off(s, k, bsbo)) = hi;
+            *reinterpret_cast<__nv_bfloat16*>(bop + core_off(R + s, k, bsbo)) =
+                __float2bfloat16_rn(x - __bfloat162float(hi));
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
     bool ok = true;
     // thread 0: the MMAs of pass `pass` (tiles pass*T .. pass*T + T - 1), refilling the ring
     // one tile behind (the stage of tile g - 1 is free once its MMAs, committed one tile
@@ -190,31 +207,33 @@ shared_tc_kernel(const TcBlock* __restrict__ blocks, const unsigned char* __rest
         ++commits;
     };
     if (t == 0) {
-        while (issued < kTcStages && issued < 2 * T) copy_tile(issued++);
         run_pass(0);
         if (!ok) fail_sh = 1;
     }
+    // lanes 1..31 of warp 0 wait here for lane 0: spinning on `done` beside it would
+    // suspend the warp in try_wait and hold lane 0's loop back
+    __syncwarp();
     if (!mbar_wait(&done, 0)) fail_sh = 1;                   // pass 1 complete
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     const bool fail1 = fail_sh != 0;
     if (!fail1) {
         // Y_s = (D hi + D lo) / (chi + c_s lam): hi/lo parts into the B operand of pass 2
-        for (int mt = 0; mt < MT; ++mt) {
+        for (int mt = warp >> 2; mt < MT; mt += kTcThreads / 128) {
             float d[NB];
-            tmem_load_row<NB>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(mt * NB), d);
-            const int j = mt * 128 + 32 * warp + lane;
-            if (j < kpad) {
-                const double lj = j < n ? (double)lam[B.lam_off + j] : 0.0;
-                for (int row = 0; row < NB; ++row) {
-                    float v = 0.f;
-                    if (j < n && row < 2 * R) {
-                        const int s = row < R ? row : row - R;
-                        const float y = (float)((double)(d[s] + d[R + s]) / (chi + p.c[s] * lj));
-                        const float hi = __bfloat162float(__float2bfloat16_rn(y));
-                        v = row < R ? hi : y - hi;
-                    }
-                    *reinterpret_cast<__nv_bfloat16*>(bop + core_off(row, j, bsbo)) = __float2bfloat16_rn(v);
+            tmem_load_row<NB>(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(mt * NB), d);
+            const int j = mt * 128 + 32 * (warp & 3) + lane;
+            if (j < n) {                  // rows >= 2R and columns >= n keep the zeros of X
+                const float lj = lam[B.lam_off + j], chif = (float)chi;
+#pragma unroll
+                for (int s = 0; s < NB / 2; ++s) {
+                    if (s >= R) break;
+                    // FP32 is ample here: y is kept to ~16 bits (hi + lo)
+                    const float y = (d[s] + d[R + s]) / fmaf((float)p.c[s], lj, chif);
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(y);
+                    *reinterpret_cast<__nv_bfloat16*>(bop + core_off(s, j, bsbo)) = hi;
+                    *reinterpret_cast<__nv_bfloat16*>(bop + core_off(R + s, j, bsbo)) =
+                        __float2bfloat16_rn(y - __bfloat162float(hi));
                 }
             }
         }
@@ -227,16 +246,17 @@ shared_tc_kernel(const TcBlock* __restrict__ blocks, const unsigned char* __rest
         run_pass(1);
         if (!ok) fail_sh = 1;
     }
+    __syncwarp();
     if (!fail1 && !mbar_wait(&done, 1)) fail_sh = 1;          // pass 2 complete
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     const bool fail2 = fail_sh != 0;
     if (!fail2) {
         // V_s = D hi + D lo (rows k of Q_i Y), staged as fp32 in the ring
-        for (int mt = 0; mt < MT; ++mt) {
+        for (int mt = warp >> 2; mt < MT; mt += kTcThreads / 128) {
             float d[NB];
-            tmem_load_row<NB>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(mt * NB), d);
-            const int k = mt * 128 + 32 * warp + lane;
+            tmem_load_row<NB>(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(mt * NB), d);
+            const int k = mt * 128 + 32 * (warp & 3) + lane;
             if (k < n)
                 for (int s = 0; s < R; ++s) vst[(size_t)s * npad + k] = d[s] + d[R + s];
         }
@@ -245,14 +265,22 @@ shared_tc_kernel(const TcBlock* __restrict__ blocks, const unsigned char* __rest
     __syncthreads();
     if (!fail2) {
         // z_s = L^{-T} V_s per element: z[i] = sum_{j >= i} Linv[j][i] V[j]
-        for (int idx = t; idx < R * n; idx += kTcThreads) {
-            const int s = idx / n, k = idx - s * n;
-            const int el = k / np, i = k - el * np;
+        const int ncell = n / np;
+        for (int q = t; q < ncell * R; q += kTcThreads) {
+            const int el = q / R, s = q - el * R;
             const double* L0 = linv + (int64_t)(B.cell0 + el) * np * np;
             const float* V = vst + (size_t)s * npad + el * np;
-            double acc = 0.0;
-            for (int j = i; j < np; ++j) acc = fma(L0[j * np + i], (double)V[j], acc);
-            p.z[s][B.in_off + k] = acc;
+            double* z = p.z[s] + B.in_off + (int64_t)el * np;
+            double vv[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) vv[j] = (double)V[j];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                double acc = 0.0;
+#pragma unroll
+                for (int j = i; j < NP; ++j) acc = fma(__ldg(L0 + j * NP + i), vv[j], acc);
+                z[i] = acc;
+            }
         }
     }
     if (fail2 && t == 0) {
@@ -274,19 +302,36 @@ size_t shared_tc_smem(int max_kpad, int nb) {
     return ring + bop;
 }
 
+template <int NB>
+static cudaError_t launch_tc_np(int np, const TcBlock* blocks, int n_blocks, const unsigned char* tiles,
+                                const float* lam, const double* linv, double chi, const TcRhs& p, size_t smem,
+                                int* err, cudaStream_t s) {
+    const void* fn = nullptr;
+    switch (np) {
+        case 3: fn = (const void*)shared_tc_kernel<NB, 3>; break;
+        case 6: fn = (const void*)shared_tc_kernel<NB, 6>; break;
+        case 10: fn = (const void*)shared_tc_kernel<NB, 10>; break;
+        case 15: fn = (const void*)shared_tc_kernel<NB, 15>; break;
+        default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    switch (np) {
+        case 3: shared_tc_kernel<NB, 3><<<n_blocks, kTcThreads, smem, s>>>(blocks, tiles, lam, linv, chi, p, err); break;
+        case 6: shared_tc_kernel<NB, 6><<<n_blocks, kTcThreads, smem, s>>>(blocks, tiles, lam, linv, chi, p, err); break;
+        case 10: shared_tc_kernel<NB, 10><<<n_blocks, kTcThreads, smem, s>>>(blocks, tiles, lam, linv, chi, p, err); break;
+        default: shared_tc_kernel<NB, 15><<<n_blocks, kTcThreads, smem, s>>>(blocks, tiles, lam, linv, chi, p, err); break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_shared_tc(const TcBlock* blocks, int n_blocks, const unsigned char* tiles,
                              const float* lam, const double* linv, int np, double chi,
                              const TcRhs& p, int max_kpad, int* err, cudaStream_t s) {
     const int nb = 2 * p.nrhs <= 16 ? 16 : 32;
     const size_t smem = shared_tc_smem(max_kpad, nb);
-    const void* fn = nb == 16 ? (const void*)shared_tc_kernel<16> : (const void*)shared_tc_kernel<32>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (nb == 16)
-        shared_tc_kernel<16><<<n_blocks, kTcThreads, smem, s>>>(blocks, tiles, lam, linv, np, chi, p, err);
-    else
-        shared_tc_kernel<32><<<n_blocks, kTcThreads, smem, s>>>(blocks, tiles, lam, linv, np, chi, p, err);
-    return cudaGetLastError();
+    return nb == 16 ? launch_tc_np<16>(np, blocks, n_blocks, tiles, lam, linv, chi, p, smem, err, s)
+                    : launch_tc_np<32>(np, blocks, n_blocks, tiles, lam, linv, chi, p, smem, err, s);
 }
 
 }  // namespace polydg
