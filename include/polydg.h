@@ -331,7 +331,8 @@ int sim_set_potential(sim_ctx *sim, const double *u_dev, const double *uprev_dev
 int sim_set_history(sim_ctx *sim, const double *hist_dev, int count, void *stream);
 
 /* Restore a simulation's ionic state and step index k >= 0 (checkpoint / resume; with
- * sim_set_history for the potentials, a resumed run continues bit for bit).  Nodal form:
+ * sim_set_history for the potentials and, in the nodal form, sim_set_ionic_aux, a resumed
+ * run continues bit for bit).  Nodal form:
  * y_dev is [5][n_nodes] in sim_get_state's node order (required).  Modal form
  * (sim_set_ionic_form, chosen before this call): Y_dev is [5][n_dofs], per state the
  * caller-order DG coefficients as sim_get_ionic_coeffs returns them (required); y_dev, if
@@ -345,6 +346,17 @@ int sim_set_state(sim_ctx *sim, const double *y_dev, const double *Y_dev, int64_
 /* Modal form only: copy the DG coefficients of the five ionic states to Y_dev
  * ([5][n_dofs], per state caller order).  EINVAL for the nodal form. */
 int sim_get_ionic_coeffs(sim_ctx *sim, double *Y_dev, void *stream);
+
+/* Nodal form only: the functions of each node's ionic state that the update carries from
+ * one step to the next instead of evaluating them ([4][n_nodes] in sim_get_state's node
+ * order: E_Na, E_K, exp(-K_o/5), exp((25 - Na_i)/3) of the Sec. 2 model; each step updates
+ * them from the step's small concentration increments, and every 256th step evaluates
+ * them afresh).  sim_get_ionic_aux copies them to aux_dev.  sim_set_ionic_aux, called after
+ * sim_set_state, restores them, so that the resumed run continues bit for bit; without it
+ * the first resumed step evaluates them from the restored state, which changes the
+ * results by rounding only.  Enqueued on `stream`.  EINVAL for the modal form. */
+int sim_get_ionic_aux(sim_ctx *sim, double *aux_dev, void *stream);
+int sim_set_ionic_aux(sim_ctx *sim, const double *aux_dev, void *stream);
 
 /* Current step index k. */
 int64_t sim_step_index(const sim_ctx *sim);

@@ -12,7 +12,7 @@ from ._native import (PolyDG, ASM, Simulation, PolyDGError, load, polydg_setup, 
                       GuessModel, guess_n_params, guess_create, guess_propose, guess_train_step,
                       sim_set_guess, SharedLocal, shared_local_setup, shared_local_apply,
                       sim_set_shared_local, sim_set_ionic_form, sim_set_state, sim_get_ionic_coeffs,
-                      set_wait_limit,
+                      sim_get_ionic_aux, sim_set_ionic_aux, set_wait_limit,
                       EXPORTS, LIB_PATH, POLYDG_OK, POLYDG_EINVAL, POLYDG_ENOMEM, POLYDG_ECUDA, POLYDG_ENOTSPD, POLYDG_ENOTCONV,
                       POLYDG_EBREAKDOWN, POLYDG_ENONFINITE)
 
@@ -23,4 +23,4 @@ __all__ = ["PolyDG", "ASM", "Simulation", "PolyDGError", "load", "polydg_setup",
            "GuessModel", "guess_n_params", "guess_create", "guess_propose", "guess_train_step",
            "sim_set_guess", "SharedLocal", "shared_local_setup", "shared_local_apply",
            "sim_set_shared_local", "sim_set_ionic_form", "sim_set_state", "sim_get_ionic_coeffs",
-           "set_wait_limit", "EXPORTS", "LIB_PATH"]
+           "sim_get_ionic_aux", "sim_set_ionic_aux", "set_wait_limit", "EXPORTS", "LIB_PATH"]

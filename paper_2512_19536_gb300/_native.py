@@ -32,7 +32,7 @@ EXPORTS = ["polydg_last_error", "polydg_setup", "polydg_setup3d", "polydg_get_in
            "shared_local_setup", "shared_local_info", "shared_local_apply", "shared_local_destroy",
            "sim_set_shared_local", "asm_autotune", "pcg_solve_trace", "pcg_lanczos_extremes",
            "sim_set_history", "sim_set_ionic_form", "polydg_set_wait_limit", "sim_set_state",
-           "sim_get_ionic_coeffs"]
+           "sim_get_ionic_coeffs", "sim_get_ionic_aux", "sim_set_ionic_aux"]
 
 
 class polydg_mesh(C.Structure):
@@ -152,6 +152,9 @@ def load() -> C.CDLL:
     L.sim_set_state.restype = i32
     L.sim_get_ionic_coeffs.argtypes = [vp, vp, vp]
     L.sim_get_ionic_coeffs.restype = i32
+    for name in ("sim_get_ionic_aux", "sim_set_ionic_aux"):
+        getattr(L, name).argtypes = [vp, vp, vp]
+        getattr(L, name).restype = i32
     for name in ("guess_n_params", "guess_create", "guess_get_params", "guess_set_scales",
                  "guess_propose", "guess_train_step", "sim_set_guess"):
         getattr(L, name).restype = i32
@@ -479,6 +482,17 @@ def sim_set_state(sim: Simulation, k, y=None, Y=None, stream=None):
 def sim_get_ionic_coeffs(sim: Simulation, Y, stream=None):
     """Modal form: the DG coefficients of the five ionic states into Y [5, n_dofs]."""
     _check(load().sim_get_ionic_coeffs(sim.h, _dev(Y), _stream(stream)))
+
+
+def sim_get_ionic_aux(sim: Simulation, aux, stream=None):
+    """Nodal form: the per-node functions the update carries (E_Na, E_K, exp(-K_o/5),
+    exp((25 - Na_i)/3)) into aux [4, n_nodes], in sim_get_state's node order."""
+    _check(load().sim_get_ionic_aux(sim.h, _dev(aux), _stream(stream)))
+
+
+def sim_set_ionic_aux(sim: Simulation, aux, stream=None):
+    """Nodal form: restore the carried functions after sim_set_state (bit-identical resume)."""
+    _check(load().sim_set_ionic_aux(sim.h, _dev(aux), _stream(stream)))
 
 
 def set_wait_limit(polls):

@@ -237,6 +237,16 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 
     P.pn_off = P.y0_off + r128((size_t)max_aggs * nq * 8);
     P.td_off = P.pn_off + r128((size_t)max_need * np * 8);
     P.smem = P.td_off + td_reserve;
+    // CM phase: each element's block-row panel of K_h is copied into a per-warp ring that
+    // reuses [0, y0_off) -- the P phase's slots and staging and r0s, all idle by then --
+    // when at least one slot per warp fits and no row has more than 32 blocks
+    {
+        int max_nb = 0;
+        for (int64_t e = 0; e < H.nc; ++e) max_nb = std::max(max_nb, (int)(H.row_ptr[e + 1] - H.row_ptr[e]));
+        P.cm_slot_bytes = r128((size_t)max_nb * np * np * 8 + 16);
+        const int64_t cst = (int64_t)(P.y0_off / ((size_t)NW * P.cm_slot_bytes));
+        P.cm_stages = (max_nb <= 32) ? (int)std::min<int64_t>(kMaxCmStages, cst) : 0;
+    }
     // LOCAL tiles balanced by bytes
     std::vector<GemvTile> tiles;
     std::vector<int64_t> tbytes;
@@ -318,6 +328,8 @@ static PersistArgs persist_args(polydg_ctx* c, asm_ctx* pc, const Plan& P, PcgWo
     a.y0_off = P.y0_off;
     a.pn_off = P.pn_off;
     a.td_off = P.td_off;
+    a.cm_stages = P.cm_stages;
+    a.cm_slot_bytes = (int)P.cm_slot_bytes;
     a.row_ptr = c->K.row_ptr;
     a.val = c->K.val;
     a.cta_chunk = P.cta_chunk;
@@ -402,7 +414,9 @@ static int setup_device(polydg_ctx* c, polydg_ctx** out) {
     // device layout: every n_p x n_p block column-major, so that a row of blocks
     // is one column-major panel (coalesced warp loads in the matvec kernel)
     const int np = H.n_p;
-    std::vector<double> Kt(H.Kval.size()), Kmt(H.Kminus_val.size());
+    // K_h values plus two doubles: a panel copy of the CM phase starts on the 16-byte
+    // boundary at or below its first block and may end up to 15 bytes past its last
+    std::vector<double> Kt(H.Kval.size() + 2, 0.0), Kmt(H.Kminus_val.size());
     for (int64_t bi = 0; bi < c->K.nblk; ++bi)
         for (int i = 0; i < np; ++i)
             for (int j = 0; j < np; ++j) {
@@ -1121,7 +1135,7 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
     int st;
     if ((st = sm->work.alloc(n)) || (st = dalloc(&sm->U, n)) || (st = dalloc(&sm->Uprev, n)) ||
         (st = dalloc(&sm->Uprev2, n)) || (st = dalloc(&sm->xg, n)) ||
-        (st = dalloc(&sm->I, n)) || (st = dalloc(&sm->y, 5 * nn)) || (st = dalloc(&sm->d_y0, 5)) ||
+        (st = dalloc(&sm->I, n)) || (st = dalloc(&sm->y, 5 * nn)) || (st = dalloc(&sm->yc, 4 * nn)) || (st = dalloc(&sm->d_y0, 5)) ||
         (st = dalloc(&sm->d_ss, 1)) || (st = dalloc(&sm->ring, kHistRing * n)) ||
         (st = dalloc(&sm->kuring, kHistRing * n)) || (st = dalloc(&sm->subW, 2 * n)) || (st = dalloc(&sm->gram, kSubMaxPairs * kSubMaxCtas)))
         return fail(st);
@@ -1203,7 +1217,7 @@ static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
         CU(launch_ionic_modal(np, sm->U, sm->Uprev, c->d_node_ptr, c->d_node_w, c->d_node_phi, c->d_Minv,
                               sm->Ym, sm->y, nn, H.nc, dt, sm->I, sm->d_ss, s));
     else
-        CU(launch_ionic(np, sm->U, sm->Uprev, c->d_node_ptr, c->d_node_w, c->d_node_phi, sm->y, nn,
+        CU(launch_ionic(np, sm->U, sm->Uprev, c->d_node_ptr, c->d_node_w, c->d_node_phi, sm->y, sm->yc, nn,
                         H.nc, dt, sm->I, sm->d_ss, s));
     CU(launch_matvec(MODE_RHS, np, c->K, c->K.val_minus, sm->U, w.b, sm->I, sm->F, -H.chi_cm * dt,
                      dt, sm->d_ss, dt, sm->prm.stim_duration, s));
@@ -1495,6 +1509,24 @@ int sim_get_state(sim_ctx* sm, double* u_dev, double* y_dev, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     CU(launch_permute(sm->U, nullptr, u_dev, c->d_to_caller, c->H.nc, c->H.n_p, 0, nullptr, s));
     if (y_dev) CU(launch_node_gather(sm->y, y_dev, c->d_node_pos, (int64_t)c->H.node_w.size(), s));
+    return POLYDG_OK;
+}
+
+int sim_get_ionic_aux(sim_ctx* sm, double* aux_dev, void* stream) {
+    if (!sm || !aux_dev) { set_error("sim_get_ionic_aux: null argument"); return POLYDG_EINVAL; }
+    if (sm->Ym) { set_error("sim_get_ionic_aux: the modal form carries no per-node functions"); return POLYDG_EINVAL; }
+    polydg_ctx* c = sm->ctx;
+    CU(launch_node_gather(sm->yc, aux_dev, c->d_node_pos, (int64_t)c->H.node_w.size(), (cudaStream_t)stream, 4));
+    return POLYDG_OK;
+}
+
+int sim_set_ionic_aux(sim_ctx* sm, const double* aux_dev, void* stream) {
+    if (!sm || !aux_dev) { set_error("sim_set_ionic_aux: null argument"); return POLYDG_EINVAL; }
+    if (sm->Ym) { set_error("sim_set_ionic_aux: the modal form carries no per-node functions"); return POLYDG_EINVAL; }
+    polydg_ctx* c = sm->ctx;
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(launch_node_scatter(aux_dev, sm->yc, c->d_node_pos, (int64_t)c->H.node_w.size(), s, 4));
+    CU(launch_ionic_aux_valid(sm->d_ss, s));
     return POLYDG_OK;
 }
 
@@ -1924,7 +1956,7 @@ void sim_destroy(sim_ctx* sm) {
     if (!sm) return;
     for (auto e : sm->ev) cudaEventDestroy(e);
     sm->work.release();
-    dfree(sm->U); dfree(sm->Uprev); dfree(sm->Uprev2); dfree(sm->xg); dfree(sm->I); dfree(sm->F); dfree(sm->y); dfree(sm->d_y0);
+    dfree(sm->U); dfree(sm->Uprev); dfree(sm->Uprev2); dfree(sm->xg); dfree(sm->I); dfree(sm->F); dfree(sm->y); dfree(sm->yc); dfree(sm->d_y0);
     dfree(sm->Ym);
     dfree(sm->ring); dfree(sm->kuring); dfree(sm->subW); dfree(sm->gram);
     dfree(sm->d_ss);

@@ -97,6 +97,8 @@ struct Plan {
     int64_t* elem_ptr = nullptr;
     double est_seconds = 0.0;           // cost model: slowest CTA's P phase per iteration
     int max_need = 0, max_aggs = 0;     // staged elements per chunk, agglomerates per CTA
+    int cm_stages = 0;                  // K_h panel slots per warp in the CM phase (0: loads)
+    size_t cm_slot_bytes = 0;
     std::vector<GemvTile> h_tiles;      // the tile sequence and its modelled costs (autotuning)
     std::vector<double> h_cost, h_stage;
     std::vector<int32_t> h_tile_ptr;
@@ -188,6 +190,7 @@ struct sim_ctx {
     double* subW = nullptr;             // [2][n] r0 = b - K U^k and K (xg - U^k) of the subspace guess
     double* gram = nullptr;             // [kSubMaxPairs][kSubMaxCtas] Gram partial sums
     double *U = nullptr, *Uprev = nullptr, *I = nullptr, *F = nullptr, *y = nullptr;
+    double* yc = nullptr;               // per node: E_Na, E_K, exp(-K_o/5), exp((25 - Na_i)/3) (nodal form)
     double* d_y0 = nullptr;
     double* Ym = nullptr;               // [5][n] modal ionic state (sim_set_ionic_form 1), or null
     SimScalars* d_ss = nullptr;

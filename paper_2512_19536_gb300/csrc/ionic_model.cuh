@@ -14,8 +14,10 @@
 // The device forms below evaluate the same expressions with the exponentials of V
 // and of K_o regrouped (exp(a + b) = exp(a) exp(b), one exponential per potential),
 // the reciprocals of a node batched into one division, and the Nernst potentials after
-// an Euler step updated from the old ones; results differ from the plain forms by
-// rounding only.
+// an Euler step updated from the old ones; the per-node update also carries E_Na, E_K
+// and the two concentration exponentials from one step to the next (NodeCache) and
+// takes exp(-u~/720) from exp(-u/720).  Results differ from the plain forms by rounding
+// only.
 #pragma once
 
 #include <cmath>
@@ -76,8 +78,8 @@ inline NodeConsts node_consts() {
     return k;
 }
 
-// exp(-V/s) for s = 10, 18, 20, 80, 2.5 from B = exp(-V/720).
-struct VPowers { double e10, e18, e20, e80, e25; };
+// exp(-V/s) for s = 10, 18, 20, 80, 2.5 from B = exp(-V/720) (kept in B).
+struct VPowers { double e10, e18, e20, e80, e25, B; };
 
 BC_HD VPowers vpowers(double V) {
     const double B = exp(-V * (1.0 / 720.0));
@@ -89,15 +91,29 @@ BC_HD VPowers vpowers(double V) {
     p.e18 = B32 * B8;
     p.e10 = B64 * B8;
     p.e25 = B256 * B32;
+    p.B = B;
     return p;
 }
 
-// exp(-V/10) and exp(-V/18) only (the sodium gate of the current).
-BC_HD void vpowers_m(double V, double& e10, double& e18) {
-    const double B = exp(-V * (1.0 / 720.0));
+// exp(-V/10) and exp(-V/18) only (the sodium gate of the current), from B = exp(-V/720).
+BC_HD void vpowers_m_from(double B, double& e10, double& e18) {
     const double B2 = B * B, B4 = B2 * B2, B8 = B4 * B4, B16 = B8 * B8, B32 = B16 * B16;
     e18 = B32 * B8;
     e10 = (B32 * B32) * B8;
+}
+
+BC_HD void vpowers_m(double V, double& e10, double& e18) {
+    vpowers_m_from(exp(-V * (1.0 / 720.0)), e10, e18);
+}
+
+// exp(a): for |a| < 2^-6 the Taylor polynomial of degree 7 (remainder < a^8 / 8! < 1e-19
+// relative), else the library function.  For the ratio of an exponential at two nearby
+// arguments.
+BC_HD double exp_small(double a) {
+    if (fabs(a) < 0x1p-6)
+        return 1.0 + a * (1.0 + a * (0.5 + a * (1.0 / 6.0 + a * (1.0 / 24.0 + a * (1.0 / 120.0 +
+                     a * (1.0 / 720.0 + a * (1.0 / 5040.0)))))));
+    return exp(a);
 }
 
 // Reciprocals of M nonzero values with one division: prefix products, the reciprocal
@@ -142,11 +158,27 @@ constexpr double kInvTau = 1.0 / tau;
 // update of the potentials after an Euler step, see current_after_step).
 struct Nernst { double ENa, EK, iNao, iNai, iKo, iKi; };
 
+// Functions of a node's concentrations that the update needs, carried from one step to
+// the next: E_Na, E_K, X = exp(-K_o/5) and exp((25 - Na_i)/3).  Each step changes the
+// concentrations by small increments, so the new values follow from the old ones by
+// logarithms and exponentials of numbers near 1 and 0 (short series).
+struct NodeCache { double ENa, EK, X, ep; };
+
+BC_HD NodeCache node_cache(double Ko, double Nai) {
+    const double Ki = 140.0 + (18.0 - Nai);
+    const double Nao = 144.0 - beta * (Nai - 18.0);
+    return NodeCache{RTF * log(Nao / Nai), RTF * log(Ko / Ki), exp(-Ko * kInv5), exp((25.0 - Nai) * kInv3)};
+}
+
 // y'(V, y) of the Sec. 2 model (= -m(u, y)) at one point: d[0..4] for n, h, K_o, Na_i,
-// Ca_i; also the Nernst potentials of the state in *ne (may be null).
+// Ca_i; also the Nernst potentials of the state in *ne (may be null).  CACHED: E_Na, E_K
+// and the two concentration exponentials are read from *c instead of evaluated; else,
+// when c is given, they are stored there.  *Bv (may be null) receives exp(-V/720).
+template <bool CACHED = false>
 BC_HD void rates(const NodeConsts& k, double V, double n, double h, double Ko, double Nai, double Cai,
-                 double* d, Nernst* ne = nullptr) {
+                 double* d, Nernst* ne = nullptr, NodeCache* c = nullptr, double* Bv = nullptr) {
     const VPowers p = vpowers(V);
+    if (Bv) *Bv = p.B;
     const double xn = V + 34.0, xm = V + 30.0;
     const bool sn = fabs(xn) < 1e-5, sm = fabs(xm) < 1e-5;       // |x| < 1e-6 s, s = 10
     const double exn = k.an * p.e10, exm = k.am * p.e10;
@@ -156,8 +188,8 @@ BC_HD void rates(const NodeConsts& k, double V, double n, double h, double Ko, d
     const double am_den = sm ? 1.0 : 1.0 - exm;
     const double Ki = 140.0 + (18.0 - Nai);
     const double Nao = 144.0 - beta * (Nai - 18.0);
-    const double X = exp(-Ko * kInv5), X2 = X * X, X5 = X2 * X2 * X;
-    const double ep = exp((25.0 - Nai) * kInv3);
+    const double X = CACHED ? c->X : exp(-Ko * kInv5), X2 = X * X, X5 = X2 * X2 * X;
+    const double ep = CACHED ? c->ep : exp((25.0 - Nai) * kInv3);
     double den[11] = {sn ? 1.0 : 1.0 - exn,                  // alpha_n
                       1.0 + k.bh * p.e10,                    // beta_h
                       am_num + bm * am_den,                  // m_inf
@@ -173,8 +205,9 @@ BC_HD void rates(const NodeConsts& k, double V, double n, double h, double Ko, d
     const double ah = k.ah * p.e20;
     const double bh = inv[1];
     const double minf = am_num * inv[2];
-    const double ENa = RTF * log(Nao * inv[7]);
-    const double EK = RTF * log(Ko * inv[8]);
+    const double ENa = CACHED ? c->ENa : RTF * log(Nao * inv[7]);
+    const double EK = CACHED ? c->EK : RTF * log(Ko * inv[8]);
+    if (!CACHED && c) *c = NodeCache{ENa, EK, X, ep};
     const double INa = (gNa * minf * minf * minf * h + gNaL) * (V - ENa);
     const double IK = (gK * (n * n) * (n * n) + gAHP * Cai * inv[3] + gKL) * (V - EK);
     const double pump = rho * inv[4];
@@ -191,15 +224,20 @@ BC_HD void rates(const NodeConsts& k, double V, double n, double h, double Ko, d
     }
 }
 
-// Sodium gate m_inf(V) = num / den (the division is left to the caller's batch).
-BC_HD void minf_parts(const NodeConsts& k, double V, double& num, double& den) {
+// Sodium gate m_inf(V) = num / den (the division is left to the caller's batch); B is
+// exp(-V/720).
+BC_HD void minf_parts_b(const NodeConsts& k, double V, double B, double& num, double& den) {
     double e10, e18;
-    vpowers_m(V, e10, e18);
+    vpowers_m_from(B, e10, e18);
     const double xm = V + 30.0;
     const bool sm = fabs(xm) < 1e-5;
     const double exm = k.am * e10, bm = k.bm * e18;
     num = sm ? 0.1 * (10.0 + 0.5 * xm) : 0.1 * xm;
     den = num + bm * (sm ? 1.0 : 1.0 - exm);
+}
+
+BC_HD void minf_parts(const NodeConsts& k, double V, double& num, double& den) {
+    minf_parts_b(k, V, exp(-V * (1.0 / 720.0)), num, den);
 }
 
 // I_Na + I_K + I_Cl at potential V for state (n, h, K_o, Na_i, Ca_i).
@@ -222,18 +260,27 @@ BC_HD double total_current(const NodeConsts& k, double V, double n, double h, do
 //   E_Na' = E_Na + RTF (ln(1 - beta dNa / Na_o) - ln(1 + dNa / Na_i)),
 //   E_K'  = E_K  + RTF (ln(1 + dK / K_o) - ln(1 - dNa / K_i)),
 // logarithms of numbers within ~1e-3 of 1 (a short series) instead of two full ones.
-BC_HD double current_after_step(const NodeConsts& k, double V, double n, double h, double Ko,
-                                double Nai, double Cai, const Nernst& ne, double dK, double dNa) {
+// B = exp(-V/720); the new potentials go to *ENa1, *EK1 when given.
+BC_HD double current_after_step_b(const NodeConsts& k, double V, double B, double n, double h, double Ko,
+                                  double Nai, double Cai, const Nernst& ne, double dK, double dNa,
+                                  double* ENa1 = nullptr, double* EK1 = nullptr) {
     double num, den;
-    minf_parts(k, V, num, den);
+    minf_parts_b(k, V, B, num, den);
     double dd[2] = {den, 1.0 + Cai}, inv[2];
     batch_reciprocal(dd, inv);
     const double minf = num * inv[0];
     const double ENa = ne.ENa + RTF * (log1p_small(-beta * dNa * ne.iNao) - log1p_small(dNa * ne.iNai));
     const double EK = ne.EK + RTF * (log1p_small(dK * ne.iKo) - log1p_small(-dNa * ne.iKi));
+    if (ENa1) *ENa1 = ENa;
+    if (EK1) *EK1 = EK;
     const double INa = (gNa * minf * minf * minf * h + gNaL) * (V - ENa);
     const double IK = (gK * (n * n) * (n * n) + gAHP * Cai * inv[1] + gKL) * (V - EK);
     return INa + IK + gClL * (V - k.ECl);
+}
+
+BC_HD double current_after_step(const NodeConsts& k, double V, double n, double h, double Ko,
+                                double Nai, double Cai, const Nernst& ne, double dK, double dNa) {
+    return current_after_step_b(k, V, exp(-V * (1.0 / 720.0)), n, h, Ko, Nai, Cai, ne, dK, dNa);
 }
 
 // One explicit Euler step y <- y + dt y'(V, y) (Sec. 2 model, per quadrature node).
@@ -263,6 +310,29 @@ BC_HD double euler_and_current(const NodeConsts& k, double V, double Vx, double 
     Nai += dNa;
     Cai += dt * d[4];
     return current_after_step(k, Vx, n, h, Ko, Nai, Cai, ne, dK, dNa);
+}
+
+// The same step with the node's carried functions c (CACHED: c holds the old state's
+// values; else they are evaluated) and c left holding the new state's: E_Na and E_K as
+// above, X and the sodium exponential times exp(-dK/5) and exp(-dNa/3), and
+// exp(-Vx/720) = exp(-V/720) exp((V - Vx)/720).
+template <bool CACHED>
+BC_HD double euler_and_current_c(const NodeConsts& k, double V, double Vx, double dt, double& n,
+                                 double& h, double& Ko, double& Nai, double& Cai, NodeCache& c) {
+    double d[5], B;
+    Nernst ne;
+    rates<CACHED>(k, V, n, h, Ko, Nai, Cai, d, &ne, &c, &B);
+    const double dK = dt * d[2], dNa = dt * d[3];
+    n += dt * d[0];
+    h += dt * d[1];
+    Ko += dK;
+    Nai += dNa;
+    Cai += dt * d[4];
+    const double Bx = B * exp_small((V - Vx) * (1.0 / 720.0));
+    const double f = current_after_step_b(k, Vx, Bx, n, h, Ko, Nai, Cai, ne, dK, dNa, &c.ENa, &c.EK);
+    c.X *= exp_small(-dK * kInv5);
+    c.ep *= exp_small(-dNa * kInv3);
+    return f;
 }
 
 // Rest state at potential V0: gates at steady state, K_o = 4, Na_i = 18, Ca_i = 0.

@@ -39,7 +39,7 @@ struct SimScalars {
     int32_t sub_dirs;      // directions of this step's subspace guess
     double theta_sub[kSubMaxDirs];   // their coefficients
     int32_t kd_len;        // consecutive increment products K D_j held by their ring, up to kd_step
-    int32_t pad2;
+    int32_t yc_ok;         // the nodal ionic update's carried functions match the state
     int64_t kd_step;
 };
 
@@ -116,10 +116,13 @@ struct PersistArgs {
     int trace_cap;
     int apply_only;                            // 1: z = B_ad^{-1} b once (r = b, no solve)
     uint32_t wait_limit;                       // polls of a grid barrier before it gives up
-    int pad_wait;
+    int cm_stages;                             // CM phase: K_h panel slots per warp (0: loads)
+    int cm_slot_bytes;
+    int pad_cm;
 };
 
 constexpr int kMaxWarpStages = 4;              // copy slots per warp in the P phase
+constexpr int kMaxCmStages = 4;                // K_h panel slots per warp in the CM phase
 
 // Shared local solves (shared_local.cu): one subdomain's eigenbasis in the store.
 struct SharedBlock {
@@ -301,7 +304,7 @@ cudaError_t launch_to_half(const float* w32, __half* w16, int P, cudaStream_t s)
 
 // Ionic update + ion-current load (Eq. fully-discrete-1).
 cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int64_t* node_ptr,
-                         const double* node_w, const double* node_phi, double* y, int64_t nn,
+                         const double* node_w, const double* node_phi, double* y, double* yc, int64_t nn,
                          int64_t nc, double dt, double* I, const SimScalars* ss, cudaStream_t s);
 // Modal ionic state (the second line of Eq. fully-discrete-1 in the DG basis): Ym is
 // [5][nc n_p], Minv the per-cell inverse mass blocks [nc][n_p][n_p] (row-major).
@@ -311,14 +314,16 @@ cudaError_t launch_ionic_modal(int np, const double* U, const double* Uprev, con
                                const SimScalars* ss, cudaStream_t s);
 cudaError_t launch_init_modal(double* Ym, int64_t nc, int np, const double* y0, cudaStream_t s);
 cudaError_t launch_node_gather(const double* y_int, double* y_caller,
-                               const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s);
+                               const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s, int ns = 5);
 cudaError_t launch_step_finish(double* U, double* Uprev, double* Uprev2, const double* x0,
                                const double* x1, int64_t n, const PcgScalars* sc, SimScalars* ss,
                                double* ring, cudaStream_t s);
 cudaError_t launch_step_begin(PcgScalars* sc, SimScalars* ss, cudaStream_t s);
 cudaError_t launch_init_y(double* y, int64_t nn, const double* y0, cudaStream_t s);
 cudaError_t launch_node_scatter(const double* y_caller, double* y_int,
-                                const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s);
+                                const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s, int ns = 5);
+// The nodal update's carried functions (SimScalars::yc_ok) match the restored state.
+cudaError_t launch_ionic_aux_valid(SimScalars* ss, cudaStream_t s);
 // Step index k of a simulation (and its failed flag cleared), for a restored state.
 cudaError_t launch_set_step(SimScalars* ss, int64_t k, cudaStream_t s);
 

@@ -13,6 +13,10 @@ namespace polydg {
 // Warp per cell: nodes of cell e are node_ptr[e]..node_ptr[e+1]-1.  Per node:
 //   u^k(x_q), y^{k+1} = y^k + dt y'(u^k, y^k),  u~ = 3/2 U^k - 1/2 U^{k-1} (U^0 at k = 0),
 //   I_e[i] = sum_q w_q f(u~(x_q), y^{k+1}_q) phi_i(x_q).
+// yc carries E_Na, E_K, exp(-K_o/5) and exp((25 - Na_i)/3) of each node's state from one
+// step to the next (bc::NodeCache): the update reads them instead of two logarithms and
+// two exponentials and leaves the new state's.  ionic_cache_kernel evaluates them afresh
+// before the update when the state was set from outside (ss->yc_ok = 0) and every 256 steps.
 // The cell's coefficient vectors sit in shared memory (broadcast reads), so a thread
 // keeps only its node's basis values and the NP partial sums in registers: two
 // 256-thread blocks fit on an SM, which the fp64-latency-bound node update needs.
@@ -22,8 +26,9 @@ template <int NP>
 __global__ void __launch_bounds__(kIonicThreads, 2)
 ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
              const int64_t* __restrict__ node_ptr, const double* __restrict__ node_w,
-             const double* __restrict__ node_phi, double* __restrict__ y, int64_t nn, int64_t nc,
-             double dt, double* __restrict__ I, const SimScalars* ss, const bc::NodeConsts kc) {
+             const double* __restrict__ node_phi, double* __restrict__ y, double* __restrict__ yc,
+             int64_t nn, int64_t nc, double dt, double* __restrict__ I, const SimScalars* ss,
+             const bc::NodeConsts kc) {
     __shared__ double su[kIonicThreads / 32][2][NP];
     if (ss->failed) return;
     const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -51,8 +56,10 @@ ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
         }
         double n = y[q], h = y[nn + q], Ko = y[2 * nn + q], Nai = y[3 * nn + q], Cai = y[4 * nn + q];
         // explicit Euler with u^k, then f(u~, y^{k+1})
-        const double f = bc::euler_and_current(kc, uk, ux, dt, n, h, Ko, Nai, Cai);
+        bc::NodeCache c{yc[q], yc[nn + q], yc[2 * nn + q], yc[3 * nn + q]};
+        const double f = bc::euler_and_current_c<true>(kc, uk, ux, dt, n, h, Ko, Nai, Cai, c);
         y[q] = n; y[nn + q] = h; y[2 * nn + q] = Ko; y[3 * nn + q] = Nai; y[4 * nn + q] = Cai;
+        yc[q] = c.ENa; yc[nn + q] = c.EK; yc[2 * nn + q] = c.X; yc[3 * nn + q] = c.ep;
         const double wf = node_w[q] * f;
         // the basis values again (L1 hits): keeping them in registers across the node
         // update would spill
@@ -66,16 +73,31 @@ ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
     }
 }
 
+// The carried functions of every node's state, evaluated from the state (skipped while
+// ss->yc_ok holds, except every 256th step).
+__global__ void ionic_cache_kernel(const double* __restrict__ y, double* __restrict__ yc, int64_t nn,
+                                   const SimScalars* ss) {
+    if (ss->failed || (ss->yc_ok != 0 && (ss->k & 255) != 0)) return;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nn) return;
+    const bc::NodeCache c = bc::node_cache(y[2 * nn + q], y[3 * nn + q]);
+    yc[q] = c.ENa;
+    yc[nn + q] = c.EK;
+    yc[2 * nn + q] = c.X;
+    yc[3 * nn + q] = c.ep;
+}
+
 cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int64_t* node_ptr,
-                         const double* node_w, const double* node_phi, double* y, int64_t nn,
+                         const double* node_w, const double* node_phi, double* y, double* yc, int64_t nn,
                          int64_t nc, double dt, double* I, const SimScalars* ss, cudaStream_t s) {
     const unsigned g = (unsigned)((nc * 32 + kIonicThreads - 1) / kIonicThreads);
     static const bc::NodeConsts kc = bc::node_consts();
+    ionic_cache_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(y, yc, nn, ss);
     switch (np) {
-        case 3: ionic_kernel<3><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss, kc); break;
-        case 6: ionic_kernel<6><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss, kc); break;
-        case 10: ionic_kernel<10><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss, kc); break;
-        case 15: ionic_kernel<15><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, nn, nc, dt, I, ss, kc); break;
+        case 3: ionic_kernel<3><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, yc, nn, nc, dt, I, ss, kc); break;
+        case 6: ionic_kernel<6><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, yc, nn, nc, dt, I, ss, kc); break;
+        case 10: ionic_kernel<10><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, yc, nn, nc, dt, I, ss, kc); break;
+        case 15: ionic_kernel<15><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, yc, nn, nc, dt, I, ss, kc); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -220,41 +242,47 @@ cudaError_t launch_init_modal(double* Ym, int64_t nc, int np, const double* y0, 
 
 // y_caller[pos[q]][s] = y_int[q][s] for the 5 state rows.
 __global__ void node_gather_kernel(const double* __restrict__ yi, double* __restrict__ yc,
-                                   const int64_t* __restrict__ pos, int64_t nn) {
+                                   const int64_t* __restrict__ pos, int64_t nn, int ns) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nn) return;
     const int64_t d = pos[q];
-#pragma unroll
-    for (int s = 0; s < 5; ++s) yc[s * nn + d] = yi[s * nn + q];
+    for (int s = 0; s < ns; ++s) yc[s * nn + d] = yi[s * nn + q];
 }
 
 cudaError_t launch_node_gather(const double* y_int, double* y_caller,
-                               const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s) {
+                               const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s, int ns) {
     node_gather_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(y_int, y_caller,
-                                                                   node_to_caller_pos, nn);
+                                                                   node_to_caller_pos, nn, ns);
     return cudaGetLastError();
 }
 
 // The reverse of node_gather_kernel: caller node order -> internal node order.
 __global__ void node_scatter_kernel(const double* __restrict__ yc, double* __restrict__ yi,
-                                    const int64_t* __restrict__ pos, int64_t nn) {
+                                    const int64_t* __restrict__ pos, int64_t nn, int ns) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nn) return;
     const int64_t d = pos[q];
-#pragma unroll
-    for (int s = 0; s < 5; ++s) yi[s * nn + q] = yc[s * nn + d];
+    for (int s = 0; s < ns; ++s) yi[s * nn + q] = yc[s * nn + d];
 }
 
 cudaError_t launch_node_scatter(const double* y_caller, double* y_int,
-                                const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s) {
+                                const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s, int ns) {
     node_scatter_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(y_caller, y_int,
-                                                                    node_to_caller_pos, nn);
+                                                                    node_to_caller_pos, nn, ns);
+    return cudaGetLastError();
+}
+
+__global__ void ionic_aux_valid_kernel(SimScalars* ss) { ss->yc_ok = 1; }
+
+cudaError_t launch_ionic_aux_valid(SimScalars* ss, cudaStream_t s) {
+    ionic_aux_valid_kernel<<<1, 1, 0, s>>>(ss);
     return cudaGetLastError();
 }
 
 __global__ void set_step_kernel(SimScalars* ss, int64_t k) {
     ss->k = k;
     ss->failed = 0;
+    ss->yc_ok = 0;             // the state was set from outside
 }
 
 cudaError_t launch_set_step(SimScalars* ss, int64_t k, cudaStream_t s) {
@@ -308,6 +336,7 @@ __global__ void step_finish_kernel(double* __restrict__ U, double* __restrict__ 
 __global__ void step_stats_kernel(const PcgScalars* sc, SimScalars* ss) {
     if (threadIdx.x != 0 || ss->failed) return;
     if (ss->hist_len < kHistRing) ss->hist_len += 1;
+    ss->yc_ok = 1;             // the step's ionic update left the new state's carried functions
     ss->k += 1;
     ss->steps_done += 1;
     ss->total_its += sc->it;

@@ -37,13 +37,14 @@
 namespace polydg {
 
 // The whole solve as seen by CTA `cta` of the G CTAs working on it.
-template <int DT, int NP>
+template <int DT, int NP, bool CMS>
 __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int cta, const unsigned G,
                                               unsigned char* smem) {
     using T = typename StoreType<DT>::T;
     using X = typename StoreType<DT>::X;
     constexpr int NW = kPersistThreads / 32;
     __shared__ __align__(8) uint64_t wbars[NW][kMaxWarpStages];
+    __shared__ __align__(8) uint64_t cmbars[NW][kMaxCmStages];
     __shared__ double scal[3];            // alpha, beta, pq from thread 0
     __shared__ int scode;                 // thread 0's verdict after a grid sum
     __shared__ double red[3 * kPersistThreads], outv[3];   // grid-sum scratch
@@ -143,11 +144,15 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         n_rows += rn.row_end - rn.row_begin;
     }
     const bool has_rows = warp < n_rows;
+    const int rows_w = has_rows ? (n_rows - 1 - warp) / NW + 1 : 0;   // this warp's rows per P phase
     uint32_t wseq = 0;                // rows this warp consumed so far (all iterations)
     uint32_t n_done = 0, n_issued = 0;  // copies seen complete / issued (copy c: slot c % S)
+    int iss_left = 0;                 // rows of the current P phase not yet issued
     bool wfail = false;               // a copy wait timed out: no more waits or copies
     // issue side (lane 0): run and row of the warp's next copy; after the CTA's last
-    // run it starts over at the warp's first row (the inverses are constant)
+    // run it starts over at the warp's first row (the next P phase's first copy).  With
+    // the CM ring (CMS) the copies stop at the end of each P phase, which leaves the
+    // slots to the CM phase, and the next P phase's first ones go out when it ends.
     int iss_run = 0, iss_row = 0, first_run = 0, first_row = 0;
     __syncthreads();
     if (has_rows) {
@@ -169,13 +174,52 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
             iss_row = rd[iss_run].row_begin + over;
         }
     };
+    // lane 0: the first copies of a P phase (at most S, at most the warp's rows)
+    auto issue_first = [&]() {
+        const int m = min(S, rows_w);
+        if (lane == 0)
+            for (int j = 0; j < m; ++j) issue((int)((n_issued + j) % S));
+        n_issued += m;
+        iss_left = rows_w - m;
+    };
     if (has_rows) {
-        if (lane == 0) {
+        if (lane == 0)
             for (int k = 0; k < S; ++k) mbar_init(&wbars[warp][k]);
-            for (int k = 0; k < S; ++k) issue(k);
+        if (CMS) {
+            issue_first();
+        } else {                      // no CM ring: the copies run on into the next P phase
+            if (lane == 0)
+                for (int k = 0; k < S; ++k) issue(k);
+            n_issued = S;
         }
-        n_issued = S;
     }
+    bool p_armed = true;              // the coming P phase's first copies are in flight
+    // CM phase: this warp's elements (chunk by chunk: ce0 + warp, + NW, ...) stream their
+    // K_h block-row panels through CS slots of cm_slot_bytes in [0, y0_off)
+    const int CS = CMS ? a.cm_stages : 1;     // (1: a divisor for the dead code of CMS = false)
+    uint32_t cm_seq = 0, cm_done = 0, cm_issued = 0;   // panels consumed / seen complete / issued
+    bool cmfail = false;
+    int cm_ch = ch1;                  // issue side: chunk and element of the next panel
+    int64_t cm_e = 0;
+    auto cm_norm = [&]() {
+        while (cm_ch < ch1 && cm_e >= a.chunk_elem[cm_ch + 1]) {
+            ++cm_ch;
+            if (cm_ch < ch1) cm_e = a.chunk_elem[cm_ch] + warp;
+        }
+    };
+    const uint64_t cm_pol = evict_first_policy();
+    // lane 0: element cm_e's panel into slot k (from the 16-byte boundary at or below it;
+    // the values array carries two doubles of slack past its end)
+    auto cm_issue = [&](int k) {
+        const int64_t b0 = a.row_ptr[cm_e], b1 = a.row_ptr[cm_e + 1];
+        const uintptr_t src = reinterpret_cast<uintptr_t>(a.val + b0 * NP * NP);
+        const uintptr_t s16 = src & ~(uintptr_t)15;
+        const uint32_t bytes = (uint32_t)(((uintptr_t)(b1 - b0) * NP * NP * 8 + (src - s16) + 15) & ~(uintptr_t)15);
+        bulk_load(smem + ((size_t)warp * CS + k) * a.cm_slot_bytes, reinterpret_cast<const void*>(s16), bytes,
+                  &cmbars[warp][k], cm_pol);
+    };
+    if (CMS && CS > 0 && lane == 0)
+        for (int k = 0; k < CS; ++k) mbar_init(&cmbars[warp][k]);
     bool ok = barrier_sum<2>(a.gs, G, cta, gen, a.err, a.partials, v2, red, outv, [](const double*) {}, wl);
     const double bb = v2[0];
     double rr = v2[1];
@@ -195,6 +239,8 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
     while (!done) {
         // ---------------------------------------------------------------- P
         if (timing && threadIdx.x == 0) t_mark = clock64();
+        if (CMS && !p_armed && has_rows && !wfail) issue_first();
+        p_armed = true;
         const double* rin = a.r[par];
         double* rout = a.r[par ^ 1];
         const double* pold = a.p[pp];
@@ -325,14 +371,16 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                     ++n_done;
                     const double zr = row_dot(slot(warp, k), xin, rn.ld, lane, 0, 1);
                     __syncwarp();                 // every lane is done with the slot
-                    if (lane == 0) {
-                        a.zl[rn.in_off + row] = zr;
-                        issue(k);
+                    if (lane == 0) a.zl[rn.in_off + row] = zr;
+                    if (!CMS || iss_left > 0) {
+                        if (lane == 0) issue(k);
+                        ++n_issued;
+                        --iss_left;
                     }
-                    ++n_issued;
                 }
             }
         }
+        p_armed = false;
         if (threadIdx.x == 0 && n_own > 0) {     // K_h rows of the CM phase's first chunk into L2
             const int64_t pe1 = a.chunk_elem[ch0 + 1];
             // a bulk prefetch takes a 16-byte aligned address and a multiple of 16 bytes;
@@ -473,6 +521,22 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         // z = z_loc + R_0^T y0 for own and neighbour elements; w = K z on own elements,
         // chunk by chunk of the CTA's elements
         double v3[3] = {0.0, 0.0, 0.0};           // r.z, z.q_k, z.w
+        const bool cm_stream = CMS && CS > 0 && !apply;
+        if (cm_stream) {
+            // the ring's region ([0, y0_off): P slots and staging, r0s) is free once every
+            // thread is past the coarse phase; the first CS panels fly during the z staging
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            cm_ch = ch0;
+            cm_e = ch0 < ch1 ? a.chunk_elem[ch0] + warp : 0;
+            cm_norm();
+            for (int m = 0; m < CS && cm_ch < ch1 && !cmfail; ++m) {
+                if (lane == 0) cm_issue((int)(cm_issued % CS));
+                ++cm_issued;
+                cm_e += NW;
+                cm_norm();
+            }
+        }
         for (int ch = ch0; ch < ch1; ++ch) {
             const int64_t ce0 = a.chunk_elem[ch], ce1 = a.chunk_elem[ch + 1];
             const int n_chunk = (int)(ce1 - ce0);
@@ -499,7 +563,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
             }
             __syncthreads();
             if (apply) continue;                  // z is the result: no matvec
-            local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, ce0, ce1, [&](int64_t e, int i, double kz) {
+            auto emit = [&](int64_t e, int i, double kz) {
                 const int64_t t = e * NP + i;
                 const double zv = pn[(e - ce0) * NP + i];
                 if (pipe) {                       // zv = m (u on the first pass), kz = K m
@@ -526,13 +590,54 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 v3[0] = fma(__ldcg(rk + t), zv, v3[0]);
                 v3[1] = fma(zv, __ldcg(qk + t), v3[1]);
                 v3[2] = fma(zv, kz, v3[2]);
-            });
+            };
+            if (!cm_stream) {
+                local_rows<NP>(a.row_ptr, a.col_local, a.val, pn, ce0, ce1, emit);
+            } else {
+                // the same elements in the same order as the issue side: panel cm_seq is in
+                // slot cm_seq % CS; once read, the slot takes the warp's panel CS further on
+                for (int64_t e = ce0 + warp; e < ce1; e += NW) {
+                    const int k = (int)(cm_seq % CS);
+                    const int32_t b0 = a.row_ptr[e];
+                    const int nb = a.row_ptr[e + 1] - b0;
+                    const int clv = lane < nb ? __ldg(a.col_local + b0 + lane) : 0;
+                    if (!cmfail && !__all_sync(0xffffffffu, mbar_wait(&cmbars[warp][k], (cm_seq / CS) & 1))) {
+                        cmfail = true;
+                        if (lane == 0) atomicExch(a.err, 1);
+                    }
+                    double kz = 0.0;
+                    if (!cmfail) {                // else the solve stops at the next barrier
+                        ++cm_done;
+                        const double* V = reinterpret_cast<const double*>(smem + ((size_t)warp * CS + k) * a.cm_slot_bytes) +
+                                          (((int64_t)b0 * NP * NP) & 1);
+                        kz = panel_rows<NP>(V, clv, nb, pn, lane);
+                        __syncwarp();             // every lane is done with the slot
+                        if (cm_ch < ch1) {
+                            if (lane == 0) cm_issue(k);
+                            ++cm_issued;
+                            cm_e += NW;
+                            cm_norm();
+                        }
+                    }
+                    ++cm_seq;
+                    if (lane < NP) emit(e, lane, kz);
+                }
+            }
         }
         if (apply) break;                         // status kOK: z = B_ad^{-1} b is complete
         // beta, p.q and alpha by thread 0: code 0 go on, 2 non-finite, 4 breakdown
         if (timing) {
             __syncthreads();
             if (threadIdx.x == 0) cyc_cm += clock64() - t_mark;
+        }
+        if (cm_stream) {
+            // every warp is done with its panels: the next P phase's first rows fly
+            // during the grid reduction (their slots overlap the CM ring)
+            __syncthreads();
+            if (has_rows && !wfail && !cmfail) {
+                issue_first();
+                p_armed = true;
+            }
         }
         if (pipe) {                               // the own rows are updated: a plain barrier
             ok = grid_barrier(a.gs, G, gen, a.err, wl);
@@ -577,6 +682,8 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         for (uint32_t c = n_done; c < n_issued; ++c)
             if (!mbar_wait(&wbars[warp][c % S], (c / S) & 1)) break;
     }
+    for (uint32_t c = cm_done; c < cm_issued; ++c)      // and for its K_h panels
+        if (!mbar_wait(&cmbars[warp][c % CS], (c / CS) & 1)) break;
     if (timing && threadIdx.x == 0) {
         a.cta_cycles[cta] = cyc_p;
         a.cta_cycles[G + cta] = cyc_cm;
@@ -598,7 +705,7 @@ template <int DT, int NP>
 __global__ void __launch_bounds__(kPersistThreads, 1)
 pcg_persistent_kernel(const __grid_constant__ PersistArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    pcg_solve_cta<DT, NP>(a, blockIdx.x, gridDim.x, smem);
+    pcg_solve_cta<DT, NP, true>(a, blockIdx.x, gridDim.x, smem);
 }
 
 // Independent solves of several simulations in one launch: CTA b works on
@@ -618,7 +725,7 @@ pcg_batched_kernel(const PersistArgs* __restrict__ args, const int2* __restrict_
         for (int k = threadIdx.x; k < (int)(sizeof(PersistArgs) / 8); k += blockDim.x) dst[k] = src[k];
     }
     __syncthreads();
-    pcg_solve_cta<DT, NP>(sa, m.y, (unsigned)sa.grid, smem);
+    pcg_solve_cta<DT, NP, false>(sa, m.y, (unsigned)sa.grid, smem);
 }
 
 template <int DT>

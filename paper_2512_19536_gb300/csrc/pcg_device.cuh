@@ -279,4 +279,30 @@ __device__ __forceinline__ void local_rows(const int32_t* __restrict__ row_ptr,
     }
 }
 
+// Rows of one element of y = K x from its block-row panel V in shared memory (nb
+// column-major NP x NP blocks, as in local_rows), with x read from the CTA-local staging
+// xn.  Block s's local element id is in lane s of clv (nb <= 32); lane (i, g) sums
+// columns g, g + G, ... and lanes i < NP return row i's total.
+template <int NP>
+__device__ __forceinline__ double panel_rows(const double* V, int clv, int nb, const double* xn, int lane) {
+    constexpr int G = 32 / NP;
+    const int g = (lane < G * NP) ? lane / NP : G;   // the spare lanes are not summed
+    const int i = lane - (lane / NP) * NP;
+    const int ncol = nb * NP;
+    double a0 = 0.0, a1 = 0.0;
+    for (int cb = 0; cb < ncol; cb += 2 * G) {        // the same trip count in every lane
+        const int c0 = cb + g, c1 = cb + G + g;
+        const int s0 = min(c0, ncol - 1) / NP, s1 = min(c1, ncol - 1) / NP;
+        const int k0 = __shfl_sync(0xffffffffu, clv, s0);
+        const int k1 = __shfl_sync(0xffffffffu, clv, s1);
+        if (c0 < ncol) a0 = fma(V[c0 * NP + i], xn[k0 * NP + (c0 - s0 * NP)], a0);
+        if (c1 < ncol) a1 = fma(V[c1 * NP + i], xn[k1 * NP + (c1 - s1 * NP)], a1);
+    }
+    const double acc = a0 + a1;
+    double tot = acc;
+#pragma unroll
+    for (int k = 1; k < G; ++k) tot += __shfl_down_sync(0xffffffffu, acc, k * NP);
+    return tot;
+}
+
 }  // namespace polydg
