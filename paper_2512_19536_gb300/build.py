@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpolydg.so")
-SOURCES = ["host_setup.cpp", "eig.cpp", "kernels_linalg.cu", "kernels_pcg.cu", "kernels_group.cu", "kernels_ionic.cu", "kernels_guess.cu", "shared_local.cu", "shared_local_tc.cu", "chol_blocked.cu", "api.cu",
+SOURCES = ["host_setup.cpp", "eig.cpp", "kernels_linalg.cu", "kernels_pcg.cu", "kernels_group.cu", "kernels_ionic.cu", "kernels_guess.cu", "shared_local.cu", "shared_local_tc.cu", "chol_blocked.cu", "guess_tc.cu", "api.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1226,7 +1226,7 @@ static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
         if (sm->guess) {
             const GuessFeat f = guess_features(c, sm->guess);
             CU(launch_guess_propose(np, f, sm->guess->w16, sm->U, sm->Uprev, sm->Uprev2, sm->xg, H.nc,
-                                    sm->d_ss, s));
+                                    sm->d_ss, sm->guess->d_err, sm->guess->n_sm, s));
             xg = sm->xg;
         }
         CU(launch_guess_subspace(np, c->K, w.b, sm->U, xg, sm->ring, sm->kuring, sm->subW, sm->gram, n,
@@ -1235,7 +1235,7 @@ static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
     } else if (sm->guess) {     // from k = 2 on: learned proposal, kept if its residual is smaller
         const GuessFeat f = guess_features(c, sm->guess);
         CU(launch_guess_propose(np, f, sm->guess->w16, sm->U, sm->Uprev, sm->Uprev2, sm->xg, H.nc,
-                                sm->d_ss, s));
+                                sm->d_ss, sm->guess->d_err, sm->guess->n_sm, s));
         CU(launch_guess_select(np, c->K, w.b, sm->xg, sm->U, w.partials, sm->d_ss, sm->guess_policy, s));
         CU(launch_select_copy(sm->U, sm->xg, w.x[0], n, sm->d_ss, s));
     } else {
@@ -1830,8 +1830,10 @@ int guess_create(int n_p, const double* params, const double* scales, guess_mode
     int st;
     if ((st = upload(&g->w32, w)) || (st = dalloc(&g->m, g->P)) || (st = dalloc(&g->v, g->P)) ||
         (st = dalloc(&g->w16, g->P)) || (st = dalloc(&g->part, (size_t)g->grid_max * g->P)) ||
-        (st = dalloc(&g->lpart, g->grid_max)) || (st = dalloc(&g->loss, 1)))
+        (st = dalloc(&g->lpart, g->grid_max)) || (st = dalloc(&g->loss, 1)) || (st = dalloc(&g->d_err, 1)))
         return fail(st);
+    g->n_sm = std::max(1, n_sm);
+    CU(cudaMemset(g->d_err, 0, sizeof(int)));
     CU(cudaMemset(g->m, 0, g->P * sizeof(float)));
     CU(cudaMemset(g->v, 0, g->P * sizeof(float)));
     CU(guess_prepare(n_p));
@@ -1876,8 +1878,16 @@ int guess_propose(guess_model* g, polydg_ctx* c, const double* uk, const double*
     CU(launch_permute(uk1, nullptr, w.r[1], c->d_to_caller, c->H.nc, np, 1, nullptr, s));
     CU(launch_permute(uk2, nullptr, w.b, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
     CU(launch_guess_propose(np, guess_features(c, g), g->w16, w.r[0], w.r[1], w.b, w.z, c->H.nc,
-                            nullptr, s));
+                            nullptr, g->d_err, g->n_sm, s));
     CU(launch_permute(w.z, nullptr, x_dev, c->d_to_caller, c->H.nc, np, 0, nullptr, s));
+    int h_err = 0;
+    CU(cudaMemcpyAsync(&h_err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (h_err) {
+        CU(cudaMemset(g->d_err, 0, sizeof(int)));
+        set_error("guess_propose: a device-side wait timed out");
+        return POLYDG_ECUDA;
+    }
     return POLYDG_OK;
 }
 
@@ -1934,7 +1944,7 @@ int sim_set_guess(sim_ctx* sm, guess_model* g, int policy) {
 
 void guess_destroy(guess_model* g) {
     if (!g) return;
-    dfree(g->w32); dfree(g->m); dfree(g->v); dfree(g->w16); dfree(g->part); dfree(g->lpart);
+    dfree(g->w32); dfree(g->m); dfree(g->v); dfree(g->w16); dfree(g->d_err); dfree(g->part); dfree(g->lpart);
     dfree(g->loss); dfree(g->samples);
     delete g;
 }

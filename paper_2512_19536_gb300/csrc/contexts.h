@@ -167,6 +167,8 @@ struct guess_model {
     double scales[5] = {-67.0, 50.0, 1.0, 1.0, 0.05};   // u_rest, s_u, s_d, h_ref, dt_ref
     float *w32 = nullptr, *m = nullptr, *v = nullptr, *part = nullptr;
     __half* w16 = nullptr;
+    int* d_err = nullptr;               // raised by the inference kernel if a device wait ran out
+    int n_sm = 1;
     double *lpart = nullptr, *loss = nullptr;
     int64_t* samples = nullptr;
     int64_t sample_cap = 0;

@@ -261,12 +261,14 @@ struct GuessFeat {
     double u_rest, s_u, s_d, h_ref, dt_ref, dt;
 };
 int guess_param_count(int np);
-size_t guess_propose_smem(int np);
 size_t guess_train_smem(int np);
 cudaError_t guess_prepare(int np);
+// The network's proposal x0 = U^k + s_d o for every element (guess_tc.cu, tcgen05);
+// *err is raised if a device-side wait ran out.
 cudaError_t launch_guess_propose(int np, const GuessFeat& f, const __half* w16, const double* Uk,
                                  const double* Uk1, const double* Uk2, double* xg, int64_t nc,
-                                 const SimScalars* ss, cudaStream_t s);
+                                 const SimScalars* ss, int* err, int n_sm, cudaStream_t s);
+cudaError_t guess_propose_tc_prepare(int np);
 cudaError_t launch_guess_select(int np, const DeviceMatrix& K, const double* b, const double* xg,
                                 const double* uk, double* partials, SimScalars* ss, int policy,
                                 cudaStream_t s);

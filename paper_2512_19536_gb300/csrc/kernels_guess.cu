@@ -6,7 +6,7 @@
 // proposal is x0 = U^k + s_d o, kept only if |b - K x0|_2 < |b - K U^k|_2.  Training
 // minimises the mean squared error to (U^{k+1} - U^k) / s_d with Adam.
 //
-// Inference: fp16 weights staged in shared memory, fp32 activations and accumulation.
+// Inference: guess_tc.cu (tensor cores, FP16 operands, FP32 accumulation).
 // Training: fp32 weights (master copy), activations and gradients; per-CTA partial
 // gradients summed in CTA order (deterministic), then one Adam update per parameter.
 #include <algorithm>
@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "device.cuh"
+#include "guess_features.cuh"
 #include "kernels.h"
 
 namespace polydg {
@@ -23,8 +24,6 @@ constexpr int kGT = 32;                   // elements (samples) per tile
 constexpr int kGThreads = 256;
 constexpr int kH = kGuessHidden;          // 128
 constexpr int kHP = kH + 1;               // padded row stride of transposed weights
-
-__host__ __device__ constexpr int guess_inputs(int np) { return 9 * np + 3; }
 
 // Offsets of the parameter groups in the flat (canonical) layout.
 struct ParamOffsets {
@@ -78,47 +77,6 @@ __device__ __forceinline__ void stage_weights(const S* __restrict__ src, int np,
     for (int q = threadIdx.x; q < np; q += blockDim.x) b3[q] = (float)src[o.b3 + q];
 }
 
-// Features of element e into x[0 .. 9 NP + 3) (fp32), by one warp: lane l handles
-// component l of the own vector [a | d1 | d2] and its mean and max over the face
-// neighbours (the blocks of row e of K_h after the diagonal one).  off(c) is the
-// position of cell c's first coefficient in the U arrays.
-template <int NP, typename Off>
-__device__ __forceinline__ void element_features(const GuessFeat& f, const double* __restrict__ Uk,
-                                                 const double* __restrict__ Uk1,
-                                                 const double* __restrict__ Uk2, int64_t e, float* x,
-                                                 Off&& off) {
-    const int lane = threadIdx.x & 31;
-    auto own = [&](int64_t cell, int l) {
-        const int grp = l / NP, j = l - grp * NP;
-        const int64_t o = off(cell) + j;
-        if (grp == 0) return (Uk[o] - (j == 0 ? f.u_rest : 0.0)) / f.s_u;
-        if (grp == 1) return (Uk[o] - Uk1[o]) / f.s_d;
-        return (Uk1[o] - Uk2[o]) / f.s_d;
-    };
-    const int32_t b0 = f.row_ptr[e], b1 = f.row_ptr[e + 1];
-    const int cnt = b1 - b0 - 1;
-    for (int l = lane; l < 3 * NP; l += 32) {
-        x[l] = (float)own(e, l);
-        double sum = 0.0, mx = 0.0;
-        for (int32_t b = b0 + 1; b < b1; ++b) {
-            const double v = own(f.col[b], l);
-            sum += v;
-            mx = (b == b0 + 1) ? v : fmax(mx, v);
-        }
-        x[3 * NP + l] = cnt > 0 ? (float)(sum / cnt) : 0.f;
-        x[6 * NP + l] = cnt > 0 ? (float)mx : 0.f;
-    }
-    if (lane == 0) {
-        x[9 * NP] = (float)(f.diam[e] / f.h_ref);
-        x[9 * NP + 1] = (float)(f.dt / f.dt_ref);
-        x[9 * NP + 2] = (float)cnt / 10.f;
-    }
-}
-
-__device__ __forceinline__ void zero_row(float* x, int F) {
-    for (int l = threadIdx.x & 31; l < F; l += 32) x[l] = 0.f;
-}
-
 // Dense layer out[s][j] = act(b[j] + sum_i Wt[i * kHP + j] in[s][i]) for the tile's
 // kGT samples: thread (j, half) computes 16 samples of hidden unit j.
 template <typename W, bool RELU>
@@ -145,50 +103,6 @@ __device__ __forceinline__ void output_layer(const W* w3t, const float* b3, cons
         float acc = b3[c];
         for (int i = 0; i < kH; ++i) acc = fmaf((float)w3t[i * NP + c], h2[s * kH + i], acc);
         o[q] = acc;
-    }
-}
-
-// ------------------------------------------------------------------ inference
-template <int NP>
-__global__ void __launch_bounds__(kGThreads)
-guess_propose_kernel(GuessFeat f, const __half* __restrict__ w16, const double* __restrict__ Uk,
-                     const double* __restrict__ Uk1, const double* __restrict__ Uk2,
-                     double* __restrict__ xg, int64_t nc, const SimScalars* ss) {
-    if (ss && (ss->failed || ss->k < 2)) return;
-    constexpr int F = guess_inputs(NP);
-    extern __shared__ __align__(16) unsigned char gsm[];
-    __half* w1t = reinterpret_cast<__half*>(gsm);
-    __half* w2t = w1t + F * kHP;
-    __half* w3t = w2t + kH * kHP;
-    float* b1 = reinterpret_cast<float*>(gsm + guess_weights_bytes16(NP));
-    float* b2 = b1 + kH;
-    float* b3 = b2 + kH;
-    float* xs = b3 + 16;
-    float* h1 = xs + kGT * F;
-    float* h2 = h1 + kGT * kH;
-    float* o = h2 + kGT * kH;
-    __shared__ int64_t elems[kGT];
-    stage_weights(w16, NP, w1t, w2t, w3t, b1, b2, b3);
-    for (int64_t t0 = (int64_t)blockIdx.x * kGT; t0 < nc; t0 += (int64_t)gridDim.x * kGT) {
-        const int n = (int)min((int64_t)kGT, nc - t0);
-        if (threadIdx.x < kGT) elems[threadIdx.x] = t0 + threadIdx.x;
-        __syncthreads();
-        for (int sm = threadIdx.x >> 5; sm < kGT; sm += blockDim.x >> 5) {
-            if (sm < n) element_features<NP>(f, Uk, Uk1, Uk2, elems[sm], xs + sm * F, [](int64_t e) { return e * NP; });
-            else zero_row(xs + sm * F, F);
-        }
-        __syncthreads();
-        hidden_layer<__half, true>(w1t, b1, xs, F, h1);
-        __syncthreads();
-        hidden_layer<__half, true>(w2t, b2, h1, kH, h2);
-        __syncthreads();
-        output_layer<__half, NP>(w3t, b3, h2, o);
-        __syncthreads();
-        for (int q = threadIdx.x; q < n * NP; q += blockDim.x) {
-            const int64_t t = t0 * NP + q;
-            xg[t] = Uk[t] + f.s_d * (double)o[q];
-        }
-        __syncthreads();
     }
 }
 
@@ -786,10 +700,6 @@ __global__ void to_half_kernel(const float* __restrict__ w32, __half* __restrict
 }
 
 // ------------------------------------------------------------------ launchers
-size_t guess_propose_smem(int np) {
-    const int F = guess_inputs(np);
-    return guess_weights_bytes16(np) + (size_t)(2 * kH + 16 + kGT * F + 2 * kGT * kH + kGT * np) * sizeof(float);
-}
 
 size_t guess_train_smem(int np) {
     const int F = guess_inputs(np);
@@ -821,27 +731,13 @@ size_t guess_train_smem(int np) {
 // before any launch, so that launches can be recorded into CUDA graphs).
 cudaError_t guess_prepare(int np) {
     GUESS_NP_SWITCH(np, {
-        cudaError_t e = cudaFuncSetAttribute(guess_propose_kernel<NP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)guess_propose_smem(np));
+        cudaError_t e = guess_propose_tc_prepare(np);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(guess_train_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)guess_train_smem(np));
         return e;
     })
     return cudaSuccess;
-}
-
-cudaError_t launch_guess_propose(int np, const GuessFeat& f, const __half* w16, const double* Uk,
-                                 const double* Uk1, const double* Uk2, double* xg, int64_t nc,
-                                 const SimScalars* ss, cudaStream_t s) {
-    const size_t smem = guess_propose_smem(np);
-    const unsigned grid = (unsigned)std::min<int64_t>((nc + kGT - 1) / kGT, 4 * 152);
-    if (grid == 0) return cudaSuccess;
-    GUESS_NP_SWITCH(np, {
-        guess_propose_kernel<NP><<<grid, kGThreads, smem, s>>>(f, w16, Uk, Uk1, Uk2, xg, nc, ss);
-    })
-    return cudaGetLastError();
 }
 
 cudaError_t launch_guess_select(int np, const DeviceMatrix& K, const double* b, const double* xg,

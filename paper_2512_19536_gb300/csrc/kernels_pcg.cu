@@ -197,26 +197,17 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
     // CM phase: this warp's elements (chunk by chunk: ce0 + warp, + NW, ...) stream their
     // K_h block-row panels through CS slots of cm_slot_bytes in [0, y0_off)
     const int CS = CMS ? a.cm_stages : 1;     // (1: a divisor for the dead code of CMS = false)
-    uint32_t cm_seq = 0, cm_done = 0, cm_issued = 0;   // panels consumed / seen complete / issued
+    uint32_t cm_base = 0;             // panels of the earlier CM phases (all consumed)
     bool cmfail = false;
-    int cm_ch = ch1;                  // issue side: chunk and element of the next panel
-    int64_t cm_e = 0;
-    auto cm_norm = [&]() {
-        while (cm_ch < ch1 && cm_e >= a.chunk_elem[cm_ch + 1]) {
-            ++cm_ch;
-            if (cm_ch < ch1) cm_e = a.chunk_elem[cm_ch] + warp;
-        }
-    };
-    const uint64_t cm_pol = evict_first_policy();
-    // lane 0: element cm_e's panel into slot k (from the 16-byte boundary at or below it;
+    // lane 0: element e's panel into slot k (from the 16-byte boundary at or below it;
     // the values array carries two doubles of slack past its end)
-    auto cm_issue = [&](int k) {
-        const int64_t b0 = a.row_ptr[cm_e], b1 = a.row_ptr[cm_e + 1];
+    auto cm_issue = [&](int k, int64_t e) {
+        const int64_t b0 = a.row_ptr[e], b1 = a.row_ptr[e + 1];
         const uintptr_t src = reinterpret_cast<uintptr_t>(a.val + b0 * NP * NP);
         const uintptr_t s16 = src & ~(uintptr_t)15;
         const uint32_t bytes = (uint32_t)(((uintptr_t)(b1 - b0) * NP * NP * 8 + (src - s16) + 15) & ~(uintptr_t)15);
         bulk_load(smem + ((size_t)warp * CS + k) * a.cm_slot_bytes, reinterpret_cast<const void*>(s16), bytes,
-                  &cmbars[warp][k], cm_pol);
+                  &cmbars[warp][k], evict_first_policy());
     };
     if (CMS && CS > 0 && lane == 0)
         for (int k = 0; k < CS; ++k) mbar_init(&cmbars[warp][k]);
@@ -522,6 +513,16 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         // chunk by chunk of the CTA's elements
         double v3[3] = {0.0, 0.0, 0.0};           // r.z, z.q_k, z.w
         const bool cm_stream = CMS && CS > 0 && !apply;
+        // this phase's panels: consumed, seen complete, issued (panel j: slot (cm_base + j) % CS)
+        uint32_t cm_seq = 0, cm_done = 0, cm_issued = 0;
+        int cm_ch = ch1;                  // issue side: chunk and element of the next panel
+        int64_t cm_e = 0;
+        auto cm_norm = [&]() {
+            while (cm_ch < ch1 && cm_e >= a.chunk_elem[cm_ch + 1]) {
+                ++cm_ch;
+                if (cm_ch < ch1) cm_e = a.chunk_elem[cm_ch] + warp;
+            }
+        };
         if (cm_stream) {
             // the ring's region ([0, y0_off): P slots and staging, r0s) is free once every
             // thread is past the coarse phase; the first CS panels fly during the z staging
@@ -530,8 +531,8 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
             cm_ch = ch0;
             cm_e = ch0 < ch1 ? a.chunk_elem[ch0] + warp : 0;
             cm_norm();
-            for (int m = 0; m < CS && cm_ch < ch1 && !cmfail; ++m) {
-                if (lane == 0) cm_issue((int)(cm_issued % CS));
+            for (int m = 0; m < CS && cm_ch < ch1; ++m) {
+                if (lane == 0) cm_issue((int)((cm_base + cm_issued) % CS), cm_e);
                 ++cm_issued;
                 cm_e += NW;
                 cm_norm();
@@ -597,13 +598,18 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 // the same elements in the same order as the issue side: panel cm_seq is in
                 // slot cm_seq % CS; once read, the slot takes the warp's panel CS further on
                 for (int64_t e = ce0 + warp; e < ce1; e += NW) {
-                    const int k = (int)(cm_seq % CS);
+                    const uint32_t g = cm_base + cm_seq;
+                    const int k = (int)(g % CS);
                     const int32_t b0 = a.row_ptr[e];
                     const int nb = a.row_ptr[e + 1] - b0;
                     const int clv = lane < nb ? __ldg(a.col_local + b0 + lane) : 0;
-                    if (!cmfail && !__all_sync(0xffffffffu, mbar_wait(&cmbars[warp][k], (cm_seq / CS) & 1))) {
+                    if (!cmfail && !__all_sync(0xffffffffu, mbar_wait(&cmbars[warp][k], (g / CS) & 1))) {
                         cmfail = true;
                         if (lane == 0) atomicExch(a.err, 1);
+                        // bounded wait for the panels still in flight, before anything else
+                        // may reuse their slots
+                        for (uint32_t c = cm_done; c < cm_issued; ++c)
+                            if (!mbar_wait(&cmbars[warp][(cm_base + c) % CS], ((cm_base + c) / CS) & 1)) break;
                     }
                     double kz = 0.0;
                     if (!cmfail) {                // else the solve stops at the next barrier
@@ -613,7 +619,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                         kz = panel_rows<NP>(V, clv, nb, pn, lane);
                         __syncwarp();             // every lane is done with the slot
                         if (cm_ch < ch1) {
-                            if (lane == 0) cm_issue(k);
+                            if (lane == 0) cm_issue(k, cm_e);
                             ++cm_issued;
                             cm_e += NW;
                             cm_norm();
@@ -624,6 +630,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 }
             }
         }
+        cm_base += cm_seq;
         if (apply) break;                         // status kOK: z = B_ad^{-1} b is complete
         // beta, p.q and alpha by thread 0: code 0 go on, 2 non-finite, 4 breakdown
         if (timing) {
@@ -682,8 +689,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         for (uint32_t c = n_done; c < n_issued; ++c)
             if (!mbar_wait(&wbars[warp][c % S], (c / S) & 1)) break;
     }
-    for (uint32_t c = cm_done; c < cm_issued; ++c)      // and for its K_h panels
-        if (!mbar_wait(&cmbars[warp][c % CS], (c / CS) & 1)) break;
+
     if (timing && threadIdx.x == 0) {
         a.cta_cycles[cta] = cyc_p;
         a.cta_cycles[G + cta] = cyc_cm;

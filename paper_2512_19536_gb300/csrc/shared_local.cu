@@ -107,6 +107,31 @@ shared_local_apply_kernel(const SharedBlock* __restrict__ blocks, const T* __res
     }
 }
 
+// Caller order <-> internal order for the R vectors of one application in one launch
+// (grid.y = vector): to_internal dst[k][t] = src[k][c n_p + j], else the reverse, with
+// element e = t / n_p of internal order at caller cell c = to_caller[e].
+struct PermPtrs {
+    const double* src[kMaxTcRhs];
+    double* dst[kMaxTcRhs];
+};
+
+__global__ void permute_many_kernel(PermPtrs p, const int64_t* __restrict__ to_caller, int64_t nc, int np,
+                                    int to_internal) {
+    const int k = blockIdx.y;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nc * np) return;
+    const int64_t e = t / np, j = t - e * np, c = to_caller[e];
+    if (to_internal) p.dst[k][t] = p.src[k][c * np + j];
+    else p.dst[k][c * np + j] = p.src[k][t];
+}
+
+static cudaError_t launch_permute_many(const PermPtrs& p, int nvec, const int64_t* to_caller, int64_t nc,
+                                       int np, int to_internal, cudaStream_t s) {
+    const dim3 grid((unsigned)((nc * np + 255) / 256), (unsigned)nvec);
+    permute_many_kernel<<<grid, 256, 0, s>>>(p, to_caller, nc, np, to_internal);
+    return cudaGetLastError();
+}
+
 }  // namespace polydg
 
 namespace polydg {
@@ -349,16 +374,21 @@ int shared_local_apply(shared_local* sl, int nrhs, const double* const* r_dev, d
     const int64_t n = c->H.nc * np;
     cudaStream_t s = (cudaStream_t)stream;
     RhsPtrs p = {};
+    PermPtrs pin = {}, pout = {};
     for (int k = 0; k < nrhs; ++k) {
         if (!(sigmas[k] > 0)) { set_error("shared_local_apply: conductivities must be > 0"); return POLYDG_EINVAL; }
         for (int t = 0; t < 2; ++t)
             if (!sl->tmp[2 * k + t])
                 if (int st = dalloc(&sl->tmp[2 * k + t], n)) return st;
-        CU(launch_permute(r_dev[k], nullptr, sl->tmp[2 * k], c->d_to_caller, c->H.nc, np, 1, nullptr, s));
+        pin.src[k] = r_dev[k];
+        pin.dst[k] = sl->tmp[2 * k];
+        pout.src[k] = sl->tmp[2 * k + 1];
+        pout.dst[k] = z_dev[k];
         p.r[k] = sl->tmp[2 * k];
         p.z[k] = sl->tmp[2 * k + 1];
         p.c[k] = 0.5 * c->H.dt * sigmas[k];
     }
+    CU(launch_permute_many(pin, nrhs, c->d_to_caller, c->H.nc, np, 1, s));
     const double chi = c->H.chi_cm;
     if (sl->tiles) {                         // tensor cores: both passes as tcgen05 BF16 GEMMs
         TcRhs tp = {};
@@ -374,8 +404,7 @@ int shared_local_apply(shared_local* sl, int nrhs, const double* const* r_dev, d
             set_error("shared_local_apply: a device-side wait timed out");
             return POLYDG_ECUDA;
         }
-        for (int k = 0; k < nrhs; ++k)
-            CU(launch_permute(sl->tmp[2 * k + 1], nullptr, z_dev[k], c->d_to_caller, c->H.nc, np, 0, nullptr, s));
+        CU(launch_permute_many(pout, nrhs, c->d_to_caller, c->H.nc, np, 0, s));
         return POLYDG_OK;
     }
     const size_t smem = 2 * (size_t)kMaxRhs * sl->max_ld * sizeof(float);
@@ -402,8 +431,7 @@ int shared_local_apply(shared_local* sl, int nrhs, const double* const* r_dev, d
     }
 #undef LAUNCH
     CU(cudaGetLastError());
-    for (int k = 0; k < nrhs; ++k)
-        CU(launch_permute(sl->tmp[2 * k + 1], nullptr, z_dev[k], c->d_to_caller, c->H.nc, np, 0, nullptr, s));
+    CU(launch_permute_many(pout, nrhs, c->d_to_caller, c->H.nc, np, 0, s));
     return POLYDG_OK;
 }
 
