@@ -1225,8 +1225,8 @@ static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
         const double* xg = nullptr;
         if (sm->guess) {
             const GuessFeat f = guess_features(c, sm->guess);
-            CU(launch_guess_propose(np, f, sm->guess->w16, sm->U, sm->Uprev, sm->Uprev2, sm->xg, H.nc,
-                                    sm->d_ss, sm->guess->d_err, sm->guess->n_sm, s));
+            CU(launch_guess_propose(np, f, sm->guess->img, sm->U, sm->Uprev, sm->Uprev2, sm->xg, H.nc,
+                                    sm->d_ss, sm->gxt, sm->guess->d_err, sm->guess->n_sm, s));
             xg = sm->xg;
         }
         CU(launch_guess_subspace(np, c->K, w.b, sm->U, xg, sm->ring, sm->kuring, sm->subW, sm->gram, n,
@@ -1234,8 +1234,8 @@ static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
         CU(launch_subspace_copy(sm->U, xg, sm->ring, sm->kuring, sm->subW, w.x[0], n, sm->d_ss, s));
     } else if (sm->guess) {     // from k = 2 on: learned proposal, kept if its residual is smaller
         const GuessFeat f = guess_features(c, sm->guess);
-        CU(launch_guess_propose(np, f, sm->guess->w16, sm->U, sm->Uprev, sm->Uprev2, sm->xg, H.nc,
-                                sm->d_ss, sm->guess->d_err, sm->guess->n_sm, s));
+        CU(launch_guess_propose(np, f, sm->guess->img, sm->U, sm->Uprev, sm->Uprev2, sm->xg, H.nc,
+                                sm->d_ss, sm->gxt, sm->guess->d_err, sm->guess->n_sm, s));
         CU(launch_guess_select(np, c->K, w.b, sm->xg, sm->U, w.partials, sm->d_ss, sm->guess_policy, s));
         CU(launch_select_copy(sm->U, sm->xg, w.x[0], n, sm->d_ss, s));
     } else {
@@ -1830,7 +1830,8 @@ int guess_create(int n_p, const double* params, const double* scales, guess_mode
     int st;
     if ((st = upload(&g->w32, w)) || (st = dalloc(&g->m, g->P)) || (st = dalloc(&g->v, g->P)) ||
         (st = dalloc(&g->w16, g->P)) || (st = dalloc(&g->part, (size_t)g->grid_max * g->P)) ||
-        (st = dalloc(&g->lpart, g->grid_max)) || (st = dalloc(&g->loss, 1)) || (st = dalloc(&g->d_err, 1)))
+        (st = dalloc(&g->lpart, g->grid_max)) || (st = dalloc(&g->loss, 1)) || (st = dalloc(&g->d_err, 1)) ||
+        (st = dalloc(&g->img, guess_tc_image_bytes(n_p))))
         return fail(st);
     g->n_sm = std::max(1, n_sm);
     CU(cudaMemset(g->d_err, 0, sizeof(int)));
@@ -1838,6 +1839,7 @@ int guess_create(int n_p, const double* params, const double* scales, guess_mode
     CU(cudaMemset(g->v, 0, g->P * sizeof(float)));
     CU(guess_prepare(n_p));
     CU(launch_to_half(g->w32, g->w16, g->P, 0));
+    CU(launch_guess_tc_image(n_p, g->w16, g->img, 0));
     CU(cudaDeviceSynchronize());
     *out = g;
     return POLYDG_OK;
@@ -1877,8 +1879,16 @@ int guess_propose(guess_model* g, polydg_ctx* c, const double* uk, const double*
     CU(launch_permute(uk, nullptr, w.r[0], c->d_to_caller, c->H.nc, np, 1, nullptr, s));
     CU(launch_permute(uk1, nullptr, w.r[1], c->d_to_caller, c->H.nc, np, 1, nullptr, s));
     CU(launch_permute(uk2, nullptr, w.b, c->d_to_caller, c->H.nc, np, 1, nullptr, s));
-    CU(launch_guess_propose(np, guess_features(c, g), g->w16, w.r[0], w.r[1], w.b, w.z, c->H.nc,
-                            nullptr, g->d_err, g->n_sm, s));
+    const int64_t tiles = (c->H.nc + 127) / 128;
+    if (tiles > g->xt_tiles) {
+        CU(cudaStreamSynchronize(s));     // the previous call's tiles are no longer read
+        dfree(g->xt);
+        g->xt_tiles = 0;
+        if (int st = dalloc(&g->xt, (size_t)tiles * guess_tc_tile_bytes(np))) return st;
+        g->xt_tiles = tiles;
+    }
+    CU(launch_guess_propose(np, guess_features(c, g), g->img, w.r[0], w.r[1], w.b, w.z, c->H.nc,
+                            nullptr, g->xt, g->d_err, g->n_sm, s));
     CU(launch_permute(w.z, nullptr, x_dev, c->d_to_caller, c->H.nc, np, 0, nullptr, s));
     int h_err = 0;
     CU(cudaMemcpyAsync(&h_err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1922,6 +1932,7 @@ int guess_train_step(guess_model* g, polydg_ctx* c, const double* traj_dev, int6
     const float c1 = (float)(1.0 - std::pow(b1, (double)g->t)), c2 = (float)(1.0 - std::pow(b2, (double)g->t));
     CU(launch_guess_adam(g->part, grid, g->P, g->w32, g->m, g->v, g->w16, (float)lr, (float)b1, (float)b2,
                          1e-8f, c1, c2, g->lpart, 1.0 / ((double)n_samples * np), g->loss, s));
+    CU(launch_guess_tc_image(np, g->w16, g->img, s));       // the inference kernel's weight image
     double l = 0.0;
     CU(cudaMemcpyAsync(&l, g->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -1934,6 +1945,10 @@ int sim_set_guess(sim_ctx* sm, guess_model* g, int policy) {
     if (g && g->np != sm->ctx->H.n_p) { set_error("sim_set_guess: model and mesh differ in n_p"); return POLYDG_EINVAL; }
     if (policy < 0 || policy > 3) { set_error("sim_set_guess: policy must be 0, 1, 2 or 3"); return POLYDG_EINVAL; }
     if (!g && policy != 0 && policy != 3) { set_error("sim_set_guess: policies 1 and 2 need a model"); return POLYDG_EINVAL; }
+    if (g && !sm->gxt) {
+        const int64_t tiles = (sm->ctx->H.nc + 127) / 128;
+        if (int st = dalloc(&sm->gxt, (size_t)tiles * guess_tc_tile_bytes(g->np))) return st;
+    }
     if (sm->guess != g || sm->guess_policy != policy) {
         sm->guess = g;
         sm->guess_policy = policy;
@@ -1944,7 +1959,7 @@ int sim_set_guess(sim_ctx* sm, guess_model* g, int policy) {
 
 void guess_destroy(guess_model* g) {
     if (!g) return;
-    dfree(g->w32); dfree(g->m); dfree(g->v); dfree(g->w16); dfree(g->d_err); dfree(g->part); dfree(g->lpart);
+    dfree(g->w32); dfree(g->m); dfree(g->v); dfree(g->w16); dfree(g->d_err); dfree(g->img); dfree(g->xt); dfree(g->part); dfree(g->lpart);
     dfree(g->loss); dfree(g->samples);
     delete g;
 }
@@ -1966,7 +1981,7 @@ void sim_destroy(sim_ctx* sm) {
     if (!sm) return;
     for (auto e : sm->ev) cudaEventDestroy(e);
     sm->work.release();
-    dfree(sm->U); dfree(sm->Uprev); dfree(sm->Uprev2); dfree(sm->xg); dfree(sm->I); dfree(sm->F); dfree(sm->y); dfree(sm->yc); dfree(sm->d_y0);
+    dfree(sm->U); dfree(sm->Uprev); dfree(sm->Uprev2); dfree(sm->xg); dfree(sm->I); dfree(sm->F); dfree(sm->y); dfree(sm->yc); dfree(sm->gxt); dfree(sm->d_y0);
     dfree(sm->Ym);
     dfree(sm->ring); dfree(sm->kuring); dfree(sm->subW); dfree(sm->gram);
     dfree(sm->d_ss);

@@ -169,6 +169,9 @@ struct guess_model {
     __half* w16 = nullptr;
     int* d_err = nullptr;               // raised by the inference kernel if a device wait ran out
     int n_sm = 1;
+    unsigned char* img = nullptr;       // the weights as tensor-core operands (guess_tc.cu)
+    unsigned char* xt = nullptr;        // feature tiles of guess_propose calls
+    int64_t xt_tiles = 0;
     double *lpart = nullptr, *loss = nullptr;
     int64_t* samples = nullptr;
     int64_t sample_cap = 0;
@@ -193,6 +196,7 @@ struct sim_ctx {
     double* gram = nullptr;             // [kSubMaxPairs][kSubMaxCtas] Gram partial sums
     double *U = nullptr, *Uprev = nullptr, *I = nullptr, *F = nullptr, *y = nullptr;
     double* yc = nullptr;               // per node: E_Na, E_K, exp(-K_o/5), exp((25 - Na_i)/3) (nodal form)
+    unsigned char* gxt = nullptr;       // feature tiles of the learned guess (with a model)
     double* d_y0 = nullptr;
     double* Ym = nullptr;               // [5][n] modal ionic state (sim_set_ionic_form 1), or null
     SimScalars* d_ss = nullptr;

@@ -263,12 +263,17 @@ struct GuessFeat {
 int guess_param_count(int np);
 size_t guess_train_smem(int np);
 cudaError_t guess_prepare(int np);
-// The network's proposal x0 = U^k + s_d o for every element (guess_tc.cu, tcgen05);
-// *err is raised if a device-side wait ran out.
-cudaError_t launch_guess_propose(int np, const GuessFeat& f, const __half* w16, const double* Uk,
+// The network's proposal x0 = U^k + s_d o for every element (guess_tc.cu, tcgen05): the
+// features into xt (guess_tc_tile_bytes(np) per 128 elements), then the three layers with
+// the weight image img (guess_tc_image_bytes(np), from launch_guess_tc_image after every
+// change of the FP16 weights); *err is raised if a device-side wait ran out.
+cudaError_t launch_guess_propose(int np, const GuessFeat& f, const unsigned char* img, const double* Uk,
                                  const double* Uk1, const double* Uk2, double* xg, int64_t nc,
-                                 const SimScalars* ss, int* err, int n_sm, cudaStream_t s);
+                                 const SimScalars* ss, unsigned char* xt, int* err, int n_sm, cudaStream_t s);
 cudaError_t guess_propose_tc_prepare(int np);
+size_t guess_tc_image_bytes(int np);
+size_t guess_tc_tile_bytes(int np);
+cudaError_t launch_guess_tc_image(int np, const __half* w16, unsigned char* img, cudaStream_t s);
 cudaError_t launch_guess_select(int np, const DeviceMatrix& K, const double* b, const double* xg,
                                 const double* uk, double* partials, SimScalars* ss, int policy,
                                 cudaStream_t s);

@@ -37,6 +37,7 @@ namespace {
 
 constexpr int kTcThreads = 512;                // 16 warps: warp w reads TMEM lanes 32 (w % 4)..
 constexpr int kTcStages = 6;                   // ring of 16 KB A tiles
+constexpr int kTcLag = 2;                      // a stage is refilled kTcLag tiles after its MMAs
 constexpr uint32_t kTileBytes = 128 * 64 * 2;  // one 128 x 64 BF16 tile
 
 using tc::smem_desc;
@@ -142,8 +143,9 @@ shared_tc_kernel(const TcBlock* __restrict__ blocks, const unsigned char* __rest
 
     bool ok = true;
     // thread 0: the MMAs of pass `pass` (tiles pass*T .. pass*T + T - 1), refilling the ring
-    // one tile behind (the stage of tile g - 1 is free once its MMAs, committed one tile
-    // earlier, have completed), then one commit of `done` for the whole pass
+    // kTcLag tiles behind (the stage of tile g - kTcLag is free once its MMAs, committed
+    // kTcLag tiles earlier, have completed: by then they usually have, so the issue loop
+    // rarely waits on them), then one commit of `done` for the whole pass
     auto run_pass = [&](int pass) {
         for (int g = pass * T; g < (pass + 1) * T; ++g) {
             const int s = g % kTcStages;
@@ -158,8 +160,8 @@ shared_tc_kernel(const TcBlock* __restrict__ blocks, const unsigned char* __rest
                 mma_bf16(tmem + (uint32_t)(mt * NB), smem_desc(abase + kk * 256u, 128u, 1024u),
                          smem_desc(bbase + kk * 256u, 128u, bsbo), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
             mma_commit(&empty[s]);
-            if (g >= 1 && issued < 2 * T) {
-                const int gp = g - 1;
+            if (g >= kTcLag && issued < 2 * T) {
+                const int gp = g - kTcLag;
                 if (!mbar_wait(&empty[gp % kTcStages], (gp / kTcStages) & 1)) { ok = false; break; }
                 copy_tile(issued++);
             }
