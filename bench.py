@@ -483,7 +483,7 @@ def bench_voronoi(args, pd, torch, stream, rank, world, local, with_cpu, steps=N
         "clocks": clocks.summary(),
         "e2e": {"value": world * e2e_rank, "unit": "time-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": (11 if guess is not None else 10) * steps,
+        "gpu_launches": (12 if guess is not None else 10) * steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "kernel": "pcg_persistent_kernel<fp32 store, n_p=10>",
@@ -589,7 +589,7 @@ def bench_hex(args, pd, torch, stream, rank, world, local):
         "clocks": clocks.summary(),
         "e2e": {"value": world * e2e_rank, "unit": "time-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": (11 if guess is not None else 10) * steps,
+        "gpu_launches": (12 if guess is not None else 10) * steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "kernel": "pcg_persistent_kernel<fp32 store, n_p=10> (distributed coarse rows)",
@@ -775,7 +775,7 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_val, "unit": "simulation-steps/s",
                 "h2d_bytes_per_step": 17 * 8 * n_all, "d2h_bytes_per_step": 8 * n_all},
-        "gpu_launches": ((10 if guess is not None else 9) * S + 1) * steps,
+        "gpu_launches": ((11 if guess is not None else 9) * S + 1) * steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                      "kernel": "pcg_group_kernel<bf16 store, n_p=10> (whole step time)",
