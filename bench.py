@@ -13,7 +13,7 @@ update at the quadrature nodes, right-hand side, initial guess, and the persiste
 kernel.  Forms timed on the same setup:
   * mixed + learned (reported): fp32 local inverses in flexible PCG (fp64 residual, dots,
     coarse solve and matvec); initial guess = Galerkin projection onto the learned
-    proposal (weights in paper_2512_19536_gb300/guess_p3_voronoi4096.npz) and the last 16
+    proposal (weights in paper_2512_19536_gb300/guess_p3_voronoi4096.npz) and the last 24
     solution increments;
   * the increments alone (no network), and x0 = U^k, as ablations;
   * fp64 plain: fp64 local inverses in standard PCG, x0 = U^k.
@@ -166,7 +166,7 @@ def load_guess(pd):
     return pd.guess_create(int(z["n_p"]), z["params"], z["scales"])
 
 
-GUESS_POLICY = 3   # Galerkin projection onto the learned proposal and the last 16 solution increments
+GUESS_POLICY = 3   # Galerkin projection onto the learned proposal and the last 24 solution increments
 
 
 def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clocks=None,
@@ -200,7 +200,7 @@ def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clo
 
 def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None, warm=12, ionic_form="nodal"):
     """Same metric with the state crossing the host boundary every step: the last
-    solutions the step depends on (U^k .. U^{k-16}: the initial guess reads them) copied in
+    solutions the step depends on (U^k .. U^{k-24}: the initial guess reads them) copied in
     from pinned host memory and restored with sim_set_history, U^{k+1} copied back to
     pinned host memory.  The same steps as the device-timed forms: `warm` untimed, then
     `steps` timed."""
@@ -210,7 +210,7 @@ def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None, warm=12, ionic_fo
         pd.sim_set_ionic_form(sim, ionic_form)
     pd.sim_set_guess(sim, guess, GUESS_POLICY)
     n = ctx.n_dofs
-    H = 17
+    H = 25
     host_hist = torch.empty((H, n), dtype=torch.float64).pin_memory()   # row 0 = U^k
     dev_hist = torch.empty((H, n), dtype=torch.float64, device="cuda")
     dev_u = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -454,9 +454,9 @@ def bench_voronoi(args, pd, torch, stream, rank, world, local, with_cpu, steps=N
         "data": "synthetic",
         "config": {"workload": WORKLOAD,
                    "form": ("mixed + learned: fp32 local inverses, flexible PCG; initial guess = "
-                            "Galerkin projection onto the network's proposal and the last 16 "
+                            "Galerkin projection onto the network's proposal and the last 24 "
                             "solution increments") if guess is not None else
-                   "mixed: fp32 local inverses, flexible PCG, initial guess from the last 16 "
+                   "mixed: fp32 local inverses, flexible PCG, initial guess from the last 24 "
                    "solution increments (guess weights file missing)",
                    "ionic_form": form,
                    "rtol": 1e-8, "iterations_per_step": st["total_iterations"] / steps,
@@ -552,7 +552,7 @@ def bench_hex(args, pd, torch, stream, rank, world, local):
                    "form": "mixed + learned: fp32 local inverses, flexible PCG (fp64 residual, dots, "
                            "coarse solve, matvec); initial guess = Galerkin projection onto the "
                            "network's proposal (trained on 2D Voronoi P3 trajectories of the plain "
-                           "solver, seeds 0-7) and the last 16 solution increments; the gain over "
+                           "solver, seeds 0-7) and the last 24 solution increments; the gain over "
                            "fp64 plain is the fp32 inverses' and the increments' (see the "
                            "increments-only ablation: the network's direction does not help on this "
                            "mesh)",
@@ -672,11 +672,11 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
                        + inf["restrict_bytes"] + 12 * 8 * ctx.n_dofs)
         alg += g_its * per_it
     achieved = alg / (sec * 1e9)
-    # e2e: every simulation's state (the last 17 solutions the initial guess reads) through
+    # e2e: every simulation's state (the last 25 solutions the initial guess reads) through
     # pinned host memory each step, the new potential back
     sims = [x[2] for x in trip]
     n_all = sum(ctx.n_dofs for ctx, _, _ in trip)
-    H = 17
+    H = 25
     hh = [torch.zeros((H, ctx.n_dofs), dtype=torch.float64).pin_memory() for ctx, _, _ in trip]
     dh = [torch.empty((H, ctx.n_dofs), dtype=torch.float64, device="cuda") for ctx, _, _ in trip]
     du = [torch.empty(ctx.n_dofs, dtype=torch.float64, device="cuda") for ctx, _, _ in trip]
@@ -761,7 +761,7 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
                            "solve in lockstep, each subdomain's local solves one bf16 pass over Q_i^T "
                            "and one over Q_i for all 4 (flexible PCG, fp64 residual/dots/coarse/"
                            "matvec); every simulation's initial guess the Galerkin projection onto "
-                           "the network's proposal and its last 16 solution increments; one "
+                           "the network's proposal and its last 24 solution increments; one "
                            "persistent launch per step, captured step graph",
                    "cells": [w.mesh.n_cells for w in ws[::per_mesh]], "dofs": n_all,
                    "ctas_per_sim": groups, "iterations_per_step": its,
@@ -774,7 +774,7 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
                    "l2": "working set > L2 (no flush needed)", "parallelism": f"replicas x{world}"},
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_val, "unit": "simulation-steps/s",
-                "h2d_bytes_per_step": 17 * 8 * n_all, "d2h_bytes_per_step": 8 * n_all},
+                "h2d_bytes_per_step": 25 * 8 * n_all, "d2h_bytes_per_step": 8 * n_all},
         "gpu_launches": ((11 if guess is not None else 9) * S + 1) * steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,

@@ -319,26 +319,29 @@ int sim_get_state(sim_ctx *sim, double *u_dev, double *y_dev, void *stream);
 
 /* Overwrite U^k and U^{k-1} (caller order device vectors; uprev_dev may be
  * NULL to use u_dev for both).  The history kept for the subspace guess (policy 3 of
- * sim_set_guess) restarts from these two. */
+ * sim_set_guess) restarts from these two; the nodal ionic update's carried functions of
+ * u^{k-1} (sim_get_ionic_aux) are evaluated afresh at the next step. */
 int sim_set_potential(sim_ctx *sim, const double *u_dev, const double *uprev_dev,
                       void *stream);
 
 /* Overwrite the last `count` solutions: hist_dev is a caller-order device array
  * [count][n_dofs] holding U^k, U^{k-1}, ..., U^{k-count+1}.  U^k, U^{k-1} and U^{k-2}
- * become the simulation's potentials, and the first min(count, 17, k + 1) solutions the
+ * become the simulation's potentials, and the first min(count, 25, k + 1) solutions the
  * history of the subspace guess (a caller that keeps the state on the host restores
- * all of it this way).  Enqueued on `stream`. */
+ * all of it this way); the nodal ionic update's carried functions of u^{k-1} are evaluated
+ * afresh at the next step unless sim_set_ionic_aux restores them afterwards.  Enqueued on
+ * `stream`. */
 int sim_set_history(sim_ctx *sim, const double *hist_dev, int count, void *stream);
 
 /* Restore a simulation's ionic state and step index k >= 0 (checkpoint / resume; with
- * sim_set_history for the potentials and, in the nodal form, sim_set_ionic_aux, a resumed
- * run continues bit for bit).  Nodal form:
+ * sim_set_history for the potentials and then, in the nodal form, sim_set_ionic_aux, a
+ * resumed run continues bit for bit).  Nodal form:
  * y_dev is [5][n_nodes] in sim_get_state's node order (required).  Modal form
  * (sim_set_ionic_form, chosen before this call): Y_dev is [5][n_dofs], per state the
  * caller-order DG coefficients as sim_get_ionic_coeffs returns them (required); y_dev, if
  * given, restores the states at the nodes that sim_get_state reports until the next step.
  * The index k sets the time t^k = k dt of the stimulus and the first-step extrapolation
- * (k = 0), and bounds the history sim_set_history keeps (min(count, 17, k + 1)
+ * (k = 0), and bounds the history sim_set_history keeps (min(count, 25, k + 1)
  * solutions), so call this before sim_set_history.  Clears a failed flag of an earlier
  * step.  Enqueued on `stream`.  Errors: EINVAL, ECUDA. */
 int sim_set_state(sim_ctx *sim, const double *y_dev, const double *Y_dev, int64_t k, void *stream);
@@ -347,14 +350,15 @@ int sim_set_state(sim_ctx *sim, const double *y_dev, const double *Y_dev, int64_
  * ([5][n_dofs], per state caller order).  EINVAL for the nodal form. */
 int sim_get_ionic_coeffs(sim_ctx *sim, double *Y_dev, void *stream);
 
-/* Nodal form only: the functions of each node's ionic state that the update carries from
- * one step to the next instead of evaluating them ([4][n_nodes] in sim_get_state's node
- * order: E_Na, E_K, exp(-K_o/5), exp((25 - Na_i)/3) of the Sec. 2 model; each step updates
- * them from the step's small concentration increments, and every 256th step evaluates
- * them afresh).  sim_get_ionic_aux copies them to aux_dev.  sim_set_ionic_aux, called after
- * sim_set_state, restores them, so that the resumed run continues bit for bit; without it
- * the first resumed step evaluates them from the restored state, which changes the
- * results by rounding only.  Enqueued on `stream`.  EINVAL for the modal form. */
+/* Nodal form only: the functions of each node's state that the update carries from one
+ * step to the next instead of evaluating them ([6][n_nodes] in sim_get_state's node
+ * order: E_Na, E_K, exp(-K_o/5), exp((25 - Na_i)/3) of the Sec. 2 model, the potential
+ * u^{k-1} at the node and exp(-u^{k-1}/720); each step updates them from the step's small
+ * increments, and every 256th step evaluates them afresh).  sim_get_ionic_aux copies them
+ * to aux_dev.  sim_set_ionic_aux, called after sim_set_state and sim_set_history, restores
+ * them, so that the resumed run continues bit for bit; without it the first resumed step
+ * evaluates them from the restored state and potentials, which changes the results by
+ * rounding only.  Enqueued on `stream`.  EINVAL for the modal form. */
 int sim_get_ionic_aux(sim_ctx *sim, double *aux_dev, void *stream);
 int sim_set_ionic_aux(sim_ctx *sim, const double *aux_dev, void *stream);
 
@@ -445,7 +449,7 @@ int guess_train_step(guess_model *model, polydg_ctx *ctx, const double *traj_dev
  *             U^{k-j+1} - U^{k-j}, theta the Galerkin projection V^T K V theta = V^T (b -
  *             K U^k) (the K-norm of the error is smallest; directions with negligible
  *             Schur-complement pivots dropped).  Policy 3 works without a model (the
- *             increments alone) and keeps the last 17 solutions on the device.
+ *             increments alone) and keeps the last 25 solutions on the device.
  * The FP64 stopping test decides convergence either way, so only iteration counts
  * change.  The model must outlive its use; it may be shared by several simulations. */
 int sim_set_guess(sim_ctx *sim, guess_model *model, int policy);

@@ -486,12 +486,14 @@ def sim_get_ionic_coeffs(sim: Simulation, Y, stream=None):
 
 def sim_get_ionic_aux(sim: Simulation, aux, stream=None):
     """Nodal form: the per-node functions the update carries (E_Na, E_K, exp(-K_o/5),
-    exp((25 - Na_i)/3)) into aux [4, n_nodes], in sim_get_state's node order."""
+    exp((25 - Na_i)/3), u^{k-1}, exp(-u^{k-1}/720)) into aux [6, n_nodes], in
+    sim_get_state's node order."""
     _check(load().sim_get_ionic_aux(sim.h, _dev(aux), _stream(stream)))
 
 
 def sim_set_ionic_aux(sim: Simulation, aux, stream=None):
-    """Nodal form: restore the carried functions after sim_set_state (bit-identical resume)."""
+    """Nodal form: restore the carried functions after sim_set_state and sim_set_history
+    (bit-identical resume)."""
     _check(load().sim_set_ionic_aux(sim.h, _dev(aux), _stream(stream)))
 
 
@@ -590,7 +592,7 @@ def sim_set_guess(sim: Simulation, model, policy=0):
     """policy 0: start from the proposal only if its residual is smaller; 1: always;
     2: from U^k + theta (proposal - U^k), theta minimising the residual on that line;
     3: Galerkin projection onto the proposal (if a model is given) and the last
-    sixteen solution increments (model may be None)."""
+    24 solution increments (model may be None)."""
     _check(load().sim_set_guess(sim.h, model.h if model is not None else None, int(policy)))
     sim.guess = model
 

@@ -1135,7 +1135,7 @@ int sim_create(polydg_ctx* c, asm_ctx* pc, const sim_params* prm, sim_ctx** out)
     int st;
     if ((st = sm->work.alloc(n)) || (st = dalloc(&sm->U, n)) || (st = dalloc(&sm->Uprev, n)) ||
         (st = dalloc(&sm->Uprev2, n)) || (st = dalloc(&sm->xg, n)) ||
-        (st = dalloc(&sm->I, n)) || (st = dalloc(&sm->y, 5 * nn)) || (st = dalloc(&sm->yc, 4 * nn)) || (st = dalloc(&sm->d_y0, 5)) ||
+        (st = dalloc(&sm->I, n)) || (st = dalloc(&sm->y, 5 * nn)) || (st = dalloc(&sm->yc, 6 * nn)) || (st = dalloc(&sm->d_y0, 5)) ||
         (st = dalloc(&sm->d_ss, 1)) || (st = dalloc(&sm->ring, kHistRing * n)) ||
         (st = dalloc(&sm->kuring, kHistRing * n)) || (st = dalloc(&sm->subW, 2 * n)) || (st = dalloc(&sm->gram, kSubMaxPairs * kSubMaxCtas)))
         return fail(st);
@@ -1516,7 +1516,7 @@ int sim_get_ionic_aux(sim_ctx* sm, double* aux_dev, void* stream) {
     if (!sm || !aux_dev) { set_error("sim_get_ionic_aux: null argument"); return POLYDG_EINVAL; }
     if (sm->Ym) { set_error("sim_get_ionic_aux: the modal form carries no per-node functions"); return POLYDG_EINVAL; }
     polydg_ctx* c = sm->ctx;
-    CU(launch_node_gather(sm->yc, aux_dev, c->d_node_pos, (int64_t)c->H.node_w.size(), (cudaStream_t)stream, 4));
+    CU(launch_node_gather(sm->yc, aux_dev, c->d_node_pos, (int64_t)c->H.node_w.size(), (cudaStream_t)stream, 6));
     return POLYDG_OK;
 }
 
@@ -1525,7 +1525,7 @@ int sim_set_ionic_aux(sim_ctx* sm, const double* aux_dev, void* stream) {
     if (sm->Ym) { set_error("sim_set_ionic_aux: the modal form carries no per-node functions"); return POLYDG_EINVAL; }
     polydg_ctx* c = sm->ctx;
     cudaStream_t s = (cudaStream_t)stream;
-    CU(launch_node_scatter(aux_dev, sm->yc, c->d_node_pos, (int64_t)c->H.node_w.size(), s, 4));
+    CU(launch_node_scatter(aux_dev, sm->yc, c->d_node_pos, (int64_t)c->H.node_w.size(), s, 6));
     CU(launch_ionic_aux_valid(sm->d_ss, s));
     return POLYDG_OK;
 }
@@ -1541,6 +1541,7 @@ int sim_set_potential(sim_ctx* sm, const double* u_dev, const double* uprev_dev,
                        cudaMemcpyDeviceToDevice, s));
     CU(launch_history_reset(c->H.n_p, c->K, sm->ring, sm->kuring, sm->U, sm->Uprev, c->H.nc * c->H.n_p,
                             sm->d_ss, s));
+    CU(launch_ionic_aux_valid(sm->d_ss, s, -1));  // the carried u^{k-1} no longer matches
     return POLYDG_OK;
 }
 
@@ -1549,6 +1550,7 @@ int sim_set_history(sim_ctx* sm, const double* hist_dev, int count, void* stream
     polydg_ctx* c = sm->ctx;
     CU(launch_history_set(c->K, hist_dev, count, sm->ring, sm->kuring, sm->U, sm->Uprev, sm->Uprev2,
                           c->d_to_caller, c->H.nc, c->H.n_p, sm->d_ss, (cudaStream_t)stream));
+    CU(launch_ionic_aux_valid(sm->d_ss, (cudaStream_t)stream, -1));   // the carried u^{k-1} no longer matches
     return POLYDG_OK;
 }
 

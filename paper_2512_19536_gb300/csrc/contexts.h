@@ -195,7 +195,8 @@ struct sim_ctx {
     double* subW = nullptr;             // [2][n] r0 = b - K U^k and K (xg - U^k) of the subspace guess
     double* gram = nullptr;             // [kSubMaxPairs][kSubMaxCtas] Gram partial sums
     double *U = nullptr, *Uprev = nullptr, *I = nullptr, *F = nullptr, *y = nullptr;
-    double* yc = nullptr;               // per node: E_Na, E_K, exp(-K_o/5), exp((25 - Na_i)/3) (nodal form)
+    double* yc = nullptr;               // per node: E_Na, E_K, exp(-K_o/5), exp((25 - Na_i)/3),
+                                        // u^{k-1}, exp(-u^{k-1}/720) (nodal form)
     unsigned char* gxt = nullptr;       // feature tiles of the learned guess (with a model)
     double* d_y0 = nullptr;
     double* Ym = nullptr;               // [5][n] modal ionic state (sim_set_ionic_form 1), or null

@@ -81,8 +81,7 @@ inline NodeConsts node_consts() {
 // exp(-V/s) for s = 10, 18, 20, 80, 2.5 from B = exp(-V/720) (kept in B).
 struct VPowers { double e10, e18, e20, e80, e25, B; };
 
-BC_HD VPowers vpowers(double V) {
-    const double B = exp(-V * (1.0 / 720.0));
+BC_HD VPowers vpowers_from(double B) {
     const double B2 = B * B, B4 = B2 * B2, B8 = B4 * B4, B16 = B8 * B8, B32 = B16 * B16;
     const double B64 = B32 * B32, B256 = (B64 * B64) * (B64 * B64);
     VPowers p;
@@ -94,6 +93,8 @@ BC_HD VPowers vpowers(double V) {
     p.B = B;
     return p;
 }
+
+BC_HD VPowers vpowers(double V) { return vpowers_from(exp(-V * (1.0 / 720.0))); }
 
 // exp(-V/10) and exp(-V/18) only (the sodium gate of the current), from B = exp(-V/720).
 BC_HD void vpowers_m_from(double B, double& e10, double& e18) {
@@ -158,27 +159,28 @@ constexpr double kInvTau = 1.0 / tau;
 // update of the potentials after an Euler step, see current_after_step).
 struct Nernst { double ENa, EK, iNao, iNai, iKo, iKi; };
 
-// Functions of a node's concentrations that the update needs, carried from one step to
-// the next: E_Na, E_K, X = exp(-K_o/5) and exp((25 - Na_i)/3).  Each step changes the
-// concentrations by small increments, so the new values follow from the old ones by
-// logarithms and exponentials of numbers near 1 and 0 (short series).
-struct NodeCache { double ENa, EK, X, ep; };
+// Functions of a node's state that the update needs, carried from one step to the next:
+// E_Na, E_K, X = exp(-K_o/5), exp((25 - Na_i)/3), the potential u at the node and
+// B = exp(-u/720).  Each step changes the concentrations by small increments, so their
+// functions follow from the old ones by logarithms and exponentials of numbers near 1 and
+// 0 (short series); u^k's B follows from u^{k-1}'s the same way.
+struct NodeCache { double ENa, EK, X, ep, up, B; };
 
-BC_HD NodeCache node_cache(double Ko, double Nai) {
+BC_HD NodeCache node_cache(double Ko, double Nai, double u) {
     const double Ki = 140.0 + (18.0 - Nai);
     const double Nao = 144.0 - beta * (Nai - 18.0);
-    return NodeCache{RTF * log(Nao / Nai), RTF * log(Ko / Ki), exp(-Ko * kInv5), exp((25.0 - Nai) * kInv3)};
+    return NodeCache{RTF * log(Nao / Nai), RTF * log(Ko / Ki), exp(-Ko * kInv5), exp((25.0 - Nai) * kInv3),
+                     u, exp(-u * (1.0 / 720.0))};
 }
 
 // y'(V, y) of the Sec. 2 model (= -m(u, y)) at one point: d[0..4] for n, h, K_o, Na_i,
-// Ca_i; also the Nernst potentials of the state in *ne (may be null).  CACHED: E_Na, E_K
-// and the two concentration exponentials are read from *c instead of evaluated; else,
-// when c is given, they are stored there.  *Bv (may be null) receives exp(-V/720).
+// Ca_i; also the Nernst potentials of the state in *ne (may be null).  CACHED: E_Na, E_K,
+// the two concentration exponentials and B = exp(-V/720) are read from *c instead of
+// evaluated.
 template <bool CACHED = false>
 BC_HD void rates(const NodeConsts& k, double V, double n, double h, double Ko, double Nai, double Cai,
-                 double* d, Nernst* ne = nullptr, NodeCache* c = nullptr, double* Bv = nullptr) {
-    const VPowers p = vpowers(V);
-    if (Bv) *Bv = p.B;
+                 double* d, Nernst* ne = nullptr, const NodeCache* c = nullptr) {
+    const VPowers p = CACHED ? vpowers_from(c->B) : vpowers(V);
     const double xn = V + 34.0, xm = V + 30.0;
     const bool sn = fabs(xn) < 1e-5, sm = fabs(xm) < 1e-5;       // |x| < 1e-6 s, s = 10
     const double exn = k.an * p.e10, exm = k.am * p.e10;
@@ -207,7 +209,6 @@ BC_HD void rates(const NodeConsts& k, double V, double n, double h, double Ko, d
     const double minf = am_num * inv[2];
     const double ENa = CACHED ? c->ENa : RTF * log(Nao * inv[7]);
     const double EK = CACHED ? c->EK : RTF * log(Ko * inv[8]);
-    if (!CACHED && c) *c = NodeCache{ENa, EK, X, ep};
     const double INa = (gNa * minf * minf * minf * h + gNaL) * (V - ENa);
     const double IK = (gK * (n * n) * (n * n) + gAHP * Cai * inv[3] + gKL) * (V - EK);
     const double pump = rho * inv[4];
@@ -312,16 +313,16 @@ BC_HD double euler_and_current(const NodeConsts& k, double V, double Vx, double 
     return current_after_step(k, Vx, n, h, Ko, Nai, Cai, ne, dK, dNa);
 }
 
-// The same step with the node's carried functions c (CACHED: c holds the old state's
-// values; else they are evaluated) and c left holding the new state's: E_Na and E_K as
-// above, X and the sodium exponential times exp(-dK/5) and exp(-dNa/3), and
-// exp(-Vx/720) = exp(-V/720) exp((V - Vx)/720).
-template <bool CACHED>
+// The same step with the node's carried functions c: on entry the old state's (with c.B
+// already exp(-V/720) for this step's V), on return the new state's -- E_Na and E_K as
+// above, X and the sodium exponential times exp(-dK/5) and exp(-dNa/3), c.up = V -- and
+// the current at Vx with exp(-Vx/720) = exp(-V/720) exp((V - Vx)/720).
 BC_HD double euler_and_current_c(const NodeConsts& k, double V, double Vx, double dt, double& n,
                                  double& h, double& Ko, double& Nai, double& Cai, NodeCache& c) {
-    double d[5], B;
+    double d[5];
     Nernst ne;
-    rates<CACHED>(k, V, n, h, Ko, Nai, Cai, d, &ne, &c, &B);
+    rates<true>(k, V, n, h, Ko, Nai, Cai, d, &ne, &c);
+    const double B = c.B;
     const double dK = dt * d[2], dNa = dt * d[3];
     n += dt * d[0];
     h += dt * d[1];
@@ -332,6 +333,7 @@ BC_HD double euler_and_current_c(const NodeConsts& k, double V, double Vx, doubl
     const double f = current_after_step_b(k, Vx, Bx, n, h, Ko, Nai, Cai, ne, dK, dNa, &c.ENa, &c.EK);
     c.X *= exp_small(-dK * kInv5);
     c.ep *= exp_small(-dNa * kInv3);
+    c.up = V;
     return f;
 }
 

@@ -15,7 +15,7 @@ enum MatvecMode { MODE_PLAIN = 0, MODE_RHS = 3 };
 // Subspace initial guess (policy 3): the last kHistDirs solution increments, plus the
 // learned proposal, combined by a Galerkin projection.  The solutions live in a ring
 // of kHistRing vectors indexed by step (slot k mod kHistRing holds U^k).
-constexpr int kHistDirs = 16;
+constexpr int kHistDirs = 24;
 constexpr int kHistRing = kHistDirs + 1;
 constexpr int kSubMaxDirs = kHistDirs + 1;                       // + the learned proposal
 constexpr int kSubMaxPairs = kSubMaxDirs + kSubMaxDirs * (kSubMaxDirs + 1) / 2;
@@ -39,7 +39,8 @@ struct SimScalars {
     int32_t sub_dirs;      // directions of this step's subspace guess
     double theta_sub[kSubMaxDirs];   // their coefficients
     int32_t kd_len;        // consecutive increment products K D_j held by their ring, up to kd_step
-    int32_t yc_ok;         // the nodal ionic update's carried functions match the state
+    int32_t yc_ok;         // the nodal ionic update's carried functions match: bit 0 those of
+                           // the concentrations (the state), bit 1 those of u^{k-1}
     int64_t kd_step;
 };
 
@@ -329,8 +330,9 @@ cudaError_t launch_step_begin(PcgScalars* sc, SimScalars* ss, cudaStream_t s);
 cudaError_t launch_init_y(double* y, int64_t nn, const double* y0, cudaStream_t s);
 cudaError_t launch_node_scatter(const double* y_caller, double* y_int,
                                 const int64_t* node_to_caller_pos, int64_t nn, cudaStream_t s, int ns = 5);
-// The nodal update's carried functions (SimScalars::yc_ok) match the restored state.
-cudaError_t launch_ionic_aux_valid(SimScalars* ss, cudaStream_t s);
+// The nodal update's carried functions: all of them match (ok = 3: restored with the
+// state), or those of u^{k-1} no longer do (ok < 0: the potentials were set from outside).
+cudaError_t launch_ionic_aux_valid(SimScalars* ss, cudaStream_t s, int ok = 3);
 // Step index k of a simulation (and its failed flag cleared), for a restored state.
 cudaError_t launch_set_step(SimScalars* ss, int64_t k, cudaStream_t s);
 

@@ -337,8 +337,8 @@ history_products_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __re
 // on the directions whose Schur-complement pivots stay above 1e-13 of the largest diagonal
 // (greedy, largest pivot first), the others left at zero.  The guess is used when it
 // lowers the K-norm of the error (gain c.theta > 0).
-constexpr int kGramThreads = 256;
-constexpr int kGramRows = 128;           // rows per shared-memory tile
+constexpr int kGramThreads = 512;       // one thread per (i <= j) pair and per c_i: up to 350
+constexpr int kGramRows = 64;           // rows per shared-memory tile
 
 __global__ void __launch_bounds__(kGramThreads)
 subspace_gram_kernel(const double* __restrict__ W, const double* U, const double* xg,

@@ -13,10 +13,12 @@ namespace polydg {
 // Warp per cell: nodes of cell e are node_ptr[e]..node_ptr[e+1]-1.  Per node:
 //   u^k(x_q), y^{k+1} = y^k + dt y'(u^k, y^k),  u~ = 3/2 U^k - 1/2 U^{k-1} (U^0 at k = 0),
 //   I_e[i] = sum_q w_q f(u~(x_q), y^{k+1}_q) phi_i(x_q).
-// yc carries E_Na, E_K, exp(-K_o/5) and exp((25 - Na_i)/3) of each node's state from one
-// step to the next (bc::NodeCache): the update reads them instead of two logarithms and
-// two exponentials and leaves the new state's.  ionic_cache_kernel evaluates them afresh
-// before the update when the state was set from outside (ss->yc_ok = 0) and every 256 steps.
+// yc carries E_Na, E_K, exp(-K_o/5), exp((25 - Na_i)/3), u^{k-1}(x_q) and exp(-u^{k-1}/720)
+// of each node from one step to the next (bc::NodeCache): the update reads them instead of
+// two logarithms, three exponentials and the projection of U^{k-1}
+// (u~ = 3/2 u^k - 1/2 u^{k-1} at the node), and leaves the new state's.  ionic_cache_kernel
+// evaluates them afresh before the update when the state or the potentials were set from
+// outside (ss->yc_ok = 0) and every 256 steps.
 // The cell's coefficient vectors sit in shared memory (broadcast reads), so a thread
 // keeps only its node's basis values and the NP partial sums in registers: two
 // 256-thread blocks fit on an SM, which the fp64-latency-bound node update needs.
@@ -29,17 +31,13 @@ ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
              const double* __restrict__ node_phi, double* __restrict__ y, double* __restrict__ yc,
              int64_t nn, int64_t nc, double dt, double* __restrict__ I, const SimScalars* ss,
              const bc::NodeConsts kc) {
-    __shared__ double su[kIonicThreads / 32][2][NP];
+    __shared__ double su[kIonicThreads / 32][NP];
     if (ss->failed) return;
     const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     if (e >= nc) return;
     const bool first = (ss->k == 0);
-    if (lane < NP) {
-        const double ue = U[e * NP + lane];
-        su[wl][0][lane] = ue;
-        su[wl][1][lane] = first ? ue : 1.5 * ue - 0.5 * Uprev[e * NP + lane];
-    }
+    if (lane < NP) su[wl][lane] = U[e * NP + lane];
     __syncwarp();
     double acc[NP];
 #pragma unroll
@@ -47,19 +45,19 @@ ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
     const int64_t q1 = node_ptr[e + 1];
     for (int64_t q = node_ptr[e] + lane; q < q1; q += 32) {
         const double* ph = node_phi + q * NP;
-        double uk = 0.0, ux = 0.0;
+        double uk = 0.0;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
-            const double pv = __ldg(ph + j);
-            uk = fma(pv, su[wl][0][j], uk);
-            ux = fma(pv, su[wl][1][j], ux);
-        }
+        for (int j = 0; j < NP; ++j) uk = fma(__ldg(ph + j), su[wl][j], uk);
         double n = y[q], h = y[nn + q], Ko = y[2 * nn + q], Nai = y[3 * nn + q], Cai = y[4 * nn + q];
+        bc::NodeCache c{yc[q], yc[nn + q], yc[2 * nn + q], yc[3 * nn + q], yc[4 * nn + q], yc[5 * nn + q]};
+        // u~ = 3/2 u^k - 1/2 u^{k-1} (u^0 at k = 0); exp(-u^k/720) from exp(-u^{k-1}/720)
+        const double ux = first ? uk : 1.5 * uk - 0.5 * c.up;
+        c.B *= bc::exp_small((c.up - uk) * (1.0 / 720.0));
         // explicit Euler with u^k, then f(u~, y^{k+1})
-        bc::NodeCache c{yc[q], yc[nn + q], yc[2 * nn + q], yc[3 * nn + q]};
-        const double f = bc::euler_and_current_c<true>(kc, uk, ux, dt, n, h, Ko, Nai, Cai, c);
+        const double f = bc::euler_and_current_c(kc, uk, ux, dt, n, h, Ko, Nai, Cai, c);
         y[q] = n; y[nn + q] = h; y[2 * nn + q] = Ko; y[3 * nn + q] = Nai; y[4 * nn + q] = Cai;
         yc[q] = c.ENa; yc[nn + q] = c.EK; yc[2 * nn + q] = c.X; yc[3 * nn + q] = c.ep;
+        yc[4 * nn + q] = c.up; yc[5 * nn + q] = c.B;
         const double wf = node_w[q] * f;
         // the basis values again (L1 hits): keeping them in registers across the node
         // update would spill
@@ -73,18 +71,39 @@ ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
     }
 }
 
-// The carried functions of every node's state, evaluated from the state (skipped while
-// ss->yc_ok holds, except every 256th step).
-__global__ void ionic_cache_kernel(const double* __restrict__ y, double* __restrict__ yc, int64_t nn,
-                                   const SimScalars* ss) {
-    if (ss->failed || (ss->yc_ok != 0 && (ss->k & 255) != 0)) return;
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nn) return;
-    const bc::NodeCache c = bc::node_cache(y[2 * nn + q], y[3 * nn + q]);
-    yc[q] = c.ENa;
-    yc[nn + q] = c.EK;
-    yc[2 * nn + q] = c.X;
-    yc[3 * nn + q] = c.ep;
+// The carried functions of every node, evaluated from the state and from U^{k-1} (U^0 at
+// k = 0), warp per cell: all of them every 256th step and when the state was set from
+// outside (bit 0 of ss->yc_ok clear), those of u^{k-1} alone when only the potentials were
+// (bit 1 clear); nothing otherwise.
+template <int NP>
+__global__ void __launch_bounds__(kIonicThreads)
+ionic_cache_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
+                   const int64_t* __restrict__ node_ptr, const double* __restrict__ node_phi,
+                   const double* __restrict__ y, double* __restrict__ yc, int64_t nn, int64_t nc,
+                   const SimScalars* ss) {
+    __shared__ double su[kIonicThreads / 32][NP];
+    if (ss->failed) return;
+    const bool all = (ss->k & 255) == 0 || !(ss->yc_ok & 1);
+    if (!all && (ss->yc_ok & 2)) return;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    if (e >= nc) return;
+    if (lane < NP) su[wl][lane] = (ss->k == 0 ? U : Uprev)[e * NP + lane];
+    __syncwarp();
+    for (int64_t q = node_ptr[e] + lane; q < node_ptr[e + 1]; q += 32) {
+        double up = 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) up = fma(node_phi[q * NP + j], su[wl][j], up);
+        if (all) {
+            const bc::NodeCache c = bc::node_cache(y[2 * nn + q], y[3 * nn + q], up);
+            yc[q] = c.ENa;
+            yc[nn + q] = c.EK;
+            yc[2 * nn + q] = c.X;
+            yc[3 * nn + q] = c.ep;
+        }
+        yc[4 * nn + q] = up;
+        yc[5 * nn + q] = exp(-up * (1.0 / 720.0));
+    }
 }
 
 cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int64_t* node_ptr,
@@ -92,7 +111,13 @@ cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int
                          int64_t nc, double dt, double* I, const SimScalars* ss, cudaStream_t s) {
     const unsigned g = (unsigned)((nc * 32 + kIonicThreads - 1) / kIonicThreads);
     static const bc::NodeConsts kc = bc::node_consts();
-    ionic_cache_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(y, yc, nn, ss);
+    switch (np) {
+        case 3: ionic_cache_kernel<3><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_phi, y, yc, nn, nc, ss); break;
+        case 6: ionic_cache_kernel<6><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_phi, y, yc, nn, nc, ss); break;
+        case 10: ionic_cache_kernel<10><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_phi, y, yc, nn, nc, ss); break;
+        case 15: ionic_cache_kernel<15><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_phi, y, yc, nn, nc, ss); break;
+        default: return cudaErrorInvalidValue;
+    }
     switch (np) {
         case 3: ionic_kernel<3><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, yc, nn, nc, dt, I, ss, kc); break;
         case 6: ionic_kernel<6><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, yc, nn, nc, dt, I, ss, kc); break;
@@ -272,10 +297,10 @@ cudaError_t launch_node_scatter(const double* y_caller, double* y_int,
     return cudaGetLastError();
 }
 
-__global__ void ionic_aux_valid_kernel(SimScalars* ss) { ss->yc_ok = 1; }
+__global__ void ionic_aux_flag_kernel(SimScalars* ss, int ok) { ss->yc_ok = ok < 0 ? (ss->yc_ok & 1) : ok; }
 
-cudaError_t launch_ionic_aux_valid(SimScalars* ss, cudaStream_t s) {
-    ionic_aux_valid_kernel<<<1, 1, 0, s>>>(ss);
+cudaError_t launch_ionic_aux_valid(SimScalars* ss, cudaStream_t s, int ok) {
+    ionic_aux_flag_kernel<<<1, 1, 0, s>>>(ss, ok);
     return cudaGetLastError();
 }
 
@@ -336,7 +361,7 @@ __global__ void step_finish_kernel(double* __restrict__ U, double* __restrict__ 
 __global__ void step_stats_kernel(const PcgScalars* sc, SimScalars* ss) {
     if (threadIdx.x != 0 || ss->failed) return;
     if (ss->hist_len < kHistRing) ss->hist_len += 1;
-    ss->yc_ok = 1;             // the step's ionic update left the new state's carried functions
+    ss->yc_ok = 3;             // the step's ionic update left the new state's carried functions
     ss->k += 1;
     ss->steps_done += 1;
     ss->total_its += sc->it;

@@ -6,7 +6,7 @@
 For each evaluation workload -- the 4096-cell Voronoi P3 recipe with the given seeds (the
 training set is seeds 0-7) and the n^3 jittered hexahedral P2 mesh -- the coupled steps run
 in the mixed form (fp32 local inverses, flexible PCG to 1e-8) with four initial guesses:
-  * subspace:   Galerkin projection onto the network's proposal and the last 16 solution
+  * subspace:   Galerkin projection onto the network's proposal and the last 24 solution
                 increments (policy 3 with the model);
   * increments: the same projection without the network (policy 3, no model);
   * proposal:   the network's proposal alone, kept when its residual is below U^k's

@@ -234,7 +234,9 @@ def test_coupled_steps_with_trained_guess_match_oracle(vor):
 def subspace_run(w, d, steps, model=None, rtol=1e-8, reset_history=False):
     """Per-step iteration counts and the final potential of a policy-3 run; with
     reset_history the simulation's own last solutions are restored through
-    sim_set_history before every step (a host-side state round trip)."""
+    sim_set_history before every step, followed by the per-node functions its ionic update
+    carries (sim_set_ionic_aux: setting the potentials invalidates them) -- a host-side
+    state round trip."""
     import torch
     pd = lib()
     ctx = gpu_ctx(w)
@@ -245,7 +247,10 @@ def subspace_run(w, d, steps, model=None, rtol=1e-8, reset_history=False):
     pd.sim_get_state(sim, hist[0])
     for _ in range(steps):
         if reset_history:
-            pd.sim_set_history(sim, torch.stack(hist[::-1][:17]))
+            aux = torch.empty(6 * ctx.info.n_nodes, dtype=torch.float64, device="cuda")
+            pd.sim_get_ionic_aux(sim, aux)
+            pd.sim_set_history(sim, torch.stack(hist[::-1][:25]))
+            pd.sim_set_ionic_aux(sim, aux)
         st = pd.monodomain_step(sim, 1)
         assert st["status"] == 0
         its.append(st["total_iterations"])
@@ -271,7 +276,7 @@ def test_subspace_guess_iterations_and_answer_match_oracle(vor):
     for _ in range(steps):
         st = md.state
         b, y_new = md.rhs(st)
-        x0, _ = G.subspace_guess(d.K, b, hist[::-1], m=16)
+        x0, _ = G.subspace_guess(d.K, b, hist[::-1], m=24)
         r = pcg(d.K, b, x0=x0, prec=S.apply, rtol=1e-8)
         ref_its.append(r.iterations)
         plain_its.append(pcg(d.K, b, x0=st.U, prec=S.apply, rtol=1e-8).iterations)

@@ -1,9 +1,9 @@
 """Checkpoint / resume and bounded device waits, on a GB300 (through the C ABI).
 
-* Resume: a simulation stepped k times, its state saved to the host (the last 17
+* Resume: a simulation stepped k times, its state saved to the host (the last 25
   potentials, the ionic state -- with, for the per-node form, the functions of it that the
   update carries -- and the step index), then restored into a fresh simulation with
-  sim_set_state + sim_set_ionic_aux + sim_set_history, continues bit for bit like one that
+  sim_set_state + sim_set_history + sim_set_ionic_aux, continues bit for bit like one that
   was never interrupted -- per-node and modal ionic forms, with the subspace initial guess.
   Without the carried functions the resumed run agrees to rounding; the carried functions
   agree with their definitions evaluated from the state.
@@ -19,7 +19,7 @@ from test_gpu_parity import lib, dev, host, mnorm_rel, gpu_ctx
 
 pytestmark = pytest.mark.gpu
 
-H = 17     # solutions the subspace initial guess reads
+H = 25     # solutions the subspace initial guess reads
 
 
 def make_sim(pd, ctx, pc, w, form):
@@ -41,7 +41,7 @@ def snapshot(pd, sim, ctx, n_nodes, form):
         Y = torch.empty(5 * ctx.n_dofs, dtype=torch.float64, device="cuda")
         pd.sim_get_ionic_coeffs(sim, Y)
     else:
-        Y = torch.empty(4 * n_nodes, dtype=torch.float64, device="cuda")
+        Y = torch.empty(6 * n_nodes, dtype=torch.float64, device="cuda")
         pd.sim_get_ionic_aux(sim, Y)
     torch.cuda.synchronize()
     return u.cpu(), y.cpu(), Y.cpu()
@@ -62,7 +62,7 @@ def test_resumed_run_is_bit_identical(voronoi256, form):
 
     # the interrupted run: k1 steps, the state to the host (the potentials step by step)
     run = make_sim(pd, ctx, pc, w, form)
-    hist = []
+    hist = [snapshot(pd, run, ctx, n_nodes, form)[0]]           # U^0, then U^1 .. U^k1
     for _ in range(k1):
         pd.monodomain_step(run, 1)
         hist.append(snapshot(pd, run, ctx, n_nodes, form)[0])
@@ -70,14 +70,15 @@ def test_resumed_run_is_bit_identical(voronoi256, form):
     assert run.step_index == k1
     run.close()
 
-    # a fresh simulation resumes from the host copies
+    # a fresh simulation resumes from the host copies (the carried functions last: setting
+    # the potentials invalidates them)
     res = make_sim(pd, ctx, pc, w, form)
     pd.sim_set_state(res, k1, y=y_k.cuda(), Y=Y_k.cuda() if form == "modal" else None)
-    if form == "nodal":
-        pd.sim_set_ionic_aux(res, Y_k.cuda())
     assert res.step_index == k1
     last = torch.stack(hist[::-1][:H]).contiguous().cuda()        # U^k, U^{k-1}, ...
     pd.sim_set_history(res, last)
+    if form == "nodal":
+        pd.sim_set_ionic_aux(res, Y_k.cuda())
     pd.monodomain_step(res, k2)
     u_res, y_res, Y_res = snapshot(pd, res, ctx, n_nodes, form)
     assert res.step_index == k1 + k2
@@ -90,7 +91,8 @@ def test_resumed_run_is_bit_identical(voronoi256, form):
 
 def carried_from_state(y):
     """E_Na, E_K, exp(-K_o/5), exp((25 - Na_i)/3) of nodal states y [5, n] (Sec. 2 model:
-    K_i = 140 + (18 - Na_i), Na_o = 144 - 7 (Na_i - 18), E = 26.64 ln(c_out / c_in))."""
+    K_i = 140 + (18 - Na_i), Na_o = 144 - 7 (Na_i - 18), E = 26.64 ln(c_out / c_in)); the
+    carried u^{k-1} and exp(-u^{k-1}/720) are checked against each other."""
     Ko, Nai = y[2], y[3]
     Ki = 140.0 + (18.0 - Nai)
     Nao = 144.0 - 7.0 * (Nai - 18.0)
@@ -99,10 +101,11 @@ def carried_from_state(y):
 
 
 def test_carried_ionic_functions_track_the_state(voronoi256):
-    """The nodal update carries four functions of each node's state from step to step
-    (updated from the step's increments, evaluated afresh every 256th step); after 255
-    carried steps -- the longest stretch, the stimulus on for the first 20 -- they agree with
-    their definitions evaluated from the state to within a few hundred ulps."""
+    """The nodal update carries functions of each node's state from step to step (updated
+    from the step's increments, evaluated afresh every 256th step); after 255 carried steps
+    -- the longest stretch, the stimulus on for the first 20 -- they agree with their
+    definitions evaluated from the state to within a few hundred ulps, and the carried
+    exp(-u^{k-1}/720) with the carried u^{k-1}."""
     pd = lib()
     w, d = voronoi256
     ctx = gpu_ctx(w)
@@ -112,10 +115,13 @@ def test_carried_ionic_functions_track_the_state(voronoi256):
     pd.monodomain_step(sim, 256)          # steps k = 0..255: evaluated at k = 0, then carried
     _, y, aux = snapshot(pd, sim, ctx, n_nodes, "nodal")
     y = y.numpy().reshape(5, -1)
-    aux = aux.numpy().reshape(4, -1)
+    aux = aux.numpy().reshape(6, -1)
     ref = carried_from_state(y)
-    rel = np.abs(aux - ref) / np.abs(ref).max(axis=1, keepdims=True)
+    rel = np.abs(aux[:4] - ref) / np.abs(ref).max(axis=1, keepdims=True)
     assert rel.max() <= 1e-12, rel.max(axis=1)
+    B = np.exp(-aux[4] / 720.0)
+    assert np.max(np.abs(aux[5] - B) / B) <= 1e-12
+    assert np.max(np.abs(aux[4] - w.u_rest)) > 0.1   # the potential left its initial rest value
     assert np.ptp(y[2]) > 1e-6            # the concentrations did move
 
 
@@ -133,7 +139,7 @@ def test_resume_without_the_carried_functions_differs_by_rounding(voronoi256):
     pd.monodomain_step(ref, k1 + k2)
     u_ref, _, _ = snapshot(pd, ref, ctx, n_nodes, "nodal")
     run = make_sim(pd, ctx, pc, w, "nodal")
-    hist = []
+    hist = [snapshot(pd, run, ctx, n_nodes, "nodal")[0]]        # U^0, then U^1 .. U^k1
     for _ in range(k1):
         pd.monodomain_step(run, 1)
         hist.append(snapshot(pd, run, ctx, n_nodes, "nodal")[0])
