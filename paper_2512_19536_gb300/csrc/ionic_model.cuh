@@ -107,11 +107,14 @@ BC_HD void vpowers_m(double V, double& e10, double& e18) {
     vpowers_m_from(exp(-V * (1.0 / 720.0)), e10, e18);
 }
 
-// exp(a): for |a| < 2^-6 the Taylor polynomial of degree 7 (remainder < a^8 / 8! < 1e-19
-// relative), else the library function.  For the ratio of an exponential at two nearby
-// arguments.
+// exp(a): for |a| < 2^-18 the Taylor polynomial of degree 3 (remainder < a^4 / 4! < 1e-23
+// relative), for |a| < 2^-6 that of degree 7 (< a^8 / 8! < 1e-19), else the library
+// function.  For the ratio of an exponential at two nearby arguments (the concentrations
+// move by ~1e-6 relative per step, the potential by up to a few mV).
 BC_HD double exp_small(double a) {
-    if (fabs(a) < 0x1p-6)
+    const double fa = fabs(a);
+    if (fa < 0x1p-18) return 1.0 + a * (1.0 + a * (0.5 + a * (1.0 / 6.0)));
+    if (fa < 0x1p-6)
         return 1.0 + a * (1.0 + a * (0.5 + a * (1.0 / 6.0 + a * (1.0 / 24.0 + a * (1.0 / 120.0 +
                      a * (1.0 / 720.0 + a * (1.0 / 5040.0)))))));
     return exp(a);
@@ -136,10 +139,12 @@ BC_HD void batch_reciprocal(const double (&x)[M], double (&inv)[M]) {
     inv[0] = r;
 }
 
-// ln(1 + a): the Taylor series for |a| < 2^-10 (six terms: relative error < a^6 / 7 <
-// 2e-19), else the library function.
+// ln(1 + a): the Taylor series, three terms for |a| < 2^-18 (relative error < a^3 / 4 <
+// 2e-17) and six for |a| < 2^-10 (< a^6 / 7 < 2e-19), else the library function.
 BC_HD double log1p_small(double a) {
-    if (fabs(a) < 0x1p-10) {
+    const double fa = fabs(a);
+    if (fa < 0x1p-18) return a - a * a * (0.5 - a * (1.0 / 3.0));
+    if (fa < 0x1p-10) {
         const double a2 = a * a;
         return a - a2 * (0.5 - a * (1.0 / 3.0 - a * (0.25 - a * (0.2 - a * (1.0 / 6.0)))));
     }
