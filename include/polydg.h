@@ -184,10 +184,11 @@ int polydg_setup(const polydg_mesh *mesh, int p, const int32_t *subdomain_of_cel
 
 /* polydg_setup on a polyhedral mesh (degree p = 2, n_p = 10: the device kernels are
  * instantiated for n_p in {3, 6, 10, 15}, and only P2 maps to one of them in 3D).  Element integrals use
- * the cone of tetrahedra from each cell's vertex average, each with a collapsed
- * rule of (p + 1)^3 points: Gauss-Jacobi in the two collapsed directions (weights
- * s^2 and t, the Jacobian's factors) and Gauss-Legendre in the third, exact for
- * polynomials of degree 2p + 1; face integrals use the collapsed rule with
+ * the cone of tetrahedra from each cell's vertex average, each with a rule exact for
+ * polynomials of degree 2p + 1: for p = 2 the fully symmetric 14-point rule of
+ * degree 5, otherwise a collapsed rule of (p + 1)^3 points (Gauss-Jacobi in the
+ * two collapsed directions, weights s^2 and t, the Jacobian's factors, and
+ * Gauss-Legendre in the third); face integrals use the collapsed rule with
  * (p + 1)^2 points per facet.  The quadrature-node tables (ionic state)
  * follow the same element rule.  Errors as polydg_setup, plus EINVAL for a facet
  * shared by more than two cells or without opposite orientation, and for a cell

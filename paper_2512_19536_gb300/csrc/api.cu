@@ -444,6 +444,7 @@ static int setup_device(polydg_ctx* c, polydg_ctx** out) {
         (st = upload(&c->d_node_pos, H.node_to_caller_pos)) ||
         (st = upload(&c->d_to_internal, H.to_internal)))
         return fail(st);
+    c->ionic_lpc = ionic_lanes_per_cell(H.node_ptr.data(), H.nc);
     {
         std::vector<double> diam(H.nc);
         for (int64_t e = 0; e < H.nc; ++e) diam[e] = H.diam[H.to_caller[e]];
@@ -1218,7 +1219,7 @@ static int enqueue_step_pre(sim_ctx* sm, cudaStream_t s) {
                               sm->Ym, sm->y, nn, H.nc, dt, sm->I, sm->d_ss, s));
     else
         CU(launch_ionic(np, sm->U, sm->Uprev, c->d_node_ptr, c->d_node_w, c->d_node_phi, sm->y, sm->yc, nn,
-                        H.nc, dt, sm->I, sm->d_ss, s));
+                        H.nc, dt, sm->I, sm->d_ss, c->ionic_lpc, s));
     CU(launch_matvec(MODE_RHS, np, c->K, c->K.val_minus, sm->U, w.b, sm->I, sm->F, -H.chi_cm * dt,
                      dt, sm->d_ss, dt, sm->prm.stim_duration, s));
     if (sm->guess_policy == 3) {  // subspace of the learned proposal and the last increments

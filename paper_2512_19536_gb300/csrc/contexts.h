@@ -120,6 +120,7 @@ struct polydg_ctx {
     DeviceMatrix K;
     int64_t* d_to_caller = nullptr;
     int64_t* d_node_ptr = nullptr;
+    int ionic_lpc = 32;             // lanes per cell of the ionic kernel (ionic_lanes_per_cell)
     double* d_node_w = nullptr;
     double* d_node_phi = nullptr;
     double* d_Minv = nullptr;           // [nc][n_p][n_p] inverse mass blocks (modal ionic state)

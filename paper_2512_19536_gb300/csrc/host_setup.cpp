@@ -144,12 +144,101 @@ static void cell_apex3d(const HostSetup& S, int64_t c, double* apex) {
     for (int d = 0; d < 3; ++d) apex[d] /= (double)ids.size();
 }
 
+// Fully symmetric 14-point rule on a tetrahedron, exact to degree 5 -- the degree of the
+// 3 x 3 x 3 collapsed rule with about half its points (the element quadrature nodes carry
+// the ionic state, so their number sets the cost of the ionic update).  Barycentric
+// orbits, in this order: (a, a, a, 1 - 3a) and (b, b, b, 1 - 3b) with the odd coordinate
+// at vertex 0..3, then (c, c, 1/2 - c, 1/2 - c) with the c's at the vertex pairs (0,1),
+// (0,2), (0,3), (1,2), (1,3), (2,3).  A rule invariant under the vertex permutations is
+// exact for a polynomial when it is exact for its average over the permutations, so
+// degree 5 needs only the invariant polynomials: with P_k = sum_i l_i^k and
+// l_1 + .. + l_4 = 1 these are spanned by 1, P_2, P_3, P_4, P_2^2 and P_2 P_3, whose
+// means over the tetrahedron are 1, 2/5, 1/5, 4/35, 6/35, 13/140 (the mean of l^alpha is
+// 3! alpha! / (|alpha| + 3)!).  The six equations in (a, b, c, w_a, w_b, w_c) are solved
+// once by Newton's method with a central-difference Jacobian from a nearby start.
+struct SymTet5 { double lam[14][4]; double w[14]; };
+
+static void sym_tet5_points(const double* v, SymTet5& r) {
+    int k = 0;
+    for (int o = 0; o < 2; ++o)
+        for (int i = 0; i < 4; ++i, ++k) {
+            for (int j = 0; j < 4; ++j) r.lam[k][j] = v[o];
+            r.lam[k][i] = 1.0 - 3.0 * v[o];
+            r.w[k] = v[3 + o];
+        }
+    for (int i = 0; i < 4; ++i)
+        for (int j = i + 1; j < 4; ++j, ++k) {
+            for (int l = 0; l < 4; ++l) r.lam[k][l] = 0.5 - v[2];
+            r.lam[k][i] = r.lam[k][j] = v[2];
+            r.w[k] = v[5];
+        }
+}
+
+static void sym_tet5_residual(const double* v, double* F) {
+    static const double mean[6] = {1.0, 2.0 / 5.0, 1.0 / 5.0, 4.0 / 35.0, 6.0 / 35.0, 13.0 / 140.0};
+    SymTet5 r;
+    sym_tet5_points(v, r);
+    for (int e = 0; e < 6; ++e) F[e] = -mean[e];
+    for (int k = 0; k < 14; ++k) {
+        double P2 = 0.0, P3 = 0.0, P4 = 0.0;
+        for (int i = 0; i < 4; ++i) {
+            const double l = r.lam[k][i], l2 = l * l;
+            P2 += l2; P3 += l2 * l; P4 += l2 * l2;
+        }
+        const double g[6] = {1.0, P2, P3, P4, P2 * P2, P2 * P3};
+        for (int e = 0; e < 6; ++e) F[e] += r.w[k] * g[e];
+    }
+}
+
+static const SymTet5& sym_tet5() {
+    static const SymTet5 rule = [] {
+        double v[6] = {0.09, 0.31, 0.045, 0.07, 0.11, 0.04};
+        for (int it = 0; it < 40; ++it) {
+            double J[6][7], F[6];
+            sym_tet5_residual(v, F);
+            for (int c = 0; c < 6; ++c) {
+                const double h = 1e-6;
+                double vp[6], vm[6], Fp[6], Fm[6];
+                for (int i = 0; i < 6; ++i) vp[i] = vm[i] = v[i];
+                vp[c] += h;
+                vm[c] -= h;
+                sym_tet5_residual(vp, Fp);
+                sym_tet5_residual(vm, Fm);
+                for (int r = 0; r < 6; ++r) J[r][c] = (Fp[r] - Fm[r]) / (2.0 * h);
+            }
+            for (int r = 0; r < 6; ++r) J[r][6] = -F[r];
+            for (int c = 0; c < 6; ++c) {              // elimination with partial pivoting
+                int piv = c;
+                for (int r = c + 1; r < 6; ++r)
+                    if (std::fabs(J[r][c]) > std::fabs(J[piv][c])) piv = r;
+                for (int k = 0; k < 7; ++k) std::swap(J[c][k], J[piv][k]);
+                for (int r = c + 1; r < 6; ++r) {
+                    const double f = J[r][c] / J[c][c];
+                    for (int k = c; k < 7; ++k) J[r][k] -= f * J[c][k];
+                }
+            }
+            double dx[6];
+            for (int r = 5; r >= 0; --r) {
+                double t = J[r][6];
+                for (int k = r + 1; k < 6; ++k) t -= J[r][k] * dx[k];
+                dx[r] = t / J[r][r];
+            }
+            for (int i = 0; i < 6; ++i) v[i] += dx[i];
+        }
+        SymTet5 r;
+        sym_tet5_points(v, r);
+        return r;
+    }();
+    return rule;
+}
+
 // 2D: fan of triangles (v0, v_k, v_{k+1}); on each the collapsed rule
 // x(s,t) = A + s (B - A) + s t (C - B), weight w_s w_t s |(B-A) x (C-A)|.
 // 3D: cone of tetrahedra (apex, a, b, c) over the outward facets; on each
 // x(s,t,u) = A + s (B-A) + s t (C-B) + s t u (D-C) with Jacobian 6|T| s^2 t, taken as
 // the weights of npts-point Gauss-Jacobi rules in s (s^2) and t (t), Gauss-Legendre in
-// u: exact to total degree 2 npts - 1.
+// u: exact to total degree 2 npts - 1; for npts = 3 the symmetric 14-point rule of the
+// same degree instead.
 void element_rule(const HostSetup& S, int64_t c, int npts, std::vector<double>& xs,
                   std::vector<double>& w) {
     std::vector<double> g, gw;
@@ -188,6 +277,16 @@ void element_rule(const HostSetup& S, int64_t c, int npts, std::vector<double>& 
         const double six_vol = std::fabs(e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) -
                                          e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
                                          e1[2] * (e2[0] * e3[1] - e2[1] * e3[0]));
+        if (npts == 3) {
+            const SymTet5& R = sym_tet5();
+            for (int q = 0; q < 14; ++q) {
+                for (int d = 0; d < 3; ++d)
+                    xs.push_back(R.lam[q][0] * A[d] + R.lam[q][1] * B[d] + R.lam[q][2] * C[d] +
+                                 R.lam[q][3] * D[d]);
+                w.push_back(R.w[q] * (six_vol / 6.0));
+            }
+            continue;
+        }
         for (int i = 0; i < npts; ++i)
             for (int j = 0; j < npts; ++j)
                 for (int l = 0; l < npts; ++l) {
@@ -201,7 +300,7 @@ void element_rule(const HostSetup& S, int64_t c, int npts, std::vector<double>& 
 
 static int64_t element_rule_size(const HostSetup& S, int64_t c, int npts) {
     const int64_t m = S.cell_ptr[c + 1] - S.cell_ptr[c];
-    return S.dim == 2 ? (m - 2) * npts * npts : (m / 3) * npts * npts * npts;
+    return S.dim == 2 ? (m - 2) * npts * npts : (m / 3) * (npts == 3 ? 14 : npts * npts * npts);
 }
 
 // ---------------------------------------------------------------- geometry

@@ -310,10 +310,12 @@ cudaError_t launch_guess_adam(const float* part, int ncta, int P, float* w32, fl
                               const double* lpart, double inv_count, double* loss, cudaStream_t s);
 cudaError_t launch_to_half(const float* w32, __half* w16, int P, cudaStream_t s);
 
-// Ionic update + ion-current load (Eq. fully-discrete-1).
+// Ionic update + ion-current load (Eq. fully-discrete-1), lpc lanes per cell (8, 16 or
+// 32, from ionic_lanes_per_cell on the host copy of node_ptr).
 cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int64_t* node_ptr,
                          const double* node_w, const double* node_phi, double* y, double* yc, int64_t nn,
-                         int64_t nc, double dt, double* I, const SimScalars* ss, cudaStream_t s);
+                         int64_t nc, double dt, double* I, const SimScalars* ss, int lpc, cudaStream_t s);
+int ionic_lanes_per_cell(const int64_t* node_ptr, int64_t nc);
 // Modal ionic state (the second line of Eq. fully-discrete-1 in the DG basis): Ym is
 // [5][nc n_p], Minv the per-cell inverse mass blocks [nc][n_p][n_p] (row-major).
 cudaError_t launch_ionic_modal(int np, const double* U, const double* Uprev, const int64_t* node_ptr,

@@ -10,7 +10,12 @@
 
 namespace polydg {
 
-// Warp per cell: nodes of cell e are node_ptr[e]..node_ptr[e+1]-1.  Per node:
+// LPC lanes per cell (32 / LPC consecutive cells per warp; nodes of cell e are
+// node_ptr[e]..node_ptr[e+1]-1, lane l of its group takes nodes l, l + LPC, ...).  The
+// host picks LPC from the cells' node counts (ionic_lanes_per_cell): a warp instruction
+// costs the fp64 pipe the same with idle lanes, so the pick is the one with the fewest
+// passes, e.g. 8 for 168-node cells (21 full passes per 4 cells, where a warp per cell
+// would run 6 passes with 8 of 32 lanes busy in the last).  Per node:
 //   u^k(x_q), y^{k+1} = y^k + dt y'(u^k, y^k),  u~ = 3/2 U^k - 1/2 U^{k-1} (U^0 at k = 0),
 //   I_e[i] = sum_q w_q f(u~(x_q), y^{k+1}_q) phi_i(x_q).
 // yc carries E_Na, E_K, exp(-K_o/5), exp((25 - Na_i)/3), u^{k-1}(x_q) and exp(-u^{k-1}/720)
@@ -24,30 +29,34 @@ namespace polydg {
 // 256-thread blocks fit on an SM, which the fp64-latency-bound node update needs.
 constexpr int kIonicThreads = 256;
 
-template <int NP>
+template <int NP, int LPC>
 __global__ void __launch_bounds__(kIonicThreads, 2)
 ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
              const int64_t* __restrict__ node_ptr, const double* __restrict__ node_w,
              const double* __restrict__ node_phi, double* __restrict__ y, double* __restrict__ yc,
              int64_t nn, int64_t nc, double dt, double* __restrict__ I, const SimScalars* ss,
              const bc::NodeConsts kc) {
-    __shared__ double su[kIonicThreads / 32][NP];
+    constexpr int CPW = 32 / LPC;                 // cells per warp
+    __shared__ double su[kIonicThreads / 32][CPW][NP];
     if (ss->failed) return;
-    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t e0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * CPW;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    if (e >= nc) return;
+    if (e0 >= nc) return;                         // the whole warp: the sums below need all lanes
+    const int cw = lane / LPC, sl = lane % LPC;
+    const int64_t e = e0 + cw;
     const bool first = (ss->k == 0);
-    if (lane < NP) su[wl][lane] = U[e * NP + lane];
+    for (int t = lane; t < CPW * NP; t += 32)
+        su[wl][t / NP][t % NP] = e0 + t / NP < nc ? U[e0 * NP + t] : 0.0;
     __syncwarp();
     double acc[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) acc[j] = 0.0;
-    const int64_t q1 = node_ptr[e + 1];
-    for (int64_t q = node_ptr[e] + lane; q < q1; q += 32) {
+    const int64_t q1 = e < nc ? node_ptr[e + 1] : 0;
+    for (int64_t q = e < nc ? node_ptr[e] + sl : 0; q < q1; q += LPC) {
         const double* ph = node_phi + q * NP;
         double uk = 0.0;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) uk = fma(__ldg(ph + j), su[wl][j], uk);
+        for (int j = 0; j < NP; ++j) uk = fma(__ldg(ph + j), su[wl][cw][j], uk);
         double n = y[q], h = y[nn + q], Ko = y[2 * nn + q], Nai = y[3 * nn + q], Cai = y[4 * nn + q];
         bc::NodeCache c{yc[q], yc[nn + q], yc[2 * nn + q], yc[3 * nn + q], yc[4 * nn + q], yc[5 * nn + q]};
         // u~ = 3/2 u^k - 1/2 u^{k-1} (u^0 at k = 0); exp(-u^k/720) from exp(-u^{k-1}/720)
@@ -64,11 +73,31 @@ ionic_kernel(const double* __restrict__ U, const double* __restrict__ Uprev,
 #pragma unroll
         for (int j = 0; j < NP; ++j) acc[j] = fma(wf, __ldg(ph + j), acc[j]);
     }
+    // sums over each cell's LPC lanes (xor offsets below LPC stay inside the group)
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
-        const double s = warp_sum(acc[j]);
-        if (lane == 0) I[e * NP + j] = s;
+        double s = acc[j];
+#pragma unroll
+        for (int o = LPC / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (sl == 0 && e < nc) I[e * NP + j] = s;
     }
+}
+
+int ionic_lanes_per_cell(const int64_t* node_ptr, int64_t nc) {
+    int best = 32;
+    long double best_cost = 0.0L;
+    for (int lpc : {32, 16, 8}) {
+        const int cpw = 32 / lpc;
+        long double passes = 0.0L;
+        for (int64_t g = 0; g < nc; g += cpw) {
+            int64_t m = 0;
+            for (int64_t e = g; e < std::min<int64_t>(nc, g + cpw); ++e)
+                m = std::max<int64_t>(m, (node_ptr[e + 1] - node_ptr[e] + lpc - 1) / lpc);
+            passes += (long double)m;
+        }
+        if (lpc == 32 || passes <= best_cost) { best = lpc; best_cost = passes; }
+    }
+    return best;
 }
 
 // The carried functions of every node, evaluated from the state and from U^{k-1} (U^0 at
@@ -108,9 +137,12 @@ ionic_cache_kernel(const double* __restrict__ U, const double* __restrict__ Upre
 
 cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int64_t* node_ptr,
                          const double* node_w, const double* node_phi, double* y, double* yc, int64_t nn,
-                         int64_t nc, double dt, double* I, const SimScalars* ss, cudaStream_t s) {
+                         int64_t nc, double dt, double* I, const SimScalars* ss, int lpc, cudaStream_t s) {
     const unsigned g = (unsigned)((nc * 32 + kIonicThreads - 1) / kIonicThreads);
     static const bc::NodeConsts kc = bc::node_consts();
+    if (lpc != 32 && lpc != 16 && lpc != 8) return cudaErrorInvalidValue;
+    const int64_t warps = (nc + 32 / lpc - 1) / (32 / lpc);
+    const unsigned gi = (unsigned)((warps * 32 + kIonicThreads - 1) / kIonicThreads);
     switch (np) {
         case 3: ionic_cache_kernel<3><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_phi, y, yc, nn, nc, ss); break;
         case 6: ionic_cache_kernel<6><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_phi, y, yc, nn, nc, ss); break;
@@ -118,13 +150,23 @@ cudaError_t launch_ionic(int np, const double* U, const double* Uprev, const int
         case 15: ionic_cache_kernel<15><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_phi, y, yc, nn, nc, ss); break;
         default: return cudaErrorInvalidValue;
     }
+    auto run = [&](auto kern) {
+        kern<<<gi, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, yc, nn, nc, dt, I, ss, kc);
+    };
+#define POLYDG_IONIC_CASE(NP_)                                                  \
+    case NP_:                                                                   \
+        if (lpc == 32) run(ionic_kernel<NP_, 32>);                              \
+        else if (lpc == 16) run(ionic_kernel<NP_, 16>);                         \
+        else run(ionic_kernel<NP_, 8>);                                         \
+        break;
     switch (np) {
-        case 3: ionic_kernel<3><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, yc, nn, nc, dt, I, ss, kc); break;
-        case 6: ionic_kernel<6><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, yc, nn, nc, dt, I, ss, kc); break;
-        case 10: ionic_kernel<10><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, yc, nn, nc, dt, I, ss, kc); break;
-        case 15: ionic_kernel<15><<<g, kIonicThreads, 0, s>>>(U, Uprev, node_ptr, node_w, node_phi, y, yc, nn, nc, dt, I, ss, kc); break;
+        POLYDG_IONIC_CASE(3)
+        POLYDG_IONIC_CASE(6)
+        POLYDG_IONIC_CASE(10)
+        POLYDG_IONIC_CASE(15)
         default: return cudaErrorInvalidValue;
     }
+#undef POLYDG_IONIC_CASE
     return cudaGetLastError();
 }
 

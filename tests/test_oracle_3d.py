@@ -5,6 +5,7 @@ barycentric monomials, the divergence theorem facet by facet, Legendre
 orthogonality on a box, the constant and linear functions of the SIP form, a
 manufactured Neumann problem's h^(p+1) rate, and the Schwarz special cases.
 """
+import itertools
 import math
 
 import numpy as np
@@ -66,7 +67,7 @@ def test_tet_rule_barycentric_moments_to_degree_2n_minus_1():
     vol = abs(np.linalg.det(P[1:] - P[0])) / 6.0
     for n in (2, 3):
         x, w = quadrature.tet_rule(*P, n)
-        assert len(w) == n ** 3
+        assert len(w) == (14 if n == 3 else n ** 3)
         Lb = np.linalg.solve(np.vstack([P.T, np.ones(4)]), np.vstack([x.T, np.ones(len(x))]))
         for e in [(0, 0, 0, 0), (1, 0, 0, 0), (0, 0, 0, 2), (1, 1, 0, 0), (0, 1, 1, 1),
                   (2 * n - 1, 0, 0, 0), (0, 0, 0, 2 * n - 1), (0, n - 1, 0, n), (1, 1, 1, 2 * n - 4)]:
@@ -75,6 +76,36 @@ def test_tet_rule_barycentric_moments_to_degree_2n_minus_1():
             got = np.sum(w * np.prod([Lb[i] ** e[i] for i in range(4)], axis=0))
             want = 6 * vol * np.prod([math.factorial(k) for k in e]) / math.factorial(sum(e) + 3)
             assert np.isclose(got, want, rtol=1e-12), (n, e)
+
+
+def test_symmetric_tet_rule_is_exact_to_degree_5_and_no_further():
+    # every barycentric monomial of degree <= 5 on a random tetrahedron (126 of them),
+    # against 6|T| a! b! c! d! / (a + b + c + d + 3)!; positive weights, interior points,
+    # the point set closed under the vertex permutations; some degree-6 monomial is missed
+    rng = np.random.default_rng(5)
+    P = rng.standard_normal((4, 3))
+    vol = abs(np.linalg.det(P[1:] - P[0])) / 6.0
+    x, w = quadrature.tet_rule(*P, 3)
+    L, wr = quadrature.tet_symmetric_deg5()
+    assert len(w) == 14 and np.all(wr > 0) and np.all(L > 0) and np.allclose(L.sum(1), 1.0)
+    assert np.isclose(w.sum(), vol, rtol=1e-14)
+    for perm in itertools.permutations(range(4)):
+        Lp = L[:, perm]
+        for k in range(14):
+            j = np.argmin(np.abs(L - Lp[k]).sum(1))
+            assert np.abs(L[j] - Lp[k]).max() < 1e-15 and wr[j] == wr[k]
+    Lb = np.linalg.solve(np.vstack([P.T, np.ones(4)]), np.vstack([x.T, np.ones(len(x))]))
+    missed = 0
+    for e in itertools.product(range(7), repeat=4):
+        if sum(e) > 6:
+            continue
+        got = np.sum(w * np.prod([Lb[i] ** e[i] for i in range(4)], axis=0))
+        want = 6 * vol * np.prod([math.factorial(k) for k in e]) / math.factorial(sum(e) + 3)
+        if sum(e) <= 5:
+            assert np.isclose(got, want, rtol=1e-12), e
+        else:
+            missed += not np.isclose(got, want, rtol=1e-6)
+    assert missed > 0
 
 
 @pytest.mark.parametrize("p", [1, 2])
