@@ -155,14 +155,19 @@ typedef struct {
 
 /* Sizes of a preconditioner, for bandwidth accounting. */
 typedef struct {
-    int64_t local_store_bytes;   /* bytes of the stored K_i^{-1}, all subdomains */
+    int64_t local_store_bytes;   /* bytes of K_i^{-1} that one application streams,
+                                    all subdomains (the lower triangles when
+                                    rows_per_tile is 2)                         */
     int64_t coarse_bytes;        /* bytes of K_0^{-1} (float64)                  */
     int64_t restrict_bytes;      /* bytes of the stored rows of R_0 (float64)   */
     int32_t n_subdomains;
     int32_t n_coarse;            /* coarse DOFs n_0 (0: one-level)              */
     int32_t precision;           /* POLYDG_FP64/FP32/BF16                       */
     int32_t grid;                /* CTAs of the persistent PCG kernel           */
-    int32_t rows_per_tile;       /* rows of K_i^{-1} per bulk copy (1)          */
+    int32_t rows_per_tile;       /* rows of K_i^{-1} per bulk copy: 1, or 2 when
+                                    the PCG kernel streams the lower triangles as
+                                    pairs of rows m and n_i - 1 - m (FP32 store and
+                                    at least four subdomains per CTA)           */
     int32_t l2_keep_permille;    /* share of the K_i^{-1} cache lines kept in L2 across
                                     iterations (evict-last), per mille (asm_autotune) */
 } asm_info;

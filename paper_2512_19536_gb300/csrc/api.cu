@@ -189,17 +189,25 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 
         for (size_t k = 0; k < need.size(); ++k) need_aggl[k] = agg_internal[need[k]];
     P.max_need = max_need;
     P.max_aggs = max_aggs;
+    // fp32 stores with enough subdomains for every CTA to take whole ones: the P phase
+    // streams the symmetric pair-row store (half the bytes), each CTA summing the upper
+    // triangle's share of its subdomains' rows itself
+    const int NWp = kPersistThreads / 32;
+    P.sym = (pc && !batched && P.dtype == 1 && pc->d_sym && (int64_t)local_ids.size() >= 4 * (int64_t)G) ? 1 : 0;
+    P.sym_bufld = P.sym ? (pc->sym_max_n + 127) / 128 * 128 : 0;
     // shared memory: 2 tile buffers, staged r' (store type), r' and q (fp64), z (2 x rows),
     // r0/q0, p of the needed elements
     auto r128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
+    // r0s doubles as the symmetric P phase's column-sum buffer (idle there)
+    const size_t r0_bytes = std::max((size_t)n0 * 8, (size_t)(NWp + 1) * P.sym_bufld * 4);
     const size_t cap = 208 * 1024;              // + ~15 KB static shared memory of the kernel
     constexpr int kMaxRuns = 128;                // run descriptors (48 bytes) per CTA
     const size_t td_reserve = r128(kMaxRuns * 48);
-    const size_t fixed = r128((size_t)max_ld * xsz) + r128((size_t)max_ld * 8) + r128((size_t)n0 * 8) +
+    const size_t fixed = r128((size_t)max_ld * xsz) + r128((size_t)max_ld * 8) + r128(r0_bytes) +
                          r128((size_t)max_aggs * nq * 8) + r128((size_t)max_need * np * 8) + td_reserve;
     // per warp, as many one-row copy slots (up to kMaxWarpStages) as the rest leaves room for
     const int NW = kPersistThreads / 32;
-    const size_t slot = pc ? r128((size_t)max_ld * esz) : 0;
+    const size_t slot = !pc ? 0 : P.sym ? (size_t)sym_ld(pc->sym_max_n) * 4 : r128((size_t)max_ld * esz);
     const int64_t wst = (pc && fixed < cap) ? (int64_t)((cap - fixed) / (NW * slot)) : (pc ? 0 : 1);
     if (wst < 1) {
         set_error("pcg: a subdomain or coarse space is too large for the shared-memory plan");
@@ -228,12 +236,12 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 
         while (P.pair_lanes < 32 && P.pair_lanes * 16 < pc->max_pairs) P.pair_lanes *= 2;
         P.r0_split = (int64_t)pc->n_pairs * pc->nq > 8192 ? 1 : 0;
     }
-    P.rows = P.small ? 32 : 16;                  // partition granularity (rows per tile)
+    P.rows = P.small ? 32 : P.sym ? (1 << 30) : 16;   // partition granularity (rows per tile)
     const int rows = P.rows;
     P.xs_off = (size_t)NW * P.wstages * slot;
     P.rp_off = P.xs_off + r128((size_t)max_ld * xsz);
     P.r0_off = P.rp_off + r128((size_t)max_ld * 8);
-    P.y0_off = P.r0_off + r128((size_t)n0 * 8);
+    P.y0_off = P.r0_off + r128(r0_bytes);
     P.pn_off = P.y0_off + r128((size_t)max_aggs * nq * 8);
     P.td_off = P.pn_off + r128((size_t)max_need * np * 8);
     P.smem = P.td_off + td_reserve;
@@ -254,7 +262,13 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 
         const GemvBlock& B = pc->blocks[b];
         for (int r0 = 0; r0 < B.nrows; r0 += rows) {
             tiles.push_back({b, r0});
-            tbytes.push_back((int64_t)std::min(rows, B.nrows - r0) * B.ld * esz);
+            if (P.sym) {
+                int64_t sb = 0;
+                for (int q = 0; q < (B.ncols + 1) / 2; ++q) sb += 4 * (int64_t)sym_len(B.ncols, q);
+                tbytes.push_back(sb);
+            } else {
+                tbytes.push_back((int64_t)std::min(rows, B.nrows - r0) * B.ld * esz);
+            }
         }
     }
     // Split the tile sequence into G contiguous runs of about equal estimated time:
@@ -294,7 +308,7 @@ static int build_plan(polydg_ctx* c, asm_ctx* pc, int G, Plan& P, int batched = 
         int l2 = 0;
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
         const double kh = 8.0 * np * np * (double)H.col.size();
-        const double keep = (0.6 * l2 - kh) / (double)pc->store_bytes;
+        const double keep = (0.6 * l2 - kh) / (double)(P.sym ? pc->sym_bytes : pc->store_bytes);
         P.l2_keep = (float)std::max(0.0, std::min(1.0, keep));
     }
     int occ = 0;
@@ -316,6 +330,7 @@ static PersistArgs persist_args(polydg_ctx* c, asm_ctx* pc, const Plan& P, PcgWo
     a.nq = coarse ? pc->nq : 1;
     a.nc = c->H.nc;
     a.slot_bytes = P.slot_bytes;
+    a.sym_bufld = P.sym ? P.sym_bufld : 0;
     a.redundant = P.redundant;
     a.small = P.small;
     a.pair_lanes = P.pair_lanes;
@@ -345,7 +360,10 @@ static PersistArgs persist_args(polydg_ctx* c, asm_ctx* pc, const Plan& P, PcgWo
     a.runs = P.runs;
     a.run_ptr = P.run_ptr;
     a.sub_pairs = P.sub_pairs;
-    a.store = pc ? (P.dtype == 0 ? (const void*)pc->st64 : P.dtype == 1 ? (const void*)pc->st32 : (const void*)pc->st16) : nullptr;
+    a.store = pc ? (P.dtype == 0 ? (const void*)pc->st64
+                    : P.dtype == 1 ? (P.sym ? (const void*)pc->d_sym : (const void*)pc->st32)
+                                   : (const void*)pc->st16)
+                 : nullptr;
     a.st64 = pc ? pc->st64 : nullptr;
     a.K0inv = coarse ? pc->st64 + pc->off0 : nullptr;
     a.pair_ptr = coarse ? pc->d_pair_ptr : c->d_zero_ptr;
@@ -729,8 +747,32 @@ int asm_setup(polydg_ctx* c, const int32_t* coarse_of_cell, int q, int precision
                 pc->sub_pairs.push_back(b);
         B.pair_count = (int32_t)pc->sub_pairs.size() - B.pair_begin;
     }
+    // fp32 stores: the lower triangles again as pair rows (sym_ld), which the persistent
+    // kernel streams instead of the full rows when every CTA can take whole subdomains
+    int64_t sym_tot = 0;
+    if (precision == POLYDG_FP32 && H.n_sub >= 1 && H.n_sub <= 65535) {
+        int max_n = 0;
+        for (int m = 0; m < H.n_sub; ++m) max_n = std::max(max_n, (int)mats[m].n);
+        int64_t tot = 0, bytes = 0;
+        for (int m = 0; m < H.n_sub; ++m) {
+            const int n = (int)mats[m].n;
+            pc->blocks[m].sym_off = (int32_t)std::min<int64_t>(tot, INT32_MAX);
+            tot += (int64_t)((n + 1) / 2) * sym_ld(n);
+            for (int q = 0; q < (n + 1) / 2; ++q) bytes += 4 * (int64_t)sym_len(n, q);
+        }
+        if (max_n > 32 && max_n <= 128 * kSymT && tot < INT32_MAX) {
+            sym_tot = tot;
+            pc->sym_bytes = bytes;
+            pc->sym_max_n = max_n;
+        }
+    }
     pc->n_blocks = (int)pc->blocks.size();
     if ((st = upload(&pc->d_blocks, pc->blocks))) return fail(st);
+    if (sym_tot > 0 &&
+        ((st = dalloc(&pc->d_sym, sym_tot)) ||
+         (st = cu(launch_sym_pack(pc->d_blocks, H.n_sub, pc->st32, pc->d_sym, 0), "sym pack")) ||
+         (st = cu(cudaDeviceSynchronize(), "sym pack sync"))))
+        return fail(st);
     const int64_t npairs = std::max<int64_t>(pc->n_pairs, 1) * std::max(pc->nq, 1);
     if ((st = dalloc(&pc->d_r0p, npairs)) || (st = dalloc(&pc->d_y0, std::max<int64_t>(n0, 1))) ||
         (st = dalloc(&pc->d_r0g, std::max<int64_t>(n0, 1))))
@@ -914,7 +956,7 @@ int asm_get_info(const asm_ctx* pc, asm_info* out) {
         if (B.kind == KIND_LOCAL) local += (int64_t)B.nrows * B.ld * esz;
         else if (B.kind == KIND_RESTRICT) restr += (int64_t)B.nrows * B.ld * 8;
     }
-    out->local_store_bytes = local;
+    out->local_store_bytes = pc->plan.sym ? pc->sym_bytes : local;
     out->coarse_bytes = pc->has_coarse ? pc->n0 * pc->ld0 * 8 : 0;
     out->restrict_bytes = restr;
     out->n_subdomains = pc->ctx->H.n_sub;
@@ -922,7 +964,7 @@ int asm_get_info(const asm_ctx* pc, asm_info* out) {
     out->precision = pc->precision;
     out->grid = pc->plan.grid;
     out->l2_keep_permille = (int32_t)std::lround(1000.0 * pc->plan.l2_keep);
-    out->rows_per_tile = 1;                 // each bulk copy carries one row
+    out->rows_per_tile = pc->plan.sym ? 2 : 1;   // rows per bulk copy (a pair of triangle rows)
     return POLYDG_OK;
 }
 
@@ -1996,6 +2038,7 @@ void asm_destroy(asm_ctx* pc) {
     if (!pc) return;
     pc->plan.release();
     dfree(pc->d_blocks); dfree(pc->st64); dfree(pc->st32); dfree(pc->st16);
+    dfree(pc->d_sym);
     dfree(pc->d_T); dfree(pc->d_agg); dfree(pc->d_pair_ptr); dfree(pc->d_r0p);
     dfree(pc->d_y0); dfree(pc->d_r0g);
     delete pc;

@@ -99,6 +99,8 @@ struct Plan {
     int max_need = 0, max_aggs = 0;     // staged elements per chunk, agglomerates per CTA
     int cm_stages = 0;                  // K_h panel slots per warp in the CM phase (0: loads)
     size_t cm_slot_bytes = 0;
+    int sym = 0;                        // P phase from the symmetric pair-row store
+    int sym_bufld = 0;                  // floats per warp of its column-sum buffer
     std::vector<GemvTile> h_tiles;      // the tile sequence and its modelled costs (autotuning)
     std::vector<double> h_cost, h_stage;
     std::vector<int32_t> h_tile_ptr;
@@ -159,6 +161,9 @@ struct asm_ctx {
     double* d_r0p = nullptr;
     double* d_y0 = nullptr;
     int64_t store_bytes = 0;            // bytes of the dense stores read per apply
+    float* d_sym = nullptr;             // fp32 stores: lower triangles as pair rows (sym_ld)
+    int64_t sym_bytes = 0;              // bytes one apply copies from d_sym
+    int sym_max_n = 0;                  // largest subdomain of d_sym
 };
 
 // Learned initial-guess network (fp32 master weights and Adam state, fp16 copy for

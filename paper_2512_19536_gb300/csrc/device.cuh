@@ -55,8 +55,19 @@ struct GemvBlock {
     int32_t dtype;        // 0 fp64, 1 fp32, 2 bf16
     int32_t pair_begin;   // LOCAL: first entry of its RESTRICT blocks in the sub_pairs list
     int32_t pair_count;   // LOCAL: number of (agglomerate, subdomain) pairs of this subdomain
-    int32_t pad;
+    int32_t sym_off;      // LOCAL, fp32 stores: first float of its pair rows in the symmetric store
 };
+
+// Symmetric pair-row store of an n x n local inverse (the P phase of the persistent PCG
+// kernel with fp32 stores): pair m < (n + 1) / 2 holds row m of the lower triangle
+// (columns 0..m, zero-padded to a multiple of 4), then row n - 1 - m (columns 0..n-1-m,
+// zero-padded likewise; empty when n - 1 - m == m), diagonal entries halved.  Pair rows sit sym_ld(n) floats
+// apart; a copy of pair m carries sym_len(n, m) floats (16-byte multiples throughout).
+__host__ __device__ __forceinline__ int sym_ld(int n) { return (n + 10) & ~3; }
+__host__ __device__ __forceinline__ int sym_len(int n, int m) {
+    return ((m + 4) & ~3) + (n - 1 - m != m ? ((n - m + 3) & ~3) : 0);
+}
+constexpr int kSymT = 5;                      // float4 column groups per lane: n <= 128 kSymT
 
 struct GemvTile {
     int32_t block;

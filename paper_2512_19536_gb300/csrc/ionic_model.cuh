@@ -37,6 +37,18 @@ constexpr double gamma = 0.0445, beta = 7.0, tau = 1000.0;
 constexpr double Cli = 6.0, Clo = 130.0, gCa = 0.1, ECa = 120.0, RTF = 26.64;
 constexpr int kStates = 5;
 
+// |x| < t for t > 0, as an integer comparison of the bit patterns (non-negative doubles
+// order like their patterns; NaN and infinities compare false as with fabs): on this GPU a
+// double comparison takes a slot of the narrow fp64 pipe that bounds the node update.
+BC_HD bool abs_below(double x, double t) {
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)(__double_as_longlong(x) & 0x7fffffffffffffffLL) <
+           (unsigned long long)__double_as_longlong(t);
+#else
+    return std::fabs(x) < t;
+#endif
+}
+
 // x / (1 - exp(-x/s)); the removable point x = 0 takes its first-order limit.
 BC_HD double lin_exp(double x, double s) {
     if (fabs(x / s) < 1e-6) return s * (1.0 + 0.5 * x / s);
@@ -112,9 +124,8 @@ BC_HD void vpowers_m(double V, double& e10, double& e18) {
 // function.  For the ratio of an exponential at two nearby arguments (the concentrations
 // move by ~1e-6 relative per step, the potential by up to a few mV).
 BC_HD double exp_small(double a) {
-    const double fa = fabs(a);
-    if (fa < 0x1p-18) return 1.0 + a * (1.0 + a * (0.5 + a * (1.0 / 6.0)));
-    if (fa < 0x1p-6)
+    if (abs_below(a, 0x1p-18)) return 1.0 + a * (1.0 + a * (0.5 + a * (1.0 / 6.0)));
+    if (abs_below(a, 0x1p-6))
         return 1.0 + a * (1.0 + a * (0.5 + a * (1.0 / 6.0 + a * (1.0 / 24.0 + a * (1.0 / 120.0 +
                      a * (1.0 / 720.0 + a * (1.0 / 5040.0)))))));
     return exp(a);
@@ -142,9 +153,8 @@ BC_HD void batch_reciprocal(const double (&x)[M], double (&inv)[M]) {
 // ln(1 + a): the Taylor series, three terms for |a| < 2^-18 (relative error < a^3 / 4 <
 // 2e-17) and six for |a| < 2^-10 (< a^6 / 7 < 2e-19), else the library function.
 BC_HD double log1p_small(double a) {
-    const double fa = fabs(a);
-    if (fa < 0x1p-18) return a - a * a * (0.5 - a * (1.0 / 3.0));
-    if (fa < 0x1p-10) {
+    if (abs_below(a, 0x1p-18)) return a - a * a * (0.5 - a * (1.0 / 3.0));
+    if (abs_below(a, 0x1p-10)) {
         const double a2 = a * a;
         return a - a2 * (0.5 - a * (1.0 / 3.0 - a * (0.25 - a * (0.2 - a * (1.0 / 6.0)))));
     }
@@ -153,7 +163,7 @@ BC_HD double log1p_small(double a) {
 
 // x / (1 - ex) for ex = exp(-x/s) given; the removable point x = 0 takes its limit.
 BC_HD double lin_exp_given(double x, double s, double ex) {
-    if (fabs(x) < 1e-6 * s) return s + 0.5 * x;
+    if (abs_below(x, 1e-6 * s)) return s + 0.5 * x;
     return x / (1.0 - ex);
 }
 
@@ -187,7 +197,7 @@ BC_HD void rates(const NodeConsts& k, double V, double n, double h, double Ko, d
                  double* d, Nernst* ne = nullptr, const NodeCache* c = nullptr) {
     const VPowers p = CACHED ? vpowers_from(c->B) : vpowers(V);
     const double xn = V + 34.0, xm = V + 30.0;
-    const bool sn = fabs(xn) < 1e-5, sm = fabs(xm) < 1e-5;       // |x| < 1e-6 s, s = 10
+    const bool sn = abs_below(xn, 1e-5), sm = abs_below(xm, 1e-5);   // |x| < 1e-6 s, s = 10
     const double exn = k.an * p.e10, exm = k.am * p.e10;
     const double bm = k.bm * p.e18;
     // m_inf = am / (am + bm), am = 0.1 xm / (1 - exm): 0.1 xm / (0.1 xm + bm (1 - exm))
@@ -236,7 +246,7 @@ BC_HD void minf_parts_b(const NodeConsts& k, double V, double B, double& num, do
     double e10, e18;
     vpowers_m_from(B, e10, e18);
     const double xm = V + 30.0;
-    const bool sm = fabs(xm) < 1e-5;
+    const bool sm = abs_below(xm, 1e-5);
     const double exm = k.am * e10, bm = k.bm * e18;
     num = sm ? 0.1 * (10.0 + 0.5 * xm) : 0.1 * xm;
     den = num + bm * (sm ? 1.0 : 1.0 - exm);

@@ -119,7 +119,10 @@ struct PersistArgs {
     uint32_t wait_limit;                       // polls of a grid barrier before it gives up
     int cm_stages;                             // CM phase: K_h panel slots per warp (0: loads)
     int cm_slot_bytes;
-    int pad_cm;
+    int sym_bufld;                             // > 0: the P phase streams the symmetric pair-row
+                                               // store (fp32, whole subdomains per CTA; store
+                                               // points at it); floats per warp of its
+                                               // column-sum buffer at r0_off
 };
 
 constexpr int kMaxWarpStages = 4;              // copy slots per warp in the P phase
@@ -221,6 +224,10 @@ cudaError_t launch_pcg_persistent(int dtype, int np, const PersistArgs& a, size_
 cudaError_t launch_pcg_batched(int dtype, int np, const PersistArgs* args_dev, const int2* map_dev,
                                int n_cta, size_t smem, cudaStream_t s);
 cudaError_t persistent_occupancy(int dtype, int np, size_t smem, int* blocks_per_sm, int batched);
+// The symmetric pair-row store of the fp32 local inverses (LOCAL blocks 0..n_local-1,
+// each at its sym_off).
+cudaError_t launch_sym_pack(const GemvBlock* blocks, int n_local, const float* st32, float* sym,
+                            cudaStream_t s);
 // Lockstep groups (kernels_group.cu): one cooperative launch of n_cta CTAs, CTA b runs
 // as CTA map[b].y of group map[b].x (args on the device).  qdtype 1 fp32, 2 bf16 store.
 cudaError_t launch_pcg_groups(int qdtype, int np, const GroupArgs* args_dev, const int2* map_dev,

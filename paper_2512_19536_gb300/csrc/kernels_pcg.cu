@@ -56,6 +56,7 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
     const double rtol2 = sc->rtol2;
     const int maxit = sc->maxit;
     const bool apply = a.apply_only != 0;
+    const bool sym = DT == 1 && CMS && a.sym_bufld > 0;   // P phase from the symmetric pair-row store
     const uint32_t wl = a.wait_limit;
     // Pipelined PCG (sc->flexible == 2; Ghysels and Vanroose's rearrangement): per iteration
     // the P phase applies the local solves to w and sums gamma = r.u, delta = w.u and |r|^2 in
@@ -138,10 +139,16 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
             d.block = rn.block;
             d.pair_begin = B.pair_begin;
             d.pair_count = B.pair_count;
+            if (sym) {                            // whole subdomain: its pair rows
+                d.mat_off = B.sym_off;
+                d.row_begin = 0;
+                d.row_end = (B.ncols + 1) / 2;
+                d.ld = sym_ld(B.ncols);
+            }
             d.ord = n_rows;
             rd[k] = d;
         }
-        n_rows += rn.row_end - rn.row_begin;
+        n_rows += sym ? (rn.row_end - rn.row_begin + 1) / 2 : rn.row_end - rn.row_begin;
     }
     const bool has_rows = warp < n_rows;
     const int rows_w = has_rows ? (n_rows - 1 - warp) / NW + 1 : 0;   // this warp's rows per P phase
@@ -164,8 +171,12 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
     const uint64_t l2pol = stream_policy(a.l2_keep);
     auto issue = [&](int k) {
         const RunDesc& d = rd[iss_run];
-        bulk_load(slot(warp, k), reinterpret_cast<const T*>(a.store) + d.mat_off + (int64_t)iss_row * d.ld,
-                  (uint32_t)((size_t)d.ld * sizeof(T)), &wbars[warp][k], l2pol);
+        if (sym)
+            bulk_load(slot(warp, k), reinterpret_cast<const float*>(a.store) + d.mat_off + (int64_t)iss_row * d.ld,
+                      (uint32_t)(sym_len(d.ncols, iss_row) * sizeof(float)), &wbars[warp][k], l2pol);
+        else
+            bulk_load(slot(warp, k), reinterpret_cast<const T*>(a.store) + d.mat_off + (int64_t)iss_row * d.ld,
+                      (uint32_t)((size_t)d.ld * sizeof(T)), &wbars[warp][k], l2pol);
         iss_row += NW;
         while (iss_row >= rd[iss_run].row_end) {
             const int over = iss_row - rd[iss_run].row_end;
@@ -308,17 +319,20 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 // r' of the run's subdomain (all its DOFs: the product's input), and
                 // the commit of the run's own rows: p_k, q_k, x += alpha p_k, r'
                 __syncthreads();                  // the previous run's readers of xs / rp are done
-                for (int j = threadIdx.x; j < rn.ld; j += blockDim.x) {
+                // (symmetric store: the run is the whole subdomain, every DOF its own)
+                const int xlen = sym ? (rn.ncols + 3) & ~3 : rn.ld;
+                for (int j = threadIdx.x; j < xlen; j += blockDim.x) {
                     double r_ = 0.0;
+                    const bool own = sym || (j >= rn.row_begin && j < rn.row_end);
                     if (j < rn.ncols && pipe) {
                         const int64_t t = rn.in_off + j;
                         r_ = __ldcg(vin + t);
-                        if (!pinit && j >= rn.row_begin && j < rn.row_end) pdots(t);
+                        if (!pinit && own) pdots(t);
                     } else if (j < rn.ncols) {
                         const int64_t t = rn.in_off + j;
                         const double qk = fma(be, __ldcg(qold + t), __ldcg(a.w + t));
                         r_ = fma(-al, qk, __ldcg(rin + t));
-                        if (j >= rn.row_begin && j < rn.row_end) {
+                        if (own) {
                             const double pk = fma(be, __ldcg(pold + t), __ldcg(a.z + t));
                             pnew[t] = pk;
                             qnew[t] = qk;
@@ -352,6 +366,47 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
                 // this warp's rows of the run: z_loc = row . r'
                 const X* xin = (DT == 0) ? reinterpret_cast<const X*>(rp) : xs;
                 const int k0 = ((warp - rn.ord) % NW + NW) % NW;
+                if constexpr (DT == 1 && CMS) {
+                    if (sym) {                    // pair rows; column sums in registers
+                        float4 cacc[kSymT];
+                        // row sums: one per row, each written once (after the warps' buffers)
+                        float* rsum = reinterpret_cast<float*>(smem + a.r0_off) + NW * a.sym_bufld;
+#pragma unroll
+                        for (int t = 0; t < kSymT; ++t) cacc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        for (int row = k0; row < rn.row_end; row += NW, ++wseq) {
+                            const int k = wseq % S;
+                            if (!wfail && !mbar_wait(&wbars[warp][k], (wseq / S) & 1)) {
+                                wfail = true;
+                                if (lane == 0) atomicExch(a.err, 1);
+                            }
+                            if (wfail) continue;
+                            ++n_done;
+                            sym_pair(reinterpret_cast<const float*>(slot(warp, k)), xs, rn.ncols, row, lane, cacc,
+                                     rsum);
+                            __syncwarp();         // every lane is done with the slot
+                            if (!CMS || iss_left > 0) {
+                                if (lane == 0) issue(k);
+                                ++n_issued;
+                                --iss_left;
+                            }
+                        }
+                        // z_loc: the row sum and the warps' column sums in warp order
+                        // (deterministic); the buffers are in r0s, idle until the coarse phase
+                        float* buf = reinterpret_cast<float*>(smem + a.r0_off);
+                        __syncthreads();
+#pragma unroll
+                        for (int t = 0; t < kSymT; ++t)
+                            if (128 * t < rn.ncols)
+                                *reinterpret_cast<float4*>(buf + warp * a.sym_bufld + 128 * t + 4 * lane) = cacc[t];
+                        __syncthreads();
+                        for (int j = threadIdx.x; j < rn.ncols; j += blockDim.x) {
+                            float sv = rsum[j];
+                            for (int w = 0; w < NW; ++w) sv += buf[w * a.sym_bufld + j];
+                            a.zl[rn.in_off + j] = (double)sv;
+                        }
+                        continue;
+                    }
+                }
                 for (int row = rn.row_begin + k0; row < rn.row_end; row += NW, ++wseq) {
                     const int k = wseq % S;
                     if (!wfail && !mbar_wait(&wbars[warp][k], (wseq / S) & 1)) {
@@ -704,6 +759,37 @@ __device__ __forceinline__ void pcg_solve_cta(const PersistArgs& a, const int ct
         sc->done = done ? done : 1;
         sc->pass = 0;
     }
+}
+
+// The symmetric pair-row store (sym_ld / sym_len) of the fp32 local inverses, block
+// blockIdx.y: the lower triangles of the stored rows (the inverse is symmetric; its lower
+// triangle defines it), the diagonal entries halved (exact: the P phase adds each of them
+// twice, once in its row's sum and once in its column's).
+__global__ void sym_pack_kernel(const GemvBlock* __restrict__ blocks, const float* __restrict__ st32,
+                                float* __restrict__ sym) {
+    const GemvBlock B = blocks[blockIdx.y];
+    const int n = B.ncols, ld = sym_ld(n), npair = (n + 1) / 2;
+    const int64_t total = (int64_t)npair * ld;
+    float* dst = sym + B.sym_off;
+    const float* src = st32 + B.mat_off;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i / ld), c = (int)(i % ld);
+        const int la = (m + 4) & ~3, b = n - 1 - m;
+        float v = 0.f;
+        if (c < la) {
+            if (c <= m) v = src[(int64_t)m * B.ld + c] * (c == m ? 0.5f : 1.f);
+        } else if (b != m && c - la <= b) {
+            v = src[(int64_t)b * B.ld + (c - la)] * (c - la == b ? 0.5f : 1.f);
+        }
+        dst[i] = v;
+    }
+}
+
+cudaError_t launch_sym_pack(const GemvBlock* blocks, int n_local, const float* st32, float* sym,
+                            cudaStream_t s) {
+    if (n_local < 1 || n_local > 65535) return cudaErrorInvalidValue;
+    sym_pack_kernel<<<dim3(32, n_local), 256, 0, s>>>(blocks, st32, sym);
+    return cudaGetLastError();
 }
 
 // One solve on all CTAs of the launch.

@@ -226,6 +226,48 @@ __device__ __forceinline__ float fma_x(float a, float b, float c) { return fmaf(
 
 // What the P phase needs of one run (contiguous rows of one subdomain's local
 // inverse), staged in shared memory at kernel start.
+// One pair row of the symmetric store (rows m and n-1-m of the lower triangle of an
+// n x n fp32 local inverse A, the diagonal entries halved, see sym_ld) against the staged
+// r' in x (zero past n): lane l keeps the sums of columns 128 t + 4 l .. + 3 in acc[t].
+// Each entry a_mk of row m adds a_mk x_m to column k (the upper triangle's share of row
+// k), and the row's own sum_{k <= m} a_mk x_k goes to rsum[m]; the halved diagonal enters
+// both, so once every pair of the subdomain is done, rsum[j] plus column j is
+// sum_k a_jk x_k over the whole row j.
+template <int TT>
+__device__ __forceinline__ void sym_pair(const float* A, const float* x, int n, int m, int lane,
+                                         float4 (&acc)[TT], float* rsum) {
+    const int b = n - 1 - m;
+    const int la = (m + 4) & ~3;
+    const float xm = x[m], xb = x[b];
+    float dA = 0.f, dB = 0.f;
+#pragma unroll
+    for (int t = 0; t < TT; ++t) {
+        const int c = 128 * t + 4 * lane;
+        if (128 * t < la && c < la) {
+            const float4 u = *reinterpret_cast<const float4*>(A + c);
+            const float4 v = *reinterpret_cast<const float4*>(x + c);
+            dA = fmaf(u.x, v.x, dA); dA = fmaf(u.y, v.y, dA);
+            dA = fmaf(u.z, v.z, dA); dA = fmaf(u.w, v.w, dA);
+            acc[t].x = fmaf(u.x, xm, acc[t].x); acc[t].y = fmaf(u.y, xm, acc[t].y);
+            acc[t].z = fmaf(u.z, xm, acc[t].z); acc[t].w = fmaf(u.w, xm, acc[t].w);
+        }
+        if (b != m && 128 * t <= b && c <= b) {
+            const float4 u = *reinterpret_cast<const float4*>(A + la + c);
+            const float4 v = *reinterpret_cast<const float4*>(x + c);
+            dB = fmaf(u.x, v.x, dB); dB = fmaf(u.y, v.y, dB);
+            dB = fmaf(u.z, v.z, dB); dB = fmaf(u.w, v.w, dB);
+            acc[t].x = fmaf(u.x, xb, acc[t].x); acc[t].y = fmaf(u.y, xb, acc[t].y);
+            acc[t].z = fmaf(u.z, xb, acc[t].z); acc[t].w = fmaf(u.w, xb, acc[t].w);
+        }
+    }
+    dA = warp_sumf(dA);
+    dB = warp_sumf(dB);
+    if (lane == 0) {
+        rsum[m] = dA;
+        if (b != m) rsum[b] = dB;
+    }
+}
+
 struct RunDesc {
     int64_t mat_off;      // element offset of the block in the store
     int64_t in_off;       // first DOF of the block's subdomain
