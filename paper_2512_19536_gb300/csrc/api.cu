@@ -1245,6 +1245,8 @@ static GuessFeat guess_features(const polydg_ctx* c, const guess_model* g) {
     f.h_ref = g->scales[3];
     f.dt_ref = g->scales[4];
     f.dt = c->H.dt;
+    f.inv_s_u = 1.0 / f.s_u;
+    f.inv_s_d = 1.0 / f.s_d;
     return f;
 }
 

@@ -13,7 +13,9 @@ __host__ __device__ constexpr int guess_inputs(int np) { return 9 * np + 3; }
 // Features of element e into x[0 .. 9 NP + 3) (fp32), by one warp: lane l handles
 // component l of the own vector [a | d1 | d2] and its mean and max over the face
 // neighbours (the blocks of row e of K_h after the diagonal one).  off(c) is the
-// position of cell c's first coefficient in the U arrays.
+// position of cell c's first coefficient in the U arrays.  The scales enter as
+// reciprocals: a division costs GB300's narrow fp64 pipe about ten times a product, and
+// the features are rounded to fp16 afterwards.
 template <int NP, typename Off>
 __device__ __forceinline__ void element_features(const GuessFeat& f, const double* __restrict__ Uk,
                                                  const double* __restrict__ Uk1,
@@ -23,9 +25,9 @@ __device__ __forceinline__ void element_features(const GuessFeat& f, const doubl
     auto own = [&](int64_t cell, int l) {
         const int grp = l / NP, j = l - grp * NP;
         const int64_t o = off(cell) + j;
-        if (grp == 0) return (Uk[o] - (j == 0 ? f.u_rest : 0.0)) / f.s_u;
-        if (grp == 1) return (Uk[o] - Uk1[o]) / f.s_d;
-        return (Uk1[o] - Uk2[o]) / f.s_d;
+        if (grp == 0) return (Uk[o] - (j == 0 ? f.u_rest : 0.0)) * f.inv_s_u;
+        if (grp == 1) return (Uk[o] - Uk1[o]) * f.inv_s_d;
+        return (Uk1[o] - Uk2[o]) * f.inv_s_d;
     };
     const int32_t b0 = f.row_ptr[e], b1 = f.row_ptr[e + 1];
     const int cnt = b1 - b0 - 1;

@@ -267,6 +267,7 @@ struct GuessFeat {
     const int32_t* col;
     const double* diam;        // [nc] internal order
     double u_rest, s_u, s_d, h_ref, dt_ref, dt;
+    double inv_s_u, inv_s_d;   // 1 / s_u, 1 / s_d (products instead of divisions on the narrow fp64 pipe)
 };
 int guess_param_count(int np);
 size_t guess_train_smem(int np);

@@ -3,8 +3,9 @@ JSON line per step (PCG iterations, relative residual, device time of the PCG la
 
 A small driver for profilers and quick checks: it sets up the workload, the
 preconditioner in the chosen precision (fp32/bf16 local inverses run flexible PCG) and
-the initial-guess policy, then steps one step per call, so the n-th launch of each kernel
-belongs to step n.  Workloads: hex<N> (N^3 jittered hexahedra, P2, subdomains of 4^3
+the initial-guess policy (--guess: with the trained network's proposal, as bench.py's
+measured form), then steps one step per call, so the n-th launch of each kernel belongs
+to step n.  Workloads: hex<N> (N^3 jittered hexahedra, P2, subdomains of 4^3
 cells = coarse agglomerates, coarse P1), voronoi<N> (N-cell Voronoi mesh, P3, k-means
 subdomains of ~64 cells = coarse agglomerates, coarse P1).
 
@@ -41,6 +42,8 @@ def main(argv=None):
     ap.add_argument("--ionic-form", choices=["nodal", "modal"], default="nodal")
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--shared-rhs", type=int, default=0)
+    ap.add_argument("--guess", action="store_true",
+                    help="the trained network (guess_p3_voronoi4096.npz) as the learned proposal")
     a = ap.parse_args(argv)
     import torch
     w = make_workload(a.workload)
@@ -52,8 +55,14 @@ def main(argv=None):
                         flexible=a.precision != "fp64")
     if a.ionic_form != "nodal":
         pd.sim_set_ionic_form(sim, a.ionic_form)
+    guess = None
+    if a.guess:
+        import os
+        import numpy as np
+        z = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "guess_p3_voronoi4096.npz"))
+        guess = pd.guess_create(int(z["n_p"]), z["params"], z["scales"])
     if a.policy >= 0:
-        pd.sim_set_guess(sim, None, a.policy)
+        pd.sim_set_guess(sim, guess, a.policy)
     stream = torch.cuda.current_stream()
     for k in range(a.steps):
         st = pd.monodomain_step(sim, 1, stream=stream)
@@ -61,6 +70,8 @@ def main(argv=None):
                           "relres": st["last_relres"], "pcg_ms": 1e3 * st["pcg_seconds"],
                           "status": st["status"]}), flush=True)
     sim.close()
+    if guess is not None:
+        guess.close()
     pc.close()
     ctx.close()
 
