@@ -38,7 +38,7 @@ constexpr double Cli = 6.0, Clo = 130.0, gCa = 0.1, ECa = 120.0, RTF = 26.64;
 constexpr int kStates = 5;
 
 // |x| < t for t > 0, as an integer comparison of the bit patterns (non-negative doubles
-// order like their patterns; NaN and infinities compare false as with fabs): on this GPU a
+// order like their patterns; NaN and infinities compare false as with fabs): on GB300 a
 // double comparison takes a slot of the narrow fp64 pipe that bounds the node update.
 BC_HD bool abs_below(double x, double t) {
 #ifdef __CUDA_ARCH__
