@@ -198,6 +198,33 @@ def time_form(pd, torch, w, ctx, precision, flexible, steps, warmup, stream, clo
     return pc, sim, st, ms
 
 
+class HostHistory:
+    """The last H solutions of one simulation in pinned host memory, kept as a ring (row
+    `head` the newest, then older ones upwards, wrapping): a new solution is written into
+    the row that the oldest one held, so no step shifts the history on the host.
+    `upload` copies the rows to a device [H, n] tensor newest first (two copies where the
+    ring wraps); `push_from` reads a solution into the ring (non-blocking from a device
+    tensor: the caller synchronises before the next upload)."""
+
+    def __init__(self, torch, H, n, pin=True):
+        ring = torch.zeros((H, n), dtype=torch.float64)
+        self.ring = ring.pin_memory() if pin else ring
+        self.H = H
+        self.head = 0
+        self.count = 0
+
+    def push_from(self, src, non_blocking=False):
+        self.head = (self.head - 1) % self.H
+        self.ring[self.head].copy_(src, non_blocking=non_blocking)
+        self.count = min(self.H, self.count + 1)
+
+    def upload(self, dst):
+        a = self.H - self.head
+        dst[:a].copy_(self.ring[self.head:], non_blocking=True)
+        if self.head:
+            dst[a:].copy_(self.ring[:self.head], non_blocking=True)
+
+
 def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None, warm=12, ionic_form="nodal"):
     """Same metric with the state crossing the host boundary every step: the last
     solutions the step depends on (U^k .. U^{k-24}: the initial guess reads them) copied in
@@ -211,31 +238,22 @@ def time_e2e(pd, torch, w, ctx, pc, steps, stream, guess=None, warm=12, ionic_fo
     pd.sim_set_guess(sim, guess, GUESS_POLICY)
     n = ctx.n_dofs
     H = 25
-    host_hist = torch.empty((H, n), dtype=torch.float64).pin_memory()   # row 0 = U^k
+    hist = HostHistory(torch, H, n)                 # U^k, U^{k-1}, ... in pinned host memory
     dev_hist = torch.empty((H, n), dtype=torch.float64, device="cuda")
     dev_u = torch.empty(n, dtype=torch.float64, device="cuda")
-    host_new = torch.empty(n, dtype=torch.float64).pin_memory()
-    sols = []
     for _ in range(warm):
         pd.monodomain_step(sim, 1, stream)
         pd.sim_get_state(sim, dev_u, stream=stream)
-        sols.append(dev_u.cpu())
-    host_hist.zero_()
-    for h in range(min(H, len(sols))):
-        host_hist[h].copy_(sols[-1 - h])
-    count = min(H, len(sols))
+        hist.push_from(dev_u.cpu())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        dev_hist.copy_(host_hist, non_blocking=True)
-        pd.sim_set_history(sim, dev_hist[:count], stream)
-        count = min(H, count + 1)
+        hist.upload(dev_hist)
+        pd.sim_set_history(sim, dev_hist[:hist.count], stream)
         pd.monodomain_step(sim, 1, stream)
         pd.sim_get_state(sim, dev_u, stream=stream)
-        host_new.copy_(dev_u, non_blocking=True)
+        hist.push_from(dev_u, non_blocking=True)
         torch.cuda.synchronize()
-        host_hist[1:].copy_(host_hist[:-1].clone())
-        host_hist[0].copy_(host_new)
     dt = time.perf_counter() - t0
     sim.close()
     return steps / dt, H * 8 * n, 8 * n
@@ -677,10 +695,9 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
     sims = [x[2] for x in trip]
     n_all = sum(ctx.n_dofs for ctx, _, _ in trip)
     H = 25
-    hh = [torch.zeros((H, ctx.n_dofs), dtype=torch.float64).pin_memory() for ctx, _, _ in trip]
+    hh = [HostHistory(torch, H, ctx.n_dofs) for ctx, _, _ in trip]
     dh = [torch.empty((H, ctx.n_dofs), dtype=torch.float64, device="cuda") for ctx, _, _ in trip]
     du = [torch.empty(ctx.n_dofs, dtype=torch.float64, device="cuda") for ctx, _, _ in trip]
-    hn = [torch.empty(ctx.n_dofs, dtype=torch.float64).pin_memory() for ctx, _, _ in trip]
     # a fresh batch of the same form, its warm-up steps recorded on the host
     del bt
     trip_e = make("fp32", True, True)
@@ -689,34 +706,27 @@ def bench_batch(args, pd, torch, stream, rank, world, local):
             pd.sim_set_shared_local(trip_e[k][2], shared[m0 // per_mesh])
     sims = [x[2] for x in trip_e]
     bt = pd.batch_create(sims)
-    count = 0
     for _ in range(args.warmup):
         pd.batch_step(bt, 1, stream)
         for s_, d_, h_ in zip(sims, du, hh):
             pd.sim_get_state(s_, d_, stream=stream)
-            h_[1:].copy_(h_[:-1].clone())
-            h_[0].copy_(d_)
-        count = min(H, count + 1)
+            h_.push_from(d_)
     torch.cuda.synchronize()
     e_steps = steps
     t0 = time.perf_counter()
     for _ in range(e_steps):
         for s_, d_, h_ in zip(sims, dh, hh):
-            d_.copy_(h_, non_blocking=True)
-            pd.sim_set_history(s_, d_[:count], stream)
+            h_.upload(d_)
+            pd.sim_set_history(s_, d_[:h_.count], stream)
         pd.batch_step(bt, 1, stream)
-        for s_, d_, h_ in zip(sims, du, hn):
+        for s_, d_, h_ in zip(sims, du, hh):
             pd.sim_get_state(s_, d_, stream=stream)
-            h_.copy_(d_, non_blocking=True)
+            h_.push_from(d_, non_blocking=True)
         torch.cuda.synchronize()
-        for h_, n_ in zip(hh, hn):
-            h_[1:].copy_(h_[:-1].clone())
-            h_[0].copy_(n_)
-        count = min(H, count + 1)
     e2e_rate = S * e_steps / (time.perf_counter() - t0)
     groups = bt.groups().tolist()
     bt.close()
-    del trip, trip_e, sims, shared, du, dh, hh, hn
+    del trip, trip_e, sims, shared, du, dh, hh
     torch.cuda.empty_cache()
     # the same simulations with their own fp32 local inverses, one CTA group each
     trip32 = make("fp32", True, True)
